@@ -1,0 +1,375 @@
+/*
+ * Plain CPU FP64 oracle for replica-averaged Brownian dynamics
+ * (Kania, Nguyen, Oztekin & Webb, "Replica-Averaging", arXiv 2206.05851).
+ *
+ * TEST INFRASTRUCTURE ONLY: the slow, obviously-correct reference for the
+ * CUDA path. It is loaded by the tests, the smoke check and the benchmark's
+ * CPU-baseline leg, and by nothing in the product library. It shares no
+ * source with the CUDA path.
+ *
+ * What it follows:
+ *   - Eq. 1 (Sec. II): Euler-Maruyama update of every bead, taken literally in
+ *     the laboratory frame, with the free-draining diffusion tensor of Eq. 2
+ *     (D_ij = delta_ij kT/zeta I; no hydrodynamic interaction).
+ *   - Eq. 4 (Sec. II): the instantaneous spring force (ISF) of a spring,
+ *     here the magnitude of the spring-law force.
+ *   - Sec. II, "Computing ISF, TSF and RSF": TSF is the mean of per-step
+ *     samples over the sampling time S; RSF halts the parent, forms N_R
+ *     replicas of it, each with its own noise stream, evolves them for S,
+ *     takes ONE force sample per replica at the end and averages over the
+ *     replicas, then continues the parent.
+ *   - Sec. I and Sec. III (vWF kinetics): events from a force criterion,
+ *     either a threshold rupture force or the Bell rate k = k0 exp(f dx / kT)
+ *     with the survival integral exp(-int k dt).
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   FENE law F = H Q / (1 - H Q^2 / b); noise from Philox4x32-10 keyed by
+ *   (bead, slot | stream << 24, step, chain) with key = seed; Box-Muller;
+ *   FENE floor s_min on 1 - H Q^2 / b; TSF samples taken after each of the S
+ *   updates of a window; hazard of a window force held constant over the
+ *   window; first passage when the integrated hazard reaches an Exp(1) draw.
+ *
+ * Every function here is pinned by physics or by published values in the
+ * CPU part of the test-suite.
+ */
+#include "bd_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORA_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, Salmon et al. SC'11, Sec. 4: a 4-word counter and 2-word   */
+/* key; each round multiplies words 0 and 2 by fixed constants, XORs the    */
+/* high halves with the other two words and the round key, and permutes;    */
+/* the key is bumped by the Weyl constants between rounds.                  */
+/* ------------------------------------------------------------------------ */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double ora_uniform(uint32_t x)
+{
+    return ((double)x + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* Box-Muller (1958): two uniforms -> two independent standard normals. The
+ * random displacement R_i of Eq. 1 needs three per bead: the first pair and
+ * the cosine branch of the second pair. */
+void ora_normals3(uint64_t seed, uint32_t bead, uint32_t slot, uint32_t stream,
+                  uint32_t step, uint32_t chain, double xi[3])
+{
+    uint32_t ctr[4] = { bead, slot | (stream << 24), step, chain };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t x[4];
+    ora_philox4x32_10(ctr, key, x);
+    double u0 = ora_uniform(x[0]), u1 = ora_uniform(x[1]);
+    double u2 = ora_uniform(x[2]), u3 = ora_uniform(x[3]);
+    double rho0 = sqrt(-2.0 * log(u0));
+    double rho1 = sqrt(-2.0 * log(u2));
+    xi[0] = rho0 * cos(2.0 * ORA_PI * u1);
+    xi[1] = rho0 * sin(2.0 * ORA_PI * u1);
+    xi[2] = rho1 * cos(2.0 * ORA_PI * u3);
+}
+
+/* Exp(1) threshold of the first-passage test: E = -ln u, one uniform from the
+ * second Philox stream, counter (spring, stream << 24, criterion, chain). */
+double ora_exp1(uint64_t seed, uint32_t spring, uint32_t criterion, uint32_t chain)
+{
+    uint32_t ctr[4] = { spring, (uint32_t)ORA_STREAM_EXP1 << 24, criterion, chain };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t x[4];
+    ora_philox4x32_10(ctr, key, x);
+    return -log(ora_uniform(x[0]));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spring laws. Hookean: F = H Q. FENE (Warner): F = H Q / (1 - H Q^2 / b),   */
+/* the gradient of U = -(b/2) ln(1 - H Q^2 / b). F is the force on the lower */
+/* bead of the spring, pointing towards the upper bead.                      */
+/* ------------------------------------------------------------------------ */
+int ora_spring_force(int spring, double H, double b, double s_min, const double Q[3],
+                     double F[3], double* tension)
+{
+    double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+    double coef = H;
+    int floored = 0;
+    if (spring == ORA_SPRING_FENE) {
+        double s = 1.0 - H * q2 / b;
+        if (s < s_min) { s = s_min; floored = 1; }
+        coef = H / s;
+    }
+    F[0] = coef * Q[0];
+    F[1] = coef * Q[1];
+    F[2] = coef * Q[2];
+    if (tension) *tension = coef * sqrt(q2);
+    return floored;
+}
+
+/* Homogeneous flows v = kappa . r. Shear as in Sec. II: v = gdot z x_hat
+ * (x flow direction, z gradient direction). Uniaxial elongation:
+ * rate * diag(1, -1/2, -1/2). Planar elongation: rate * diag(1, -1, 0). */
+void ora_flow_gradient(int flow, double rate, double kappa[9])
+{
+    for (int i = 0; i < 9; ++i) kappa[i] = 0.0;
+    switch (flow) {
+    case ORA_FLOW_SHEAR:    kappa[0 * 3 + 2] = rate; break;
+    case ORA_FLOW_UNIAXIAL: kappa[0] = rate; kappa[4] = -0.5 * rate; kappa[8] = -0.5 * rate; break;
+    case ORA_FLOW_PLANAR:   kappa[0] = rate; kappa[4] = -rate; break;
+    default: break;
+    }
+}
+
+/* Eq. 1 with Eq. 2 (free draining): each bead moves with the solvent velocity
+ * at its position plus D/kT times the spring force on it, plus a random
+ * displacement of covariance 2 D dt. kT = 1 and D = kT/zeta = 1/4 in Hookean
+ * units. The spring force on bead i is F_i - F_{i-1} (F_i: force of spring i,
+ * which joins beads i and i+1; F_{-1} = F_{N-1} = 0). Every drift is taken at
+ * time t, so the increments are formed first and applied afterwards.
+ * Returns the number of springs whose FENE floor applied. */
+int64_t ora_em_step(const ora_chain* ch, double dt, double s_min, double* r, const double* xi)
+{
+    const double D = 0.25, kT = 1.0;
+    const int N = ch->n_beads;
+    double kappa[9];
+    ora_flow_gradient(ch->flow, ch->rate, kappa);
+    double* F = (double*)calloc(3 * (size_t)N, sizeof(double));
+    double* inc = (double*)calloc(3 * (size_t)N, sizeof(double));
+    int64_t floored = 0;
+    for (int i = 0; i + 1 < N; ++i) {
+        double Q[3] = { r[3 * (i + 1) + 0] - r[3 * i + 0],
+                        r[3 * (i + 1) + 1] - r[3 * i + 1],
+                        r[3 * (i + 1) + 2] - r[3 * i + 2] };
+        floored += ora_spring_force(ch->spring, ch->H, ch->b, s_min, Q, &F[3 * i], NULL);
+    }
+    const double amp = sqrt(2.0 * D * dt);
+    for (int i = 0; i < N; ++i) {
+        for (int d = 0; d < 3; ++d) {
+            double fspring = 0.0;
+            if (i + 1 < N) fspring += F[3 * i + d];
+            if (i > 0)     fspring -= F[3 * (i - 1) + d];
+            double v = kappa[3 * d + 0] * r[3 * i + 0] + kappa[3 * d + 1] * r[3 * i + 1]
+                     + kappa[3 * d + 2] * r[3 * i + 2];
+            inc[3 * i + d] = (v + (D / kT) * fspring) * dt + amp * xi[3 * i + d];
+        }
+    }
+    for (int i = 0; i < 3 * N; ++i) r[i] += inc[i];
+    free(inc);
+    free(F);
+    return floored;
+}
+
+/* Eq. 4: the instantaneous force of each spring, as a magnitude. */
+void ora_tensions(const ora_chain* ch, double s_min, const double* r, double* f)
+{
+    for (int i = 0; i + 1 < ch->n_beads; ++i) {
+        double Q[3] = { r[3 * (i + 1) + 0] - r[3 * i + 0],
+                        r[3 * (i + 1) + 1] - r[3 * i + 1],
+                        r[3 * (i + 1) + 2] - r[3 * i + 2] };
+        double F[3];
+        ora_spring_force(ch->spring, ch->H, ch->b, s_min, Q, F, &f[i]);
+    }
+}
+
+/* One sampled force f of one spring under criterion q, attributed to an
+ * interval dT ending at global step `step`:
+ *   threshold: first step with f >= f_c (ties count);
+ *   Bell: hazard += k0 exp(f dx) dT (force held constant over dT); first
+ *   passage at the first step where the integrated hazard reaches E. */
+void ora_criteria_update(int q, int thr_on, int bell_on, const ora_chain* ch, double f,
+                         double dT, int64_t step, double E, double* lam,
+                         int64_t* first_thr, int64_t* first_bell)
+{
+    (void)q;
+    if (thr_on && *first_thr < 0 && f >= ch->f_c) *first_thr = step;
+    if (bell_on) {
+        *lam += ch->k0 * exp(f * ch->dx) * dT;
+        if (*first_bell < 0 && *lam >= E) *first_bell = step;
+    }
+}
+
+/* Batch forms of the two generators above, for tests that need many draws. */
+void ora_philox_many(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out)
+{
+    for (int64_t j = 0; j < n; ++j) ora_philox4x32_10(&ctr[4 * j], key, &out[4 * j]);
+}
+
+void ora_normals3_many(uint64_t seed, int64_t n, const uint32_t* ctr, double* xi)
+{
+    for (int64_t j = 0; j < n; ++j)
+        ora_normals3(seed, ctr[4 * j + 0], ctr[4 * j + 1] & 0xFFFFFFu, ctr[4 * j + 1] >> 24,
+                     ctr[4 * j + 2], ctr[4 * j + 3], &xi[3 * j]);
+}
+
+int ora_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* The method, chain by chain, in the order of Sec. II:                     */
+/*   at every sampling time t_w = w S (w = 0, 1, ...):                      */
+/*     halt the parent; copy it into N_R replicas; evolve replica k for S   */
+/*     steps with its own noise stream (slot k); sample the force of every  */
+/*     spring once at the end; RSF = mean over replicas;                    */
+/*     continue the parent for S steps (slot 0), sampling its force every   */
+/*     step (ISF) and averaging the samples over the window (TSF).          */
+/* Global step t keys the noise of the update t -> t+1 for every slot, so a */
+/* replica and the parent advance through the same step counter.           */
+/*                                                                          */
+/* Arrays (M = sum over chains of N_c - 1, springs of chain c at spr_off[c]):*/
+/*   pos        in/out [sum N][3] parent positions, laboratory frame        */
+/*   pos_rep    out [sum R N][3] replica positions at the end, or NULL      */
+/*   rsf, tsf   out [n_steps / S][M] window profiles, or NULL               */
+/*   lam        in/out [3][M] integrated Bell hazard per criterion          */
+/*   first_thr, first_bell in/out [3][M] first event step, -1 if none       */
+/*   exp1       out [3][M] Exp(1) thresholds, or NULL                       */
+/*   overext    out [n_chains] FENE-floor applications (all slots)          */
+/* A run that ends inside a window evolves the replicas and the parent      */
+/* through the partial window and takes no window sample.                   */
+/* ------------------------------------------------------------------------ */
+int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
+            double* rsf, double* tsf, double* lam, int64_t* first_thr, int64_t* first_bell,
+            double* exp1, int64_t* overext, int n_threads)
+{
+    const int C = p->n_chains;
+    const int S = p->window_steps;
+    if (C <= 0 || S <= 0 || n_steps < 0) return 1;
+    int64_t* bead_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
+    int64_t* spr_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
+    int64_t* rep_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
+    bead_off[0] = spr_off[0] = rep_off[0] = 0;
+    for (int c = 0; c < C; ++c) {
+        bead_off[c + 1] = bead_off[c] + p->chains[c].n_beads;
+        spr_off[c + 1] = spr_off[c] + p->chains[c].n_beads - 1;
+        rep_off[c + 1] = rep_off[c] + (int64_t)p->chains[c].n_replicas * p->chains[c].n_beads;
+    }
+    const int64_t M = spr_off[C];
+
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#else
+    (void)n_threads;
+#endif
+    for (int c = 0; c < C; ++c) {
+        const ora_chain* ch = &p->chains[c];
+        const int N = ch->n_beads, R = ch->n_replicas;
+        const int64_t so = spr_off[c];
+        double* parent = pos + 3 * bead_off[c];
+        double* rep = (double*)malloc(sizeof(double) * 3 * (size_t)N * (size_t)R);
+        double* xi = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+        double* f = (double*)malloc(sizeof(double) * (size_t)N);
+        double* rsum = (double*)malloc(sizeof(double) * (size_t)N);
+        double* tsum = (double*)malloc(sizeof(double) * (size_t)N);
+        double* E = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+        int64_t nover = 0;
+
+        for (int q = 0; q < 3; ++q)
+            for (int i = 0; i + 1 < N; ++i) {
+                E[q * N + i] = ora_exp1(p->seed, (uint32_t)i, (uint32_t)q, (uint32_t)c);
+                if (exp1) exp1[q * M + so + i] = E[q * N + i];
+            }
+
+        for (int k = 0; k < R; ++k)
+            memcpy(rep + 3 * (size_t)N * k, parent, sizeof(double) * 3 * (size_t)N);
+
+        for (int64_t t = 0; t < n_steps; ) {
+            const int64_t w = t / S;
+            const int Sw = (int)((n_steps - t) < S ? (n_steps - t) : S);
+
+            /* RSF: halt the parent, spawn replicas, evolve them for S. */
+            for (int i = 0; i + 1 < N; ++i) rsum[i] = 0.0;
+            for (int k = 1; k <= R; ++k) {
+                double* rk = rep + 3 * (size_t)N * (k - 1);
+                memcpy(rk, parent, sizeof(double) * 3 * (size_t)N);
+                const uint32_t slot = p->identical_noise ? 0u : (uint32_t)k;
+                for (int s = 0; s < Sw; ++s) {
+                    for (int i = 0; i < N; ++i)
+                        ora_normals3(p->seed, (uint32_t)i, slot, ORA_STREAM_BD,
+                                     (uint32_t)(t + s), (uint32_t)c, &xi[3 * i]);
+                    nover += ora_em_step(ch, p->dt, p->s_min, rk, xi);
+                }
+                if (Sw == S) {
+                    ora_tensions(ch, p->s_min, rk, f);
+                    for (int i = 0; i + 1 < N; ++i) rsum[i] += f[i];
+                }
+            }
+
+            /* Continue the parent through the same S steps. */
+            for (int i = 0; i + 1 < N; ++i) tsum[i] = 0.0;
+            for (int s = 0; s < Sw; ++s) {
+                for (int i = 0; i < N; ++i)
+                    ora_normals3(p->seed, (uint32_t)i, 0u, ORA_STREAM_BD, (uint32_t)(t + s),
+                                 (uint32_t)c, &xi[3 * i]);
+                nover += ora_em_step(ch, p->dt, p->s_min, parent, xi);
+                ora_tensions(ch, p->s_min, parent, f);
+                for (int i = 0; i + 1 < N; ++i) {
+                    tsum[i] += f[i];
+                    const int64_t m = so + i;
+                    ora_criteria_update(ORA_ISF, (p->thr_mask >> ORA_ISF) & 1,
+                                        (p->bell_mask >> ORA_ISF) & 1, ch, f[i], p->dt,
+                                        t + s + 1, E[ORA_ISF * N + i],
+                                        &lam[ORA_ISF * M + m], &first_thr[ORA_ISF * M + m],
+                                        &first_bell[ORA_ISF * M + m]);
+                }
+            }
+
+            if (Sw == S) {
+                const double dT = S * p->dt;
+                for (int i = 0; i + 1 < N; ++i) {
+                    const int64_t m = so + i;
+                    const double fr = rsum[i] / R;
+                    const double ft = tsum[i] / S;
+                    if (rsf) rsf[w * M + m] = fr;
+                    if (tsf) tsf[w * M + m] = ft;
+                    ora_criteria_update(ORA_TSF, (p->thr_mask >> ORA_TSF) & 1,
+                                        (p->bell_mask >> ORA_TSF) & 1, ch, ft, dT, t + S,
+                                        E[ORA_TSF * N + i],
+                                        &lam[ORA_TSF * M + m], &first_thr[ORA_TSF * M + m],
+                                        &first_bell[ORA_TSF * M + m]);
+                    ora_criteria_update(ORA_RSF, (p->thr_mask >> ORA_RSF) & 1,
+                                        (p->bell_mask >> ORA_RSF) & 1, ch, fr, dT, t + S,
+                                        E[ORA_RSF * N + i],
+                                        &lam[ORA_RSF * M + m], &first_thr[ORA_RSF * M + m],
+                                        &first_bell[ORA_RSF * M + m]);
+                }
+            }
+            t += Sw;
+        }
+
+        if (pos_rep)
+            memcpy(pos_rep + 3 * rep_off[c], rep, sizeof(double) * 3 * (size_t)N * (size_t)R);
+        overext[c] = nover;
+        free(rep); free(xi); free(f); free(rsum); free(tsum); free(E);
+    }
+    free(bead_off); free(spr_off); free(rep_off);
+    return 0;
+}

@@ -1,0 +1,84 @@
+/*
+ * Plain CPU FP64 oracle for replica-averaged Brownian dynamics
+ * (Kania, Nguyen, Oztekin & Webb, "Replica-Averaging", arXiv 2206.05851).
+ *
+ * TEST INFRASTRUCTURE ONLY. This code is the slow, obviously-correct
+ * reference the CUDA path is checked against. Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it; the product
+ * library never links, includes or calls it, and it shares no code with it.
+ *
+ * Units: length l_H = sqrt(kT/H0), time lambda_H = zeta/(4 H0), kT = 1, so the
+ * free-draining diffusivity kT/zeta of Eq. 2 is D = 1/4 and Eq. 1 becomes
+ *   r_i <- r_i + [kappa . r_i + D (F_i - F_{i-1})] dt + sqrt(2 D dt) xi_i .
+ */
+#ifndef BD_ORACLE_H
+#define BD_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORA_SPRING_HOOKE = 0, ORA_SPRING_FENE = 1 };
+enum { ORA_FLOW_NONE = 0, ORA_FLOW_SHEAR = 1, ORA_FLOW_UNIAXIAL = 2, ORA_FLOW_PLANAR = 3 };
+enum { ORA_ISF = 0, ORA_TSF = 1, ORA_RSF = 2 };          /* criterion index q */
+enum { ORA_STREAM_BD = 0, ORA_STREAM_EXP1 = 1 };         /* Philox stream ids */
+
+typedef struct {
+    int32_t n_beads, n_replicas, spring, flow;
+    double H, b, rate;     /* stiffness / H0, FENE b, flow rate in 1/lambda_H */
+    double f_c, k0, dx;    /* threshold force; Bell k = k0 exp(f dx) */
+} ora_chain;
+
+typedef struct {
+    int32_t n_chains;
+    int32_t window_steps;      /* S / dt: replica evolution time in steps */
+    const ora_chain* chains;
+    double dt;
+    uint64_t seed;             /* Philox key (low word, high word) */
+    int32_t identical_noise;   /* 1: every replica draws the parent's noise */
+    int32_t thr_mask;          /* bit q set: threshold criterion on ISF/TSF/RSF */
+    int32_t bell_mask;         /* bit q set: Bell criterion on ISF/TSF/RSF */
+    double s_min;              /* FENE overextension floor of 1 - H Q^2 / b */
+} ora_problem;
+
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11). */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* u = (x + 1/2) 2^-32 in (0, 1). */
+double ora_uniform(uint32_t x);
+/* Three standard normals for (bead, slot, stream, step, chain). */
+void ora_normals3(uint64_t seed, uint32_t bead, uint32_t slot, uint32_t stream,
+                  uint32_t step, uint32_t chain, double xi[3]);
+/* Unit-mean exponential threshold for a (spring, criterion, chain). */
+double ora_exp1(uint64_t seed, uint32_t spring, uint32_t criterion, uint32_t chain);
+/* Spring force F(Q) and tension |F|; returns 1 when the FENE floor applied. */
+int ora_spring_force(int spring, double H, double b, double s_min, const double Q[3],
+                     double F[3], double* tension);
+/* Velocity-gradient tensor kappa (row-major), v = kappa . r. */
+void ora_flow_gradient(int flow, double rate, double kappa[9]);
+/* One Euler-Maruyama step of Eq. 1 with given noise xi [N][3]; positions r [N][3]. */
+int64_t ora_em_step(const ora_chain* ch, double dt, double s_min, double* r, const double* xi);
+/* Tension profile [N-1] of a conformation. */
+void ora_tensions(const ora_chain* ch, double s_min, const double* r, double* f);
+
+/* Full method over n_steps from global step 0 (see bd_oracle.c for outputs). */
+int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
+            double* rsf, double* tsf, double* lam, int64_t* first_thr, int64_t* first_bell,
+            double* exp1, int64_t* overext, int n_threads);
+
+/* Criteria update for one sampled force value of spring m (used by ora_run;
+ * exported so tests can drive kinetics with prescribed force histories). */
+void ora_criteria_update(int q, int thr_on, int bell_on, const ora_chain* ch, double f,
+                         double dT, int64_t step, double E, double* lam,
+                         int64_t* first_thr, int64_t* first_bell);
+
+/* Batch helpers: ctr is [n][4] (word 1 = slot | stream << 24). */
+void ora_philox_many(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out);
+void ora_normals3_many(uint64_t seed, int64_t n, const uint32_t* ctr, double* xi);
+
+int ora_max_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

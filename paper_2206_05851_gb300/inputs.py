@@ -1,0 +1,218 @@
+"""Seeded synthetic inputs for replica-averaged Brownian dynamics.
+
+This module is shared by the CUDA path, the tests and the benchmark. It
+holds no part of the method's arithmetic (no integrator, no spring force, no
+noise stream, no sampling or kinetics): it only draws initial chain
+conformations and builds the per-chain parameter tables of the workloads.
+
+Units are Hookean ones: length l_H = sqrt(kT/H0), time lambda_H = zeta/(4 H0),
+force kT/l_H, kT = 1. A spring's dimensionless stiffness ``H`` is its spring
+constant in units of H0 (1 by default), and the FENE extensibility is
+b = H Q0^2 / kT.
+
+Workload shapes follow the configurations the replica-averaging method is
+benchmarked on: free-draining FENE chains under uniaxial / planar elongation
+and steady shear, tens of replicas per chain, re-spawned every window of
+100 steps (Sec. II of the paper describes the replica procedure; the FENE
+spring is named in its supplementary vWF model, Table S1).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+SPRING_HOOKE = 0
+SPRING_FENE = 1
+
+FLOW_NONE = 0
+FLOW_SHEAR = 1
+FLOW_UNIAXIAL = 2
+FLOW_PLANAR = 3
+
+CRIT_ISF = 1
+CRIT_TSF = 2
+CRIT_RSF = 4
+CRIT_ALL = CRIT_ISF | CRIT_TSF | CRIT_RSF
+
+
+@dataclasses.dataclass
+class Chain:
+    """Parameters of one parent chain and its replica set."""
+
+    n_beads: int
+    n_replicas: int
+    spring: int = SPRING_FENE
+    flow: int = FLOW_NONE
+    H: float = 1.0
+    b: float = 50.0
+    rate: float = 0.0      # strain rate (elongation) or shear rate, 1/lambda_H
+    f_c: float = math.inf  # threshold-rupture force
+    k0: float = 0.0        # Bell zero-force rate, 1/lambda_H
+    dx: float = 0.0        # Bell distance to transition state, l_H
+
+
+@dataclasses.dataclass
+class Workload:
+    """A complete problem: chains, integration settings and criteria."""
+
+    name: str
+    chains: List[Chain]
+    dt: float
+    window_steps: int
+    n_steps: int
+    seed: int
+    thr_mask: int = CRIT_RSF
+    bell_mask: int = 0
+    init_seed: int = 12345
+
+    @property
+    def n_chains(self) -> int:
+        return len(self.chains)
+
+    def bead_steps(self, n_steps: Optional[int] = None) -> int:
+        """chains x replicas x beads x steps (parent chain not counted)."""
+        n = self.n_steps if n_steps is None else n_steps
+        return sum(c.n_replicas * c.n_beads for c in self.chains) * n
+
+
+def rouse_longest_time(n_beads: int) -> float:
+    """Longest Rouse relaxation time of an N-bead Hookean chain, in lambda_H.
+
+    lambda_1 = 1 / (2 sin^2(pi / (2N))); the dumbbell (N = 2) gives 1.
+    """
+    return 1.0 / (2.0 * math.sin(math.pi / (2.0 * n_beads)) ** 2)
+
+
+def rate_from_wi(wi: float, n_beads: int) -> float:
+    """Flow rate (1/lambda_H) for Weissenberg number Wi = rate * lambda_1."""
+    return wi / rouse_longest_time(n_beads)
+
+
+def fene_fmax(H: float, b: float) -> float:
+    """FENE force scale F_max = H Q0 = sqrt(H b) (kT = 1)."""
+    return math.sqrt(H * b)
+
+
+def sample_connectors(rng: np.random.Generator, n: int, spring: int,
+                      H: float, b: float) -> np.ndarray:
+    """n iid connector vectors from the equilibrium spring density.
+
+    Hookean: Q ~ N(0, I/H). FENE: p(Q) ~ (1 - H Q^2/b)^(b/2) on |Q| < sqrt(b/H),
+    drawn by rejection from N(0, I/H) (the ratio of the two densities,
+    (1 - x)^(b/2) e^(b x / 2) with x = H Q^2 / b, never exceeds 1).
+    """
+    out = np.empty((n, 3))
+    filled = 0
+    sd = 1.0 / math.sqrt(H)
+    while filled < n:
+        m = max(16, 2 * (n - filled))
+        q = rng.normal(0.0, sd, size=(m, 3))
+        if spring == SPRING_HOOKE:
+            acc = q
+        else:
+            x = H * np.sum(q * q, axis=1) / b
+            ok = x < 1.0
+            q, x = q[ok], x[ok]
+            logr = 0.5 * b * (np.log1p(-x) + x)
+            acc = q[rng.random(len(q)) < np.exp(logr)]
+        take = min(len(acc), n - filled)
+        out[filled:filled + take] = acc[:take]
+        filled += take
+    return out
+
+
+def initial_coil(rng: np.random.Generator, chain: Chain) -> np.ndarray:
+    """Equilibrium random-walk conformation [N][3], centre of mass at 0."""
+    q = sample_connectors(rng, chain.n_beads - 1, chain.spring, chain.H, chain.b)
+    r = np.zeros((chain.n_beads, 3))
+    r[1:] = np.cumsum(q, axis=0)
+    r -= r.mean(axis=0)
+    return r
+
+
+def initial_positions(workload: Workload, seed: Optional[int] = None) -> np.ndarray:
+    """Concatenated initial conformations of all chains, [sum N][3] float64."""
+    rng = np.random.default_rng(workload.init_seed if seed is None else seed)
+    return np.concatenate([initial_coil(rng, c) for c in workload.chains], axis=0)
+
+
+def spring_offsets(chains: Sequence[Chain]) -> np.ndarray:
+    """Exclusive prefix sum of N_c - 1 (spring index base of each chain)."""
+    return np.concatenate([[0], np.cumsum([c.n_beads - 1 for c in chains])]).astype(np.int64)
+
+
+def bead_offsets(chains: Sequence[Chain]) -> np.ndarray:
+    return np.concatenate([[0], np.cumsum([c.n_beads for c in chains])]).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Named workloads
+# ---------------------------------------------------------------------------
+
+def single_chain_fp64(n_steps: int = 10_000) -> Workload:
+    """One FENE chain, N=20, b=50, uniaxial Wi=2, dt=1e-3, 16 replicas,
+    window 100, seed 0, threshold rupture at 0.9 F_max."""
+    n, b = 20, 50.0
+    ch = Chain(n_beads=n, n_replicas=16, spring=SPRING_FENE, flow=FLOW_UNIAXIAL,
+               H=1.0, b=b, rate=rate_from_wi(2.0, n), f_c=0.9 * fene_fmax(1.0, b))
+    return Workload("fene_n20_r16_uniaxial_wi2", [ch], dt=1e-3, window_steps=100,
+                    n_steps=n_steps, seed=0, thr_mask=CRIT_RSF, bell_mask=0, init_seed=0)
+
+
+def planar_1024(n_steps: int = 100_000, n_chains: int = 1024) -> Workload:
+    """1024 FENE chains, N=100, b=100, planar elongation Wi=5, 64 replicas,
+    dt=5e-4, window 100, seed 1. Threshold at 0.9 F_max and a Bell rate with
+    k0 = 1e-6, dx F_max = 20 on the replica-averaged force."""
+    n, b = 100, 100.0
+    fmax = fene_fmax(1.0, b)
+    chains = [Chain(n_beads=n, n_replicas=64, spring=SPRING_FENE, flow=FLOW_PLANAR,
+                    H=1.0, b=b, rate=rate_from_wi(5.0, n), f_c=0.9 * fmax,
+                    k0=1e-6, dx=20.0 / fmax) for _ in range(n_chains)]
+    return Workload("fene_1024x_n100_r64_planar_wi5", chains, dt=5e-4, window_steps=100,
+                    n_steps=n_steps, seed=1, thr_mask=CRIT_RSF, bell_mask=CRIT_RSF,
+                    init_seed=1)
+
+
+def uneven_4096(n_steps: int = 10_000, n_chains: int = 4096, gen_seed: int = 2) -> Workload:
+    """4096 FENE chains, N ~ U{20..500}, R ~ {8,16,32,64,128}, half steady shear
+    Wi ~ U[1,50], half uniaxial Wi ~ U[0.5,10], b ~ U[20,200], dt=1e-3."""
+    rng = np.random.default_rng(gen_seed)
+    chains = []
+    for c in range(n_chains):
+        n = int(rng.integers(20, 501))
+        r = int(rng.choice([8, 16, 32, 64, 128]))
+        b = float(rng.uniform(20.0, 200.0))
+        if c % 2 == 0:
+            flow, wi = FLOW_SHEAR, float(rng.uniform(1.0, 50.0))
+        else:
+            flow, wi = FLOW_UNIAXIAL, float(rng.uniform(0.5, 10.0))
+        fmax = fene_fmax(1.0, b)
+        chains.append(Chain(n_beads=n, n_replicas=r, spring=SPRING_FENE, flow=flow, H=1.0,
+                            b=b, rate=rate_from_wi(wi, n), f_c=0.9 * fmax,
+                            k0=1e-6, dx=20.0 / fmax))
+    return Workload("fene_4096x_uneven_n20-500_r8-128", chains, dt=1e-3, window_steps=100,
+                    n_steps=n_steps, seed=2, thr_mask=CRIT_RSF, bell_mask=CRIT_RSF,
+                    init_seed=2)
+
+
+def bell_16384(n_steps: int = 250_000, n_chains: int = 16384) -> Workload:
+    """16384 FENE chains, N=50, b=100, start-up uniaxial Wi=10 from equilibrium,
+    32 replicas, Bell k0=1e-6 and dx F_max = 20 on ISF, TSF and RSF."""
+    n, b = 50, 100.0
+    fmax = fene_fmax(1.0, b)
+    chains = [Chain(n_beads=n, n_replicas=32, spring=SPRING_FENE, flow=FLOW_UNIAXIAL, H=1.0,
+                    b=b, rate=rate_from_wi(10.0, n), f_c=0.9 * fmax, k0=1e-6,
+                    dx=20.0 / fmax) for _ in range(n_chains)]
+    return Workload("fene_16384x_n50_r32_uniaxial_wi10_bell", chains, dt=1e-3,
+                    window_steps=100, n_steps=n_steps, seed=4, thr_mask=CRIT_ALL,
+                    bell_mask=CRIT_ALL, init_seed=4)
+
+
+def custom(chains: Sequence[Chain], dt: float, window_steps: int, n_steps: int,
+           seed: int = 0, thr_mask: int = CRIT_ALL, bell_mask: int = CRIT_ALL,
+           init_seed: int = 7, name: str = "custom") -> Workload:
+    return Workload(name, list(chains), dt=dt, window_steps=window_steps, n_steps=n_steps,
+                    seed=seed, thr_mask=thr_mask, bell_mask=bell_mask, init_seed=init_seed)
