@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the replica-averaged Brownian-dynamics hot path on GB300.
+
+Workload: 1024 independent FENE chains, N = 100 beads, b = 100, planar
+elongational flow at Wi = 5, 64 replicas per chain re-spawned every 100
+steps, dt = 5e-4, FP32 integration with FP64 replica reduction; threshold
+(0.9 F_max) and Bell (k0 = 1e-6, dx F_max = 20) criteria on the
+replica-averaged force. One bench step = 10^4 integration steps of every
+chain and replica (100 windows) plus event detection, so the default
+--steps 10 times the whole 10^5-step run. Inputs are synthetic (equilibrium
+FENE coils from a seeded generator) and resident in HBM.
+
+Metric: bead-steps/s = chains x replicas x beads x steps / time.
+
+--impl reference times the CPU FP64 oracle (the only reference this method
+has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("bead-steps/s (chains×replicas×beads×steps) FP32 batched vs FP64 plain, "
+          "1 GB300")
+# Minimal lane-instructions per slot-bead-step of the FP32 replica step
+# (Philox4x32-10 40, uniforms 8, Box-Muller 18, spring force 10,
+# Laplacian 6, update 13); see the design notes for the count.
+ALGO_OPS_PER_BEAD_STEP = 95
+SMS, LANES_PER_CLK_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk", type=int, default=10_000, help="integration steps per bench step")
+    ap.add_argument("--chains", type=int, default=1024)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except Exception:
+            return None
+    return None
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"bdra_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        idx = vis.split(",")[int(os.environ.get("LOCAL_RANK", "0"))] if vis else os.environ.get("LOCAL_RANK", "0")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(wl, pos0, n_chains=None, n_steps=1000):
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    n_chains = n_chains or min(cores, wl.n_chains)
+    sub = wl.chains[:n_chains]
+    sub_pos = pos0[:sum(c.n_beads for c in sub)]
+    t = time.perf_counter()
+    O.run(sub, wl.dt, wl.window_steps, n_steps, wl.seed, sub_pos, thr_mask=wl.thr_mask,
+          bell_mask=wl.bell_mask, n_threads=min(cores, n_chains), want_replicas=False,
+          chain_ids=list(range(n_chains)))
+    dt = time.perf_counter() - t
+    bead_steps = sum(c.n_replicas * c.n_beads for c in sub) * n_steps
+    return {"value": bead_steps / dt, "unit": "bead-steps/s", "cores": min(cores, n_chains),
+            "kind": "oracle",
+            "sample": f"first {n_chains} chains of the workload, {n_steps} steps "
+                      f"({bead_steps:.3g} bead-steps, {dt:.1f} s wall, FP64, OpenMP over chains)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2206_05851_gb300 import inputs as I
+    wl = I.planar_1024(n_chains=args.chains)
+    pos0 = I.initial_positions(wl)
+    cores = os.cpu_count() or 1
+    n_chains = min(cores, wl.n_chains)
+    n_steps = 400
+    for _ in range(args.warmup):
+        cpu_baseline(wl, pos0, n_chains, n_steps)
+    vals = [cpu_baseline(wl, pos0, n_chains, n_steps) for _ in range(args.steps)]
+    bead_steps = sum(c.n_replicas * c.n_beads for c in wl.chains[:n_chains]) * n_steps
+    total_t = sum(bead_steps / v["value"] for v in vals)
+    value = bead_steps * len(vals) / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "bead-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / len(vals), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "reference": "CPU FP64 oracle (plain C, OpenMP over chains)",
+                       "sample_per_step": f"{n_chains} chains x {n_steps} steps"},
+            "cpu_baseline": {"value": value, "unit": "bead-steps/s", "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": "bead-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2206_05851_gb300 import bdra, build as B
+    from paper_2206_05851_gb300 import inputs as I
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 and not B.up_to_date():
+        B.build()
+    if world > 1:
+        dist.barrier()
+    bdra.load()
+
+    wl = I.planar_1024(n_chains=args.chains)
+    # ranks own independent chain sets: same shapes, their own seeds (weak scaling)
+    seed = wl.seed + 1000 * rank
+    pos0 = I.initial_positions(wl, seed=wl.init_seed + rank)
+    S = wl.window_steps
+    chunk = args.chunk
+    total_windows = (args.warmup + args.steps) * chunk // S + 1
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    ctx = bdra.Context(wl.chains, wl.dt, S, seed, torch.from_numpy(pos0).cuda(),
+                       precision=bdra.BD_PREC_FP32, max_windows=total_windows,
+                       thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=sptr)
+    bead_steps_chunk = sum(c.n_replicas * c.n_beads for c in wl.chains) * chunk
+    slot_bead_steps_chunk = bead_steps_chunk        # replica slots only (the replica kernel)
+    ev_cap = 6 * ctx.M
+    ev_buf = torch.zeros(ev_cap * 24, dtype=torch.uint8, device="cuda")
+    ls_buf = torch.zeros((len(wl.chains), 3), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def bench_step():
+        ctx.step(chunk)
+        return bdra.bd_detect_events(ctx.ptr, ev_buf, ev_cap, ls_buf)
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    bdra.bd_enable_timing(ctx.ptr, True)
+    bdra.bd_kernel_times(ctx.ptr)
+    launches0 = ctx.info().kernel_launches
+    clocks = ClockSampler()
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()                 # evict L2 between timed steps
+        n_events = bench_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = ctx.info().kernel_launches - launches0    # our kernels only
+    (par_ms, rep_ms), (par_n, rep_n) = bdra.bd_kernel_times(ctx.ptr)
+    bdra.bd_enable_timing(ctx.ptr, False)
+    t_max = t_ms
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = bead_steps_chunk * args.steps * world / (t_max / 1e3)
+
+    # roofline of the dominant kernel (replica kernel), measured live
+    rep_units = slot_bead_steps_chunk * args.steps
+    achieved = ALGO_OPS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3) / 1e12
+    peak = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "replica_kernel<float,13>", "avg_launch_ms": rep_ms / max(rep_n, 1),
+            "launches": rep_n, "share_of_step": rep_ms / t_ms,
+            "peak_basis": f"issue rate {SMS} SMs x {LANES_PER_CLK_PER_SM} lane-instr/clk x "
+                          f"{SM_MAX_MHZ:.0f} MHz (derived, not measured)",
+            "ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP}
+    if clk:
+        roof["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6 / 1e12)
+    parent_share = par_ms / t_ms
+
+    out = {"metric": METRIC, "value": value, "unit": "bead-steps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": wl.name, "chains_per_gpu": len(wl.chains), "beads": 100,
+                      "replicas": 64, "flow": "planar elongation", "Wi": 5, "b": 100,
+                      "dt": wl.dt, "window_steps": S, "steps_per_bench_step": chunk,
+                      "timed_integration_steps": chunk * args.steps,
+                      "criteria": "threshold + Bell on RSF", "precision": "FP32 integrate, FP64 reduce",
+                      "l2": "flushed (256 MB write) between timed steps",
+                      "parallelism": f"chains sharded over {world} GPU(s), no collective on the data path"},
+           "gpu_launches": int(launches), "events_detected": int(n_events),
+           "parent_kernel_share": parent_share}
+    if clk:
+        out["clocks"] = clk
+    out["roofline"] = roof
+    peaks = measured_peaks()
+    if peaks:
+        out["measured_peaks_file"] = {k: peaks[k] for k in list(peaks)[:8]}
+
+    if rank == 0 and world == 1:
+        # plain FP64 path on the same chains, 1000 steps, and the FP32 force
+        # error against it
+        if not args.no_fp64:
+            n64 = 1000
+            c64 = bdra.Context(wl.chains, wl.dt, S, seed, torch.from_numpy(pos0).cuda(),
+                               precision=bdra.BD_PREC_FP64, max_windows=n64 // S + 1,
+                               thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=sptr)
+            c64.step(S)
+            torch.cuda.synchronize()
+            c64.set_positions(torch.from_numpy(pos0).cuda(), 0)
+            torch.cuda.synchronize()
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c64.step(n64)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            t64 = a.elapsed_time(b_) / 1e3
+            v64 = sum(c.n_replicas * c.n_beads for c in wl.chains) * n64 / t64
+            ctx.set_positions(torch.from_numpy(pos0).cuda(), 0)
+            ctx.step(n64)
+            nw = n64 // S
+            errs = []
+            for w in range(nw):
+                r32 = ctx.replica_average(w)
+                r64 = c64.replica_average(w)
+                errs.append(float(np.abs(r32 - r64).max() / np.abs(r64).max()))
+            c64.close()
+            out["fp64_plain"] = {"value": v64, "unit": "bead-steps/s",
+                                 "sample": f"same {len(wl.chains)} chains, {n64} steps",
+                                 "speedup_fp32_over_fp64": value / v64,
+                                 "rsf_max_rel_err_fp32_vs_fp64": max(errs)}
+        # end to end through the C ABI with host buffers
+        if not args.no_e2e:
+            pos_h = torch.from_numpy(pos0).pin_memory()
+            ev_h = np.zeros(ev_cap, dtype=bdra.EVENT_DTYPE)
+            rsf_h = np.zeros(ctx.M)
+            e2e_steps = 2
+
+            def e2e_step():
+                bdra.bd_set_positions(ctx.ptr, pos_h, 0)
+                ctx.step(chunk)
+                n = bdra.bd_detect_events(ctx.ptr, ev_h, ev_cap, None)
+                bdra.bd_replica_average(ctx.ptr, chunk // S - 1, rsf_h)
+                return n
+
+            e2e_step()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nev = 0
+            for _ in range(e2e_steps):
+                nev = e2e_step()
+            torch.cuda.synchronize()
+            te = (time.perf_counter() - t0) / e2e_steps
+            out["e2e"] = {"value": bead_steps_chunk / te, "unit": "bead-steps/s",
+                          "h2d_bytes_per_step": int(pos_h.numel() * 8),
+                          "d2h_bytes_per_step": int(nev * 24 + ctx.M * 8 + 8),
+                          "steps": e2e_steps}
+        if not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(wl, pos0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * bdra.h - C ABI of the GB300 library for replica-averaged Brownian dynamics
+ * (Kania, Nguyen, Oztekin & Webb, "Replica-Averaging: An algorithm to study
+ * mechano-reactive processes for polymers under flow conditions",
+ * arXiv 2206.05851).
+ *
+ * Problem statement (Sec. II): bead-spring chains evolve by the overdamped
+ * Langevin update of Eq. 1 under an imposed flow. At every sampling time the
+ * parent chain is halted, N_R replicas of it are formed, each with its own
+ * random-number stream, evolved for the evolution time S, and the force of
+ * every spring (Eq. 4) is sampled once per replica at the end and averaged
+ * over the replicas (the replica-averaged spring force, RSF); then the parent
+ * continues. The time-averaged (TSF) and instantaneous (ISF) spring forces are
+ * the two comparison estimators. Events follow from a force criterion
+ * (Sec. I: a threshold rupture force; Sec. III: the Bell rate
+ * k = k0 exp(f dx / kT) and the survival exp(-integral of k dt)).
+ *
+ * Model realised here: free-draining chains (Eq. 2 diagonal diffusion, no
+ * hydrodynamic interaction), Hookean or FENE springs F = H Q / (1 - H Q^2/b),
+ * homogeneous shear (v = gdot z x_hat, Sec. II), uniaxial or planar
+ * elongation. Units: length sqrt(kT/H0), time zeta/(4 H0), kT = 1.
+ *
+ * Conventions for every entry point:
+ *   - All functions are extern "C", never throw, and return a bd_status.
+ *     On failure the context keeps its previous state and bd_last_error()
+ *     describes the cause. A NULL context gives BD_E_INVALID.
+ *   - Array arguments may be host or device pointers of the context's device;
+ *     the library detects which. Device arrays are read or written in stream
+ *     order on the context's stream; host arrays are copied synchronously
+ *     (the call returns once the data are in place). The caller owns every
+ *     array it passes; the context owns all of its device state.
+ *   - Layouts: positions are float64 [sum_c N_c][3] (chains in order, beads in
+ *     order, x y z). Spring profiles are float64 [M] with
+ *     M = sum_c (N_c - 1), chain c's springs starting at sum_{c'<c} (N_c' - 1).
+ *   - Noise: Philox4x32-10 (Salmon et al., SC'11) with key = (seed low word,
+ *     seed high word) and counter (bead, slot | stream << 24, step, chain);
+ *     slot 0 is the parent, slots 1..R the replicas; stream 0 drives Eq. 1,
+ *     stream 1 the Exp(1) thresholds of the Bell first-passage test. Results
+ *     therefore do not depend on the launch shape.
+ */
+#ifndef BDRA_H
+#define BDRA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bd_ctx bd_ctx;
+
+typedef enum {
+    BD_OK = 0,
+    BD_E_INVALID = 1,   /* bad argument or configuration */
+    BD_E_CUDA = 2,      /* a CUDA call failed (message in bd_last_error) */
+    BD_E_OOM = 3,       /* device allocation failed */
+    BD_E_STATE = 4,     /* call not valid in the context's current state */
+    BD_E_TIMEOUT = 5,   /* reserved: no entry point waits on the device without bound */
+    BD_E_CAPACITY = 6   /* output or history capacity exceeded */
+} bd_status;
+
+enum { BD_SPRING_HOOKE = 0, BD_SPRING_FENE = 1 };
+enum { BD_FLOW_NONE = 0, BD_FLOW_SHEAR = 1, BD_FLOW_UNIAXIAL = 2, BD_FLOW_PLANAR = 3 };
+/* BD_PREC_FP64: every step in float64. BD_PREC_FP32: Eq. 1 integrated in
+ * float32; the cross-replica force reduction and the Bell hazard
+ * (log-survival) accumulate in float64. */
+enum { BD_PREC_FP64 = 0, BD_PREC_FP32 = 1 };
+/* Criterion bits (also the criterion index q = 0, 1, 2 of bd_event). */
+enum { BD_CRIT_ISF = 1, BD_CRIT_TSF = 2, BD_CRIT_RSF = 4 };
+/* BD_FLAG_IDENTICAL_NOISE: every replica draws the parent's noise (slot 0),
+ * so replicas reproduce the parent exactly - a consistency check. */
+enum { BD_FLAG_IDENTICAL_NOISE = 1 };
+
+/* One parent chain with its replica set. */
+typedef struct {
+    int32_t n_beads;     /* N, 2 <= N <= 512 */
+    int32_t n_replicas;  /* N_R, 1 <= N_R <= 4096 */
+    int32_t spring;      /* BD_SPRING_* */
+    int32_t flow;        /* BD_FLOW_* */
+    double H;            /* spring constant in units of H0 (> 0) */
+    double b;            /* FENE extensibility H Q0^2 / kT (> 0; unused for Hooke) */
+    double rate;         /* shear rate or elongation rate, 1 / (zeta/(4 H0)) */
+    double f_c;          /* threshold-rupture force (kT / l_H) */
+    double k0;           /* Bell zero-force rate */
+    double dx;           /* Bell distance to the transition state (l_H) */
+} bd_chain_desc;
+
+typedef struct {
+    int32_t n_chains;             /* >= 1 */
+    int32_t window_steps;         /* S / dt: replica evolution time in steps, >= 1 */
+    const bd_chain_desc* chains;  /* host array [n_chains], copied by bd_create */
+    double dt;                    /* time step (> 0) */
+    uint64_t seed;                /* Philox key */
+    int32_t precision;            /* BD_PREC_* */
+    int32_t flags;                /* BD_FLAG_* */
+    int32_t thr_mask;             /* BD_CRIT_* bits with a threshold criterion */
+    int32_t bell_mask;            /* BD_CRIT_* bits with a Bell criterion */
+    int64_t max_windows;          /* capacity of the per-window profile history */
+    double s_min;                 /* FENE floor of 1 - H Q^2 / b (e.g. 1e-3) */
+    void* stream;                 /* cudaStream_t for all work; NULL = default stream */
+    int32_t lanes_hint;           /* 0: autotuned launch shape; else springs per lane */
+    int32_t reserved;             /* must be 0 */
+} bd_config;
+
+/* A first event of one spring under one criterion. */
+typedef struct {
+    int32_t chain;      /* chain index */
+    int32_t spring;     /* spring index within the chain, 0 .. N-2 */
+    int32_t criterion;  /* 0 ISF, 1 TSF, 2 RSF */
+    int32_t kind;       /* 0 threshold rupture, 1 Bell first passage */
+    int64_t step;       /* global step at which it occurred */
+} bd_event;
+
+typedef struct {
+    int64_t n_springs;        /* M */
+    int64_t step;             /* global step of the parents */
+    int64_t windows_done;     /* completed sampling windows */
+    int64_t overextensions;   /* FENE-floor applications so far, all slots */
+    int64_t device_bytes;     /* device memory held by the context */
+    int64_t kernel_launches;  /* CUDA kernels launched by this context so far */
+    int32_t n_launch_classes; /* kernel launches per bd_step chunk */
+    int32_t precision;
+} bd_info;
+
+/* Creates a context on the current CUDA device: validates cfg, plans the
+ * launch shapes, allocates the device state and sets every parent to
+ * init_pos (float64 [sum N][3], host or device; any frame) at step 0 with its
+ * replicas spawned from it. Cites Sec. II (problem set-up). *out receives the
+ * context, or NULL on failure. */
+bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out);
+
+/* Replica spawn (Sec. II): replicas 1..N_R of every chain <- parent. Also
+ * performed automatically by bd_step at the start of every window. */
+bd_status bd_spawn_replicas(bd_ctx* ctx);
+
+/* Advances every parent and replica by n_steps Eq. 1 updates (Sec. II),
+ * spawning replicas at each window start, sampling RSF (replicas, once at the
+ * window end) and TSF/ISF (parent, every step), and updating the ISF
+ * criteria. Asynchronous on the context's stream. BD_E_CAPACITY if the run
+ * would pass max_windows windows. n_steps = 0 is a no-op. */
+bd_status bd_step(bd_ctx* ctx, int64_t n_steps);
+
+/* Replica-averaged spring force of one completed window (Sec. II, RSF):
+ * out [M] float64 = mean over each chain's replicas of the spring force at the
+ * window end, reduced in float64 in a fixed order. */
+bd_status bd_replica_average(bd_ctx* ctx, int64_t window, double* out);
+
+/* Time-averaged spring force of one completed window (Sec. II, TSF):
+ * out [M] float64 = mean of the parent's spring force over the window's steps. */
+bd_status bd_time_average(bd_ctx* ctx, int64_t window, double* out);
+
+/* Mechano-reactive events (Sec. I threshold rupture; Sec. III Bell kinetics):
+ * applies the TSF and RSF criteria to every window completed since the last
+ * call, then writes the first event of every (chain, spring, criterion, kind)
+ * seen so far, ordered by chain, spring, criterion, kind, into out[capacity]
+ * (host or device), sets *n_out (host) to their number and, if log_surv is not
+ * NULL, writes log_surv [n_chains][3] float64 = -sum over springs of the
+ * integrated Bell hazard per criterion. Synchronises the stream.
+ * BD_E_CAPACITY if there are more than capacity events (*n_out holds the
+ * count; out holds the first capacity). */
+bd_status bd_detect_events(bd_ctx* ctx, bd_event* out, int64_t capacity, int64_t* n_out,
+                           double* log_surv);
+
+/* Kinetic state per criterion q and spring m (after applying pending windows):
+ * hazard [3][M] float64 integrated Bell hazard; first_thr / first_bell
+ * [3][M] int64 first event step or -1. Any pointer may be NULL. */
+bd_status bd_get_kinetics(bd_ctx* ctx, double* hazard, int64_t* first_thr,
+                          int64_t* first_bell);
+
+/* Conformations in each chain's centre-of-mass frame (Eq. 5 frame), float64.
+ * all_slots = 0: parents, [sum N][3]. all_slots = 1: every slot, chain-major,
+ * slot 0 (parent) then replicas 1..N_R, [sum (N_R+1) N][3]. *step (may be
+ * NULL) receives the global step. */
+bd_status bd_get_positions(bd_ctx* ctx, int32_t all_slots, double* out, int64_t* step);
+
+/* Restart: every parent <- pos (float64 [sum N][3], any frame), replicas
+ * spawned from it, global step <- step (a multiple of window_steps), window
+ * history and kinetic state cleared. */
+bd_status bd_set_positions(bd_ctx* ctx, const double* pos, int64_t step);
+
+/* Counters and sizes (host struct). */
+bd_status bd_get_info(bd_ctx* ctx, bd_info* out);
+
+/* Kernel timing for measurement tools. enable != 0: from now on every
+ * parent-kernel and replica-kernel launch of bd_step is bracketed by CUDA
+ * events on the context's stream (enable = 0 stops). bd_kernel_times
+ * synchronises the stream, returns the accumulated device time in
+ * milliseconds and the launch counts since the last call (index 0: parent
+ * kernels, 1: replica kernels) and resets them. ms and launches are host
+ * arrays of 2; either may be NULL. */
+bd_status bd_enable_timing(bd_ctx* ctx, int32_t enable);
+bd_status bd_kernel_times(bd_ctx* ctx, double* ms, int64_t* launches);
+
+/* Diagnostic: the three standard normals the integrator draws for each of n
+ * counters ctr [n][4] (word 1 = slot | stream << 24) under key `seed`, in the
+ * given precision, written as float64 [n][3]. ctr and out may be host or
+ * device. Runs on the current device and stream `stream`; synchronises. */
+bd_status bd_philox_normals(uint64_t seed, int64_t n, const uint32_t* ctr, int32_t precision,
+                            double* out, void* stream);
+
+/* Message of the last failure on ctx (never NULL). */
+const char* bd_last_error(const bd_ctx* ctx);
+/* Name of a status code (never NULL). */
+const char* bd_status_string(bd_status s);
+/* Releases the context and its device memory; NULL is ignored. */
+void bd_destroy(bd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDRA_H */

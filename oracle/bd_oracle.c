@@ -282,6 +282,7 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
     for (int c = 0; c < C; ++c) {
         const ora_chain* ch = &p->chains[c];
         const int N = ch->n_beads, R = ch->n_replicas;
+        const uint32_t cid = p->chain_ids ? (uint32_t)p->chain_ids[c] : (uint32_t)c;
         const int64_t so = spr_off[c];
         double* parent = pos + 3 * bead_off[c];
         double* rep = (double*)malloc(sizeof(double) * 3 * (size_t)N * (size_t)R);
@@ -294,7 +295,7 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
 
         for (int q = 0; q < 3; ++q)
             for (int i = 0; i + 1 < N; ++i) {
-                E[q * N + i] = ora_exp1(p->seed, (uint32_t)i, (uint32_t)q, (uint32_t)c);
+                E[q * N + i] = ora_exp1(p->seed, (uint32_t)i, (uint32_t)q, cid);
                 if (exp1) exp1[q * M + so + i] = E[q * N + i];
             }
 
@@ -314,7 +315,7 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
                 for (int s = 0; s < Sw; ++s) {
                     for (int i = 0; i < N; ++i)
                         ora_normals3(p->seed, (uint32_t)i, slot, ORA_STREAM_BD,
-                                     (uint32_t)(t + s), (uint32_t)c, &xi[3 * i]);
+                                     (uint32_t)(t + s), cid, &xi[3 * i]);
                     nover += ora_em_step(ch, p->dt, p->s_min, rk, xi);
                 }
                 if (Sw == S) {
@@ -328,7 +329,7 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
             for (int s = 0; s < Sw; ++s) {
                 for (int i = 0; i < N; ++i)
                     ora_normals3(p->seed, (uint32_t)i, 0u, ORA_STREAM_BD, (uint32_t)(t + s),
-                                 (uint32_t)c, &xi[3 * i]);
+                                 cid, &xi[3 * i]);
                 nover += ora_em_step(ch, p->dt, p->s_min, parent, xi);
                 ora_tensions(ch, p->s_min, parent, f);
                 for (int i = 0; i + 1 < N; ++i) {

@@ -40,6 +40,7 @@ typedef struct {
     int32_t thr_mask;          /* bit q set: threshold criterion on ISF/TSF/RSF */
     int32_t bell_mask;         /* bit q set: Bell criterion on ISF/TSF/RSF */
     double s_min;              /* FENE overextension floor of 1 - H Q^2 / b */
+    const int32_t* chain_ids;  /* noise-counter chain id of each chain; NULL = 0, 1, ... */
 } ora_problem;
 
 /* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11). */

@@ -47,7 +47,7 @@ class _Problem(ctypes.Structure):
                 ("chains", ctypes.POINTER(_Chain)), ("dt", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("identical_noise", ctypes.c_int32),
                 ("thr_mask", ctypes.c_int32), ("bell_mask", ctypes.c_int32),
-                ("s_min", ctypes.c_double)]
+                ("s_min", ctypes.c_double), ("chain_ids", ctypes.POINTER(ctypes.c_int32))]
 
 
 _lib = None
@@ -198,18 +198,24 @@ def max_threads() -> int:
 def run(chains, dt: float, window_steps: int, n_steps: int, seed: int, pos0: np.ndarray,
         thr_mask: int = 7, bell_mask: int = 7, identical_noise: bool = False,
         s_min: float = S_MIN_DEFAULT, n_threads: int = 1,
-        want_replicas: bool = True, want_windows: bool = True) -> Dict[str, np.ndarray]:
+        want_replicas: bool = True, want_windows: bool = True,
+        chain_ids: Optional[Sequence[int]] = None) -> Dict[str, np.ndarray]:
     """Run the replica-averaging method from global step 0 on all chains.
 
     ``thr_mask`` / ``bell_mask`` use bit q for criterion q (0 ISF, 1 TSF,
-    2 RSF). Returns laboratory-frame parent positions, replica positions,
+    2 RSF). ``chain_ids`` gives each chain's id in the noise counter (default
+    0, 1, ...), so a sample of a larger problem can be run on its own.
+    Returns laboratory-frame parent positions, replica positions,
     per-window RSF/TSF profiles, Bell hazards, first-event steps (-1 none),
     Exp(1) thresholds and FENE-floor counts.
     """
     C = len(chains)
     cs = (_Chain * C)(*[_chain_struct(c) for c in chains])
+    ids = None if chain_ids is None else np.ascontiguousarray(chain_ids, dtype=np.int32)
     prob = _Problem(C, int(window_steps), cs, float(dt), int(seed), int(bool(identical_noise)),
-                    int(thr_mask), int(bell_mask), float(s_min))
+                    int(thr_mask), int(bell_mask), float(s_min),
+                    _p(ids, ctypes.c_int32) if ids is not None
+                    else ctypes.POINTER(ctypes.c_int32)())
     n_beads = sum(c.n_beads for c in chains)
     M = sum(c.n_beads - 1 for c in chains)
     n_rep_beads = sum(c.n_beads * c.n_replicas for c in chains)

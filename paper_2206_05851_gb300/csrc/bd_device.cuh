@@ -1,0 +1,208 @@
+// Device-side building blocks of the replica-averaged Brownian-dynamics path:
+// the counter-based noise of Eq. 1, the spring law and the parameter blocks
+// that the host hands to the kernels. Written for sm_103a.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/bdra.h"
+
+namespace bdra {
+
+// ---------------------------------------------------------------------------
+// Parameter blocks (plain data, shared by host and device code)
+// ---------------------------------------------------------------------------
+
+// One chain, as the kernels need it. Bond vectors Q_i = r_{i+1} - r_i of
+// every slot (0 = parent, 1..R = replicas) are stored slot-major:
+// state[(state_off + slot * (N-1) + i) * 3 + d].
+struct ChainDev {
+    int32_t N, R, n_groups, pad;
+    int64_t bead_off;    // first bead of this chain in a [sum N][3] position array
+    int64_t slot_bead_off;  // first bead in an all-slot [sum (R+1) N][3] array
+    int64_t state_off;   // bond index of slot 0, bond 0
+    int64_t spr_off;     // first spring of this chain in an [M] profile
+    int64_t part_off;    // first entry of group 0 in a per-window partial row
+    double H, Hinvb;     // spring constant; H/b for FENE, 0 for Hooke
+    double kxx, kyy, kzz, kxz;   // velocity gradient, v = kappa . r
+    double f_c, k0, dx;  // threshold force; Bell rate k0 exp(f dx)
+};
+
+// One CTA's work: the parent of `chain` plus replicas rep_begin+1 ..
+// rep_begin+rep_count.
+struct ItemDev {
+    int32_t chain, group, rep_begin, rep_count;
+};
+
+struct StepParams {
+    const ChainDev* chains;
+    const ItemDev* items;       // replica kernel: one (chain, group) per CTA
+    const int32_t* parent_items;  // parent kernel: chain ids of this launch
+    int32_t n_parent_items;
+    int32_t parent_G;           // lanes per parent in the parent kernel
+    void* state;                // T [state_elems][3]
+    void* snap;                 // T [chunk windows][M][3] parent at window starts
+    int64_t w_snap0;            // window index of snapshot 0
+    double* part_hist;          // [max_windows][part_stride] per-group replica sums
+    double* tsf_hist;           // [max_windows][M] parent window means
+    double* tsf_acc;            // [M] parent's running sum inside the current window
+    double* lam;                // [3][M] integrated Bell hazard
+    int64_t* first_thr;         // [3][M]
+    int64_t* first_bell;        // [3][M]
+    const double* exp1;         // [3][M] Exp(1) thresholds
+    unsigned long long* overext;  // [n_chains]
+    int64_t part_stride, M;
+    int64_t t0, n_steps;
+    double dt, s_min;
+    int32_t S, flags, thr_mask, bell_mask;
+    uint32_t key0, key1;
+    // Philox round keys (key + r * Weyl constant, r = 0..9): read straight
+    // from the kernel-parameter bank instead of occupying registers.
+    uint32_t rk0[10], rk1[10];
+};
+
+enum { CRIT_Q_ISF = 0, CRIT_Q_TSF = 1, CRIT_Q_RSF = 2 };
+enum { STREAM_BD = 0, STREAM_EXP1 = 1 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies, XOR of the high halves with the other counter words
+// and the round key, and a fixed permutation; Weyl key schedule. The key is
+// uniform across the grid, so the round keys fold into uniform registers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c.x;
+        const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Same generator with precomputed round keys rk0[r] = k0 + r W0,
+// rk1[r] = k1 + r W1 (as held in StepParams).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk0)[10],
+                                                  const uint32_t (&rk1)[10])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c.x;
+        const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Standard normals from one Philox output (Box-Muller): the pair
+// sqrt(-2 ln u0) (cos, sin)(2 pi u1) and the cosine branch of the pair from
+// (u2, u3), with u = (x + 1/2) 2^-32.
+// ---------------------------------------------------------------------------
+template <typename T, bool FAST> struct Normals;
+
+template <bool FAST> struct Normals<float, FAST> {
+    static __device__ __forceinline__ void draw(uint4 x, float& z0, float& z1, float& z2)
+    {
+        const float s = 2.3283064365386963e-10f;       // 2^-32
+        const float h = 1.1641532182693481e-10f;       // 2^-33
+        const float u0 = fmaf((float)x.x, s, h);
+        const float u1 = fmaf((float)x.y, s, h);
+        const float u2 = fmaf((float)x.z, s, h);
+        const float u3 = fmaf((float)x.w, s, h);
+        if (FAST) {
+            // Hardware log2 / sin / cos. The angles are shifted to (-pi, pi),
+            // the accurate range of the hardware units: cos(2 pi u) =
+            // -cos(2 pi u - pi), sin(2 pi u) = -sin(2 pi u - pi).
+            const float ln2 = 0.69314718055994531f;
+            const float twopi = 6.2831853071795865f, pi = 3.1415926535897932f;
+            float a0 = -2.0f * ln2 * __log2f(u0);
+            float a2 = -2.0f * ln2 * __log2f(u2);
+            a0 = fmaxf(a0, 0.0f);
+            a2 = fmaxf(a2, 0.0f);
+            float r0, r2;
+            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(a0));
+            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r2) : "f"(a2));
+            float sn, cs;
+            __sincosf(fmaf(u1, twopi, -pi), &sn, &cs);
+            const float c3 = __cosf(fmaf(u3, twopi, -pi));
+            z0 = -r0 * cs;
+            z1 = -r0 * sn;
+            z2 = -r2 * c3;
+        } else {
+            const float r0 = sqrtf(-2.0f * logf(u0));
+            const float r2 = sqrtf(-2.0f * logf(u2));
+            float sn, cs;
+            sincospif(2.0f * u1, &sn, &cs);
+            z0 = r0 * cs;
+            z1 = r0 * sn;
+            z2 = r2 * cospif(2.0f * u3);
+        }
+    }
+};
+
+template <bool FAST> struct Normals<double, FAST> {
+    static __device__ __forceinline__ void draw(uint4 x, double& z0, double& z1, double& z2)
+    {
+        const double s = 2.3283064365386963e-10;       // 2^-32
+        const double u0 = ((double)x.x + 0.5) * s;
+        const double u1 = ((double)x.y + 0.5) * s;
+        const double u2 = ((double)x.z + 0.5) * s;
+        const double u3 = ((double)x.w + 0.5) * s;
+        const double r0 = sqrt(-2.0 * log(u0));
+        const double r2 = sqrt(-2.0 * log(u2));
+        double sn, cs;
+        sincospi(2.0 * u1, &sn, &cs);
+        z0 = r0 * cs;
+        z1 = r0 * sn;
+        z2 = r2 * cospi(2.0 * u3);
+    }
+};
+
+template <typename T, bool FAST>
+__device__ __forceinline__ void bead_noise(uint32_t bead, uint32_t slot, uint32_t step,
+                                           uint32_t chain, const StepParams& p,
+                                           T& z0, T& z1, T& z2)
+{
+    const uint4 x = philox4x32_10_rk(
+        make_uint4(bead, slot | ((uint32_t)STREAM_BD << 24), step, chain), p.rk0, p.rk1);
+    Normals<T, FAST>::draw(x, z0, z1, z2);
+}
+
+// ---------------------------------------------------------------------------
+// Spring law: F = H Q / s with s = 1 - (H/b) Q^2 (FENE, floored at s_min;
+// Hooke has H/b = 0 so s = 1). Returns the coefficient H / s.
+// ---------------------------------------------------------------------------
+template <typename T, bool FAST> struct Div {
+    static __device__ __forceinline__ T div(T a, T b) { return a / b; }
+};
+template <> struct Div<float, true> {
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+};
+
+template <typename T, bool FAST>
+__device__ __forceinline__ T spring_coef(T qx, T qy, T qz, T H, T Hinvb, T smin, int& floored)
+{
+    const T q2 = qx * qx + qy * qy + qz * qz;
+    T s = T(1) - Hinvb * q2;
+    if (s < smin) { s = smin; ++floored; }
+    return Div<T, FAST>::div(H, s);
+}
+
+template <typename T, bool FAST>
+__device__ __forceinline__ T spring_tension(T qx, T qy, T qz, T H, T Hinvb, T smin)
+{
+    int dummy = 0;
+    const T c = spring_coef<T, FAST>(qx, qy, qz, H, Hinvb, smin, dummy);
+    return c * sqrt(qx * qx + qy * qy + qz * qz);
+}
+
+}  // namespace bdra

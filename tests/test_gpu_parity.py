@@ -1,0 +1,363 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs and the same Philox draws.
+
+Tolerances (relative, per chain, centre-of-mass frame): 1e-10 in FP64 mode,
+1e-4 in FP32 mode; event steps equal in FP64 mode; FP32 event steps equal
+except at near-ties of the force with the threshold (|f - f_c| < 1e-3 f_c).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2206_05851_gb300 import bdra
+from paper_2206_05851_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {bdra.BD_PREC_FP64: 1e-10, bdra.BD_PREC_FP32: 1e-4}
+PRECS = [bdra.BD_PREC_FP64, bdra.BD_PREC_FP32]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2206_05851_gb300 import build as B
+    B.build()
+    torch.cuda.init()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def gpu_run(chains, dt, S, steps, seed, pos0, prec, thr=7, bell=7, flags=0, lanes=0,
+            want_all=True):
+    total = sum(steps)
+    ctx = bdra.Context(chains, dt, S, seed, pos0, precision=prec, max_windows=total // S + 1,
+                       thr_mask=thr, bell_mask=bell, flags=flags, stream=_stream(),
+                       lanes_hint=lanes)
+    for n in steps:
+        ctx.step(n)
+    nw = total // S
+    out = dict(pos=ctx.positions(False),
+               allpos=ctx.positions(True) if want_all else None,
+               rsf=np.array([ctx.replica_average(w) for w in range(nw)]).reshape(nw, ctx.M),
+               tsf=np.array([ctx.time_average(w) for w in range(nw)]).reshape(nw, ctx.M))
+    out["haz"], out["first_thr"], out["first_bell"] = ctx.kinetics()
+    out["events"], out["log_surv"] = ctx.events()
+    out["info"] = ctx.info()
+    ctx.close()
+    return out
+
+
+def ora_run(chains, dt, S, n, seed, pos0, thr=7, bell=7, identical=False, chain_ids=None):
+    return O.run(chains, dt, S, n, seed, pos0, thr_mask=thr, bell_mask=bell,
+                 identical_noise=identical, n_threads=8, chain_ids=chain_ids)
+
+
+def _split_replicas(allpos, chains):
+    """GPU all-slot array -> (parents, replicas chain-major) like the oracle."""
+    par, rep, o = [], [], 0
+    for c in chains:
+        blk = allpos[o:o + (c.n_replicas + 1) * c.n_beads].reshape(c.n_replicas + 1, c.n_beads, 3)
+        par.append(blk[0])
+        rep.append(blk[1:].reshape(-1, 3))
+        o += (c.n_replicas + 1) * c.n_beads
+    return np.concatenate(par), np.concatenate(rep)
+
+
+def rel_err_chains(got, want, sizes):
+    worst, o = 0.0, 0
+    for n in sizes:
+        g, w = got[o:o + n], want[o:o + n]
+        worst = max(worst, float(np.abs(g - w).max() / max(np.abs(w).max(), 1e-300)))
+        o += n
+    return worst
+
+
+def compare_states(g, r, chains, tol):
+    nb = [c.n_beads for c in chains]
+    assert rel_err_chains(g["pos"], O.com_frame(r["pos"], nb), nb) <= tol
+    if g["allpos"] is not None:
+        par, rep = _split_replicas(g["allpos"], chains)
+        np.testing.assert_array_equal(par, g["pos"])
+        sizes = [c.n_beads for c in chains for _ in range(c.n_replicas)]
+        assert rel_err_chains(rep, O.com_frame(r["rep"], sizes), sizes) <= tol
+
+
+def compare_profiles(g, r, tol):
+    for key in ("rsf", "tsf"):
+        a, b = g[key], r[key]
+        assert a.shape == b.shape
+        if a.size:
+            err = np.abs(a - b).max() / np.abs(b).max()
+            assert err <= tol, f"{key} rel err {err:.3e}"
+
+
+def compare_events_exact(g, r):
+    np.testing.assert_array_equal(g["first_thr"], r["first_thr"])
+    np.testing.assert_array_equal(g["first_bell"], r["first_bell"])
+    np.testing.assert_allclose(g["haz"], r["lam"], rtol=1e-9, atol=1e-300)
+
+
+def compare_events_fp32(g, r, chains, S):
+    """Window criteria: equal except at near-ties; ISF: nearly all equal."""
+    fc = np.concatenate([[c.f_c] * (c.n_beads - 1) for c in chains])
+    for q, key in ((O.TSF, "tsf"), (O.RSF, "rsf")):
+        prof = r[key]
+        for m in np.nonzero(g["first_thr"][q] != r["first_thr"][q])[0]:
+            last = max(g["first_thr"][q][m], r["first_thr"][q][m])
+            upto = prof.shape[0] if last < 0 else last // S
+            near = np.abs(prof[:upto, m] - fc[m]) < 1e-3 * fc[m]
+            assert near.any(), f"criterion {q} spring {m}: threshold event differs, no near-tie"
+    n_isf = max(1, int((r["first_thr"][O.ISF] >= 0).sum()))
+    diff = int((g["first_thr"][O.ISF] != r["first_thr"][O.ISF]).sum())
+    assert diff <= max(1, n_isf // 20)
+    np.testing.assert_allclose(g["haz"], r["lam"], rtol=2e-3, atol=1e-12)
+
+
+def c1_like(rate_wi=2.0, n=20, R=16, b=50.0):
+    return I.Chain(n_beads=n, n_replicas=R, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL, H=1.0,
+                   b=b, rate=I.rate_from_wi(rate_wi, n), f_c=0.9 * math.sqrt(b))
+
+
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_normals_match_oracle(prec):
+    rng = np.random.default_rng(0)
+    n = 200_000
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:, 1] &= 0x00FFFFFF
+    seed = 0x1234_5678_9ABC_DEF0
+    got = np.zeros((n, 3))
+    bdra.bd_philox_normals(seed, ctr, prec, got)
+    want = O.normals3_many(seed, ctr)
+    if prec == bdra.BD_PREC_FP64:
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+    else:
+        err = np.abs(got - want)
+        assert np.median(err) < 1e-6
+        assert np.quantile(err, 0.999) < 2e-5
+        assert err.max() < 2e-3       # rare draws with u -> 1 (tiny normal, coarse log)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_single_chain_1000_steps(prec):
+    wl = I.single_chain_fp64(n_steps=1000)
+    pos0 = I.initial_positions(wl)
+    g = gpu_run(wl.chains, wl.dt, wl.window_steps, [1000], wl.seed, pos0, prec)
+    r = ora_run(wl.chains, wl.dt, wl.window_steps, 1000, wl.seed, pos0)
+    compare_states(g, r, wl.chains, TOL[prec])
+    compare_profiles(g, r, TOL[prec])
+    assert g["info"].overextensions == int(r["overext"].sum()) == 0
+
+
+def _ragged_chains():
+    spec = [(2, 1, I.FLOW_NONE, 0.0), (5, 3, I.FLOW_SHEAR, 1.5), (20, 16, I.FLOW_UNIAXIAL, 0.3),
+            (33, 7, I.FLOW_PLANAR, 0.2), (100, 64, I.FLOW_PLANAR, 0.01),
+            (129, 9, I.FLOW_SHEAR, 0.05), (257, 5, I.FLOW_UNIAXIAL, 0.002),
+            (500, 130, I.FLOW_SHEAR, 0.01)]
+    out = []
+    for k, (n, R, flow, rate) in enumerate(spec):
+        b = 20.0 + 15 * k
+        out.append(I.Chain(n_beads=n, n_replicas=R, spring=I.SPRING_FENE, flow=flow, H=1.0 + 0.1 * k,
+                           b=b, rate=rate, f_c=0.35 * math.sqrt(b * (1.0 + 0.1 * k)),
+                           k0=1e-3, dx=1.0 / math.sqrt(b)))
+    return out
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_batch_split_calls(prec):
+    chains = _ragged_chains()
+    S, dt, seed = 7, 1e-3, 11
+    steps = [10, 1, 33, 96]          # 140 steps = 20 windows; calls end mid-window
+    pos0 = I.initial_positions(I.custom(chains, dt, S, 140), seed=5)
+    g = gpu_run(chains, dt, S, steps, seed, pos0, prec)
+    r = ora_run(chains, dt, S, 140, seed, pos0)
+    compare_states(g, r, chains, TOL[prec])
+    compare_profiles(g, r, TOL[prec])
+    if prec == bdra.BD_PREC_FP64:
+        compare_events_exact(g, r)
+    else:
+        compare_events_fp32(g, r, chains, S)
+
+
+def _event_chains():
+    b = 30.0
+    return [I.Chain(n_beads=16, n_replicas=24, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL,
+                    b=b, rate=0.8, f_c=0.55 * math.sqrt(b), k0=1e-4, dx=8.0 / math.sqrt(b)),
+            I.Chain(n_beads=40, n_replicas=12, spring=I.SPRING_FENE, flow=I.FLOW_SHEAR,
+                    b=b, rate=3.0, f_c=0.5 * math.sqrt(b), k0=1e-4, dx=8.0 / math.sqrt(b)),
+            I.Chain(n_beads=9, n_replicas=5, spring=I.SPRING_HOOKE, flow=I.FLOW_PLANAR,
+                    b=b, rate=0.4, f_c=2.5, k0=1e-3, dx=1.0)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_events_and_kinetics(prec):
+    chains = _event_chains()
+    S, dt, n, seed = 20, 2e-3, 2000, 3
+    pos0 = I.initial_positions(I.custom(chains, dt, S, n), seed=8)
+    g = gpu_run(chains, dt, S, [n], seed, pos0, prec, want_all=False)
+    r = ora_run(chains, dt, S, n, seed, pos0)
+    assert (r["first_thr"] >= 0).sum() > 20 and (r["first_bell"] >= 0).sum() > 10
+    if prec == bdra.BD_PREC_FP64:
+        compare_events_exact(g, r)
+    else:
+        compare_events_fp32(g, r, chains, S)
+    # the event list is the kinetic state, in (chain, spring, criterion, kind) order
+    ev = g["events"]
+    so = I.spring_offsets(chains)
+    m = so[ev["chain"]] + ev["spring"]
+    for e, mm in zip(ev, m):
+        arr = g["first_thr"] if e["kind"] == 0 else g["first_bell"]
+        assert arr[e["criterion"], mm] == e["step"]
+    assert len(ev) == (g["first_thr"] >= 0).sum() + (g["first_bell"] >= 0).sum()
+    keys = list(zip(ev["chain"], ev["spring"], ev["criterion"], ev["kind"]))
+    assert keys == sorted(keys)
+    # log-survival = -sum of hazards per chain and criterion
+    for c in range(len(chains)):
+        np.testing.assert_allclose(g["log_surv"][c], -g["haz"][:, so[c]:so[c + 1]].sum(axis=1),
+                                   rtol=1e-12)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_identical_noise_replicas_reproduce_parent(prec):
+    chains = _ragged_chains()[:6]
+    S, dt = 13, 1e-3
+    pos0 = I.initial_positions(I.custom(chains, dt, S, 91), seed=2)
+    g = gpu_run(chains, dt, S, [91], 4, pos0, prec, flags=bdra.BD_FLAG_IDENTICAL_NOISE)
+    par, rep = _split_replicas(g["allpos"], chains)
+    o = 0
+    for c, ch in enumerate(chains):
+        p = g["pos"][sum(x.n_beads for x in chains[:c]):][:ch.n_beads]
+        for k in range(ch.n_replicas):
+            np.testing.assert_array_equal(rep[o + k * ch.n_beads:o + (k + 1) * ch.n_beads], p)
+        o += ch.n_replicas * ch.n_beads
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_results_do_not_depend_on_tile(prec):
+    chains = [I.Chain(n_beads=31, n_replicas=11, spring=I.SPRING_FENE, flow=I.FLOW_SHEAR,
+                      b=40.0, rate=1.0, f_c=3.0, k0=1e-3, dx=0.3),
+              I.Chain(n_beads=20, n_replicas=40, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL,
+                      b=40.0, rate=0.2, f_c=3.0, k0=1e-3, dx=0.3)]
+    S, dt = 10, 1e-3
+    pos0 = I.initial_positions(I.custom(chains, dt, S, 60), seed=9)
+    runs = [gpu_run(chains, dt, S, [60], 7, pos0, prec, lanes=L) for L in (2, 4, 7, 10, 13, 16)]
+    for g in runs[1:]:
+        for key in ("allpos", "rsf", "tsf", "haz", "first_thr", "first_bell"):
+            np.testing.assert_array_equal(g[key], runs[0][key])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_edge_cases(prec):
+    # N = 2 (one spring), R = 1, window of one step
+    ch = [I.Chain(n_beads=2, n_replicas=1, spring=I.SPRING_FENE, b=10.0, f_c=2.0, k0=1e-2, dx=0.5)]
+    pos0 = np.array([[0.0, 0.0, 0.0], [1.0, 0.5, -0.2]])
+    g = gpu_run(ch, 1e-3, 1, [5, 0, 7], 1, pos0, prec)
+    r = ora_run(ch, 1e-3, 1, 12, 1, pos0)
+    compare_states(g, r, ch, TOL[prec])
+    compare_profiles(g, r, TOL[prec])
+    # maximum chain length (512 beads, 16 springs per lane, 32 lanes per slot)
+    ch = [I.Chain(n_beads=512, n_replicas=3, spring=I.SPRING_FENE, flow=I.FLOW_SHEAR, b=100.0,
+                  rate=0.01)]
+    pos0 = I.initial_positions(I.custom(ch, 1e-3, 4, 12), seed=3)
+    g = gpu_run(ch, 1e-3, 4, [12], 2, pos0, prec, thr=0, bell=0)
+    r = ora_run(ch, 1e-3, 4, 12, 2, pos0, thr=0, bell=0)
+    compare_states(g, r, ch, TOL[prec])
+    compare_profiles(g, r, TOL[prec])
+
+
+def test_many_replica_groups():
+    # 1000 replicas of a short chain: several CTAs per chain, one parent copy
+    ch = [I.Chain(n_beads=24, n_replicas=1000, spring=I.SPRING_FENE, flow=I.FLOW_PLANAR,
+                  b=50.0, rate=0.05)]
+    pos0 = I.initial_positions(I.custom(ch, 1e-3, 10, 30), seed=4)
+    for prec in PRECS:
+        g = gpu_run(ch, 1e-3, 10, [30], 6, pos0, prec, thr=0, bell=0)
+        r = ora_run(ch, 1e-3, 10, 30, 6, pos0, thr=0, bell=0)
+        compare_states(g, r, ch, TOL[prec])
+        compare_profiles(g, r, TOL[prec])
+
+
+def test_capacity_and_state_errors():
+    ch = [I.Chain(n_beads=8, n_replicas=2, spring=I.SPRING_FENE, b=20.0, f_c=0.1)]
+    pos0 = I.initial_positions(I.custom(ch, 1e-3, 5, 10), seed=1)
+    ctx = bdra.Context(ch, 1e-3, 5, 0, pos0, max_windows=2, thr_mask=7, stream=_stream())
+    ctx.step(10)
+    with pytest.raises(bdra.BdError) as e:
+        ctx.step(5)
+    assert e.value.status == bdra.BD_E_CAPACITY
+    with pytest.raises(bdra.BdError):
+        ctx.replica_average(2)
+    # event capacity: count still reported
+    out = np.zeros(1, dtype=bdra.EVENT_DTYPE)
+    with pytest.raises(bdra.BdError) as e:
+        bdra.bd_detect_events(ctx.ptr, out, 1)
+    assert e.value.status == bdra.BD_E_CAPACITY
+    with pytest.raises(bdra.BdError):
+        ctx.set_positions(pos0, step=3)
+    ctx.close()
+
+
+def test_restart_and_spawn():
+    chains = _ragged_chains()[1:4]
+    S, dt = 10, 1e-3
+    pos0 = I.initial_positions(I.custom(chains, dt, S, 40), seed=6)
+    ctx = bdra.Context(chains, dt, S, 3, pos0, precision=bdra.BD_PREC_FP64, max_windows=8,
+                       thr_mask=7, bell_mask=7, stream=_stream())
+    ctx.step(25)
+    ctx.set_positions(pos0, 0)          # restart from the same conformation
+    ctx.step(40)
+    again = ctx.positions(True)
+    fresh = gpu_run(chains, dt, S, [40], 3, pos0, bdra.BD_PREC_FP64)
+    np.testing.assert_array_equal(again, fresh["allpos"])
+    np.testing.assert_array_equal(ctx.kinetics()[1], fresh["first_thr"])
+    ctx.step(5)
+    ctx.spawn()
+    par, rep = _split_replicas(ctx.positions(True), chains)
+    o, po = 0, 0
+    for ch in chains:
+        for k in range(ch.n_replicas):
+            np.testing.assert_allclose(rep[o + k * ch.n_beads:o + (k + 1) * ch.n_beads],
+                                       par[po:po + ch.n_beads], rtol=0, atol=1e-12)
+        o += ch.n_replicas * ch.n_beads
+        po += ch.n_beads
+    ctx.close()
+
+
+def test_device_and_host_buffers_agree():
+    import torch
+    chains = _ragged_chains()[2:4]
+    pos0 = I.initial_positions(I.custom(chains, 1e-3, 10, 30), seed=1)
+    ctx = bdra.Context(chains, 1e-3, 10, 2, torch.from_numpy(pos0).cuda(), max_windows=3,
+                       thr_mask=7, stream=_stream())
+    ctx.step(30)
+    d = torch.zeros(ctx.M, dtype=torch.float64, device="cuda")
+    bdra.bd_replica_average(ctx.ptr, 2, d)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d.cpu().numpy(), ctx.replica_average(2))
+    ctx.close()
+
+
+def test_full_size_sampled_parity():
+    # The benchmark's launch configuration: 1024 chains, N = 100, 64 replicas,
+    # planar elongation Wi = 5, FP32 integration. Sampled chains are re-run
+    # on their own by the oracle (same chain ids in the noise counter).
+    wl = I.planar_1024(n_steps=200)
+    pos0 = I.initial_positions(wl)
+    g = gpu_run(wl.chains, wl.dt, wl.window_steps, [200], wl.seed, pos0, bdra.BD_PREC_FP32,
+                thr=wl.thr_mask, bell=wl.bell_mask, want_all=False)
+    sample = [0, 517, 1023]
+    sub = [wl.chains[c] for c in sample]
+    sub_pos = np.concatenate([pos0[100 * c:100 * (c + 1)] for c in sample])
+    r = ora_run(sub, wl.dt, wl.window_steps, 200, wl.seed, sub_pos, thr=wl.thr_mask,
+                bell=wl.bell_mask, chain_ids=sample)
+    got = np.concatenate([g["pos"][100 * c:100 * (c + 1)] for c in sample])
+    assert rel_err_chains(got, O.com_frame(r["pos"], [100] * 3), [100] * 3) <= 1e-4
+    rs = np.concatenate([g["rsf"][:, 99 * c:99 * (c + 1)] for c in sample], axis=1)
+    assert np.abs(rs - r["rsf"]).max() / np.abs(r["rsf"]).max() <= 1e-4
