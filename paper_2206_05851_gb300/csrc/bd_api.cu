@@ -178,19 +178,13 @@ TileChoice choose_tile(int N, int R, int wmax, int hint)
     return best;
 }
 
+// The parent kernel is latency-bound (one slot per chain): the smallest tile
+// that fits a chain in one warp gives the shortest step.
 int choose_parent_tile(int N)
 {
-    int best = 0;
-    double best_u = -1;
-    for (int t = 0; t < kNumTiles; ++t) {
-        const int L = kTiles[t];
-        const int G = (N + L - 1) / L;
-        if (G > 32) continue;
-        const int P = 32 / G;
-        const double u = (double)P * N / (32.0 * L);
-        if (u > best_u + 1e-9) { best_u = u; best = L; }
-    }
-    return best;
+    for (int t = 0; t < kNumTiles; ++t)
+        if ((N + kTiles[t] - 1) / kTiles[t] <= 32) return kTiles[t];
+    return 0;
 }
 
 bd_status validate(bd_ctx* ctx, const bd_config* cfg)
@@ -303,7 +297,7 @@ bd_status plan(bd_ctx* ctx)
         rc.smem = std::max(rc.smem, smem);
         ctx->h_items.push_back(q.it);
     }
-    // parent launches: one per (L, G) class, four warps per CTA
+    // parent launches: one per (L, G) class, two warps per CTA
     std::stable_sort(par.begin(), par.end());
     ctx->h_parent_items.clear();
     ctx->par_classes.clear();
@@ -311,12 +305,12 @@ bd_status plan(bd_ctx* ctx)
         const int L = par[k].first.first, G = par[k].first.second;
         if (ctx->par_classes.empty() || ctx->par_classes.back().L != L ||
             ctx->par_classes.back().G != G)
-            ctx->par_classes.push_back(ParClass{L, G, 128, 0, (int)k, 0});
+            ctx->par_classes.push_back(ParClass{L, G, 64, 0, (int)k, 0});
         ctx->par_classes.back().item_count++;
         ctx->h_parent_items.push_back(par[k].second);
     }
     for (ParClass& pc : ctx->par_classes) {
-        const int per_cta = 4 * (32 / pc.G);
+        const int per_cta = (pc.threads / 32) * (32 / pc.G);
         pc.grid = (pc.item_count + per_cta - 1) / per_cta;
     }
     // snapshot chunk: up to 64 windows, capped at ~512 MB

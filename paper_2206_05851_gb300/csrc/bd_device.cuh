@@ -115,29 +115,33 @@ template <bool FAST> struct Normals<float, FAST> {
         const float s = 2.3283064365386963e-10f;       // 2^-32
         const float h = 1.1641532182693481e-10f;       // 2^-33
         const float u0 = fmaf((float)x.x, s, h);
-        const float u1 = fmaf((float)x.y, s, h);
         const float u2 = fmaf((float)x.z, s, h);
-        const float u3 = fmaf((float)x.w, s, h);
         if (FAST) {
-            // Hardware log2 / sin / cos. The angles are shifted to (-pi, pi),
-            // the accurate range of the hardware units: cos(2 pi u) =
-            // -cos(2 pi u - pi), sin(2 pi u) = -sin(2 pi u - pi).
+            // Angles 2 pi u - pi in (-pi, pi), the accurate range of the
+            // hardware sin/cos: cos(2 pi u) = -cos(2 pi u - pi) and likewise
+            // for sin. The angle uniforms take the top 23 bits of their word
+            // (float in [1, 2) built from the bits; error <= 2^-24 in u); the
+            // radial uniforms, which enter a logarithm, are converted in full.
             const float ln2 = 0.69314718055994531f;
-            const float twopi = 6.2831853071795865f, pi = 3.1415926535897932f;
-            float a0 = -2.0f * ln2 * __log2f(u0);
-            float a2 = -2.0f * ln2 * __log2f(u2);
-            a0 = fmaxf(a0, 0.0f);
-            a2 = fmaxf(a2, 0.0f);
+            const float twopi = 6.2831853071795865f;
+            const float off = -6.2831853071795865f * (1.5f - 5.9604644775390625e-8f);
+            const float f1 = __uint_as_float(0x3F800000u | (x.y >> 9));
+            const float f3 = __uint_as_float(0x3F800000u | (x.w >> 9));
+            const float a0 = -2.0f * ln2 * __log2f(u0);
+            const float a2 = -2.0f * ln2 * __log2f(u2);
             float r0, r2;
-            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(a0));
-            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r2) : "f"(a2));
+            // |a| guards the approximate log2 of values within an ulp of 1
+            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(fabsf(a0)));
+            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r2) : "f"(fabsf(a2)));
             float sn, cs;
-            __sincosf(fmaf(u1, twopi, -pi), &sn, &cs);
-            const float c3 = __cosf(fmaf(u3, twopi, -pi));
+            __sincosf(fmaf(f1, twopi, off), &sn, &cs);
+            const float c3 = __cosf(fmaf(f3, twopi, off));
             z0 = -r0 * cs;
             z1 = -r0 * sn;
             z2 = -r2 * c3;
         } else {
+            const float u1 = fmaf((float)x.y, s, h);
+            const float u3 = fmaf((float)x.w, s, h);
             const float r0 = sqrtf(-2.0f * logf(u0));
             const float r2 = sqrtf(-2.0f * logf(u2));
             float sn, cs;
@@ -188,11 +192,16 @@ template <> struct Div<float, true> {
     static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
 };
 
+template <typename T>
+__device__ __forceinline__ T bond_q2(T qx, T qy, T qz)
+{
+    return fma(qx, qx, fma(qy, qy, qz * qz));
+}
+
 template <typename T, bool FAST>
 __device__ __forceinline__ T spring_coef(T qx, T qy, T qz, T H, T Hinvb, T smin, int& floored)
 {
-    const T q2 = qx * qx + qy * qy + qz * qz;
-    T s = T(1) - Hinvb * q2;
+    T s = fma(-Hinvb, bond_q2(qx, qy, qz), T(1));
     if (s < smin) { s = smin; ++floored; }
     return Div<T, FAST>::div(H, s);
 }
@@ -202,7 +211,7 @@ __device__ __forceinline__ T spring_tension(T qx, T qy, T qz, T H, T Hinvb, T sm
 {
     int dummy = 0;
     const T c = spring_coef<T, FAST>(qx, qy, qz, H, Hinvb, smin, dummy);
-    return c * sqrt(qx * qx + qy * qy + qz * qz);
+    return c * sqrt(bond_q2(qx, qy, qz));
 }
 
 }  // namespace bdra

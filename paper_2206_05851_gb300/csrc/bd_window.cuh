@@ -39,9 +39,20 @@
 namespace bdra {
 
 // Launch bound per tile: float 512 threads (16 warps, 128 registers: four
-// warps on each SM sub-partition), double 256 threads.
+// warps on each SM sub-partition), double 256 threads. The build may override
+// them (BD_F32_THREADS / BD_F32_MIN_BLOCKS) to trade registers for warps.
+#ifndef BD_F32_THREADS
+#define BD_F32_THREADS 512
+#endif
+#ifndef BD_F32_MIN_BLOCKS
+#define BD_F32_MIN_BLOCKS 1
+#endif
+#ifndef BD_F64_THREADS
+#define BD_F64_THREADS 256
+#endif
 template <typename T, int L> struct Tile {
-    static constexpr int max_threads = (sizeof(T) == 4) ? 512 : 256;
+    static constexpr int max_threads = (sizeof(T) == 4) ? BD_F32_THREADS : BD_F64_THREADS;
+    static constexpr int min_blocks = (sizeof(T) == 4) ? BD_F32_MIN_BLOCKS : 1;
 };
 
 template <typename T> __device__ __forceinline__ T shfl(T v, int src)
@@ -183,7 +194,7 @@ __device__ __forceinline__ void store_bonds(const T (&qx)[L], const T (&qy)[L], 
 // parent kernel at every window start inside the current chunk.
 // ---------------------------------------------------------------------------
 template <typename T, int L, bool FAST>
-__global__ void __launch_bounds__(Tile<T, L>::max_threads, 1)
+__global__ void __launch_bounds__(Tile<T, L>::max_threads, Tile<T, L>::min_blocks)
 replica_kernel(const StepParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -279,15 +290,18 @@ parent_kernel(const StepParams p)
     const int64_t M = p.M;
     const bool isf_thr = (p.thr_mask & BD_CRIT_ISF) != 0;
     const bool isf_bell = (p.bell_mask & BD_CRIT_ISF) != 0;
-    const T fc = (T)ch.f_c, k0dt = (T)(ch.k0 * p.dt), dxs = (T)ch.dx;
+    const T fc = (T)ch.f_c;
+    const double k0dt = ch.k0 * p.dt, dxs = ch.dx;
 
     T* state = reinterpret_cast<T*>(p.state) + ch.state_off * 3;
     T* snap = reinterpret_cast<T*>(p.snap);
     T qx[L], qy[L], qz[L];
     load_bonds<T, L>(qx, qy, qz, state, lc);
 
-    // per-spring sampling state of this lane's springs
-    T tsf[L], haz[L], rem[L];
+    // per-spring sampling state of this lane's springs; the Bell hazard is
+    // accumulated in float64 whatever the integration precision
+    T tsf[L];
+    double haz[L], rem[L];
     uint32_t thr_done = 0, bell_done = 0;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
@@ -295,8 +309,8 @@ parent_kernel(const StepParams p)
         const int64_t m = ch.spr_off + i;
         const bool v = active && i < nb;
         tsf[j] = v ? (T)p.tsf_acc[m] : T(0);
-        haz[j] = T(0);
-        rem[j] = v ? (T)(p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m]) : T(0);
+        haz[j] = 0.0;
+        rem[j] = v ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0;
         if (!v || p.first_thr[CRIT_Q_ISF * M + m] >= 0) thr_done |= 1u << j;
         if (!v || p.first_bell[CRIT_Q_ISF * M + m] >= 0) bell_done |= 1u << j;
     }
@@ -322,7 +336,7 @@ parent_kernel(const StepParams p)
                         p.first_thr[CRIT_Q_ISF * M + ch.spr_off + i] = t + 1;
                     }
                     if (isf_bell) {
-                        haz[j] = fma(k0dt, exp(dxs * f), haz[j]);
+                        haz[j] = fma(k0dt, exp(dxs * (double)f), haz[j]);
                         if (!(bell_done & (1u << j)) && haz[j] >= rem[j]) {
                             bell_done |= 1u << j;
                             p.first_bell[CRIT_Q_ISF * M + ch.spr_off + i] = t + 1;
@@ -342,10 +356,10 @@ parent_kernel(const StepParams p)
                         p.tsf_hist[w * M + m] = (double)tsf[j] / (double)p.S;
                         tsf[j] = T(0);
                         if (isf_bell) {
-                            const double lam = p.lam[CRIT_Q_ISF * M + m] + (double)haz[j];
+                            const double lam = p.lam[CRIT_Q_ISF * M + m] + haz[j];
                             p.lam[CRIT_Q_ISF * M + m] = lam;
-                            haz[j] = T(0);
-                            rem[j] = (T)(p.exp1[CRIT_Q_ISF * M + m] - lam);
+                            haz[j] = 0.0;
+                            rem[j] = p.exp1[CRIT_Q_ISF * M + m] - lam;
                         }
                     }
                 }
@@ -361,7 +375,7 @@ parent_kernel(const StepParams p)
             if (i < nb) {
                 const int64_t m = ch.spr_off + i;
                 p.tsf_acc[m] = (double)tsf[j];
-                if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += (double)haz[j];
+                if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += haz[j];
             }
         }
     }

@@ -116,7 +116,13 @@ def compare_events_fp32(g, r, chains, S):
     n_isf = max(1, int((r["first_thr"][O.ISF] >= 0).sum()))
     diff = int((g["first_thr"][O.ISF] != r["first_thr"][O.ISF]).sum())
     assert diff <= max(1, n_isf // 20)
-    np.testing.assert_allclose(g["haz"], r["lam"], rtol=2e-3, atol=1e-12)
+    # Bell hazards: k0 exp(dx f) turns a relative force error e into a hazard
+    # error of about dx f e, so compare the log-hazard (the log-survival
+    # exponent) to 1e-4 of its size, plus an absolute floor.
+    pos = r["lam"] > 0
+    lg, lr = np.log(g["haz"][pos]), np.log(r["lam"][pos])
+    assert np.all(np.abs(lg - lr) <= 1e-4 * np.abs(lr) + 2e-3)
+    np.testing.assert_array_equal(g["haz"][~pos], r["lam"][~pos])
 
 
 def c1_like(rate_wi=2.0, n=20, R=16, b=50.0):
@@ -249,8 +255,16 @@ def test_results_do_not_depend_on_tile(prec):
     pos0 = I.initial_positions(I.custom(chains, dt, S, 60), seed=9)
     runs = [gpu_run(chains, dt, S, [60], 7, pos0, prec, lanes=L) for L in (2, 4, 7, 10, 13, 16)]
     for g in runs[1:]:
-        for key in ("allpos", "rsf", "tsf", "haz", "first_thr", "first_bell"):
+        # trajectories, parent samples and kinetics are bitwise the same
+        for key in ("allpos", "tsf", "first_thr", "first_bell"):
             np.testing.assert_array_equal(g[key], runs[0][key])
+        # the tile decides how replicas split into CTAs, hence the order of
+        # the float64 replica sum: equal up to its last bits (exactly equal
+        # in FP32 mode, where the float64 sums of float samples are exact)
+        np.testing.assert_allclose(g["rsf"], runs[0]["rsf"], rtol=4e-16, atol=0)
+        np.testing.assert_allclose(g["haz"], runs[0]["haz"], rtol=1e-14, atol=0)
+        if prec == bdra.BD_PREC_FP32:
+            np.testing.assert_array_equal(g["rsf"], runs[0]["rsf"])
 
 
 @pytest.mark.parametrize("prec", PRECS)
