@@ -198,6 +198,46 @@ bd_status bd_kernel_times(bd_ctx* ctx, double* ms, int64_t* launches);
 bd_status bd_philox_normals(uint64_t seed, int64_t n, const uint32_t* ctr, int32_t precision,
                             double* out, void* stream);
 
+/* Largest n_springs bd_compact_events_noalloc accepts (its fixed scratch
+ * holds one count per 256 springs: 32 KiB of device memory). */
+#define BD_NOALLOC_MAX_SPRINGS (1 << 20)
+
+/* Event compaction that allocates nothing. (The paper has no counterpart:
+ * this is a deployment variant of the event list of bd_detect_events.)
+ *
+ * Who needs it: callers that may not allocate device memory at the point
+ * of the call, such as code running while a CUDA stream is being captured
+ * into a graph (where cudaMalloc is not allowed), a host application or
+ * engine that owns a fixed device-memory arena and forbids allocation by its
+ * plug-ins, or a real-time loop that must not stall on the allocator. It
+ * calls no cudaMalloc / cudaFree and no allocating library routine.
+ *
+ * Input (all device memory of the current device, caller-owned):
+ * first_thr / first_bell int64 [3][n_springs] first event steps (-1 = none),
+ * as bd_get_kinetics returns them; spring_offsets int64 [n_chains + 1],
+ * chain c owning springs spring_offsets[c] .. spring_offsets[c+1]-1.
+ * Output (device): out[capacity] receives the events in the order of
+ * bd_detect_events (chain, spring, criterion, kind); *n_out (device int64)
+ * receives the total number, which may exceed capacity (then only the first
+ * capacity records are written). Asynchronous on `stream`.
+ *
+ * Scratch: a fixed file-scope device array (BD_NOALLOC_MAX_SPRINGS / 256 + 1
+ * int64, held by every device that loads the library until exit), shared by
+ * every call on a device and overwritten by each; no value from an earlier
+ * call is read. Calls that overlap on the GPU (different streams, or
+ * different host threads without ordering) race on it and must be
+ * serialised by the caller. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.
+ *
+ * Errors: BD_E_INVALID for NULL pointers or negative sizes, BD_E_CAPACITY if
+ * n_springs > BD_NOALLOC_MAX_SPRINGS, BD_E_CUDA if the look-up or a launch
+ * fails. */
+bd_status bd_compact_events_noalloc(const int64_t* first_thr, const int64_t* first_bell,
+                                    int64_t n_springs, const int64_t* spring_offsets,
+                                    int32_t n_chains, bd_event* out, int64_t capacity,
+                                    int64_t* n_out, void* stream);
+
 /* Message of the last failure on ctx (never NULL). */
 const char* bd_last_error(const bd_ctx* ctx);
 /* Name of a status code (never NULL). */

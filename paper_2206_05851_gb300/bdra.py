@@ -95,6 +95,8 @@ def load() -> ctypes.CDLL:
         "bd_enable_timing": ([vp, ctypes.c_int32], st),
         "bd_kernel_times": ([vp, P(ctypes.c_double), P(ctypes.c_int64)], st),
         "bd_philox_normals": ([ctypes.c_uint64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp], st),
+        "bd_compact_events_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.c_int32, vp,
+                                       ctypes.c_int64, vp, vp], st),
         "bd_last_error": ([vp], ctypes.c_char_p),
         "bd_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "bd_destroy": ([vp], None),
@@ -231,6 +233,19 @@ def bd_kernel_times(ctx: int):
     n = (ctypes.c_int64 * 2)()
     _check(load().bd_kernel_times(ctx, ms, n), ctx)
     return (ms[0], ms[1]), (n[0], n[1])
+
+
+NOALLOC_MAX_SPRINGS = 1 << 20
+
+
+def bd_compact_events_noalloc(first_thr, first_bell, n_springs: int, spring_offsets,
+                              n_chains: int, out, capacity: int, n_out,
+                              stream: Optional[int] = None) -> None:
+    """Allocation-free event compaction; every array is device memory."""
+    _check(load().bd_compact_events_noalloc(
+        _ptr(first_thr)[0], _ptr(first_bell)[0], int(n_springs), _ptr(spring_offsets)[0],
+        int(n_chains), _ptr(out)[0] if capacity > 0 else None, int(capacity), _ptr(n_out)[0],
+        stream))
 
 
 def bd_philox_normals(seed: int, ctr, precision: int, out, stream: Optional[int] = None) -> None:

@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "libbdra.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 UNITS = [("bd_window_f32.cu", ["-fmad=false"]), ("bd_window_f64.cu", ["-fmad=false"]),
-         ("bd_support.cu", []), ("bd_api.cu", [])]
+         ("bd_support.cu", []), ("bd_api.cu", []), ("bd_noalloc.cu", [])]
 
 
 def _nvcc() -> str:
