@@ -32,10 +32,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("bead-steps/s (chains×replicas×beads×steps) FP32 batched vs FP64 plain, "
           "1 GB300")
-# Minimal lane-instructions per slot-bead-step of the FP32 replica step
-# (Philox4x32-10 40, uniforms 8, Box-Muller 18, spring force 10,
-# Laplacian 6, update 13); see the design notes for the count.
-ALGO_OPS_PER_BEAD_STEP = 95
+# Minimal lane-instructions per slot-bead-step of the float32 replica step on
+# an SM with two-wide float32 instructions: Philox4x32-10 39 (20 wide
+# multiplies less the step word's shared one, 20 three-input XORs), two
+# integer-to-float conversions, 8 special-function ops (2 log2, 2 sqrt, sin,
+# 2 cos, 1 reciprocal), 19 packed float32 ops (38 float32 operations: uniform
+# scaling 4, Box-Muller products 7, spring law 8, Laplacian 6, update 13) and
+# 4 bit/compare ops (angle bits 2, floor clamp and count 2). See the design
+# notes.
+ALGO_OPS_PER_BEAD_STEP = 72
 SMS, LANES_PER_CLK_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -256,7 +261,7 @@ def main():
     peak = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": None,
-            "kernel": "replica_kernel<float,13>", "avg_launch_ms": rep_ms / max(rep_n, 1),
+            "kernel": "replica kernel (planner's float32 tile)", "avg_launch_ms": rep_ms / max(rep_n, 1),
             "launches": rep_n, "share_of_step": rep_ms / t_ms,
             "peak_basis": f"issue rate {SMS} SMs x {LANES_PER_CLK_PER_SM} lane-instr/clk x "
                           f"{SM_MAX_MHZ:.0f} MHz (derived, not measured)",

@@ -98,8 +98,9 @@ typedef struct {
     int64_t max_windows;          /* capacity of the per-window profile history */
     double s_min;                 /* FENE floor of 1 - H Q^2 / b (e.g. 1e-3) */
     void* stream;                 /* cudaStream_t for all work; NULL = default stream */
-    int32_t lanes_hint;           /* 0: autotuned launch shape; else springs per lane */
-    int32_t reserved;             /* must be 0 */
+    int32_t lanes_hint;           /* 0: planner's choice; else springs per lane (tile) */
+    int32_t layout_hint;          /* 0: planner's choice; 1: one replica per lane;
+                                     2: two replicas per lane (float32 only) */
 } bd_config;
 
 /* A first event of one spring under one criterion. */

@@ -47,7 +47,7 @@ class bd_config(ctypes.Structure):
                 ("flags", ctypes.c_int32), ("thr_mask", ctypes.c_int32),
                 ("bell_mask", ctypes.c_int32), ("max_windows", ctypes.c_int64),
                 ("s_min", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("lanes_hint", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lanes_hint", ctypes.c_int32), ("layout_hint", ctypes.c_int32)]
 
 
 class bd_event(ctypes.Structure):
@@ -145,7 +145,7 @@ def _need(a, nbytes: int, what: str) -> int:
 def make_config(chains: Sequence, dt: float, window_steps: int, seed: int, precision: int,
                 max_windows: int, thr_mask: int = 0, bell_mask: int = 0, flags: int = 0,
                 s_min: float = 1e-3, stream: Optional[int] = None,
-                lanes_hint: int = 0) -> Tuple[bd_config, ctypes.Array]:
+                lanes_hint: int = 0, layout_hint: int = 0) -> Tuple[bd_config, ctypes.Array]:
     """Build a bd_config (and the chain array it points to) from chain records
     with the fields of bd_chain_desc."""
     arr = (bd_chain_desc * len(chains))(*[
@@ -154,7 +154,7 @@ def make_config(chains: Sequence, dt: float, window_steps: int, seed: int, preci
                       float(c.dx)) for c in chains])
     cfg = bd_config(len(chains), int(window_steps), arr, float(dt), int(seed), int(precision),
                     int(flags), int(thr_mask), int(bell_mask), int(max_windows), float(s_min),
-                    stream, int(lanes_hint), 0)
+                    stream, int(lanes_hint), int(layout_hint))
     return cfg, arr
 
 
@@ -265,11 +265,12 @@ class Context:
     def __init__(self, chains: Sequence, dt: float, window_steps: int, seed: int,
                  init_pos, precision: int = BD_PREC_FP32, max_windows: int = 1024,
                  thr_mask: int = 0, bell_mask: int = 0, flags: int = 0,
-                 s_min: float = 1e-3, stream: Optional[int] = None, lanes_hint: int = 0):
+                 s_min: float = 1e-3, stream: Optional[int] = None, lanes_hint: int = 0,
+                 layout_hint: int = 0):
         self.chains = list(chains)
         self.cfg, self._arr = make_config(self.chains, dt, window_steps, seed, precision,
                                           max_windows, thr_mask, bell_mask, flags, s_min,
-                                          stream, lanes_hint)
+                                          stream, lanes_hint, layout_hint)
         self.ptr = bd_create(self.cfg, init_pos)
         self.M = sum(c.n_beads - 1 for c in self.chains)
         self.n_beads = sum(c.n_beads for c in self.chains)

@@ -45,10 +45,12 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, out: str = None,
-          defines=()) -> str:
-    """Compile csrc/ into libbdra.so (or `out`), with optional -D defines."""
+          defines=(), csrc: str = None) -> str:
+    """Compile csrc/ (or another source directory) into libbdra.so (or `out`),
+    with optional -D defines."""
     lib = out or LIB
-    if not force and out is None and not defines and up_to_date():
+    src_dir = csrc or CSRC
+    if not force and out is None and not defines and csrc is None and up_to_date():
         return LIB
     objdir = os.path.join(os.path.dirname(lib), "_build") if out else os.path.join(PKG, "_build")
     os.makedirs(objdir, exist_ok=True)
@@ -58,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, out: str = None,
         src, extra = unit
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
         cmd = [nvcc, *ARCH, *COMMON, *[f"-D{d}" for d in defines], *extra, "-c",
-               os.path.join(CSRC, src), "-o", obj]
+               os.path.join(src_dir, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -19,6 +19,7 @@ namespace {
 
 struct RepClass {      // one replica-kernel launch: items with the same tile and width
     int L, threads;
+    bool paired;       // two replicas per lane (replica2_kernel)
     size_t smem;
     int item_begin, item_count;
 };
@@ -156,24 +157,37 @@ void round_keys(uint64_t seed, uint32_t* rk0, uint32_t* rk1)
 // split into the fewest groups that fit, and the cost is the lane-steps issued
 // per useful bead-step, with a fixed per-lane overhead for the halo exchange.
 // ---------------------------------------------------------------------------
-struct TileChoice { int L, G, P, groups, warps; double cost; };
+struct TileChoice { int L, G, P, groups, warps; bool paired; double cost; };
 
-TileChoice choose_tile(int N, int R, int wmax, int hint)
+// Estimated issue slots per lane-step: one replica per lane ~100 per spring
+// plus the halo exchange; two replicas per lane ~140 per spring pair (packed
+// float32 arithmetic, per-replica Philox and special functions).
+constexpr double kLaneCostOne = 100.0, kLaneCostPair = 140.0, kLaneFixed = 40.0;
+
+TileChoice choose_tile(int N, int R, int wmax, int hint, int layout, bool f64)
 {
-    TileChoice best{0, 0, 0, 0, 0, 1e300};
-    for (int t = 0; t < kNumTiles; ++t) {
-        const int L = kTiles[t];
-        if (hint && L != hint) continue;
-        const int G = (N + L - 1) / L;
-        if (G > 32) continue;
-        const int P = 32 / G;
-        const int cap = P * wmax;
-        const int groups = (R + cap - 1) / cap;
-        const int per = (R + groups - 1) / groups;
-        const int warps = (per + P - 1) / P;
-        const double lane_cost = 100.0 * L + 40.0;   // ~instructions per lane-step
-        const double cost = (double)groups * warps * 32 * lane_cost / ((double)R * N);
-        if (cost < best.cost - 1e-9) best = {L, G, P, groups, warps, cost};
+    TileChoice best{0, 0, 0, 0, 0, false, 1e300};
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool paired = pass == 1;
+        if (paired && (f64 || layout == 1)) continue;
+        if (!paired && layout == 2) continue;
+        const int* tiles = paired ? kPairTiles : kTiles;
+        const int ntiles = paired ? kNumPairTiles : kNumTiles;
+        for (int t = 0; t < ntiles; ++t) {
+            const int L = tiles[t];
+            if (hint && L != hint) continue;
+            const int G = (N + L - 1) / L;
+            if (G > 32) continue;
+            const int P = 32 / G;                  // slots (or slot pairs) per warp
+            const int per_warp = paired ? 2 * P : P;
+            const int cap = per_warp * wmax;
+            const int groups = (R + cap - 1) / cap;
+            const int per = (R + groups - 1) / groups;
+            const int warps = (per + per_warp - 1) / per_warp;
+            const double lane_cost = (paired ? kLaneCostPair : kLaneCostOne) * L + kLaneFixed;
+            const double cost = (double)groups * warps * 32 * lane_cost / ((double)R * N);
+            if (cost < best.cost - 1e-9) best = {L, G, P, groups, warps, paired, cost};
+        }
     }
     return best;
 }
@@ -201,11 +215,17 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
     if ((cfg->thr_mask & ~7) || (cfg->bell_mask & ~7))
         return fail(ctx, BD_E_INVALID, "criterion masks use bits 0..2 only");
     if (cfg->flags & ~BD_FLAG_IDENTICAL_NOISE) return fail(ctx, BD_E_INVALID, "unknown flags");
-    if (cfg->reserved != 0) return fail(ctx, BD_E_INVALID, "reserved must be 0");
+    if (cfg->layout_hint < 0 || cfg->layout_hint > 2)
+        return fail(ctx, BD_E_INVALID, "layout_hint must be 0, 1 or 2");
+    if (cfg->layout_hint == 2 && cfg->precision != BD_PREC_FP32)
+        return fail(ctx, BD_E_INVALID, "two replicas per lane needs float32 integration");
     if (cfg->lanes_hint) {
-        bool ok = false;
-        for (int t = 0; t < kNumTiles; ++t) ok |= kTiles[t] == cfg->lanes_hint;
-        if (!ok) return fail(ctx, BD_E_INVALID, "lanes_hint %d is not a compiled tile", cfg->lanes_hint);
+        bool one = false, two = false;
+        for (int t = 0; t < kNumTiles; ++t) one |= kTiles[t] == cfg->lanes_hint;
+        for (int t = 0; t < kNumPairTiles; ++t) two |= kPairTiles[t] == cfg->lanes_hint;
+        if (cfg->layout_hint == 2 ? !two : (cfg->layout_hint == 1 || cfg->precision == BD_PREC_FP64) ? !one : !(one || two))
+            return fail(ctx, BD_E_INVALID, "lanes_hint %d is not a compiled tile for this layout",
+                        cfg->lanes_hint);
     }
     for (int c = 0; c < cfg->n_chains; ++c) {
         const bd_chain_desc& d = cfg->chains[c];
@@ -238,13 +258,14 @@ bd_status plan(bd_ctx* ctx)
     const int wmax = (ctx->f64 ? max_threads_f64() : max_threads_f32()) / 32;
     ctx->h_chains.resize(C);
     int64_t bead = 0, slot_bead = 0, bond = 0, spr = 0, part = 0;
-    struct Pending { int L, warps; ItemDev it; };
+    struct Pending { int L, warps; bool paired; ItemDev it; };
     std::vector<Pending> pend;
     std::vector<std::pair<std::pair<int, int>, int>> par;   // ((L, G), chain)
     for (int c = 0; c < C; ++c) {
         const bd_chain_desc& d = ctx->chains[c];
         ChainDev& h = ctx->h_chains[c];
-        const TileChoice tc = choose_tile(d.n_beads, d.n_replicas, wmax, cfg.lanes_hint);
+        const TileChoice tc = choose_tile(d.n_beads, d.n_replicas, wmax, cfg.lanes_hint,
+                                          cfg.layout_hint, ctx->f64);
         if (!tc.L) return fail(ctx, BD_E_INVALID, "chain %d: no tile fits N=%d", c, d.n_beads);
         h.N = d.n_beads; h.R = d.n_replicas; h.n_groups = tc.groups; h.pad = 0;
         h.bead_off = bead; h.slot_bead_off = slot_bead; h.state_off = bond;
@@ -259,15 +280,28 @@ bd_status plan(bd_ctx* ctx)
         default: break;
         }
         h.f_c = d.f_c; h.k0 = d.k0; h.dx = d.dx;
+        // float32 step constants, rounded as (float)(double expression);
+        // sqrt(2 D dt) carries the sign of the fast float normals (-1)
+        h.f32[0] = (float)h.H;
+        h.f32[1] = (float)h.Hinvb;
+        h.f32[2] = (float)(0.25 * cfg.dt);
+        h.f32[3] = (float)std::sqrt(0.5 * cfg.dt) * -1.0f;
+        h.f32[4] = (float)(h.kxx * cfg.dt);
+        h.f32[5] = (float)(h.kyy * cfg.dt);
+        h.f32[6] = (float)(h.kzz * cfg.dt);
+        h.f32[7] = (float)(h.kxz * cfg.dt);
+        h.f32[8] = (float)cfg.s_min;
+        h.f32_pad = 0.0f;
         const int nb = d.n_beads - 1;
         int begin = 0;
         for (int g = 0; g < tc.groups; ++g) {
             const int cnt = d.n_replicas / tc.groups + (g < d.n_replicas % tc.groups ? 1 : 0);
-            const int warps = (cnt + tc.P - 1) / tc.P;
-            pend.push_back({tc.L, warps, ItemDev{c, g, begin, cnt}});
+            const int per_warp = tc.paired ? 2 * tc.P : tc.P;
+            const int warps = (cnt + per_warp - 1) / per_warp;
+            pend.push_back({tc.L, warps, tc.paired, ItemDev{c, g, begin, cnt}});
             begin += cnt;
         }
-        const int Lp = cfg.lanes_hint ? cfg.lanes_hint : choose_parent_tile(d.n_beads);
+        const int Lp = choose_parent_tile(d.n_beads);
         par.push_back({{Lp, (d.n_beads + Lp - 1) / Lp}, c});
         bead += d.n_beads;
         slot_bead += (int64_t)(d.n_replicas + 1) * d.n_beads;
@@ -280,6 +314,7 @@ bd_status plan(bd_ctx* ctx)
 
     // replica launches: one per (L, warps) class
     std::stable_sort(pend.begin(), pend.end(), [](const Pending& a, const Pending& b) {
+        if (a.paired != b.paired) return a.paired < b.paired;
         return a.L != b.L ? a.L < b.L : a.warps < b.warps;
     });
     ctx->h_items.clear();
@@ -289,8 +324,9 @@ bd_status plan(bd_ctx* ctx)
         const ChainDev& h = ctx->h_chains[q.it.chain];
         const size_t smem = (size_t)q.it.rep_count * (h.N - 1) * ctx->tsize;
         if (ctx->rep_classes.empty() || ctx->rep_classes.back().L != q.L ||
-            ctx->rep_classes.back().threads != q.warps * 32) {
-            ctx->rep_classes.push_back(RepClass{q.L, q.warps * 32, smem, (int)k, 0});
+            ctx->rep_classes.back().threads != q.warps * 32 ||
+            ctx->rep_classes.back().paired != q.paired) {
+            ctx->rep_classes.push_back(RepClass{q.L, q.warps * 32, q.paired, smem, (int)k, 0});
         }
         RepClass& rc = ctx->rep_classes.back();
         rc.item_count++;
@@ -535,7 +571,8 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
         BD_TRY(dalloc(ctx, (void**)&ctx->d_evt_scratch, sizeof(int64_t) * (size_t)(event_blocks(M) + 1)));
         for (const RepClass& rc : ctx->rep_classes) {
             cudaError_t e = ctx->f64 ? prepare_replica_f64(rc.L, rc.smem, nullptr)
-                                     : prepare_replica_f32(rc.L, rc.smem, nullptr);
+                            : rc.paired ? prepare_replica2_f32(rc.L, rc.smem)
+                                        : prepare_replica_f32(rc.L, rc.smem, nullptr);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 s = fail(ctx, BD_E_CUDA, "kernel set-up for tile %d (%zu B shared): %s", rc.L,
@@ -613,7 +650,8 @@ bd_status bd_step(bd_ctx* ctx, int64_t n_steps)
             p.items = ctx->d_items + rc.item_begin;
             TimedLaunch tl(ctx, 1);
             BD_CUDA(ctx, ctx->f64 ? launch_replica_f64(rc.L, rc.item_count, rc.threads, rc.smem, ctx->stream, p)
-                                  : launch_replica_f32(rc.L, rc.item_count, rc.threads, rc.smem, ctx->stream, p));
+                         : rc.paired ? launch_replica2_f32(rc.L, rc.item_count, rc.threads, rc.smem, ctx->stream, p)
+                                     : launch_replica_f32(rc.L, rc.item_count, rc.threads, rc.smem, ctx->stream, p));
             ++ctx->launches;
         }
         t = chunk_end;

@@ -27,6 +27,12 @@ struct ChainDev {
     double H, Hinvb;     // spring constant; H/b for FENE, 0 for Hooke
     double kxx, kyy, kzz, kxz;   // velocity gradient, v = kappa . r
     double f_c, k0, dx;  // threshold force; Bell rate k0 exp(f dx)
+    // float32 step constants, rounded once on the host from the values
+    // above (so the kernels never rebuild them from doubles): H, H/b, D dt,
+    // sqrt(2 D dt) times the fast normals' sign, kappa_xx dt, kappa_yy dt,
+    // kappa_zz dt, kappa_xz dt, s_min
+    float f32[9];
+    float f32_pad;
 };
 
 // One CTA's work: the parent of `chain` plus replicas rep_begin+1 ..
@@ -106,10 +112,70 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk0)
 // Standard normals from one Philox output (Box-Muller): the pair
 // sqrt(-2 ln u0) (cos, sin)(2 pi u1) and the cosine branch of the pair from
 // (u2, u3), with u = (x + 1/2) 2^-32.
+//
+// Normals<T, FAST>::sign: the FAST float path returns the three normals with
+// their sign flipped (it evaluates cos and sin of 2 pi u - pi, the accurate
+// range of the hardware units, and cos(2 pi u - pi) = -cos(2 pi u)). The
+// step multiplies its noise coefficient by `sign`, which undoes the flip
+// exactly: (-a) - (-b) = -(a - b) and (-c)(-d) = c d in floating point.
 // ---------------------------------------------------------------------------
 template <typename T, bool FAST> struct Normals;
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Hardware log2 / sin / cos with denormals flushed: the Box-Muller
+// arguments are never denormal (u >= 2^-33, |angle| >= 2 pi 2^-24), so the
+// flush changes no result and spares the denormal handling.
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float sin_approx(float x)
+{
+    float r;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float cos_approx(float x)
+{
+    float r;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Building blocks of the fast float Box-Muller, shared by the one-slot and
+// two-slot (packed) paths so both round identically.
+struct FastBM {
+    static constexpr float s32 = 2.3283064365386963e-10f;      // 2^-32
+    static constexpr float h32 = 1.1641532182693481e-10f;      // 2^-33
+    static constexpr float m2ln2 = -2.0f * 0.69314718055994531f;
+    static constexpr float twopi = 6.2831853071795865f;
+    static constexpr float off = -6.2831853071795865f * (1.5f - 5.9604644775390625e-8f);
+    // angle uniform from the top 23 bits: float in [1, 2) (error <= 2^-24 in u)
+    static __device__ __forceinline__ float angle_bits(uint32_t w)
+    {
+        return __uint_as_float(0x3F800000u | (w >> 9));
+    }
+};
+
 template <bool FAST> struct Normals<float, FAST> {
+    static constexpr float sign = FAST ? -1.0f : 1.0f;
     static __device__ __forceinline__ void draw(uint4 x, float& z0, float& z1, float& z2)
     {
         const float s = 2.3283064365386963e-10f;       // 2^-32
@@ -117,28 +183,20 @@ template <bool FAST> struct Normals<float, FAST> {
         const float u0 = fmaf((float)x.x, s, h);
         const float u2 = fmaf((float)x.z, s, h);
         if (FAST) {
-            // Angles 2 pi u - pi in (-pi, pi), the accurate range of the
-            // hardware sin/cos: cos(2 pi u) = -cos(2 pi u - pi) and likewise
-            // for sin. The angle uniforms take the top 23 bits of their word
-            // (float in [1, 2) built from the bits; error <= 2^-24 in u); the
-            // radial uniforms, which enter a logarithm, are converted in full.
-            const float ln2 = 0.69314718055994531f;
-            const float twopi = 6.2831853071795865f;
-            const float off = -6.2831853071795865f * (1.5f - 5.9604644775390625e-8f);
-            const float f1 = __uint_as_float(0x3F800000u | (x.y >> 9));
-            const float f3 = __uint_as_float(0x3F800000u | (x.w >> 9));
-            const float a0 = -2.0f * ln2 * __log2f(u0);
-            const float a2 = -2.0f * ln2 * __log2f(u2);
-            float r0, r2;
+            // Angles 2 pi u - pi in (-pi, pi); the results are the normals
+            // with flipped sign (see `sign`). The radial uniforms, which
+            // enter a logarithm, are converted in full.
+            const float a0 = FastBM::m2ln2 * lg2_approx(u0);
+            const float a2 = FastBM::m2ln2 * lg2_approx(u2);
             // |a| guards the approximate log2 of values within an ulp of 1
-            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(fabsf(a0)));
-            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r2) : "f"(fabsf(a2)));
-            float sn, cs;
-            __sincosf(fmaf(f1, twopi, off), &sn, &cs);
-            const float c3 = __cosf(fmaf(f3, twopi, off));
-            z0 = -r0 * cs;
-            z1 = -r0 * sn;
-            z2 = -r2 * c3;
+            const float r0 = sqrt_approx(fabsf(a0));
+            const float r2 = sqrt_approx(fabsf(a2));
+            const float t1 = fmaf(FastBM::angle_bits(x.y), FastBM::twopi, FastBM::off);
+            const float sn = sin_approx(t1), cs = cos_approx(t1);
+            const float c3 = cos_approx(fmaf(FastBM::angle_bits(x.w), FastBM::twopi, FastBM::off));
+            z0 = r0 * cs;
+            z1 = r0 * sn;
+            z2 = r2 * c3;
         } else {
             const float u1 = fmaf((float)x.y, s, h);
             const float u3 = fmaf((float)x.w, s, h);
@@ -154,6 +212,7 @@ template <bool FAST> struct Normals<float, FAST> {
 };
 
 template <bool FAST> struct Normals<double, FAST> {
+    static constexpr double sign = 1.0;
     static __device__ __forceinline__ void draw(uint4 x, double& z0, double& z1, double& z2)
     {
         const double s = 2.3283064365386963e-10;       // 2^-32
@@ -189,7 +248,7 @@ template <typename T, bool FAST> struct Div {
     static __device__ __forceinline__ T div(T a, T b) { return a / b; }
 };
 template <> struct Div<float, true> {
-    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
 };
 
 template <typename T>
@@ -201,9 +260,9 @@ __device__ __forceinline__ T bond_q2(T qx, T qy, T qz)
 template <typename T, bool FAST>
 __device__ __forceinline__ T spring_coef(T qx, T qy, T qz, T H, T Hinvb, T smin, int& floored)
 {
-    T s = fma(-Hinvb, bond_q2(qx, qy, qz), T(1));
-    if (s < smin) { s = smin; ++floored; }
-    return Div<T, FAST>::div(H, s);
+    const T s = fma(-Hinvb, bond_q2(qx, qy, qz), T(1));
+    floored += s < smin;
+    return Div<T, FAST>::div(H, fmax(s, smin));
 }
 
 template <typename T, bool FAST>

@@ -263,7 +263,8 @@ __global__ void normals_kernel(int64_t n, const uint32_t* ctr, StepParams p, dou
     const uint4 x = philox4x32_10_rk(c, p.rk0, p.rk1);
     T z0, z1, z2;
     Normals<T, FAST>::draw(x, z0, z1, z2);
-    out[3 * j] = (double)z0; out[3 * j + 1] = (double)z1; out[3 * j + 2] = (double)z2;
+    const T sg = Normals<T, FAST>::sign;      // undo the fast path's sign flip
+    out[3 * j] = (double)(sg * z0); out[3 * j + 1] = (double)(sg * z1); out[3 * j + 2] = (double)(sg * z2);
 }
 
 }  // namespace

@@ -60,25 +60,34 @@ template <typename T> __device__ __forceinline__ T shfl(T v, int src)
     return __shfl_sync(0xffffffffu, v, src);
 }
 
-// Per-chain constants of the step, in the integration precision.
-template <typename T> struct StepConst {
+// Per-chain constants of the step, in the integration precision. The noise
+// coefficient carries the sign convention of the normals (Normals::sign).
+template <typename T, bool FAST> struct StepConst {
     T H, Hinvb, smin;
     T cd;                  // D dt
-    T cn;                  // sqrt(2 D dt)
+    T cn;                  // sqrt(2 D dt), times the sign convention of the normals
     T axx, ayy, azz, axz;  // kappa dt
     __device__ __forceinline__ void load(const ChainDev& ch, const StepParams& p)
     {
-        H = (T)ch.H; Hinvb = (T)ch.Hinvb; smin = (T)p.s_min;
-        cd = (T)(0.25 * p.dt);
-        cn = (T)sqrt(0.5 * p.dt);
-        axx = (T)(ch.kxx * p.dt); ayy = (T)(ch.kyy * p.dt);
-        azz = (T)(ch.kzz * p.dt); axz = (T)(ch.kxz * p.dt);
+        if (sizeof(T) == 4 && FAST) {
+            // host-rounded float constants (ChainDev::f32)
+            H = (T)ch.f32[0]; Hinvb = (T)ch.f32[1]; cd = (T)ch.f32[2]; cn = (T)ch.f32[3];
+            axx = (T)ch.f32[4]; ayy = (T)ch.f32[5]; azz = (T)ch.f32[6]; axz = (T)ch.f32[7];
+            smin = (T)ch.f32[8];
+        } else {
+            H = (T)ch.H; Hinvb = (T)ch.Hinvb; smin = (T)p.s_min;
+            cd = (T)(0.25 * p.dt);
+            cn = (T)sqrt(0.5 * p.dt) * (T)Normals<T, FAST>::sign;
+            axx = (T)(ch.kxx * p.dt); ayy = (T)(ch.kyy * p.dt);
+            azz = (T)(ch.kzz * p.dt); axz = (T)(ch.kxz * p.dt);
+        }
     }
 };
 
 // Per-lane position inside its slot.
 struct LaneCtx {
     int bead0, nb;
+    int nv;                // springs of this lane inside the chain (0 if inactive)
     int src_prev, src_next;
     bool has_prev, has_next, active;
     uint32_t slot_key, chain;
@@ -90,6 +99,7 @@ __device__ __forceinline__ LaneCtx make_lane(int seg, int G, int L, int lane, in
     LaneCtx c;
     c.bead0 = seg * L;
     c.nb = nb;
+    c.nv = active ? max(0, min(L, nb - seg * L)) : 0;
     c.has_prev = seg > 0;
     c.has_next = seg + 1 < G;
     c.src_prev = c.has_prev ? lane - 1 : lane;
@@ -104,7 +114,7 @@ __device__ __forceinline__ LaneCtx make_lane(int seg, int G, int L, int lane, in
 // Returns how many spring forces hit the FENE floor.
 template <typename T, int L, bool FAST>
 __device__ __forceinline__ int step_bonds(T (&qx)[L], T (&qy)[L], T (&qz)[L], const LaneCtx& lc,
-                                          const StepConst<T>& k, uint32_t step,
+                                          const StepConst<T, FAST>& k, uint32_t step,
                                           const StepParams& p)
 {
     int fl = 0;
@@ -143,7 +153,7 @@ __device__ __forceinline__ int step_bonds(T (&qx)[L], T (&qy)[L], T (&qz)[L], co
             fpx = fnx; fpy = fny; fpz = fnz;
             xnx = hx; xny = hy; xnz = hz;
         }
-        if (lc.active && lc.bead0 + j < lc.nb) {
+        if (j < lc.nv) {
             const T lx = fma(T(-2), fcx, fpx + fmx);
             const T ly = fma(T(-2), fcy, fpy + fmy);
             const T lz = fma(T(-2), fcz, fpz + fmz);
@@ -215,7 +225,7 @@ replica_kernel(const StepParams p)
     const uint32_t key = (p.flags & BD_FLAG_IDENTICAL_NOISE) ? 0u : (uint32_t)kglob;
     const LaneCtx lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, active, key,
                                  (uint32_t)it.chain);
-    StepConst<T> k;
+    StepConst<T, FAST> k;
     k.load(ch, p);
 
     T* state = reinterpret_cast<T*>(p.state) + (ch.state_off + (int64_t)kglob * nb) * 3;
@@ -285,7 +295,7 @@ parent_kernel(const StepParams p)
     const int nb = ch.N - 1;
     const LaneCtx lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, active, 0u,
                                  (uint32_t)c);
-    StepConst<T> k;
+    StepConst<T, FAST> k;
     k.load(ch, p);
     const int64_t M = p.M;
     const bool isf_thr = (p.thr_mask & BD_CRIT_ISF) != 0;

@@ -1,0 +1,244 @@
+// Replica kernel with two replicas per lane (float32 only).
+//
+// Same method and the same rounding sequence as replica_kernel<float, L,
+// true> (bd_window.cuh), but every lane carries replicas 2s+1 and 2s+2 of the
+// same L springs side by side in float2 registers, so the float32 arithmetic
+// of a step (spring law, Laplacian, update, Box-Muller products) issues as
+// packed two-wide instructions (FFMA2 / FADD2 / FMUL2 on sm_100-class SMs).
+// Philox and the special-function unit work stay per replica. A packed
+// operation rounds each half exactly like its scalar form, and a - b is
+// written fma(b, -1, a) (exact product, one rounding), so both layouts give
+// bitwise-equal results.
+#pragma once
+
+#include "bd_window.cuh"
+
+namespace bdra {
+
+struct F2 {
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b)
+    {
+        return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+    }
+    static __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+};
+
+// Spring coefficient H / s for both halves; floor counts per half.
+__device__ __forceinline__ float2 spring_coef2(float2 qx, float2 qy, float2 qz, float2 H2,
+                                               float2 nHinvb2, float smin, int& fla, int& flb)
+{
+    const float2 q2 = F2::fma(qx, qx, F2::fma(qy, qy, F2::mul(qz, qz)));
+    const float2 s = F2::fma(nHinvb2, q2, F2::splat(1.0f));
+    fla += s.x < smin;
+    flb += s.y < smin;
+    return F2::mul(H2, make_float2(rcp_approx(fmaxf(s.x, smin)), rcp_approx(fmaxf(s.y, smin))));
+}
+
+// The three normals of one bead for both replicas (sign-flipped, see
+// Normals<float, true>::sign).
+__device__ __forceinline__ void bead_noise2(uint32_t bead, uint32_t ka, uint32_t kb, uint32_t step,
+                                            uint32_t chain, const StepParams& p, float2& z0,
+                                            float2& z1, float2& z2)
+{
+    const uint32_t w1 = (uint32_t)STREAM_BD << 24;
+    const uint4 xa = philox4x32_10_rk(make_uint4(bead, ka | w1, step, chain), p.rk0, p.rk1);
+    const uint4 xb = philox4x32_10_rk(make_uint4(bead, kb | w1, step, chain), p.rk0, p.rk1);
+    const float2 S = F2::splat(FastBM::s32), Hh = F2::splat(FastBM::h32);
+    const float2 u0 = F2::fma(make_float2((float)xa.x, (float)xb.x), S, Hh);
+    const float2 u2 = F2::fma(make_float2((float)xa.z, (float)xb.z), S, Hh);
+    const float2 a0 = F2::mul(F2::splat(FastBM::m2ln2), make_float2(lg2_approx(u0.x), lg2_approx(u0.y)));
+    const float2 a2 = F2::mul(F2::splat(FastBM::m2ln2), make_float2(lg2_approx(u2.x), lg2_approx(u2.y)));
+    const float2 r0 = make_float2(sqrt_approx(fabsf(a0.x)), sqrt_approx(fabsf(a0.y)));
+    const float2 r2 = make_float2(sqrt_approx(fabsf(a2.x)), sqrt_approx(fabsf(a2.y)));
+    const float2 t1 = F2::fma(make_float2(FastBM::angle_bits(xa.y), FastBM::angle_bits(xb.y)),
+                              F2::splat(FastBM::twopi), F2::splat(FastBM::off));
+    const float2 t3 = F2::fma(make_float2(FastBM::angle_bits(xa.w), FastBM::angle_bits(xb.w)),
+                              F2::splat(FastBM::twopi), F2::splat(FastBM::off));
+    z0 = F2::mul(r0, make_float2(cos_approx(t1.x), cos_approx(t1.y)));
+    z1 = F2::mul(r0, make_float2(sin_approx(t1.x), sin_approx(t1.y)));
+    z2 = F2::mul(r2, make_float2(cos_approx(t3.x), cos_approx(t3.y)));
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src)
+{
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Packed per-chain constants.
+struct StepConst2 {
+    float2 H, nHinvb, cd, cn, axx, ayy, azz, axz;
+    float smin;
+    __device__ __forceinline__ void load(const ChainDev& ch, const StepParams& p)
+    {
+        StepConst<float, true> k;
+        k.load(ch, p);
+        H = F2::splat(k.H); nHinvb = F2::splat(-k.Hinvb); cd = F2::splat(k.cd); cn = F2::splat(k.cn);
+        axx = F2::splat(k.axx); ayy = F2::splat(k.ayy); azz = F2::splat(k.azz); axz = F2::splat(k.axz);
+        smin = k.smin;
+    }
+};
+
+// One Eq. 1 step (bond form) of both replicas' L bonds; all lanes call it.
+template <int L>
+__device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], float2 (&qz)[L],
+                                            const LaneCtx& lc, uint32_t kb, bool act_b,
+                                            const StepConst2& k, uint32_t step,
+                                            const StepParams& p, int& fl_out)
+{
+    int fla = 0, flb = 0;
+    const float2 c0 = spring_coef2(qx[0], qy[0], qz[0], k.H, k.nHinvb, k.smin, fla, flb);
+    const float2 f0x = F2::mul(c0, qx[0]), f0y = F2::mul(c0, qy[0]), f0z = F2::mul(c0, qz[0]);
+    float2 fLx = f0x, fLy = f0y, fLz = f0z;
+    if (L > 1) {
+        const float2 cL = spring_coef2(qx[L - 1], qy[L - 1], qz[L - 1], k.H, k.nHinvb, k.smin, fla, flb);
+        fLx = F2::mul(cL, qx[L - 1]); fLy = F2::mul(cL, qy[L - 1]); fLz = F2::mul(cL, qz[L - 1]);
+    }
+    float2 fmx = shfl2(fLx, lc.src_prev), fmy = shfl2(fLy, lc.src_prev), fmz = shfl2(fLz, lc.src_prev);
+    float2 fnx = shfl2(f0x, lc.src_next), fny = shfl2(f0y, lc.src_next), fnz = shfl2(f0z, lc.src_next);
+    const float2 zero = F2::splat(0.0f);
+    if (!lc.has_prev) { fmx = zero; fmy = zero; fmz = zero; }
+    if (!lc.has_next) { fnx = zero; fny = zero; fnz = zero; }
+    float2 xcx, xcy, xcz;
+    bead_noise2((uint32_t)lc.bead0, lc.slot_key, kb, step, lc.chain, p, xcx, xcy, xcz);
+    const float2 hx = shfl2(xcx, lc.src_next), hy = shfl2(xcy, lc.src_next), hz = shfl2(xcz, lc.src_next);
+    const float2 m2 = F2::splat(-2.0f);
+
+    float2 fcx = f0x, fcy = f0y, fcz = f0z;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        float2 fpx, fpy, fpz, xnx, xny, xnz;
+        if (j + 1 < L) {
+            if (j + 1 == L - 1) {
+                fpx = fLx; fpy = fLy; fpz = fLz;
+            } else {
+                const float2 c = spring_coef2(qx[j + 1], qy[j + 1], qz[j + 1], k.H, k.nHinvb, k.smin, fla, flb);
+                fpx = F2::mul(c, qx[j + 1]); fpy = F2::mul(c, qy[j + 1]); fpz = F2::mul(c, qz[j + 1]);
+            }
+            uint32_t bj = (uint32_t)(lc.bead0 + j + 1);
+            asm volatile("" : "+r"(bj));     // keep per-bead Philox work inside the step loop
+            bead_noise2(bj, lc.slot_key, kb, step, lc.chain, p, xnx, xny, xnz);
+        } else {
+            fpx = fnx; fpy = fny; fpz = fnz;
+            xnx = hx; xny = hy; xnz = hz;
+        }
+        if (j < lc.nv) {
+            const float2 lx = F2::fma(m2, fcx, F2::add(fpx, fmx));
+            const float2 ly = F2::fma(m2, fcy, F2::add(fpy, fmy));
+            const float2 lz = F2::fma(m2, fcz, F2::add(fpz, fmz));
+            const float2 ox = qx[j], oy = qy[j], oz = qz[j];
+            qx[j] = F2::fma(k.cn, F2::sub(xnx, xcx), F2::fma(k.cd, lx, F2::fma(k.axz, oz, F2::fma(k.axx, ox, ox))));
+            qy[j] = F2::fma(k.cn, F2::sub(xny, xcy), F2::fma(k.cd, ly, F2::fma(k.ayy, oy, oy)));
+            qz[j] = F2::fma(k.cn, F2::sub(xnz, xcz), F2::fma(k.cd, lz, F2::fma(k.azz, oz, oz)));
+        }
+        fmx = fcx; fmy = fcy; fmz = fcz;
+        fcx = fpx; fcy = fpy; fcz = fpz;
+        xcx = xnx; xcy = xny; xcz = xnz;
+    }
+    fl_out += lc.active ? fla + (act_b ? flb : 0) : 0;
+}
+
+// CTA = one (chain, group); lane pair-slot s holds replicas
+// rep_begin + 2s + 1 (.x) and rep_begin + 2s + 2 (.y).
+template <int L>
+__global__ void __launch_bounds__(Tile<float, L>::max_threads, Tile<float, L>::min_blocks)
+replica2_kernel(const StepParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* sm_f = reinterpret_cast<float*>(smem_raw);      // [rep_count][N-1]
+
+    const ItemDev it = p.items[blockIdx.x];
+    const ChainDev ch = p.chains[it.chain];
+    const int nb = ch.N - 1;
+    const int G = (ch.N + L - 1) / L;
+    const int P = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int sw = lane / G;
+    const int pair = warp * P + sw;
+    const int ra = 2 * pair, rb = 2 * pair + 1;             // replica slots of this group
+    const bool act_a = (sw < P) && (ra < it.rep_count);
+    const bool act_b = (sw < P) && (rb < it.rep_count);
+    const int ka = it.rep_begin + ra + 1, kb = it.rep_begin + rb + 1;
+    const bool same = (p.flags & BD_FLAG_IDENTICAL_NOISE) != 0;
+    const LaneCtx lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, act_a,
+                                 same ? 0u : (uint32_t)ka, (uint32_t)it.chain);
+    const uint32_t keyb = same ? 0u : (uint32_t)kb;
+    StepConst2 k;
+    k.load(ch, p);
+
+    float* state = reinterpret_cast<float*>(p.state) + ch.state_off * 3;
+    const float* sa = state + (int64_t)ka * nb * 3;
+    const float* sb = state + (int64_t)kb * nb * 3;
+    const float* snap = reinterpret_cast<const float*>(p.snap);
+    float2 qx[L], qy[L], qz[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        const int i = lc.bead0 + j;
+        const bool v = i < nb;
+        qx[j] = make_float2(v && act_a ? sa[3 * i] : 0.0f, v && act_b ? sb[3 * i] : 0.0f);
+        qy[j] = make_float2(v && act_a ? sa[3 * i + 1] : 0.0f, v && act_b ? sb[3 * i + 1] : 0.0f);
+        qz[j] = make_float2(v && act_a ? sa[3 * i + 2] : 0.0f, v && act_b ? sb[3 * i + 2] : 0.0f);
+    }
+
+    int floored = 0;
+    int s_in = (int)(p.t0 % p.S);
+    int64_t w = p.t0 / p.S;
+    const int64_t t_end = p.t0 + p.n_steps;
+#pragma unroll 1
+    for (int64_t t = p.t0; t < t_end; ++t) {
+        if (s_in == 0) {  // spawn both replicas from the halted parent (Sec. II)
+            const float* src = snap + ((w - p.w_snap0) * p.M + ch.spr_off) * 3;
+#pragma unroll
+            for (int j = 0; j < L; ++j) {
+                const int i = lc.bead0 + j;
+                if (act_a && i < nb) {
+                    const float x = src[3 * i], y = src[3 * i + 1], z = src[3 * i + 2];
+                    qx[j] = make_float2(x, x); qy[j] = make_float2(y, y); qz[j] = make_float2(z, z);
+                }
+            }
+        }
+        step_bonds2<L>(qx, qy, qz, lc, keyb, act_b, k, (uint32_t)t, p, floored);
+        if (++s_in == p.S) {
+            s_in = 0;
+            if (act_a) {
+#pragma unroll
+                for (int j = 0; j < L; ++j) {
+                    const int i = lc.bead0 + j;
+                    if (i < nb) {
+                        sm_f[ra * nb + i] = spring_tension<float, true>(qx[j].x, qy[j].x, qz[j].x, k.H.x, -k.nHinvb.x, k.smin);
+                        if (act_b)
+                            sm_f[rb * nb + i] = spring_tension<float, true>(qx[j].y, qy[j].y, qz[j].y, k.H.y, -k.nHinvb.y, k.smin);
+                    }
+                }
+            }
+            __syncthreads();
+            double* prow = p.part_hist + w * p.part_stride + ch.part_off + (int64_t)it.group * nb;
+            for (int i = warp; i < nb; i += nwarps) {
+                double acc = 0.0;
+                for (int r = lane; r < it.rep_count; r += 32) acc += (double)sm_f[r * nb + i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) prow[i] = acc;
+            }
+            ++w;
+            __syncthreads();
+        }
+    }
+    float* da = state + (int64_t)ka * nb * 3;
+    float* db = state + (int64_t)kb * nb * 3;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        const int i = lc.bead0 + j;
+        if (i < nb) {
+            if (act_a) { da[3 * i] = qx[j].x; da[3 * i + 1] = qy[j].x; da[3 * i + 2] = qz[j].x; }
+            if (act_b) { db[3 * i] = qx[j].y; db[3 * i + 1] = qy[j].y; db[3 * i + 2] = qz[j].y; }
+        }
+    }
+    if (floored) atomicAdd(p.overext + it.chain, (unsigned long long)floored);
+}
+
+}  // namespace bdra

@@ -34,11 +34,11 @@ def _stream():
 
 
 def gpu_run(chains, dt, S, steps, seed, pos0, prec, thr=7, bell=7, flags=0, lanes=0,
-            want_all=True):
+            want_all=True, layout=0):
     total = sum(steps)
     ctx = bdra.Context(chains, dt, S, seed, pos0, precision=prec, max_windows=total // S + 1,
                        thr_mask=thr, bell_mask=bell, flags=flags, stream=_stream(),
-                       lanes_hint=lanes)
+                       lanes_hint=lanes, layout_hint=layout)
     for n in steps:
         ctx.step(n)
     nw = total // S
@@ -240,12 +240,16 @@ def test_events_and_kinetics(prec):
                                    rtol=1e-12)
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_identical_noise_replicas_reproduce_parent(prec):
+@pytest.mark.parametrize("prec,layout", [(bdra.BD_PREC_FP64, 0), (bdra.BD_PREC_FP32, 1),
+                                         (bdra.BD_PREC_FP32, 2)])
+def test_identical_noise_replicas_reproduce_parent(prec, layout):
+    # the parent kernel (one slot per lane) and the replica kernels (one or
+    # two replicas per lane) round every step identically
     chains = _ragged_chains()[:6]
     S, dt = 13, 1e-3
     pos0 = I.initial_positions(I.custom(chains, dt, S, 91), seed=2)
-    g = gpu_run(chains, dt, S, [91], 4, pos0, prec, flags=bdra.BD_FLAG_IDENTICAL_NOISE)
+    g = gpu_run(chains, dt, S, [91], 4, pos0, prec, flags=bdra.BD_FLAG_IDENTICAL_NOISE,
+                layout=layout)
     par, rep = _split_replicas(g["allpos"], chains)
     o = 0
     for c, ch in enumerate(chains):
@@ -263,7 +267,10 @@ def test_results_do_not_depend_on_tile(prec):
                       b=40.0, rate=0.2, f_c=3.0, k0=1e-3, dx=0.3)]
     S, dt = 10, 1e-3
     pos0 = I.initial_positions(I.custom(chains, dt, S, 60), seed=9)
-    runs = [gpu_run(chains, dt, S, [60], 7, pos0, prec, lanes=L) for L in (2, 4, 7, 10, 13, 16)]
+    shapes = [(1, L) for L in (2, 4, 7, 10, 13, 16)]
+    if prec == bdra.BD_PREC_FP32:      # two replicas per lane, packed float32 arithmetic
+        shapes += [(2, L) for L in (4, 7)]
+    runs = [gpu_run(chains, dt, S, [60], 7, pos0, prec, lanes=L, layout=lay) for lay, L in shapes]
     for g in runs[1:]:
         # trajectories, parent samples and kinetics are bitwise the same
         for key in ("allpos", "tsf", "first_thr", "first_bell"):
