@@ -137,7 +137,9 @@ bd_status bd_spawn_replicas(bd_ctx* ctx);
 /* Advances every parent and replica by n_steps Eq. 1 updates (Sec. II),
  * spawning replicas at each window start, sampling RSF (replicas, once at the
  * window end) and TSF/ISF (parent, every step), and updating the ISF
- * criteria. Asynchronous on the context's stream. BD_E_CAPACITY if the run
+ * criteria. The work runs in chunks of up to 64 windows, each one launch of
+ * a CUDA graph (parent kernels, then one persistent replica kernel per step
+ * variant), asynchronous on the context's stream. BD_E_CAPACITY if the run
  * would pass max_windows windows. n_steps = 0 is a no-op. */
 bd_status bd_step(bd_ctx* ctx, int64_t n_steps);
 
@@ -182,9 +184,11 @@ bd_status bd_set_positions(bd_ctx* ctx, const double* pos, int64_t step);
 /* Counters and sizes (host struct). */
 bd_status bd_get_info(bd_ctx* ctx, bd_info* out);
 
-/* Kernel timing for measurement tools. enable != 0: from now on every
- * parent-kernel and replica-kernel launch of bd_step is bracketed by CUDA
- * events on the context's stream (enable = 0 stops). bd_kernel_times
+/* Kernel timing for measurement tools. Each chunk graph that bd_step launches
+ * records CUDA events before its parent kernels, between the parent and
+ * replica kernels, and after the replica kernels. enable != 0: after every
+ * chunk bd_step waits for those events and accumulates the two intervals
+ * (enable = 0 stops; bd_step then never waits). bd_kernel_times
  * synchronises the stream, returns the accumulated device time in
  * milliseconds and the launch counts since the last call (index 0: parent
  * kernels, 1: replica kernels) and resets them. ms and launches are host

@@ -17,11 +17,10 @@ using namespace bdra;
 
 namespace {
 
-struct RepClass {      // one replica-kernel launch: items with the same tile and width
-    int L, threads;
-    bool paired;       // two replicas per lane (replica2_kernel)
-    size_t smem;
+struct VarClass {      // one persistent replica launch: the work items of one step variant
+    int variant;
     int item_begin, item_count;
+    int grid, threads;
 };
 struct ParClass {      // one parent-kernel launch
     int L, G, threads, grid;
@@ -42,8 +41,9 @@ struct bd_ctx {
     std::vector<ChainDev> h_chains;
     std::vector<ItemDev> h_items;
     std::vector<int32_t> h_parent_items;
-    std::vector<RepClass> rep_classes;
+    std::vector<VarClass> var_classes;
     std::vector<ParClass> par_classes;
+    double var_cost[2 * kPairBase];     // issue cost per warp-step of each variant
     uint32_t rk0[10], rk1[10];
 
     ChainDev* d_chains = nullptr;
@@ -63,6 +63,16 @@ struct bd_ctx {
     double* d_exp1 = nullptr;
     unsigned long long* d_overext = nullptr;
     int64_t* d_evt_scratch = nullptr;
+    int32_t* d_queue = nullptr;         // one work-item counter per variant launch
+    // the step chunk as a CUDA graph: queue reset, parent kernels, one
+    // persistent replica kernel per variant (parallel branches), and three
+    // event records (start, after the parents, after the replicas)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<cudaGraphNode_t> par_nodes, rep_nodes;
+    cudaGraphNode_t ev_nodes[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t idle_ev[3] = {nullptr, nullptr, nullptr};
+    int n_sm = 0;
     void* d_io = nullptr;
     size_t io_bytes = 0;
     size_t bytes = 0;
@@ -70,8 +80,8 @@ struct bd_ctx {
     std::string err;
     int64_t launches = 0;
     bool timing = false;
-    struct Timed { int kind; cudaEvent_t a, b; };
-    std::vector<Timed> timed;
+    double timed_ms[2] = {0.0, 0.0};   // accumulated parent / replica time
+    int64_t timed_n[2] = {0, 0};
 };
 
 namespace {
@@ -157,37 +167,40 @@ void round_keys(uint64_t seed, uint32_t* rk0, uint32_t* rk1)
 // split into the fewest groups that fit, and the cost is the lane-steps issued
 // per useful bead-step, with a fixed per-lane overhead for the halo exchange.
 // ---------------------------------------------------------------------------
-struct TileChoice { int L, G, P, groups, warps; bool paired; double cost; };
+struct VariantChoice { int variant, per_warp, groups; double cost; };
 
-// Estimated issue slots per lane-step: one replica per lane ~100 per spring
-// plus the halo exchange; two replicas per lane ~140 per spring pair (packed
-// float32 arithmetic, per-replica Philox and special functions).
-constexpr double kLaneCostOne = 100.0, kLaneCostPair = 140.0, kLaneFixed = 40.0;
-
-TileChoice choose_tile(int N, int R, int wmax, int hint, int layout, bool f64)
+// Default issue cost per warp-step (lane-instructions): one replica per lane
+// ~100 per spring plus the halo exchange; two replicas per lane ~140 per
+// spring pair (packed float32 arithmetic, per-replica Philox and special
+// functions). bd_autotune replaces these with measured times.
+double default_variant_cost(int v)
 {
-    TileChoice best{0, 0, 0, 0, 0, false, 1e300};
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool paired = pass == 1;
-        if (paired && (f64 || layout == 1)) continue;
-        if (!paired && layout == 2) continue;
-        const int* tiles = paired ? kPairTiles : kTiles;
-        const int ntiles = paired ? kNumPairTiles : kNumTiles;
-        for (int t = 0; t < ntiles; ++t) {
-            const int L = tiles[t];
-            if (hint && L != hint) continue;
-            const int G = (N + L - 1) / L;
-            if (G > 32) continue;
-            const int P = 32 / G;                  // slots (or slot pairs) per warp
-            const int per_warp = paired ? 2 * P : P;
-            const int cap = per_warp * wmax;
-            const int groups = (R + cap - 1) / cap;
-            const int per = (R + groups - 1) / groups;
-            const int warps = (per + per_warp - 1) / per_warp;
-            const double lane_cost = (paired ? kLaneCostPair : kLaneCostOne) * L + kLaneFixed;
-            const double cost = (double)groups * warps * 32 * lane_cost / ((double)R * N);
-            if (cost < best.cost - 1e-9) best = {L, G, P, groups, warps, paired, cost};
-        }
+    const int L = variant_tile(v);
+    return variant_paired(v) ? 140.0 * L + 60.0 : 100.0 * L + 40.0;
+}
+
+// The step variant for a chain: a warp holds P = 32 / ceil(N / L) replicas
+// (2P with two replicas per lane); the chain needs ceil(R / per_warp) warp
+// items, and the cost is their issue work per useful bead-step.
+VariantChoice choose_variant(const bd_ctx* ctx, int N, int R)
+{
+    const bd_config& cfg = ctx->cfg;
+    const int* vars = ctx->f64 ? kVariantsF64 : kVariantsF32;
+    const int nv = ctx->f64 ? kNumVariantsF64 : kNumVariantsF32;
+    VariantChoice best{0, 0, 0, 1e300};
+    for (int t = 0; t < nv; ++t) {
+        const int v = vars[t];
+        const bool paired = variant_paired(v);
+        const int L = variant_tile(v);
+        if (cfg.lanes_hint && L != cfg.lanes_hint) continue;
+        if (cfg.layout_hint == 1 && paired) continue;
+        if (cfg.layout_hint == 2 && !paired) continue;
+        const int G = (N + L - 1) / L;
+        if (G > 32) continue;
+        const int per_warp = (paired ? 2 : 1) * (32 / G);
+        const int groups = (R + per_warp - 1) / per_warp;
+        const double cost = groups * ctx->var_cost[v] / ((double)R * N);
+        if (cost < best.cost - 1e-12) best = {v, per_warp, groups, cost};
     }
     return best;
 }
@@ -220,11 +233,18 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
     if (cfg->layout_hint == 2 && cfg->precision != BD_PREC_FP32)
         return fail(ctx, BD_E_INVALID, "two replicas per lane needs float32 integration");
     if (cfg->lanes_hint) {
-        bool one = false, two = false;
-        for (int t = 0; t < kNumTiles; ++t) one |= kTiles[t] == cfg->lanes_hint;
-        for (int t = 0; t < kNumPairTiles; ++t) two |= kPairTiles[t] == cfg->lanes_hint;
-        if (cfg->layout_hint == 2 ? !two : (cfg->layout_hint == 1 || cfg->precision == BD_PREC_FP64) ? !one : !(one || two))
-            return fail(ctx, BD_E_INVALID, "lanes_hint %d is not a compiled tile for this layout",
+        const bool f64 = cfg->precision == BD_PREC_FP64;
+        const int* vars = f64 ? kVariantsF64 : kVariantsF32;
+        const int nv = f64 ? kNumVariantsF64 : kNumVariantsF32;
+        bool ok = false;
+        for (int t = 0; t < nv; ++t) {
+            const bool paired = variant_paired(vars[t]);
+            if (variant_tile(vars[t]) != cfg->lanes_hint) continue;
+            if ((cfg->layout_hint == 1 && paired) || (cfg->layout_hint == 2 && !paired)) continue;
+            ok = true;
+        }
+        if (!ok)
+            return fail(ctx, BD_E_INVALID, "lanes_hint %d is not a compiled step variant for this layout",
                         cfg->lanes_hint);
     }
     for (int c = 0; c < cfg->n_chains; ++c) {
@@ -255,19 +275,17 @@ bd_status plan(bd_ctx* ctx)
 {
     const bd_config& cfg = ctx->cfg;
     const int C = cfg.n_chains;
-    const int wmax = (ctx->f64 ? max_threads_f64() : max_threads_f32()) / 32;
     ctx->h_chains.resize(C);
     int64_t bead = 0, slot_bead = 0, bond = 0, spr = 0, part = 0;
-    struct Pending { int L, warps; bool paired; ItemDev it; };
-    std::vector<Pending> pend;
+    std::vector<ItemDev> items;
     std::vector<std::pair<std::pair<int, int>, int>> par;   // ((L, G), chain)
     for (int c = 0; c < C; ++c) {
         const bd_chain_desc& d = ctx->chains[c];
         ChainDev& h = ctx->h_chains[c];
-        const TileChoice tc = choose_tile(d.n_beads, d.n_replicas, wmax, cfg.lanes_hint,
-                                          cfg.layout_hint, ctx->f64);
-        if (!tc.L) return fail(ctx, BD_E_INVALID, "chain %d: no tile fits N=%d", c, d.n_beads);
-        h.N = d.n_beads; h.R = d.n_replicas; h.n_groups = tc.groups; h.pad = 0;
+        const VariantChoice vc = choose_variant(ctx, d.n_beads, d.n_replicas);
+        if (!vc.variant)
+            return fail(ctx, BD_E_INVALID, "chain %d: no step variant fits N=%d", c, d.n_beads);
+        h.N = d.n_beads; h.R = d.n_replicas; h.n_groups = vc.groups; h.pad = 0;
         h.bead_off = bead; h.slot_bead_off = slot_bead; h.state_off = bond;
         h.spr_off = spr; h.part_off = part;
         h.H = d.H;
@@ -293,12 +311,11 @@ bd_status plan(bd_ctx* ctx)
         h.f32[8] = (float)cfg.s_min;
         h.f32_pad = 0.0f;
         const int nb = d.n_beads - 1;
+        // warp items: replicas split as evenly as the warp capacity allows
         int begin = 0;
-        for (int g = 0; g < tc.groups; ++g) {
-            const int cnt = d.n_replicas / tc.groups + (g < d.n_replicas % tc.groups ? 1 : 0);
-            const int per_warp = tc.paired ? 2 * tc.P : tc.P;
-            const int warps = (cnt + per_warp - 1) / per_warp;
-            pend.push_back({tc.L, warps, tc.paired, ItemDev{c, g, begin, cnt}});
+        for (int g = 0; g < vc.groups; ++g) {
+            const int cnt = d.n_replicas / vc.groups + (g < d.n_replicas % vc.groups ? 1 : 0);
+            items.push_back(ItemDev{c, g, begin, cnt, vc.variant, 0});
             begin += cnt;
         }
         const int Lp = choose_parent_tile(d.n_beads);
@@ -307,31 +324,33 @@ bd_status plan(bd_ctx* ctx)
         slot_bead += (int64_t)(d.n_replicas + 1) * d.n_beads;
         bond += (int64_t)(d.n_replicas + 1) * nb;
         spr += nb;
-        part += (int64_t)tc.groups * nb;
+        part += (int64_t)vc.groups * nb;
     }
     ctx->n_beads = bead; ctx->n_slot_beads = slot_bead; ctx->state_bonds = bond;
     ctx->M = spr; ctx->part_stride = part;
 
-    // replica launches: one per (L, warps) class
-    std::stable_sort(pend.begin(), pend.end(), [](const Pending& a, const Pending& b) {
-        if (a.paired != b.paired) return a.paired < b.paired;
-        return a.L != b.L ? a.L < b.L : a.warps < b.warps;
-    });
-    ctx->h_items.clear();
-    ctx->rep_classes.clear();
-    for (size_t k = 0; k < pend.size(); ++k) {
-        const Pending& q = pend[k];
-        const ChainDev& h = ctx->h_chains[q.it.chain];
-        const size_t smem = (size_t)q.it.rep_count * (h.N - 1) * ctx->tsize;
-        if (ctx->rep_classes.empty() || ctx->rep_classes.back().L != q.L ||
-            ctx->rep_classes.back().threads != q.warps * 32 ||
-            ctx->rep_classes.back().paired != q.paired) {
-            ctx->rep_classes.push_back(RepClass{q.L, q.warps * 32, q.paired, smem, (int)k, 0});
+    // persistent replica launches: one per variant, items in chain order
+    std::stable_sort(items.begin(), items.end(),
+                     [](const ItemDev& x, const ItemDev& y) { return x.variant < y.variant; });
+    ctx->h_items = items;
+    ctx->var_classes.clear();
+    const int threads = ctx->f64 ? persist_threads_f64() : persist_threads_f32();
+    for (size_t k = 0; k < items.size(); ++k) {
+        if (ctx->var_classes.empty() || ctx->var_classes.back().variant != items[k].variant)
+            ctx->var_classes.push_back(VarClass{items[k].variant, (int)k, 0, 0, threads});
+        ctx->var_classes.back().item_count++;
+    }
+    for (VarClass& vc : ctx->var_classes) {
+        int per_sm = 1;
+        cudaError_t e = ctx->f64 ? persist_blocks_per_sm_f64(vc.variant, &per_sm)
+                                 : persist_blocks_per_sm_f32(vc.variant, &per_sm);
+        if (e != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            return fail(ctx, BD_E_CUDA, "occupancy of variant %d: %s", vc.variant, cudaGetErrorString(e));
         }
-        RepClass& rc = ctx->rep_classes.back();
-        rc.item_count++;
-        rc.smem = std::max(rc.smem, smem);
-        ctx->h_items.push_back(q.it);
+        const int warps = threads / 32;
+        const int need = (vc.item_count + warps - 1) / warps;
+        vc.grid = std::max(1, std::min(need, per_sm * ctx->n_sm));
     }
     // parent launches: one per (L, G) class, two warps per CTA
     std::stable_sort(par.begin(), par.end());
@@ -385,6 +404,110 @@ StepParams base_params(const bd_ctx* ctx)
     std::memcpy(p.rk0, ctx->rk0, sizeof(p.rk0));
     std::memcpy(p.rk1, ctx->rk1, sizeof(p.rk1));
     return p;
+}
+
+// Kernel-node parameters of the chunk graph for one chunk [t0, t0 + n).
+// `pp` / `rp` hold one StepParams per node (kernelParams point into them).
+void chunk_params(const bd_ctx* ctx, int64_t t0, int64_t n, int64_t w0,
+                  std::vector<StepParams>& pp, std::vector<StepParams>& rp)
+{
+    StepParams p = base_params(ctx);
+    p.t0 = t0; p.n_steps = n; p.w_snap0 = w0;
+    pp.assign(ctx->par_classes.size(), p);
+    for (size_t k = 0; k < ctx->par_classes.size(); ++k) {
+        const ParClass& pc = ctx->par_classes[k];
+        pp[k].parent_items = ctx->d_parent_items + pc.item_begin;
+        pp[k].n_parent_items = pc.item_count;
+        pp[k].parent_G = pc.G;
+    }
+    rp.assign(ctx->var_classes.size(), p);
+    for (size_t k = 0; k < ctx->var_classes.size(); ++k) {
+        const VarClass& vc = ctx->var_classes[k];
+        rp[k].items = ctx->d_items + vc.item_begin;
+        rp[k].n_items = vc.item_count;
+        rp[k].queue = ctx->d_queue + k;
+    }
+}
+
+cudaKernelNodeParams parent_node(const bd_ctx* ctx, size_t k, StepParams* pk, void** args)
+{
+    const ParClass& pc = ctx->par_classes[k];
+    args[0] = pk;
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void*>(ctx->f64 ? parent_func_f64(pc.L) : parent_func_f32(pc.L));
+    kp.gridDim = dim3(pc.grid);
+    kp.blockDim = dim3(pc.threads);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    return kp;
+}
+
+cudaKernelNodeParams replica_node(const bd_ctx* ctx, size_t k, StepParams* rk, void** args)
+{
+    const VarClass& vc = ctx->var_classes[k];
+    args[0] = rk;
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void*>(ctx->f64 ? persist_func_f64(vc.variant) : persist_func_f32(vc.variant));
+    kp.gridDim = dim3(vc.grid);
+    kp.blockDim = dim3(vc.threads);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    return kp;
+}
+
+void drop_graph(bd_ctx* ctx)
+{
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+    ctx->par_nodes.clear();
+    ctx->rep_nodes.clear();
+    cudaGetLastError();
+}
+
+// Builds the chunk graph: start event -> queue reset -> parent kernels (in
+// sequence) -> mid event -> replica kernels (parallel) -> end event.
+bd_status build_graph(bd_ctx* ctx)
+{
+    drop_graph(ctx);
+    for (int i = 0; i < 3; ++i)
+        if (!ctx->idle_ev[i]) BD_CUDA(ctx, cudaEventCreate(&ctx->idle_ev[i]));
+    BD_CUDA(ctx, cudaGraphCreate(&ctx->graph, 0));
+    std::vector<StepParams> pp, rp;
+    chunk_params(ctx, 0, 0, 0, pp, rp);
+    cudaGraphNode_t prev;
+    BD_CUDA(ctx, cudaGraphAddEventRecordNode(&ctx->ev_nodes[0], ctx->graph, nullptr, 0, ctx->idle_ev[0]));
+    cudaMemsetParams ms = {};
+    ms.dst = ctx->d_queue;
+    ms.value = 0;
+    ms.elementSize = sizeof(int32_t);
+    ms.width = ctx->var_classes.size();
+    ms.height = 1;
+    ms.pitch = 0;
+    cudaGraphNode_t mnode;
+    BD_CUDA(ctx, cudaGraphAddMemsetNode(&mnode, ctx->graph, &ctx->ev_nodes[0], 1, &ms));
+    prev = mnode;
+    for (size_t k = 0; k < ctx->par_classes.size(); ++k) {
+        void* args[1];
+        cudaKernelNodeParams kp = parent_node(ctx, k, &pp[k], args);
+        cudaGraphNode_t nd;
+        BD_CUDA(ctx, cudaGraphAddKernelNode(&nd, ctx->graph, &prev, 1, &kp));
+        ctx->par_nodes.push_back(nd);
+        prev = nd;
+    }
+    BD_CUDA(ctx, cudaGraphAddEventRecordNode(&ctx->ev_nodes[1], ctx->graph, &prev, 1, ctx->idle_ev[1]));
+    for (size_t k = 0; k < ctx->var_classes.size(); ++k) {
+        void* args[1];
+        cudaKernelNodeParams kp = replica_node(ctx, k, &rp[k], args);
+        cudaGraphNode_t nd;
+        BD_CUDA(ctx, cudaGraphAddKernelNode(&nd, ctx->graph, &ctx->ev_nodes[1], 1, &kp));
+        ctx->rep_nodes.push_back(nd);
+    }
+    BD_CUDA(ctx, cudaGraphAddEventRecordNode(&ctx->ev_nodes[2], ctx->graph, ctx->rep_nodes.data(),
+                                             ctx->rep_nodes.size(), ctx->idle_ev[2]));
+    BD_CUDA(ctx, cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+    return BD_OK;
 }
 
 bd_status reset_kinetics(bd_ctx* ctx)
@@ -455,40 +578,13 @@ bd_status upload(bd_ctx* ctx, T** dst, const std::vector<T>& v)
     return BD_OK;
 }
 
-void drop_timed(bd_ctx* ctx)
-{
-    for (auto& t : ctx->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
-    ctx->timed.clear();
-}
-
-// Records an event pair around one launch when timing is enabled.
-struct TimedLaunch {
-    bd_ctx* ctx;
-    int kind;
-    cudaEvent_t a = nullptr, b = nullptr;
-    TimedLaunch(bd_ctx* c, int k) : ctx(c), kind(k)
-    {
-        if (!ctx->timing) return;
-        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
-            cudaGetLastError();
-            a = b = nullptr;
-            return;
-        }
-        cudaEventRecord(a, ctx->stream);
-    }
-    ~TimedLaunch()
-    {
-        if (!a) return;
-        cudaEventRecord(b, ctx->stream);
-        ctx->timed.push_back({kind, a, b});
-    }
-};
-
 void release(bd_ctx* ctx)
 {
     if (!ctx) return;
     if (!ctx->allocs.empty()) cudaStreamSynchronize(ctx->stream);
-    drop_timed(ctx);
+    drop_graph(ctx);
+    for (int i = 0; i < 3; ++i)
+        if (ctx->idle_ev[i]) { cudaEventDestroy(ctx->idle_ev[i]); ctx->idle_ev[i] = nullptr; }
     for (void* p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
     cudaGetLastError();
@@ -538,8 +634,11 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
 #define BD_TRY(x) do { s = (x); if (s != BD_OK) goto failed; } while (0)
     {
         cudaError_t e = cudaGetDevice(&ctx->device);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
         if (e != cudaSuccess) { cudaGetLastError(); s = fail(ctx, BD_E_CUDA, "no CUDA device: %s", cudaGetErrorString(e)); goto failed; }
     }
+    for (int v = 0; v < 2 * kPairBase; ++v) ctx->var_cost[v] = default_variant_cost(v);
     BD_TRY(plan(ctx));
     {
         const int64_t M = ctx->M, C = cfg->n_chains, W = cfg->max_windows;
@@ -569,17 +668,8 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
         BD_TRY(dalloc(ctx, (void**)&ctx->d_exp1, sizeof(double) * 3 * (size_t)M));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_overext, sizeof(unsigned long long) * (size_t)C));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_evt_scratch, sizeof(int64_t) * (size_t)(event_blocks(M) + 1)));
-        for (const RepClass& rc : ctx->rep_classes) {
-            cudaError_t e = ctx->f64 ? prepare_replica_f64(rc.L, rc.smem, nullptr)
-                            : rc.paired ? prepare_replica2_f32(rc.L, rc.smem)
-                                        : prepare_replica_f32(rc.L, rc.smem, nullptr);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                s = fail(ctx, BD_E_CUDA, "kernel set-up for tile %d (%zu B shared): %s", rc.L,
-                         rc.smem, cudaGetErrorString(e));
-                goto failed;
-            }
-        }
+        BD_TRY(dalloc(ctx, (void**)&ctx->d_queue, sizeof(int32_t) * ctx->var_classes.size()));
+        BD_TRY(build_graph(ctx));
         {
             cudaError_t e = run_exp1(ctx->d_chains, ctx->d_spring_chain, M, ctx->rk0[0], ctx->rk1[0],
                                      ctx->d_exp1, ctx->stream);
@@ -629,30 +719,33 @@ bd_status bd_step(bd_ctx* ctx, int64_t n_steps)
     if (t_end / S > ctx->cfg.max_windows)
         return fail(ctx, BD_E_CAPACITY, "run to step %lld needs %lld windows; max_windows is %lld",
                     (long long)t_end, (long long)(t_end / S), (long long)ctx->cfg.max_windows);
-    StepParams p = base_params(ctx);
+    std::vector<StepParams> pp, rp;
+    std::vector<void*> pargs(ctx->par_nodes.size()), rargs(ctx->rep_nodes.size());
     int64_t t = ctx->step;
     while (t < t_end) {
         const int64_t w_first = (t + S - 1) / S;
         const int64_t chunk_end = std::min(t_end, (w_first + ctx->chunk_windows) * S);
-        p.t0 = t;
-        p.n_steps = chunk_end - t;
-        p.w_snap0 = w_first;
-        for (const ParClass& pc : ctx->par_classes) {
-            p.parent_items = ctx->d_parent_items + pc.item_begin;
-            p.n_parent_items = pc.item_count;
-            p.parent_G = pc.G;
-            TimedLaunch tl(ctx, 0);
-            BD_CUDA(ctx, ctx->f64 ? launch_parent_f64(pc.L, pc.grid, pc.threads, ctx->stream, p)
-                                  : launch_parent_f32(pc.L, pc.grid, pc.threads, ctx->stream, p));
-            ++ctx->launches;
+        chunk_params(ctx, t, chunk_end - t, w_first, pp, rp);
+        for (size_t k = 0; k < ctx->par_nodes.size(); ++k) {
+            cudaKernelNodeParams kp = parent_node(ctx, k, &pp[k], &pargs[k]);
+            BD_CUDA(ctx, cudaGraphExecKernelNodeSetParams(ctx->gexec, ctx->par_nodes[k], &kp));
         }
-        for (const RepClass& rc : ctx->rep_classes) {
-            p.items = ctx->d_items + rc.item_begin;
-            TimedLaunch tl(ctx, 1);
-            BD_CUDA(ctx, ctx->f64 ? launch_replica_f64(rc.L, rc.item_count, rc.threads, rc.smem, ctx->stream, p)
-                         : rc.paired ? launch_replica2_f32(rc.L, rc.item_count, rc.threads, rc.smem, ctx->stream, p)
-                                     : launch_replica_f32(rc.L, rc.item_count, rc.threads, rc.smem, ctx->stream, p));
-            ++ctx->launches;
+        for (size_t k = 0; k < ctx->rep_nodes.size(); ++k) {
+            cudaKernelNodeParams kp = replica_node(ctx, k, &rp[k], &rargs[k]);
+            BD_CUDA(ctx, cudaGraphExecKernelNodeSetParams(ctx->gexec, ctx->rep_nodes[k], &kp));
+        }
+        BD_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
+        ctx->launches += (int64_t)(ctx->par_nodes.size() + ctx->rep_nodes.size());
+        if (ctx->timing) {
+            // the graph's own events: read them before the next launch re-records them
+            float x = 0.0f, y = 0.0f;
+            BD_CUDA(ctx, cudaEventSynchronize(ctx->idle_ev[2]));
+            BD_CUDA(ctx, cudaEventElapsedTime(&x, ctx->idle_ev[0], ctx->idle_ev[1]));
+            BD_CUDA(ctx, cudaEventElapsedTime(&y, ctx->idle_ev[1], ctx->idle_ev[2]));
+            ctx->timed_ms[0] += x;
+            ctx->timed_ms[1] += y;
+            ctx->timed_n[0] += (int64_t)ctx->par_nodes.size();
+            ctx->timed_n[1] += (int64_t)ctx->rep_nodes.size();
         }
         t = chunk_end;
         ctx->step = t;
@@ -807,7 +900,7 @@ bd_status bd_get_info(bd_ctx* ctx, bd_info* out)
     out->overextensions = tot;
     out->device_bytes = (int64_t)ctx->bytes;
     out->kernel_launches = ctx->launches;
-    out->n_launch_classes = (int32_t)(ctx->rep_classes.size() + ctx->par_classes.size());
+    out->n_launch_classes = (int32_t)(ctx->var_classes.size() + ctx->par_classes.size());
     out->precision = ctx->cfg.precision;
     return BD_OK;
 }
@@ -823,21 +916,10 @@ bd_status bd_kernel_times(bd_ctx* ctx, double* ms, int64_t* launches)
 {
     if (!ctx) return BD_E_INVALID;
     BD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    double t[2] = {0.0, 0.0};
-    int64_t n[2] = {0, 0};
-    for (auto& e : ctx->timed) {
-        float x = 0.0f;
-        if (cudaEventElapsedTime(&x, e.a, e.b) != cudaSuccess) {
-            cudaGetLastError();
-            drop_timed(ctx);
-            return fail(ctx, BD_E_CUDA, "cudaEventElapsedTime failed");
-        }
-        t[e.kind] += x;
-        n[e.kind] += 1;
-    }
-    drop_timed(ctx);
-    if (ms) { ms[0] = t[0]; ms[1] = t[1]; }
-    if (launches) { launches[0] = n[0]; launches[1] = n[1]; }
+    if (ms) { ms[0] = ctx->timed_ms[0]; ms[1] = ctx->timed_ms[1]; }
+    if (launches) { launches[0] = ctx->timed_n[0]; launches[1] = ctx->timed_n[1]; }
+    ctx->timed_ms[0] = ctx->timed_ms[1] = 0.0;
+    ctx->timed_n[0] = ctx->timed_n[1] = 0;
     return BD_OK;
 }
 

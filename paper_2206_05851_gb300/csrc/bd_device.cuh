@@ -35,15 +35,24 @@ struct ChainDev {
     float f32_pad;
 };
 
-// One CTA's work: the parent of `chain` plus replicas rep_begin+1 ..
-// rep_begin+rep_count.
+// One warp's work: replicas rep_begin+1 .. rep_begin+rep_count of `chain`
+// (group `group` of the chain's replica-force partial sums), evolved with
+// the step variant `variant` (springs per lane, one or two replicas per
+// lane; see Variant).
 struct ItemDev {
     int32_t chain, group, rep_begin, rep_count;
+    int32_t variant, pad;
 };
+
+// Step variants: one replica per lane with L springs (code L), or two
+// replicas per lane with L springs (code kPairBase + L, float32 only).
+constexpr int32_t kPairBase = 100;
 
 struct StepParams {
     const ChainDev* chains;
-    const ItemDev* items;       // replica kernel: one (chain, group) per CTA
+    const ItemDev* items;       // replica kernel: warp work items, longest first
+    int32_t n_items;
+    int32_t* queue;             // next unclaimed work item (zeroed before each launch)
     const int32_t* parent_items;  // parent kernel: chain ids of this launch
     int32_t n_parent_items;
     int32_t parent_G;           // lanes per parent in the parent kernel

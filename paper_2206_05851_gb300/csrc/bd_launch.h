@@ -6,24 +6,29 @@
 
 namespace bdra {
 
-static const int kTiles[] = {2, 4, 7, 10, 13, 16};   // springs per lane
+// Parent-kernel tiles (springs per lane).
+static const int kTiles[] = {2, 4, 7, 10, 13, 16};
 static const int kNumTiles = 6;
-// springs per lane with two replicas per lane (larger tiles spill at 128 registers)
-static const int kPairTiles[] = {4, 7};
-static const int kNumPairTiles = 2;
 
-cudaError_t launch_replica_f32(int L, int grid, int threads, size_t smem, cudaStream_t st,
-                               const StepParams& p);
-cudaError_t launch_replica_f64(int L, int grid, int threads, size_t smem, cudaStream_t st,
-                               const StepParams& p);
-cudaError_t launch_parent_f32(int L, int grid, int threads, cudaStream_t st, const StepParams& p);
-cudaError_t launch_parent_f64(int L, int grid, int threads, cudaStream_t st, const StepParams& p);
-cudaError_t prepare_replica_f32(int L, size_t smem, cudaFuncAttributes* attr);
-cudaError_t prepare_replica_f64(int L, size_t smem, cudaFuncAttributes* attr);
-cudaError_t launch_replica2_f32(int L, int grid, int threads, size_t smem, cudaStream_t st,
-                                const StepParams& p);
-cudaError_t prepare_replica2_f32(int L, size_t smem);
-int max_threads_f32();
-int max_threads_f64();
+// Replica step variants compiled into the persistent kernel (ItemDev::variant):
+// float32: one replica per lane with 4..16 springs, two replicas per lane
+// with 4 or 7 springs (larger pair tiles spill at 128 registers);
+// float64: one replica per lane with 2..16 springs.
+static const int kVariantsF32[] = {4, 7, 10, 13, 16, kPairBase + 4, kPairBase + 7};
+static const int kNumVariantsF32 = 7;
+static const int kVariantsF64[] = {2, 4, 7, 10, 13, 16};
+static const int kNumVariantsF64 = 6;
+
+inline bool variant_paired(int v) { return v >= kPairBase; }
+inline int variant_tile(int v) { return v >= kPairBase ? v - kPairBase : v; }
+
+const void* parent_func_f32(int L);
+const void* parent_func_f64(int L);
+const void* persist_func_f32(int variant);
+const void* persist_func_f64(int variant);
+int persist_threads_f32();
+int persist_threads_f64();
+cudaError_t persist_blocks_per_sm_f32(int variant, int* n);
+cudaError_t persist_blocks_per_sm_f64(int variant, int* n);
 
 }  // namespace bdra

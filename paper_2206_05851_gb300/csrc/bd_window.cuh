@@ -198,30 +198,39 @@ __device__ __forceinline__ void store_bonds(const T (&qx)[L], const T (&qy)[L], 
 }
 
 // ---------------------------------------------------------------------------
-// Replicas. CTA = one (chain, group); slot s of the CTA is replica
-// rep_begin + s + 1. State of replica k: state[(state_off + k (N-1)) * 3 ...].
-// Snapshots: snap[((w - w_snap0) * M + spr_off + i) * 3 + d], written by the
-// parent kernel at every window start inside the current chunk.
+// Replicas, one warp work item (one replica per lane run). Lane run s of the
+// warp is replica rep_begin + s + 1; state of replica k lives at
+// state[(state_off + k (N-1)) * 3 ...]. Snapshots: snap[((w - w_snap0) * M +
+// spr_off + i) * 3 + d], written by the parent kernel at every window start
+// of the current chunk. wsm: this warp's scratch of kWarpScratch values.
 // ---------------------------------------------------------------------------
-template <typename T, int L, bool FAST>
-__global__ void __launch_bounds__(Tile<T, L>::max_threads, Tile<T, L>::min_blocks)
-replica_kernel(const StepParams p)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm_f = reinterpret_cast<T*>(smem_raw);            // [rep_count][N-1] end-of-window forces
+constexpr int kWarpScratch = 512;   // >= slots per warp x springs = P (N-1) <= 32 L
 
-    const ItemDev it = p.items[blockIdx.x];
+// Window end: float64 sum over this warp's replicas of each spring's force,
+// in replica order, one partial per (window, spring, group).
+template <typename T>
+__device__ __forceinline__ void warp_window_sum(const T* wsm, int nb, int count, double* prow)
+{
+    __syncwarp();
+    for (int i = (int)(threadIdx.x & 31); i < nb; i += 32) {
+        double acc = 0.0;
+        for (int s = 0; s < count; ++s) acc += (double)wsm[s * nb + i];
+        prow[i] = acc;
+    }
+    __syncwarp();
+}
+
+template <typename T, int L, bool FAST>
+__device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams& p, T* wsm)
+{
     const ChainDev ch = p.chains[it.chain];
     const int nb = ch.N - 1;
     const int G = (ch.N + L - 1) / L;
     const int P = 32 / G;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
     const int sw = lane / G;
-    const int slot = warp * P + sw;
-    const bool active = (sw < P) && (slot < it.rep_count);
-    const int kglob = it.rep_begin + slot + 1;
+    const bool active = (sw < P) && (sw < it.rep_count);
+    const int kglob = it.rep_begin + sw + 1;
     const uint32_t key = (p.flags & BD_FLAG_IDENTICAL_NOISE) ? 0u : (uint32_t)kglob;
     const LaneCtx lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, active, key,
                                  (uint32_t)it.chain);
@@ -235,12 +244,12 @@ replica_kernel(const StepParams p)
 
     int floored = 0;
     int s_in = (int)(p.t0 % p.S);
-    int64_t w = p.t0 / p.S;
-    const int64_t t_end = p.t0 + p.n_steps;
+    int w = (int)(p.t0 / p.S);                      // window index (< 2^31)
+    const uint32_t t_end = (uint32_t)(p.t0 + p.n_steps);   // steps stay below 2^32
 #pragma unroll 1
-    for (int64_t t = p.t0; t < t_end; ++t) {
+    for (uint32_t t = (uint32_t)p.t0; t < t_end; ++t) {
         if (s_in == 0)   // spawn: copy the halted parent (Sec. II)
-            load_bonds<T, L>(qx, qy, qz, snap + ((w - p.w_snap0) * p.M + ch.spr_off) * 3, lc);
+            load_bonds<T, L>(qx, qy, qz, snap + ((int64_t)(w - p.w_snap0) * p.M + ch.spr_off) * 3, lc);
         floored += step_bonds<T, L, FAST>(qx, qy, qz, lc, k, (uint32_t)t, p);
         if (++s_in == p.S) {
             // one force sample per replica at the end of the evolution time
@@ -250,23 +259,13 @@ replica_kernel(const StepParams p)
                 for (int j = 0; j < L; ++j) {
                     const int i = lc.bead0 + j;
                     if (i < nb)
-                        sm_f[slot * nb + i] =
+                        wsm[sw * nb + i] =
                             spring_tension<T, FAST>(qx[j], qy[j], qz[j], k.H, k.Hinvb, k.smin);
                 }
             }
-            __syncthreads();
-            // float64 sum over this group's replicas, fixed order: lane r takes
-            // replicas r, r+32, ..., then a butterfly over the warp.
-            double* prow = p.part_hist + w * p.part_stride + ch.part_off + (int64_t)it.group * nb;
-            for (int i = warp; i < nb; i += nwarps) {
-                double acc = 0.0;
-                for (int r = lane; r < it.rep_count; r += 32) acc += (double)sm_f[r * nb + i];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) prow[i] = acc;
-            }
+            warp_window_sum<T>(wsm, nb, it.rep_count,
+                               p.part_hist + (int64_t)w * p.part_stride + ch.part_off + (int64_t)it.group * nb);
             ++w;
-            __syncthreads();
         }
     }
     store_bonds<T, L>(qx, qy, qz, state, lc);

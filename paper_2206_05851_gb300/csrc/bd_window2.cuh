@@ -140,26 +140,18 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
     fl_out += lc.active ? fla + (act_b ? flb : 0) : 0;
 }
 
-// CTA = one (chain, group); lane pair-slot s holds replicas
+// One warp work item with two replicas per lane: lane run s holds replicas
 // rep_begin + 2s + 1 (.x) and rep_begin + 2s + 2 (.y).
 template <int L>
-__global__ void __launch_bounds__(Tile<float, L>::max_threads, Tile<float, L>::min_blocks)
-replica2_kernel(const StepParams p)
+__device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParams& p, float* wsm)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* sm_f = reinterpret_cast<float*>(smem_raw);      // [rep_count][N-1]
-
-    const ItemDev it = p.items[blockIdx.x];
     const ChainDev ch = p.chains[it.chain];
     const int nb = ch.N - 1;
     const int G = (ch.N + L - 1) / L;
     const int P = 32 / G;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
     const int sw = lane / G;
-    const int pair = warp * P + sw;
-    const int ra = 2 * pair, rb = 2 * pair + 1;             // replica slots of this group
+    const int ra = 2 * sw, rb = 2 * sw + 1;                 // replica slots of this item
     const bool act_a = (sw < P) && (ra < it.rep_count);
     const bool act_b = (sw < P) && (rb < it.rep_count);
     const int ka = it.rep_begin + ra + 1, kb = it.rep_begin + rb + 1;
@@ -171,8 +163,8 @@ replica2_kernel(const StepParams p)
     k.load(ch, p);
 
     float* state = reinterpret_cast<float*>(p.state) + ch.state_off * 3;
-    const float* sa = state + (int64_t)ka * nb * 3;
-    const float* sb = state + (int64_t)kb * nb * 3;
+    float* sa = state + (int64_t)ka * nb * 3;
+    float* sb = state + (int64_t)kb * nb * 3;
     const float* snap = reinterpret_cast<const float*>(p.snap);
     float2 qx[L], qy[L], qz[L];
 #pragma unroll
@@ -186,12 +178,12 @@ replica2_kernel(const StepParams p)
 
     int floored = 0;
     int s_in = (int)(p.t0 % p.S);
-    int64_t w = p.t0 / p.S;
-    const int64_t t_end = p.t0 + p.n_steps;
+    int w = (int)(p.t0 / p.S);                      // window index (< 2^31)
+    const uint32_t t_end = (uint32_t)(p.t0 + p.n_steps);   // steps stay below 2^32
 #pragma unroll 1
-    for (int64_t t = p.t0; t < t_end; ++t) {
+    for (uint32_t t = (uint32_t)p.t0; t < t_end; ++t) {
         if (s_in == 0) {  // spawn both replicas from the halted parent (Sec. II)
-            const float* src = snap + ((w - p.w_snap0) * p.M + ch.spr_off) * 3;
+            const float* src = snap + ((int64_t)(w - p.w_snap0) * p.M + ch.spr_off) * 3;
 #pragma unroll
             for (int j = 0; j < L; ++j) {
                 const int i = lc.bead0 + j;
@@ -209,33 +201,23 @@ replica2_kernel(const StepParams p)
                 for (int j = 0; j < L; ++j) {
                     const int i = lc.bead0 + j;
                     if (i < nb) {
-                        sm_f[ra * nb + i] = spring_tension<float, true>(qx[j].x, qy[j].x, qz[j].x, k.H.x, -k.nHinvb.x, k.smin);
+                        wsm[ra * nb + i] = spring_tension<float, true>(qx[j].x, qy[j].x, qz[j].x, k.H.x, -k.nHinvb.x, k.smin);
                         if (act_b)
-                            sm_f[rb * nb + i] = spring_tension<float, true>(qx[j].y, qy[j].y, qz[j].y, k.H.y, -k.nHinvb.y, k.smin);
+                            wsm[rb * nb + i] = spring_tension<float, true>(qx[j].y, qy[j].y, qz[j].y, k.H.y, -k.nHinvb.y, k.smin);
                     }
                 }
             }
-            __syncthreads();
-            double* prow = p.part_hist + w * p.part_stride + ch.part_off + (int64_t)it.group * nb;
-            for (int i = warp; i < nb; i += nwarps) {
-                double acc = 0.0;
-                for (int r = lane; r < it.rep_count; r += 32) acc += (double)sm_f[r * nb + i];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) prow[i] = acc;
-            }
+            warp_window_sum<float>(wsm, nb, it.rep_count,
+                                   p.part_hist + (int64_t)w * p.part_stride + ch.part_off + (int64_t)it.group * nb);
             ++w;
-            __syncthreads();
         }
     }
-    float* da = state + (int64_t)ka * nb * 3;
-    float* db = state + (int64_t)kb * nb * 3;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
         const int i = lc.bead0 + j;
         if (i < nb) {
-            if (act_a) { da[3 * i] = qx[j].x; da[3 * i + 1] = qy[j].x; da[3 * i + 2] = qz[j].x; }
-            if (act_b) { db[3 * i] = qx[j].y; db[3 * i + 1] = qy[j].y; db[3 * i + 2] = qz[j].y; }
+            if (act_a) { sa[3 * i] = qx[j].x; sa[3 * i + 1] = qy[j].x; sa[3 * i + 2] = qz[j].x; }
+            if (act_b) { sb[3 * i] = qx[j].y; sb[3 * i + 1] = qy[j].y; sb[3 * i + 2] = qz[j].y; }
         }
     }
     if (floored) atomicAdd(p.overext + it.chain, (unsigned long long)floored);

@@ -1,66 +1,46 @@
-// Instantiations of the parent and replica kernels for double state
-// (see bd_window.cuh). Compiled with -fmad=false.
-#include "bd_window.cuh"
+// Instantiations of the parent kernel and the persistent replica kernel for
+// double state (bd_window.cuh, bd_window2.cuh, bd_persist.cuh). Compiled with
+// -fmad=false.
+#include "bd_persist.cuh"
 #include "bd_launch.h"
 
 namespace bdra {
 
 namespace {
-template <int L>
-cudaError_t launch_rep(int grid, int threads, size_t smem, cudaStream_t st, const StepParams& p)
-{
-    replica_kernel<double, L, false><<<grid, threads, smem, st>>>(p);
-    return cudaGetLastError();
-}
-template <int L>
-cudaError_t launch_par(int grid, int threads, cudaStream_t st, const StepParams& p)
-{
-    parent_kernel<double, L, false><<<grid, threads, 0, st>>>(p);
-    return cudaGetLastError();
-}
-template <int L>
-cudaError_t prepare_rep(size_t smem, cudaFuncAttributes* attr)
-{
-    cudaError_t e = cudaFuncSetAttribute(replica_kernel<double, L, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return attr ? cudaFuncGetAttributes(attr, replica_kernel<double, L, false>) : cudaSuccess;
-}
+template <int L> const void* parent_fn() { return (const void*)parent_kernel<double, L, false>; }
 }  // namespace
 
-#define BD_TILES(X) X(2) X(4) X(7) X(10) X(13) X(16)
+#define BD_PARENT_TILES(X) X(2) X(4) X(7) X(10) X(13) X(16)
 
-cudaError_t launch_replica_f64(int L, int grid, int threads, size_t smem, cudaStream_t st,
-                                const StepParams& p)
+const void* parent_func_f64(int L)
 {
     switch (L) {
-#define X(l) case l: return launch_rep<l>(grid, threads, smem, st, p);
-        BD_TILES(X)
+#define X(l) case l: return parent_fn<l>();
+        BD_PARENT_TILES(X)
 #undef X
-    default: return cudaErrorInvalidValue;
+    default: return nullptr;
     }
 }
 
-cudaError_t launch_parent_f64(int L, int grid, int threads, cudaStream_t st, const StepParams& p)
+#define BD_VARIANTS(X) X(2) X(4) X(7) X(10) X(13) X(16)
+
+const void* persist_func_f64(int v)
 {
-    switch (L) {
-#define X(l) case l: return launch_par<l>(grid, threads, st, p);
-        BD_TILES(X)
+    switch (v) {
+#define X(x) case x: return (const void*)replica_persist_kernel<double, false, x>;
+        BD_VARIANTS(X)
 #undef X
-    default: return cudaErrorInvalidValue;
+    default: return nullptr;
     }
 }
 
-cudaError_t prepare_replica_f64(int L, size_t smem, cudaFuncAttributes* attr)
-{
-    switch (L) {
-#define X(l) case l: return prepare_rep<l>(smem, attr);
-        BD_TILES(X)
-#undef X
-    default: return cudaErrorInvalidValue;
-    }
-}
+int persist_threads_f64() { return Persist<double>::threads; }
 
-int max_threads_f64() { return Tile<double, 2>::max_threads; }
+cudaError_t persist_blocks_per_sm_f64(int v, int* n)
+{
+    const void* f = persist_func_f64(v);
+    if (!f) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, f, Persist<double>::threads, 0);
+}
 
 }  // namespace bdra
