@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk", type=int, default=10_000, help="integration steps per bench step")
-    ap.add_argument("--chains", type=int, default=1024)
+    ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count")
+    ap.add_argument("--workload", default="planar_1024",
+                    choices=["planar_1024", "uneven_4096", "bell_16384"])
+    ap.add_argument("--autotune", action="store_true", help="measure step variants first")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -143,12 +146,19 @@ def cpu_baseline(wl, pos0, n_chains=None, n_steps=1000):
                       f"({bead_steps:.3g} bead-steps, {dt:.1f} s wall, FP64, OpenMP over chains)"}
 
 
+def make_workload(args):
+    from paper_2206_05851_gb300 import inputs as I
+    kw = {"n_chains": args.chains} if args.chains else {}
+    return {"planar_1024": I.planar_1024, "uneven_4096": I.uneven_4096,
+            "bell_16384": I.bell_16384}[args.workload](**kw)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2206_05851_gb300 import inputs as I
-    wl = I.planar_1024(n_chains=args.chains)
+    wl = make_workload(args)
     pos0 = I.initial_positions(wl)
     cores = os.cpu_count() or 1
     n_chains = min(cores, wl.n_chains)
@@ -200,7 +210,7 @@ def main():
         dist.barrier()
     bdra.load()
 
-    wl = I.planar_1024(n_chains=args.chains)
+    wl = make_workload(args)
     # ranks own independent chain sets: same shapes, their own seeds (weak scaling)
     seed = wl.seed + 1000 * rank
     pos0 = I.initial_positions(wl, seed=wl.init_seed + rank)
@@ -212,6 +222,8 @@ def main():
     ctx = bdra.Context(wl.chains, wl.dt, S, seed, torch.from_numpy(pos0).cuda(),
                        precision=bdra.BD_PREC_FP32, max_windows=total_windows,
                        thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=sptr)
+    if args.autotune:
+        ctx.autotune(probe_steps=32)
     bead_steps_chunk = sum(c.n_replicas * c.n_beads for c in wl.chains) * chunk
     slot_bead_steps_chunk = bead_steps_chunk        # replica slots only (the replica kernel)
     ev_cap = 6 * ctx.M
@@ -274,11 +286,13 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
-           "config": {"workload": wl.name, "chains_per_gpu": len(wl.chains), "beads": 100,
-                      "replicas": 64, "flow": "planar elongation", "Wi": 5, "b": 100,
+           "config": {"workload": wl.name, "chains_per_gpu": len(wl.chains),
+                      "beads": sorted({c.n_beads for c in wl.chains})[:1] + sorted({c.n_beads for c in wl.chains})[-1:],
+                      "replicas": sorted({c.n_replicas for c in wl.chains}),
                       "dt": wl.dt, "window_steps": S, "steps_per_bench_step": chunk,
                       "timed_integration_steps": chunk * args.steps,
-                      "criteria": "threshold + Bell on RSF", "precision": "FP32 integrate, FP64 reduce",
+                      "criteria": f"threshold mask {wl.thr_mask}, Bell mask {wl.bell_mask} (1 ISF, 2 TSF, 4 RSF)",
+                      "precision": "FP32 integrate, FP64 reduce", "autotuned": bool(args.autotune),
                       "l2": "flushed (256 MB write) between timed steps",
                       "parallelism": f"chains sharded over {world} GPU(s), no collective on the data path"},
            "gpu_launches": int(launches), "events_detected": int(n_events),

@@ -184,6 +184,25 @@ bd_status bd_set_positions(bd_ctx* ctx, const double* pos, int64_t step);
 /* Counters and sizes (host struct). */
 bd_status bd_get_info(bd_ctx* ctx, bd_info* out);
 
+/* Autotuner of the launch shapes (the batching form of the method: chains of
+ * uneven bead and replica counts share one persistent launch). For every
+ * compiled step variant - springs per lane, one or two replicas per lane -
+ * times the persistent replica kernel on this context's chains (a scratch
+ * copy of the state, probe_steps steps with no window boundary inside) and
+ * records the throughput cost of one warp-step; then re-plans every chain
+ * with the measured costs (per chain, the variant that minimises work items
+ * x cost per useful bead-step) and rebuilds the step graph. Costs are cached
+ * per device and precision for the process; force != 0 measures again. Must
+ * be called before the first bd_step (BD_E_STATE otherwise). Synchronises. */
+bd_status bd_autotune(bd_ctx* ctx, int32_t probe_steps, int32_t force);
+
+/* The current plan: variant[c] (springs per lane, plus 100 for two replicas
+ * per lane) and groups[c] (warp work items) per chain, host arrays of
+ * n_chains; cost_ns (host, may be NULL) receives the per-warp-step cost of
+ * each compiled variant in the order float32 {4, 7, 10, 13, 16, 104, 107} or
+ * float64 {2, 4, 7, 10, 13, 16}. Any pointer may be NULL. */
+bd_status bd_get_plan(bd_ctx* ctx, int32_t* variant, int32_t* groups, double* cost_ns);
+
 /* Kernel timing for measurement tools. Each chunk graph that bd_step launches
  * records CUDA events before its parent kernels, between the parent and
  * replica kernels, and after the replica kernels. enable != 0: after every

@@ -92,6 +92,8 @@ def load() -> ctypes.CDLL:
         "bd_get_positions": ([vp, ctypes.c_int32, vp, P(ctypes.c_int64)], st),
         "bd_set_positions": ([vp, vp, ctypes.c_int64], st),
         "bd_get_info": ([vp, P(bd_info)], st),
+        "bd_autotune": ([vp, ctypes.c_int32, ctypes.c_int32], st),
+        "bd_get_plan": ([vp, vp, vp, vp], st),
         "bd_enable_timing": ([vp, ctypes.c_int32], st),
         "bd_kernel_times": ([vp, P(ctypes.c_double), P(ctypes.c_int64)], st),
         "bd_philox_normals": ([ctypes.c_uint64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp], st),
@@ -223,6 +225,20 @@ def bd_set_positions(ctx: int, pos, step: int = 0) -> None:
     _check(load().bd_set_positions(ctx, _ptr(pos)[0], int(step)), ctx)
 
 
+def bd_autotune(ctx: int, probe_steps: int = 32, force: bool = False) -> None:
+    _check(load().bd_autotune(ctx, int(probe_steps), int(bool(force))), ctx)
+
+
+def bd_get_plan(ctx: int, n_chains: int, precision: int = BD_PREC_FP32):
+    """(variant per chain, groups per chain, {variant: cost ns per warp-step})."""
+    v = np.zeros(n_chains, dtype=np.int32)
+    g = np.zeros(n_chains, dtype=np.int32)
+    names = [2, 4, 7, 10, 13, 16] if precision == BD_PREC_FP64 else [4, 7, 10, 13, 16, 104, 107]
+    c = np.zeros(len(names))
+    _check(load().bd_get_plan(ctx, v.ctypes.data, g.ctypes.data, c.ctypes.data), ctx)
+    return v, g, dict(zip(names, c.tolist()))
+
+
 def bd_enable_timing(ctx: int, enable: bool) -> None:
     _check(load().bd_enable_timing(ctx, int(bool(enable))), ctx)
 
@@ -314,6 +330,12 @@ class Context:
 
     def set_positions(self, pos, step: int = 0) -> None:
         bd_set_positions(self.ptr, pos, step)
+
+    def autotune(self, probe_steps: int = 32, force: bool = False) -> None:
+        bd_autotune(self.ptr, probe_steps, force)
+
+    def plan(self):
+        return bd_get_plan(self.ptr, len(self.chains), self.cfg.precision)
 
     def kinetics(self):
         haz = np.zeros((3, self.M))

@@ -6,6 +6,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -22,9 +24,9 @@ struct VarClass {      // one persistent replica launch: the work items of one s
     int item_begin, item_count;
     int grid, threads;
 };
-struct ParClass {      // one parent-kernel launch
-    int L, G, threads, grid;
-    int item_begin, item_count;
+struct ParClass {      // one parent-kernel launch: the parent warps of one tile
+    int L, threads, grid;
+    int warp_begin, warp_count;
 };
 
 }  // namespace
@@ -41,6 +43,7 @@ struct bd_ctx {
     std::vector<ChainDev> h_chains;
     std::vector<ItemDev> h_items;
     std::vector<int32_t> h_parent_items;
+    std::vector<ParentWarp> h_parent_warps;
     std::vector<VarClass> var_classes;
     std::vector<ParClass> par_classes;
     double var_cost[2 * kPairBase];     // issue cost per warp-step of each variant
@@ -49,6 +52,7 @@ struct bd_ctx {
     ChainDev* d_chains = nullptr;
     ItemDev* d_items = nullptr;
     int32_t* d_parent_items = nullptr;
+    ParentWarp* d_parent_warps = nullptr;
     int32_t* d_spring_chain = nullptr;
     int64_t* d_pair_parent = nullptr;   // [n_chains + 1] prefix of 1 per chain
     int64_t* d_pair_all = nullptr;      // [n_chains + 1] prefix of R + 1 per chain
@@ -121,6 +125,15 @@ bd_status dalloc(bd_ctx* ctx, void** p, size_t n)
     ctx->allocs.push_back(*p);
     ctx->bytes += n;
     return BD_OK;
+}
+
+void dfree(bd_ctx* ctx, void* p, size_t n)
+{
+    if (!p) return;
+    cudaFree(p);
+    auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+    if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+    ctx->bytes -= n;
 }
 
 bool is_device_ptr(const void* p)
@@ -352,21 +365,28 @@ bd_status plan(bd_ctx* ctx)
         const int need = (vc.item_count + warps - 1) / warps;
         vc.grid = std::max(1, std::min(need, per_sm * ctx->n_sm));
     }
-    // parent launches: one per (L, G) class, two warps per CTA
+    // parent launches: one per tile; warps pack parents of equal lane count
     std::stable_sort(par.begin(), par.end());
     ctx->h_parent_items.clear();
+    ctx->h_parent_warps.clear();
     ctx->par_classes.clear();
-    for (size_t k = 0; k < par.size(); ++k) {
-        const int L = par[k].first.first, G = par[k].first.second;
-        if (ctx->par_classes.empty() || ctx->par_classes.back().L != L ||
-            ctx->par_classes.back().G != G)
-            ctx->par_classes.push_back(ParClass{L, G, 64, 0, (int)k, 0});
-        ctx->par_classes.back().item_count++;
-        ctx->h_parent_items.push_back(par[k].second);
+    for (size_t k = 0; k < par.size();) {
+        const int L = par[k].first.first, G = par[k].first.second, P = 32 / G;
+        if (ctx->par_classes.empty() || ctx->par_classes.back().L != L)
+            ctx->par_classes.push_back(ParClass{L, 64, 0, (int)ctx->h_parent_warps.size(), 0});
+        size_t e = k;
+        while (e < par.size() && par[e].first == par[k].first) ++e;
+        for (size_t j = k; j < e; j += P) {
+            const int cnt = (int)std::min<size_t>(P, e - j);
+            ctx->h_parent_warps.push_back(ParentWarp{(int32_t)ctx->h_parent_items.size(), cnt, G, 0});
+            for (int s = 0; s < cnt; ++s) ctx->h_parent_items.push_back(par[j + s].second);
+            ctx->par_classes.back().warp_count++;
+        }
+        k = e;
     }
     for (ParClass& pc : ctx->par_classes) {
-        const int per_cta = (pc.threads / 32) * (32 / pc.G);
-        pc.grid = (pc.item_count + per_cta - 1) / per_cta;
+        const int per_cta = pc.threads / 32;
+        pc.grid = (pc.warp_count + per_cta - 1) / per_cta;
     }
     // snapshot chunk: up to 64 windows, capped at ~512 MB
     const int64_t per_window = ctx->M * 3 * (int64_t)ctx->tsize;
@@ -416,9 +436,8 @@ void chunk_params(const bd_ctx* ctx, int64_t t0, int64_t n, int64_t w0,
     pp.assign(ctx->par_classes.size(), p);
     for (size_t k = 0; k < ctx->par_classes.size(); ++k) {
         const ParClass& pc = ctx->par_classes[k];
-        pp[k].parent_items = ctx->d_parent_items + pc.item_begin;
-        pp[k].n_parent_items = pc.item_count;
-        pp[k].parent_G = pc.G;
+        pp[k].parent_warps = ctx->d_parent_warps + pc.warp_begin;
+        pp[k].n_parent_warps = pc.warp_count;
     }
     rp.assign(ctx->var_classes.size(), p);
     for (size_t k = 0; k < ctx->var_classes.size(); ++k) {
@@ -466,8 +485,9 @@ void drop_graph(bd_ctx* ctx)
     cudaGetLastError();
 }
 
-// Builds the chunk graph: start event -> queue reset -> parent kernels (in
-// sequence) -> mid event -> replica kernels (parallel) -> end event.
+// Builds the chunk graph: start event -> queue reset -> parent kernels (one
+// per tile, parallel) -> mid event -> replica kernels (one per variant,
+// parallel) -> end event.
 bd_status build_graph(bd_ctx* ctx)
 {
     drop_graph(ctx);
@@ -488,15 +508,15 @@ bd_status build_graph(bd_ctx* ctx)
     cudaGraphNode_t mnode;
     BD_CUDA(ctx, cudaGraphAddMemsetNode(&mnode, ctx->graph, &ctx->ev_nodes[0], 1, &ms));
     prev = mnode;
-    for (size_t k = 0; k < ctx->par_classes.size(); ++k) {
+    for (size_t k = 0; k < ctx->par_classes.size(); ++k) {      // parallel branches
         void* args[1];
         cudaKernelNodeParams kp = parent_node(ctx, k, &pp[k], args);
         cudaGraphNode_t nd;
         BD_CUDA(ctx, cudaGraphAddKernelNode(&nd, ctx->graph, &prev, 1, &kp));
         ctx->par_nodes.push_back(nd);
-        prev = nd;
     }
-    BD_CUDA(ctx, cudaGraphAddEventRecordNode(&ctx->ev_nodes[1], ctx->graph, &prev, 1, ctx->idle_ev[1]));
+    BD_CUDA(ctx, cudaGraphAddEventRecordNode(&ctx->ev_nodes[1], ctx->graph, ctx->par_nodes.data(),
+                                             ctx->par_nodes.size(), ctx->idle_ev[1]));
     for (size_t k = 0; k < ctx->var_classes.size(); ++k) {
         void* args[1];
         cudaKernelNodeParams kp = replica_node(ctx, k, &rp[k], args);
@@ -590,6 +610,132 @@ void release(bd_ctx* ctx)
     cudaGetLastError();
 }
 
+// Measured issue cost per warp-step of each variant, per (device,
+// precision), shared by every context of the process.
+std::mutex g_tune_mutex;
+std::map<std::pair<int, int>, std::vector<double>> g_tune_cache;
+
+// Times every compiled step variant on the context's own chains: a scratch
+// copy of the state, steps 1 .. probe_steps of a window too long to end (no
+// spawn, no window-end reduction), enough warp items to fill the GPU four
+// times over. cost[v] = kernel time / (work items x steps): the GPU's
+// throughput cost of one warp-step of variant v, in nanoseconds.
+bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost)
+{
+    cost.assign(2 * kPairBase, 0.0);
+    const int* vars = ctx->f64 ? kVariantsF64 : kVariantsF32;
+    const int nv = ctx->f64 ? kNumVariantsF64 : kNumVariantsF32;
+    const int threads = ctx->f64 ? persist_threads_f64() : persist_threads_f32();
+    const size_t state_bytes = ctx->tsize * 3 * (size_t)ctx->state_bonds;
+    void* tstate = nullptr;
+    unsigned long long* tover = nullptr;
+    int32_t* tqueue = nullptr;
+    ItemDev* titems = nullptr;
+    size_t titems_cap = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bd_status st = BD_OK;
+#define BD_PROBE(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cudaGetLastError(); st = fail(ctx, BD_E_CUDA, "autotune: %s failed: %s", #call, cudaGetErrorString(e_)); goto done; } } while (0)
+    BD_PROBE(cudaMalloc(&tstate, state_bytes));
+    BD_PROBE(cudaMalloc((void**)&tover, sizeof(unsigned long long) * ctx->cfg.n_chains));
+    BD_PROBE(cudaMalloc((void**)&tqueue, sizeof(int32_t)));
+    BD_PROBE(cudaMemcpyAsync(tstate, ctx->d_state, state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    BD_PROBE(cudaEventCreate(&e0));
+    BD_PROBE(cudaEventCreate(&e1));
+    for (int t = 0; t < nv; ++t) {
+        const int v = vars[t];
+        const int L = variant_tile(v);
+        std::vector<ItemDev> items;
+        for (int c = 0; c < ctx->cfg.n_chains; ++c) {
+            const int N = ctx->chains[c].n_beads, R = ctx->chains[c].n_replicas;
+            const int G = (N + L - 1) / L;
+            if (G > 32) continue;
+            const int per_warp = (variant_paired(v) ? 2 : 1) * (32 / G);
+            const int groups = (R + per_warp - 1) / per_warp;
+            int begin = 0;
+            for (int g = 0; g < groups; ++g) {
+                const int cnt = R / groups + (g < R % groups ? 1 : 0);
+                items.push_back(ItemDev{c, g, begin, cnt, v, 0});
+                begin += cnt;
+            }
+        }
+        if (items.empty()) continue;
+        int per_sm = 1;
+        BD_PROBE(ctx->f64 ? persist_blocks_per_sm_f64(v, &per_sm) : persist_blocks_per_sm_f32(v, &per_sm));
+        const size_t resident = (size_t)per_sm * ctx->n_sm * (threads / 32);
+        const size_t base = items.size();
+        while (items.size() < 4 * resident) items.push_back(items[items.size() % base]);
+        if (items.size() > titems_cap) {
+            if (titems) cudaFree(titems);
+            titems = nullptr;
+            BD_PROBE(cudaMalloc((void**)&titems, sizeof(ItemDev) * items.size()));
+            titems_cap = items.size();
+        }
+        BD_PROBE(cudaMemcpyAsync(titems, items.data(), sizeof(ItemDev) * items.size(),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+        StepParams p = base_params(ctx);
+        p.state = tstate;
+        p.overext = tover;
+        p.items = titems;
+        p.n_items = (int32_t)items.size();
+        p.queue = tqueue;
+        p.S = 1 << 30;                 // no window starts or ends inside the probe
+        p.t0 = 1;
+        p.n_steps = probe_steps;
+        p.w_snap0 = 0;
+        void* args[1] = {&p};
+        const void* fn = ctx->f64 ? persist_func_f64(v) : persist_func_f32(v);
+        const dim3 grid((unsigned)std::max<size_t>(1, std::min<size_t>((items.size() + threads / 32 - 1) / (threads / 32), (size_t)per_sm * ctx->n_sm)));
+        for (int rep = 0; rep < 2; ++rep) {      // first launch warms up
+            BD_PROBE(cudaMemsetAsync(tqueue, 0, sizeof(int32_t), ctx->stream));
+            BD_PROBE(cudaEventRecord(e0, ctx->stream));
+            BD_PROBE(cudaLaunchKernel(fn, grid, dim3(threads), args, 0, ctx->stream));
+            BD_PROBE(cudaEventRecord(e1, ctx->stream));
+            ++ctx->launches;
+        }
+        BD_PROBE(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        BD_PROBE(cudaEventElapsedTime(&ms, e0, e1));
+        cost[v] = (double)ms * 1e6 / ((double)items.size() * probe_steps);
+    }
+done:
+#undef BD_PROBE
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(ctx->stream);
+    if (titems) cudaFree(titems);
+    if (tqueue) cudaFree(tqueue);
+    if (tover) cudaFree(tover);
+    if (tstate) cudaFree(tstate);
+    cudaGetLastError();
+    return st;
+}
+
+// Re-plans with the current variant costs and rebuilds what depends on the
+// plan (chain table, work items, partial-sum history, queues, graph). Only
+// valid before the first window completes.
+bd_status replan(bd_ctx* ctx)
+{
+    BD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const size_t old_items = ctx->h_items.size();
+    const int64_t old_part = ctx->part_stride;
+    const size_t old_queue = ctx->var_classes.size();
+    bd_status s = plan(ctx);
+    if (s != BD_OK) return s;
+    BD_CUDA(ctx, cudaMemcpyAsync(ctx->d_chains, ctx->h_chains.data(), sizeof(ChainDev) * ctx->h_chains.size(),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    dfree(ctx, ctx->d_items, sizeof(ItemDev) * std::max<size_t>(old_items, 1));
+    ctx->d_items = nullptr;
+    if ((s = upload(ctx, &ctx->d_items, ctx->h_items)) != BD_OK) return s;
+    dfree(ctx, ctx->d_part, std::max<size_t>(sizeof(double) * (size_t)ctx->cfg.max_windows * (size_t)old_part, 16));
+    ctx->d_part = nullptr;
+    if ((s = dalloc(ctx, (void**)&ctx->d_part, sizeof(double) * (size_t)ctx->cfg.max_windows * (size_t)ctx->part_stride)) != BD_OK)
+        return s;
+    dfree(ctx, ctx->d_queue, std::max<size_t>(sizeof(int32_t) * old_queue, 16));
+    ctx->d_queue = nullptr;
+    if ((s = dalloc(ctx, (void**)&ctx->d_queue, sizeof(int32_t) * ctx->var_classes.size())) != BD_OK) return s;
+    return build_graph(ctx);
+}
+
 }  // namespace
 
 extern "C" {
@@ -654,6 +800,7 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
         BD_TRY(upload(ctx, &ctx->d_chains, ctx->h_chains));
         BD_TRY(upload(ctx, &ctx->d_items, ctx->h_items));
         BD_TRY(upload(ctx, &ctx->d_parent_items, ctx->h_parent_items));
+        BD_TRY(upload(ctx, &ctx->d_parent_warps, ctx->h_parent_warps));
         BD_TRY(upload(ctx, &ctx->d_spring_chain, spring_chain));
         BD_TRY(upload(ctx, &ctx->d_pair_parent, pair_parent));
         BD_TRY(upload(ctx, &ctx->d_pair_all, pair_all));
@@ -920,6 +1067,50 @@ bd_status bd_kernel_times(bd_ctx* ctx, double* ms, int64_t* launches)
     if (launches) { launches[0] = ctx->timed_n[0]; launches[1] = ctx->timed_n[1]; }
     ctx->timed_ms[0] = ctx->timed_ms[1] = 0.0;
     ctx->timed_n[0] = ctx->timed_n[1] = 0;
+    return BD_OK;
+}
+
+bd_status bd_autotune(bd_ctx* ctx, int32_t probe_steps, int32_t force)
+{
+    if (!ctx) return BD_E_INVALID;
+    if (probe_steps < 1) return fail(ctx, BD_E_INVALID, "probe_steps must be >= 1");
+    if (ctx->step != 0) return fail(ctx, BD_E_STATE, "bd_autotune must come before the first bd_step");
+    const std::pair<int, int> key(ctx->device, ctx->cfg.precision);
+    std::vector<double> cost;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && !force) cost = it->second;
+    }
+    if (cost.empty()) {
+        bd_status s = autotune_probe(ctx, probe_steps, cost);
+        if (s != BD_OK) return s;
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        std::vector<double>& c = g_tune_cache[key];
+        if (c.empty()) c.assign(2 * kPairBase, 0.0);
+        for (int v = 0; v < 2 * kPairBase; ++v) if (cost[v] > 0) c[v] = cost[v];
+        cost = c;
+    }
+    for (int v = 0; v < 2 * kPairBase; ++v)
+        if (cost[v] > 0) ctx->var_cost[v] = cost[v];
+    return replan(ctx);
+}
+
+bd_status bd_get_plan(bd_ctx* ctx, int32_t* variant, int32_t* groups, double* cost_ns)
+{
+    if (!ctx) return BD_E_INVALID;
+    std::vector<int32_t> first(ctx->cfg.n_chains, -1);
+    for (const ItemDev& it : ctx->h_items)
+        if (first[it.chain] < 0) first[it.chain] = it.variant;
+    for (int c = 0; c < ctx->cfg.n_chains; ++c) {
+        if (variant) variant[c] = first[c];
+        if (groups) groups[c] = ctx->h_chains[c].n_groups;
+    }
+    if (cost_ns) {
+        const int* vars = ctx->f64 ? kVariantsF64 : kVariantsF32;
+        const int nv = ctx->f64 ? kNumVariantsF64 : kNumVariantsF32;
+        for (int t = 0; t < nv; ++t) cost_ns[t] = ctx->var_cost[vars[t]];
+    }
     return BD_OK;
 }
 

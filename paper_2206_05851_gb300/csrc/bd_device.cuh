@@ -44,6 +44,12 @@ struct ItemDev {
     int32_t variant, pad;
 };
 
+// One warp of the parent kernel: `count` parents, chains
+// parent_items[first .. first+count-1], each on G lanes.
+struct ParentWarp {
+    int32_t first, count, G, pad;
+};
+
 // Step variants: one replica per lane with L springs (code L), or two
 // replicas per lane with L springs (code kPairBase + L, float32 only).
 constexpr int32_t kPairBase = 100;
@@ -53,9 +59,9 @@ struct StepParams {
     const ItemDev* items;       // replica kernel: warp work items, longest first
     int32_t n_items;
     int32_t* queue;             // next unclaimed work item (zeroed before each launch)
-    const int32_t* parent_items;  // parent kernel: chain ids of this launch
-    int32_t n_parent_items;
-    int32_t parent_G;           // lanes per parent in the parent kernel
+    const int32_t* parent_items;  // parent kernel: chain ids
+    const ParentWarp* parent_warps;  // parent kernel: warps of this launch
+    int32_t n_parent_warps;
     void* state;                // T [state_elems][3]
     void* snap;                 // T [chunk windows][M][3] parent at window starts
     int64_t w_snap0;            // window index of snapshot 0

@@ -273,7 +273,8 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
 }
 
 // ---------------------------------------------------------------------------
-// Parents. Warp w of CTA b holds P parents: chains parent_items[(b W + w) P + s].
+// Parents. Global warp g holds parent_warps[g].count parents (chains
+// parent_items[first + s]), each on G lanes.
 // Per step: update, then sample the parent's spring forces (ISF): TSF window
 // sums and ISF threshold / Bell criteria. Window sums and the window's hazard
 // stay in registers; the integrated hazard lives in p.lam (float64).
@@ -283,13 +284,14 @@ __global__ void __launch_bounds__(Tile<T, L>::max_threads, 1)
 parent_kernel(const StepParams p)
 {
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int G = p.parent_G;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= p.n_parent_warps) return;          // whole warp: no shuffle partner left behind
+    const ParentWarp pw = p.parent_warps[gw];
+    const int G = pw.G;
     const int P = 32 / G;
     const int sw = lane / G;
-    const int idx = (blockIdx.x * (blockDim.x >> 5) + warp) * P + sw;
-    const bool active = (sw < P) && (idx < p.n_parent_items);
-    const int c = active ? p.parent_items[idx] : p.parent_items[0];
+    const bool active = (sw < P) && (sw < pw.count);
+    const int c = p.parent_items[pw.first + (active ? sw : 0)];
     const ChainDev ch = p.chains[c];
     const int nb = ch.N - 1;
     const LaneCtx lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, active, 0u,

@@ -393,3 +393,33 @@ def test_full_size_sampled_parity():
     assert rel_err_chains(got, O.com_frame(r["pos"], [100] * 3), [100] * 3) <= 1e-4
     rs = np.concatenate([g["rsf"][:, 99 * c:99 * (c + 1)] for c in sample], axis=1)
     assert np.abs(rs - r["rsf"]).max() / np.abs(r["rsf"]).max() <= 1e-4
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_autotune_changes_shapes_not_results(prec):
+    # the autotuner times every step variant and re-plans; results must not move
+    chains = _ragged_chains()
+    S, dt, seed, n = 7, 1e-3, 11, 70
+    pos0 = I.initial_positions(I.custom(chains, dt, S, n), seed=5)
+    base = gpu_run(chains, dt, S, [n], seed, pos0, prec)
+    ctx = bdra.Context(chains, dt, S, seed, pos0, precision=prec, max_windows=n // S + 1,
+                       thr_mask=7, bell_mask=7, stream=_stream())
+    ctx.autotune(probe_steps=8, force=True)
+    variants, groups, costs = ctx.plan()
+    assert all(c > 0 for c in costs.values())
+    for ch, v, g in zip(chains, variants, groups):
+        L = v % 100
+        per_warp = (2 if v >= 100 else 1) * (32 // -(-ch.n_beads // L))
+        assert -(-ch.n_beads // L) <= 32 and g == -(-ch.n_replicas // per_warp)
+    ctx.step(n)
+    allpos = ctx.positions(True)
+    rsf = np.array([ctx.replica_average(w) for w in range(n // S)])
+    with pytest.raises(bdra.BdError) as e:       # only before the first step
+        ctx.autotune(8)
+    assert e.value.status == bdra.BD_E_STATE
+    ctx.close()
+    np.testing.assert_array_equal(allpos, base["allpos"])
+    if prec == bdra.BD_PREC_FP32:
+        np.testing.assert_array_equal(rsf, base["rsf"])
+    else:
+        np.testing.assert_allclose(rsf, base["rsf"], rtol=2e-15, atol=0)
