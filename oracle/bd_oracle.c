@@ -224,6 +224,195 @@ void ora_normals3_many(uint64_t seed, int64_t n, const uint32_t* ctr, double* xi
                      ctr[4 * j + 2], ctr[4 * j + 3], &xi[3 * j]);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Pathwise derivatives with frozen noise (forward-mode tangents).          */
+/* Parameters theta = (rate, b, H) of every chain. Each slot carries, beside */
+/* its positions r, the three tangents dr/dtheta_j; the Euler map of Eq. 1   */
+/* is differentiated with the noise held fixed, and a spawned replica copies */
+/* the parent's tangents with its positions. The RSF tangent follows from    */
+/* the tension f = |F(Q)| of each replica at the window end.                 */
+/* ------------------------------------------------------------------------ */
+
+/* Spring-law derivatives at connector Q: force F = c Q with c = H / s,
+ * s = 1 - H Q^2 / b (Hooke: c = H). dF = c dQ + (dc/dq2) 2 (Q.dQ) Q for a
+ * change of Q; dc/dH and dc/db for a change of the parameters (zero for b,
+ * and constant in Q, once the floor applies). */
+static void ora_spring_partials(const ora_chain* ch, double s_min, const double Q[3],
+                                double* c, double* dc_dq2, double* dc_dH, double* dc_db)
+{
+    const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+    if (ch->spring != ORA_SPRING_FENE) {
+        *c = ch->H; *dc_dq2 = 0.0; *dc_dH = 1.0; *dc_db = 0.0;
+        return;
+    }
+    double s = 1.0 - ch->H * q2 / ch->b;
+    if (s < s_min) {
+        *c = ch->H / s_min; *dc_dq2 = 0.0; *dc_dH = 1.0 / s_min; *dc_db = 0.0;
+        return;
+    }
+    *c = ch->H / s;
+    *dc_dq2 = ch->H * ch->H / (ch->b * s * s);               /* -H/s^2 * ds/dq2 */
+    *dc_dH = 1.0 / s + ch->H * q2 / (ch->b * s * s);         /* 1/s^2 */
+    *dc_db = -ch->H * ch->H * q2 / (ch->b * ch->b * s * s);  /* -H/s^2 * ds/db  */
+}
+
+/* Directional derivative of the spring force: dF for a connector change dQ
+ * and parameter changes (dH, db). */
+static void ora_force_tangent(const ora_chain* ch, double s_min, const double Q[3],
+                              const double dQ[3], double dH, double db, double dF[3])
+{
+    double c, dcq, dcH, dcb;
+    ora_spring_partials(ch, s_min, Q, &c, &dcq, &dcH, &dcb);
+    const double qdq = Q[0] * dQ[0] + Q[1] * dQ[1] + Q[2] * dQ[2];
+    const double dc = dcq * 2.0 * qdq + dcH * dH + dcb * db;
+    for (int d = 0; d < 3; ++d) dF[d] = c * dQ[d] + dc * Q[d];
+}
+
+/* One Eq. 1 step of positions r and of their tangents tr[3][N][3] (for rate,
+ * b, H), noise xi frozen. The tangent of a drift term is taken at time t. */
+static int64_t ora_em_step_tangent(const ora_chain* ch, double dt, double s_min, double* r,
+                                   double* tr, const double* xi)
+{
+    const double D = 0.25, kT = 1.0;
+    const int N = ch->n_beads;
+    double kappa[9], khat[9];
+    ora_flow_gradient(ch->flow, ch->rate, kappa);
+    ora_flow_gradient(ch->flow, 1.0, khat);                 /* d kappa / d rate */
+    double* dr = (double*)calloc(3 * (size_t)N * 3, sizeof(double));
+    for (int j = 0; j < 3; ++j) {
+        const double dH = j == 2 ? 1.0 : 0.0, db = j == 1 ? 1.0 : 0.0;
+        double* t = tr + 3 * (size_t)N * j;
+        double* F = (double*)calloc(3 * (size_t)N, sizeof(double));
+        for (int i = 0; i + 1 < N; ++i) {
+            double Q[3], dQ[3];
+            for (int d = 0; d < 3; ++d) {
+                Q[d] = r[3 * (i + 1) + d] - r[3 * i + d];
+                dQ[d] = t[3 * (i + 1) + d] - t[3 * i + d];
+            }
+            ora_force_tangent(ch, s_min, Q, dQ, dH, db, &F[3 * i]);
+        }
+        for (int i = 0; i < N; ++i) {
+            for (int d = 0; d < 3; ++d) {
+                double dfs = 0.0;
+                if (i + 1 < N) dfs += F[3 * i + d];
+                if (i > 0)     dfs -= F[3 * (i - 1) + d];
+                double dv = kappa[3 * d + 0] * t[3 * i + 0] + kappa[3 * d + 1] * t[3 * i + 1]
+                          + kappa[3 * d + 2] * t[3 * i + 2];
+                if (j == 0)
+                    dv += khat[3 * d + 0] * r[3 * i + 0] + khat[3 * d + 1] * r[3 * i + 1]
+                        + khat[3 * d + 2] * r[3 * i + 2];
+                dr[(3 * (size_t)N) * j + 3 * i + d] = (dv + (D / kT) * dfs) * dt;
+            }
+        }
+        free(F);
+    }
+    const int64_t fl = ora_em_step(ch, dt, s_min, r, xi);
+    for (size_t k = 0; k < 3 * (size_t)N * 3; ++k) tr[k] += dr[k];
+    free(dr);
+    return fl;
+}
+
+/* Tension f = c |Q| of spring i and its tangent for (dQ, dH, db). */
+static double ora_tension_tangent(const ora_chain* ch, double s_min, const double Q[3],
+                                  const double dQ[3], double dH, double db)
+{
+    double c, dcq, dcH, dcb;
+    ora_spring_partials(ch, s_min, Q, &c, &dcq, &dcH, &dcb);
+    const double q = sqrt(Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2]);
+    if (q == 0.0) return 0.0;
+    const double qdq = Q[0] * dQ[0] + Q[1] * dQ[1] + Q[2] * dQ[2];
+    const double dc = dcq * 2.0 * qdq + dcH * dH + dcb * db;
+    return dc * q + c * qdq / q;
+}
+
+/* RSF profiles and their tangents d RSF[w][m] / d theta_j, written to
+ * drsf[j][w][M] (j = 0 rate, 1 b, 2 H), for the same run as ora_run
+ * (criteria are not evaluated). pos is advanced in place. */
+int ora_rsf_tangent(const ora_problem* p, int64_t n_steps, double* pos, double* rsf,
+                    double* drsf, int n_threads)
+{
+    const int C = p->n_chains;
+    const int S = p->window_steps;
+    if (C <= 0 || S <= 0 || n_steps < 0) return 1;
+    int64_t* bead_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
+    int64_t* spr_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
+    bead_off[0] = spr_off[0] = 0;
+    for (int c = 0; c < C; ++c) {
+        bead_off[c + 1] = bead_off[c] + p->chains[c].n_beads;
+        spr_off[c + 1] = spr_off[c] + p->chains[c].n_beads - 1;
+    }
+    const int64_t M = spr_off[C];
+    const int64_t W = n_steps / S;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#else
+    (void)n_threads;
+#endif
+    for (int c = 0; c < C; ++c) {
+        const ora_chain* ch = &p->chains[c];
+        const int N = ch->n_beads, R = ch->n_replicas;
+        const uint32_t cid = p->chain_ids ? (uint32_t)p->chain_ids[c] : (uint32_t)c;
+        const size_t sz = 3 * (size_t)N;
+        double* par = pos + 3 * bead_off[c];
+        double* tpar = (double*)calloc(3 * sz, sizeof(double));
+        double* rk = (double*)malloc(sizeof(double) * sz);
+        double* tk = (double*)malloc(sizeof(double) * 3 * sz);
+        double* xi = (double*)malloc(sizeof(double) * sz);
+        double* acc = (double*)malloc(sizeof(double) * 4 * (size_t)N);
+        for (int64_t t = 0; t < n_steps; ) {
+            const int64_t w = t / S;
+            const int Sw = (int)((n_steps - t) < S ? (n_steps - t) : S);
+            for (int i = 0; i < 4 * N; ++i) acc[i] = 0.0;
+            for (int k = 1; k <= R; ++k) {
+                memcpy(rk, par, sizeof(double) * sz);
+                memcpy(tk, tpar, sizeof(double) * 3 * sz);
+                const uint32_t slot = p->identical_noise ? 0u : (uint32_t)k;
+                for (int s = 0; s < Sw; ++s) {
+                    for (int i = 0; i < N; ++i)
+                        ora_normals3(p->seed, (uint32_t)i, slot, ORA_STREAM_BD,
+                                     (uint32_t)(t + s), cid, &xi[3 * i]);
+                    ora_em_step_tangent(ch, p->dt, p->s_min, rk, tk, xi);
+                }
+                if (Sw == S) {
+                    for (int i = 0; i + 1 < N; ++i) {
+                        double Q[3];
+                        for (int d = 0; d < 3; ++d) Q[d] = rk[3 * (i + 1) + d] - rk[3 * i + d];
+                        double F[3], f;
+                        ora_spring_force(ch->spring, ch->H, ch->b, p->s_min, Q, F, &f);
+                        acc[i] += f;
+                        for (int j = 0; j < 3; ++j) {
+                            double dQ[3];
+                            const double* tj = tk + sz * j;
+                            for (int d = 0; d < 3; ++d) dQ[d] = tj[3 * (i + 1) + d] - tj[3 * i + d];
+                            acc[(size_t)N * (j + 1) + i] += ora_tension_tangent(
+                                ch, p->s_min, Q, dQ, j == 2 ? 1.0 : 0.0, j == 1 ? 1.0 : 0.0);
+                        }
+                    }
+                }
+            }
+            for (int s = 0; s < Sw; ++s) {
+                for (int i = 0; i < N; ++i)
+                    ora_normals3(p->seed, (uint32_t)i, 0u, ORA_STREAM_BD, (uint32_t)(t + s), cid,
+                                 &xi[3 * i]);
+                ora_em_step_tangent(ch, p->dt, p->s_min, par, tpar, xi);
+            }
+            if (Sw == S) {
+                for (int i = 0; i + 1 < N; ++i) {
+                    const int64_t m = spr_off[c] + i;
+                    if (rsf) rsf[w * M + m] = acc[i] / R;
+                    for (int j = 0; j < 3; ++j)
+                        drsf[((int64_t)j * W + w) * M + m] = acc[(size_t)N * (j + 1) + i] / R;
+                }
+            }
+            t += Sw;
+        }
+        free(tpar); free(rk); free(tk); free(xi); free(acc);
+    }
+    free(bead_off); free(spr_off);
+    return 0;
+}
+
 int ora_max_threads(void)
 {
 #ifdef _OPENMP

@@ -77,6 +77,12 @@ void ora_criteria_update(int q, int thr_on, int bell_on, const ora_chain* ch, do
 void ora_philox_many(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out);
 void ora_normals3_many(uint64_t seed, int64_t n, const uint32_t* ctr, double* xi);
 
+/* RSF profiles rsf[W][M] (may be NULL) and their pathwise derivatives with
+ * frozen noise drsf[3][W][M] with respect to (rate, b, H) of each chain's own
+ * parameters, W = n_steps / window_steps. pos is advanced in place. */
+int ora_rsf_tangent(const ora_problem* p, int64_t n_steps, double* pos, double* rsf,
+                    double* drsf, int n_threads);
+
 int ora_max_threads(void);
 
 #ifdef __cplusplus

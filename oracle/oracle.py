@@ -82,6 +82,8 @@ def lib():
         _lib.ora_philox_many.argtypes = [ctypes.c_int64, u32p, u32p, u32p]
         _lib.ora_normals3_many.argtypes = [ctypes.c_uint64, ctypes.c_int64, u32p, f64p]
         _lib.ora_max_threads.restype = ctypes.c_int
+        _lib.ora_rsf_tangent.argtypes = [P(_Problem), ctypes.c_int64, f64p, f64p, f64p, ctypes.c_int]
+        _lib.ora_rsf_tangent.restype = ctypes.c_int
     return _lib
 
 
@@ -240,6 +242,32 @@ def run(chains, dt: float, window_steps: int, n_steps: int, seed: int, pos0: np.
         raise ValueError("oracle rejected the problem")
     return dict(pos=pos, rep=rep, rsf=rsf, tsf=tsf, lam=lam, first_thr=ft, first_bell=fb,
                 exp1=e1, overext=over)
+
+
+def rsf_tangent(chains, dt: float, window_steps: int, n_steps: int, seed: int, pos0: np.ndarray,
+                identical_noise: bool = False, s_min: float = S_MIN_DEFAULT, n_threads: int = 1,
+                chain_ids: Optional[Sequence[int]] = None):
+    """RSF [W][M] and its pathwise derivative (frozen noise) [3][W][M] with
+    respect to each chain's (rate, b, H)."""
+    C = len(chains)
+    cs = (_Chain * C)(*[_chain_struct(c) for c in chains])
+    ids = None if chain_ids is None else np.ascontiguousarray(chain_ids, dtype=np.int32)
+    prob = _Problem(C, int(window_steps), cs, float(dt), int(seed), int(bool(identical_noise)),
+                    0, 0, float(s_min),
+                    _p(ids, ctypes.c_int32) if ids is not None
+                    else ctypes.POINTER(ctypes.c_int32)())
+    n_beads = sum(c.n_beads for c in chains)
+    M = sum(c.n_beads - 1 for c in chains)
+    W = n_steps // window_steps
+    pos = np.ascontiguousarray(pos0, dtype=np.float64).copy().reshape(n_beads, 3)
+    rsf = np.zeros((W, M))
+    drsf = np.zeros((3, W, M))
+    rc = lib().ora_rsf_tangent(ctypes.byref(prob), int(n_steps), _p(pos, ctypes.c_double),
+                               _p(rsf, ctypes.c_double), _p(drsf, ctypes.c_double),
+                               int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle rejected the problem")
+    return rsf, drsf
 
 
 def com_frame(pos: np.ndarray, n_beads: Sequence[int]) -> np.ndarray:
