@@ -101,6 +101,9 @@ typedef struct {
     int32_t lanes_hint;           /* 0: planner's choice; else springs per lane (tile) */
     int32_t layout_hint;          /* 0: planner's choice; 1: one replica per lane;
                                      2: two replicas per lane (float32 only) */
+    int32_t checkpoint_steps;     /* 0: no adjoint; else K, a multiple of window_steps:
+                                     bd_step keeps the parent conformation every K
+                                     steps so that bd_adjoint can recompute the run */
 } bd_config;
 
 /* A first event of one spring under one criterion. */
@@ -214,6 +217,37 @@ bd_status bd_get_plan(bd_ctx* ctx, int32_t* variant, int32_t* groups, double* co
  * arrays of 2; either may be NULL. */
 bd_status bd_enable_timing(bd_ctx* ctx, int32_t enable);
 bd_status bd_kernel_times(bd_ctx* ctx, double* ms, int64_t* launches);
+
+/* Adjoint of the replica-averaged force (Sec. II) and of the Bell survival on
+ * it (Sec. III): gradients with respect to each chain's strain rate, FENE b
+ * and spring constant H, by reverse-mode differentiation of the discrete
+ * Eq. 1 map with the noise held fixed (pathwise derivatives; the gradient of
+ * the run that bd_step produced, with the same Philox draws).
+ *
+ * Objective: L = sum_{w,m} grad_rsf[w][m] RSF_w[m]
+ *              + sum_c grad_log_surv[c] log S_c,
+ * log S_c = -sum_w sum_{m of c} k0 exp(RSF_w[m] dx) (window_steps dt), the
+ * Bell log-survival of chain c under the RSF criterion (whatever bell_mask
+ * is). The sums run over the windows completed since the origin - the
+ * step of bd_create or of the last bd_set_positions, whose conformation is
+ * held fixed - up to the current step; earlier rows of grad_rsf are ignored.
+ *   grad_rsf       float64 [windows_done][M] (rows by window index, as
+ *                  bd_replica_average numbers them), or NULL;
+ *   grad_log_surv  float64 [n_chains], or NULL;
+ *   grad_params    float64 [n_chains][3] out: dL/d(rate, b, H); b enters
+ *                  through H/b only for FENE springs (0 for Hooke).
+ * Host or device arrays. Needs cfg.checkpoint_steps = K > 0 (BD_E_STATE
+ * otherwise). Recomputes the parent from its checkpoints K steps at a time
+ * and each window's replicas from the recomputed parent (bitwise the forward
+ * trajectories), then runs the adjoint recursions backwards: replicas
+ * seeded at each window end, their summed sensitivity injected into the
+ * parent's adjoint at the window start. The parameter gradients accumulate
+ * in the integration precision over blocks of 16 steps and in float64
+ * across blocks, lanes and warps. Work buffers (about (K + 1) M and
+ * min(K / window_steps, fit) (window_steps + 1) x all-slot bonds states) are
+ * allocated on the first call and kept. Synchronises the stream. */
+bd_status bd_adjoint(bd_ctx* ctx, const double* grad_rsf, const double* grad_log_surv,
+                     double* grad_params);
 
 /* Diagnostic: the three standard normals the integrator draws for each of n
  * counters ctr [n][4] (word 1 = slot | stream << 24) under key `seed`, in the

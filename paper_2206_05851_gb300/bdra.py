@@ -47,7 +47,8 @@ class bd_config(ctypes.Structure):
                 ("flags", ctypes.c_int32), ("thr_mask", ctypes.c_int32),
                 ("bell_mask", ctypes.c_int32), ("max_windows", ctypes.c_int64),
                 ("s_min", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("lanes_hint", ctypes.c_int32), ("layout_hint", ctypes.c_int32)]
+                ("lanes_hint", ctypes.c_int32), ("layout_hint", ctypes.c_int32),
+                ("checkpoint_steps", ctypes.c_int32)]
 
 
 class bd_event(ctypes.Structure):
@@ -96,6 +97,7 @@ def load() -> ctypes.CDLL:
         "bd_get_plan": ([vp, vp, vp, vp], st),
         "bd_enable_timing": ([vp, ctypes.c_int32], st),
         "bd_kernel_times": ([vp, P(ctypes.c_double), P(ctypes.c_int64)], st),
+        "bd_adjoint": ([vp, vp, vp, vp], st),
         "bd_philox_normals": ([ctypes.c_uint64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp], st),
         "bd_compact_events_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.c_int32, vp,
                                        ctypes.c_int64, vp, vp], st),
@@ -147,7 +149,8 @@ def _need(a, nbytes: int, what: str) -> int:
 def make_config(chains: Sequence, dt: float, window_steps: int, seed: int, precision: int,
                 max_windows: int, thr_mask: int = 0, bell_mask: int = 0, flags: int = 0,
                 s_min: float = 1e-3, stream: Optional[int] = None,
-                lanes_hint: int = 0, layout_hint: int = 0) -> Tuple[bd_config, ctypes.Array]:
+                lanes_hint: int = 0, layout_hint: int = 0,
+                checkpoint_steps: int = 0) -> Tuple[bd_config, ctypes.Array]:
     """Build a bd_config (and the chain array it points to) from chain records
     with the fields of bd_chain_desc."""
     arr = (bd_chain_desc * len(chains))(*[
@@ -156,7 +159,7 @@ def make_config(chains: Sequence, dt: float, window_steps: int, seed: int, preci
                       float(c.dx)) for c in chains])
     cfg = bd_config(len(chains), int(window_steps), arr, float(dt), int(seed), int(precision),
                     int(flags), int(thr_mask), int(bell_mask), int(max_windows), float(s_min),
-                    stream, int(lanes_hint), int(layout_hint))
+                    stream, int(lanes_hint), int(layout_hint), int(checkpoint_steps))
     return cfg, arr
 
 
@@ -251,6 +254,19 @@ def bd_kernel_times(ctx: int):
     return (ms[0], ms[1]), (n[0], n[1])
 
 
+def bd_adjoint(ctx: int, n_chains: int, M: int, windows: int, grad_rsf=None,
+               grad_log_surv=None, out=None):
+    """dL/d(rate, b, H) per chain, [n_chains][3] float64, for
+    L = sum grad_rsf * RSF + sum grad_log_surv * log S (RSF-criterion Bell
+    log-survival). grad_rsf [windows][M], grad_log_surv [n_chains]: host or
+    device arrays, or None."""
+    out = np.zeros((n_chains, 3)) if out is None else out
+    g = _need(grad_rsf, 8 * windows * M, "grad_rsf") if grad_rsf is not None else None
+    l = _need(grad_log_surv, 8 * n_chains, "grad_log_surv") if grad_log_surv is not None else None
+    _check(load().bd_adjoint(ctx, g, l, _need(out, 24 * n_chains, "grad_params")), ctx)
+    return out
+
+
 NOALLOC_MAX_SPRINGS = 1 << 20
 
 
@@ -282,11 +298,11 @@ class Context:
                  init_pos, precision: int = BD_PREC_FP32, max_windows: int = 1024,
                  thr_mask: int = 0, bell_mask: int = 0, flags: int = 0,
                  s_min: float = 1e-3, stream: Optional[int] = None, lanes_hint: int = 0,
-                 layout_hint: int = 0):
+                 layout_hint: int = 0, checkpoint_steps: int = 0):
         self.chains = list(chains)
         self.cfg, self._arr = make_config(self.chains, dt, window_steps, seed, precision,
                                           max_windows, thr_mask, bell_mask, flags, s_min,
-                                          stream, lanes_hint, layout_hint)
+                                          stream, lanes_hint, layout_hint, checkpoint_steps)
         self.ptr = bd_create(self.cfg, init_pos)
         self.M = sum(c.n_beads - 1 for c in self.chains)
         self.n_beads = sum(c.n_beads for c in self.chains)
@@ -343,6 +359,13 @@ class Context:
         fb = np.zeros((3, self.M), dtype=np.int64)
         bd_get_kinetics(self.ptr, haz, ft, fb)
         return haz, ft, fb
+
+    def adjoint(self, grad_rsf=None, grad_log_surv=None, out=None):
+        """Gradient [n_chains][3] of sum grad_rsf * RSF + sum grad_log_surv *
+        log S with respect to (rate, b, H); see bd_adjoint."""
+        windows = self.info().windows_done
+        return bd_adjoint(self.ptr, len(self.chains), self.M, windows, grad_rsf,
+                          grad_log_surv, out)
 
     def events(self, capacity: int = 1 << 16):
         out = np.zeros(capacity, dtype=EVENT_DTYPE)

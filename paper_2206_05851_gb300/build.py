@@ -1,9 +1,10 @@
 """Builds the CUDA library libbdra.so in-tree for sm_103a.
 
-Four translation units compile in parallel: the float32 and float64
-instantiations of the parent / replica kernels (with -fmad=false, so every
-fused multiply-add is the explicit one written in the source), the support
-kernels and the C ABI. Only nvcc is needed; no CMake.
+The translation units compile in parallel: the float32 and float64
+instantiations of the parent / replica kernels and of the adjoint kernels
+(with -fmad=false, so every fused multiply-add is the explicit one written
+in the source), the support kernels, the C ABI and the allocation-free
+event compaction. Only nvcc is needed; no CMake.
 """
 from __future__ import annotations
 
@@ -19,6 +20,7 @@ LIB = os.path.join(PKG, "libbdra.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 UNITS = [("bd_window_f32.cu", ["-fmad=false"]), ("bd_window_f64.cu", ["-fmad=false"]),
+         ("bd_adjoint_f32.cu", ["-fmad=false"]), ("bd_adjoint_f64.cu", ["-fmad=false"]),
          ("bd_support.cu", []), ("bd_api.cu", []), ("bd_noalloc.cu", [])]
 
 

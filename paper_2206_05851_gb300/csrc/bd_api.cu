@@ -28,6 +28,10 @@ struct ParClass {      // one parent-kernel launch: the parent warps of one tile
     int L, threads, grid;
     int warp_begin, warp_count;
 };
+struct AdjClass {      // one adjoint replica-window launch: the work items of one tile
+    int L;
+    int item_begin, item_count;
+};
 
 }  // namespace
 
@@ -86,6 +90,26 @@ struct bd_ctx {
     bool timing = false;
     double timed_ms[2] = {0.0, 0.0};   // accumulated parent / replica time
     int64_t timed_n[2] = {0, 0};
+    // adjoint (cfg.checkpoint_steps > 0): parent checkpoints every K steps
+    // from `origin` (the step of bd_create / bd_set_positions), the adjoint
+    // plan, and work buffers allocated by the first bd_adjoint
+    int64_t origin = 0;
+    void* d_ckpt = nullptr;
+    int64_t n_ckpt = 0;
+    std::vector<AdjChain> h_adj;
+    std::vector<ItemDev> h_adj_items;
+    std::vector<AdjClass> adj_classes;
+    int64_t adj_stride = 0, rep_batch = 0;
+    AdjChain* d_adj = nullptr;
+    ItemDev* d_adj_items = nullptr;
+    void* d_segbuf = nullptr;
+    void* d_repbuf = nullptr;
+    void* d_lamP = nullptr;
+    double* d_mu = nullptr;
+    double* d_gls = nullptr;
+    double* d_grad = nullptr;
+    double* d_G = nullptr;
+    size_t G_bytes = 0;
 };
 
 namespace {
@@ -241,6 +265,8 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
     if ((cfg->thr_mask & ~7) || (cfg->bell_mask & ~7))
         return fail(ctx, BD_E_INVALID, "criterion masks use bits 0..2 only");
     if (cfg->flags & ~BD_FLAG_IDENTICAL_NOISE) return fail(ctx, BD_E_INVALID, "unknown flags");
+    if (cfg->checkpoint_steps < 0 || (cfg->checkpoint_steps > 0 && cfg->checkpoint_steps % cfg->window_steps))
+        return fail(ctx, BD_E_INVALID, "checkpoint_steps must be 0 or a positive multiple of window_steps");
     if (cfg->layout_hint < 0 || cfg->layout_hint > 2)
         return fail(ctx, BD_E_INVALID, "layout_hint must be 0, 1 or 2");
     if (cfg->layout_hint == 2 && cfg->precision != BD_PREC_FP32)
@@ -736,6 +762,124 @@ bd_status replan(bd_ctx* ctx)
     return build_graph(ctx);
 }
 
+
+// ---------------------------------------------------------------------------
+// Adjoint plan: per chain the smallest replica tile of kAdjTiles that fits a
+// replica in one warp, its replicas split into warp items of up to 32 / G;
+// checkpoint storage for every K steps of max_windows windows.
+// ---------------------------------------------------------------------------
+bd_status adj_plan(bd_ctx* ctx)
+{
+    const bd_config& cfg = ctx->cfg;
+    const int C = cfg.n_chains;
+    ctx->h_adj.assign(C, AdjChain{});
+    std::vector<std::pair<int, ItemDev>> items;
+    int64_t part = 0;
+    for (int c = 0; c < C; ++c) {
+        const bd_chain_desc& d = ctx->chains[c];
+        int L = 0;
+        for (int t = 0; t < kNumAdjTiles && !L; ++t)
+            if ((d.n_beads + kAdjTiles[t] - 1) / kAdjTiles[t] <= 32) L = kAdjTiles[t];
+        if (!L) return fail(ctx, BD_E_INVALID, "chain %d: no adjoint tile fits N=%d", c, d.n_beads);
+        const int G = (d.n_beads + L - 1) / L, P = 32 / G;
+        const int groups = (d.n_replicas + P - 1) / P;
+        AdjChain& a = ctx->h_adj[c];
+        a.part_off = part;
+        a.n_groups = groups;
+        a.pad = 0;
+        a.khat[0] = a.khat[1] = a.khat[2] = a.khat[3] = 0.0;
+        switch (d.flow) {
+        case BD_FLOW_SHEAR: a.khat[3] = 1.0; break;
+        case BD_FLOW_UNIAXIAL: a.khat[0] = 1.0; a.khat[1] = -0.5; a.khat[2] = -0.5; break;
+        case BD_FLOW_PLANAR: a.khat[0] = 1.0; a.khat[1] = -1.0; break;
+        default: break;
+        }
+        int begin = 0;
+        for (int g = 0; g < groups; ++g) {
+            const int cnt = d.n_replicas / groups + (g < d.n_replicas % groups ? 1 : 0);
+            items.push_back({L, ItemDev{c, g, begin, cnt, L, 0}});
+            begin += cnt;
+        }
+        part += (int64_t)groups * (d.n_beads - 1);
+    }
+    ctx->adj_stride = part;
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<int, ItemDev>& x, const std::pair<int, ItemDev>& y) { return x.first < y.first; });
+    ctx->h_adj_items.clear();
+    ctx->adj_classes.clear();
+    for (size_t k = 0; k < items.size(); ++k) {
+        if (ctx->adj_classes.empty() || ctx->adj_classes.back().L != items[k].first)
+            ctx->adj_classes.push_back(AdjClass{items[k].first, (int)k, 0});
+        ctx->adj_classes.back().item_count++;
+        ctx->h_adj_items.push_back(items[k].second);
+    }
+    bd_status s;
+    if ((s = upload(ctx, &ctx->d_adj, ctx->h_adj)) != BD_OK) return s;
+    if ((s = upload(ctx, &ctx->d_adj_items, ctx->h_adj_items)) != BD_OK) return s;
+    ctx->n_ckpt = cfg.max_windows * (int64_t)cfg.window_steps / cfg.checkpoint_steps + 1;
+    return dalloc(ctx, &ctx->d_ckpt, ctx->tsize * 3 * (size_t)ctx->M * (size_t)ctx->n_ckpt);
+}
+
+// Work buffers of bd_adjoint: a K-row parent segment, the parent adjoint,
+// and replica-window batches sized to about 4 GiB.
+bd_status adj_buffers(bd_ctx* ctx)
+{
+    if (ctx->d_segbuf) return BD_OK;
+    const int64_t K = ctx->cfg.checkpoint_steps, S = ctx->cfg.window_steps, M = ctx->M;
+    const size_t per_window = ctx->tsize * 3 * (size_t)ctx->state_bonds * (size_t)(S + 1) +
+                              sizeof(double) * 3 * (size_t)ctx->adj_stride;
+    const int64_t budget = 4ll << 30;
+    ctx->rep_batch = std::max<int64_t>(1, std::min<int64_t>({K / S, 65535, budget / (int64_t)per_window}));
+    bd_status s;
+    if ((s = dalloc(ctx, &ctx->d_segbuf, ctx->tsize * 3 * (size_t)M * (size_t)K)) != BD_OK) return s;
+    if ((s = dalloc(ctx, &ctx->d_lamP, ctx->tsize * 3 * (size_t)M)) != BD_OK) return s;
+    if ((s = dalloc(ctx, &ctx->d_repbuf, ctx->tsize * 3 * (size_t)ctx->state_bonds * (size_t)(S + 1) *
+                                             (size_t)ctx->rep_batch)) != BD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&ctx->d_mu, sizeof(double) * 3 * (size_t)ctx->adj_stride *
+                                                 (size_t)ctx->rep_batch)) != BD_OK) return s;
+    if ((s = dalloc(ctx, (void**)&ctx->d_gls, sizeof(double) * (size_t)ctx->cfg.n_chains)) != BD_OK) return s;
+    return dalloc(ctx, (void**)&ctx->d_grad, sizeof(double) * 3 * (size_t)ctx->cfg.n_chains);
+}
+
+// Keeps the parent checkpoints of the windows [w_first, w_end) whose
+// snapshots the last chunk wrote (rows w - w_first of the snapshot buffer).
+bd_status keep_checkpoints(bd_ctx* ctx, int64_t w_first, int64_t w_end)
+{
+    const int64_t K = ctx->cfg.checkpoint_steps, S = ctx->cfg.window_steps;
+    const size_t row = ctx->tsize * 3 * (size_t)ctx->M;
+    for (int64_t w = w_first; w < w_end; ++w) {
+        const int64_t t = w * S - ctx->origin;
+        if (t < 0 || t % K) continue;
+        const int64_t j = t / K;
+        if (j >= ctx->n_ckpt) continue;
+        BD_CUDA(ctx, cudaMemcpyAsync((char*)ctx->d_ckpt + j * row, (const char*)ctx->d_snap + (w - w_first) * row,
+                                     row, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return BD_OK;
+}
+
+bd_status adj_launch(bd_ctx* ctx, int kind, int L, dim3 grid, AdjParams* a)
+{
+    const void* fn = ctx->f64 ? adj_func_f64(kind, L) : adj_func_f32(kind, L);
+    if (!fn) return fail(ctx, BD_E_INVALID, "no adjoint kernel %d for tile %d", kind, L);
+    void* args[1] = {a};
+    BD_CUDA(ctx, cudaLaunchKernel(fn, grid, dim3(kAdjThreads), args, 0, ctx->stream));
+    ++ctx->launches;
+    return BD_OK;
+}
+
+// Parent kernels of the adjoint over every parent tile.
+bd_status adj_parents(bd_ctx* ctx, int kind, AdjParams a)
+{
+    for (const ParClass& pc : ctx->par_classes) {
+        a.sp.parent_warps = ctx->d_parent_warps + pc.warp_begin;
+        a.sp.n_parent_warps = pc.warp_count;
+        const int per_cta = kAdjThreads / 32;
+        bd_status s = adj_launch(ctx, kind, pc.L, dim3((pc.warp_count + per_cta - 1) / per_cta), &a);
+        if (s != BD_OK) return s;
+    }
+    return BD_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -817,6 +961,7 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
         BD_TRY(dalloc(ctx, (void**)&ctx->d_evt_scratch, sizeof(int64_t) * (size_t)(event_blocks(M) + 1)));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_queue, sizeof(int32_t) * ctx->var_classes.size()));
         BD_TRY(build_graph(ctx));
+        if (cfg->checkpoint_steps > 0) BD_TRY(adj_plan(ctx));
         {
             cudaError_t e = run_exp1(ctx->d_chains, ctx->d_spring_chain, M, ctx->rk0[0], ctx->rk1[0],
                                      ctx->d_exp1, ctx->stream);
@@ -883,6 +1028,10 @@ bd_status bd_step(bd_ctx* ctx, int64_t n_steps)
         }
         BD_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
         ctx->launches += (int64_t)(ctx->par_nodes.size() + ctx->rep_nodes.size());
+        if (ctx->cfg.checkpoint_steps > 0) {
+            bd_status s = keep_checkpoints(ctx, w_first, (chunk_end + S - 1) / S);
+            if (s != BD_OK) return s;
+        }
         if (ctx->timing) {
             // the graph's own events: read them before the next launch re-records them
             float x = 0.0f, y = 0.0f;
@@ -1027,6 +1176,7 @@ bd_status bd_set_positions(bd_ctx* ctx, const double* pos, int64_t step)
     s = load_positions(ctx, pos);
     if (s != BD_OK) return s;
     ctx->step = step;
+    ctx->origin = step;
     ctx->windows_detected = step / ctx->cfg.window_steps;
     return BD_OK;
 }
@@ -1111,6 +1261,101 @@ bd_status bd_get_plan(bd_ctx* ctx, int32_t* variant, int32_t* groups, double* co
         const int nv = ctx->f64 ? kNumVariantsF64 : kNumVariantsF32;
         for (int t = 0; t < nv; ++t) cost_ns[t] = ctx->var_cost[vars[t]];
     }
+    return BD_OK;
+}
+
+bd_status bd_adjoint(bd_ctx* ctx, const double* grad_rsf, const double* grad_log_surv,
+                     double* grad_params)
+{
+    if (!ctx) return BD_E_INVALID;
+    if (!grad_params) return fail(ctx, BD_E_INVALID, "grad_params is NULL");
+    const int64_t K = ctx->cfg.checkpoint_steps, S = ctx->cfg.window_steps, M = ctx->M;
+    const int C = ctx->cfg.n_chains;
+    if (K <= 0) return fail(ctx, BD_E_STATE, "bd_adjoint needs checkpoint_steps > 0 in the configuration");
+    bd_status s = adj_buffers(ctx);
+    if (s != BD_OK) return s;
+    const int64_t w_lo = ctx->origin / S, w_hi = ctx->step / S;
+    BD_CUDA(ctx, cudaMemsetAsync(ctx->d_grad, 0, sizeof(double) * 3 * (size_t)C, ctx->stream));
+    if (w_hi > w_lo && (grad_rsf || grad_log_surv)) {
+        const int64_t n_w = w_hi - w_lo;
+        const size_t gb = sizeof(double) * (size_t)n_w * (size_t)M;
+        if (ctx->G_bytes < gb) {
+            dfree(ctx, ctx->d_G, ctx->G_bytes);
+            ctx->d_G = nullptr;
+            ctx->G_bytes = 0;
+            if ((s = dalloc(ctx, (void**)&ctx->d_G, gb)) != BD_OK) return s;
+            ctx->G_bytes = gb;
+        }
+        const double* grs = nullptr;
+        if (grad_rsf) {
+            grs = grad_rsf + w_lo * M;
+            if (!is_device_ptr(grad_rsf)) {
+                BD_CUDA(ctx, cudaMemcpyAsync(ctx->d_G, grs, gb, cudaMemcpyHostToDevice, ctx->stream));
+                grs = ctx->d_G;          // the seed kernel updates it in place
+            }
+        }
+        const double* gls = grad_log_surv;
+        if (gls && !is_device_ptr(gls)) {
+            BD_CUDA(ctx, cudaMemcpyAsync(ctx->d_gls, gls, sizeof(double) * (size_t)C, cudaMemcpyHostToDevice,
+                                         ctx->stream));
+            gls = ctx->d_gls;
+        }
+        ++ctx->launches;
+        BD_CUDA(ctx, run_adj_seed(ctx->d_chains, ctx->d_spring_chain, M, ctx->d_part, ctx->part_stride, w_lo,
+                                  n_w, grs, gls, (int)S, ctx->cfg.dt, ctx->d_G, ctx->stream));
+        BD_CUDA(ctx, cudaMemsetAsync(ctx->d_lamP, 0, ctx->tsize * 3 * (size_t)M, ctx->stream));
+
+        AdjParams a;
+        std::memset(&a, 0, sizeof(a));
+        a.sp = base_params(ctx);
+        a.adj = ctx->d_adj;
+        a.ckpt = ctx->d_ckpt;
+        a.segbuf = ctx->d_segbuf;
+        a.repbuf = ctx->d_repbuf;
+        a.state_bonds = ctx->state_bonds;
+        a.lamP = ctx->d_lamP;
+        a.G = ctx->d_G;
+        a.mu = ctx->d_mu;
+        a.mu_stride = ctx->adj_stride;
+        a.w_lo = w_lo;
+        a.w_hi = w_hi;
+        a.grad = ctx->d_grad;
+        const int64_t t_max = (w_hi - 1) * S;           // start of the last window
+        const int64_t j_max = (t_max - ctx->origin) / K;
+        const int per_cta = kAdjThreads / 32;
+        for (int64_t j = j_max; j >= 0; --j) {
+            // parent states of steps [seg_t0, seg_t0 + n) from checkpoint j
+            const int64_t seg_t0 = ctx->origin + j * K;
+            const int64_t n = (j == j_max) ? t_max - seg_t0 + 1 : K;
+            a.seg_t0 = seg_t0;
+            a.ckpt_index = j;
+            a.t0 = seg_t0;
+            a.n_steps = (int32_t)(n - 1);
+            if ((s = adj_parents(ctx, ADJ_PARENT_RECOMPUTE, a)) != BD_OK) return s;
+            // windows starting in the segment, in batches from the top down;
+            // after each batch the parent sweeps back over the batch's steps
+            const int64_t wa = seg_t0 / S, wb = std::min(w_hi, (seg_t0 + n - 1) / S + 1);
+            for (int64_t b1 = wb; b1 > wa;) {
+                const int64_t b0 = std::max(wa, b1 - ctx->rep_batch);
+                a.mu_w0 = b0;
+                a.w_batch0 = b0;
+                for (const AdjClass& ac : ctx->adj_classes) {
+                    a.items = ctx->d_adj_items + ac.item_begin;
+                    a.n_items = ac.item_count;
+                    const dim3 grid((unsigned)((ac.item_count + per_cta - 1) / per_cta), (unsigned)(b1 - b0));
+                    if ((s = adj_launch(ctx, ADJ_REPLICA_WINDOW, ac.L, grid, &a)) != BD_OK) return s;
+                }
+                const int64_t t_lo = b0 * S, t_hi = std::min(b1 * S, seg_t0 + n);
+                a.t0 = t_lo;
+                a.n_steps = (int32_t)(t_hi - t_lo);
+                if ((s = adj_parents(ctx, ADJ_PARENT_BACKWARD, a)) != BD_OK) return s;
+                b1 = b0;
+            }
+        }
+    }
+    s = deliver(ctx, grad_params, ctx->d_grad, sizeof(double) * 3 * (size_t)C, is_device_ptr(grad_params));
+    if (s != BD_OK) return s;
+    BD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return BD_OK;
 }
 

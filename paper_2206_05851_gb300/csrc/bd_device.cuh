@@ -83,6 +83,36 @@ struct StepParams {
     uint32_t rk0[10], rk1[10];
 };
 
+// Adjoint (bd_adjoint.cuh): per chain, for the adjoint only.
+struct AdjChain {
+    int64_t part_off;    // first entry of this chain's group 0 in a mu row
+    int32_t n_groups;    // adjoint replica groups (warp items) of the chain
+    int32_t pad;
+    double khat[4];      // kappa / rate: xx, yy, zz, xz
+};
+
+struct AdjParams {
+    StepParams sp;             // forward parameters: chains, parent warps, keys, dt, S
+    const AdjChain* adj;
+    const ItemDev* items;      // replica work items of this launch (one tile)
+    int32_t n_items;
+    int32_t n_steps;           // parent kernels: steps of this launch
+    int64_t t0;                // parent kernels: first step
+    const void* ckpt;          // T [n_ckpt][M][3] parent every K steps from the origin
+    int64_t ckpt_index;        // checkpoint the parent recompute starts from
+    void* segbuf;              // T [K + 1][M][3] parent states of the segment
+    int64_t seg_t0;            // step of segbuf row 0
+    void* repbuf;              // T [batch][S + 1][state_bonds][3] replica states
+    int64_t state_bonds;
+    int64_t w_batch0;          // replica kernel: window of blockIdx.y = 0
+    void* lamP;                // T [M][3] parent adjoint carried between segments
+    const double* G;           // [w_hi - w_lo][M] dObjective / dRSF, row 0 = window w_lo
+    double* mu;                // [rows][mu_stride][3] window sensitivities
+    int64_t mu_w0, mu_stride;
+    int64_t w_lo, w_hi;        // the objective's windows: w_lo <= w < w_hi
+    double* grad;              // [n_chains][3] dObjective / d(rate, b, H)
+};
+
 enum { CRIT_Q_ISF = 0, CRIT_Q_TSF = 1, CRIT_Q_RSF = 2 };
 enum { STREAM_BD = 0, STREAM_EXP1 = 1 };
 

@@ -31,4 +31,14 @@ int persist_threads_f64();
 cudaError_t persist_blocks_per_sm_f32(int variant, int* n);
 cudaError_t persist_blocks_per_sm_f64(int variant, int* n);
 
+// Adjoint kernels (bd_adjoint.cuh), launched with kAdjThreads threads: the
+// parent kernels exist for every tile of kTiles, the replica-window kernel
+// for the tiles of kAdjTiles.
+enum { ADJ_PARENT_RECOMPUTE = 0, ADJ_REPLICA_WINDOW = 1, ADJ_PARENT_BACKWARD = 2 };
+static const int kAdjTiles[] = {4, 7, 16};
+static const int kNumAdjTiles = 3;
+static const int kAdjThreads = 128;
+const void* adj_func_f32(int kind, int L);
+const void* adj_func_f64(int kind, int L);
+
 }  // namespace bdra

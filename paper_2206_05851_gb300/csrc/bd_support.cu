@@ -150,6 +150,31 @@ __global__ void window_criteria_kernel(const ChainDev* chains, const int32_t* sp
     }
 }
 
+// Seed of the adjoint: dObjective / dRSF for windows w_lo .. w_lo + n_w - 1,
+// G[w - w_lo][m] = grad_rsf[w - w_lo][m] (if given) plus, for the Bell
+// log-survival of the RSF criterion, log S_c = -sum_w sum_i k0 exp(RSF dx) S dt
+// (Sec. III), the term grad_log_surv[c] * (-k0 dx exp(RSF dx) S dt).
+__global__ void adj_seed_kernel(const ChainDev* chains, const int32_t* spring_chain, int64_t M,
+                                const double* part_hist, int64_t part_stride, int64_t w_lo,
+                                int64_t n_w, const double* grad_rsf, const double* grad_log_surv,
+                                int S, double dt, double* G)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_w * M) return;
+    const int64_t r = e / M, m = e - r * M;
+    double g = grad_rsf ? grad_rsf[e] : 0.0;
+    if (grad_log_surv) {
+        const int c = spring_chain[m];
+        const double gl = grad_log_surv[c];
+        if (gl != 0.0) {
+            const ChainDev ch = chains[c];
+            const double f = rsf_of(ch, part_hist, part_stride, w_lo + r, m - ch.spr_off);
+            g -= gl * ch.k0 * ch.dx * exp(f * ch.dx) * ((double)S * dt);
+        }
+    }
+    G[e] = g;
+}
+
 __device__ __forceinline__ int events_of(int64_t m, int64_t M, const int64_t* first_thr,
                                          const int64_t* first_bell)
 {
@@ -343,6 +368,16 @@ cudaError_t run_events(const ChainDev* chains, const int32_t* spring_chain, int6
     event_scan_kernel<<<1, kThreads, 0, st>>>(block_scratch, nb);
     event_write_kernel<<<nb, kThreads, 0, st>>>(chains, spring_chain, M, first_thr, first_bell,
                                                 block_scratch, out, capacity);
+    return cudaGetLastError();
+}
+
+cudaError_t run_adj_seed(const ChainDev* chains, const int32_t* spring_chain, int64_t M,
+                         const double* part_hist, int64_t part_stride, int64_t w_lo, int64_t n_w,
+                         const double* grad_rsf, const double* grad_log_surv, int S, double dt,
+                         double* G, cudaStream_t st)
+{
+    adj_seed_kernel<<<blocks_for(n_w * M), kThreads, 0, st>>>(
+        chains, spring_chain, M, part_hist, part_stride, w_lo, n_w, grad_rsf, grad_log_surv, S, dt, G);
     return cudaGetLastError();
 }
 

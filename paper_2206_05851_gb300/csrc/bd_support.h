@@ -29,6 +29,10 @@ cudaError_t run_events(const ChainDev* chains, const int32_t* spring_chain, int6
                        bd_event* out, int64_t capacity, cudaStream_t st);
 cudaError_t run_log_survival(const ChainDev* chains, int n_chains, int64_t M, const double* lam,
                              double* out, cudaStream_t st);
+cudaError_t run_adj_seed(const ChainDev* chains, const int32_t* spring_chain, int64_t M,
+                         const double* part_hist, int64_t part_stride, int64_t w_lo, int64_t n_w,
+                         const double* grad_rsf, const double* grad_log_surv, int S, double dt,
+                         double* G, cudaStream_t st);
 cudaError_t run_normals(bool f64, int64_t n, const uint32_t* ctr, const StepParams& p, double* out,
                         cudaStream_t st);
 

@@ -87,7 +87,8 @@ def test_bad_chain_rejected_without_device(lib, field, value):
                                 dict(flags=2), dict(lanes_hint=3), dict(lanes_hint=2),
                                 dict(layout_hint=3),
                                 dict(layout_hint=2, precision=bdra.BD_PREC_FP64),
-                                dict(layout_hint=2, lanes_hint=13)])
+                                dict(layout_hint=2, lanes_hint=13),
+                                dict(checkpoint_steps=15), dict(checkpoint_steps=-10)])
 def test_bad_config_rejected_without_device(lib, kw):
     ch = I.Chain(n_beads=100, n_replicas=4, spring=I.SPRING_FENE, b=50.0)
     cfg, _keep = _cfg([ch], **kw)
