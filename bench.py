@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -186,6 +187,54 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def adjoint_line(sptr):
+    """Forward run plus reverse-mode adjoint of the differentiation workload
+    (256 FENE chains, N=200, 32 replicas, 2e4 steps, parent checkpoints every
+    1000 steps, float32 integration): gradients of the mid-chain RSF averaged
+    over the windows plus the Bell log-survival w.r.t. (rate, b, H)."""
+    import numpy as np
+    import torch
+    from paper_2206_05851_gb300 import bdra
+    from paper_2206_05851_gb300 import inputs as I
+
+    wl = I.adjoint_256()
+    pos0 = torch.from_numpy(I.initial_positions(wl)).cuda()
+    S, n = wl.window_steps, wl.n_steps
+    W = n // S
+    offs = I.spring_offsets(wl.chains)
+    G = np.zeros((W, int(offs[-1])))
+    for c, ch in enumerate(wl.chains):
+        G[:, offs[c] + (ch.n_beads - 1) // 2] = 1.0 / W
+    G = torch.from_numpy(G).cuda()
+    gls = torch.ones(len(wl.chains), dtype=torch.float64, device="cuda")
+    grad = torch.empty((len(wl.chains), 3), dtype=torch.float64, device="cuda")
+    ctx = bdra.Context(wl.chains, wl.dt, S, wl.seed, pos0, precision=bdra.BD_PREC_FP32,
+                       max_windows=W, bell_mask=I.CRIT_RSF, stream=sptr,
+                       checkpoint_steps=I.ADJOINT_CHECKPOINT_STEPS)
+    ctx.step(I.ADJOINT_CHECKPOINT_STEPS)            # warm-up; allocates the work buffers
+    bdra.bd_adjoint(ctx.ptr, len(wl.chains), ctx.M, I.ADJOINT_CHECKPOINT_STEPS // S, G, gls, grad)
+    ctx.set_positions(pos0, 0)
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    ctx.step(n)
+    e[1].record(stream)
+    bdra.bd_adjoint(ctx.ptr, len(wl.chains), ctx.M, W, G, gls, grad)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    fwd, adj = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+    info = ctx.info()
+    ctx.close()
+    bead_steps = wl.bead_steps()
+    return {"workload": wl.name, "precision": "FP32 integrate, FP64 reduce",
+            "checkpoint_steps": I.ADJOINT_CHECKPOINT_STEPS, "steps": n,
+            "forward_s": fwd, "adjoint_s": adj, "adjoint_over_forward": adj / fwd,
+            "value": bead_steps / (fwd + adj), "unit": "bead-steps/s (forward + adjoint)",
+            "device_bytes": int(info.device_bytes),
+            "grad_finite": bool(torch.isfinite(grad).all().item())}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -195,7 +244,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2206_05851_gb300 import bdra, build as B
+    from paper_2206_05851_gb300 import bdra, build as B, shard
     from paper_2206_05851_gb300 import inputs as I
 
     rank = int(os.environ.get("RANK", "0"))
@@ -212,8 +261,8 @@ def main():
 
     wl = make_workload(args)
     # ranks own independent chain sets: same shapes, their own seeds (weak scaling)
-    seed = wl.seed + 1000 * rank
-    pos0 = I.initial_positions(wl, seed=wl.init_seed + rank)
+    seed, init_seed = shard.rank_keys(wl.seed, wl.init_seed, rank)
+    pos0 = I.initial_positions(wl, seed=init_seed)
     S = wl.window_steps
     chunk = args.chunk
     total_windows = (args.warmup + args.steps) * chunk // S + 1
@@ -260,12 +309,8 @@ def main():
     launches = ctx.info().kernel_launches - launches0    # our kernels only
     (par_ms, rep_ms), (par_n, rep_n) = bdra.bd_kernel_times(ctx.ptr)
     bdra.bd_enable_timing(ctx.ptr, False)
-    t_max = t_ms
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = bead_steps_chunk * args.steps * world / (t_max / 1e3)
+    t_max = shard.max_over_ranks(t_ms, dist, "cuda")
+    value = shard.whole_job_rate(bead_steps_chunk * args.steps, world, t_max / 1e3)
 
     # roofline of the dominant kernel (replica kernel), measured live
     rep_units = slot_bead_steps_chunk * args.steps
@@ -362,6 +407,8 @@ def main():
                           "h2d_bytes_per_step": int(pos_h.numel() * 8),
                           "d2h_bytes_per_step": int(nev * 24 + ctx.M * 8 + 8),
                           "steps": e2e_steps}
+        if not args.no_adjoint:
+            out["adjoint"] = adjoint_line(sptr)
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(wl, pos0)
     if rank == 0:

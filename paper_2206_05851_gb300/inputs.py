@@ -212,15 +212,16 @@ def bell_16384(n_steps: int = 250_000, n_chains: int = 16384) -> Workload:
 
 
 def adjoint_256(n_steps: int = 20_000, n_chains: int = 256) -> Workload:
-    """256 FENE chains, N=200, b=100, 32 replicas, uniaxial elongation Wi=10,
-    dt=1e-3, window 100, Bell k0=1e-6 and dx F_max = 20 on the replica-averaged
-    force; differentiated with parent checkpoints every 1000 steps."""
+    """256 FENE chains, N=200, b=100, H=1, 32 replicas, uniaxial elongation
+    Wi=5, dt=1e-3, window 100, Bell k0=1e-6 and dx F_max = 20 on the
+    replica-averaged force; differentiated with parent checkpoints every 1000
+    steps."""
     n, b = 200, 100.0
     fmax = fene_fmax(1.0, b)
     chains = [Chain(n_beads=n, n_replicas=32, spring=SPRING_FENE, flow=FLOW_UNIAXIAL, H=1.0,
-                    b=b, rate=rate_from_wi(10.0, n), f_c=0.9 * fmax, k0=1e-6,
+                    b=b, rate=rate_from_wi(5.0, n), f_c=0.9 * fmax, k0=1e-6,
                     dx=20.0 / fmax) for _ in range(n_chains)]
-    return Workload("fene_256x_n200_r32_uniaxial_wi10_adjoint", chains, dt=1e-3,
+    return Workload("fene_256x_n200_r32_uniaxial_wi5_adjoint", chains, dt=1e-3,
                     window_steps=100, n_steps=n_steps, seed=5, thr_mask=0,
                     bell_mask=CRIT_RSF, init_seed=5)
 

@@ -9,9 +9,10 @@ sum_{w,m of c} (G[w][m] - g_c k0 dx exp(dx RSF_w[m]) S dt) dRSF_w[m]/dtheta_c.
 
 Tolerances: FP64 1e-10 relative to the largest gradient of each parameter
 (the two sides differentiate the same discrete map and differ by rounding
-order only). FP32: the integration runs in float32, so the gradient carries
-the float32 trajectory's deviation from the float64 one; the bound 2e-3 of
-the largest gradient is derived in the design notes.
+order only; measured 1e-14). FP32: the integration runs in float32, so the
+gradient carries the float32 trajectory's deviation from the float64 one;
+bound 1e-3 of the largest gradient (measured up to 1.2e-4 on the 256-chain
+workload, 1e-5 on the small cases).
 """
 import dataclasses
 
@@ -134,7 +135,7 @@ def test_fp32_adjoint_matches_oracle_tangent():
     ctx = gpu_forward(chains, DT, S, n, SEED, pos0, F32, K)
     got = ctx.adjoint(G, gls)
     ctx.close()
-    assert_close(got, want, 2e-3, "fp32")
+    assert_close(got, want, 1e-3, "fp32")
 
 
 def test_device_arrays_and_objective_parts():
@@ -250,7 +251,7 @@ def test_autograd_function_backward_is_the_adjoint():
 
 
 def test_adjoint_workload_full_size_sampled_chains():
-    """256 FENE chains, N=200, 32 replicas, 2e4 steps, checkpoints every 1000
+    """256 FENE chains, N=200, 32 replicas, Wi=5, 2e4 steps, checkpoints every 1000
     steps, float32: the mid-chain RSF averaged over the windows plus the
     Bell log-survival; the gradients of two sampled chains against the FP64
     oracle's tangent of those chains (with their own noise streams)."""
@@ -279,4 +280,4 @@ def test_adjoint_workload_full_size_sampled_chains():
     Gs = np.concatenate([G[:, offs[c]:offs[c + 1]] for c in sample], axis=1)
     want = oracle_grad(sub, r, dr, Gs, gls[sample], wl.dt, S_)
     assert so[-1] == Gs.shape[1]
-    assert_close(got[sample], want, 2e-3, "adjoint workload")
+    assert_close(got[sample], want, 1e-3, "adjoint workload")
