@@ -15,26 +15,60 @@
 
 namespace bdra {
 
-struct F2 {
-    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// Which groups of the step's float32 operations issue as packed two-wide
+// instructions (the others issue as two scalar ones; both forms round
+// identically, so the choice never changes a result). A packed operation
+// occupies both halves of the FMA pipe, and the heavy half is also where the
+// Philox 32 x 32 -> 64 multiplies run, so packing saves issue slots at the
+// price of heavy-pipe cycles; the mask sets the balance.
+#ifndef BD_PACK_MASK
+#define BD_PACK_MASK 31
+#endif
+enum { PK_UNIF = 1, PK_BM = 2, PK_SPRING = 4, PK_LAP = 8, PK_UPD = 16 };
+
+template <int GROUP>
+struct F2G {
+    static constexpr bool packed = (BD_PACK_MASK & GROUP) != 0;
+    static __device__ __forceinline__ float2 add(float2 a, float2 b)
+    {
+        if (packed) return __fadd2_rn(a, b);
+        return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+    }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b)
+    {
+        if (packed) return __fmul2_rn(a, b);
+        return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+    }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c)
+    {
+        if (packed) return __ffma2_rn(a, b, c);
+        return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+    }
+    // a - b as fma(b, -1, a): exact product, one rounding
     static __device__ __forceinline__ float2 sub(float2 a, float2 b)
     {
-        return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+        return fma(b, make_float2(-1.0f, -1.0f), a);
     }
+};
+
+struct F2 {
     static __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 };
+using F2U = F2G<PK_UNIF>;
+using F2B = F2G<PK_BM>;
+using F2S = F2G<PK_SPRING>;
+using F2L = F2G<PK_LAP>;
+using F2P = F2G<PK_UPD>;
 
 // Spring coefficient H / s for both halves; floor counts per half.
 __device__ __forceinline__ float2 spring_coef2(float2 qx, float2 qy, float2 qz, float2 H2,
                                                float2 nHinvb2, float smin, int& fla, int& flb)
 {
-    const float2 q2 = F2::fma(qx, qx, F2::fma(qy, qy, F2::mul(qz, qz)));
-    const float2 s = F2::fma(nHinvb2, q2, F2::splat(1.0f));
+    const float2 q2 = F2S::fma(qx, qx, F2S::fma(qy, qy, F2S::mul(qz, qz)));
+    const float2 s = F2S::fma(nHinvb2, q2, F2::splat(1.0f));
     fla += s.x < smin;
     flb += s.y < smin;
-    return F2::mul(H2, make_float2(rcp_approx(fmaxf(s.x, smin)), rcp_approx(fmaxf(s.y, smin))));
+    return F2S::mul(H2, make_float2(rcp_approx(fmaxf(s.x, smin)), rcp_approx(fmaxf(s.y, smin))));
 }
 
 // The three normals of one bead for both replicas (sign-flipped, see
@@ -47,19 +81,19 @@ __device__ __forceinline__ void bead_noise2(uint32_t bead, uint32_t ka, uint32_t
     const uint4 xa = philox4x32_10_rk(make_uint4(bead, ka | w1, step, chain), p.rk0, p.rk1);
     const uint4 xb = philox4x32_10_rk(make_uint4(bead, kb | w1, step, chain), p.rk0, p.rk1);
     const float2 S = F2::splat(FastBM::s32), Hh = F2::splat(FastBM::h32);
-    const float2 u0 = F2::fma(make_float2((float)xa.x, (float)xb.x), S, Hh);
-    const float2 u2 = F2::fma(make_float2((float)xa.z, (float)xb.z), S, Hh);
-    const float2 a0 = F2::mul(F2::splat(FastBM::m2ln2), make_float2(lg2_approx(u0.x), lg2_approx(u0.y)));
-    const float2 a2 = F2::mul(F2::splat(FastBM::m2ln2), make_float2(lg2_approx(u2.x), lg2_approx(u2.y)));
+    const float2 u0 = F2U::fma(make_float2((float)xa.x, (float)xb.x), S, Hh);
+    const float2 u2 = F2U::fma(make_float2((float)xa.z, (float)xb.z), S, Hh);
+    const float2 a0 = F2B::mul(F2::splat(FastBM::m2ln2), make_float2(lg2_approx(u0.x), lg2_approx(u0.y)));
+    const float2 a2 = F2B::mul(F2::splat(FastBM::m2ln2), make_float2(lg2_approx(u2.x), lg2_approx(u2.y)));
     const float2 r0 = make_float2(sqrt_approx(fabsf(a0.x)), sqrt_approx(fabsf(a0.y)));
     const float2 r2 = make_float2(sqrt_approx(fabsf(a2.x)), sqrt_approx(fabsf(a2.y)));
-    const float2 t1 = F2::fma(make_float2(FastBM::angle_bits(xa.y), FastBM::angle_bits(xb.y)),
-                              F2::splat(FastBM::twopi), F2::splat(FastBM::off));
-    const float2 t3 = F2::fma(make_float2(FastBM::angle_bits(xa.w), FastBM::angle_bits(xb.w)),
-                              F2::splat(FastBM::twopi), F2::splat(FastBM::off));
-    z0 = F2::mul(r0, make_float2(cos_approx(t1.x), cos_approx(t1.y)));
-    z1 = F2::mul(r0, make_float2(sin_approx(t1.x), sin_approx(t1.y)));
-    z2 = F2::mul(r2, make_float2(cos_approx(t3.x), cos_approx(t3.y)));
+    const float2 t1 = F2U::fma(make_float2(FastBM::angle_bits(xa.y), FastBM::angle_bits(xb.y)),
+                               F2::splat(FastBM::twopi), F2::splat(FastBM::off));
+    const float2 t3 = F2U::fma(make_float2(FastBM::angle_bits(xa.w), FastBM::angle_bits(xb.w)),
+                               F2::splat(FastBM::twopi), F2::splat(FastBM::off));
+    z0 = F2B::mul(r0, make_float2(cos_approx(t1.x), cos_approx(t1.y)));
+    z1 = F2B::mul(r0, make_float2(sin_approx(t1.x), sin_approx(t1.y)));
+    z2 = F2B::mul(r2, make_float2(cos_approx(t3.x), cos_approx(t3.y)));
 }
 
 __device__ __forceinline__ float2 shfl2(float2 v, int src)
@@ -90,11 +124,11 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
 {
     int fla = 0, flb = 0;
     const float2 c0 = spring_coef2(qx[0], qy[0], qz[0], k.H, k.nHinvb, k.smin, fla, flb);
-    const float2 f0x = F2::mul(c0, qx[0]), f0y = F2::mul(c0, qy[0]), f0z = F2::mul(c0, qz[0]);
+    const float2 f0x = F2S::mul(c0, qx[0]), f0y = F2S::mul(c0, qy[0]), f0z = F2S::mul(c0, qz[0]);
     float2 fLx = f0x, fLy = f0y, fLz = f0z;
     if (L > 1) {
         const float2 cL = spring_coef2(qx[L - 1], qy[L - 1], qz[L - 1], k.H, k.nHinvb, k.smin, fla, flb);
-        fLx = F2::mul(cL, qx[L - 1]); fLy = F2::mul(cL, qy[L - 1]); fLz = F2::mul(cL, qz[L - 1]);
+        fLx = F2S::mul(cL, qx[L - 1]); fLy = F2S::mul(cL, qy[L - 1]); fLz = F2S::mul(cL, qz[L - 1]);
     }
     float2 fmx = shfl2(fLx, lc.src_prev), fmy = shfl2(fLy, lc.src_prev), fmz = shfl2(fLz, lc.src_prev);
     float2 fnx = shfl2(f0x, lc.src_next), fny = shfl2(f0y, lc.src_next), fnz = shfl2(f0z, lc.src_next);
@@ -115,7 +149,7 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
                 fpx = fLx; fpy = fLy; fpz = fLz;
             } else {
                 const float2 c = spring_coef2(qx[j + 1], qy[j + 1], qz[j + 1], k.H, k.nHinvb, k.smin, fla, flb);
-                fpx = F2::mul(c, qx[j + 1]); fpy = F2::mul(c, qy[j + 1]); fpz = F2::mul(c, qz[j + 1]);
+                fpx = F2S::mul(c, qx[j + 1]); fpy = F2S::mul(c, qy[j + 1]); fpz = F2S::mul(c, qz[j + 1]);
             }
             uint32_t bj = (uint32_t)(lc.bead0 + j + 1);
             asm volatile("" : "+r"(bj));     // keep per-bead Philox work inside the step loop
@@ -125,13 +159,13 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
             xnx = hx; xny = hy; xnz = hz;
         }
         if (j < lc.nv) {
-            const float2 lx = F2::fma(m2, fcx, F2::add(fpx, fmx));
-            const float2 ly = F2::fma(m2, fcy, F2::add(fpy, fmy));
-            const float2 lz = F2::fma(m2, fcz, F2::add(fpz, fmz));
+            const float2 lx = F2L::fma(m2, fcx, F2L::add(fpx, fmx));
+            const float2 ly = F2L::fma(m2, fcy, F2L::add(fpy, fmy));
+            const float2 lz = F2L::fma(m2, fcz, F2L::add(fpz, fmz));
             const float2 ox = qx[j], oy = qy[j], oz = qz[j];
-            qx[j] = F2::fma(k.cn, F2::sub(xnx, xcx), F2::fma(k.cd, lx, F2::fma(k.axz, oz, F2::fma(k.axx, ox, ox))));
-            qy[j] = F2::fma(k.cn, F2::sub(xny, xcy), F2::fma(k.cd, ly, F2::fma(k.ayy, oy, oy)));
-            qz[j] = F2::fma(k.cn, F2::sub(xnz, xcz), F2::fma(k.cd, lz, F2::fma(k.azz, oz, oz)));
+            qx[j] = F2P::fma(k.cn, F2P::sub(xnx, xcx), F2P::fma(k.cd, lx, F2P::fma(k.axz, oz, F2P::fma(k.axx, ox, ox))));
+            qy[j] = F2P::fma(k.cn, F2P::sub(xny, xcy), F2P::fma(k.cd, ly, F2P::fma(k.ayy, oy, oy)));
+            qz[j] = F2P::fma(k.cn, F2P::sub(xnz, xcz), F2P::fma(k.cd, lz, F2P::fma(k.azz, oz, oz)));
         }
         fmx = fcx; fmy = fcy; fmz = fcz;
         fcx = fpx; fcy = fpy; fcz = fpz;
