@@ -399,7 +399,7 @@ bd_status plan(bd_ctx* ctx)
     for (size_t k = 0; k < par.size();) {
         const int L = par[k].first.first, G = par[k].first.second, P = 32 / G;
         if (ctx->par_classes.empty() || ctx->par_classes.back().L != L)
-            ctx->par_classes.push_back(ParClass{L, 64, 0, (int)ctx->h_parent_warps.size(), 0});
+            ctx->par_classes.push_back(ParClass{L, kParentThreads, 0, (int)ctx->h_parent_warps.size(), 0});
         size_t e = k;
         while (e < par.size() && par[e].first == par[k].first) ++e;
         for (size_t j = k; j < e; j += P) {
@@ -495,7 +495,7 @@ cudaKernelNodeParams replica_node(const bd_ctx* ctx, size_t k, StepParams* rk, v
     kp.func = const_cast<void*>(ctx->f64 ? persist_func_f64(vc.variant) : persist_func_f32(vc.variant));
     kp.gridDim = dim3(vc.grid);
     kp.blockDim = dim3(vc.threads);
-    kp.sharedMemBytes = 0;
+    kp.sharedMemBytes = (unsigned)(ctx->f64 ? persist_smem_f64(vc.variant) : persist_smem_f32(vc.variant));
     kp.kernelParams = args;
     return kp;
 }
@@ -714,7 +714,8 @@ bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost
         for (int rep = 0; rep < 2; ++rep) {      // first launch warms up
             BD_PROBE(cudaMemsetAsync(tqueue, 0, sizeof(int32_t), ctx->stream));
             BD_PROBE(cudaEventRecord(e0, ctx->stream));
-            BD_PROBE(cudaLaunchKernel(fn, grid, dim3(threads), args, 0, ctx->stream));
+            BD_PROBE(cudaLaunchKernel(fn, grid, dim3(threads), args,
+                                      ctx->f64 ? persist_smem_f64(v) : persist_smem_f32(v), ctx->stream));
             BD_PROBE(cudaEventRecord(e1, ctx->stream));
             ++ctx->launches;
         }

@@ -44,6 +44,9 @@ struct ItemDev {
     int32_t variant, pad;
 };
 
+// Threads of every parent-kernel CTA (the kernel sizes its shared tables by it).
+constexpr int kParentThreads = 64;
+
 // One warp of the parent kernel: `count` parents, chains
 // parent_items[first .. first+count-1], each on G lanes.
 struct ParentWarp {
@@ -152,6 +155,45 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk0)
     }
     return c;
 }
+
+// The same generator split by what the counter words depend on, for the
+// integrator's counter (bead, slot word, step, chain): after two rounds the
+// state is (B.x ^ S.x, B.y, S.y ^ B.z, S.z), where B depends only on (bead,
+// chain) and S only on (step, slot word). B is computed once per bead and S
+// once per step, so a bead-step runs rounds 3..10 only. Exact integer
+// arithmetic: the output is bitwise that of philox4x32_10_rk.
+struct PhiloxSplit {
+    static __device__ __forceinline__ uint4 bead_part(uint32_t bead, uint32_t chain,
+                                                      const uint32_t (&rk0)[10],
+                                                      const uint32_t (&rk1)[10])
+    {
+        const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)bead;
+        const uint32_t x2 = (uint32_t)(p0 >> 32) ^ chain ^ rk1[0];
+        const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)x2;
+        return make_uint4((uint32_t)(p1 >> 32) ^ rk0[1], (uint32_t)p1, (uint32_t)p0 ^ rk1[1], 0u);
+    }
+    static __device__ __forceinline__ uint3 step_part(uint32_t step, uint32_t slot_word,
+                                                      const uint32_t (&rk0)[10])
+    {
+        const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)step;
+        const uint32_t x0 = (uint32_t)(p1 >> 32) ^ slot_word ^ rk0[0];
+        const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)x0;
+        return make_uint3((uint32_t)p1, (uint32_t)(p0 >> 32), (uint32_t)p0);
+    }
+    static __device__ __forceinline__ uint4 finish(uint4 b, uint3 s, const uint32_t (&rk0)[10],
+                                                   const uint32_t (&rk1)[10])
+    {
+        uint4 c = make_uint4(b.x ^ s.x, b.y, s.y ^ b.z, s.z);
+#pragma unroll
+        for (int r = 2; r < 10; ++r) {
+            const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c.x;
+            const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c.z;
+            c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1,
+                           (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r], (uint32_t)p0);
+        }
+        return c;
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Standard normals from one Philox output (Box-Muller): the pair
@@ -274,6 +316,15 @@ template <bool FAST> struct Normals<double, FAST> {
         z2 = r2 * cospi(2.0 * u3);
     }
 };
+
+// The same normals from the split generator: bp = PhiloxSplit::bead_part of
+// the bead, sp = PhiloxSplit::step_part of the step and slot word.
+template <typename T, bool FAST>
+__device__ __forceinline__ void bead_noise_split(uint4 bp, uint3 sp, const StepParams& p,
+                                                 T& z0, T& z1, T& z2)
+{
+    Normals<T, FAST>::draw(PhiloxSplit::finish(bp, sp, p.rk0, p.rk1), z0, z1, z2);
+}
 
 template <typename T, bool FAST>
 __device__ __forceinline__ void bead_noise(uint32_t bead, uint32_t slot, uint32_t step,

@@ -30,6 +30,8 @@ int persist_threads_f32();
 int persist_threads_f64();
 cudaError_t persist_blocks_per_sm_f32(int variant, int* n);
 cudaError_t persist_blocks_per_sm_f64(int variant, int* n);
+size_t persist_smem_f32(int variant);     // dynamic shared memory per CTA
+size_t persist_smem_f64(int variant);
 
 // Adjoint kernels (bd_adjoint.cuh), launched with kAdjThreads threads: the
 // parent kernels exist for every tile of kTiles, the replica-window kernel

@@ -111,13 +111,18 @@ __device__ __forceinline__ LaneCtx make_lane(int seg, int G, int L, int lane, in
 }
 
 // One Eq. 1 step of the lane's L bonds; every lane of the warp must call it.
-// Returns how many spring forces hit the FENE floor.
-template <typename T, int L, bool FAST>
+// Returns how many spring forces hit the FENE floor. With TAB the noise comes
+// from the split generator: ptab[b] holds PhiloxSplit::bead_part of the
+// lane's bead b (indexed from the lane's slot), the step part is computed
+// here once per step.
+template <typename T, int L, bool FAST, bool TAB = false>
 __device__ __forceinline__ int step_bonds(T (&qx)[L], T (&qy)[L], T (&qz)[L], const LaneCtx& lc,
                                           const StepConst<T, FAST>& k, uint32_t step,
-                                          const StepParams& p)
+                                          const StepParams& p, const uint4* ptab = nullptr)
 {
     int fl = 0;
+    uint3 sp = make_uint3(0u, 0u, 0u);
+    if (TAB) sp = PhiloxSplit::step_part(step, lc.slot_key | ((uint32_t)STREAM_BD << 24), p.rk0);
     const T c0 = spring_coef<T, FAST>(qx[0], qy[0], qz[0], k.H, k.Hinvb, k.smin, fl);
     const T f0x = c0 * qx[0], f0y = c0 * qy[0], f0z = c0 * qz[0];
     T fLx = f0x, fLy = f0y, fLz = f0z;
@@ -132,7 +137,10 @@ __device__ __forceinline__ int step_bonds(T (&qx)[L], T (&qy)[L], T (&qz)[L], co
     if (!lc.has_next) { fnx = T(0); fny = T(0); fnz = T(0); }
     // noise of this lane's first bead; the next lane's first bead closes our last spring
     T xcx, xcy, xcz;
-    bead_noise<T, FAST>((uint32_t)lc.bead0, lc.slot_key, step, lc.chain, p, xcx, xcy, xcz);
+    if (TAB)
+        bead_noise_split<T, FAST>(ptab[lc.bead0], sp, p, xcx, xcy, xcz);
+    else
+        bead_noise<T, FAST>((uint32_t)lc.bead0, lc.slot_key, step, lc.chain, p, xcx, xcy, xcz);
     const T hx = shfl(xcx, lc.src_next), hy = shfl(xcy, lc.src_next), hz = shfl(xcz, lc.src_next);
 
     T fcx = f0x, fcy = f0y, fcz = f0z;
@@ -147,8 +155,14 @@ __device__ __forceinline__ int step_bonds(T (&qx)[L], T (&qy)[L], T (&qz)[L], co
                                                  k.smin, fl);
                 fpx = c * qx[j + 1]; fpy = c * qy[j + 1]; fpz = c * qz[j + 1];
             }
-            bead_noise<T, FAST>((uint32_t)(lc.bead0 + j + 1), lc.slot_key, step, lc.chain, p,
-                                xnx, xny, xnz);
+            if (TAB) {
+                uint32_t bj = (uint32_t)(lc.bead0 + j + 1);
+                asm volatile("" : "+r"(bj));     // keep the table load inside the step loop
+                bead_noise_split<T, FAST>(ptab[bj], sp, p, xnx, xny, xnz);
+            } else {
+                bead_noise<T, FAST>((uint32_t)(lc.bead0 + j + 1), lc.slot_key, step, lc.chain, p,
+                                    xnx, xny, xnz);
+            }
         } else {
             fpx = fnx; fpy = fny; fpz = fnz;
             xnx = hx; xny = hy; xnz = hz;
@@ -220,8 +234,11 @@ __device__ __forceinline__ void warp_window_sum(const T* wsm, int nb, int count,
     __syncwarp();
 }
 
-template <typename T, int L, bool FAST>
-__device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams& p, T* wsm)
+// With TAB, ptab is this warp's table of 32 L bead parts of the Philox
+// counter (filled here for the item's chain).
+template <typename T, int L, bool FAST, bool TAB = false>
+__device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams& p, T* wsm,
+                                             uint4* ptab = nullptr)
 {
     const ChainDev ch = p.chains[it.chain];
     const int nb = ch.N - 1;
@@ -236,6 +253,11 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
                                  (uint32_t)it.chain);
     StepConst<T, FAST> k;
     k.load(ch, p);
+    if (TAB) {
+        for (int b = lane; b < G * L; b += 32)
+            ptab[b] = PhiloxSplit::bead_part((uint32_t)b, (uint32_t)it.chain, p.rk0, p.rk1);
+        __syncwarp();
+    }
 
     T* state = reinterpret_cast<T*>(p.state) + (ch.state_off + (int64_t)kglob * nb) * 3;
     const T* snap = reinterpret_cast<const T*>(p.snap);
@@ -250,7 +272,7 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
     for (uint32_t t = (uint32_t)p.t0; t < t_end; ++t) {
         if (s_in == 0)   // spawn: copy the halted parent (Sec. II)
             load_bonds<T, L>(qx, qy, qz, snap + ((int64_t)(w - p.w_snap0) * p.M + ch.spr_off) * 3, lc);
-        floored += step_bonds<T, L, FAST>(qx, qy, qz, lc, k, (uint32_t)t, p);
+        floored += step_bonds<T, L, FAST, TAB>(qx, qy, qz, lc, k, (uint32_t)t, p, ptab);
         if (++s_in == p.S) {
             // one force sample per replica at the end of the evolution time
             s_in = 0;
@@ -270,6 +292,7 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
     }
     store_bonds<T, L>(qx, qy, qz, state, lc);
     if (floored) atomicAdd(p.overext + it.chain, (unsigned long long)floored);
+    if (TAB) __syncwarp();     // every lane is done with ptab before the next item refills it
 }
 
 // ---------------------------------------------------------------------------
@@ -280,10 +303,14 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
 // stay in registers; the integrated hazard lives in p.lam (float64).
 // ---------------------------------------------------------------------------
 template <typename T, int L, bool FAST>
-__global__ void __launch_bounds__(Tile<T, L>::max_threads, 1)
+__global__ void __launch_bounds__(kParentThreads)
 parent_kernel(const StepParams p)
 {
+    // per warp: the split-Philox bead parts of its parents' beads, parent s
+    // at [s G L, (s + 1) G L)
+    __shared__ uint4 ptab_all[kParentThreads / 32][32 * L];
     const int lane = threadIdx.x & 31;
+    if ((int)(threadIdx.x >> 5) >= kParentThreads / 32) return;   // whole warps beyond the table
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= p.n_parent_warps) return;          // whole warp: no shuffle partner left behind
     const ParentWarp pw = p.parent_warps[gw];
@@ -298,6 +325,14 @@ parent_kernel(const StepParams p)
                                  (uint32_t)c);
     StepConst<T, FAST> k;
     k.load(ch, p);
+    uint4* ptab = ptab_all[threadIdx.x >> 5];
+    for (int e = lane; e < P * G * L; e += 32) {
+        const int s2 = e / (G * L);
+        const int c2 = p.parent_items[pw.first + min(s2, pw.count - 1)];
+        ptab[e] = PhiloxSplit::bead_part((uint32_t)(e - s2 * G * L), (uint32_t)c2, p.rk0, p.rk1);
+    }
+    __syncwarp();
+    const uint4* my_tab = ptab + (sw < P ? sw : 0) * G * L;
     const int64_t M = p.M;
     const bool isf_thr = (p.thr_mask & BD_CRIT_ISF) != 0;
     const bool isf_bell = (p.bell_mask & BD_CRIT_ISF) != 0;
@@ -334,7 +369,7 @@ parent_kernel(const StepParams p)
     for (int64_t t = p.t0; t < t_end; ++t) {
         if (s_in == 0)   // the conformation the replicas of window w start from
             store_bonds<T, L>(qx, qy, qz, snap + ((w - p.w_snap0) * M + ch.spr_off) * 3, lc);
-        floored += step_bonds<T, L, FAST>(qx, qy, qz, lc, k, (uint32_t)t, p);
+        floored += step_bonds<T, L, FAST, true>(qx, qy, qz, lc, k, (uint32_t)t, p, my_tab);
         if (active) {
 #pragma unroll
             for (int j = 0; j < L; ++j) {

@@ -71,15 +71,10 @@ __device__ __forceinline__ float2 spring_coef2(float2 qx, float2 qy, float2 qz, 
     return F2S::mul(H2, make_float2(rcp_approx(fmaxf(s.x, smin)), rcp_approx(fmaxf(s.y, smin))));
 }
 
-// The three normals of one bead for both replicas (sign-flipped, see
-// Normals<float, true>::sign).
-__device__ __forceinline__ void bead_noise2(uint32_t bead, uint32_t ka, uint32_t kb, uint32_t step,
-                                            uint32_t chain, const StepParams& p, float2& z0,
-                                            float2& z1, float2& z2)
+// Box-Muller of two Philox outputs (replicas .x and .y), sign-flipped normals
+// (see Normals<float, true>::sign).
+__device__ __forceinline__ void box_muller2(uint4 xa, uint4 xb, float2& z0, float2& z1, float2& z2)
 {
-    const uint32_t w1 = (uint32_t)STREAM_BD << 24;
-    const uint4 xa = philox4x32_10_rk(make_uint4(bead, ka | w1, step, chain), p.rk0, p.rk1);
-    const uint4 xb = philox4x32_10_rk(make_uint4(bead, kb | w1, step, chain), p.rk0, p.rk1);
     const float2 S = F2::splat(FastBM::s32), Hh = F2::splat(FastBM::h32);
     const float2 u0 = F2U::fma(make_float2((float)xa.x, (float)xb.x), S, Hh);
     const float2 u2 = F2U::fma(make_float2((float)xa.z, (float)xb.z), S, Hh);
@@ -94,6 +89,28 @@ __device__ __forceinline__ void bead_noise2(uint32_t bead, uint32_t ka, uint32_t
     z0 = F2B::mul(r0, make_float2(cos_approx(t1.x), cos_approx(t1.y)));
     z1 = F2B::mul(r0, make_float2(sin_approx(t1.x), sin_approx(t1.y)));
     z2 = F2B::mul(r2, make_float2(cos_approx(t3.x), cos_approx(t3.y)));
+}
+
+// Noise of one bead for both replicas. With a bead table (TAB) the Philox
+// rounds that depend only on (bead, chain) come from ptab[bead] and those
+// that depend only on (step, slot) from spa / spb (PhiloxSplit); otherwise
+// the full generator runs.
+template <bool TAB>
+__device__ __forceinline__ void bead_noise2(uint32_t bead, uint32_t ka, uint32_t kb, uint32_t step,
+                                            uint32_t chain, const StepParams& p, const uint4* ptab,
+                                            uint3 spa, uint3 spb, float2& z0, float2& z1, float2& z2)
+{
+    uint4 xa, xb;
+    if (TAB) {
+        const uint4 bp = ptab[bead];
+        xa = PhiloxSplit::finish(bp, spa, p.rk0, p.rk1);
+        xb = PhiloxSplit::finish(bp, spb, p.rk0, p.rk1);
+    } else {
+        const uint32_t w1 = (uint32_t)STREAM_BD << 24;
+        xa = philox4x32_10_rk(make_uint4(bead, ka | w1, step, chain), p.rk0, p.rk1);
+        xb = philox4x32_10_rk(make_uint4(bead, kb | w1, step, chain), p.rk0, p.rk1);
+    }
+    box_muller2(xa, xb, z0, z1, z2);
 }
 
 __device__ __forceinline__ float2 shfl2(float2 v, int src)
@@ -116,12 +133,18 @@ struct StepConst2 {
 };
 
 // One Eq. 1 step (bond form) of both replicas' L bonds; all lanes call it.
-template <int L>
+template <int L, bool TAB>
 __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], float2 (&qz)[L],
                                             const LaneCtx& lc, uint32_t kb, bool act_b,
                                             const StepConst2& k, uint32_t step,
-                                            const StepParams& p, int& fl_out)
+                                            const StepParams& p, const uint4* ptab, int& fl_out)
 {
+    uint3 spa = make_uint3(0u, 0u, 0u), spb = spa;
+    if (TAB) {
+        const uint32_t w1 = (uint32_t)STREAM_BD << 24;
+        spa = PhiloxSplit::step_part(step, lc.slot_key | w1, p.rk0);
+        spb = PhiloxSplit::step_part(step, kb | w1, p.rk0);
+    }
     int fla = 0, flb = 0;
     const float2 c0 = spring_coef2(qx[0], qy[0], qz[0], k.H, k.nHinvb, k.smin, fla, flb);
     const float2 f0x = F2S::mul(c0, qx[0]), f0y = F2S::mul(c0, qy[0]), f0z = F2S::mul(c0, qz[0]);
@@ -136,7 +159,7 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
     if (!lc.has_prev) { fmx = zero; fmy = zero; fmz = zero; }
     if (!lc.has_next) { fnx = zero; fny = zero; fnz = zero; }
     float2 xcx, xcy, xcz;
-    bead_noise2((uint32_t)lc.bead0, lc.slot_key, kb, step, lc.chain, p, xcx, xcy, xcz);
+    bead_noise2<TAB>((uint32_t)lc.bead0, lc.slot_key, kb, step, lc.chain, p, ptab, spa, spb, xcx, xcy, xcz);
     const float2 hx = shfl2(xcx, lc.src_next), hy = shfl2(xcy, lc.src_next), hz = shfl2(xcz, lc.src_next);
     const float2 m2 = F2::splat(-2.0f);
 
@@ -153,7 +176,7 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
             }
             uint32_t bj = (uint32_t)(lc.bead0 + j + 1);
             asm volatile("" : "+r"(bj));     // keep per-bead Philox work inside the step loop
-            bead_noise2(bj, lc.slot_key, kb, step, lc.chain, p, xnx, xny, xnz);
+            bead_noise2<TAB>(bj, lc.slot_key, kb, step, lc.chain, p, ptab, spa, spb, xnx, xny, xnz);
         } else {
             fpx = fnx; fpy = fny; fpz = fnz;
             xnx = hx; xny = hy; xnz = hz;
@@ -175,9 +198,11 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
 }
 
 // One warp work item with two replicas per lane: lane run s holds replicas
-// rep_begin + 2s + 1 (.x) and rep_begin + 2s + 2 (.y).
-template <int L>
-__device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParams& p, float* wsm)
+// rep_begin + 2s + 1 (.x) and rep_begin + 2s + 2 (.y). With TAB, ptab is
+// this warp's table of 32 L bead parts of the Philox counter.
+template <int L, bool TAB>
+__device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParams& p, float* wsm,
+                                              uint4* ptab)
 {
     const ChainDev ch = p.chains[it.chain];
     const int nb = ch.N - 1;
@@ -195,6 +220,11 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
     const uint32_t keyb = same ? 0u : (uint32_t)kb;
     StepConst2 k;
     k.load(ch, p);
+    if (TAB) {       // bead parts of the noise counter for every bead a lane of this chain draws
+        for (int b = lane; b < G * L; b += 32)
+            ptab[b] = PhiloxSplit::bead_part((uint32_t)b, (uint32_t)it.chain, p.rk0, p.rk1);
+        __syncwarp();
+    }
 
     float* state = reinterpret_cast<float*>(p.state) + ch.state_off * 3;
     float* sa = state + (int64_t)ka * nb * 3;
@@ -227,7 +257,7 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
                 }
             }
         }
-        step_bonds2<L>(qx, qy, qz, lc, keyb, act_b, k, (uint32_t)t, p, floored);
+        step_bonds2<L, TAB>(qx, qy, qz, lc, keyb, act_b, k, (uint32_t)t, p, ptab, floored);
         if (++s_in == p.S) {
             s_in = 0;
             if (act_a) {
@@ -255,6 +285,7 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
         }
     }
     if (floored) atomicAdd(p.overext + it.chain, (unsigned long long)floored);
+    if (TAB) __syncwarp();     // every lane is done with ptab before the next item refills it
 }
 
 }  // namespace bdra

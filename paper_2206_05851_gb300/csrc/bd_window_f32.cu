@@ -36,11 +36,26 @@ const void* persist_func_f32(int v)
 
 int persist_threads_f32() { return Persist<float>::threads; }
 
+size_t persist_smem_f32(int v)
+{
+    switch (v) {
+#define X(x) case x: return PersistSmem<float, true, x>::bytes;
+        BD_VARIANTS(X)
+#undef X
+    default: return 0;
+    }
+}
+
+// Occupancy with the variant's dynamic shared memory, which is also allowed
+// here (above the default 48 KiB) for the current device.
 cudaError_t persist_blocks_per_sm_f32(int v, int* n)
 {
     const void* f = persist_func_f32(v);
     if (!f) return cudaErrorInvalidValue;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, f, Persist<float>::threads, 0);
+    const size_t smem = persist_smem_f32(v);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, f, Persist<float>::threads, smem);
 }
 
 }  // namespace bdra

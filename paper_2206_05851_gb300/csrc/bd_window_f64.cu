@@ -36,11 +36,26 @@ const void* persist_func_f64(int v)
 
 int persist_threads_f64() { return Persist<double>::threads; }
 
+size_t persist_smem_f64(int v)
+{
+    switch (v) {
+#define X(x) case x: return PersistSmem<double, false, x>::bytes;
+        BD_VARIANTS(X)
+#undef X
+    default: return 0;
+    }
+}
+
+// Occupancy with the variant's dynamic shared memory, which is also allowed
+// here (above the default 48 KiB) for the current device.
 cudaError_t persist_blocks_per_sm_f64(int v, int* n)
 {
     const void* f = persist_func_f64(v);
     if (!f) return cudaErrorInvalidValue;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, f, Persist<double>::threads, 0);
+    const size_t smem = persist_smem_f64(v);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, f, Persist<double>::threads, smem);
 }
 
 }  // namespace bdra
