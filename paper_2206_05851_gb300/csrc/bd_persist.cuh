@@ -29,6 +29,8 @@ template <typename T, bool FAST, int V> struct PersistSmem {
     static constexpr int tab_per_warp = tab ? 32 * L : 0;
     static constexpr size_t bytes = wsm_bytes + (size_t)warps * tab_per_warp * sizeof(uint4);
     static_assert(wsm_bytes % 16 == 0, "table must start 16-byte aligned");
+    // window-end scratch: replicas per warp x springs <= (2 if paired) x 32 L
+    static_assert((V >= kPairBase ? 64 : 32) * L <= kWarpScratch, "window scratch too small for the tile");
 };
 
 template <typename T, bool FAST, int V>
