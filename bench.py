@@ -33,14 +33,16 @@ sys.path.insert(0, ROOT)
 METRIC = ("bead-steps/s (chains×replicas×beads×steps) FP32 batched vs FP64 plain, "
           "1 GB300")
 # Minimal lane-instructions per slot-bead-step of the float32 replica step on
-# an SM with two-wide float32 instructions: Philox4x32-10 39 (20 wide
-# multiplies less the step word's shared one, 20 three-input XORs), two
-# integer-to-float conversions, 8 special-function ops (2 log2, 2 sqrt, sin,
-# 2 cos, 1 reciprocal), 19 packed float32 ops (38 float32 operations: uniform
-# scaling 4, Box-Muller products 7, spring law 8, Laplacian 6, update 13) and
-# 4 bit/compare ops (angle bits 2, floor clamp and count 2). See the design
-# notes.
-ALGO_OPS_PER_BEAD_STEP = 72
+# an SM with two-wide float32 instructions: Philox4x32-10 34.5 (rounds 3-10:
+# 16 wide multiplies and 16 three-input XORs; the round-2 output is two XORs of
+# a per-bead part, loaded from a table once per bead and replica pair (0.5),
+# and a per-step part - rounds 1-2 amortise away), 2 integer-to-float
+# conversions, 8 special-function ops (2 log2, 2 sqrt, sin, 2 cos, 1
+# reciprocal), 19 packed float32 ops (38 float32 operations: uniform scaling
+# 4, Box-Muller products 7, spring law 8, Laplacian 6, update 13) and 4
+# bit/compare ops (angle bits 2, floor clamp and count 2).
+ALGO_OPS_PER_BEAD_STEP = 67.5
+PHILOX_ROUNDS_PER_BEAD_STEP = 8
 SMS, LANES_PER_CLK_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -287,6 +289,7 @@ def main():
     for _ in range(args.warmup):
         bench_step()
     torch.cuda.synchronize()
+    philox_peak = bdra.bd_probe_philox_rounds(sptr)      # measured ceiling, outside the timed region
     bdra.bd_enable_timing(ctx.ptr, True)
     bdra.bd_kernel_times(ctx.ptr)
     launches0 = ctx.info().kernel_launches
@@ -325,6 +328,12 @@ def main():
             "ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP}
     if clk:
         roof["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6 / 1e12)
+    # the same kernel against the measured ceiling of its dominant work
+    rounds = PHILOX_ROUNDS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3)
+    roof_philox = {"bound": "alu (Philox rounds: 32x32->64 multiplies + XOR3)", "achieved": rounds / 1e12,
+                   "peak": philox_peak / 1e12, "unit": "T rounds/s", "frac": rounds / philox_peak,
+                   "peak_basis": "measured by bd_probe_philox_rounds on this GPU just before the timed region",
+                   "rounds_per_bead_step": PHILOX_ROUNDS_PER_BEAD_STEP}
     parent_share = par_ms / t_ms
 
     out = {"metric": METRIC, "value": value, "unit": "bead-steps/s", "n_gpus": world,
@@ -345,6 +354,7 @@ def main():
     if clk:
         out["clocks"] = clk
     out["roofline"] = roof
+    out["roofline_philox"] = roof_philox
     peaks = measured_peaks()
     if peaks:
         out["measured_peaks_file"] = {k: peaks[k] for k in list(peaks)[:8]}

@@ -256,6 +256,17 @@ bd_status bd_adjoint(bd_ctx* ctx, const double* grad_rsf, const double* grad_log
 bd_status bd_philox_normals(uint64_t seed, int64_t n, const uint32_t* ctr, int32_t precision,
                             double* out, void* stream);
 
+/* Measurement: the device's throughput for the integrator's dominant work,
+ * Philox4x32 rounds (two 32 x 32 -> 64 multiplies and two three-input XORs
+ * each), from a kernel of independent round chains at full occupancy on the
+ * current device (about 2 ms). *rounds_per_s (host) receives rounds per
+ * second for the whole device. The replica step runs 8 rounds per
+ * slot-bead-step (the two others are amortised per bead and per step), so
+ * 8 x slot-bead-steps/s over this rate is the step's fraction of the
+ * multiply-bound ceiling. Runs on `stream`; synchronises. BD_E_INVALID for a
+ * NULL pointer, BD_E_OOM / BD_E_CUDA on device failures. */
+bd_status bd_probe_philox_rounds(void* stream, double* rounds_per_s);
+
 /* Largest n_springs bd_compact_events_noalloc accepts (its fixed scratch
  * holds one count per 256 springs: 32 KiB of device memory). */
 #define BD_NOALLOC_MAX_SPRINGS (1 << 20)

@@ -98,6 +98,7 @@ def load() -> ctypes.CDLL:
         "bd_enable_timing": ([vp, ctypes.c_int32], st),
         "bd_kernel_times": ([vp, P(ctypes.c_double), P(ctypes.c_int64)], st),
         "bd_adjoint": ([vp, vp, vp, vp], st),
+        "bd_probe_philox_rounds": ([vp, P(ctypes.c_double)], st),
         "bd_philox_normals": ([ctypes.c_uint64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp], st),
         "bd_compact_events_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.c_int32, vp,
                                        ctypes.c_int64, vp, vp], st),
@@ -265,6 +266,13 @@ def bd_adjoint(ctx: int, n_chains: int, M: int, windows: int, grad_rsf=None,
     l = _need(grad_log_surv, 8 * n_chains, "grad_log_surv") if grad_log_surv is not None else None
     _check(load().bd_adjoint(ctx, g, l, _need(out, 24 * n_chains, "grad_params")), ctx)
     return out
+
+
+def bd_probe_philox_rounds(stream: Optional[int] = None) -> float:
+    """Measured Philox4x32 rounds per second of the current device."""
+    r = ctypes.c_double(0.0)
+    _check(load().bd_probe_philox_rounds(stream, ctypes.byref(r)))
+    return r.value
 
 
 NOALLOC_MAX_SPRINGS = 1 << 20

@@ -3,8 +3,8 @@
 The translation units compile in parallel: the float32 and float64
 instantiations of the parent / replica kernels and of the adjoint kernels
 (with -fmad=false, so every fused multiply-add is the explicit one written
-in the source), the support kernels, the C ABI and the allocation-free
-event compaction. Only nvcc is needed; no CMake.
+in the source), the support kernels, the C ABI, the allocation-free
+event compaction and the Philox-round throughput probe. Only nvcc is needed; no CMake.
 """
 from __future__ import annotations
 
@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 UNITS = [("bd_window_f32.cu", ["-fmad=false"]), ("bd_window_f64.cu", ["-fmad=false"]),
          ("bd_adjoint_f32.cu", ["-fmad=false"]), ("bd_adjoint_f64.cu", ["-fmad=false"]),
-         ("bd_support.cu", []), ("bd_api.cu", []), ("bd_noalloc.cu", [])]
+         ("bd_support.cu", []), ("bd_api.cu", []), ("bd_noalloc.cu", []), ("bd_probe.cu", [])]
 
 
 def _nvcc() -> str:

@@ -162,6 +162,23 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk0)
 // chain) and S only on (step, slot word). B is computed once per bead and S
 // once per step, so a bead-step runs rounds 3..10 only. Exact integer
 // arithmetic: the output is bitwise that of philox4x32_10_rk.
+// High and low words of a Philox 32 x 32 -> 64 product. BD_PHILOX_HILO
+// selects two 32-bit multiplies (high, low) instead of one wide multiply.
+#ifndef BD_PHILOX_HILO
+#define BD_PHILOX_HILO 0
+#endif
+__device__ __forceinline__ void philox_mulhilo(uint32_t m, uint32_t x, uint32_t& hi, uint32_t& lo)
+{
+#if BD_PHILOX_HILO
+    hi = __umulhi(m, x);
+    lo = m * x;
+#else
+    const unsigned long long p = (unsigned long long)m * (unsigned long long)x;
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+#endif
+}
+
 struct PhiloxSplit {
     static __device__ __forceinline__ uint4 bead_part(uint32_t bead, uint32_t chain,
                                                       const uint32_t (&rk0)[10],
@@ -186,10 +203,10 @@ struct PhiloxSplit {
         uint4 c = make_uint4(b.x ^ s.x, b.y, s.y ^ b.z, s.z);
 #pragma unroll
         for (int r = 2; r < 10; ++r) {
-            const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c.x;
-            const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c.z;
-            c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1,
-                           (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r], (uint32_t)p0);
+            uint32_t hi0, lo0, hi1, lo1;
+            philox_mulhilo(0xD2511F53u, c.x, hi0, lo0);
+            philox_mulhilo(0xCD9E8D57u, c.z, hi1, lo1);
+            c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
         }
         return c;
     }

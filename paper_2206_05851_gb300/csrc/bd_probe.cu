@@ -1,0 +1,80 @@
+// Measured ceiling of the integrator's dominant work: Philox4x32 rounds.
+// Every thread runs independent round chains (two 32 x 32 -> 64 multiplies
+// and two three-input XORs per round, exactly the round of the integrator's
+// generator) at full occupancy with no memory traffic in the loop, so the
+// rate it reports is the SM's throughput for that instruction mix.
+#include <cuda_runtime.h>
+
+#include "bd_device.cuh"
+
+namespace bdra {
+namespace {
+
+constexpr int kProbeChains = 8;
+constexpr int kProbeThreads = 512;
+
+__global__ void __launch_bounds__(kProbeThreads, 2)
+philox_round_probe(uint32_t* sink, int iters, uint32_t k0, uint32_t k1)
+{
+    uint4 c[kProbeChains];
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) c[j] = make_uint4(g, (uint32_t)j, g ^ 0x5bd1e995u, (uint32_t)j * 7u);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < kProbeChains; ++j) {
+            uint32_t hi0, lo0, hi1, lo1;
+            philox_mulhilo(0xD2511F53u, c[j].x, hi0, lo0);
+            philox_mulhilo(0xCD9E8D57u, c[j].z, hi1, lo1);
+            c[j] = make_uint4(hi1 ^ c[j].y ^ k0, lo1, hi0 ^ c[j].w ^ k1, lo0);
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) acc ^= c[j].x ^ c[j].y ^ c[j].z ^ c[j].w;
+    sink[g] = acc;
+}
+
+}  // namespace
+}  // namespace bdra
+
+using namespace bdra;
+
+extern "C" bd_status bd_probe_philox_rounds(void* stream, double* rounds_per_s)
+{
+    if (!rounds_per_s) return BD_E_INVALID;
+    *rounds_per_s = 0.0;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return BD_E_CUDA;
+    }
+    const int blocks = 2 * sms, iters = 4096;
+    uint32_t* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bd_status s = BD_OK;
+    float ms = 0.0f;
+    if (cudaMalloc((void**)&sink, sizeof(uint32_t) * (size_t)blocks * kProbeThreads) != cudaSuccess) {
+        cudaGetLastError();
+        return BD_E_OOM;
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) s = BD_E_CUDA;
+    if (s == BD_OK) {
+        philox_round_probe<<<blocks, kProbeThreads, 0, st>>>(sink, 256, 1u, 2u);    // warm-up
+        cudaEventRecord(e0, st);
+        philox_round_probe<<<blocks, kProbeThreads, 0, st>>>(sink, iters, 1u, 2u);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess || !(ms > 0.0f))
+            s = BD_E_CUDA;
+    }
+    if (s == BD_OK)
+        *rounds_per_s = (double)blocks * kProbeThreads * iters * kProbeChains / (ms * 1e-3);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    cudaGetLastError();
+    return s;
+}

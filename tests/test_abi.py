@@ -105,6 +105,10 @@ def test_null_arguments_rejected(lib):
     lib.bd_destroy(None)    # NULL is ignored
 
 
+def test_probe_rejects_null_output(lib):
+    assert lib.bd_probe_philox_rounds(None, None) == bdra.BD_E_INVALID
+
+
 def test_binding_fails_loudly_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(bdra, "_lib", None)
     monkeypatch.setattr(bdra, "LIB_PATH", str(tmp_path / "missing.so"))
