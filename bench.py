@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--only-adjoint", action="store_true",
+                    help="time only the differentiation workload (for profiling)")
+    ap.add_argument("--adjoint-chains", type=int, default=0, help="override its chain count")
+    ap.add_argument("--adjoint-steps", type=int, default=0, help="override its step count")
     return ap.parse_args()
 
 
@@ -189,7 +193,7 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def adjoint_line(sptr):
+def adjoint_line(sptr, n_chains=0, n_steps=0):
     """Forward run plus reverse-mode adjoint of the differentiation workload
     (256 FENE chains, N=200, 32 replicas, 2e4 steps, parent checkpoints every
     1000 steps, float32 integration): gradients of the mid-chain RSF averaged
@@ -199,7 +203,12 @@ def adjoint_line(sptr):
     from paper_2206_05851_gb300 import bdra
     from paper_2206_05851_gb300 import inputs as I
 
-    wl = I.adjoint_256()
+    kw = {}
+    if n_chains:
+        kw["n_chains"] = n_chains
+    if n_steps:
+        kw["n_steps"] = n_steps
+    wl = I.adjoint_256(**kw)
     pos0 = torch.from_numpy(I.initial_positions(wl)).cuda()
     S, n = wl.window_steps, wl.n_steps
     W = n // S
@@ -213,8 +222,9 @@ def adjoint_line(sptr):
     ctx = bdra.Context(wl.chains, wl.dt, S, wl.seed, pos0, precision=bdra.BD_PREC_FP32,
                        max_windows=W, bell_mask=I.CRIT_RSF, stream=sptr,
                        checkpoint_steps=I.ADJOINT_CHECKPOINT_STEPS)
-    ctx.step(I.ADJOINT_CHECKPOINT_STEPS)            # warm-up; allocates the work buffers
-    bdra.bd_adjoint(ctx.ptr, len(wl.chains), ctx.M, I.ADJOINT_CHECKPOINT_STEPS // S, G, gls, grad)
+    warm = min(I.ADJOINT_CHECKPOINT_STEPS, n)
+    ctx.step(warm)                                  # warm-up; allocates the work buffers
+    bdra.bd_adjoint(ctx.ptr, len(wl.chains), ctx.M, warm // S, G, gls, grad)
     ctx.set_positions(pos0, 0)
     stream = torch.cuda.current_stream()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -241,6 +251,16 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only_adjoint:
+        import torch
+        from paper_2206_05851_gb300 import bdra, build as B
+        if not B.up_to_date():
+            B.build()
+        bdra.load()
+        line = adjoint_line(torch.cuda.current_stream().cuda_stream, args.adjoint_chains,
+                            args.adjoint_steps)
+        print(json.dumps({"adjoint": line}), flush=True)
         return
     import numpy as np
     import torch
@@ -418,7 +438,7 @@ def main():
                           "d2h_bytes_per_step": int(nev * 24 + ctx.M * 8 + 8),
                           "steps": e2e_steps}
         if not args.no_adjoint:
-            out["adjoint"] = adjoint_line(sptr)
+            out["adjoint"] = adjoint_line(sptr, args.adjoint_chains, args.adjoint_steps)
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(wl, pos0)
     if rank == 0:
