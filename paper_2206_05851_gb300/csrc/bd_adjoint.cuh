@@ -30,6 +30,11 @@
 
 namespace bdra {
 
+// Reciprocal for the derivative factors: the hardware approximation in float
+// (about one ulp), a correctly rounded division in double.
+template <typename T> __device__ __forceinline__ T adj_recip(T x) { return T(1) / x; }
+template <> __device__ __forceinline__ float adj_recip<float>(float x) { return rcp_approx(x); }
+
 // Spring-law factors at Q: c = H/s and its slopes (on the floor only dc/dH).
 template <typename T>
 struct SpringD {
@@ -38,10 +43,10 @@ struct SpringD {
     {
         const T s = fma(-Hinvb, q2, T(1));
         if (s < smin) {
-            const T is = T(1) / smin;
+            const T is = adj_recip(smin);
             c = H * is; dcq = T(0); dcH = is; dcb = T(0);
         } else {
-            const T is = T(1) / s;
+            const T is = adj_recip(s);
             const T is2 = is * is;
             c = H * is;
             dcq = H * Hinvb * is2;              // H^2 / (b s^2)
@@ -100,12 +105,29 @@ struct GradAcc {
     }
 };
 
-// One adjoint step of the lane's L bonds: lx/ly/lz hold lambda at t+1 on
-// entry and lambda at t on exit; the state at t is read from `q` (the slot's
-// bond row, [N-1][3]). Adds the step's parameter gradients to g. Every lane
-// of the warp calls it.
+// The lane's L bonds of a stored state (slot row [N-1][3]); zero past the
+// lane's springs.
 template <typename T, int L>
-__device__ __forceinline__ void adjoint_step(const T* q, T (&lx)[L], T (&ly)[L], T (&lz)[L],
+__device__ __forceinline__ void load_lane(const T* q, const LaneCtx& lc, T (&x)[L], T (&y)[L],
+                                          T (&z)[L])
+{
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        if (j < lc.nv) {
+            const int i = lc.bead0 + j;
+            x[j] = q[3 * i + 0]; y[j] = q[3 * i + 1]; z[j] = q[3 * i + 2];
+        } else {
+            x[j] = T(0); y[j] = T(0); z[j] = T(0);
+        }
+    }
+}
+
+// One adjoint step of the lane's L bonds: lx/ly/lz hold lambda at t+1 on
+// entry and lambda at t on exit; qx/qy/qz hold the state at t. Adds the
+// step's parameter gradients to g. Every lane of the warp calls it.
+template <typename T, int L>
+__device__ __forceinline__ void adjoint_step(const T (&qx)[L], const T (&qy)[L], const T (&qz)[L],
+                                             T (&lx)[L], T (&ly)[L], T (&lz)[L],
                                              const LaneCtx& lc, const AdjConst<T>& k, T (&g)[3])
 {
     T pmx = shfl(lx[L - 1], lc.src_prev), pmy = shfl(ly[L - 1], lc.src_prev), pmz = shfl(lz[L - 1], lc.src_prev);
@@ -120,17 +142,16 @@ __device__ __forceinline__ void adjoint_step(const T* q, T (&lx)[L], T (&ly)[L],
         if (j + 1 < L) { nx = lx[j + 1]; ny = ly[j + 1]; nz = lz[j + 1]; }
         else { nx = pnx; ny = pny; nz = pnz; }
         if (j < lc.nv) {
-            const int i = lc.bead0 + j;
-            const T qx = q[3 * i + 0], qy = q[3 * i + 1], qz = q[3 * i + 2];
+            const T qxj = qx[j], qyj = qy[j], qzj = qz[j];
             const T Lx = fma(T(-2), cx, mx + nx), Ly = fma(T(-2), cy, my + ny), Lz = fma(T(-2), cz, mz + nz);
             SpringD<T> sd;
-            sd.at(fma(qx, qx, fma(qy, qy, qz * qz)), k.H, k.Hinvb, k.smin);
-            const T qL = fma(qx, Lx, fma(qy, Ly, qz * Lz));
+            sd.at(fma(qxj, qxj, fma(qyj, qyj, qzj * qzj)), k.H, k.Hinvb, k.smin);
+            const T qL = fma(qxj, Lx, fma(qyj, Ly, qzj * Lz));
             const T a = T(2) * sd.dcq * qL;
-            lx[j] = fma(k.cd, fma(sd.c, Lx, a * qx), fma(k.fl.kxx, cx, cx));
-            ly[j] = fma(k.cd, fma(sd.c, Ly, a * qy), fma(k.fl.kyy, cy, cy));
-            lz[j] = fma(k.cd, fma(sd.c, Lz, a * qz), fma(k.fl.kzz, cz, fma(k.fl.kxz, cx, cz)));
-            g[0] = fma(cx, fma(k.fl.hxx, qx, k.fl.hxz * qz), fma(cy, k.fl.hyy * qy, fma(cz, k.fl.hzz * qz, g[0])));
+            lx[j] = fma(k.cd, fma(sd.c, Lx, a * qxj), fma(k.fl.kxx, cx, cx));
+            ly[j] = fma(k.cd, fma(sd.c, Ly, a * qyj), fma(k.fl.kyy, cy, cy));
+            lz[j] = fma(k.cd, fma(sd.c, Lz, a * qzj), fma(k.fl.kzz, cz, fma(k.fl.kxz, cx, cz)));
+            g[0] = fma(cx, fma(k.fl.hxx, qxj, k.fl.hxz * qzj), fma(cy, k.fl.hyy * qyj, fma(cz, k.fl.hzz * qzj, g[0])));
             g[1] = fma(k.cd * sd.dcb, qL, g[1]);
             g[2] = fma(k.cd * sd.dcH, qL, g[2]);
         }
@@ -159,19 +180,40 @@ __device__ __forceinline__ bool parent_lane(const StepParams& p, ParentLane& out
     return true;
 }
 
+// Fills a parent warp's split-Philox table (parent s at [s G L, (s + 1) G L))
+// and returns this lane's part of it.
+template <int L>
+__device__ __forceinline__ const uint4* parent_table(const StepParams& p, uint4* tab)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const ParentWarp pw = p.parent_warps[gw];
+    const int G = pw.G, P = 32 / G, sw = lane / G;
+    for (int e = lane; e < P * G * L; e += 32) {
+        const int s2 = e / (G * L);
+        const int c2 = p.parent_items[pw.first + min(s2, pw.count - 1)];
+        tab[e] = PhiloxSplit::bead_part((uint32_t)(e - s2 * G * L), (uint32_t)c2, p.rk0, p.rk1);
+    }
+    __syncwarp();
+    return tab + (sw < P ? sw : 0) * G * L;
+}
+
 // ---------------------------------------------------------------------------
 // Parent recompute: checkpoint ckpt_index (the parent at seg_t0 = t0) ->
 // segbuf rows 0 .. n_steps (the states at steps t0 .. t0 + n_steps).
 // ---------------------------------------------------------------------------
 template <typename T, int L, bool FAST>
-__global__ void __launch_bounds__(128) adj_parent_recompute_kernel(const AdjParams a)
+__global__ void __launch_bounds__(kAdjThreads) adj_parent_recompute_kernel(const AdjParams a)
 {
+    __shared__ uint4 tab_all[kAdjThreads / 32][32 * L];    // split-Philox bead parts per warp
     const StepParams& p = a.sp;
     ParentLane pl;
+    if ((int)(threadIdx.x >> 5) >= kAdjThreads / 32) return;
     if (!parent_lane<L>(p, pl)) return;
     const ChainDev ch = p.chains[pl.chain];
     StepConst<T, FAST> k;
     k.load(ch, p);
+    const uint4* tab = parent_table<L>(p, tab_all[threadIdx.x >> 5]);
     const T* ck = reinterpret_cast<const T*>(a.ckpt) + (a.ckpt_index * p.M + ch.spr_off) * 3;
     T* seg = reinterpret_cast<T*>(a.segbuf) + ch.spr_off * 3;
     T qx[L], qy[L], qz[L];
@@ -179,7 +221,7 @@ __global__ void __launch_bounds__(128) adj_parent_recompute_kernel(const AdjPara
     store_bonds<T, L>(qx, qy, qz, seg, pl.lc);
 #pragma unroll 1
     for (int s = 0; s < a.n_steps; ++s) {
-        step_bonds<T, L, FAST>(qx, qy, qz, pl.lc, k, (uint32_t)(a.t0 + s), p);
+        step_bonds<T, L, FAST, true>(qx, qy, qz, pl.lc, k, (uint32_t)(a.t0 + s), p, tab);
         store_bonds<T, L>(qx, qy, qz, seg + (int64_t)(s + 1) * p.M * 3, pl.lc);
     }
 }
@@ -192,9 +234,11 @@ __global__ void __launch_bounds__(128) adj_parent_recompute_kernel(const AdjPara
 // only the bonds it wrote itself, so the two sweeps need no synchronisation.
 // ---------------------------------------------------------------------------
 template <typename T, int L, bool FAST>
-__global__ void __launch_bounds__(128) adj_replica_window_kernel(const AdjParams a)
+__global__ void __launch_bounds__(kAdjThreads) adj_replica_window_kernel(const AdjParams a)
 {
+    __shared__ uint4 tab_all[kAdjThreads / 32][32 * L];    // split-Philox bead parts per warp
     const StepParams& p = a.sp;
+    if ((int)(threadIdx.x >> 5) >= kAdjThreads / 32) return;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= a.n_items) return;                        // whole warp
     const ItemDev it = a.items[gw];
@@ -216,6 +260,10 @@ __global__ void __launch_bounds__(128) adj_replica_window_kernel(const AdjParams
 
     // forward: spawn from the parent at tw, S steps, every state kept
     {
+        uint4* tab = tab_all[threadIdx.x >> 5];
+        for (int b = lane; b < G * L; b += 32)
+            tab[b] = PhiloxSplit::bead_part((uint32_t)b, (uint32_t)it.chain, p.rk0, p.rk1);
+        __syncwarp();
         StepConst<T, FAST> k;
         k.load(ch, p);
         T qx[L], qy[L], qz[L];
@@ -224,7 +272,7 @@ __global__ void __launch_bounds__(128) adj_replica_window_kernel(const AdjParams
         store_bonds<T, L>(qx, qy, qz, rb, lc);
 #pragma unroll 1
         for (int s = 0; s < p.S; ++s) {
-            step_bonds<T, L, FAST>(qx, qy, qz, lc, k, (uint32_t)(tw + s), p);
+            step_bonds<T, L, FAST, true>(qx, qy, qz, lc, k, (uint32_t)(tw + s), p, tab);
             store_bonds<T, L>(qx, qy, qz, rb + (int64_t)(s + 1) * row, lc);
         }
     }
@@ -258,10 +306,17 @@ __global__ void __launch_bounds__(128) adj_replica_window_kernel(const AdjParams
             }
         }
     }
+    // states are loaded one step ahead of the sweep that uses them
+    T qx[L], qy[L], qz[L];
+    load_lane<T, L>(rb + (int64_t)(p.S - 1) * row, lc, qx, qy, qz);
 #pragma unroll 1
     for (int s = p.S - 1; s >= 0; --s) {
-        adjoint_step<T, L>(rb + (int64_t)s * row, lx, ly, lz, lc, k, ga.part);
+        T nx[L], ny[L], nz[L];
+        load_lane<T, L>(rb + (int64_t)(s > 0 ? s - 1 : 0) * row, lc, nx, ny, nz);
+        adjoint_step<T, L>(qx, qy, qz, lx, ly, lz, lc, k, ga.part);
         ga.tick();
+#pragma unroll
+        for (int j = 0; j < L; ++j) { qx[j] = nx[j]; qy[j] = ny[j]; qz[j] = nz[j]; }
     }
     ga.fold();
 
@@ -298,7 +353,7 @@ __global__ void __launch_bounds__(128) adj_replica_window_kernel(const AdjParams
 // lambda back to lamP.
 // ---------------------------------------------------------------------------
 template <typename T, int L>
-__global__ void __launch_bounds__(128) adj_parent_backward_kernel(const AdjParams a)
+__global__ void __launch_bounds__(kAdjThreads) adj_parent_backward_kernel(const AdjParams a)
 {
     const StepParams& p = a.sp;
     ParentLane pl;
@@ -315,11 +370,19 @@ __global__ void __launch_bounds__(128) adj_parent_backward_kernel(const AdjParam
     ga.init();
     T lx[L], ly[L], lz[L];
     load_bonds<T, L>(lx, ly, lz, lp, lc);
+    // states are loaded one step ahead of the sweep that uses them
+    T qx[L], qy[L], qz[L];
+    if (a.n_steps > 0)
+        load_lane<T, L>(seg + (a.t0 + a.n_steps - 1 - a.seg_t0) * p.M * 3, lc, qx, qy, qz);
 #pragma unroll 1
     for (int s = a.n_steps - 1; s >= 0; --s) {
         const int64_t t = a.t0 + s;
-        adjoint_step<T, L>(seg + (t - a.seg_t0) * p.M * 3, lx, ly, lz, lc, k, ga.part);
+        T nx[L], ny[L], nz[L];
+        load_lane<T, L>(seg + ((s > 0 ? t - 1 : t) - a.seg_t0) * p.M * 3, lc, nx, ny, nz);
+        adjoint_step<T, L>(qx, qy, qz, lx, ly, lz, lc, k, ga.part);
         ga.tick();
+#pragma unroll
+        for (int j = 0; j < L; ++j) { qx[j] = nx[j]; qy[j] = ny[j]; qz[j] = nz[j]; }
         const int64_t w = t / p.S;
         if (t == w * p.S && w >= a.w_lo && w < a.w_hi) {
             const double* mrow = a.mu + ((w - a.mu_w0) * a.mu_stride + ac.part_off) * 3;

@@ -44,8 +44,10 @@ struct ItemDev {
     int32_t variant, pad;
 };
 
-// Threads of every parent-kernel CTA (the kernel sizes its shared tables by it).
+// Threads of every parent-kernel CTA and of every adjoint-kernel CTA (the
+// kernels size their shared tables by them).
 constexpr int kParentThreads = 64;
+constexpr int kAdjThreads = 128;
 
 // One warp of the parent kernel: `count` parents, chains
 // parent_items[first .. first+count-1], each on G lanes.

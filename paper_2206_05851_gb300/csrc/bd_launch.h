@@ -33,13 +33,12 @@ cudaError_t persist_blocks_per_sm_f64(int variant, int* n);
 size_t persist_smem_f32(int variant);     // dynamic shared memory per CTA
 size_t persist_smem_f64(int variant);
 
-// Adjoint kernels (bd_adjoint.cuh), launched with kAdjThreads threads: the
+// Adjoint kernels (bd_adjoint.cuh), launched with kAdjThreads threads (bd_device.cuh): the
 // parent kernels exist for every tile of kTiles, the replica-window kernel
 // for the tiles of kAdjTiles.
 enum { ADJ_PARENT_RECOMPUTE = 0, ADJ_REPLICA_WINDOW = 1, ADJ_PARENT_BACKWARD = 2 };
 static const int kAdjTiles[] = {4, 7, 16};
 static const int kNumAdjTiles = 3;
-static const int kAdjThreads = 128;
 const void* adj_func_f32(int kind, int L);
 const void* adj_func_f64(int kind, int L);
 
