@@ -102,10 +102,16 @@ struct bd_ctx {
     int64_t adj_stride = 0, rep_batch = 0;
     AdjChain* d_adj = nullptr;
     ItemDev* d_adj_items = nullptr;
-    void* d_segbuf = nullptr;
+    void* d_seg[2] = {nullptr, nullptr};    // parent segments, alternating
     void* d_repbuf = nullptr;
     void* d_lamP = nullptr;
-    double* d_mu = nullptr;
+    double* d_mu[2] = {nullptr, nullptr};   // window sensitivities, alternating batches
+    // the parent's backward sweeps run on their own stream, overlapping the
+    // next batch of replica windows; events order the shared buffers
+    cudaStream_t adj_stream = nullptr;
+    cudaEvent_t ev_init = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_win[2] = {nullptr, nullptr}, ev_mu_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_seg_free[2] = {nullptr, nullptr};
     double* d_gls = nullptr;
     double* d_grad = nullptr;
     double* d_G = nullptr;
@@ -631,6 +637,12 @@ void release(bd_ctx* ctx)
     drop_graph(ctx);
     for (int i = 0; i < 3; ++i)
         if (ctx->idle_ev[i]) { cudaEventDestroy(ctx->idle_ev[i]); ctx->idle_ev[i] = nullptr; }
+    cudaEvent_t* evs[] = {&ctx->ev_init, &ctx->ev_done, &ctx->ev_win[0], &ctx->ev_win[1],
+                          &ctx->ev_mu_free[0], &ctx->ev_mu_free[1], &ctx->ev_seg_free[0],
+                          &ctx->ev_seg_free[1]};
+    for (cudaEvent_t* e : evs)
+        if (*e) { cudaEventDestroy(*e); *e = nullptr; }
+    if (ctx->adj_stream) { cudaStreamDestroy(ctx->adj_stream); ctx->adj_stream = nullptr; }
     for (void* p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
     cudaGetLastError();
@@ -822,22 +834,35 @@ bd_status adj_plan(bd_ctx* ctx)
 }
 
 // Work buffers of bd_adjoint: a K-row parent segment, the parent adjoint,
-// and replica-window batches sized to about 4 GiB.
+// and replica-window batches sized to a quarter of the free device memory
+// (between 1 and 32 GiB).
 bd_status adj_buffers(bd_ctx* ctx)
 {
-    if (ctx->d_segbuf) return BD_OK;
+    if (ctx->d_seg[0]) return BD_OK;
     const int64_t K = ctx->cfg.checkpoint_steps, S = ctx->cfg.window_steps, M = ctx->M;
     const size_t per_window = ctx->tsize * 3 * (size_t)ctx->state_bonds * (size_t)(S + 1) +
-                              sizeof(double) * 3 * (size_t)ctx->adj_stride;
-    const int64_t budget = 4ll << 30;
+                              sizeof(double) * 3 * 2 * (size_t)ctx->adj_stride;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    const int64_t budget = std::min<int64_t>(32ll << 30, std::max<int64_t>(1ll << 30, (int64_t)(free_b / 4)));
     ctx->rep_batch = std::max<int64_t>(1, std::min<int64_t>({K / S, 65535, budget / (int64_t)per_window}));
+    BD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->adj_stream, cudaStreamNonBlocking));
+    cudaEvent_t* evs[] = {&ctx->ev_init, &ctx->ev_done, &ctx->ev_win[0], &ctx->ev_win[1],
+                          &ctx->ev_mu_free[0], &ctx->ev_mu_free[1], &ctx->ev_seg_free[0],
+                          &ctx->ev_seg_free[1]};
+    for (cudaEvent_t* e : evs) BD_CUDA(ctx, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     bd_status s;
-    if ((s = dalloc(ctx, &ctx->d_segbuf, ctx->tsize * 3 * (size_t)M * (size_t)K)) != BD_OK) return s;
+    for (int b = 0; b < 2; ++b) {
+        if ((s = dalloc(ctx, &ctx->d_seg[b], ctx->tsize * 3 * (size_t)M * (size_t)K)) != BD_OK) return s;
+        if ((s = dalloc(ctx, (void**)&ctx->d_mu[b], sizeof(double) * 3 * (size_t)ctx->adj_stride *
+                                                        (size_t)ctx->rep_batch)) != BD_OK) return s;
+    }
     if ((s = dalloc(ctx, &ctx->d_lamP, ctx->tsize * 3 * (size_t)M)) != BD_OK) return s;
     if ((s = dalloc(ctx, &ctx->d_repbuf, ctx->tsize * 3 * (size_t)ctx->state_bonds * (size_t)(S + 1) *
                                              (size_t)ctx->rep_batch)) != BD_OK) return s;
-    if ((s = dalloc(ctx, (void**)&ctx->d_mu, sizeof(double) * 3 * (size_t)ctx->adj_stride *
-                                                 (size_t)ctx->rep_batch)) != BD_OK) return s;
     if ((s = dalloc(ctx, (void**)&ctx->d_gls, sizeof(double) * (size_t)ctx->cfg.n_chains)) != BD_OK) return s;
     return dalloc(ctx, (void**)&ctx->d_grad, sizeof(double) * 3 * (size_t)ctx->cfg.n_chains);
 }
@@ -859,24 +884,24 @@ bd_status keep_checkpoints(bd_ctx* ctx, int64_t w_first, int64_t w_end)
     return BD_OK;
 }
 
-bd_status adj_launch(bd_ctx* ctx, int kind, int L, dim3 grid, AdjParams* a)
+bd_status adj_launch(bd_ctx* ctx, int kind, int L, dim3 grid, AdjParams* a, cudaStream_t st)
 {
     const void* fn = ctx->f64 ? adj_func_f64(kind, L) : adj_func_f32(kind, L);
     if (!fn) return fail(ctx, BD_E_INVALID, "no adjoint kernel %d for tile %d", kind, L);
     void* args[1] = {a};
-    BD_CUDA(ctx, cudaLaunchKernel(fn, grid, dim3(kAdjThreads), args, 0, ctx->stream));
+    BD_CUDA(ctx, cudaLaunchKernel(fn, grid, dim3(kAdjThreads), args, 0, st));
     ++ctx->launches;
     return BD_OK;
 }
 
 // Parent kernels of the adjoint over every parent tile.
-bd_status adj_parents(bd_ctx* ctx, int kind, AdjParams a)
+bd_status adj_parents(bd_ctx* ctx, int kind, AdjParams a, cudaStream_t st)
 {
     for (const ParClass& pc : ctx->par_classes) {
         a.sp.parent_warps = ctx->d_parent_warps + pc.warp_begin;
         a.sp.n_parent_warps = pc.warp_count;
         const int per_cta = kAdjThreads / 32;
-        bd_status s = adj_launch(ctx, kind, pc.L, dim3((pc.warp_count + per_cta - 1) / per_cta), &a);
+        bd_status s = adj_launch(ctx, kind, pc.L, dim3((pc.warp_count + per_cta - 1) / per_cta), &a, st);
         if (s != BD_OK) return s;
     }
     return BD_OK;
@@ -1311,12 +1336,10 @@ bd_status bd_adjoint(bd_ctx* ctx, const double* grad_rsf, const double* grad_log
         a.sp = base_params(ctx);
         a.adj = ctx->d_adj;
         a.ckpt = ctx->d_ckpt;
-        a.segbuf = ctx->d_segbuf;
         a.repbuf = ctx->d_repbuf;
         a.state_bonds = ctx->state_bonds;
         a.lamP = ctx->d_lamP;
         a.G = ctx->d_G;
-        a.mu = ctx->d_mu;
         a.mu_stride = ctx->adj_stride;
         a.w_lo = w_lo;
         a.w_hi = w_hi;
@@ -1324,35 +1347,54 @@ bd_status bd_adjoint(bd_ctx* ctx, const double* grad_rsf, const double* grad_log
         const int64_t t_max = (w_hi - 1) * S;           // start of the last window
         const int64_t j_max = (t_max - ctx->origin) / K;
         const int per_cta = kAdjThreads / 32;
+        cudaStream_t S0 = ctx->stream, S1 = ctx->adj_stream;
+        BD_CUDA(ctx, cudaEventRecord(ctx->ev_init, S0));
+        BD_CUDA(ctx, cudaStreamWaitEvent(S1, ctx->ev_init, 0));
+        int64_t q = 0;                                  // window batches so far
         for (int64_t j = j_max; j >= 0; --j) {
-            // parent states of steps [seg_t0, seg_t0 + n) from checkpoint j
+            // parent states of steps [seg_t0, seg_t0 + n) from checkpoint j,
+            // into the segment buffer that segment j + 2 used
+            const int sb = (int)(j & 1);
             const int64_t seg_t0 = ctx->origin + j * K;
             const int64_t n = (j == j_max) ? t_max - seg_t0 + 1 : K;
+            a.segbuf = ctx->d_seg[sb];
             a.seg_t0 = seg_t0;
             a.ckpt_index = j;
             a.t0 = seg_t0;
             a.n_steps = (int32_t)(n - 1);
-            if ((s = adj_parents(ctx, ADJ_PARENT_RECOMPUTE, a)) != BD_OK) return s;
-            // windows starting in the segment, in batches from the top down;
-            // after each batch the parent sweeps back over the batch's steps
+            BD_CUDA(ctx, cudaStreamWaitEvent(S0, ctx->ev_seg_free[sb], 0));
+            if ((s = adj_parents(ctx, ADJ_PARENT_RECOMPUTE, a, S0)) != BD_OK) return s;
+            // windows starting in the segment, in batches from the top down
+            // (context stream); after each batch the parent sweeps back over
+            // the batch's steps (adjoint stream), overlapping the next batch
             const int64_t wa = seg_t0 / S, wb = std::min(w_hi, (seg_t0 + n - 1) / S + 1);
-            for (int64_t b1 = wb; b1 > wa;) {
+            for (int64_t b1 = wb; b1 > wa; ++q) {
                 const int64_t b0 = std::max(wa, b1 - ctx->rep_batch);
+                const int mb = (int)(q & 1);
+                a.mu = ctx->d_mu[mb];
                 a.mu_w0 = b0;
                 a.w_batch0 = b0;
+                BD_CUDA(ctx, cudaStreamWaitEvent(S0, ctx->ev_mu_free[mb], 0));
                 for (const AdjClass& ac : ctx->adj_classes) {
                     a.items = ctx->d_adj_items + ac.item_begin;
                     a.n_items = ac.item_count;
                     const dim3 grid((unsigned)((ac.item_count + per_cta - 1) / per_cta), (unsigned)(b1 - b0));
-                    if ((s = adj_launch(ctx, ADJ_REPLICA_WINDOW, ac.L, grid, &a)) != BD_OK) return s;
+                    if ((s = adj_launch(ctx, ADJ_REPLICA_WINDOW, ac.L, grid, &a, S0)) != BD_OK) return s;
                 }
+                BD_CUDA(ctx, cudaEventRecord(ctx->ev_win[mb], S0));
+                BD_CUDA(ctx, cudaStreamWaitEvent(S1, ctx->ev_win[mb], 0));
                 const int64_t t_lo = b0 * S, t_hi = std::min(b1 * S, seg_t0 + n);
-                a.t0 = t_lo;
-                a.n_steps = (int32_t)(t_hi - t_lo);
-                if ((s = adj_parents(ctx, ADJ_PARENT_BACKWARD, a)) != BD_OK) return s;
+                AdjParams ab = a;
+                ab.t0 = t_lo;
+                ab.n_steps = (int32_t)(t_hi - t_lo);
+                if ((s = adj_parents(ctx, ADJ_PARENT_BACKWARD, ab, S1)) != BD_OK) return s;
+                BD_CUDA(ctx, cudaEventRecord(ctx->ev_mu_free[mb], S1));
                 b1 = b0;
             }
+            BD_CUDA(ctx, cudaEventRecord(ctx->ev_seg_free[sb], S1));
         }
+        BD_CUDA(ctx, cudaEventRecord(ctx->ev_done, S1));
+        BD_CUDA(ctx, cudaStreamWaitEvent(S0, ctx->ev_done, 0));
     }
     s = deliver(ctx, grad_params, ctx->d_grad, sizeof(double) * 3 * (size_t)C, is_device_ptr(grad_params));
     if (s != BD_OK) return s;
