@@ -62,7 +62,9 @@ struct bd_ctx {
     int64_t* d_pair_all = nullptr;      // [n_chains + 1] prefix of R + 1 per chain
     void* d_state = nullptr;
     void* d_snap = nullptr;
-    double* d_part = nullptr;
+    double* d_part = nullptr;           // [part_ring][part_stride] per-group partial sums
+    double* d_rsf = nullptr;            // [max_windows][M] replica-averaged force history
+    int32_t part_ring = 0;              // windows the partial ring holds (one chunk's + 1)
     double* d_tsf = nullptr;
     double* d_tsf_acc = nullptr;
     double* d_lam = nullptr;
@@ -79,6 +81,7 @@ struct bd_ctx {
     cudaGraphExec_t gexec = nullptr;
     std::vector<cudaGraphNode_t> par_nodes, rep_nodes;
     cudaGraphNode_t ev_nodes[3] = {nullptr, nullptr, nullptr};
+    cudaGraphNode_t fold_node = nullptr;     // partial sums -> RSF history, after the replicas
     cudaEvent_t idle_ev[3] = {nullptr, nullptr, nullptr};
     int n_sm = 0;
     void* d_io = nullptr;
@@ -436,6 +439,7 @@ StepParams base_params(const bd_ctx* ctx)
     p.state = ctx->d_state;
     p.snap = ctx->d_snap;
     p.part_hist = ctx->d_part;
+    p.part_ring = ctx->part_ring;
     p.tsf_hist = ctx->d_tsf;
     p.tsf_acc = ctx->d_tsf_acc;
     p.lam = ctx->d_lam;
@@ -506,6 +510,32 @@ cudaKernelNodeParams replica_node(const bd_ctx* ctx, size_t k, StepParams* rk, v
     return kp;
 }
 
+// Kernel-node parameters of the fold of windows [w0, w1) (grid of at least one block).
+cudaKernelNodeParams fold_node_params(const bd_ctx* ctx, int64_t w0, int64_t w1, FoldParams* fp,
+                                      void** args)
+{
+    fp->chains = ctx->d_chains;
+    fp->spring_chain = ctx->d_spring_chain;
+    fp->part = ctx->d_part;
+    fp->rsf = ctx->d_rsf;
+    fp->M = ctx->M;
+    fp->part_stride = ctx->part_stride;
+    fp->w0 = w0;
+    fp->w1 = w1;
+    fp->ring = ctx->part_ring;
+    fp->pad = 0;
+    args[0] = fp;
+    const int th = rsf_fold_threads();
+    const int64_t n = std::max<int64_t>(1, (w1 - w0) * ctx->M);
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void*>(rsf_fold_func());
+    kp.gridDim = dim3((unsigned)((n + th - 1) / th));
+    kp.blockDim = dim3(th);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    return kp;
+}
+
 void drop_graph(bd_ctx* ctx)
 {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
@@ -558,6 +588,12 @@ bd_status build_graph(bd_ctx* ctx)
     }
     BD_CUDA(ctx, cudaGraphAddEventRecordNode(&ctx->ev_nodes[2], ctx->graph, ctx->rep_nodes.data(),
                                              ctx->rep_nodes.size(), ctx->idle_ev[2]));
+    {
+        FoldParams fp;
+        void* args[1];
+        cudaKernelNodeParams kp = fold_node_params(ctx, 0, 0, &fp, args);
+        BD_CUDA(ctx, cudaGraphAddKernelNode(&ctx->fold_node, ctx->graph, &ctx->ev_nodes[2], 1, &kp));
+    }
     BD_CUDA(ctx, cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
     return BD_OK;
 }
@@ -597,8 +633,8 @@ bd_status apply_windows(bd_ctx* ctx)
     const int64_t done = ctx->step / ctx->cfg.window_steps;
     if (done > ctx->windows_detected) {
         ++ctx->launches;
-        BD_CUDA(ctx, run_window_criteria(ctx->d_chains, ctx->d_spring_chain, ctx->M, ctx->d_part,
-                                         ctx->part_stride, ctx->d_tsf, ctx->windows_detected, done,
+        BD_CUDA(ctx, run_window_criteria(ctx->d_chains, ctx->d_spring_chain, ctx->M, ctx->d_rsf,
+                                         ctx->d_tsf, ctx->windows_detected, done,
                                          ctx->cfg.window_steps, ctx->cfg.dt, ctx->cfg.thr_mask,
                                          ctx->cfg.bell_mask, ctx->d_exp1, ctx->d_lam,
                                          ctx->d_first_thr, ctx->d_first_bell, ctx->stream));
@@ -765,9 +801,9 @@ bd_status replan(bd_ctx* ctx)
     dfree(ctx, ctx->d_items, sizeof(ItemDev) * std::max<size_t>(old_items, 1));
     ctx->d_items = nullptr;
     if ((s = upload(ctx, &ctx->d_items, ctx->h_items)) != BD_OK) return s;
-    dfree(ctx, ctx->d_part, std::max<size_t>(sizeof(double) * (size_t)ctx->cfg.max_windows * (size_t)old_part, 16));
+    dfree(ctx, ctx->d_part, std::max<size_t>(sizeof(double) * (size_t)ctx->part_ring * (size_t)old_part, 16));
     ctx->d_part = nullptr;
-    if ((s = dalloc(ctx, (void**)&ctx->d_part, sizeof(double) * (size_t)ctx->cfg.max_windows * (size_t)ctx->part_stride)) != BD_OK)
+    if ((s = dalloc(ctx, (void**)&ctx->d_part, sizeof(double) * (size_t)ctx->part_ring * (size_t)ctx->part_stride)) != BD_OK)
         return s;
     dfree(ctx, ctx->d_queue, std::max<size_t>(sizeof(int32_t) * old_queue, 16));
     ctx->d_queue = nullptr;
@@ -976,7 +1012,9 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
         BD_TRY(upload(ctx, &ctx->d_pair_all, pair_all));
         BD_TRY(dalloc(ctx, &ctx->d_state, ctx->tsize * 3 * (size_t)ctx->state_bonds));
         BD_TRY(dalloc(ctx, &ctx->d_snap, ctx->tsize * 3 * (size_t)M * (size_t)ctx->chunk_windows));
-        BD_TRY(dalloc(ctx, (void**)&ctx->d_part, sizeof(double) * (size_t)W * (size_t)ctx->part_stride));
+        ctx->part_ring = (int32_t)(ctx->chunk_windows + 1);
+        BD_TRY(dalloc(ctx, (void**)&ctx->d_part, sizeof(double) * (size_t)ctx->part_ring * (size_t)ctx->part_stride));
+        BD_TRY(dalloc(ctx, (void**)&ctx->d_rsf, sizeof(double) * (size_t)W * (size_t)M));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_tsf, sizeof(double) * (size_t)W * (size_t)M));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_tsf_acc, sizeof(double) * (size_t)M));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_lam, sizeof(double) * 3 * (size_t)M));
@@ -1052,8 +1090,14 @@ bd_status bd_step(bd_ctx* ctx, int64_t n_steps)
             cudaKernelNodeParams kp = replica_node(ctx, k, &rp[k], &rargs[k]);
             BD_CUDA(ctx, cudaGraphExecKernelNodeSetParams(ctx->gexec, ctx->rep_nodes[k], &kp));
         }
+        {   // fold the windows this chunk completes, [t / S, chunk_end / S), into the RSF history
+            FoldParams fp;
+            void* fargs[1];
+            cudaKernelNodeParams kp = fold_node_params(ctx, t / S, chunk_end / S, &fp, fargs);
+            BD_CUDA(ctx, cudaGraphExecKernelNodeSetParams(ctx->gexec, ctx->fold_node, &kp));
+        }
         BD_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
-        ctx->launches += (int64_t)(ctx->par_nodes.size() + ctx->rep_nodes.size());
+        ctx->launches += (int64_t)(ctx->par_nodes.size() + ctx->rep_nodes.size() + 1);
         if (ctx->cfg.checkpoint_steps > 0) {
             bd_status s = keep_checkpoints(ctx, w_first, (chunk_end + S - 1) / S);
             if (s != BD_OK) return s;
@@ -1080,17 +1124,8 @@ bd_status bd_replica_average(bd_ctx* ctx, int64_t window, double* out)
     if (!ctx || !out) return ctx ? fail(ctx, BD_E_INVALID, "out is NULL") : BD_E_INVALID;
     if (window < 0 || window >= ctx->step / ctx->cfg.window_steps)
         return fail(ctx, BD_E_INVALID, "window %lld not completed", (long long)window);
-    const bool dev = is_device_ptr(out);
-    double* dst = out;
-    if (!dev) {
-        bd_status s = ensure_io(ctx, sizeof(double) * ctx->M);
-        if (s != BD_OK) return s;
-        dst = (double*)ctx->d_io;
-    }
-    ++ctx->launches;
-    BD_CUDA(ctx, run_rsf(ctx->d_chains, ctx->d_spring_chain, ctx->M, ctx->d_part, ctx->part_stride,
-                         window, dst, ctx->stream));
-    return deliver(ctx, out, dst, sizeof(double) * ctx->M, dev);
+    return deliver(ctx, out, ctx->d_rsf + window * ctx->M, sizeof(double) * ctx->M,
+                   is_device_ptr(out));
 }
 
 bd_status bd_time_average(bd_ctx* ctx, int64_t window, double* out)
@@ -1327,7 +1362,7 @@ bd_status bd_adjoint(bd_ctx* ctx, const double* grad_rsf, const double* grad_log
             gls = ctx->d_gls;
         }
         ++ctx->launches;
-        BD_CUDA(ctx, run_adj_seed(ctx->d_chains, ctx->d_spring_chain, M, ctx->d_part, ctx->part_stride, w_lo,
+        BD_CUDA(ctx, run_adj_seed(ctx->d_chains, ctx->d_spring_chain, M, ctx->d_rsf, w_lo,
                                   n_w, grs, gls, (int)S, ctx->cfg.dt, ctx->d_G, ctx->stream));
         BD_CUDA(ctx, cudaMemsetAsync(ctx->d_lamP, 0, ctx->tsize * 3 * (size_t)M, ctx->stream));
 

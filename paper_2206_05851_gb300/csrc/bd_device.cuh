@@ -70,7 +70,7 @@ struct StepParams {
     void* state;                // T [state_elems][3]
     void* snap;                 // T [chunk windows][M][3] parent at window starts
     int64_t w_snap0;            // window index of snapshot 0
-    double* part_hist;          // [max_windows][part_stride] per-group replica sums
+    double* part_hist;          // [part_ring][part_stride] per-group replica sums, window w at w % part_ring
     double* tsf_hist;           // [max_windows][M] parent window means
     double* tsf_acc;            // [M] parent's running sum inside the current window
     double* lam;                // [3][M] integrated Bell hazard
@@ -79,6 +79,7 @@ struct StepParams {
     const double* exp1;         // [3][M] Exp(1) thresholds
     unsigned long long* overext;  // [n_chains]
     int64_t part_stride, M;
+    int32_t part_ring, pad_ring;
     int64_t t0, n_steps;
     double dt, s_min;
     int32_t S, flags, thr_mask, bell_mask;
@@ -116,6 +117,17 @@ struct AdjParams {
     int64_t mu_w0, mu_stride;
     int64_t w_lo, w_hi;        // the objective's windows: w_lo <= w < w_hi
     double* grad;              // [n_chains][3] dObjective / d(rate, b, H)
+};
+
+// Fold of the per-group partial sums of windows [w0, w1) into the RSF
+// history: rsf[w][m] = (sum over the chain's groups, in group order) / R.
+struct FoldParams {
+    const ChainDev* chains;
+    const int32_t* spring_chain;
+    const double* part;          // [ring][part_stride]
+    double* rsf;                 // [max_windows][M]
+    int64_t M, part_stride, w0, w1;
+    int32_t ring, pad;
 };
 
 enum { CRIT_Q_ISF = 0, CRIT_Q_TSF = 1, CRIT_Q_RSF = 2 };

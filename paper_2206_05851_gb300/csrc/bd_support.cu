@@ -95,31 +95,32 @@ __global__ void positions_kernel(const ChainDev* chains, const int64_t* pair_off
     for (int i = 0; i < N; ++i) { r[3 * i] -= sx; r[3 * i + 1] -= sy; r[3 * i + 2] -= sz; }
 }
 
-__device__ __forceinline__ double rsf_of(const ChainDev& ch, const double* part_hist,
-                                         int64_t part_stride, int64_t w, int64_t i)
+// RSF of window w, spring i of a chain: the chain's per-group partial sums
+// (ring slot w % ring) in group order, over R.
+__device__ __forceinline__ double rsf_of(const ChainDev& ch, const double* part, int64_t part_stride,
+                                         int64_t slot, int64_t i)
 {
     const int nb = ch.N - 1;
-    const double* row = part_hist + w * part_stride + ch.part_off + i;
+    const double* row = part + slot * part_stride + ch.part_off + i;
     double acc = 0.0;
     for (int g = 0; g < ch.n_groups; ++g) acc += row[(int64_t)g * nb];
     return acc / (double)ch.R;
 }
 
-__global__ void rsf_kernel(const ChainDev* chains, const int32_t* spring_chain, int64_t M,
-                           const double* part_hist, int64_t part_stride, int64_t w, double* out)
+__global__ void rsf_fold_kernel(const FoldParams f)
 {
-    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= M) return;
-    const ChainDev ch = chains[spring_chain[m]];
-    out[m] = rsf_of(ch, part_hist, part_stride, w, m - ch.spr_off);
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (f.w1 - f.w0) * f.M) return;
+    const int64_t r = e / f.M, m = e - r * f.M, w = f.w0 + r;
+    const ChainDev ch = f.chains[f.spring_chain[m]];
+    f.rsf[w * f.M + m] = rsf_of(ch, f.part, f.part_stride, w % f.ring, m - ch.spr_off);
 }
 
 // Threshold and Bell criteria on the window profiles TSF and RSF of windows
 // [w0, w1): the force of window w is held over its S steps and the event is
 // dated at the window end (w + 1) S.
 __global__ void window_criteria_kernel(const ChainDev* chains, const int32_t* spring_chain,
-                                       int64_t M, const double* part_hist, int64_t part_stride,
-                                       const double* tsf_hist, int64_t w0, int64_t w1, int S,
+                                       int64_t M, const double* rsf_hist, const double* tsf_hist, int64_t w0, int64_t w1, int S,
                                        double dt, int thr_mask, int bell_mask, const double* exp1,
                                        double* lam, int64_t* first_thr, int64_t* first_bell)
 {
@@ -135,8 +136,7 @@ __global__ void window_criteria_kernel(const ChainDev* chains, const int32_t* sp
         int64_t ft = first_thr[q * M + m], fb = first_bell[q * M + m];
         const double E = exp1[q * M + m];
         for (int64_t w = w0; w < w1; ++w) {
-            const double f = (q == CRIT_Q_RSF) ? rsf_of(ch, part_hist, part_stride, w, i)
-                                               : tsf_hist[w * M + m];
+            const double f = (q == CRIT_Q_RSF) ? rsf_hist[w * M + m] : tsf_hist[w * M + m];
             const int64_t step = (w + 1) * (int64_t)S;
             if (thr && ft < 0 && f >= ch.f_c) ft = step;
             if (bell) {
@@ -155,8 +155,7 @@ __global__ void window_criteria_kernel(const ChainDev* chains, const int32_t* sp
 // log-survival of the RSF criterion, log S_c = -sum_w sum_i k0 exp(RSF dx) S dt
 // (Sec. III), the term grad_log_surv[c] * (-k0 dx exp(RSF dx) S dt).
 __global__ void adj_seed_kernel(const ChainDev* chains, const int32_t* spring_chain, int64_t M,
-                                const double* part_hist, int64_t part_stride, int64_t w_lo,
-                                int64_t n_w, const double* grad_rsf, const double* grad_log_surv,
+                                const double* rsf_hist, int64_t w_lo, int64_t n_w, const double* grad_rsf, const double* grad_log_surv,
                                 int S, double dt, double* G)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,7 +167,7 @@ __global__ void adj_seed_kernel(const ChainDev* chains, const int32_t* spring_ch
         const double gl = grad_log_surv[c];
         if (gl != 0.0) {
             const ChainDev ch = chains[c];
-            const double f = rsf_of(ch, part_hist, part_stride, w_lo + r, m - ch.spr_off);
+            const double f = rsf_hist[(w_lo + r) * M + m];
             g -= gl * ch.k0 * ch.dx * exp(f * ch.dx) * ((double)S * dt);
         }
     }
@@ -334,24 +333,17 @@ cudaError_t run_positions(bool f64, const ChainDev* chains, const int64_t* pair_
     return cudaGetLastError();
 }
 
-cudaError_t run_rsf(const ChainDev* chains, const int32_t* spring_chain, int64_t M,
-                    const double* part_hist, int64_t part_stride, int64_t w, double* out,
-                    cudaStream_t st)
-{
-    if (M == 0) return cudaSuccess;
-    rsf_kernel<<<blocks_for(M), kThreads, 0, st>>>(chains, spring_chain, M, part_hist, part_stride, w, out);
-    return cudaGetLastError();
-}
+const void* rsf_fold_func() { return (const void*)rsf_fold_kernel; }
+int rsf_fold_threads() { return kThreads; }
 
 cudaError_t run_window_criteria(const ChainDev* chains, const int32_t* spring_chain, int64_t M,
-                                const double* part_hist, int64_t part_stride,
-                                const double* tsf_hist, int64_t w0, int64_t w1, int S, double dt,
+                                const double* rsf_hist, const double* tsf_hist, int64_t w0, int64_t w1, int S, double dt,
                                 int thr_mask, int bell_mask, const double* exp1, double* lam,
                                 int64_t* first_thr, int64_t* first_bell, cudaStream_t st)
 {
     if (M == 0 || w1 <= w0) return cudaSuccess;
     window_criteria_kernel<<<blocks_for(M), kThreads, 0, st>>>(
-        chains, spring_chain, M, part_hist, part_stride, tsf_hist, w0, w1, S, dt, thr_mask,
+        chains, spring_chain, M, rsf_hist, tsf_hist, w0, w1, S, dt, thr_mask,
         bell_mask, exp1, lam, first_thr, first_bell);
     return cudaGetLastError();
 }
@@ -372,12 +364,12 @@ cudaError_t run_events(const ChainDev* chains, const int32_t* spring_chain, int6
 }
 
 cudaError_t run_adj_seed(const ChainDev* chains, const int32_t* spring_chain, int64_t M,
-                         const double* part_hist, int64_t part_stride, int64_t w_lo, int64_t n_w,
+                         const double* rsf_hist, int64_t w_lo, int64_t n_w,
                          const double* grad_rsf, const double* grad_log_surv, int S, double dt,
                          double* G, cudaStream_t st)
 {
     adj_seed_kernel<<<blocks_for(n_w * M), kThreads, 0, st>>>(
-        chains, spring_chain, M, part_hist, part_stride, w_lo, n_w, grad_rsf, grad_log_surv, S, dt, G);
+        chains, spring_chain, M, rsf_hist, w_lo, n_w, grad_rsf, grad_log_surv, S, dt, G);
     return cudaGetLastError();
 }
 

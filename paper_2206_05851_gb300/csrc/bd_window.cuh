@@ -286,7 +286,7 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
                 }
             }
             warp_window_sum<T>(wsm, nb, it.rep_count,
-                               p.part_hist + (int64_t)w * p.part_stride + ch.part_off + (int64_t)it.group * nb);
+                               p.part_hist + (int64_t)(w % p.part_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb);
             ++w;
         }
     }

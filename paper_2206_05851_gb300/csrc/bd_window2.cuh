@@ -272,7 +272,7 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
                 }
             }
             warp_window_sum<float>(wsm, nb, it.rep_count,
-                                   p.part_hist + (int64_t)w * p.part_stride + ch.part_off + (int64_t)it.group * nb);
+                                   p.part_hist + (int64_t)(w % p.part_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb);
             ++w;
         }
     }
