@@ -4,7 +4,8 @@ Each check compares the oracle with something the physics fixes, computed
 here independently: potentials differentiated numerically, the exact linear
 (Rouse) map of a Hookean chain under Euler-Maruyama, its exact mean and
 covariance after n steps, the FENE equilibrium law, and the stationary FENE
-dumbbell density in a potential flow evaluated by quadrature.
+dumbbell density in a potential flow evaluated by quadrature, and the
+stationary three-bead density in the same flow by importance sampling.
 """
 import math
 
@@ -218,3 +219,37 @@ def test_fene_dumbbell_in_uniaxial_flow_matches_quadrature():
     sd = (Q[:, 0] ** 2).std() / math.sqrt(R)
     assert abs(est - qx2) < 5 * sd + 0.01 * qx2
     assert qx2 > 1.3          # the flow really stretches the dumbbell here
+
+
+def test_fene_three_bead_chain_in_uniaxial_flow_matches_stationary_density():
+    # Three free-draining beads in a potential flow: with bead diffusivity
+    # 1/4 the stationary density of the internal coordinates is
+    # exp(-U + 2 sum_i r_i . kappa . r_i) in the centre-of-mass frame, which
+    # for bonds Q1, Q2 is p0(Q1) p0(Q2) exp(4/3 (Q1.k.Q1 + Q2.k.Q2 + Q1.k.Q2))
+    # with p0 the FENE equilibrium density. Its moments by importance
+    # sampling from p0 (exact rejection sampler) against a long ensemble run.
+    b, eps = 20.0, 0.1
+    rng = np.random.default_rng(11)
+    n = 400_000
+    q1 = I.sample_connectors(rng, n, I.SPRING_FENE, 1.0, b)
+    q2 = I.sample_connectors(rng, n, I.SPRING_FENE, 1.0, b)
+    kq = lambda a, c: eps * (a[:, 0] * c[:, 0] - 0.5 * a[:, 1] * c[:, 1] - 0.5 * a[:, 2] * c[:, 2])
+    logw = (4.0 / 3.0) * (kq(q1, q1) + kq(q2, q2) + kq(q1, q2))
+    w = np.exp(logw - logw.max())
+    w /= w.sum()
+    want_xx = float(np.sum(w * 0.5 * (q1[:, 0] ** 2 + q2[:, 0] ** 2)))
+    want_x12 = float(np.sum(w * q1[:, 0] * q2[:, 0]))
+    # the oracle: 8 chains x 1000 independent replicas, one window of n steps from a straight start
+    R, dt, steps = 1000, 2e-3, 15000
+    chains = [_chain(3, spring=I.SPRING_FENE, b=b, flow=I.FLOW_UNIAXIAL, rate=eps, R=R)
+              for _ in range(8)]
+    out = O.run(chains, dt, steps, steps, seed=33, pos0=np.zeros((24, 3)), thr_mask=0,
+                bell_mask=0, n_threads=8)
+    Q = np.diff(out["rep"].reshape(8 * R, 3, 3), axis=1)          # [replica][bond][3]
+    # (halving the cross term of the density would move <Q1x Q2x> by about six standard errors)
+    xx = 0.5 * (Q[:, 0, 0] ** 2 + Q[:, 1, 0] ** 2)
+    x12 = Q[:, 0, 0] * Q[:, 1, 0]
+    for est, want in ((xx, want_xx), (x12, want_x12)):
+        sd = est.std() / math.sqrt(est.size)
+        assert abs(est.mean() - want) < 5 * sd + 0.02 * abs(want), (est.mean(), want, sd)
+    assert want_x12 > 0.1        # the flow couples the two bonds
