@@ -64,7 +64,7 @@ struct bd_ctx {
     void* d_snap = nullptr;
     double* d_part = nullptr;           // [part_ring][part_stride] per-group partial sums
     double* d_rsf = nullptr;            // [max_windows][M] replica-averaged force history
-    int32_t part_ring = 0;              // windows the partial ring holds (one chunk's + 1)
+    int32_t part_ring = 0;              // windows the snapshot and partial rings hold (one chunk's + 1)
     double* d_tsf = nullptr;
     double* d_tsf_acc = nullptr;
     double* d_lam = nullptr;
@@ -439,7 +439,7 @@ StepParams base_params(const bd_ctx* ctx)
     p.state = ctx->d_state;
     p.snap = ctx->d_snap;
     p.part_hist = ctx->d_part;
-    p.part_ring = ctx->part_ring;
+    p.win_ring = ctx->part_ring;
     p.tsf_hist = ctx->d_tsf;
     p.tsf_acc = ctx->d_tsf_acc;
     p.lam = ctx->d_lam;
@@ -464,11 +464,11 @@ StepParams base_params(const bd_ctx* ctx)
 
 // Kernel-node parameters of the chunk graph for one chunk [t0, t0 + n).
 // `pp` / `rp` hold one StepParams per node (kernelParams point into them).
-void chunk_params(const bd_ctx* ctx, int64_t t0, int64_t n, int64_t w0,
-                  std::vector<StepParams>& pp, std::vector<StepParams>& rp)
+void chunk_params(const bd_ctx* ctx, int64_t t0, int64_t n, std::vector<StepParams>& pp,
+                  std::vector<StepParams>& rp)
 {
     StepParams p = base_params(ctx);
-    p.t0 = t0; p.n_steps = n; p.w_snap0 = w0;
+    p.t0 = t0; p.n_steps = n;
     pp.assign(ctx->par_classes.size(), p);
     for (size_t k = 0; k < ctx->par_classes.size(); ++k) {
         const ParClass& pc = ctx->par_classes[k];
@@ -557,7 +557,7 @@ bd_status build_graph(bd_ctx* ctx)
         if (!ctx->idle_ev[i]) BD_CUDA(ctx, cudaEventCreate(&ctx->idle_ev[i]));
     BD_CUDA(ctx, cudaGraphCreate(&ctx->graph, 0));
     std::vector<StepParams> pp, rp;
-    chunk_params(ctx, 0, 0, 0, pp, rp);
+    chunk_params(ctx, 0, 0, pp, rp);
     cudaGraphNode_t prev;
     BD_CUDA(ctx, cudaGraphAddEventRecordNode(&ctx->ev_nodes[0], ctx->graph, nullptr, 0, ctx->idle_ev[0]));
     cudaMemsetParams ms = {};
@@ -755,7 +755,6 @@ bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost
         p.S = 1 << 30;                 // no window starts or ends inside the probe
         p.t0 = 1;
         p.n_steps = probe_steps;
-        p.w_snap0 = 0;
         void* args[1] = {&p};
         const void* fn = ctx->f64 ? persist_func_f64(v) : persist_func_f32(v);
         const dim3 grid((unsigned)std::max<size_t>(1, std::min<size_t>((items.size() + threads / 32 - 1) / (threads / 32), (size_t)per_sm * ctx->n_sm)));
@@ -914,7 +913,7 @@ bd_status keep_checkpoints(bd_ctx* ctx, int64_t w_first, int64_t w_end)
         if (t < 0 || t % K) continue;
         const int64_t j = t / K;
         if (j >= ctx->n_ckpt) continue;
-        BD_CUDA(ctx, cudaMemcpyAsync((char*)ctx->d_ckpt + j * row, (const char*)ctx->d_snap + (w - w_first) * row,
+        BD_CUDA(ctx, cudaMemcpyAsync((char*)ctx->d_ckpt + j * row, (const char*)ctx->d_snap + (w % ctx->part_ring) * row,
                                      row, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     return BD_OK;
@@ -1011,7 +1010,7 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
         BD_TRY(upload(ctx, &ctx->d_pair_parent, pair_parent));
         BD_TRY(upload(ctx, &ctx->d_pair_all, pair_all));
         BD_TRY(dalloc(ctx, &ctx->d_state, ctx->tsize * 3 * (size_t)ctx->state_bonds));
-        BD_TRY(dalloc(ctx, &ctx->d_snap, ctx->tsize * 3 * (size_t)M * (size_t)ctx->chunk_windows));
+        BD_TRY(dalloc(ctx, &ctx->d_snap, ctx->tsize * 3 * (size_t)M * (size_t)(ctx->chunk_windows + 1)));
         ctx->part_ring = (int32_t)(ctx->chunk_windows + 1);
         BD_TRY(dalloc(ctx, (void**)&ctx->d_part, sizeof(double) * (size_t)ctx->part_ring * (size_t)ctx->part_stride));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_rsf, sizeof(double) * (size_t)W * (size_t)M));
@@ -1081,7 +1080,7 @@ bd_status bd_step(bd_ctx* ctx, int64_t n_steps)
     while (t < t_end) {
         const int64_t w_first = (t + S - 1) / S;
         const int64_t chunk_end = std::min(t_end, (w_first + ctx->chunk_windows) * S);
-        chunk_params(ctx, t, chunk_end - t, w_first, pp, rp);
+        chunk_params(ctx, t, chunk_end - t, pp, rp);
         for (size_t k = 0; k < ctx->par_nodes.size(); ++k) {
             cudaKernelNodeParams kp = parent_node(ctx, k, &pp[k], &pargs[k]);
             BD_CUDA(ctx, cudaGraphExecKernelNodeSetParams(ctx->gexec, ctx->par_nodes[k], &kp));

@@ -68,9 +68,8 @@ struct StepParams {
     const ParentWarp* parent_warps;  // parent kernel: warps of this launch
     int32_t n_parent_warps;
     void* state;                // T [state_elems][3]
-    void* snap;                 // T [chunk windows][M][3] parent at window starts
-    int64_t w_snap0;            // window index of snapshot 0
-    double* part_hist;          // [part_ring][part_stride] per-group replica sums, window w at w % part_ring
+    void* snap;                 // T [win_ring][M][3] parent at the start of window w, row w % win_ring
+    double* part_hist;          // [win_ring][part_stride] per-group replica sums, window w at w % win_ring
     double* tsf_hist;           // [max_windows][M] parent window means
     double* tsf_acc;            // [M] parent's running sum inside the current window
     double* lam;                // [3][M] integrated Bell hazard
@@ -79,7 +78,7 @@ struct StepParams {
     const double* exp1;         // [3][M] Exp(1) thresholds
     unsigned long long* overext;  // [n_chains]
     int64_t part_stride, M;
-    int32_t part_ring, pad_ring;
+    int32_t win_ring, pad_ring;  // windows one chunk touches (started or ended) + 1
     int64_t t0, n_steps;
     double dt, s_min;
     int32_t S, flags, thr_mask, bell_mask;

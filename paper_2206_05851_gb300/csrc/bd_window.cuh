@@ -214,7 +214,7 @@ __device__ __forceinline__ void store_bonds(const T (&qx)[L], const T (&qy)[L], 
 // ---------------------------------------------------------------------------
 // Replicas, one warp work item (one replica per lane run). Lane run s of the
 // warp is replica rep_begin + s + 1; state of replica k lives at
-// state[(state_off + k (N-1)) * 3 ...]. Snapshots: snap[((w - w_snap0) * M +
+// state[(state_off + k (N-1)) * 3 ...]. Snapshots: snap[((w % win_ring) * M +
 // spr_off + i) * 3 + d], written by the parent kernel at every window start
 // of the current chunk. wsm: this warp's scratch of kWarpScratch values.
 // ---------------------------------------------------------------------------
@@ -271,7 +271,7 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
 #pragma unroll 1
     for (uint32_t t = (uint32_t)p.t0; t < t_end; ++t) {
         if (s_in == 0)   // spawn: copy the halted parent (Sec. II)
-            load_bonds<T, L>(qx, qy, qz, snap + ((int64_t)(w - p.w_snap0) * p.M + ch.spr_off) * 3, lc);
+            load_bonds<T, L>(qx, qy, qz, snap + ((int64_t)(w % p.win_ring) * p.M + ch.spr_off) * 3, lc);
         floored += step_bonds<T, L, FAST, TAB>(qx, qy, qz, lc, k, (uint32_t)t, p, ptab);
         if (++s_in == p.S) {
             // one force sample per replica at the end of the evolution time
@@ -286,7 +286,7 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
                 }
             }
             warp_window_sum<T>(wsm, nb, it.rep_count,
-                               p.part_hist + (int64_t)(w % p.part_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb);
+                               p.part_hist + (int64_t)(w % p.win_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb);
             ++w;
         }
     }
@@ -368,7 +368,7 @@ parent_kernel(const StepParams p)
 #pragma unroll 1
     for (int64_t t = p.t0; t < t_end; ++t) {
         if (s_in == 0)   // the conformation the replicas of window w start from
-            store_bonds<T, L>(qx, qy, qz, snap + ((w - p.w_snap0) * M + ch.spr_off) * 3, lc);
+            store_bonds<T, L>(qx, qy, qz, snap + ((w % p.win_ring) * M + ch.spr_off) * 3, lc);
         floored += step_bonds<T, L, FAST, true>(qx, qy, qz, lc, k, (uint32_t)t, p, my_tab);
         if (active) {
 #pragma unroll

@@ -247,7 +247,7 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
 #pragma unroll 1
     for (uint32_t t = (uint32_t)p.t0; t < t_end; ++t) {
         if (s_in == 0) {  // spawn both replicas from the halted parent (Sec. II)
-            const float* src = snap + ((int64_t)(w - p.w_snap0) * p.M + ch.spr_off) * 3;
+            const float* src = snap + ((int64_t)(w % p.win_ring) * p.M + ch.spr_off) * 3;
 #pragma unroll
             for (int j = 0; j < L; ++j) {
                 const int i = lc.bead0 + j;
@@ -272,7 +272,7 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
                 }
             }
             warp_window_sum<float>(wsm, nb, it.rep_count,
-                                   p.part_hist + (int64_t)(w % p.part_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb);
+                                   p.part_hist + (int64_t)(w % p.win_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb);
             ++w;
         }
     }
