@@ -444,9 +444,41 @@ int ora_max_threads(void)
 /* A run that ends inside a window evolves the replicas and the parent      */
 /* through the partial window and takes no window sample.                   */
 /* ------------------------------------------------------------------------ */
-int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
-            double* rsf, double* tsf, double* lam, int64_t* first_thr, int64_t* first_bell,
-            double* exp1, int64_t* overext, int n_threads)
+/* Conformation difference of Eq. 5 (Sec. III) between a replica rk and the
+ * halted parent P_c it was formed from, both in their own centre-of-mass
+ * frames: D(j, i) = |rhat_j^i(S, k) - rhat_j^i(P_c)|; dsum[j] = sum over beads.
+ * acc (may be NULL) receives += D(j, i). */
+static void eq5_difference(int N, const double* rk, const double* parent, double dsum[3],
+                           double* acc)
+{
+    double ck[3] = {0, 0, 0}, cp[3] = {0, 0, 0};
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < 3; ++j) { ck[j] += rk[3 * i + j]; cp[j] += parent[3 * i + j]; }
+    for (int j = 0; j < 3; ++j) { ck[j] /= N; cp[j] /= N; dsum[j] = 0.0; }
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const double d = fabs((rk[3 * i + j] - ck[j]) - (parent[3 * i + j] - cp[j]));
+            dsum[j] += d;
+            if (acc) acc[3 * i + j] += d;
+        }
+}
+
+/* z contribution to the radius of gyration of a conformation (Sec. III):
+ * sqrt(mean over beads of (z_i - z_cm)^2). */
+static double radius_gyration_z(int N, const double* r)
+{
+    double cz = 0.0;
+    for (int i = 0; i < N; ++i) cz += r[3 * i + 2];
+    cz /= N;
+    double s2 = 0.0;
+    for (int i = 0; i < N; ++i) s2 += (r[3 * i + 2] - cz) * (r[3 * i + 2] - cz);
+    return sqrt(s2 / N);
+}
+
+static int run_impl(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
+                    double* rsf, double* tsf, double* lam, int64_t* first_thr,
+                    int64_t* first_bell, double* exp1, int64_t* overext, double* dbar,
+                    double* dbead, double* rgz, int n_threads)
 {
     const int C = p->n_chains;
     const int S = p->window_steps;
@@ -454,13 +486,16 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
     int64_t* bead_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
     int64_t* spr_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
     int64_t* rep_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
-    bead_off[0] = spr_off[0] = rep_off[0] = 0;
+    int64_t* repc_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
+    bead_off[0] = spr_off[0] = rep_off[0] = repc_off[0] = 0;
     for (int c = 0; c < C; ++c) {
         bead_off[c + 1] = bead_off[c] + p->chains[c].n_beads;
         spr_off[c + 1] = spr_off[c] + p->chains[c].n_beads - 1;
         rep_off[c + 1] = rep_off[c] + (int64_t)p->chains[c].n_replicas * p->chains[c].n_beads;
+        repc_off[c + 1] = repc_off[c] + p->chains[c].n_replicas;
     }
     const int64_t M = spr_off[C];
+    const int64_t NB = bead_off[C], NR = repc_off[C];
 
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -480,6 +515,7 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
         double* rsum = (double*)malloc(sizeof(double) * (size_t)N);
         double* tsum = (double*)malloc(sizeof(double) * (size_t)N);
         double* E = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+        double* dacc = (double*)malloc(sizeof(double) * 3 * (size_t)N);
         int64_t nover = 0;
 
         for (int q = 0; q < 3; ++q)
@@ -497,6 +533,7 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
 
             /* RSF: halt the parent, spawn replicas, evolve them for S. */
             for (int i = 0; i + 1 < N; ++i) rsum[i] = 0.0;
+            for (int i = 0; i < 3 * N; ++i) dacc[i] = 0.0;
             for (int k = 1; k <= R; ++k) {
                 double* rk = rep + 3 * (size_t)N * (k - 1);
                 memcpy(rk, parent, sizeof(double) * 3 * (size_t)N);
@@ -510,7 +547,21 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
                 if (Sw == S) {
                     ora_tensions(ch, p->s_min, rk, f);
                     for (int i = 0; i + 1 < N; ++i) rsum[i] += f[i];
+                    if (dbar || dbead) {   /* Eq. 5 against the still-halted parent */
+                        double dsum[3];
+                        eq5_difference(N, rk, parent, dsum, dbead ? dacc : NULL);
+                        if (dbar)
+                            for (int j = 0; j < 3; ++j)
+                                dbar[(w * NR + repc_off[c] + k - 1) * 3 + j] = dsum[j] / N;
+                    }
                 }
+            }
+            if (Sw == S) {
+                if (dbead)
+                    for (int i = 0; i < N; ++i)
+                        for (int j = 0; j < 3; ++j)
+                            dbead[(w * NB + bead_off[c] + i) * 3 + j] = dacc[3 * i + j] / R;
+                if (rgz) rgz[w * C + c] = radius_gyration_z(N, parent);
             }
 
             /* Continue the parent through the same S steps. */
@@ -558,8 +609,33 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
         if (pos_rep)
             memcpy(pos_rep + 3 * rep_off[c], rep, sizeof(double) * 3 * (size_t)N * (size_t)R);
         overext[c] = nover;
-        free(rep); free(xi); free(f); free(rsum); free(tsum); free(E);
+        free(rep); free(xi); free(f); free(rsum); free(tsum); free(E); free(dacc);
     }
-    free(bead_off); free(spr_off); free(rep_off);
+    free(bead_off); free(spr_off); free(rep_off); free(repc_off);
     return 0;
+}
+
+int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
+            double* rsf, double* tsf, double* lam, int64_t* first_thr, int64_t* first_bell,
+            double* exp1, int64_t* overext, int n_threads)
+{
+    return run_impl(p, n_steps, pos, pos_rep, rsf, tsf, lam, first_thr, first_bell, exp1,
+                    overext, NULL, NULL, NULL, n_threads);
+}
+
+int ora_run_conformation(const ora_problem* p, int64_t n_steps, double* pos, double* dbar,
+                         double* dbead, double* rgz, int n_threads)
+{
+    if (p->n_chains <= 0) return 1;
+    int64_t M = 0;
+    for (int c = 0; c < p->n_chains; ++c) M += p->chains[c].n_beads - 1;
+    double* lam = (double*)calloc((size_t)(3 * M + 1), sizeof(double));
+    int64_t* ft = (int64_t*)malloc(sizeof(int64_t) * (size_t)(3 * M + 1));
+    int64_t* fb = (int64_t*)malloc(sizeof(int64_t) * (size_t)(3 * M + 1));
+    int64_t* ov = (int64_t*)malloc(sizeof(int64_t) * (size_t)p->n_chains);
+    for (int64_t m = 0; m < 3 * M; ++m) ft[m] = fb[m] = -1;
+    const int rc = run_impl(p, n_steps, pos, NULL, NULL, NULL, lam, ft, fb, NULL, ov, dbar,
+                            dbead, rgz, n_threads);
+    free(lam); free(ft); free(fb); free(ov);
+    return rc;
 }

@@ -67,6 +67,16 @@ int ora_run(const ora_problem* p, int64_t n_steps, double* pos, double* pos_rep,
             double* rsf, double* tsf, double* lam, int64_t* first_thr, int64_t* first_bell,
             double* exp1, int64_t* overext, int n_threads);
 
+/* The method as ora_run, returning the conformation diagnostics of Eq. 5
+ * (Sec. III) at every completed window w (W = n_steps / window_steps), any
+ * pointer may be NULL: dbar[W][sum R][3] the bead-mean |COM-frame position
+ * difference| between each replica at the window end and the halted parent
+ * it was formed from (replicas chain-major); dbead[W][sum N][3] the same per
+ * bead, averaged over the chain's replicas; rgz[W][C] the z contribution to
+ * the radius of gyration of the halted parent. pos is advanced in place. */
+int ora_run_conformation(const ora_problem* p, int64_t n_steps, double* pos, double* dbar,
+                         double* dbead, double* rgz, int n_threads);
+
 /* Criteria update for one sampled force value of spring m (used by ora_run;
  * exported so tests can drive kinetics with prescribed force histories). */
 void ora_criteria_update(int q, int thr_on, int bell_on, const ora_chain* ch, double f,

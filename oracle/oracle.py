@@ -84,6 +84,9 @@ def lib():
         _lib.ora_max_threads.restype = ctypes.c_int
         _lib.ora_rsf_tangent.argtypes = [P(_Problem), ctypes.c_int64, f64p, f64p, f64p, ctypes.c_int]
         _lib.ora_rsf_tangent.restype = ctypes.c_int
+        _lib.ora_run_conformation.argtypes = [P(_Problem), ctypes.c_int64, f64p, f64p, f64p, f64p,
+                                              ctypes.c_int]
+        _lib.ora_run_conformation.restype = ctypes.c_int
     return _lib
 
 
@@ -242,6 +245,34 @@ def run(chains, dt: float, window_steps: int, n_steps: int, seed: int, pos0: np.
         raise ValueError("oracle rejected the problem")
     return dict(pos=pos, rep=rep, rsf=rsf, tsf=tsf, lam=lam, first_thr=ft, first_bell=fb,
                 exp1=e1, overext=over)
+
+
+def conformation(chains, dt: float, window_steps: int, n_steps: int, seed: int,
+                 pos0: np.ndarray, identical_noise: bool = False,
+                 s_min: float = S_MIN_DEFAULT, n_threads: int = 1,
+                 chain_ids: Optional[Sequence[int]] = None):
+    """Eq. 5 diagnostics of every completed window: (dbar [W][sum R][3],
+    dbead [W][sum N][3], rgz [W][C]) - see ora_run_conformation."""
+    C = len(chains)
+    cs = (_Chain * C)(*[_chain_struct(c) for c in chains])
+    ids = None if chain_ids is None else np.ascontiguousarray(chain_ids, dtype=np.int32)
+    prob = _Problem(C, int(window_steps), cs, float(dt), int(seed), int(bool(identical_noise)),
+                    0, 0, float(s_min),
+                    _p(ids, ctypes.c_int32) if ids is not None
+                    else ctypes.POINTER(ctypes.c_int32)())
+    n_beads = sum(c.n_beads for c in chains)
+    n_rep = sum(c.n_replicas for c in chains)
+    nw = n_steps // window_steps
+    pos = np.ascontiguousarray(pos0, dtype=np.float64).copy().reshape(n_beads, 3)
+    dbar = np.zeros((nw, n_rep, 3))
+    dbead = np.zeros((nw, n_beads, 3))
+    rgz = np.zeros((nw, C))
+    rc = lib().ora_run_conformation(ctypes.byref(prob), int(n_steps), _p(pos, ctypes.c_double),
+                                    _p(dbar, ctypes.c_double), _p(dbead, ctypes.c_double),
+                                    _p(rgz, ctypes.c_double), int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle rejected the problem")
+    return dbar, dbead, rgz
 
 
 def rsf_tangent(chains, dt: float, window_steps: int, n_steps: int, seed: int, pos0: np.ndarray,
