@@ -68,8 +68,10 @@ enum { BD_PREC_FP64 = 0, BD_PREC_FP32 = 1 };
 /* Criterion bits (also the criterion index q = 0, 1, 2 of bd_event). */
 enum { BD_CRIT_ISF = 1, BD_CRIT_TSF = 2, BD_CRIT_RSF = 4 };
 /* BD_FLAG_IDENTICAL_NOISE: every replica draws the parent's noise (slot 0),
- * so replicas reproduce the parent exactly - a consistency check. */
-enum { BD_FLAG_IDENTICAL_NOISE = 1 };
+ * so replicas reproduce the parent exactly - a consistency check.
+ * BD_FLAG_CONFORMATION: at every window end also compute the conformation
+ * diagnostics of Eq. 5 (bd_conformation). */
+enum { BD_FLAG_IDENTICAL_NOISE = 1, BD_FLAG_CONFORMATION = 2 };
 
 /* One parent chain with its replica set. */
 typedef struct {
@@ -150,6 +152,21 @@ bd_status bd_step(bd_ctx* ctx, int64_t n_steps);
  * out [M] float64 = mean over each chain's replicas of the spring force at the
  * window end, reduced in float64 in a fixed order. */
 bd_status bd_replica_average(bd_ctx* ctx, int64_t window, double* out);
+
+/* Conformation diagnostics of one completed window (Eq. 5, Sec. III); needs
+ * BD_FLAG_CONFORMATION at bd_create (BD_E_STATE otherwise). With r-hat the
+ * bead positions in a chain's centre-of-mass frame and P_c the halted parent
+ * the replicas of the window were formed from:
+ *   dbar  [sum_c R_c][3]  per replica k (chains in order, replicas 1..R):
+ *                         (1/N) sum_i |rhat_i(S, k) - rhat_i(P_c)| per axis;
+ *   dbead [sum_c N_c][3]  per bead i: the same difference averaged over the
+ *                         chain's replicas (float64 sums in replica order);
+ *   rgz   [n_chains]      z contribution to P_c's radius of gyration,
+ *                         sqrt((1/N) sum_i zhat_i^2).
+ * Computed at every window end by the replica kernels from the bonds (the
+ * positions are their prefix sums), in float64. Any pointer may be NULL;
+ * host or device arrays. */
+bd_status bd_conformation(bd_ctx* ctx, int64_t window, double* dbar, double* dbead, double* rgz);
 
 /* Time-averaged spring force of one completed window (Sec. II, TSF):
  * out [M] float64 = mean of the parent's spring force over the window's steps. */

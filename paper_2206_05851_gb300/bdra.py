@@ -25,6 +25,7 @@ BD_OK, BD_E_INVALID, BD_E_CUDA, BD_E_OOM, BD_E_STATE, BD_E_TIMEOUT, BD_E_CAPACIT
 BD_PREC_FP64, BD_PREC_FP32 = 0, 1
 BD_CRIT_ISF, BD_CRIT_TSF, BD_CRIT_RSF = 1, 2, 4
 BD_FLAG_IDENTICAL_NOISE = 1
+BD_FLAG_CONFORMATION = 2
 
 
 class BdError(RuntimeError):
@@ -88,6 +89,7 @@ def load() -> ctypes.CDLL:
         "bd_step": ([vp, ctypes.c_int64], st),
         "bd_replica_average": ([vp, ctypes.c_int64, vp], st),
         "bd_time_average": ([vp, ctypes.c_int64, vp], st),
+        "bd_conformation": ([vp, ctypes.c_int64, vp, vp, vp], st),
         "bd_detect_events": ([vp, vp, ctypes.c_int64, P(ctypes.c_int64), vp], st),
         "bd_get_kinetics": ([vp, vp, vp, vp], st),
         "bd_get_positions": ([vp, ctypes.c_int32, vp, P(ctypes.c_int64)], st),
@@ -199,6 +201,13 @@ def bd_replica_average(ctx: int, window: int, out) -> None:
 def bd_time_average(ctx: int, window: int, out) -> None:
     M = bd_get_info(ctx).n_springs
     _check(load().bd_time_average(ctx, int(window), _need(out, 8 * M, "out")), ctx)
+
+
+def bd_conformation(ctx: int, window: int, dbar=None, dbead=None, rgz=None) -> None:
+    """Eq. 5 diagnostics of a completed window into the given arrays (any may
+    be None): dbar [sum R][3], dbead [sum N][3], rgz [n_chains] float64."""
+    args = [_ptr(a)[0] if a is not None else None for a in (dbar, dbead, rgz)]
+    _check(load().bd_conformation(ctx, int(window), *args), ctx)
 
 
 def bd_detect_events(ctx: int, out, capacity: int, log_surv=None) -> int:
@@ -360,6 +369,15 @@ class Context:
 
     def plan(self):
         return bd_get_plan(self.ptr, len(self.chains), self.cfg.precision)
+
+    def conformation(self, window: int):
+        """(dbar [sum R][3], dbead [sum N][3], rgz [n_chains]) of a completed
+        window (needs BD_FLAG_CONFORMATION)."""
+        dbar = np.zeros((sum(c.n_replicas for c in self.chains), 3))
+        dbead = np.zeros((self.n_beads, 3))
+        rgz = np.zeros(len(self.chains))
+        bd_conformation(self.ptr, window, dbar, dbead, rgz)
+        return dbar, dbead, rgz
 
     def kinetics(self):
         haz = np.zeros((3, self.M))

@@ -1,7 +1,8 @@
 """Builds the CUDA library libbdra.so in-tree for sm_103a.
 
 The translation units compile in parallel: the float32 and float64
-instantiations of the parent / replica kernels and of the adjoint kernels
+instantiations of the parent / replica kernels (the replica kernels twice:
+without and with the Eq. 5 diagnostics) and of the adjoint kernels
 (with -fmad=false, so every fused multiply-add is the explicit one written
 in the source), the support kernels, the C ABI, the allocation-free
 event compaction and the Philox-round throughput probe. Only nvcc is needed; no CMake.
@@ -20,6 +21,7 @@ LIB = os.path.join(PKG, "libbdra.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 UNITS = [("bd_window_f32.cu", ["-fmad=false"]), ("bd_window_f64.cu", ["-fmad=false"]),
+         ("bd_window_f32c.cu", ["-fmad=false"]), ("bd_window_f64c.cu", ["-fmad=false"]),
          ("bd_adjoint_f32.cu", ["-fmad=false"]), ("bd_adjoint_f64.cu", ["-fmad=false"]),
          ("bd_support.cu", []), ("bd_api.cu", []), ("bd_noalloc.cu", []), ("bd_probe.cu", [])]
 

@@ -65,6 +65,14 @@ struct bd_ctx {
     double* d_part = nullptr;           // [part_ring][part_stride] per-group partial sums
     double* d_rsf = nullptr;            // [max_windows][M] replica-averaged force history
     int32_t part_ring = 0;              // windows the snapshot and partial rings hold (one chunk's + 1)
+    // conformation diagnostics of Eq. 5 (BD_FLAG_CONFORMATION)
+    bool conf = false;
+    int64_t n_rep = 0, bpart_stride = 0;
+    int32_t* d_bead_chain = nullptr;    // [sum N] chain of each bead
+    double* d_dbar = nullptr;           // [max_windows][sum R][3]
+    double* d_dpart = nullptr;          // [part_ring][bpart_stride][3]
+    double* d_dbead = nullptr;          // [max_windows][sum N][3]
+    double* d_rgz = nullptr;            // [max_windows][n_chains]
     double* d_tsf = nullptr;
     double* d_tsf_acc = nullptr;
     double* d_lam = nullptr;
@@ -273,7 +281,8 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
     if (!(cfg->s_min > 0 && cfg->s_min < 1)) return fail(ctx, BD_E_INVALID, "s_min must be in (0, 1)");
     if ((cfg->thr_mask & ~7) || (cfg->bell_mask & ~7))
         return fail(ctx, BD_E_INVALID, "criterion masks use bits 0..2 only");
-    if (cfg->flags & ~BD_FLAG_IDENTICAL_NOISE) return fail(ctx, BD_E_INVALID, "unknown flags");
+    if (cfg->flags & ~(BD_FLAG_IDENTICAL_NOISE | BD_FLAG_CONFORMATION))
+        return fail(ctx, BD_E_INVALID, "unknown flags");
     if (cfg->checkpoint_steps < 0 || (cfg->checkpoint_steps > 0 && cfg->checkpoint_steps % cfg->window_steps))
         return fail(ctx, BD_E_INVALID, "checkpoint_steps must be 0 or a positive multiple of window_steps");
     if (cfg->layout_hint < 0 || cfg->layout_hint > 2)
@@ -324,7 +333,7 @@ bd_status plan(bd_ctx* ctx)
     const bd_config& cfg = ctx->cfg;
     const int C = cfg.n_chains;
     ctx->h_chains.resize(C);
-    int64_t bead = 0, slot_bead = 0, bond = 0, spr = 0, part = 0;
+    int64_t bead = 0, slot_bead = 0, bond = 0, spr = 0, part = 0, rep = 0, bpart = 0;
     std::vector<ItemDev> items;
     std::vector<std::pair<std::pair<int, int>, int>> par;   // ((L, G), chain)
     for (int c = 0; c < C; ++c) {
@@ -336,6 +345,7 @@ bd_status plan(bd_ctx* ctx)
         h.N = d.n_beads; h.R = d.n_replicas; h.n_groups = vc.groups; h.pad = 0;
         h.bead_off = bead; h.slot_bead_off = slot_bead; h.state_off = bond;
         h.spr_off = spr; h.part_off = part;
+        h.rep_off = rep; h.bpart_off = bpart;
         h.H = d.H;
         h.Hinvb = d.spring == BD_SPRING_FENE ? d.H / d.b : 0.0;
         h.kxx = h.kyy = h.kzz = h.kxz = 0.0;
@@ -373,7 +383,11 @@ bd_status plan(bd_ctx* ctx)
         bond += (int64_t)(d.n_replicas + 1) * nb;
         spr += nb;
         part += (int64_t)vc.groups * nb;
+        rep += d.n_replicas;
+        bpart += (int64_t)vc.groups * d.n_beads;
     }
+    ctx->n_rep = rep;
+    ctx->bpart_stride = bpart;
     ctx->n_beads = bead; ctx->n_slot_beads = slot_bead; ctx->state_bonds = bond;
     ctx->M = spr; ctx->part_stride = part;
 
@@ -390,8 +404,8 @@ bd_status plan(bd_ctx* ctx)
     }
     for (VarClass& vc : ctx->var_classes) {
         int per_sm = 1;
-        cudaError_t e = ctx->f64 ? persist_blocks_per_sm_f64(vc.variant, &per_sm)
-                                 : persist_blocks_per_sm_f32(vc.variant, &per_sm);
+        cudaError_t e = ctx->f64 ? persist_blocks_per_sm_f64(vc.variant, ctx->conf, &per_sm)
+                                 : persist_blocks_per_sm_f32(vc.variant, ctx->conf, &per_sm);
         if (e != cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             return fail(ctx, BD_E_CUDA, "occupancy of variant %d: %s", vc.variant, cudaGetErrorString(e));
@@ -440,6 +454,12 @@ StepParams base_params(const bd_ctx* ctx)
     p.snap = ctx->d_snap;
     p.part_hist = ctx->d_part;
     p.win_ring = ctx->part_ring;
+    p.dbar = ctx->d_dbar;
+    p.dbead_part = ctx->d_dpart;
+    p.rgz = ctx->d_rgz;
+    p.n_rep = ctx->n_rep;
+    p.bpart_stride = ctx->bpart_stride;
+    p.n_chains = ctx->cfg.n_chains;
     p.tsf_hist = ctx->d_tsf;
     p.tsf_acc = ctx->d_tsf_acc;
     p.lam = ctx->d_lam;
@@ -502,7 +522,8 @@ cudaKernelNodeParams replica_node(const bd_ctx* ctx, size_t k, StepParams* rk, v
     const VarClass& vc = ctx->var_classes[k];
     args[0] = rk;
     cudaKernelNodeParams kp = {};
-    kp.func = const_cast<void*>(ctx->f64 ? persist_func_f64(vc.variant) : persist_func_f32(vc.variant));
+    kp.func = const_cast<void*>(ctx->f64 ? persist_func_f64(vc.variant, ctx->conf)
+                                         : persist_func_f32(vc.variant, ctx->conf));
     kp.gridDim = dim3(vc.grid);
     kp.blockDim = dim3(vc.threads);
     kp.sharedMemBytes = (unsigned)(ctx->f64 ? persist_smem_f64(vc.variant) : persist_smem_f32(vc.variant));
@@ -524,9 +545,14 @@ cudaKernelNodeParams fold_node_params(const bd_ctx* ctx, int64_t w0, int64_t w1,
     fp->w1 = w1;
     fp->ring = ctx->part_ring;
     fp->pad = 0;
+    fp->bead_chain = ctx->d_bead_chain;
+    fp->dpart = ctx->d_dpart;
+    fp->dbead = ctx->d_dbead;
+    fp->NB = ctx->conf ? ctx->n_beads : 0;
+    fp->bpart_stride = ctx->bpart_stride;
     args[0] = fp;
     const int th = rsf_fold_threads();
-    const int64_t n = std::max<int64_t>(1, (w1 - w0) * ctx->M);
+    const int64_t n = std::max<int64_t>(1, (w1 - w0) * (ctx->M + fp->NB));
     cudaKernelNodeParams kp = {};
     kp.func = const_cast<void*>(rsf_fold_func());
     kp.gridDim = dim3((unsigned)((n + th - 1) / th));
@@ -734,7 +760,7 @@ bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost
         }
         if (items.empty()) continue;
         int per_sm = 1;
-        BD_PROBE(ctx->f64 ? persist_blocks_per_sm_f64(v, &per_sm) : persist_blocks_per_sm_f32(v, &per_sm));
+        BD_PROBE(ctx->f64 ? persist_blocks_per_sm_f64(v, false, &per_sm) : persist_blocks_per_sm_f32(v, false, &per_sm));
         const size_t resident = (size_t)per_sm * ctx->n_sm * (threads / 32);
         const size_t base = items.size();
         while (items.size() < 4 * resident) items.push_back(items[items.size() % base]);
@@ -756,7 +782,7 @@ bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost
         p.t0 = 1;
         p.n_steps = probe_steps;
         void* args[1] = {&p};
-        const void* fn = ctx->f64 ? persist_func_f64(v) : persist_func_f32(v);
+        const void* fn = ctx->f64 ? persist_func_f64(v, false) : persist_func_f32(v, false);
         const dim3 grid((unsigned)std::max<size_t>(1, std::min<size_t>((items.size() + threads / 32 - 1) / (threads / 32), (size_t)per_sm * ctx->n_sm)));
         for (int rep = 0; rep < 2; ++rep) {      // first launch warms up
             BD_PROBE(cudaMemsetAsync(tqueue, 0, sizeof(int32_t), ctx->stream));
@@ -792,6 +818,7 @@ bd_status replan(bd_ctx* ctx)
     BD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     const size_t old_items = ctx->h_items.size();
     const int64_t old_part = ctx->part_stride;
+    const int64_t old_bpart = ctx->bpart_stride;
     const size_t old_queue = ctx->var_classes.size();
     bd_status s = plan(ctx);
     if (s != BD_OK) return s;
@@ -804,6 +831,13 @@ bd_status replan(bd_ctx* ctx)
     ctx->d_part = nullptr;
     if ((s = dalloc(ctx, (void**)&ctx->d_part, sizeof(double) * (size_t)ctx->part_ring * (size_t)ctx->part_stride)) != BD_OK)
         return s;
+    if (ctx->conf) {
+        dfree(ctx, ctx->d_dpart, std::max<size_t>(sizeof(double) * 3 * (size_t)ctx->part_ring * (size_t)old_bpart, 16));
+        ctx->d_dpart = nullptr;
+        if ((s = dalloc(ctx, (void**)&ctx->d_dpart, sizeof(double) * 3 * (size_t)ctx->part_ring *
+                                                        (size_t)ctx->bpart_stride)) != BD_OK)
+            return s;
+    }
     dfree(ctx, ctx->d_queue, std::max<size_t>(sizeof(int32_t) * old_queue, 16));
     ctx->d_queue = nullptr;
     if ((s = dalloc(ctx, (void**)&ctx->d_queue, sizeof(int32_t) * ctx->var_classes.size())) != BD_OK) return s;
@@ -979,6 +1013,7 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
     ctx->cfg.chains = ctx->chains.data();
     ctx->stream = (cudaStream_t)cfg->stream;
     ctx->f64 = cfg->precision == BD_PREC_FP64;
+    ctx->conf = (cfg->flags & BD_FLAG_CONFORMATION) != 0;
     ctx->tsize = ctx->f64 ? sizeof(double) : sizeof(float);
     round_keys(cfg->seed, ctx->rk0, ctx->rk1);
 
@@ -1014,6 +1049,17 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
         ctx->part_ring = (int32_t)(ctx->chunk_windows + 1);
         BD_TRY(dalloc(ctx, (void**)&ctx->d_part, sizeof(double) * (size_t)ctx->part_ring * (size_t)ctx->part_stride));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_rsf, sizeof(double) * (size_t)W * (size_t)M));
+        if (ctx->conf) {
+            std::vector<int32_t> bead_chain(ctx->n_beads);
+            for (int c = 0; c < C; ++c)
+                for (int i = 0; i < ctx->chains[c].n_beads; ++i) bead_chain[ctx->h_chains[c].bead_off + i] = c;
+            BD_TRY(upload(ctx, &ctx->d_bead_chain, bead_chain));
+            BD_TRY(dalloc(ctx, (void**)&ctx->d_dbar, sizeof(double) * 3 * (size_t)W * (size_t)ctx->n_rep));
+            BD_TRY(dalloc(ctx, (void**)&ctx->d_dpart, sizeof(double) * 3 * (size_t)ctx->part_ring *
+                                                          (size_t)ctx->bpart_stride));
+            BD_TRY(dalloc(ctx, (void**)&ctx->d_dbead, sizeof(double) * 3 * (size_t)W * (size_t)ctx->n_beads));
+            BD_TRY(dalloc(ctx, (void**)&ctx->d_rgz, sizeof(double) * (size_t)W * (size_t)C));
+        }
         BD_TRY(dalloc(ctx, (void**)&ctx->d_tsf, sizeof(double) * (size_t)W * (size_t)M));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_tsf_acc, sizeof(double) * (size_t)M));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_lam, sizeof(double) * 3 * (size_t)M));
@@ -1125,6 +1171,25 @@ bd_status bd_replica_average(bd_ctx* ctx, int64_t window, double* out)
         return fail(ctx, BD_E_INVALID, "window %lld not completed", (long long)window);
     return deliver(ctx, out, ctx->d_rsf + window * ctx->M, sizeof(double) * ctx->M,
                    is_device_ptr(out));
+}
+
+bd_status bd_conformation(bd_ctx* ctx, int64_t window, double* dbar, double* dbead, double* rgz)
+{
+    if (!ctx) return BD_E_INVALID;
+    if (!ctx->conf) return fail(ctx, BD_E_STATE, "created without BD_FLAG_CONFORMATION");
+    if (window < 0 || window >= ctx->step / ctx->cfg.window_steps)
+        return fail(ctx, BD_E_INVALID, "window %lld not completed", (long long)window);
+    bd_status s;
+    if (dbar && (s = deliver(ctx, dbar, ctx->d_dbar + window * ctx->n_rep * 3,
+                             sizeof(double) * 3 * (size_t)ctx->n_rep, is_device_ptr(dbar))) != BD_OK)
+        return s;
+    if (dbead && (s = deliver(ctx, dbead, ctx->d_dbead + window * ctx->n_beads * 3,
+                              sizeof(double) * 3 * (size_t)ctx->n_beads, is_device_ptr(dbead))) != BD_OK)
+        return s;
+    if (rgz && (s = deliver(ctx, rgz, ctx->d_rgz + window * ctx->cfg.n_chains,
+                            sizeof(double) * (size_t)ctx->cfg.n_chains, is_device_ptr(rgz))) != BD_OK)
+        return s;
+    return BD_OK;
 }
 
 bd_status bd_time_average(bd_ctx* ctx, int64_t window, double* out)

@@ -24,6 +24,8 @@ struct ChainDev {
     int64_t state_off;   // bond index of slot 0, bond 0
     int64_t spr_off;     // first spring of this chain in an [M] profile
     int64_t part_off;    // first entry of group 0 in a per-window partial row
+    int64_t rep_off;     // replicas of the chains before this one (sum R)
+    int64_t bpart_off;   // first entry of group 0 in a per-window per-bead partial row
     double H, Hinvb;     // spring constant; H/b for FENE, 0 for Hooke
     double kxx, kyy, kzz, kxz;   // velocity gradient, v = kappa . r
     double f_c, k0, dx;  // threshold force; Bell rate k0 exp(f dx)
@@ -77,6 +79,12 @@ struct StepParams {
     int64_t* first_bell;        // [3][M]
     const double* exp1;         // [3][M] Exp(1) thresholds
     unsigned long long* overext;  // [n_chains]
+    // conformation diagnostics of Eq. 5 (with BD_FLAG_CONFORMATION)
+    double* dbar;               // [max_windows][sum R][3] replica vs halted parent, bead mean
+    double* dbead_part;         // [win_ring][bpart_stride][3] per-group per-bead sums
+    double* rgz;                // [max_windows][n_chains] parent's z radius of gyration
+    int64_t n_rep, bpart_stride;
+    int32_t n_chains, pad_conf;
     int64_t part_stride, M;
     int32_t win_ring, pad_ring;  // windows one chunk touches (started or ended) + 1
     int64_t t0, n_steps;
@@ -127,6 +135,11 @@ struct FoldParams {
     double* rsf;                 // [max_windows][M]
     int64_t M, part_stride, w0, w1;
     int32_t ring, pad;
+    // per-bead conformation differences (NB = 0: none): [ring][bpart_stride][3] -> [max_windows][NB][3]
+    const int32_t* bead_chain;   // [NB]
+    const double* dpart;
+    double* dbead;
+    int64_t NB, bpart_stride;
 };
 
 enum { CRIT_Q_ISF = 0, CRIT_Q_TSF = 1, CRIT_Q_RSF = 2 };

@@ -24,12 +24,16 @@ inline int variant_tile(int v) { return v >= kPairBase ? v - kPairBase : v; }
 
 const void* parent_func_f32(int L);
 const void* parent_func_f64(int L);
-const void* persist_func_f32(int variant);
-const void* persist_func_f64(int variant);
+const void* persist_plain_f32(int variant);     // without the Eq. 5 diagnostics
+const void* persist_plain_f64(int variant);
+const void* persist_conf_f32(int variant);      // with them (bd_window_f32c.cu)
+const void* persist_conf_f64(int variant);
+const void* persist_func_f32(int variant, bool conf);
+const void* persist_func_f64(int variant, bool conf);
 int persist_threads_f32();
 int persist_threads_f64();
-cudaError_t persist_blocks_per_sm_f32(int variant, int* n);
-cudaError_t persist_blocks_per_sm_f64(int variant, int* n);
+cudaError_t persist_blocks_per_sm_f32(int variant, bool conf, int* n);
+cudaError_t persist_blocks_per_sm_f64(int variant, bool conf, int* n);
 size_t persist_smem_f32(int variant);     // dynamic shared memory per CTA
 size_t persist_smem_f64(int variant);
 

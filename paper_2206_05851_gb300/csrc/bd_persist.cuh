@@ -33,7 +33,7 @@ template <typename T, bool FAST, int V> struct PersistSmem {
     static_assert((V >= kPairBase ? 64 : 32) * L <= kWarpScratch, "window scratch too small for the tile");
 };
 
-template <typename T, bool FAST, int V>
+template <typename T, bool FAST, int V, bool CONF = false>
 __global__ void __launch_bounds__(Persist<T>::threads, 1) replica_persist_kernel(const StepParams p)
 {
     using SM = PersistSmem<T, FAST, V>;
@@ -49,9 +49,9 @@ __global__ void __launch_bounds__(Persist<T>::threads, 1) replica_persist_kernel
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= p.n_items) break;
         if constexpr (V >= kPairBase)
-            run_pair_item<V - kPairBase, SM::tab>(p.items[idx], p, wsm, ptab);
+            run_pair_item<V - kPairBase, SM::tab, CONF>(p.items[idx], p, wsm, ptab);
         else
-            run_one_item<T, V, FAST, SM::tab>(p.items[idx], p, wsm, ptab);
+            run_one_item<T, V, FAST, SM::tab, CONF>(p.items[idx], p, wsm, ptab);
     }
 }
 

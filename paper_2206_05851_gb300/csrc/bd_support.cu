@@ -107,13 +107,31 @@ __device__ __forceinline__ double rsf_of(const ChainDev& ch, const double* part,
     return acc / (double)ch.R;
 }
 
+// One thread per (window, spring) for the RSF and, with the conformation
+// diagnostics, per (window, bead) for the per-bead Eq. 5 difference:
+// dbead[w][bead][c] = (sum over the chain's groups, in group order) / R.
 __global__ void rsf_fold_kernel(const FoldParams f)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (f.w1 - f.w0) * f.M) return;
-    const int64_t r = e / f.M, m = e - r * f.M, w = f.w0 + r;
-    const ChainDev ch = f.chains[f.spring_chain[m]];
-    f.rsf[w * f.M + m] = rsf_of(ch, f.part, f.part_stride, w % f.ring, m - ch.spr_off);
+    const int64_t per = f.M + f.NB;
+    if (e >= (f.w1 - f.w0) * per) return;
+    const int64_t r = e / per, x = e - r * per, w = f.w0 + r;
+    if (x < f.M) {
+        const ChainDev ch = f.chains[f.spring_chain[x]];
+        f.rsf[w * f.M + x] = rsf_of(ch, f.part, f.part_stride, w % f.ring, x - ch.spr_off);
+        return;
+    }
+    const int64_t bead = x - f.M;
+    const ChainDev ch = f.chains[f.bead_chain[bead]];
+    const int64_t i = bead - ch.bead_off;
+    const double* row = f.dpart + ((w % f.ring) * f.bpart_stride + ch.bpart_off + i) * 3;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int g = 0; g < ch.n_groups; ++g) {
+        const double* e3 = row + (int64_t)g * ch.N * 3;
+        s0 += e3[0]; s1 += e3[1]; s2 += e3[2];
+    }
+    double* out = f.dbead + (w * f.NB + bead) * 3;
+    out[0] = s0 / (double)ch.R; out[1] = s1 / (double)ch.R; out[2] = s2 / (double)ch.R;
 }
 
 // Threshold and Bell criteria on the window profiles TSF and RSF of windows

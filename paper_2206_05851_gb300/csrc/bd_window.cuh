@@ -34,6 +34,7 @@
 // roundings in both kernels and for every tile size L.
 #pragma once
 
+#include "bd_conf.cuh"
 #include "bd_device.cuh"
 
 namespace bdra {
@@ -220,6 +221,29 @@ __device__ __forceinline__ void store_bonds(const T (&qx)[L], const T (&qy)[L], 
 // ---------------------------------------------------------------------------
 constexpr int kWarpScratch = 512;   // >= slots per warp x springs = P (N-1) <= 32 L
 
+// Eq. 5 diagnostics of a work item's replicas (one per lane run) at the end
+// of window w; their bonds were just stored at state_slot (slot base of the
+// lane's replica).
+template <typename T, int L>
+__device__ __noinline__ void conformation_item(const ItemDev& it, const ChainDev& ch,
+                                               const StepParams& p, int w, const T* state_slot,
+                                               int sw, int P, int G, int bead0, bool active,
+                                               int kglob)
+{
+    const SlotRun r = slot_run((int)(threadIdx.x & 31), sw, P, G);
+    const T* pc = reinterpret_cast<const T*>(p.snap) + ((int64_t)(w % p.win_ring) * p.M + ch.spr_off) * 3;
+    double acc[L][3];
+#pragma unroll
+    for (int j = 0; j < L; ++j) acc[j][0] = acc[j][1] = acc[j][2] = 0.0;
+    eq5_replica<T, L>(state_slot, pc, bead0, r, ch.N, active, acc,
+                      p.dbar + ((int64_t)w * p.n_rep + ch.rep_off + kglob - 1) * 3);
+    if (it.group == 0)
+        eq5_rgz<T, L>(pc, bead0, r, ch.N, sw == 0, p.rgz + (int64_t)w * p.n_chains + it.chain);
+    eq5_beads_out<L>(acc, bead0, r, sw, P, ch.N, it.rep_count,
+                     p.dbead_part + ((int64_t)(w % p.win_ring) * p.bpart_stride + ch.bpart_off +
+                                     (int64_t)it.group * ch.N) * 3);
+}
+
 // Window end: float64 sum over this warp's replicas of each spring's force,
 // in replica order, one partial per (window, spring, group).
 template <typename T>
@@ -235,8 +259,10 @@ __device__ __forceinline__ void warp_window_sum(const T* wsm, int nb, int count,
 }
 
 // With TAB, ptab is this warp's table of 32 L bead parts of the Philox
-// counter (filled here for the item's chain).
-template <typename T, int L, bool FAST, bool TAB = false>
+// counter (filled here for the item's chain). CONF compiles in the Eq. 5
+// window-end diagnostics (used when BD_FLAG_CONFORMATION is set); without it
+// the step loop carries no trace of them.
+template <typename T, int L, bool FAST, bool TAB = false, bool CONF = false>
 __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams& p, T* wsm,
                                              uint4* ptab = nullptr)
 {
@@ -287,6 +313,10 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
             }
             warp_window_sum<T>(wsm, nb, it.rep_count,
                                p.part_hist + (int64_t)(w % p.win_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb);
+            if (CONF && (p.flags & BD_FLAG_CONFORMATION)) {
+                store_bonds<T, L>(qx, qy, qz, state, lc);
+                conformation_item<T, L>(it, ch, p, w, state, sw, P, G, lc.bead0, active, kglob);
+            }
             ++w;
         }
     }

@@ -197,10 +197,35 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
     fl_out += lc.active ? fla + (act_b ? flb : 0) : 0;
 }
 
+// Eq. 5 diagnostics of a work item with two replicas per lane at the end of
+// window w; their bonds were just stored at sa / sb.
+template <int L>
+__device__ __noinline__ void conformation_pair(const ItemDev& it, const ChainDev& ch,
+                                               const StepParams& p, int w, const float* sa,
+                                               const float* sb, int sw, int P, int G, int bead0,
+                                               bool act_a, bool act_b, int ka, int kb)
+{
+    const SlotRun r = slot_run((int)(threadIdx.x & 31), sw, P, G);
+    const float* pc = reinterpret_cast<const float*>(p.snap) + ((int64_t)(w % p.win_ring) * p.M + ch.spr_off) * 3;
+    double acc[L][3];
+#pragma unroll
+    for (int j = 0; j < L; ++j) acc[j][0] = acc[j][1] = acc[j][2] = 0.0;
+    eq5_replica<float, L>(sa, pc, bead0, r, ch.N, act_a, acc,
+                          p.dbar + ((int64_t)w * p.n_rep + ch.rep_off + ka - 1) * 3);
+    eq5_replica<float, L>(sb, pc, bead0, r, ch.N, act_b, acc,
+                          p.dbar + ((int64_t)w * p.n_rep + ch.rep_off + kb - 1) * 3);
+    if (it.group == 0)
+        eq5_rgz<float, L>(pc, bead0, r, ch.N, sw == 0, p.rgz + (int64_t)w * p.n_chains + it.chain);
+    eq5_beads_out<L>(acc, bead0, r, sw, P, ch.N, (it.rep_count + 1) / 2,
+                     p.dbead_part + ((int64_t)(w % p.win_ring) * p.bpart_stride + ch.bpart_off +
+                                     (int64_t)it.group * ch.N) * 3);
+}
+
 // One warp work item with two replicas per lane: lane run s holds replicas
 // rep_begin + 2s + 1 (.x) and rep_begin + 2s + 2 (.y). With TAB, ptab is
-// this warp's table of 32 L bead parts of the Philox counter.
-template <int L, bool TAB>
+// this warp's table of 32 L bead parts of the Philox counter. CONF compiles
+// in the Eq. 5 window-end diagnostics.
+template <int L, bool TAB, bool CONF = false>
 __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParams& p, float* wsm,
                                               uint4* ptab)
 {
@@ -273,6 +298,17 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
             }
             warp_window_sum<float>(wsm, nb, it.rep_count,
                                    p.part_hist + (int64_t)(w % p.win_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb);
+            if (CONF && (p.flags & BD_FLAG_CONFORMATION)) {
+#pragma unroll
+                for (int j = 0; j < L; ++j) {
+                    const int i = lc.bead0 + j;
+                    if (i < nb) {
+                        if (act_a) { sa[3 * i] = qx[j].x; sa[3 * i + 1] = qy[j].x; sa[3 * i + 2] = qz[j].x; }
+                        if (act_b) { sb[3 * i] = qx[j].y; sb[3 * i + 1] = qy[j].y; sb[3 * i + 2] = qz[j].y; }
+                    }
+                }
+                conformation_pair<L>(it, ch, p, w, sa, sb, sw, P, G, lc.bead0, act_a, act_b, ka, kb);
+            }
             ++w;
         }
     }

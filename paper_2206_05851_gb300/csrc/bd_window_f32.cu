@@ -3,6 +3,7 @@
 // -fmad=false.
 #include "bd_persist.cuh"
 #include "bd_launch.h"
+#include "bd_variants.h"
 
 namespace bdra {
 
@@ -22,16 +23,19 @@ const void* parent_func_f32(int L)
     }
 }
 
-#define BD_VARIANTS(X) X(4) X(7) X(10) X(13) X(16) X(kPairBase + 4) X(kPairBase + 7)
-
-const void* persist_func_f32(int v)
+const void* persist_plain_f32(int v)
 {
     switch (v) {
-#define X(x) case x: return (const void*)replica_persist_kernel<float, true, x>;
-        BD_VARIANTS(X)
+#define X(x) case x: return (const void*)replica_persist_kernel<float, true, x, false>;
+        BD_VARIANTS_F32(X)
 #undef X
     default: return nullptr;
     }
+}
+
+const void* persist_func_f32(int v, bool conf)
+{
+    return conf ? persist_conf_f32(v) : persist_plain_f32(v);
 }
 
 int persist_threads_f32() { return Persist<float>::threads; }
@@ -40,7 +44,7 @@ size_t persist_smem_f32(int v)
 {
     switch (v) {
 #define X(x) case x: return PersistSmem<float, true, x>::bytes;
-        BD_VARIANTS(X)
+        BD_VARIANTS_F32(X)
 #undef X
     default: return 0;
     }
@@ -48,9 +52,9 @@ size_t persist_smem_f32(int v)
 
 // Occupancy with the variant's dynamic shared memory, which is also allowed
 // here (above the default 48 KiB) for the current device.
-cudaError_t persist_blocks_per_sm_f32(int v, int* n)
+cudaError_t persist_blocks_per_sm_f32(int v, bool conf, int* n)
 {
-    const void* f = persist_func_f32(v);
+    const void* f = persist_func_f32(v, conf);
     if (!f) return cudaErrorInvalidValue;
     const size_t smem = persist_smem_f32(v);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -3,6 +3,7 @@
 // -fmad=false.
 #include "bd_persist.cuh"
 #include "bd_launch.h"
+#include "bd_variants.h"
 
 namespace bdra {
 
@@ -22,16 +23,19 @@ const void* parent_func_f64(int L)
     }
 }
 
-#define BD_VARIANTS(X) X(2) X(4) X(7) X(10) X(13) X(16)
-
-const void* persist_func_f64(int v)
+const void* persist_plain_f64(int v)
 {
     switch (v) {
-#define X(x) case x: return (const void*)replica_persist_kernel<double, false, x>;
-        BD_VARIANTS(X)
+#define X(x) case x: return (const void*)replica_persist_kernel<double, false, x, false>;
+        BD_VARIANTS_F64(X)
 #undef X
     default: return nullptr;
     }
+}
+
+const void* persist_func_f64(int v, bool conf)
+{
+    return conf ? persist_conf_f64(v) : persist_plain_f64(v);
 }
 
 int persist_threads_f64() { return Persist<double>::threads; }
@@ -40,7 +44,7 @@ size_t persist_smem_f64(int v)
 {
     switch (v) {
 #define X(x) case x: return PersistSmem<double, false, x>::bytes;
-        BD_VARIANTS(X)
+        BD_VARIANTS_F64(X)
 #undef X
     default: return 0;
     }
@@ -48,9 +52,9 @@ size_t persist_smem_f64(int v)
 
 // Occupancy with the variant's dynamic shared memory, which is also allowed
 // here (above the default 48 KiB) for the current device.
-cudaError_t persist_blocks_per_sm_f64(int v, int* n)
+cudaError_t persist_blocks_per_sm_f64(int v, bool conf, int* n)
 {
-    const void* f = persist_func_f64(v);
+    const void* f = persist_func_f64(v, conf);
     if (!f) return cudaErrorInvalidValue;
     const size_t smem = persist_smem_f64(v);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
