@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-conformation", action="store_true")
     ap.add_argument("--only-adjoint", action="store_true",
                     help="time only the differentiation workload (for profiling)")
     ap.add_argument("--adjoint-chains", type=int, default=0, help="override its chain count")
@@ -233,6 +234,31 @@ def kinetics_summary(ctx, wl, n_steps):
                            "location_hist": hist.tolist()}
         res[crit] = entry
     return res
+
+
+def conformation_line(wl, pos0, sptr, n_steps=2000):
+    """Cost of the Eq. 5 window-end diagnostics on this workload: the same
+    chains integrated n_steps with and without BD_FLAG_CONFORMATION (replica
+    kernel time from the chunk graph's events)."""
+    import torch
+    from paper_2206_05851_gb300 import bdra
+    S = wl.window_steps
+    times = {}
+    for name, flags in (("plain", 0), ("conformation", bdra.BD_FLAG_CONFORMATION)):
+        c = bdra.Context(wl.chains, wl.dt, S, wl.seed, torch.from_numpy(pos0).cuda(),
+                         precision=bdra.BD_PREC_FP32, max_windows=2 * n_steps // S + 1,
+                         thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, flags=flags, stream=sptr)
+        c.step(n_steps)                           # warm-up
+        c.set_positions(torch.from_numpy(pos0).cuda(), 0)
+        bdra.bd_enable_timing(c.ptr, True)
+        bdra.bd_kernel_times(c.ptr)
+        c.step(n_steps)
+        (_, rep_ms), _ = bdra.bd_kernel_times(c.ptr)
+        times[name] = rep_ms
+        c.close()
+    return {"steps": n_steps, "windows": n_steps // S, "replica_ms_plain": times["plain"],
+            "replica_ms_conformation": times["conformation"],
+            "overhead": times["conformation"] / times["plain"] - 1.0}
 
 
 def adjoint_line(sptr, n_chains=0, n_steps=0):
@@ -485,6 +511,8 @@ def main():
                           "steps": e2e_steps}
         if not args.no_adjoint:
             out["adjoint"] = adjoint_line(sptr, args.adjoint_chains, args.adjoint_steps)
+        if not args.no_conformation:
+            out["conformation"] = conformation_line(wl, pos0, sptr)
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(wl, pos0)
     if rank == 0:

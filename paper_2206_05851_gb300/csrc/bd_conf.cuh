@@ -10,6 +10,9 @@
 // sums and totals over a slot are warp-shuffle scans restricted to the run.
 // These functions are called by every lane of the warp, at window ends only,
 // and are kept out of line so that they add nothing to the step's registers.
+// Arithmetic is in the integration precision: the positions summed are of
+// bond differences (order one), so float keeps the differences to about
+// 1e-6 relative while the float64 pipe, slow on this GPU, stays idle.
 #pragma once
 
 #include "bd_device.cuh"
@@ -34,18 +37,20 @@ __device__ __forceinline__ SlotRun slot_run(int lane, int sw, int P, int G)
 
 // Inclusive prefix sum over the lanes of each slot (lanes outside slots get
 // junk they never use).
-__device__ __forceinline__ double slot_scan(double v, const SlotRun& r)
+template <typename T>
+__device__ __forceinline__ T slot_scan(T v, const SlotRun& r)
 {
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const double u = __shfl_up_sync(0xffffffffu, v, d);
+        const T u = __shfl_up_sync(0xffffffffu, v, d);
         if (r.seg >= d) v += u;
     }
     return v;
 }
 
 // Total over the lanes of each slot, on every lane of the slot.
-__device__ __forceinline__ double slot_total(double v, const SlotRun& r)
+template <typename T>
+__device__ __forceinline__ T slot_total(T v, const SlotRun& r)
 {
     return __shfl_sync(0xffffffffu, slot_scan(v, r), r.last);
 }
@@ -56,24 +61,24 @@ __device__ __forceinline__ double slot_total(double v, const SlotRun& r)
 // holds the replica.
 template <typename T, int L>
 __device__ __noinline__ void eq5_replica(const T* q, const T* pc, int bead0,
-                                         const SlotRun& r, int N, bool act, double (&acc)[L][3],
+                                         const SlotRun& r, int N, bool act, T (&acc)[L][3],
                                          double* dbar3)
 {
     const int nb = N - 1;
-    double dq[L][3], s[3] = {0.0, 0.0, 0.0};
+    T dq[L][3], s[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int j = 0; j < L; ++j) {
         const int b = bead0 + j;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            dq[j][c] = (act && b < nb) ? (double)q[3 * b + c] - (double)pc[3 * b + c] : 0.0;
+            dq[j][c] = (act && b < nb) ? q[3 * b + c] - pc[3 * b + c] : T(0);
             s[c] += dq[j][c];
         }
     }
-    double pos[L][3], psum[3] = {0.0, 0.0, 0.0};
+    T pos[L][3], psum[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        double x = slot_scan(s[c], r) - s[c];     // position of the lane's first bead
+        T x = slot_scan(s[c], r) - s[c];          // position of the lane's first bead
 #pragma unroll
         for (int j = 0; j < L; ++j) {
             pos[j][c] = x;
@@ -81,15 +86,15 @@ __device__ __noinline__ void eq5_replica(const T* q, const T* pc, int bead0,
             x += dq[j][c];
         }
     }
-    double dsum[3];
+    T dsum[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double cm = slot_total(psum[c], r) / N;
-        double ds = 0.0;
+        const T cm = slot_total(psum[c], r) / (T)N;
+        T ds = T(0);
 #pragma unroll
         for (int j = 0; j < L; ++j) {
             if (bead0 + j < N) {
-                const double d = fabs(pos[j][c] - cm);
+                const T d = fabs(pos[j][c] - cm);
                 ds += d;
                 if (act) acc[j][c] += d;
             }
@@ -97,7 +102,7 @@ __device__ __noinline__ void eq5_replica(const T* q, const T* pc, int bead0,
         dsum[c] = slot_total(ds, r);
     }
     if (act && dbar3 && threadIdx.x % 32 == r.last)
-        for (int c = 0; c < 3; ++c) dbar3[c] = dsum[c] / N;
+        for (int c = 0; c < 3; ++c) dbar3[c] = (double)dsum[c] / N;
 }
 
 // R_GZ of the parent conformation pc (bonds [nb][3]); the slot's last lane
@@ -107,35 +112,35 @@ __device__ __noinline__ void eq5_rgz(const T* pc, int bead0, const SlotRun& r, i
                                      bool write, double* out)
 {
     const int nb = N - 1;
-    double dz[L], s = 0.0;
+    T dz[L], s = T(0);
 #pragma unroll
     for (int j = 0; j < L; ++j) {
         const int b = bead0 + j;
-        dz[j] = b < nb ? (double)pc[3 * b + 2] : 0.0;
+        dz[j] = b < nb ? pc[3 * b + 2] : T(0);
         s += dz[j];
     }
-    double z = slot_scan(s, r) - s, zs = 0.0;
-    double zb[L];
+    T z = slot_scan(s, r) - s, zs = T(0);
+    T zb[L];
 #pragma unroll
     for (int j = 0; j < L; ++j) {
         zb[j] = z;
         if (bead0 + j < N) zs += z;
         z += dz[j];
     }
-    const double zc = slot_total(zs, r) / N;
-    double v = 0.0;
+    const T zc = slot_total(zs, r) / (T)N;
+    T v = T(0);
 #pragma unroll
     for (int j = 0; j < L; ++j)
         if (bead0 + j < N) v += (zb[j] - zc) * (zb[j] - zc);
     v = slot_total(v, r);
-    if (write && threadIdx.x % 32 == r.last) *out = sqrt(v / N);
+    if (write && threadIdx.x % 32 == r.last) *out = sqrt((double)v / N);
 }
 
 // Sum of acc over the first n_slots slots of the warp (same bead, every
 // slot), written by the lanes of slot 0 to out[N][3] (this work item's
 // per-bead partial row). Runs on every lane.
-template <int L>
-__device__ __noinline__ void eq5_beads_out(const double (&acc)[L][3], int bead0,
+template <typename T, int L>
+__device__ __noinline__ void eq5_beads_out(const T (&acc)[L][3], int bead0,
                                            const SlotRun& r, int sw, int P, int N, int n_slots,
                                            double* out)
 {
@@ -144,12 +149,12 @@ __device__ __noinline__ void eq5_beads_out(const double (&acc)[L][3], int bead0,
     for (int j = 0; j < L; ++j)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            double v = 0.0;
+            T v = T(0);
             for (int s2 = 0; s2 < P; ++s2) {
-                const double u = __shfl_sync(0xffffffffu, acc[j][c], sw < P ? s2 * r.G + r.seg : lane);
+                const T u = __shfl_sync(0xffffffffu, acc[j][c], sw < P ? s2 * r.G + r.seg : lane);
                 if (s2 < n_slots) v += u;
             }
-            if (sw == 0 && bead0 + j < N) out[3 * (bead0 + j) + c] = v;
+            if (sw == 0 && bead0 + j < N) out[3 * (bead0 + j) + c] = (double)v;
         }
 }
 

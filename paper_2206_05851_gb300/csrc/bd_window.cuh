@@ -232,14 +232,14 @@ __device__ __noinline__ void conformation_item(const ItemDev& it, const ChainDev
 {
     const SlotRun r = slot_run((int)(threadIdx.x & 31), sw, P, G);
     const T* pc = reinterpret_cast<const T*>(p.snap) + ((int64_t)(w % p.win_ring) * p.M + ch.spr_off) * 3;
-    double acc[L][3];
+    T acc[L][3];
 #pragma unroll
-    for (int j = 0; j < L; ++j) acc[j][0] = acc[j][1] = acc[j][2] = 0.0;
+    for (int j = 0; j < L; ++j) acc[j][0] = acc[j][1] = acc[j][2] = T(0);
     eq5_replica<T, L>(state_slot, pc, bead0, r, ch.N, active, acc,
                       p.dbar + ((int64_t)w * p.n_rep + ch.rep_off + kglob - 1) * 3);
     if (it.group == 0)
         eq5_rgz<T, L>(pc, bead0, r, ch.N, sw == 0, p.rgz + (int64_t)w * p.n_chains + it.chain);
-    eq5_beads_out<L>(acc, bead0, r, sw, P, ch.N, it.rep_count,
+    eq5_beads_out<T, L>(acc, bead0, r, sw, P, ch.N, it.rep_count,
                      p.dbead_part + ((int64_t)(w % p.win_ring) * p.bpart_stride + ch.bpart_off +
                                      (int64_t)it.group * ch.N) * 3);
 }

@@ -207,16 +207,16 @@ __device__ __noinline__ void conformation_pair(const ItemDev& it, const ChainDev
 {
     const SlotRun r = slot_run((int)(threadIdx.x & 31), sw, P, G);
     const float* pc = reinterpret_cast<const float*>(p.snap) + ((int64_t)(w % p.win_ring) * p.M + ch.spr_off) * 3;
-    double acc[L][3];
+    float acc[L][3];
 #pragma unroll
-    for (int j = 0; j < L; ++j) acc[j][0] = acc[j][1] = acc[j][2] = 0.0;
+    for (int j = 0; j < L; ++j) acc[j][0] = acc[j][1] = acc[j][2] = float(0);
     eq5_replica<float, L>(sa, pc, bead0, r, ch.N, act_a, acc,
                           p.dbar + ((int64_t)w * p.n_rep + ch.rep_off + ka - 1) * 3);
     eq5_replica<float, L>(sb, pc, bead0, r, ch.N, act_b, acc,
                           p.dbar + ((int64_t)w * p.n_rep + ch.rep_off + kb - 1) * 3);
     if (it.group == 0)
         eq5_rgz<float, L>(pc, bead0, r, ch.N, sw == 0, p.rgz + (int64_t)w * p.n_chains + it.chain);
-    eq5_beads_out<L>(acc, bead0, r, sw, P, ch.N, (it.rep_count + 1) / 2,
+    eq5_beads_out<float, L>(acc, bead0, r, sw, P, ch.N, (it.rep_count + 1) / 2,
                      p.dbead_part + ((int64_t)(w % p.win_ring) * p.bpart_stride + ch.bpart_off +
                                      (int64_t)it.group * ch.N) * 3);
 }
