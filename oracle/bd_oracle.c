@@ -111,7 +111,7 @@ double ora_exp1(uint64_t seed, uint32_t spring, uint32_t criterion, uint32_t cha
 /* the gradient of U = -(b/2) ln(1 - H Q^2 / b). F is the force on the lower */
 /* bead of the spring, pointing towards the upper bead.                      */
 /* ------------------------------------------------------------------------ */
-int ora_spring_force(int spring, double H, double b, double s_min, const double Q[3],
+int ora_spring_force(int spring, double H, double b, double r0, double s_min, const double Q[3],
                      double F[3], double* tension)
 {
     double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
@@ -122,11 +122,43 @@ int ora_spring_force(int spring, double H, double b, double s_min, const double 
         if (s < s_min) { s = s_min; floored = 1; }
         coef = H / s;
     }
+    if (spring == ORA_SPRING_HARMONIC) {
+        /* Sec. II: U_s = (kappa/2) (|Q| - 2a)^2, force kappa (|Q| - r0) along Q */
+        const double q = sqrt(q2);
+        coef = q > 0.0 ? H * (q - r0) / q : 0.0;
+        F[0] = coef * Q[0];
+        F[1] = coef * Q[1];
+        F[2] = coef * Q[2];
+        if (tension) *tension = H * (q - r0);          /* Eq. 4, signed */
+        return 0;
+    }
     F[0] = coef * Q[0];
     F[1] = coef * Q[1];
     F[2] = coef * Q[2];
     if (tension) *tension = coef * sqrt(q2);
     return floored;
+}
+
+/* Sec. II: U_LJ = u sum_{ij} [(2a/r_ij)^12 - 2 (2a/r_ij)^6] over non-adjacent
+ * beads; the force on bead i from bead j is -dU/dr_i = (dU/dr) r_ij / r with
+ * r_ij = r_j - r_i and dU/dr = (12 u / r) [(s/r)^6 - (s/r)^12]. */
+void ora_lj_forces(const ora_chain* ch, const double* r, double* F)
+{
+    if (!(ch->lj_u > 0.0)) return;
+    const int N = ch->n_beads;
+    const double s2 = ch->lj_sigma * ch->lj_sigma;
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 2; j < N; ++j) {
+            const double d[3] = { r[3 * j] - r[3 * i], r[3 * j + 1] - r[3 * i + 1],
+                                  r[3 * j + 2] - r[3 * i + 2] };
+            const double rr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            const double x6 = (s2 / rr) * (s2 / rr) * (s2 / rr);
+            const double dUdr_over_r = 12.0 * ch->lj_u * (x6 - x6 * x6) / rr;
+            for (int k = 0; k < 3; ++k) {
+                F[3 * i + k] += dUdr_over_r * d[k];
+                F[3 * j + k] -= dUdr_over_r * d[k];
+            }
+        }
 }
 
 /* Homogeneous flows v = kappa . r. Shear as in Sec. II: v = gdot z x_hat
@@ -163,12 +195,14 @@ int64_t ora_em_step(const ora_chain* ch, double dt, double s_min, double* r, con
         double Q[3] = { r[3 * (i + 1) + 0] - r[3 * i + 0],
                         r[3 * (i + 1) + 1] - r[3 * i + 1],
                         r[3 * (i + 1) + 2] - r[3 * i + 2] };
-        floored += ora_spring_force(ch->spring, ch->H, ch->b, s_min, Q, &F[3 * i], NULL);
+        floored += ora_spring_force(ch->spring, ch->H, ch->b, ch->r0, s_min, Q, &F[3 * i], NULL);
     }
+    double* Flj = (double*)calloc(3 * (size_t)N, sizeof(double));
+    ora_lj_forces(ch, r, Flj);
     const double amp = sqrt(2.0 * D * dt);
     for (int i = 0; i < N; ++i) {
         for (int d = 0; d < 3; ++d) {
-            double fspring = 0.0;
+            double fspring = Flj[3 * i + d];
             if (i + 1 < N) fspring += F[3 * i + d];
             if (i > 0)     fspring -= F[3 * (i - 1) + d];
             double v = kappa[3 * d + 0] * r[3 * i + 0] + kappa[3 * d + 1] * r[3 * i + 1]
@@ -179,6 +213,7 @@ int64_t ora_em_step(const ora_chain* ch, double dt, double s_min, double* r, con
     for (int i = 0; i < 3 * N; ++i) r[i] += inc[i];
     free(inc);
     free(F);
+    free(Flj);
     return floored;
 }
 
@@ -190,7 +225,7 @@ void ora_tensions(const ora_chain* ch, double s_min, const double* r, double* f)
                         r[3 * (i + 1) + 1] - r[3 * i + 1],
                         r[3 * (i + 1) + 2] - r[3 * i + 2] };
         double F[3];
-        ora_spring_force(ch->spring, ch->H, ch->b, s_min, Q, F, &f[i]);
+        ora_spring_force(ch->spring, ch->H, ch->b, ch->r0, s_min, Q, F, &f[i]);
     }
 }
 
@@ -334,6 +369,8 @@ int ora_rsf_tangent(const ora_problem* p, int64_t n_steps, double* pos, double* 
     const int C = p->n_chains;
     const int S = p->window_steps;
     if (C <= 0 || S <= 0 || n_steps < 0) return 1;
+    for (int c = 0; c < C; ++c)      /* tangents of the Hooke and FENE laws only */
+        if (p->chains[c].spring == ORA_SPRING_HARMONIC || p->chains[c].lj_u > 0.0) return 1;
     int64_t* bead_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
     int64_t* spr_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
     bead_off[0] = spr_off[0] = 0;
@@ -379,7 +416,7 @@ int ora_rsf_tangent(const ora_problem* p, int64_t n_steps, double* pos, double* 
                         double Q[3];
                         for (int d = 0; d < 3; ++d) Q[d] = rk[3 * (i + 1) + d] - rk[3 * i + d];
                         double F[3], f;
-                        ora_spring_force(ch->spring, ch->H, ch->b, p->s_min, Q, F, &f);
+                        ora_spring_force(ch->spring, ch->H, ch->b, ch->r0, p->s_min, Q, F, &f);
                         acc[i] += f;
                         for (int j = 0; j < 3; ++j) {
                             double dQ[3];

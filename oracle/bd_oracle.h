@@ -19,7 +19,7 @@
 extern "C" {
 #endif
 
-enum { ORA_SPRING_HOOKE = 0, ORA_SPRING_FENE = 1 };
+enum { ORA_SPRING_HOOKE = 0, ORA_SPRING_FENE = 1, ORA_SPRING_HARMONIC = 2 };
 enum { ORA_FLOW_NONE = 0, ORA_FLOW_SHEAR = 1, ORA_FLOW_UNIAXIAL = 2, ORA_FLOW_PLANAR = 3 };
 enum { ORA_ISF = 0, ORA_TSF = 1, ORA_RSF = 2 };          /* criterion index q */
 enum { ORA_STREAM_BD = 0, ORA_STREAM_EXP1 = 1 };         /* Philox stream ids */
@@ -28,6 +28,9 @@ typedef struct {
     int32_t n_beads, n_replicas, spring, flow;
     double H, b, rate;     /* stiffness / H0, FENE b, flow rate in 1/lambda_H */
     double f_c, k0, dx;    /* threshold force; Bell k = k0 exp(f dx) */
+    double r0;             /* rest length of the harmonic spring law */
+    double lj_u, lj_sigma; /* Lennard-Jones depth and minimum distance between
+                              non-adjacent beads (lj_u = 0: none) */
 } ora_chain;
 
 typedef struct {
@@ -52,9 +55,14 @@ void ora_normals3(uint64_t seed, uint32_t bead, uint32_t slot, uint32_t stream,
                   uint32_t step, uint32_t chain, double xi[3]);
 /* Unit-mean exponential threshold for a (spring, criterion, chain). */
 double ora_exp1(uint64_t seed, uint32_t spring, uint32_t criterion, uint32_t chain);
-/* Spring force F(Q) and tension |F|; returns 1 when the FENE floor applied. */
-int ora_spring_force(int spring, double H, double b, double s_min, const double Q[3],
+/* Spring force F(Q) and its signed magnitude along the bond (the tension;
+ * |F| for Hooke and FENE, H (|Q| - r0) for the harmonic law with rest length
+ * r0); returns 1 when the FENE floor applied. */
+int ora_spring_force(int spring, double H, double b, double r0, double s_min, const double Q[3],
                      double F[3], double* tension);
+/* Lennard-Jones forces between non-adjacent beads (|i - j| >= 2) of a
+ * conformation r [N][3], added to F [N][3]: U = u sum [(s/r)^12 - 2 (s/r)^6]. */
+void ora_lj_forces(const ora_chain* ch, const double* r, double* F);
 /* Velocity-gradient tensor kappa (row-major), v = kappa . r. */
 void ora_flow_gradient(int flow, double rate, double kappa[9]);
 /* One Euler-Maruyama step of Eq. 1 with given noise xi [N][3]; positions r [N][3]. */

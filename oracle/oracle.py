@@ -39,7 +39,8 @@ class _Chain(ctypes.Structure):
     _fields_ = [("n_beads", ctypes.c_int32), ("n_replicas", ctypes.c_int32),
                 ("spring", ctypes.c_int32), ("flow", ctypes.c_int32),
                 ("H", ctypes.c_double), ("b", ctypes.c_double), ("rate", ctypes.c_double),
-                ("f_c", ctypes.c_double), ("k0", ctypes.c_double), ("dx", ctypes.c_double)]
+                ("f_c", ctypes.c_double), ("k0", ctypes.c_double), ("dx", ctypes.c_double),
+                ("r0", ctypes.c_double), ("lj_u", ctypes.c_double), ("lj_sigma", ctypes.c_double)]
 
 
 class _Problem(ctypes.Structure):
@@ -67,7 +68,8 @@ def lib():
                                   ctypes.c_uint32]
         _lib.ora_exp1.restype = ctypes.c_double
         _lib.ora_spring_force.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                          ctypes.c_double, f64p, f64p, f64p]
+                                          ctypes.c_double, ctypes.c_double, f64p, f64p, f64p]
+        _lib.ora_lj_forces.argtypes = [P(_Chain), f64p, f64p]
         _lib.ora_spring_force.restype = ctypes.c_int
         _lib.ora_flow_gradient.argtypes = [ctypes.c_int, ctypes.c_double, f64p]
         _lib.ora_em_step.argtypes = [P(_Chain), ctypes.c_double, ctypes.c_double, f64p, f64p]
@@ -97,7 +99,8 @@ def _p(a: np.ndarray, ct):
 def _chain_struct(ch) -> _Chain:
     return _Chain(int(ch.n_beads), int(ch.n_replicas), int(ch.spring), int(ch.flow),
                   float(ch.H), float(ch.b), float(ch.rate), float(ch.f_c), float(ch.k0),
-                  float(ch.dx))
+                  float(ch.dx), float(getattr(ch, "r0", 0.0)), float(getattr(ch, "lj_u", 0.0)),
+                  float(getattr(ch, "lj_sigma", 0.0)))
 
 
 # ---------------------------------------------------------------------------
@@ -147,13 +150,23 @@ def exp1(seed: int, spring: int, criterion: int, chain: int) -> float:
 # Model pieces
 # ---------------------------------------------------------------------------
 
-def spring_force(spring: int, H: float, b: float, Q, s_min: float = S_MIN_DEFAULT):
+def spring_force(spring: int, H: float, b: float, Q, s_min: float = S_MIN_DEFAULT,
+                 r0: float = 0.0):
     q = np.ascontiguousarray(Q, dtype=np.float64)
     F = np.zeros(3)
     t = np.zeros(1)
-    fl = lib().ora_spring_force(spring, H, b, s_min, _p(q, ctypes.c_double),
+    fl = lib().ora_spring_force(spring, H, b, r0, s_min, _p(q, ctypes.c_double),
                                 _p(F, ctypes.c_double), _p(t, ctypes.c_double))
     return F, float(t[0]), int(fl)
+
+
+def lj_forces(chain, r: np.ndarray) -> np.ndarray:
+    """Lennard-Jones forces [N][3] between the non-adjacent beads of r [N][3]."""
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    F = np.zeros_like(rr)
+    cs = _chain_struct(chain)
+    lib().ora_lj_forces(ctypes.byref(cs), _p(rr, ctypes.c_double), _p(F, ctypes.c_double))
+    return F
 
 
 def flow_gradient(flow: int, rate: float) -> np.ndarray:

@@ -26,6 +26,7 @@ import numpy as np
 
 SPRING_HOOKE = 0
 SPRING_FENE = 1
+SPRING_HARMONIC = 2     # harmonic with a rest length r0 (the paper's collapsed-chain springs)
 
 FLOW_NONE = 0
 FLOW_SHEAR = 1
@@ -52,6 +53,9 @@ class Chain:
     f_c: float = math.inf  # threshold-rupture force
     k0: float = 0.0        # Bell zero-force rate, 1/lambda_H
     dx: float = 0.0        # Bell distance to transition state, l_H
+    r0: float = 0.0        # rest length of SPRING_HARMONIC
+    lj_u: float = 0.0      # Lennard-Jones depth between non-adjacent beads (0: none)
+    lj_sigma: float = 0.0  # Lennard-Jones zero-force (minimum) distance
 
 
 @dataclasses.dataclass
