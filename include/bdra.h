@@ -59,7 +59,12 @@ typedef enum {
     BD_E_CAPACITY = 6   /* output or history capacity exceeded */
 } bd_status;
 
-enum { BD_SPRING_HOOKE = 0, BD_SPRING_FENE = 1 };
+/* BD_SPRING_HARMONIC: the paper's collapsed-chain springs (Sec. II),
+ * U = (H/2)(|Q| - r0)^2 with rest length r0 (2a), usually with Lennard-Jones
+ * cohesion (lj_u > 0); the sampled spring force is the signed H (|Q| - r0)
+ * of Eq. 4. Chains of this law run one replica per lane with the pair forces
+ * of all their beads, and have no adjoint. */
+enum { BD_SPRING_HOOKE = 0, BD_SPRING_FENE = 1, BD_SPRING_HARMONIC = 2 };
 enum { BD_FLOW_NONE = 0, BD_FLOW_SHEAR = 1, BD_FLOW_UNIAXIAL = 2, BD_FLOW_PLANAR = 3 };
 /* BD_PREC_FP64: every step in float64. BD_PREC_FP32: Eq. 1 integrated in
  * float32; the cross-replica force reduction and the Bell hazard
@@ -85,6 +90,11 @@ typedef struct {
     double f_c;          /* threshold-rupture force (kT / l_H) */
     double k0;           /* Bell zero-force rate */
     double dx;           /* Bell distance to the transition state (l_H) */
+    double r0;           /* BD_SPRING_HARMONIC rest length (>= 0); unused otherwise */
+    double lj_u;         /* Lennard-Jones depth between non-adjacent beads, U = lj_u
+                            [(s/r)^12 - 2 (s/r)^6] (Sec. II); 0 = none; needs
+                            BD_SPRING_HARMONIC */
+    double lj_sigma;     /* its minimum distance s (> 0 when lj_u > 0) */
 } bd_chain_desc;
 
 typedef struct {
@@ -102,7 +112,9 @@ typedef struct {
     void* stream;                 /* cudaStream_t for all work; NULL = default stream */
     int32_t lanes_hint;           /* 0: planner's choice; else springs per lane (tile) */
     int32_t layout_hint;          /* 0: planner's choice; 1: one replica per lane;
-                                     2: two replicas per lane (float32 only) */
+                                     2: two replicas per lane (float32 only). Both
+                                     hints apply to Hooke and FENE chains; harmonic
+                                     chains always take the planner's tile */
     int32_t checkpoint_steps;     /* 0: no adjoint; else K, a multiple of window_steps:
                                      bd_step keeps the parent conformation every K
                                      steps so that bd_adjoint can recompute the run */

@@ -38,7 +38,8 @@ class bd_chain_desc(ctypes.Structure):
     _fields_ = [("n_beads", ctypes.c_int32), ("n_replicas", ctypes.c_int32),
                 ("spring", ctypes.c_int32), ("flow", ctypes.c_int32),
                 ("H", ctypes.c_double), ("b", ctypes.c_double), ("rate", ctypes.c_double),
-                ("f_c", ctypes.c_double), ("k0", ctypes.c_double), ("dx", ctypes.c_double)]
+                ("f_c", ctypes.c_double), ("k0", ctypes.c_double), ("dx", ctypes.c_double),
+                ("r0", ctypes.c_double), ("lj_u", ctypes.c_double), ("lj_sigma", ctypes.c_double)]
 
 
 class bd_config(ctypes.Structure):
@@ -159,7 +160,8 @@ def make_config(chains: Sequence, dt: float, window_steps: int, seed: int, preci
     arr = (bd_chain_desc * len(chains))(*[
         bd_chain_desc(int(c.n_beads), int(c.n_replicas), int(c.spring), int(c.flow),
                       float(c.H), float(c.b), float(c.rate), float(c.f_c), float(c.k0),
-                      float(c.dx)) for c in chains])
+                      float(c.dx), float(getattr(c, "r0", 0.0)), float(getattr(c, "lj_u", 0.0)),
+                      float(getattr(c, "lj_sigma", 0.0))) for c in chains])
     cfg = bd_config(len(chains), int(window_steps), arr, float(dt), int(seed), int(precision),
                     int(flags), int(thr_mask), int(bell_mask), int(max_windows), float(s_min),
                     stream, int(lanes_hint), int(layout_hint), int(checkpoint_steps))

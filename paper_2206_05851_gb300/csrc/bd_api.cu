@@ -27,7 +27,10 @@ struct VarClass {      // one persistent replica launch: the work items of one s
 struct ParClass {      // one parent-kernel launch: the parent warps of one tile
     int L, threads, grid;
     int warp_begin, warp_count;
+    bool lj;           // collapsed chains (harmonic springs, pair forces)
 };
+constexpr int kParentLJKey = 1000;   // planner key offset of the collapsed-chain parents
+
 struct AdjClass {      // one adjoint replica-window launch: the work items of one tile
     int L;
     int item_begin, item_count;
@@ -50,7 +53,7 @@ struct bd_ctx {
     std::vector<ParentWarp> h_parent_warps;
     std::vector<VarClass> var_classes;
     std::vector<ParClass> par_classes;
-    double var_cost[2 * kPairBase];     // issue cost per warp-step of each variant
+    double var_cost[kVariantCodes];     // issue cost per warp-step of each variant
     uint32_t rk0[10], rk1[10];
 
     ChainDev* d_chains = nullptr;
@@ -230,13 +233,16 @@ struct VariantChoice { int variant, per_warp, groups; double cost; };
 double default_variant_cost(int v)
 {
     const int L = variant_tile(v);
+    if (variant_lj(v)) return 1000.0 * L;      // pair forces: work per lane grows with its beads
     return variant_paired(v) ? 140.0 * L + 60.0 : 100.0 * L + 40.0;
 }
 
 // The step variant for a chain: a warp holds P = 32 / ceil(N / L) replicas
 // (2P with two replicas per lane); the chain needs ceil(R / per_warp) warp
-// items, and the cost is their issue work per useful bead-step.
-VariantChoice choose_variant(const bd_ctx* ctx, int N, int R)
+// items, and the cost is their issue work per useful bead-step. Collapsed
+// chains (harmonic springs) take the collapsed-chain variants, the others
+// the rest; the tile and layout hints apply to the latter.
+VariantChoice choose_variant(const bd_ctx* ctx, int N, int R, bool collapsed)
 {
     const bd_config& cfg = ctx->cfg;
     const int* vars = ctx->f64 ? kVariantsF64 : kVariantsF32;
@@ -246,9 +252,12 @@ VariantChoice choose_variant(const bd_ctx* ctx, int N, int R)
         const int v = vars[t];
         const bool paired = variant_paired(v);
         const int L = variant_tile(v);
-        if (cfg.lanes_hint && L != cfg.lanes_hint) continue;
-        if (cfg.layout_hint == 1 && paired) continue;
-        if (cfg.layout_hint == 2 && !paired) continue;
+        if (variant_lj(v) != collapsed) continue;
+        if (!collapsed) {
+            if (cfg.lanes_hint && L != cfg.lanes_hint) continue;
+            if (cfg.layout_hint == 1 && paired) continue;
+            if (cfg.layout_hint == 2 && !paired) continue;
+        }
         const int G = (N + L - 1) / L;
         if (G > 32) continue;
         const int per_warp = (paired ? 2 : 1) * (32 / G);
@@ -296,7 +305,7 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
         bool ok = false;
         for (int t = 0; t < nv; ++t) {
             const bool paired = variant_paired(vars[t]);
-            if (variant_tile(vars[t]) != cfg->lanes_hint) continue;
+            if (variant_lj(vars[t]) || variant_tile(vars[t]) != cfg->lanes_hint) continue;
             if ((cfg->layout_hint == 1 && paired) || (cfg->layout_hint == 2 && !paired)) continue;
             ok = true;
         }
@@ -310,8 +319,16 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
             return fail(ctx, BD_E_INVALID, "chain %d: n_beads %d outside [2, 512]", c, d.n_beads);
         if (d.n_replicas < 1 || d.n_replicas > 4096)
             return fail(ctx, BD_E_INVALID, "chain %d: n_replicas %d outside [1, 4096]", c, d.n_replicas);
-        if (d.spring != BD_SPRING_HOOKE && d.spring != BD_SPRING_FENE)
+        if (d.spring != BD_SPRING_HOOKE && d.spring != BD_SPRING_FENE && d.spring != BD_SPRING_HARMONIC)
             return fail(ctx, BD_E_INVALID, "chain %d: unknown spring law %d", c, d.spring);
+        if (d.spring == BD_SPRING_HARMONIC && (!(d.r0 >= 0) || !std::isfinite(d.r0)))
+            return fail(ctx, BD_E_INVALID, "chain %d: harmonic rest length must be >= 0", c);
+        if (!(d.lj_u >= 0) || !std::isfinite(d.lj_u))
+            return fail(ctx, BD_E_INVALID, "chain %d: lj_u must be >= 0", c);
+        if (d.lj_u > 0 && (d.spring != BD_SPRING_HARMONIC || !(d.lj_sigma > 0) || !std::isfinite(d.lj_sigma)))
+            return fail(ctx, BD_E_INVALID, "chain %d: Lennard-Jones needs the harmonic law and lj_sigma > 0", c);
+        if (d.spring == BD_SPRING_HARMONIC && cfg->checkpoint_steps > 0)
+            return fail(ctx, BD_E_INVALID, "chain %d: the adjoint supports Hooke and FENE chains only", c);
         if (d.flow < BD_FLOW_NONE || d.flow > BD_FLOW_PLANAR)
             return fail(ctx, BD_E_INVALID, "chain %d: unknown flow %d", c, d.flow);
         if (!(d.H > 0) || !std::isfinite(d.H)) return fail(ctx, BD_E_INVALID, "chain %d: H must be > 0", c);
@@ -321,7 +338,8 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
     }
     if (cfg->lanes_hint) {
         for (int c = 0; c < cfg->n_chains; ++c)
-            if ((cfg->chains[c].n_beads + cfg->lanes_hint - 1) / cfg->lanes_hint > 32)
+            if (cfg->chains[c].spring != BD_SPRING_HARMONIC &&
+                (cfg->chains[c].n_beads + cfg->lanes_hint - 1) / cfg->lanes_hint > 32)
                 return fail(ctx, BD_E_INVALID, "lanes_hint %d too small for chain %d (N=%d)",
                             cfg->lanes_hint, c, cfg->chains[c].n_beads);
     }
@@ -335,11 +353,13 @@ bd_status plan(bd_ctx* ctx)
     ctx->h_chains.resize(C);
     int64_t bead = 0, slot_bead = 0, bond = 0, spr = 0, part = 0, rep = 0, bpart = 0;
     std::vector<ItemDev> items;
-    std::vector<std::pair<std::pair<int, int>, int>> par;   // ((L, G), chain)
+    // ((L + kParentLJKey if collapsed, G), chain): one parent launch per key
+    std::vector<std::pair<std::pair<int, int>, int>> par;
     for (int c = 0; c < C; ++c) {
         const bd_chain_desc& d = ctx->chains[c];
         ChainDev& h = ctx->h_chains[c];
-        const VariantChoice vc = choose_variant(ctx, d.n_beads, d.n_replicas);
+        const bool collapsed = d.spring == BD_SPRING_HARMONIC;
+        const VariantChoice vc = choose_variant(ctx, d.n_beads, d.n_replicas, collapsed);
         if (!vc.variant)
             return fail(ctx, BD_E_INVALID, "chain %d: no step variant fits N=%d", c, d.n_beads);
         h.N = d.n_beads; h.R = d.n_replicas; h.n_groups = vc.groups; h.pad = 0;
@@ -356,6 +376,9 @@ bd_status plan(bd_ctx* ctx)
         default: break;
         }
         h.f_c = d.f_c; h.k0 = d.k0; h.dx = d.dx;
+        h.r0 = collapsed ? d.r0 : 0.0;
+        h.lj_u = d.lj_u;
+        h.lj_s2 = d.lj_sigma * d.lj_sigma;
         // float32 step constants, rounded as (float)(double expression);
         // sqrt(2 D dt) carries the sign of the fast float normals (-1)
         h.f32[0] = (float)h.H;
@@ -377,7 +400,7 @@ bd_status plan(bd_ctx* ctx)
             begin += cnt;
         }
         const int Lp = choose_parent_tile(d.n_beads);
-        par.push_back({{Lp, (d.n_beads + Lp - 1) / Lp}, c});
+        par.push_back({{Lp + (collapsed ? kParentLJKey : 0), (d.n_beads + Lp - 1) / Lp}, c});
         bead += d.n_beads;
         slot_bead += (int64_t)(d.n_replicas + 1) * d.n_beads;
         bond += (int64_t)(d.n_replicas + 1) * nb;
@@ -420,9 +443,11 @@ bd_status plan(bd_ctx* ctx)
     ctx->h_parent_warps.clear();
     ctx->par_classes.clear();
     for (size_t k = 0; k < par.size();) {
-        const int L = par[k].first.first, G = par[k].first.second, P = 32 / G;
-        if (ctx->par_classes.empty() || ctx->par_classes.back().L != L)
-            ctx->par_classes.push_back(ParClass{L, kParentThreads, 0, (int)ctx->h_parent_warps.size(), 0});
+        const int key = par[k].first.first, G = par[k].first.second, P = 32 / G;
+        const int L = key % kParentLJKey;
+        const bool lj = key >= kParentLJKey;
+        if (ctx->par_classes.empty() || ctx->par_classes.back().L != L || ctx->par_classes.back().lj != lj)
+            ctx->par_classes.push_back(ParClass{L, kParentThreads, 0, (int)ctx->h_parent_warps.size(), 0, lj});
         size_t e = k;
         while (e < par.size() && par[e].first == par[k].first) ++e;
         for (size_t j = k; j < e; j += P) {
@@ -509,7 +534,7 @@ cudaKernelNodeParams parent_node(const bd_ctx* ctx, size_t k, StepParams* pk, vo
     const ParClass& pc = ctx->par_classes[k];
     args[0] = pk;
     cudaKernelNodeParams kp = {};
-    kp.func = const_cast<void*>(ctx->f64 ? parent_func_f64(pc.L) : parent_func_f32(pc.L));
+    kp.func = const_cast<void*>(ctx->f64 ? parent_func_f64(pc.L, pc.lj) : parent_func_f32(pc.L, pc.lj));
     kp.gridDim = dim3(pc.grid);
     kp.blockDim = dim3(pc.threads);
     kp.sharedMemBytes = 0;
@@ -722,7 +747,7 @@ std::map<std::pair<int, int>, std::vector<double>> g_tune_cache;
 // throughput cost of one warp-step of variant v, in nanoseconds.
 bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost)
 {
-    cost.assign(2 * kPairBase, 0.0);
+    cost.assign(kVariantCodes, 0.0);
     const int* vars = ctx->f64 ? kVariantsF64 : kVariantsF32;
     const int nv = ctx->f64 ? kNumVariantsF64 : kNumVariantsF32;
     const int threads = ctx->f64 ? persist_threads_f64() : persist_threads_f32();
@@ -748,7 +773,7 @@ bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost
         for (int c = 0; c < ctx->cfg.n_chains; ++c) {
             const int N = ctx->chains[c].n_beads, R = ctx->chains[c].n_replicas;
             const int G = (N + L - 1) / L;
-            if (G > 32) continue;
+            if (G > 32 || variant_lj(v) != (ctx->chains[c].spring == BD_SPRING_HARMONIC)) continue;
             const int per_warp = (variant_paired(v) ? 2 : 1) * (32 / G);
             const int groups = (R + per_warp - 1) / per_warp;
             int begin = 0;
@@ -1024,7 +1049,7 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
             e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
         if (e != cudaSuccess) { cudaGetLastError(); s = fail(ctx, BD_E_CUDA, "no CUDA device: %s", cudaGetErrorString(e)); goto failed; }
     }
-    for (int v = 0; v < 2 * kPairBase; ++v) ctx->var_cost[v] = default_variant_cost(v);
+    for (int v = 0; v < kVariantCodes; ++v) ctx->var_cost[v] = default_variant_cost(v);
     BD_TRY(plan(ctx));
     {
         const int64_t M = ctx->M, C = cfg->n_chains, W = cfg->max_windows;
@@ -1362,11 +1387,11 @@ bd_status bd_autotune(bd_ctx* ctx, int32_t probe_steps, int32_t force)
         if (s != BD_OK) return s;
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         std::vector<double>& c = g_tune_cache[key];
-        if (c.empty()) c.assign(2 * kPairBase, 0.0);
-        for (int v = 0; v < 2 * kPairBase; ++v) if (cost[v] > 0) c[v] = cost[v];
+        if (c.empty()) c.assign(kVariantCodes, 0.0);
+        for (int v = 0; v < kVariantCodes; ++v) if (cost[v] > 0) c[v] = cost[v];
         cost = c;
     }
-    for (int v = 0; v < 2 * kPairBase; ++v)
+    for (int v = 0; v < kVariantCodes; ++v)
         if (cost[v] > 0) ctx->var_cost[v] = cost[v];
     return replan(ctx);
 }

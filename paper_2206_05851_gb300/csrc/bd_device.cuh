@@ -29,6 +29,7 @@ struct ChainDev {
     double H, Hinvb;     // spring constant; H/b for FENE, 0 for Hooke
     double kxx, kyy, kzz, kxz;   // velocity gradient, v = kappa . r
     double f_c, k0, dx;  // threshold force; Bell rate k0 exp(f dx)
+    double r0, lj_u, lj_s2;  // harmonic rest length; Lennard-Jones depth and min distance^2
     // float32 step constants, rounded once on the host from the values
     // above (so the kernels never rebuild them from doubles): H, H/b, D dt,
     // sqrt(2 D dt) times the fast normals' sign, kappa_xx dt, kappa_yy dt,
@@ -60,6 +61,9 @@ struct ParentWarp {
 // Step variants: one replica per lane with L springs (code L), or two
 // replicas per lane with L springs (code kPairBase + L, float32 only).
 constexpr int32_t kPairBase = 100;
+// Collapsed-chain variants (harmonic springs with rest length, Lennard-Jones
+// pair forces; one replica per lane): code kLJBase + L.
+constexpr int32_t kLJBase = 200;
 
 struct StepParams {
     const ChainDev* chains;

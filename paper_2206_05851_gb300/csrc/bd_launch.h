@@ -13,17 +13,26 @@ static const int kNumTiles = 6;
 // Replica step variants compiled into the persistent kernel (ItemDev::variant):
 // float32: one replica per lane with 4..16 springs, two replicas per lane
 // with 4 or 7 springs (larger pair tiles spill at 128 registers);
-// float64: one replica per lane with 2..16 springs.
-static const int kVariantsF32[] = {4, 7, 10, 13, 16, kPairBase + 4, kPairBase + 7};
-static const int kNumVariantsF32 = 7;
-static const int kVariantsF64[] = {2, 4, 7, 10, 13, 16};
-static const int kNumVariantsF64 = 6;
+// float64: one replica per lane with 2..16 springs; both precisions: the
+// collapsed-chain step (harmonic springs, Lennard-Jones pair forces) with 2,
+// 4, 7 or 16 springs per lane. (bd_variants.h lists the same.)
+static const int kVariantsF32[] = {4, 7, 10, 13, 16, kPairBase + 4, kPairBase + 7,
+                                   kLJBase + 2, kLJBase + 4, kLJBase + 7, kLJBase + 16};
+static const int kNumVariantsF32 = 11;
+static const int kVariantsF64[] = {2, 4, 7, 10, 13, 16,
+                                   kLJBase + 2, kLJBase + 4, kLJBase + 7, kLJBase + 16};
+static const int kNumVariantsF64 = 10;
 
-inline bool variant_paired(int v) { return v >= kPairBase; }
-inline int variant_tile(int v) { return v >= kPairBase ? v - kPairBase : v; }
+// Variant codes are below kVariantCodes (cost tables are indexed by code).
+constexpr int kVariantCodes = kLJBase + 32;
 
-const void* parent_func_f32(int L);
-const void* parent_func_f64(int L);
+inline bool variant_lj(int v) { return v >= kLJBase; }
+inline bool variant_paired(int v) { return v >= kPairBase && v < kLJBase; }
+inline int variant_tile(int v) { return v >= kLJBase ? v - kLJBase : v >= kPairBase ? v - kPairBase : v; }
+
+// Parent kernels per tile; lj: the collapsed-chain step.
+const void* parent_func_f32(int L, bool lj);
+const void* parent_func_f64(int L, bool lj);
 const void* persist_plain_f32(int variant);     // without the Eq. 5 diagnostics
 const void* persist_plain_f64(int variant);
 const void* persist_conf_f32(int variant);      // with them (bd_window_f32c.cu)

@@ -1,0 +1,172 @@
+// The paper's collapsed-chain model (Sec. II) in the bond layout of the
+// step kernels: harmonic springs with a rest length, F = H (|Q| - r0) Q/|Q|
+// (the signed force of Eq. 4 is H (|Q| - r0)), and Lennard-Jones cohesion
+// between non-adjacent beads, U = u [(s/r)^12 - 2 (s/r)^6].
+//
+// A step of a slot (G lanes, L bonds each): the bead positions follow from
+// the bonds by a prefix sum over the slot (up to a common offset, which pair
+// forces do not see); each lane gathers every bead of its slot by shuffles
+// and adds the pair forces on its own L beads (all pairs |i - j| >= 2, no
+// cutoff); the bond update of Eq. 1 then takes the difference of the bead
+// forces of its two beads: Q_b += [kappa Q_b + D (Fs_{b+1} - 2 Fs_b +
+// Fs_{b-1} + Flj_{b+1} - Flj_b)] dt + noise.
+#pragma once
+
+#include "bd_step.cuh"
+
+namespace bdra {
+
+template <typename T, bool FAST> struct Rsqrt {
+    static __device__ __forceinline__ T rsqrt(T x) { return T(1) / sqrt(x); }
+    static __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
+};
+template <> struct Rsqrt<float, true> {
+    static __device__ __forceinline__ float rsqrt(float x)
+    {
+        float r;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
+};
+
+// Harmonic spring with rest length: F = c Q with c = H (1 - r0 / |Q|); a bond
+// of zero length has no direction and no force.
+template <typename T, bool FAST>
+__device__ __forceinline__ T harmonic_coef(T qx, T qy, T qz, T H, T r0)
+{
+    const T q2 = bond_q2(qx, qy, qz);
+    return q2 > T(0) ? H * fma(-r0, Rsqrt<T, FAST>::rsqrt(q2), T(1)) : T(0);
+}
+
+// Eq. 4: the signed spring force H (|Q| - r0).
+template <typename T>
+__device__ __forceinline__ T harmonic_tension(T qx, T qy, T qz, T H, T r0)
+{
+    return H * (sqrt(bond_q2(qx, qy, qz)) - r0);
+}
+
+// Per-chain constants of the pair forces, in the integration precision.
+template <typename T> struct LJConst {
+    T r0, u12, s2;      // rest length; 12 u; s^2
+    int N;
+    __device__ __forceinline__ void load(const ChainDev& ch)
+    {
+        r0 = (T)ch.r0; u12 = (T)(12.0 * ch.lj_u); s2 = (T)ch.lj_s2; N = ch.N;
+    }
+};
+
+// Inclusive prefix sum over the lanes of a slot (seg: the lane's position in
+// its slot; lanes outside slots pass seg 0 and get junk they never use).
+template <typename T>
+__device__ __forceinline__ T lj_slot_scan(T v, int seg)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T u = __shfl_up_sync(0xffffffffu, v, d);
+        if (seg >= d) v += u;
+    }
+    return v;
+}
+
+// One Eq. 1 step of the lane's L bonds of a collapsed chain. in_slot: the
+// lane belongs to a slot, slot_base its first lane, seg its position in it, G
+// the lanes per slot. Every lane of the warp calls it.
+template <typename T, int L, bool FAST, bool TAB>
+__device__ __forceinline__ void step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L], const LaneCtx& lc,
+                                              const StepConst<T, FAST>& k, const LJConst<T>& kl,
+                                              bool in_slot, int seg, int G, int slot_base,
+                                              uint32_t step, const StepParams& p, const uint4* ptab)
+{
+    const int lane = threadIdx.x & 31;
+    // spring forces of the lane's bonds
+    T fx[L], fy[L], fz[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        const T c = harmonic_coef<T, FAST>(qx[j], qy[j], qz[j], k.H, kl.r0);
+        fx[j] = c * qx[j]; fy[j] = c * qy[j]; fz[j] = c * qz[j];
+    }
+    // bead positions (common offset dropped): exclusive prefix over the slot
+    T px[L], py[L], pz[L];
+    {
+        T sx = T(0), sy = T(0), sz = T(0);
+#pragma unroll
+        for (int j = 0; j < L; ++j) { sx += qx[j]; sy += qy[j]; sz += qz[j]; }
+        T x = lj_slot_scan(sx, seg) - sx, y = lj_slot_scan(sy, seg) - sy, z = lj_slot_scan(sz, seg) - sz;
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            px[j] = x; py[j] = y; pz[j] = z;
+            x += qx[j]; y += qy[j]; z += qz[j];
+        }
+    }
+    // pair forces on the lane's beads from every bead of the slot
+    T gx[L], gy[L], gz[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) gx[j] = gy[j] = gz[j] = T(0);
+#pragma unroll 1
+    for (int s2 = 0; s2 < G; ++s2) {
+        const int src = in_slot ? slot_base + s2 : lane;        // < 32: slots fit the warp
+#pragma unroll
+        for (int kk = 0; kk < L; ++kk) {
+            const T bx = __shfl_sync(0xffffffffu, px[kk], src);
+            const T by = __shfl_sync(0xffffffffu, py[kk], src);
+            const T bz = __shfl_sync(0xffffffffu, pz[kk], src);
+            const int bs = s2 * L + kk;
+#pragma unroll
+            for (int j = 0; j < L; ++j) {
+                const int b = lc.bead0 + j;
+                const int sep = b > bs ? b - bs : bs - b;
+                if (sep >= 2 && b < kl.N && bs < kl.N) {
+                    const T dx = bx - px[j], dy = by - py[j], dz = bz - pz[j];
+                    const T ir2 = Rsqrt<T, FAST>::rcp(fma(dx, dx, fma(dy, dy, dz * dz)));
+                    const T x2 = kl.s2 * ir2;
+                    const T x6 = x2 * x2 * x2;
+                    const T c = kl.u12 * fma(-x6, x6, x6) * ir2;     // 12u (x6 - x12) / r^2
+                    gx[j] = fma(c, dx, gx[j]); gy[j] = fma(c, dy, gy[j]); gz[j] = fma(c, dz, gz[j]);
+                }
+            }
+        }
+    }
+    // halo: spring force of the previous lane's last bond and the next lane's
+    // first bond; the next lane's first-bead pair force and noise
+    T fmx = shfl(fx[L - 1], lc.src_prev), fmy = shfl(fy[L - 1], lc.src_prev), fmz = shfl(fz[L - 1], lc.src_prev);
+    T fnx = shfl(fx[0], lc.src_next), fny = shfl(fy[0], lc.src_next), fnz = shfl(fz[0], lc.src_next);
+    T gnx = shfl(gx[0], lc.src_next), gny = shfl(gy[0], lc.src_next), gnz = shfl(gz[0], lc.src_next);
+    if (!lc.has_prev) { fmx = T(0); fmy = T(0); fmz = T(0); }
+    if (!lc.has_next) { fnx = T(0); fny = T(0); fnz = T(0); gnx = T(0); gny = T(0); gnz = T(0); }
+    uint3 sp = make_uint3(0u, 0u, 0u);
+    if (TAB) sp = PhiloxSplit::step_part(step, lc.slot_key | ((uint32_t)STREAM_BD << 24), p.rk0);
+    T xcx, xcy, xcz;
+    if (TAB) bead_noise_split<T, FAST>(ptab[lc.bead0], sp, p, xcx, xcy, xcz);
+    else bead_noise<T, FAST>((uint32_t)lc.bead0, lc.slot_key, step, lc.chain, p, xcx, xcy, xcz);
+    const T hx = shfl(xcx, lc.src_next), hy = shfl(xcy, lc.src_next), hz = shfl(xcz, lc.src_next);
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        T xnx, xny, xnz, fpx, fpy, fpz, ghx, ghy, ghz;
+        if (j + 1 < L) {
+            uint32_t bj = (uint32_t)(lc.bead0 + j + 1);
+            asm volatile("" : "+r"(bj));     // keep per-bead noise work inside the step loop
+            if (TAB) bead_noise_split<T, FAST>(ptab[bj], sp, p, xnx, xny, xnz);
+            else bead_noise<T, FAST>(bj, lc.slot_key, step, lc.chain, p, xnx, xny, xnz);
+            fpx = fx[j + 1]; fpy = fy[j + 1]; fpz = fz[j + 1];
+            ghx = gx[j + 1]; ghy = gy[j + 1]; ghz = gz[j + 1];
+        } else {
+            xnx = hx; xny = hy; xnz = hz;
+            fpx = fnx; fpy = fny; fpz = fnz;
+            ghx = gnx; ghy = gny; ghz = gnz;
+        }
+        if (j < lc.nv) {
+            const T lx = fma(T(-2), fx[j], fpx + fmx) + (ghx - gx[j]);
+            const T ly = fma(T(-2), fy[j], fpy + fmy) + (ghy - gy[j]);
+            const T lz = fma(T(-2), fz[j], fpz + fmz) + (ghz - gz[j]);
+            const T ox = qx[j], oy = qy[j], oz = qz[j];
+            qx[j] = fma(k.cn, xnx - xcx, fma(k.cd, lx, fma(k.axz, oz, fma(k.axx, ox, ox))));
+            qy[j] = fma(k.cn, xny - xcy, fma(k.cd, ly, fma(k.ayy, oy, oy)));
+            qz[j] = fma(k.cn, xnz - xcz, fma(k.cd, lz, fma(k.azz, oz, oz)));
+        }
+        fmx = fx[j]; fmy = fy[j]; fmz = fz[j];
+        xcx = xnx; xcy = xny; xcz = xnz;
+    }
+}
+
+}  // namespace bdra

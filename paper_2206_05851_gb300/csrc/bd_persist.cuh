@@ -22,7 +22,7 @@ template <typename T> struct Persist {
 // per-bead Philox parts (32 L entries: every bead a lane of a chain that fits
 // the tile draws).
 template <typename T, bool FAST, int V> struct PersistSmem {
-    static constexpr int L = V >= kPairBase ? V - kPairBase : V;
+    static constexpr int L = V >= kLJBase ? V - kLJBase : (V >= kPairBase ? V - kPairBase : V);
     static constexpr bool tab = sizeof(T) == 4 && FAST;
     static constexpr int warps = Persist<T>::threads / 32;
     static constexpr size_t wsm_bytes = (size_t)warps * kWarpScratch * sizeof(T);
@@ -30,7 +30,8 @@ template <typename T, bool FAST, int V> struct PersistSmem {
     static constexpr size_t bytes = wsm_bytes + (size_t)warps * tab_per_warp * sizeof(uint4);
     static_assert(wsm_bytes % 16 == 0, "table must start 16-byte aligned");
     // window-end scratch: replicas per warp x springs <= (2 if paired) x 32 L
-    static_assert((V >= kPairBase ? 64 : 32) * L <= kWarpScratch, "window scratch too small for the tile");
+    static_assert(((V >= kPairBase && V < kLJBase) ? 64 : 32) * L <= kWarpScratch,
+                  "window scratch too small for the tile");
 };
 
 template <typename T, bool FAST, int V, bool CONF = false>
@@ -48,7 +49,9 @@ __global__ void __launch_bounds__(Persist<T>::threads, 1) replica_persist_kernel
         if (lane == 0) idx = atomicAdd(p.queue, 1);
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= p.n_items) break;
-        if constexpr (V >= kPairBase)
+        if constexpr (V >= kLJBase)
+            run_one_item<T, V - kLJBase, FAST, SM::tab, CONF, true>(p.items[idx], p, wsm, ptab);
+        else if constexpr (V >= kPairBase)
             run_pair_item<V - kPairBase, SM::tab, CONF>(p.items[idx], p, wsm, ptab);
         else
             run_one_item<T, V, FAST, SM::tab, CONF>(p.items[idx], p, wsm, ptab);

@@ -8,15 +8,18 @@
 namespace bdra {
 
 namespace {
-template <int L> const void* parent_fn() { return (const void*)parent_kernel<float, L, true>; }
+template <int L> const void* parent_fn(bool lj)
+{
+    return lj ? (const void*)parent_kernel<float, L, true, true> : (const void*)parent_kernel<float, L, true, false>;
+}
 }  // namespace
 
 #define BD_PARENT_TILES(X) X(2) X(4) X(7) X(10) X(13) X(16)
 
-const void* parent_func_f32(int L)
+const void* parent_func_f32(int L, bool lj)
 {
     switch (L) {
-#define X(l) case l: return parent_fn<l>();
+#define X(l) case l: return parent_fn<l>(lj);
         BD_PARENT_TILES(X)
 #undef X
     default: return nullptr;

@@ -128,8 +128,45 @@ def sample_connectors(rng: np.random.Generator, n: int, spring: int,
     return out
 
 
+def initial_globule(rng: np.random.Generator, chain: Chain, tries: int = 48) -> np.ndarray:
+    """Compact conformation [N][3] of a harmonic chain, centre of mass at 0.
+
+    A walk with bonds of the rest length r0 (1 if r0 = 0): each new bead is
+    the candidate, among `tries` random directions, nearest the beads placed
+    so far (their centroid) that keeps at least 0.95 lj_sigma from every
+    earlier non-adjacent bead; if none does, the one farthest from them. With
+    lj_sigma = 0 the walk is freely jointed (first candidate taken). This
+    stands in for an equilibrated globule: the Lennard-Jones contacts start
+    near their minimum, none overlapping.
+    """
+    N = chain.n_beads
+    r0 = chain.r0 if chain.r0 > 0 else 1.0
+    dmin = 0.95 * chain.lj_sigma
+    r = np.zeros((N, 3))
+    for i in range(1, N):
+        u = rng.normal(size=(tries, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        cand = r[i - 1] + r0 * u
+        if dmin <= 0 or i < 2:
+            r[i] = cand[0]
+            continue
+        d = np.linalg.norm(cand[:, None, :] - r[None, :i - 1, :], axis=2).min(axis=1)
+        ok = d >= dmin
+        if ok.any():
+            cen = r[:i].mean(axis=0)
+            dist = np.linalg.norm(cand - cen, axis=1)
+            r[i] = cand[np.flatnonzero(ok)[np.argmin(dist[ok])]]
+        else:
+            r[i] = cand[np.argmax(d)]
+    r -= r.mean(axis=0)
+    return r
+
+
 def initial_coil(rng: np.random.Generator, chain: Chain) -> np.ndarray:
-    """Equilibrium random-walk conformation [N][3], centre of mass at 0."""
+    """Equilibrium random-walk conformation [N][3], centre of mass at 0
+    (for harmonic chains, the compact walk of initial_globule)."""
+    if chain.spring == SPRING_HARMONIC:
+        return initial_globule(rng, chain)
     q = sample_connectors(rng, chain.n_beads - 1, chain.spring, chain.H, chain.b)
     r = np.zeros((chain.n_beads, 3))
     r[1:] = np.cumsum(q, axis=0)
