@@ -43,6 +43,11 @@ METRIC = ("bead-steps/s (chains×replicas×beads×steps) FP32 batched vs FP64 pl
 # bit/compare ops (angle bits 2, floor clamp and count 2).
 ALGO_OPS_PER_BEAD_STEP = 67.5
 PHILOX_ROUNDS_PER_BEAD_STEP = 8
+# Minimal lane-instructions per non-adjacent Lennard-Jones pair of the
+# collapsed-chain model, the pair evaluated once: separation 3, r^2 3,
+# reciprocal 1, (s/r)^2 1, ^6 2, 12 u (x^6 - x^12) / r^2 3, force on both
+# beads 6.
+LJ_PAIR_OPS = 19
 SMS, LANES_PER_CLK_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -62,6 +67,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-conformation", action="store_true")
+    ap.add_argument("--no-collapsed", action="store_true")
+    ap.add_argument("--only-collapsed", action="store_true",
+                    help="only the collapsed-chain line (Sec. II model)")
     ap.add_argument("--only-adjoint", action="store_true",
                     help="time only the differentiation workload (for profiling)")
     ap.add_argument("--adjoint-chains", type=int, default=0, help="override its chain count")
@@ -261,6 +269,90 @@ def conformation_line(wl, pos0, sptr, n_steps=2000):
             "overhead": times["conformation"] / times["plain"] - 1.0}
 
 
+def lj_ops_per_bead_step(n_beads):
+    """Minimal lane-instructions per bead-step of the collapsed-chain step: the
+    noise and bond update of the free-draining step (ALGO_OPS_PER_BEAD_STEP)
+    plus LJ_PAIR_OPS per non-adjacent pair, each pair counted once (Newton's
+    third law): (N-1)(N-2)/2 pairs per chain-step."""
+    return ALGO_OPS_PER_BEAD_STEP + LJ_PAIR_OPS * (n_beads - 1) * (n_beads - 2) / (2.0 * n_beads)
+
+
+def collapsed_line(sptr, n_chains=0, n_steps=3000, fp64_chains=64):
+    """The paper's collapsed-chain model (harmonic springs with rest length,
+    Lennard-Jones cohesion) on its shear workload: float32 throughput, the
+    replica kernel against the issue roofline, the plain FP64 path and the
+    FP32 RSF error against it on a subset of the chains, and the CPU oracle
+    on a bounded sample."""
+    import numpy as np
+    import torch
+    from paper_2206_05851_gb300 import bdra
+    from paper_2206_05851_gb300 import inputs as I
+
+    wl = I.collapsed_1024(**({"n_chains": n_chains} if n_chains else {}))
+    pos0 = I.initial_positions(wl)
+    S = wl.window_steps
+    stream = torch.cuda.current_stream()
+    out = {"workload": wl.name, "steps": n_steps, "window_steps": S, "dt": wl.dt}
+
+    def run(chains, p0, prec, steps, timed):
+        c = bdra.Context(chains, wl.dt, S, wl.seed, torch.from_numpy(p0).cuda(), precision=prec,
+                         max_windows=2 * steps // S + 2, thr_mask=0, bell_mask=0, stream=sptr)
+        c.step(S)                                        # warm-up
+        c.set_positions(torch.from_numpy(p0).cuda(), 0)
+        if timed:
+            bdra.bd_enable_timing(c.ptr, True)
+            bdra.bd_kernel_times(c.ptr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        times = bdra.bd_kernel_times(c.ptr) if timed else None
+        rsf = [c.replica_average(w) for w in range(steps // S)]
+        c.close()
+        return t, times, rsf
+
+    t, ((par_ms, rep_ms), (_, rep_n)), _ = run(wl.chains, pos0, bdra.BD_PREC_FP32, n_steps, True)
+    units = wl.bead_steps(n_steps)
+    out["value"] = units / t
+    out["unit"] = "bead-steps/s"
+    ops = lj_ops_per_bead_step(wl.chains[0].n_beads)
+    achieved = ops * units / (rep_ms / 1e3) / 1e12
+    peak = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": "collapsed-chain replica kernel (float32)",
+                       "avg_launch_ms": rep_ms / max(rep_n, 1), "launches": rep_n,
+                       "share_of_step": rep_ms / (t * 1e3), "ops_per_bead_step": ops,
+                       "peak_basis": "issue rate, derived (as the main line's roofline)"}
+    out["parent_kernel_share"] = par_ms / (t * 1e3)
+    # FP64 and the FP32 force error on a subset
+    sub = wl.chains[:fp64_chains]
+    psub = pos0[:sum(c.n_beads for c in sub)]
+    t64, _, r64 = run(sub, psub, bdra.BD_PREC_FP64, S, False)
+    _, _, r32 = run(sub, psub, bdra.BD_PREC_FP32, S, False)
+    out["fp64_plain"] = {"value": sum(c.n_replicas * c.n_beads for c in sub) * S / t64,
+                         "unit": "bead-steps/s", "sample": f"first {len(sub)} chains, {S} steps",
+                         "rsf_max_rel_err_fp32_vs_fp64":
+                             float(max(np.abs(a - b).max() / np.abs(b).max() for a, b in zip(r32, r64)))}
+    # CPU oracle on a bounded sample
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    sub = wl.chains[:cores]
+    psub = pos0[:sum(c.n_beads for c in sub)]
+    n_cpu = 20000          # about 10-15 s of oracle work on 16 cores
+    tc = time.perf_counter()
+    O.run(sub, wl.dt, S, n_cpu, wl.seed, psub, thr_mask=0, bell_mask=0, n_threads=cores,
+          want_replicas=False, chain_ids=list(range(len(sub))))
+    tc = time.perf_counter() - tc
+    bs = sum(c.n_replicas * c.n_beads for c in sub) * n_cpu
+    out["cpu_baseline"] = {"value": bs / tc, "unit": "bead-steps/s", "cores": cores, "kind": "oracle",
+                           "sample": f"first {len(sub)} chains, {n_cpu} steps ({tc:.1f} s wall, FP64)"}
+    return out
+
+
 def adjoint_line(sptr, n_chains=0, n_steps=0):
     """Forward run plus reverse-mode adjoint of the differentiation workload
     (256 FENE chains, N=200, 32 replicas, 2e4 steps, parent checkpoints every
@@ -319,6 +411,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only_collapsed:
+        import torch
+        from paper_2206_05851_gb300 import bdra, build as B
+        if not B.up_to_date():
+            B.build()
+        bdra.load()
+        print(json.dumps({"collapsed": collapsed_line(torch.cuda.current_stream().cuda_stream,
+                                                      args.chains)}), flush=True)
         return
     if args.only_adjoint:
         import torch
@@ -513,6 +614,8 @@ def main():
             out["adjoint"] = adjoint_line(sptr, args.adjoint_chains, args.adjoint_steps)
         if not args.no_conformation:
             out["conformation"] = conformation_line(wl, pos0, sptr)
+        if not args.no_collapsed:
+            out["collapsed"] = collapsed_line(sptr)
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(wl, pos0)
     if rank == 0:

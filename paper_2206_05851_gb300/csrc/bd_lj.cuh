@@ -5,10 +5,10 @@
 //
 // A step of a slot (G lanes, L bonds each): the bead positions follow from
 // the bonds by a prefix sum over the slot (up to a common offset, which pair
-// forces do not see); each lane gathers every bead of its slot by shuffles
-// and adds the pair forces on its own L beads (all pairs |i - j| >= 2, no
-// cutoff); the bond update of Eq. 1 then takes the difference of the bead
-// forces of its two beads: Q_b += [kappa Q_b + D (Fs_{b+1} - 2 Fs_b +
+// forces do not see); the lanes of the slot exchange bead positions by
+// shuffles and add the pair forces on their beads (all pairs |i - j| >= 2,
+// no cutoff); the bond update of Eq. 1 then takes the difference of the
+// bead forces of its two beads: Q_b += [kappa Q_b + D (Fs_{b+1} - 2 Fs_b +
 // Fs_{b-1} + Flj_{b+1} - Flj_b)] dt + noise.
 #pragma once
 
@@ -69,9 +69,36 @@ __device__ __forceinline__ T lj_slot_scan(T v, int seg)
     return v;
 }
 
+// Beads that take no part in pair forces (the padding beads of a ragged
+// slot, the partners of a lane that skips a block) are moved this far away:
+// their Lennard-Jones terms underflow (float: to zero; double: below one
+// rounding unit of any force), so no pair needs a mask.
+template <typename T> __device__ __forceinline__ T lj_far() { return T(1e12); }
+
+// The pair force between bead a (mine) and bead b: c = 12 u (x^6 - x^12) / r^2
+// with x = s / r, so that c d (d = r_b - r_a) is the force on a and -c d the
+// force on b.
+template <typename T, bool FAST>
+__device__ __forceinline__ T lj_coef(T dx, T dy, T dz, const LJConst<T>& kl)
+{
+    const T ir2 = Rsqrt<T, FAST>::rcp(fma(dx, dx, fma(dy, dy, dz * dz)));
+    const T x2 = kl.s2 * ir2;
+    const T x6 = x2 * x2 * x2;
+    return fma(-x6, x6, x6) * (kl.u12 * ir2);
+}
+
 // One Eq. 1 step of the lane's L bonds of a collapsed chain. in_slot: the
 // lane belongs to a slot, slot_base its first lane, seg its position in it, G
 // the lanes per slot. Every lane of the warp calls it.
+//
+// Pair forces: every non-adjacent pair once (Newton's third law). A lane's
+// own beads pair among themselves (k >= j + 2); for d = 1 .. G/2 a lane
+// pairs its beads with those of the lane d places further round the slot's
+// ring, keeps the forces on its beads and shuffles the reactions back to
+// that lane. Every lane pair of the ring is at one cyclic distance d <= G/2
+// from exactly one of its two lanes, except at d = G/2 for even G, which
+// only the first half of the ring takes. Beads of different lanes are
+// adjacent only across the boundary to the next lane (d = 1, no wrap).
 template <typename T, int L, bool FAST, bool TAB>
 __device__ __forceinline__ void step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L], const LaneCtx& lc,
                                               const StepConst<T, FAST>& k, const LJConst<T>& kl,
@@ -95,36 +122,57 @@ __device__ __forceinline__ void step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L]
         T x = lj_slot_scan(sx, seg) - sx, y = lj_slot_scan(sy, seg) - sy, z = lj_slot_scan(sz, seg) - sz;
 #pragma unroll
         for (int j = 0; j < L; ++j) {
-            px[j] = x; py[j] = y; pz[j] = z;
+            const bool real = lc.bead0 + j < kl.N;
+            px[j] = real ? x : lj_far<T>() * (T)(lc.bead0 + j + 1);
+            py[j] = real ? y : T(0);
+            pz[j] = real ? z : T(0);
             x += qx[j]; y += qy[j]; z += qz[j];
         }
     }
-    // pair forces on the lane's beads from every bead of the slot
     T gx[L], gy[L], gz[L];
 #pragma unroll
     for (int j = 0; j < L; ++j) gx[j] = gy[j] = gz[j] = T(0);
+    // the lane's own pairs
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+#pragma unroll
+        for (int kk = j + 2; kk < L; ++kk) {
+            const T dx = px[kk] - px[j], dy = py[kk] - py[j], dz = pz[kk] - pz[j];
+            const T c = lj_coef<T, FAST>(dx, dy, dz, kl);
+            gx[j] = fma(c, dx, gx[j]); gy[j] = fma(c, dy, gy[j]); gz[j] = fma(c, dz, gz[j]);
+            gx[kk] = fma(-c, dx, gx[kk]); gy[kk] = fma(-c, dy, gy[kk]); gz[kk] = fma(-c, dz, gz[kk]);
+        }
+    // pairs with the lanes d places round the ring
+    const int half = G >> 1;
 #pragma unroll 1
-    for (int s2 = 0; s2 < G; ++s2) {
-        const int src = in_slot ? slot_base + s2 : lane;        // < 32: slots fit the warp
+    for (int d = 1; d <= half; ++d) {
+        int pf = seg + d;
+        if (pf >= G) pf -= G;
+        int pb = seg - d;
+        if (pb < 0) pb += G;
+        const int srcf = in_slot ? slot_base + pf : lane;    // < 32: slots fit the warp
+        const int srcb = in_slot ? slot_base + pb : lane;
+        const bool skip = 2 * d == G && seg >= half;
+        const bool bonded = d == 1 && seg + 1 < G;          // my last bead - its first bead
 #pragma unroll
         for (int kk = 0; kk < L; ++kk) {
-            const T bx = __shfl_sync(0xffffffffu, px[kk], src);
-            const T by = __shfl_sync(0xffffffffu, py[kk], src);
-            const T bz = __shfl_sync(0xffffffffu, pz[kk], src);
-            const int bs = s2 * L + kk;
+            T bx = __shfl_sync(0xffffffffu, px[kk], srcf);
+            const T by = __shfl_sync(0xffffffffu, py[kk], srcf);
+            const T bz = __shfl_sync(0xffffffffu, pz[kk], srcf);
+            if (skip) bx = -lj_far<T>() * T(1000);
+            T hx = T(0), hy = T(0), hz = T(0);
 #pragma unroll
             for (int j = 0; j < L; ++j) {
-                const int b = lc.bead0 + j;
-                const int sep = b > bs ? b - bs : bs - b;
-                if (sep >= 2 && b < kl.N && bs < kl.N) {
-                    const T dx = bx - px[j], dy = by - py[j], dz = bz - pz[j];
-                    const T ir2 = Rsqrt<T, FAST>::rcp(fma(dx, dx, fma(dy, dy, dz * dz)));
-                    const T x2 = kl.s2 * ir2;
-                    const T x6 = x2 * x2 * x2;
-                    const T c = kl.u12 * fma(-x6, x6, x6) * ir2;     // 12u (x6 - x12) / r^2
-                    gx[j] = fma(c, dx, gx[j]); gy[j] = fma(c, dy, gy[j]); gz[j] = fma(c, dz, gz[j]);
-                }
+                const T dx = bx - px[j], dy = by - py[j], dz = bz - pz[j];
+                T c = lj_coef<T, FAST>(dx, dy, dz, kl);
+                if (kk == 0 && j == L - 1 && bonded) c = T(0);
+                gx[j] = fma(c, dx, gx[j]); gy[j] = fma(c, dy, gy[j]); gz[j] = fma(c, dz, gz[j]);
+                hx = fma(c, dx, hx); hy = fma(c, dy, hy); hz = fma(c, dz, hz);
             }
+            // the reaction on bead kk of this lane, from the lane d places back
+            gx[kk] -= __shfl_sync(0xffffffffu, hx, srcb);
+            gy[kk] -= __shfl_sync(0xffffffffu, hy, srcb);
+            gz[kk] -= __shfl_sync(0xffffffffu, hz, srcb);
         }
     }
     // halo: spring force of the previous lane's last bond and the next lane's

@@ -252,6 +252,35 @@ def bell_16384(n_steps: int = 250_000, n_chains: int = 16384) -> Workload:
                     bell_mask=CRIT_ALL, init_seed=4)
 
 
+# The collapsed-chain model of Sec. II in these units: length a (bead radius),
+# energy kT, and time 4 tau (tau the single-bead diffusion time, so that the
+# bead diffusivity is 1/4 as in Eq. 1 above): a paper time step of 1e-5 tau is
+# 4e-5 here, its shear rate 30 / tau is 7.5, its evolution time S = 0.015 tau
+# is 1500 steps.
+COLLAPSED_DT = 4e-5
+COLLAPSED_TAU = 4.0
+
+
+def collapsed_chain(n_replicas: int, rate: float = 7.5, n_beads: int = 50) -> Chain:
+    """The paper's collapsed chain: N = 50, kappa = 400 kT/a^2, rest length
+    2a, Lennard-Jones depth u = 1 kT and minimum 2a between non-adjacent
+    beads; steady shear (v_x = rate z)."""
+    return Chain(n_beads=n_beads, n_replicas=n_replicas, spring=SPRING_HARMONIC,
+                 flow=FLOW_SHEAR if rate else FLOW_NONE, rate=rate, H=400.0, r0=2.0,
+                 lj_u=1.0, lj_sigma=2.0)
+
+
+def collapsed_1024(n_steps: int = 15_000, n_chains: int = 1024) -> Workload:
+    """1024 collapsed chains (N=50, kappa=400, u=1) in shear at gamma-dot = 30
+    / tau, 50 replicas each, dt = 1e-5 tau, evolution time S = 0.015 tau
+    (1500 steps), compact initial globules; force sampling only (no
+    criteria)."""
+    chains = [collapsed_chain(50) for _ in range(n_chains)]
+    return Workload("collapsed_1024x_n50_r50_shear30", chains, dt=COLLAPSED_DT,
+                    window_steps=1500, n_steps=n_steps, seed=6, thr_mask=0, bell_mask=0,
+                    init_seed=6)
+
+
 def adjoint_256(n_steps: int = 20_000, n_chains: int = 256) -> Workload:
     """256 FENE chains, N=200, b=100, H=1, 32 replicas, uniaxial elongation
     Wi=5, dt=1e-3, window 100, Bell k0=1e-6 and dx F_max = 20 on the
