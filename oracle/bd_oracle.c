@@ -161,6 +161,68 @@ void ora_lj_forces(const ora_chain* ch, const double* r, double* F)
         }
 }
 
+/* Eq. 3 divided by D_0 = kT/(6 pi eta a): for r = |d| >= 2a
+ *   (3a / 4r) [(1 + 2a^2/(3r^2)) I + (1 - 2a^2/r^2) d d / r^2],
+ * and for r < 2a (overlapping beads)
+ *   (3a / 4r) (r / 2a) [(8/3 - 3r/(4a)) I + (r / 4a) d d / r^2]. */
+void ora_rpy_block(double a, const double d[3], double out[9])
+{
+    const double rr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double r = sqrt(rr);
+    const double pre = 3.0 * a / (4.0 * r);
+    double ci, cd;                       /* coefficients of I and of d d / r^2 */
+    if (r >= 2.0 * a) {
+        ci = pre * (1.0 + 2.0 * a * a / (3.0 * rr));
+        cd = pre * (1.0 - 2.0 * a * a / rr);
+    } else {
+        ci = pre * (r / (2.0 * a)) * (8.0 / 3.0 - 3.0 * r / (4.0 * a));
+        cd = pre * (r / (2.0 * a)) * (r / (4.0 * a));
+    }
+    for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y)
+            out[3 * x + y] = (x == y ? ci : 0.0) + cd * d[x] * d[y] / rr;
+}
+
+/* Eq. 2 on the diagonal blocks (D_ii = D_0 I), Eq. 3 off it. */
+void ora_rpy_matrix(int N, double a, const double* r, double* D)
+{
+    const int n = 3 * N;
+    for (int i = 0; i < n * n; ++i) D[i] = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            double blk[9];
+            if (i == j) {
+                for (int k = 0; k < 9; ++k) blk[k] = (k % 4 == 0) ? 1.0 : 0.0;
+            } else {
+                const double d[3] = { r[3 * j] - r[3 * i], r[3 * j + 1] - r[3 * i + 1],
+                                      r[3 * j + 2] - r[3 * i + 2] };
+                ora_rpy_block(a, d, blk);
+            }
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y)
+                    D[(3 * i + x) * n + 3 * j + y] = blk[3 * x + y];
+        }
+}
+
+/* Cholesky-Banachiewicz, row by row: L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj
+ * for j < i, L_ii = sqrt(A_ii - sum_{k<i} L_ik^2). */
+int ora_cholesky(int n, const double* A, double* L)
+{
+    for (int i = 0; i < n * n; ++i) L[i] = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            if (i == j) {
+                if (!(s > 0.0)) return 1;
+                L[i * n + i] = sqrt(s);
+            } else {
+                L[i * n + j] = s / L[j * n + j];
+            }
+        }
+    return 0;
+}
+
 /* Homogeneous flows v = kappa . r. Shear as in Sec. II: v = gdot z x_hat
  * (x flow direction, z gradient direction). Uniaxial elongation:
  * rate * diag(1, -1/2, -1/2). Planar elongation: rate * diag(1, -1, 0). */
@@ -181,6 +243,11 @@ void ora_flow_gradient(int flow, double rate, double kappa[9])
  * units. The spring force on bead i is F_i - F_{i-1} (F_i: force of spring i,
  * which joins beads i and i+1; F_{-1} = F_{N-1} = 0). Every drift is taken at
  * time t, so the increments are formed first and applied afterwards.
+ * With hydrodynamic interaction (hi_a > 0, Eqs. 1-3) the drift is
+ * (1/kT) sum_j D_ij F_j and the random displacement sqrt(2 dt) B xi with
+ * B B^T = D: here D = D_0 W (W the tensor of ora_rpy_matrix, D_0 = 1/4) and B
+ * = sqrt(D_0) L, L the lower Cholesky factor of W. RPY is divergence-free,
+ * so Eq. 1 needs no drift correction.
  * Returns the number of springs whose FENE floor applied. */
 int64_t ora_em_step(const ora_chain* ch, double dt, double s_min, double* r, const double* xi)
 {
@@ -200,20 +267,50 @@ int64_t ora_em_step(const ora_chain* ch, double dt, double s_min, double* r, con
     double* Flj = (double*)calloc(3 * (size_t)N, sizeof(double));
     ora_lj_forces(ch, r, Flj);
     const double amp = sqrt(2.0 * D * dt);
+    /* total force on each bead */
+    double* Fb = (double*)calloc(3 * (size_t)N, sizeof(double));
+    for (int i = 0; i < N; ++i)
+        for (int d = 0; d < 3; ++d) {
+            double fb = Flj[3 * i + d];
+            if (i + 1 < N) fb += F[3 * i + d];
+            if (i > 0)     fb -= F[3 * (i - 1) + d];
+            Fb[3 * i + d] = fb;
+        }
+    /* mobility-weighted force and correlated noise (free draining: W = I) */
+    const int n = 3 * N;
+    double* drift = (double*)calloc((size_t)n, sizeof(double));
+    double* noise = (double*)calloc((size_t)n, sizeof(double));
+    if (ch->hi_a > 0.0) {
+        double* W = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+        double* Lc = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+        ora_rpy_matrix(N, ch->hi_a, r, W);
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) drift[p] += W[p * n + q] * Fb[q];
+        if (ora_cholesky(n, W, Lc)) {
+            for (int p = 0; p < n; ++p) noise[p] = NAN;   /* not positive definite */
+        } else {
+            for (int p = 0; p < n; ++p)
+                for (int q = 0; q <= p; ++q) noise[p] += Lc[p * n + q] * xi[q];
+        }
+        free(W);
+        free(Lc);
+    } else {
+        for (int p = 0; p < n; ++p) { drift[p] = Fb[p]; noise[p] = xi[p]; }
+    }
     for (int i = 0; i < N; ++i) {
         for (int d = 0; d < 3; ++d) {
-            double fspring = Flj[3 * i + d];
-            if (i + 1 < N) fspring += F[3 * i + d];
-            if (i > 0)     fspring -= F[3 * (i - 1) + d];
             double v = kappa[3 * d + 0] * r[3 * i + 0] + kappa[3 * d + 1] * r[3 * i + 1]
                      + kappa[3 * d + 2] * r[3 * i + 2];
-            inc[3 * i + d] = (v + (D / kT) * fspring) * dt + amp * xi[3 * i + d];
+            inc[3 * i + d] = (v + (D / kT) * drift[3 * i + d]) * dt + amp * noise[3 * i + d];
         }
     }
     for (int i = 0; i < 3 * N; ++i) r[i] += inc[i];
     free(inc);
     free(F);
     free(Flj);
+    free(Fb);
+    free(drift);
+    free(noise);
     return floored;
 }
 
@@ -370,7 +467,8 @@ int ora_rsf_tangent(const ora_problem* p, int64_t n_steps, double* pos, double* 
     const int S = p->window_steps;
     if (C <= 0 || S <= 0 || n_steps < 0) return 1;
     for (int c = 0; c < C; ++c)      /* tangents of the Hooke and FENE laws only */
-        if (p->chains[c].spring == ORA_SPRING_HARMONIC || p->chains[c].lj_u > 0.0) return 1;
+        if (p->chains[c].spring == ORA_SPRING_HARMONIC || p->chains[c].lj_u > 0.0 ||
+            p->chains[c].hi_a > 0.0) return 1;
     int64_t* bead_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
     int64_t* spr_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
     bead_off[0] = spr_off[0] = 0;

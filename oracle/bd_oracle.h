@@ -31,6 +31,8 @@ typedef struct {
     double r0;             /* rest length of the harmonic spring law */
     double lj_u, lj_sigma; /* Lennard-Jones depth and minimum distance between
                               non-adjacent beads (lj_u = 0: none) */
+    double hi_a;           /* bead radius a of the RPY hydrodynamic interaction
+                              (Eqs. 2-3); 0: free draining */
 } ora_chain;
 
 typedef struct {
@@ -63,6 +65,15 @@ int ora_spring_force(int spring, double H, double b, double r0, double s_min, co
 /* Lennard-Jones forces between non-adjacent beads (|i - j| >= 2) of a
  * conformation r [N][3], added to F [N][3]: U = u sum [(s/r)^12 - 2 (s/r)^6]. */
 void ora_lj_forces(const ora_chain* ch, const double* r, double* F);
+/* Eqs. 2-3: the RPY diffusion tensor block D_ij / D_0 (D_0 = kT/(6 pi eta a),
+ * the single-bead diffusivity) for the separation d = r_j - r_i of two
+ * different beads, row-major 3x3. */
+void ora_rpy_block(double a, const double d[3], double out[9]);
+/* The full 3N x 3N tensor D / D_0 of conformation r [N][3], row-major. */
+void ora_rpy_matrix(int N, double a, const double* r, double* D);
+/* Lower Cholesky factor L (L L^T = A) of the SPD n x n matrix A, row-major,
+ * upper triangle of L zero; returns 1 if A is not positive definite. */
+int ora_cholesky(int n, const double* A, double* L);
 /* Velocity-gradient tensor kappa (row-major), v = kappa . r. */
 void ora_flow_gradient(int flow, double rate, double kappa[9]);
 /* One Euler-Maruyama step of Eq. 1 with given noise xi [N][3]; positions r [N][3]. */

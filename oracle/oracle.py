@@ -40,7 +40,8 @@ class _Chain(ctypes.Structure):
                 ("spring", ctypes.c_int32), ("flow", ctypes.c_int32),
                 ("H", ctypes.c_double), ("b", ctypes.c_double), ("rate", ctypes.c_double),
                 ("f_c", ctypes.c_double), ("k0", ctypes.c_double), ("dx", ctypes.c_double),
-                ("r0", ctypes.c_double), ("lj_u", ctypes.c_double), ("lj_sigma", ctypes.c_double)]
+                ("r0", ctypes.c_double), ("lj_u", ctypes.c_double), ("lj_sigma", ctypes.c_double),
+                ("hi_a", ctypes.c_double)]
 
 
 class _Problem(ctypes.Structure):
@@ -89,6 +90,10 @@ def lib():
         _lib.ora_run_conformation.argtypes = [P(_Problem), ctypes.c_int64, f64p, f64p, f64p, f64p,
                                               ctypes.c_int]
         _lib.ora_run_conformation.restype = ctypes.c_int
+        _lib.ora_rpy_block.argtypes = [ctypes.c_double, f64p, f64p]
+        _lib.ora_rpy_matrix.argtypes = [ctypes.c_int, ctypes.c_double, f64p, f64p]
+        _lib.ora_cholesky.argtypes = [ctypes.c_int, f64p, f64p]
+        _lib.ora_cholesky.restype = ctypes.c_int
     return _lib
 
 
@@ -100,7 +105,7 @@ def _chain_struct(ch) -> _Chain:
     return _Chain(int(ch.n_beads), int(ch.n_replicas), int(ch.spring), int(ch.flow),
                   float(ch.H), float(ch.b), float(ch.rate), float(ch.f_c), float(ch.k0),
                   float(ch.dx), float(getattr(ch, "r0", 0.0)), float(getattr(ch, "lj_u", 0.0)),
-                  float(getattr(ch, "lj_sigma", 0.0)))
+                  float(getattr(ch, "lj_sigma", 0.0)), float(getattr(ch, "hi_a", 0.0)))
 
 
 # ---------------------------------------------------------------------------
@@ -167,6 +172,31 @@ def lj_forces(chain, r: np.ndarray) -> np.ndarray:
     cs = _chain_struct(chain)
     lib().ora_lj_forces(ctypes.byref(cs), _p(rr, ctypes.c_double), _p(F, ctypes.c_double))
     return F
+
+
+def rpy_block(a: float, d) -> np.ndarray:
+    """Eq. 3 / D_0 for the separation d = r_j - r_i of two beads of radius a."""
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    out = np.zeros(9)
+    lib().ora_rpy_block(a, _p(dd, ctypes.c_double), _p(out, ctypes.c_double))
+    return out.reshape(3, 3)
+
+
+def rpy_matrix(a: float, r: np.ndarray) -> np.ndarray:
+    """The 3N x 3N diffusion tensor / D_0 of conformation r [N][3]."""
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    N = len(rr)
+    D = np.zeros((3 * N, 3 * N))
+    lib().ora_rpy_matrix(N, a, _p(rr, ctypes.c_double), _p(D, ctypes.c_double))
+    return D
+
+
+def cholesky(A: np.ndarray):
+    """(lower factor, status) of the oracle's Cholesky."""
+    a = np.ascontiguousarray(A, dtype=np.float64)
+    L = np.zeros_like(a)
+    st = lib().ora_cholesky(len(a), _p(a, ctypes.c_double), _p(L, ctypes.c_double))
+    return L, int(st)
 
 
 def flow_gradient(flow: int, rate: float) -> np.ndarray:

@@ -56,6 +56,7 @@ class Chain:
     r0: float = 0.0        # rest length of SPRING_HARMONIC
     lj_u: float = 0.0      # Lennard-Jones depth between non-adjacent beads (0: none)
     lj_sigma: float = 0.0  # Lennard-Jones zero-force (minimum) distance
+    hi_a: float = 0.0      # bead radius of the RPY hydrodynamic interaction (0: free draining)
 
 
 @dataclasses.dataclass
