@@ -95,6 +95,13 @@ typedef struct {
                             [(s/r)^12 - 2 (s/r)^6] (Sec. II); 0 = none; needs
                             BD_SPRING_HARMONIC */
     double lj_sigma;     /* its minimum distance s (> 0 when lj_u > 0) */
+    double hi_a;         /* bead radius a of the Rotne-Prager-Yamakawa hydrodynamic
+                            interaction (Eqs. 1-3), in the chain's length unit;
+                            0 = free draining. With hi_a > 0: n_beads <= 64, no
+                            adjoint (checkpoint_steps 0) and no
+                            BD_FLAG_CONFORMATION; every step of every slot
+                            factors the 3N x 3N diffusion tensor (Cholesky) for
+                            the correlated noise */
 } bd_chain_desc;
 
 typedef struct {
@@ -229,10 +236,13 @@ bd_status bd_get_info(bd_ctx* ctx, bd_info* out);
 bd_status bd_autotune(bd_ctx* ctx, int32_t probe_steps, int32_t force);
 
 /* The current plan: variant[c] (springs per lane, plus 100 for two replicas
- * per lane) and groups[c] (warp work items) per chain, host arrays of
- * n_chains; cost_ns (host, may be NULL) receives the per-warp-step cost of
- * each compiled variant in the order float32 {4, 7, 10, 13, 16, 104, 107} or
- * float64 {2, 4, 7, 10, 13, 16}. Any pointer may be NULL. */
+ * per lane, 200 for the collapsed-chain step; 300 for hydrodynamic
+ * interaction, one CTA per replica) and groups[c] (work items) per chain,
+ * host arrays of n_chains; cost_ns (host, may be NULL) receives the
+ * per-warp-step cost of each compiled tile variant, 11 values in the order
+ * float32 {4, 7, 10, 13, 16, 104, 107, 202, 204, 207, 216} or 10 values in
+ * the order float64 {2, 4, 7, 10, 13, 16, 202, 204, 207, 216}. Any pointer
+ * may be NULL. */
 bd_status bd_get_plan(bd_ctx* ctx, int32_t* variant, int32_t* groups, double* cost_ns);
 
 /* Kernel timing for measurement tools. Each chunk graph that bd_step launches

@@ -39,7 +39,8 @@ class bd_chain_desc(ctypes.Structure):
                 ("spring", ctypes.c_int32), ("flow", ctypes.c_int32),
                 ("H", ctypes.c_double), ("b", ctypes.c_double), ("rate", ctypes.c_double),
                 ("f_c", ctypes.c_double), ("k0", ctypes.c_double), ("dx", ctypes.c_double),
-                ("r0", ctypes.c_double), ("lj_u", ctypes.c_double), ("lj_sigma", ctypes.c_double)]
+                ("r0", ctypes.c_double), ("lj_u", ctypes.c_double), ("lj_sigma", ctypes.c_double),
+                ("hi_a", ctypes.c_double)]
 
 
 class bd_config(ctypes.Structure):
@@ -161,7 +162,8 @@ def make_config(chains: Sequence, dt: float, window_steps: int, seed: int, preci
         bd_chain_desc(int(c.n_beads), int(c.n_replicas), int(c.spring), int(c.flow),
                       float(c.H), float(c.b), float(c.rate), float(c.f_c), float(c.k0),
                       float(c.dx), float(getattr(c, "r0", 0.0)), float(getattr(c, "lj_u", 0.0)),
-                      float(getattr(c, "lj_sigma", 0.0))) for c in chains])
+                      float(getattr(c, "lj_sigma", 0.0)), float(getattr(c, "hi_a", 0.0)))
+              for c in chains])
     cfg = bd_config(len(chains), int(window_steps), arr, float(dt), int(seed), int(precision),
                     int(flags), int(thr_mask), int(bell_mask), int(max_windows), float(s_min),
                     stream, int(lanes_hint), int(layout_hint), int(checkpoint_steps))
@@ -248,7 +250,8 @@ def bd_get_plan(ctx: int, n_chains: int, precision: int = BD_PREC_FP32):
     """(variant per chain, groups per chain, {variant: cost ns per warp-step})."""
     v = np.zeros(n_chains, dtype=np.int32)
     g = np.zeros(n_chains, dtype=np.int32)
-    names = [2, 4, 7, 10, 13, 16] if precision == BD_PREC_FP64 else [4, 7, 10, 13, 16, 104, 107]
+    names = ([2, 4, 7, 10, 13, 16, 202, 204, 207, 216] if precision == BD_PREC_FP64
+             else [4, 7, 10, 13, 16, 104, 107, 202, 204, 207, 216])
     c = np.zeros(len(names))
     _check(load().bd_get_plan(ctx, v.ctypes.data, g.ctypes.data, c.ctypes.data), ctx)
     return v, g, dict(zip(names, c.tolist()))

@@ -23,13 +23,17 @@ struct VarClass {      // one persistent replica launch: the work items of one s
     int variant;
     int item_begin, item_count;
     int grid, threads;
+    size_t smem;       // dynamic shared memory per CTA
 };
 struct ParClass {      // one parent-kernel launch: the parent warps of one tile
     int L, threads, grid;
     int warp_begin, warp_count;
     bool lj;           // collapsed chains (harmonic springs, pair forces)
+    bool hi;           // hydrodynamic interaction: one CTA per parent
+    size_t smem;
 };
 constexpr int kParentLJKey = 1000;   // planner key offset of the collapsed-chain parents
+constexpr int kParentHIKey = 2000;   // planner key of the parents with hydrodynamic interaction
 
 struct AdjClass {      // one adjoint replica-window launch: the work items of one tile
     int L;
@@ -242,9 +246,10 @@ double default_variant_cost(int v)
 // items, and the cost is their issue work per useful bead-step. Collapsed
 // chains (harmonic springs) take the collapsed-chain variants, the others
 // the rest; the tile and layout hints apply to the latter.
-VariantChoice choose_variant(const bd_ctx* ctx, int N, int R, bool collapsed)
+VariantChoice choose_variant(const bd_ctx* ctx, int N, int R, bool collapsed, bool hi)
 {
     const bd_config& cfg = ctx->cfg;
+    if (hi) return {kHIBase, 1, R, 0.0};      // one CTA per replica
     const int* vars = ctx->f64 ? kVariantsF64 : kVariantsF32;
     const int nv = ctx->f64 ? kNumVariantsF64 : kNumVariantsF32;
     VariantChoice best{0, 0, 0, 1e300};
@@ -305,7 +310,7 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
         bool ok = false;
         for (int t = 0; t < nv; ++t) {
             const bool paired = variant_paired(vars[t]);
-            if (variant_lj(vars[t]) || variant_tile(vars[t]) != cfg->lanes_hint) continue;
+            if (variant_lj(vars[t]) || variant_tile(vars[t]) != cfg->lanes_hint) continue;   // FENE/Hooke variants
             if ((cfg->layout_hint == 1 && paired) || (cfg->layout_hint == 2 && !paired)) continue;
             ok = true;
         }
@@ -329,6 +334,17 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
             return fail(ctx, BD_E_INVALID, "chain %d: Lennard-Jones needs the harmonic law and lj_sigma > 0", c);
         if (d.spring == BD_SPRING_HARMONIC && cfg->checkpoint_steps > 0)
             return fail(ctx, BD_E_INVALID, "chain %d: the adjoint supports Hooke and FENE chains only", c);
+        if (!(d.hi_a >= 0) || !std::isfinite(d.hi_a))
+            return fail(ctx, BD_E_INVALID, "chain %d: hi_a must be >= 0", c);
+        if (d.hi_a > 0) {
+            if (d.n_beads > kHIMaxBeadsHost)
+                return fail(ctx, BD_E_INVALID, "chain %d: hydrodynamic interaction needs n_beads <= %d",
+                            c, kHIMaxBeadsHost);
+            if (cfg->checkpoint_steps > 0)
+                return fail(ctx, BD_E_INVALID, "chain %d: no adjoint with hydrodynamic interaction", c);
+            if (cfg->flags & BD_FLAG_CONFORMATION)
+                return fail(ctx, BD_E_INVALID, "chain %d: no Eq. 5 diagnostics with hydrodynamic interaction", c);
+        }
         if (d.flow < BD_FLOW_NONE || d.flow > BD_FLOW_PLANAR)
             return fail(ctx, BD_E_INVALID, "chain %d: unknown flow %d", c, d.flow);
         if (!(d.H > 0) || !std::isfinite(d.H)) return fail(ctx, BD_E_INVALID, "chain %d: H must be > 0", c);
@@ -338,7 +354,7 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
     }
     if (cfg->lanes_hint) {
         for (int c = 0; c < cfg->n_chains; ++c)
-            if (cfg->chains[c].spring != BD_SPRING_HARMONIC &&
+            if (cfg->chains[c].spring != BD_SPRING_HARMONIC && !(cfg->chains[c].hi_a > 0) &&
                 (cfg->chains[c].n_beads + cfg->lanes_hint - 1) / cfg->lanes_hint > 32)
                 return fail(ctx, BD_E_INVALID, "lanes_hint %d too small for chain %d (N=%d)",
                             cfg->lanes_hint, c, cfg->chains[c].n_beads);
@@ -359,10 +375,12 @@ bd_status plan(bd_ctx* ctx)
         const bd_chain_desc& d = ctx->chains[c];
         ChainDev& h = ctx->h_chains[c];
         const bool collapsed = d.spring == BD_SPRING_HARMONIC;
-        const VariantChoice vc = choose_variant(ctx, d.n_beads, d.n_replicas, collapsed);
+        const bool hi = d.hi_a > 0;
+        const VariantChoice vc = choose_variant(ctx, d.n_beads, d.n_replicas, collapsed, hi);
         if (!vc.variant)
             return fail(ctx, BD_E_INVALID, "chain %d: no step variant fits N=%d", c, d.n_beads);
-        h.N = d.n_beads; h.R = d.n_replicas; h.n_groups = vc.groups; h.pad = 0;
+        h.N = d.n_beads; h.R = d.n_replicas; h.n_groups = vc.groups; h.spring = d.spring;
+        h.hi_a = d.hi_a;
         h.bead_off = bead; h.slot_bead_off = slot_bead; h.state_off = bond;
         h.spr_off = spr; h.part_off = part;
         h.rep_off = rep; h.bpart_off = bpart;
@@ -399,8 +417,12 @@ bd_status plan(bd_ctx* ctx)
             items.push_back(ItemDev{c, g, begin, cnt, vc.variant, 0});
             begin += cnt;
         }
-        const int Lp = choose_parent_tile(d.n_beads);
-        par.push_back({{Lp + (collapsed ? kParentLJKey : 0), (d.n_beads + Lp - 1) / Lp}, c});
+        if (hi) {
+            par.push_back({{kParentHIKey, 1}, c});
+        } else {
+            const int Lp = choose_parent_tile(d.n_beads);
+            par.push_back({{Lp + (collapsed ? kParentLJKey : 0), (d.n_beads + Lp - 1) / Lp}, c});
+        }
         bead += d.n_beads;
         slot_bead += (int64_t)(d.n_replicas + 1) * d.n_beads;
         bond += (int64_t)(d.n_replicas + 1) * nb;
@@ -422,10 +444,22 @@ bd_status plan(bd_ctx* ctx)
     const int threads = ctx->f64 ? persist_threads_f64() : persist_threads_f32();
     for (size_t k = 0; k < items.size(); ++k) {
         if (ctx->var_classes.empty() || ctx->var_classes.back().variant != items[k].variant)
-            ctx->var_classes.push_back(VarClass{items[k].variant, (int)k, 0, 0, threads});
+            ctx->var_classes.push_back(VarClass{items[k].variant, (int)k, 0, 0, threads, 0});
         ctx->var_classes.back().item_count++;
     }
     for (VarClass& vc : ctx->var_classes) {
+        if (variant_hi(vc.variant)) {          // one CTA per replica
+            cudaError_t e = ctx->f64 ? hi_prepare_f64() : hi_prepare_f32();
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, BD_E_CUDA, "hydrodynamic-interaction kernels: %s", cudaGetErrorString(e));
+            }
+            vc.threads = kHIThreadsHost;
+            vc.grid = vc.item_count;
+            vc.smem = ctx->f64 ? hi_smem_f64() : hi_smem_f32();
+            continue;
+        }
+        vc.smem = ctx->f64 ? persist_smem_f64(vc.variant) : persist_smem_f32(vc.variant);
         int per_sm = 1;
         cudaError_t e = ctx->f64 ? persist_blocks_per_sm_f64(vc.variant, ctx->conf, &per_sm)
                                  : persist_blocks_per_sm_f32(vc.variant, ctx->conf, &per_sm);
@@ -443,11 +477,16 @@ bd_status plan(bd_ctx* ctx)
     ctx->h_parent_warps.clear();
     ctx->par_classes.clear();
     for (size_t k = 0; k < par.size();) {
-        const int key = par[k].first.first, G = par[k].first.second, P = 32 / G;
-        const int L = key % kParentLJKey;
-        const bool lj = key >= kParentLJKey;
-        if (ctx->par_classes.empty() || ctx->par_classes.back().L != L || ctx->par_classes.back().lj != lj)
-            ctx->par_classes.push_back(ParClass{L, kParentThreads, 0, (int)ctx->h_parent_warps.size(), 0, lj});
+        const int key = par[k].first.first, G = par[k].first.second;
+        const bool hi = key == kParentHIKey;
+        const int P = hi ? 1 : 32 / G;           // one CTA per parent with hydrodynamic interaction
+        const int L = hi ? 0 : key % kParentLJKey;
+        const bool lj = !hi && key >= kParentLJKey;
+        if (ctx->par_classes.empty() || ctx->par_classes.back().L != L || ctx->par_classes.back().lj != lj ||
+            ctx->par_classes.back().hi != hi)
+            ctx->par_classes.push_back(ParClass{L, hi ? kHIThreadsHost : kParentThreads, 0,
+                                                (int)ctx->h_parent_warps.size(), 0, lj, hi,
+                                                hi ? (ctx->f64 ? hi_smem_f64() : hi_smem_f32()) : 0});
         size_t e = k;
         while (e < par.size() && par[e].first == par[k].first) ++e;
         for (size_t j = k; j < e; j += P) {
@@ -459,7 +498,7 @@ bd_status plan(bd_ctx* ctx)
         k = e;
     }
     for (ParClass& pc : ctx->par_classes) {
-        const int per_cta = pc.threads / 32;
+        const int per_cta = pc.hi ? 1 : pc.threads / 32;
         pc.grid = (pc.warp_count + per_cta - 1) / per_cta;
     }
     // snapshot chunk: up to 64 windows, capped at ~512 MB
@@ -534,10 +573,13 @@ cudaKernelNodeParams parent_node(const bd_ctx* ctx, size_t k, StepParams* pk, vo
     const ParClass& pc = ctx->par_classes[k];
     args[0] = pk;
     cudaKernelNodeParams kp = {};
-    kp.func = const_cast<void*>(ctx->f64 ? parent_func_f64(pc.L, pc.lj) : parent_func_f32(pc.L, pc.lj));
+    if (pc.hi)
+        kp.func = const_cast<void*>(ctx->f64 ? hi_parent_func_f64() : hi_parent_func_f32());
+    else
+        kp.func = const_cast<void*>(ctx->f64 ? parent_func_f64(pc.L, pc.lj) : parent_func_f32(pc.L, pc.lj));
     kp.gridDim = dim3(pc.grid);
     kp.blockDim = dim3(pc.threads);
-    kp.sharedMemBytes = 0;
+    kp.sharedMemBytes = (unsigned)pc.smem;
     kp.kernelParams = args;
     return kp;
 }
@@ -547,11 +589,14 @@ cudaKernelNodeParams replica_node(const bd_ctx* ctx, size_t k, StepParams* rk, v
     const VarClass& vc = ctx->var_classes[k];
     args[0] = rk;
     cudaKernelNodeParams kp = {};
-    kp.func = const_cast<void*>(ctx->f64 ? persist_func_f64(vc.variant, ctx->conf)
-                                         : persist_func_f32(vc.variant, ctx->conf));
+    if (variant_hi(vc.variant))
+        kp.func = const_cast<void*>(ctx->f64 ? hi_replica_func_f64() : hi_replica_func_f32());
+    else
+        kp.func = const_cast<void*>(ctx->f64 ? persist_func_f64(vc.variant, ctx->conf)
+                                             : persist_func_f32(vc.variant, ctx->conf));
     kp.gridDim = dim3(vc.grid);
     kp.blockDim = dim3(vc.threads);
-    kp.sharedMemBytes = (unsigned)(ctx->f64 ? persist_smem_f64(vc.variant) : persist_smem_f32(vc.variant));
+    kp.sharedMemBytes = (unsigned)vc.smem;
     kp.kernelParams = args;
     return kp;
 }
@@ -773,7 +818,8 @@ bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost
         for (int c = 0; c < ctx->cfg.n_chains; ++c) {
             const int N = ctx->chains[c].n_beads, R = ctx->chains[c].n_replicas;
             const int G = (N + L - 1) / L;
-            if (G > 32 || variant_lj(v) != (ctx->chains[c].spring == BD_SPRING_HARMONIC)) continue;
+            if (G > 32 || variant_lj(v) != (ctx->chains[c].spring == BD_SPRING_HARMONIC) ||
+                ctx->chains[c].hi_a > 0) continue;
             const int per_warp = (variant_paired(v) ? 2 : 1) * (32 / G);
             const int groups = (R + per_warp - 1) / per_warp;
             int begin = 0;

@@ -18,7 +18,7 @@ namespace bdra {
 // every slot (0 = parent, 1..R = replicas) are stored slot-major:
 // state[(state_off + slot * (N-1) + i) * 3 + d].
 struct ChainDev {
-    int32_t N, R, n_groups, pad;
+    int32_t N, R, n_groups, spring;   // spring: BD_SPRING_* law
     int64_t bead_off;    // first bead of this chain in a [sum N][3] position array
     int64_t slot_bead_off;  // first bead in an all-slot [sum (R+1) N][3] array
     int64_t state_off;   // bond index of slot 0, bond 0
@@ -30,6 +30,7 @@ struct ChainDev {
     double kxx, kyy, kzz, kxz;   // velocity gradient, v = kappa . r
     double f_c, k0, dx;  // threshold force; Bell rate k0 exp(f dx)
     double r0, lj_u, lj_s2;  // harmonic rest length; Lennard-Jones depth and min distance^2
+    double hi_a;         // RPY bead radius (hydrodynamic interaction); 0: free draining
     // float32 step constants, rounded once on the host from the values
     // above (so the kernels never rebuild them from doubles): H, H/b, D dt,
     // sqrt(2 D dt) times the fast normals' sign, kappa_xx dt, kappa_yy dt,
@@ -64,6 +65,8 @@ constexpr int32_t kPairBase = 100;
 // Collapsed-chain variants (harmonic springs with rest length, Lennard-Jones
 // pair forces; one replica per lane): code kLJBase + L.
 constexpr int32_t kLJBase = 200;
+// Chains with hydrodynamic interaction (Eqs. 1-3): one CTA per replica.
+constexpr int32_t kHIBase = 300;
 
 struct StepParams {
     const ChainDev* chains;

@@ -1,0 +1,569 @@
+// Hydrodynamic interaction (Eqs. 1-3): chains whose beads move with the
+// Rotne-Prager-Yamakawa diffusion tensor. In the units of Eq. 1 used here the
+// single-bead diffusivity is D_0 = 1/4 and D = D_0 W, with W_ii = I (Eq. 2)
+// and, for beads i != j at separation d = r_j - r_i, r = |d| (Eq. 3 over D_0,
+// a the bead radius):
+//   r >= 2a:  W_ij = (3a / 4r) [(1 + 2a^2/(3r^2)) I + (1 - 2a^2/r^2) d d / r^2]
+//   r <  2a:  W_ij = (1 - 9r/(32a)) I + (3r/(32a)) d d / r^2.
+// A step moves bead i by [kappa r_i + D_0 sum_j W_ij F_j] dt plus a random
+// displacement of covariance 2 D dt, i.e. sqrt(2 D_0 dt) L xi with L the lower
+// Cholesky factor of W and xi the bead normals (RPY is divergence-free, so
+// no drift correction).
+//
+// One CTA integrates one slot (parent or replica) of a chain of N <= 64
+// beads, its positions (centre-of-mass frame) in shared memory. The 3N x 3N
+// tensor is held as 4 x 4 tiles of its lower triangle in the registers of
+// the CTA's threads (tile t of the row-major lower order belongs to thread
+// t mod kHIThreads). Per step:
+//   - bead forces (springs, Lennard-Jones) and bead normals, one thread per bead;
+//   - the tensor's tiles, each by its owner, from the positions;
+//   - the mobility-weighted force u = W F from per-tile partial products,
+//     summed in a fixed order (no atomics: the results do not depend on timing);
+//   - right-looking blocked Cholesky over tile columns K: the owner of (K, K)
+//     factors it, the owners of (I, K) solve against it, and every owner of a
+//     tile (I, J), K < J <= I, subtracts L_IK L_JK^T - two barriers a column;
+//   - the correlated noise L xi from per-tile partials, the update and the
+//     centre-of-mass shift.
+#pragma once
+
+#include "bd_lj.cuh"
+
+namespace bdra {
+
+constexpr int kHIThreads = 256;
+constexpr int kHIMaxBeads = 64;
+constexpr int kHINT = (3 * kHIMaxBeads + 3) / 4;                  // tile rows of the largest tensor
+constexpr int kHITiles = kHINT * (kHINT + 1) / 2;                 // its lower tiles
+constexpr int kHIMaxT = (kHITiles + kHIThreads - 1) / kHIThreads; // tiles per thread
+
+template <typename T> struct HIShared {
+    alignas(16) T pos[4 * kHINT];      // bead positions [3N] (COM frame); padding 0
+    alignas(16) T frc[4 * kHINT];      // bead forces [3N]; padding 0
+    alignas(16) T xi[4 * kHINT];       // bead normals [3N]; padding 0
+    alignas(16) T diag[16];            // factor of the current diagonal tile
+    alignas(16) T panel[kHINT][16];    // factor tiles of the current tile column, by tile row
+    alignas(16) T part[kHITiles][8];   // per-tile partial products
+    T com[3];
+};
+
+__device__ __forceinline__ int hi_tile(int I, int J) { return I * (I + 1) / 2 + J; }
+
+// The RPY block of two different beads as c_i I + c_d d d^T.
+template <typename T, bool FAST>
+__device__ __forceinline__ void rpy_coef(T dx, T dy, T dz, T a, T& ci, T& cd)
+{
+    const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const T ir = Rsqrt<T, FAST>::rsqrt(r2);
+    const T r = r2 * ir;
+    if (r >= T(2) * a) {
+        const T pre = T(0.75) * a * ir;
+        const T a2r2 = a * a * ir * ir;
+        ci = pre * fma(T(2.0 / 3.0), a2r2, T(1));
+        cd = pre * fma(T(-2), a2r2, T(1)) * (ir * ir);
+    } else {
+        ci = fma(T(-9.0 / 32.0) / a, r, T(1));
+        cd = (T(3.0 / 32.0) / a) * ir;
+    }
+}
+
+// Per-thread state of the tensor tiles.
+template <typename T> struct HITiles {
+    T A[kHIMaxT][16];    // row-major 4 x 4
+    int I[kHIMaxT], J[kHIMaxT];   // -1: no tile
+};
+
+template <typename T>
+__device__ __forceinline__ void hi_tiles_init(HITiles<T>& tl, int NT)
+{
+    const int total = NT * (NT + 1) / 2;
+#pragma unroll
+    for (int s = 0; s < kHIMaxT; ++s) {
+        const int t = threadIdx.x + s * kHIThreads;
+        int I = -1, J = -1;
+        if (t < total) {
+            I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+            while (I * (I + 1) / 2 > t) --I;
+            while ((I + 1) * (I + 2) / 2 <= t) ++I;
+            J = t - I * (I + 1) / 2;
+        }
+        tl.I[s] = I;
+        tl.J[s] = J;
+    }
+}
+
+// Entries of one tile of W from the RPY coefficients of the (at most) 2 x 2
+// bead pairs it covers. The row of entry i is 3 br + PR + i (PR = r0 mod 3,
+// the tile's first row r0 = 4I), so its bead offset u and component x are
+// compile-time constants here, as are those of the columns (PC).
+template <typename T, int PR, int PC>
+__device__ __forceinline__ void hi_fill(T (&A)[16], const T (&ci)[2][2], const T (&cd)[2][2],
+                                        const T (&d)[2][2][3], int r0, int c0, int br, int bc, int n)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = (PR + i) % 3, u = (PR + i) / 3;
+            const int y = (PC + j) % 3, v = (PC + j) / 3;
+            const int p = r0 + i, q = c0 + j;
+            T w;
+            if (p >= n || q >= n) w = p == q ? T(1) : T(0);          // padding: identity
+            else if (br + u == bc + v) w = x == y ? T(1) : T(0);      // Eq. 2
+            else {
+                w = cd[u][v] * d[u][v][x] * d[u][v][y];
+                if (x == y) w += ci[u][v];
+            }
+            A[4 * i + j] = w;
+        }
+}
+
+// W's tiles from the positions (n = 3N rows; rows and columns >= n are the
+// identity's).
+template <typename T, bool FAST>
+__device__ __forceinline__ void hi_assemble(HITiles<T>& tl, const T* pos, int n, T a)
+{
+#pragma unroll
+    for (int s = 0; s < kHIMaxT; ++s) {
+        if (tl.I[s] < 0) continue;
+        const int r0 = 4 * tl.I[s], c0 = 4 * tl.J[s];
+        const int br = r0 / 3, bc = c0 / 3;
+        T ci[2][2], cd[2][2], d[2][2][3];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int bi = br + u, bj = bc + v;
+                d[u][v][0] = d[u][v][1] = d[u][v][2] = T(0);
+                ci[u][v] = cd[u][v] = T(0);
+                if (3 * bi < n && 3 * bj < n && bi != bj) {
+                    d[u][v][0] = pos[3 * bj] - pos[3 * bi];
+                    d[u][v][1] = pos[3 * bj + 1] - pos[3 * bi + 1];
+                    d[u][v][2] = pos[3 * bj + 2] - pos[3 * bi + 2];
+                    rpy_coef<T, FAST>(d[u][v][0], d[u][v][1], d[u][v][2], a, ci[u][v], cd[u][v]);
+                }
+            }
+        switch (3 * (r0 - 3 * br) + (c0 - 3 * bc)) {
+        case 0: hi_fill<T, 0, 0>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
+        case 1: hi_fill<T, 0, 1>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
+        case 2: hi_fill<T, 0, 2>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
+        case 3: hi_fill<T, 1, 0>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
+        case 4: hi_fill<T, 1, 1>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
+        case 5: hi_fill<T, 1, 2>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
+        case 6: hi_fill<T, 2, 0>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
+        case 7: hi_fill<T, 2, 1>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
+        default: hi_fill<T, 2, 2>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
+        }
+    }
+}
+
+// Factor of a diagonal tile (lower part; the upper part is left as is).
+template <typename T>
+__device__ __forceinline__ void hi_chol4(T (&A)[16])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        T s = A[5 * j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = fma(-A[4 * j + k], A[4 * j + k], s);
+        const T l = sqrt(s);
+        A[5 * j] = l;
+        const T il = T(1) / l;
+#pragma unroll
+        for (int i = j + 1; i < 4; ++i) {
+            T v = A[4 * i + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v = fma(-A[4 * i + k], A[4 * j + k], v);
+            A[4 * i + j] = v * il;
+        }
+    }
+}
+
+// X L^T = A for a tile below the diagonal tile L (lower).
+template <typename T>
+__device__ __forceinline__ void hi_trsm4(T (&A)[16], const T* L)
+{
+    T inv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) inv[c] = T(1) / L[5 * c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            T v = A[4 * r + c];
+#pragma unroll
+            for (int k = 0; k < c; ++k) v = fma(-A[4 * r + k], L[4 * c + k], v);
+            A[4 * r + c] = v * inv[c];
+        }
+}
+
+// In-place lower Cholesky factor of the CTA's tiles (every thread calls it).
+template <typename T>
+__device__ __forceinline__ void hi_cholesky(HITiles<T>& tl, HIShared<T>& sm, int NT)
+{
+#pragma unroll 1
+    for (int K = 0; K < NT; ++K) {
+#pragma unroll
+        for (int s = 0; s < kHIMaxT; ++s)
+            if (tl.I[s] == K && tl.J[s] == K) {
+                hi_chol4(tl.A[s]);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) sm.diag[e] = tl.A[s][e];
+            }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < kHIMaxT; ++s)
+            if (tl.J[s] == K && tl.I[s] > K) {
+                hi_trsm4(tl.A[s], sm.diag);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) sm.panel[tl.I[s]][e] = tl.A[s][e];
+            }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < kHIMaxT; ++s)
+            if (tl.J[s] > K) {
+                const T* Pi = sm.panel[tl.I[s]];
+                const T* Pj = sm.panel[tl.J[s]];
+                T li[16], lj[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) { li[e] = Pi[e]; lj[e] = Pj[e]; }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        T v = tl.A[s][4 * i + j];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) v = fma(-li[4 * i + k], lj[4 * j + k], v);
+                        tl.A[s][4 * i + j] = v;
+                    }
+            }
+    }
+}
+
+// Bead forces into sm.frc (springs and pair forces), one thread per bead;
+// returns the FENE floor count of the thread's spring.
+template <typename T, bool FAST>
+__device__ __forceinline__ int hi_forces(HIShared<T>& sm, int N, const StepConst<T, FAST>& k,
+                                         const ChainDev& ch, bool harmonic, bool lj)
+{
+    const int b = threadIdx.x;
+    int floored = 0;
+    if (b < N) {
+        T f[3] = {T(0), T(0), T(0)};
+        const T r0 = (T)ch.r0;
+        // springs b (to bead b+1) and b-1 (from bead b-1)
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int i = b - side;               // spring index
+            if (i < 0 || i + 1 >= N) continue;
+            const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
+            const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];
+            const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
+            T c;
+            if (harmonic) {
+                c = harmonic_coef<T, FAST>(qx, qy, qz, k.H, r0);
+            } else {
+                int fl = 0;
+                c = spring_coef<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin, fl);
+                if (side == 0) floored += fl;
+            }
+            const T sg = side == 0 ? T(1) : T(-1);
+            f[0] = fma(sg * c, qx, f[0]); f[1] = fma(sg * c, qy, f[1]); f[2] = fma(sg * c, qz, f[2]);
+        }
+        if (lj) {
+            LJConst<T> kl;
+            kl.load(ch);
+            const T x0 = sm.pos[3 * b], y0 = sm.pos[3 * b + 1], z0 = sm.pos[3 * b + 2];
+#pragma unroll 1
+            for (int j = 0; j < N; ++j) {
+                if (j == b || j == b - 1 || j == b + 1) continue;
+                const T dx = sm.pos[3 * j] - x0, dy = sm.pos[3 * j + 1] - y0, dz = sm.pos[3 * j + 2] - z0;
+                const T c = lj_coef<T, FAST>(dx, dy, dz, kl);
+                f[0] = fma(c, dx, f[0]); f[1] = fma(c, dy, f[1]); f[2] = fma(c, dz, f[2]);
+            }
+        }
+        sm.frc[3 * b] = f[0];
+        sm.frc[3 * b + 1] = f[1];
+        sm.frc[3 * b + 2] = f[2];
+    }
+    return floored;
+}
+
+// Positions from bonds [nb][3] (bead 0 at the origin), then the COM shift.
+template <typename T>
+__device__ __forceinline__ void hi_load_bonds(HIShared<T>& sm, const T* bonds, int N)
+{
+    __syncthreads();     // every thread is done reading the old positions
+    if (threadIdx.x < 3) {
+        const int c = threadIdx.x;
+        T x = T(0);
+        sm.pos[c] = x;
+        for (int i = 0; i + 1 < N; ++i) {
+            x += bonds[3 * i + c];
+            sm.pos[3 * (i + 1) + c] = x;
+        }
+        T s = T(0);
+        for (int i = 0; i < N; ++i) s += sm.pos[3 * i + c];
+        sm.com[c] = s / (T)N;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 * N) sm.pos[threadIdx.x] -= sm.com[threadIdx.x % 3];
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void hi_store_bonds(const HIShared<T>& sm, T* bonds, int N)
+{
+    for (int e = threadIdx.x; e < 3 * (N - 1); e += blockDim.x) bonds[e] = sm.pos[e + 3] - sm.pos[e];
+}
+
+// One step t -> t + 1 of the CTA's slot. Returns the thread's floor count.
+template <typename T, bool FAST>
+__device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T>& tl, const ChainDev& ch,
+                                       const StepConst<T, FAST>& k, const StepParams& p, int N, int NT,
+                                       uint32_t slot_key, uint32_t chain, uint32_t step, bool harmonic,
+                                       bool lj)
+{
+    const int n = 3 * N;
+    const int tid = threadIdx.x;
+    const int floored = hi_forces<T, FAST>(sm, N, k, ch, harmonic, lj);
+    if (tid < N) {
+        T z0, z1, z2;
+        bead_noise<T, FAST>((uint32_t)tid, slot_key, step, chain, p, z0, z1, z2);
+        sm.xi[3 * tid] = z0;
+        sm.xi[3 * tid + 1] = z1;
+        sm.xi[3 * tid + 2] = z2;
+    }
+    hi_assemble<T, FAST>(tl, sm.pos, n, (T)ch.hi_a);
+    __syncthreads();
+    // u = W F: per tile W_IJ F_J (rows I) and, below the diagonal, W_IJ^T F_I (rows J)
+#pragma unroll
+    for (int s = 0; s < kHIMaxT; ++s) {
+        if (tl.I[s] < 0) continue;
+        const int I = tl.I[s], J = tl.J[s];
+        T* out = sm.part[hi_tile(I, J)];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            T v = T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v = fma(tl.A[s][4 * i + j], sm.frc[4 * J + j], v);
+            out[i] = v;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            T v = T(0);
+            if (J < I) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v = fma(tl.A[s][4 * i + j], sm.frc[4 * I + i], v);
+            }
+            out[4 + j] = v;
+        }
+    }
+    __syncthreads();
+    T u = T(0);
+    if (tid < n) {
+        const int I = tid >> 2, c = tid & 3;
+        for (int J = 0; J <= I; ++J) u += sm.part[hi_tile(I, J)][c];
+        for (int I2 = I + 1; I2 < NT; ++I2) u += sm.part[hi_tile(I2, I)][4 + c];
+    }
+    hi_cholesky<T>(tl, sm, NT);     // its first barrier also ends the reads of sm.part above
+    // w = L xi
+#pragma unroll
+    for (int s = 0; s < kHIMaxT; ++s) {
+        if (tl.I[s] < 0) continue;
+        const int I = tl.I[s], J = tl.J[s];
+        T* out = sm.part[hi_tile(I, J)];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            T v = T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (J < I || j <= i) v = fma(tl.A[s][4 * i + j], sm.xi[4 * J + j], v);
+            out[i] = v;
+        }
+    }
+    __syncthreads();
+    T nv = T(0);
+    if (tid < n) {
+        const int I = tid >> 2, c = tid & 3;
+        T w = T(0);
+        for (int J = 0; J <= I; ++J) w += sm.part[hi_tile(I, J)][c];
+        const int x = tid % 3, b3 = tid - x;
+        const T r = sm.pos[tid];
+        // kappa . r dt: xx, yy, zz and xz (shear) only
+        T fl = x == 0 ? fma(k.axz, sm.pos[b3 + 2], fma(k.axx, r, r)) : (x == 1 ? fma(k.ayy, r, r) : fma(k.azz, r, r));
+        nv = fma(k.cn, w, fma(k.cd, u, fl));
+    }
+    __syncthreads();
+    if (tid < n) sm.pos[tid] = nv;
+    __syncthreads();
+    if (tid < 32) {
+        T s[3] = {T(0), T(0), T(0)};
+        for (int b = tid; b < N; b += 32)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s[c] += sm.pos[3 * b + c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+        }
+        if (tid == 0)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sm.com[c] = s[c] / (T)N;
+    }
+    __syncthreads();
+    if (tid < n) sm.pos[tid] -= sm.com[tid % 3];
+    __syncthreads();
+    return floored;
+}
+
+// Replicas: one CTA per work item (one replica), the items of this launch in
+// p.items. Spawn from the window-start snapshot, S steps, one force sample per
+// spring at the window end into the replica's partial row (its group).
+template <typename T, bool FAST>
+__global__ void __launch_bounds__(kHIThreads)
+hi_replica_kernel(const StepParams p)
+{
+    extern __shared__ __align__(16) unsigned char hi_smem_raw[];
+    HIShared<T>& sm = *reinterpret_cast<HIShared<T>*>(hi_smem_raw);
+    if ((int)blockIdx.x >= p.n_items) return;
+    const ItemDev it = p.items[blockIdx.x];
+    const ChainDev ch = p.chains[it.chain];
+    const int N = ch.N, nb = N - 1, NT = (3 * N + 3) / 4;
+    const bool harmonic = ch.spring == BD_SPRING_HARMONIC;
+    const bool lj = ch.lj_u > 0.0;
+    const int kglob = it.rep_begin + 1;
+    const uint32_t key = (p.flags & BD_FLAG_IDENTICAL_NOISE) ? 0u : (uint32_t)kglob;
+    StepConst<T, FAST> k;
+    k.load(ch, p);
+    for (int e = threadIdx.x; e < 4 * kHINT; e += blockDim.x) {
+        sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
+    }
+    __syncthreads();
+    HITiles<T> tl;
+    hi_tiles_init(tl, NT);
+    T* state = reinterpret_cast<T*>(p.state) + (ch.state_off + (int64_t)kglob * nb) * 3;
+    const T* snap = reinterpret_cast<const T*>(p.snap);
+    hi_load_bonds(sm, state, N);
+    int floored = 0;
+    int s_in = (int)(p.t0 % p.S);
+    int64_t w = p.t0 / p.S;
+    const int64_t t_end = p.t0 + p.n_steps;
+#pragma unroll 1
+    for (int64_t t = p.t0; t < t_end; ++t) {
+        if (s_in == 0) hi_load_bonds(sm, snap + ((w % p.win_ring) * p.M + ch.spr_off) * 3, N);
+        floored += hi_step<T, FAST>(sm, tl, ch, k, p, N, NT, key, (uint32_t)it.chain, (uint32_t)t,
+                                    harmonic, lj);
+        if (++s_in == p.S) {
+            s_in = 0;
+            const int i = threadIdx.x;
+            if (i < nb) {
+                const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
+                const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];
+                const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
+                const T f = harmonic ? harmonic_tension<T>(qx, qy, qz, k.H, (T)ch.r0)
+                                     : spring_tension<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin);
+                p.part_hist[(w % p.win_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb + i] = (double)f;
+            }
+            ++w;
+        }
+    }
+    hi_store_bonds(sm, state, N);
+    if (floored) atomicAdd(p.overext + it.chain, (unsigned long long)floored);
+}
+
+// Parents: one CTA per chain (p.parent_warps[blockIdx.x].first indexes
+// p.parent_items). Window-start snapshots, then per step the update and the
+// instantaneous force of every spring: TSF sums and the ISF criteria.
+template <typename T, bool FAST>
+__global__ void __launch_bounds__(kHIThreads)
+hi_parent_kernel(const StepParams p)
+{
+    extern __shared__ __align__(16) unsigned char hi_smem_raw[];
+    HIShared<T>& sm = *reinterpret_cast<HIShared<T>*>(hi_smem_raw);
+    if ((int)blockIdx.x >= p.n_parent_warps) return;
+    const int c = p.parent_items[p.parent_warps[blockIdx.x].first];
+    const ChainDev ch = p.chains[c];
+    const int N = ch.N, nb = N - 1, NT = (3 * N + 3) / 4;
+    const bool harmonic = ch.spring == BD_SPRING_HARMONIC;
+    const bool lj = ch.lj_u > 0.0;
+    StepConst<T, FAST> k;
+    k.load(ch, p);
+    for (int e = threadIdx.x; e < 4 * kHINT; e += blockDim.x) {
+        sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
+    }
+    __syncthreads();
+    HITiles<T> tl;
+    hi_tiles_init(tl, NT);
+    T* state = reinterpret_cast<T*>(p.state) + ch.state_off * 3;
+    T* snap = reinterpret_cast<T*>(p.snap);
+    hi_load_bonds(sm, state, N);
+    const int64_t M = p.M;
+    const int i = threadIdx.x;                 // this thread's spring
+    const bool mine = i < nb;
+    const int64_t m = ch.spr_off + i;
+    const bool isf_thr = (p.thr_mask & BD_CRIT_ISF) != 0;
+    const bool isf_bell = (p.bell_mask & BD_CRIT_ISF) != 0;
+    const T fc = (T)ch.f_c;
+    const double k0dt = ch.k0 * p.dt, dxs = ch.dx;
+    T tsf = mine ? (T)p.tsf_acc[m] : T(0);
+    double haz = 0.0, rem = mine ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0;
+    bool thr_done = !mine || p.first_thr[CRIT_Q_ISF * M + m] >= 0;
+    bool bell_done = !mine || p.first_bell[CRIT_Q_ISF * M + m] >= 0;
+    int floored = 0;
+    int s_in = (int)(p.t0 % p.S);
+    int64_t w = p.t0 / p.S;
+    const int64_t t_end = p.t0 + p.n_steps;
+#pragma unroll 1
+    for (int64_t t = p.t0; t < t_end; ++t) {
+        if (s_in == 0) {  // the conformation the replicas of window w start from
+            T* row = snap + ((w % p.win_ring) * M + ch.spr_off) * 3;
+            hi_store_bonds(sm, row, N);
+            // continue from it as the replicas do, so that replicas drawing
+            // the parent's noise repeat the parent exactly
+            hi_load_bonds(sm, row, N);
+        }
+        floored += hi_step<T, FAST>(sm, tl, ch, k, p, N, NT, 0u, (uint32_t)c, (uint32_t)t, harmonic, lj);
+        if (mine) {
+            const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
+            const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];
+            const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
+            const T f = harmonic ? harmonic_tension<T>(qx, qy, qz, k.H, (T)ch.r0)
+                                 : spring_tension<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin);
+            tsf += f;
+            if (isf_thr && !thr_done && f >= fc) {
+                thr_done = true;
+                p.first_thr[CRIT_Q_ISF * M + m] = t + 1;
+            }
+            if (isf_bell) {
+                haz = fma(k0dt, exp(dxs * (double)f), haz);
+                if (!bell_done && haz >= rem) {
+                    bell_done = true;
+                    p.first_bell[CRIT_Q_ISF * M + m] = t + 1;
+                }
+            }
+        }
+        if (++s_in == p.S) {
+            s_in = 0;
+            if (mine) {
+                p.tsf_hist[w * M + m] = (double)tsf / (double)p.S;
+                tsf = T(0);
+                if (isf_bell) {
+                    const double lam = p.lam[CRIT_Q_ISF * M + m] + haz;
+                    p.lam[CRIT_Q_ISF * M + m] = lam;
+                    haz = 0.0;
+                    rem = p.exp1[CRIT_Q_ISF * M + m] - lam;
+                }
+            }
+            ++w;
+        }
+    }
+    __syncthreads();
+    hi_store_bonds(sm, state, N);
+    if (mine) {
+        p.tsf_acc[m] = (double)tsf;
+        if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += haz;
+    }
+    if (floored) atomicAdd(p.overext + c, (unsigned long long)floored);
+}
+
+}  // namespace bdra

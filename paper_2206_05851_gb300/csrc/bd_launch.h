@@ -24,11 +24,31 @@ static const int kVariantsF64[] = {2, 4, 7, 10, 13, 16,
 static const int kNumVariantsF64 = 10;
 
 // Variant codes are below kVariantCodes (cost tables are indexed by code).
-constexpr int kVariantCodes = kLJBase + 32;
+// kHIBase (hydrodynamic interaction, one CTA per replica) is not a tile
+// variant: the planner gives it to every chain with an RPY radius.
+constexpr int kVariantCodes = kHIBase + 1;
 
-inline bool variant_lj(int v) { return v >= kLJBase; }
+inline bool variant_hi(int v) { return v == kHIBase; }
+inline bool variant_lj(int v) { return v >= kLJBase && v < kHIBase; }
 inline bool variant_paired(int v) { return v >= kPairBase && v < kLJBase; }
-inline int variant_tile(int v) { return v >= kLJBase ? v - kLJBase : v >= kPairBase ? v - kPairBase : v; }
+inline int variant_tile(int v)
+{
+    return v >= kHIBase ? 0 : v >= kLJBase ? v - kLJBase : v >= kPairBase ? v - kPairBase : v;
+}
+
+// Hydrodynamic interaction (bd_hi.cuh; bd_hi_f32.cu, bd_hi_f64.cu): kernels,
+// their CTA size and bead limit, the dynamic shared memory of a CTA, and the
+// one-time attribute set-up that allows it.
+constexpr int kHIThreadsHost = 256;
+constexpr int kHIMaxBeadsHost = 64;
+const void* hi_replica_func_f32();
+const void* hi_replica_func_f64();
+const void* hi_parent_func_f32();
+const void* hi_parent_func_f64();
+size_t hi_smem_f32();
+size_t hi_smem_f64();
+cudaError_t hi_prepare_f32();
+cudaError_t hi_prepare_f64();
 
 // Parent kernels per tile; lj: the collapsed-chain step.
 const void* parent_func_f32(int L, bool lj);

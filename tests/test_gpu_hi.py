@@ -1,0 +1,152 @@
+"""GPU parity for chains with hydrodynamic interaction (Eqs. 1-3): the
+Rotne-Prager-Yamakawa diffusion tensor, its Cholesky factor for the
+correlated noise and the mobility-weighted drift, one CTA per slot, against
+the FP64 oracle on the same seeded inputs and Philox draws.
+
+- Positions of parents and replicas, RSF and TSF profiles within 1e-10
+  (FP64) / 1e-4 (FP32) relative; FP64 first-event steps equal.
+- The paper's collapsed chain (N = 50, harmonic springs, Lennard-Jones, bead
+  radius a = 1) in shear, smaller collapsed chains, FENE and Hookean chains
+  with a bead radius in their own length unit, the two-bead chain, the
+  largest chain (N = 64, tensor of 192 rows: 48 tile rows, five tiles on some
+  threads), and free-draining chains in the same batch.
+- Identical noise: every replica equals its parent (same kernel, same
+  arithmetic).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2206_05851_gb300 import bdra
+from paper_2206_05851_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {bdra.BD_PREC_FP64: 1e-10, bdra.BD_PREC_FP32: 1e-4}
+PRECS = [bdra.BD_PREC_FP64, bdra.BD_PREC_FP32]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2206_05851_gb300 import build as B
+    B.build()
+    torch.cuda.init()
+
+
+def _collapsed(N, R, flow=I.FLOW_SHEAR, rate=7.5, hi=1.0):
+    return I.Chain(n_beads=N, n_replicas=R, spring=I.SPRING_HARMONIC, flow=flow, rate=rate,
+                   H=400.0, r0=2.0, lj_u=1.0, lj_sigma=2.0, f_c=30.0, k0=50.0, dx=0.1, hi_a=hi)
+
+
+def _collapsed_set():
+    return [_collapsed(50, 3), _collapsed(12, 4, I.FLOW_NONE, 0.0), _collapsed(3, 2, I.FLOW_UNIAXIAL, 2.0),
+            _collapsed(12, 3, hi=0.0)]                       # free draining in the same batch
+
+
+def _fene_set():
+    return [I.Chain(n_beads=20, n_replicas=3, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL, b=50.0,
+                    rate=0.5, f_c=5.0, k0=1e-2, dx=0.2, hi_a=0.5),
+            I.Chain(n_beads=64, n_replicas=2, spring=I.SPRING_FENE, flow=I.FLOW_SHEAR, b=100.0,
+                    rate=0.2, f_c=6.0, k0=1e-2, dx=0.2, hi_a=0.4),
+            I.Chain(n_beads=2, n_replicas=2, spring=I.SPRING_HOOKE, flow=I.FLOW_PLANAR, rate=0.3,
+                    f_c=2.0, k0=1e-2, dx=0.5, hi_a=0.3),
+            I.Chain(n_beads=20, n_replicas=4, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL, b=50.0,
+                    rate=0.5, f_c=5.0, k0=1e-2, dx=0.2)]
+
+
+SETS = {"collapsed": (_collapsed_set, 4e-5, 50, [20, 130, 150]),
+        "fene": (_fene_set, 1e-3, 50, [20, 130, 150])}
+
+
+def _gpu(chains, dt, S, steps, pos0, prec, seed=9, flags=0, thr=7, bell=7):
+    import torch
+    total = sum(steps)
+    ctx = bdra.Context(chains, dt, S, seed, pos0, precision=prec, max_windows=total // S + 1,
+                       thr_mask=thr, bell_mask=bell, flags=flags,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    for n in steps:
+        ctx.step(n)
+    nw = total // S
+    out = dict(pos=ctx.positions(False), allpos=ctx.positions(True),
+               rsf=np.array([ctx.replica_average(w) for w in range(nw)]).reshape(nw, ctx.M),
+               tsf=np.array([ctx.time_average(w) for w in range(nw)]).reshape(nw, ctx.M))
+    out["haz"], out["first_thr"], out["first_bell"] = ctx.kinetics()
+    out["info"] = ctx.info()
+    ctx.close()
+    return out
+
+
+def _split(allpos, chains):
+    par, rep, o = [], [], 0
+    for c in chains:
+        blk = allpos[o:o + (c.n_replicas + 1) * c.n_beads].reshape(c.n_replicas + 1, c.n_beads, 3)
+        par.append(blk[0])
+        rep.append(blk[1:].reshape(-1, 3))
+        o += (c.n_replicas + 1) * c.n_beads
+    return np.concatenate(par), np.concatenate(rep)
+
+
+def _rel(got, want, sizes):
+    worst, o = 0.0, 0
+    for n in sizes:
+        g, w = got[o:o + n], want[o:o + n]
+        worst = max(worst, float(np.abs(g - w).max() / max(np.abs(w).max(), 1e-300)))
+        o += n
+    return worst
+
+
+@pytest.fixture(scope="module", params=sorted(SETS))
+def case(request):
+    make, dt, S, steps = SETS[request.param]
+    chains = make()
+    pos0 = I.initial_positions(I.custom(chains, dt, S, sum(steps)), seed=29)
+    r = O.run(chains, dt, S, sum(steps), 9, pos0, thr_mask=7, bell_mask=7, n_threads=8)
+    return request.param, chains, dt, S, steps, pos0, r
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_hi_chains_match_oracle(case, prec):
+    name, chains, dt, S, steps, pos0, r = case
+    g = _gpu(chains, dt, S, steps, pos0, prec)
+    tol = TOL[prec]
+    nb = [c.n_beads for c in chains]
+    assert np.isfinite(g["allpos"]).all()
+    assert _rel(g["pos"], O.com_frame(r["pos"], nb), nb) <= tol
+    par, rep = _split(g["allpos"], chains)
+    np.testing.assert_array_equal(par, g["pos"])
+    sizes = [c.n_beads for c in chains for _ in range(c.n_replicas)]
+    assert _rel(rep, O.com_frame(r["rep"], sizes), sizes) <= tol
+    for key in ("rsf", "tsf"):
+        err = np.abs(g[key] - r[key]).max() / np.abs(r[key]).max()
+        assert err <= tol, f"{name}: {key} rel err {err:.3e}"
+    if prec == bdra.BD_PREC_FP64:
+        np.testing.assert_array_equal(g["first_thr"], r["first_thr"])
+        np.testing.assert_array_equal(g["first_bell"], r["first_bell"])
+        np.testing.assert_allclose(g["haz"], r["lam"], rtol=1e-9, atol=1e-300)
+        assert g["info"].overextensions == int(r["overext"].sum())
+
+
+def test_hi_moves_differently_from_free_draining():
+    # the same chain and noise with and without the interaction part
+    ch = _collapsed(12, 2)
+    fd = _collapsed(12, 2, hi=0.0)
+    pos0 = I.initial_positions(I.custom([ch], 4e-5, 50, 200), seed=3)
+    a = _gpu([ch], 4e-5, 50, [200], pos0, bdra.BD_PREC_FP64, thr=0, bell=0)["pos"]
+    b = _gpu([fd], 4e-5, 50, [200], pos0, bdra.BD_PREC_FP64, thr=0, bell=0)["pos"]
+    assert np.abs(a - b).max() > 1e-3
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_identical_noise_replicas_equal_parent(prec):
+    chains = _collapsed_set()[:3]
+    pos0 = I.initial_positions(I.custom(chains, 4e-5, 50, 120), seed=4)
+    g = _gpu(chains, 4e-5, 50, [120], pos0, prec, flags=bdra.BD_FLAG_IDENTICAL_NOISE, thr=0, bell=0)
+    par, rep = _split(g["allpos"], chains)
+    o = po = 0
+    for ch in chains:
+        p = par[po:po + ch.n_beads]
+        for k in range(ch.n_replicas):
+            np.testing.assert_array_equal(rep[o + k * ch.n_beads:o + (k + 1) * ch.n_beads], p)
+        o += ch.n_replicas * ch.n_beads
+        po += ch.n_beads
