@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-conformation", action="store_true")
     ap.add_argument("--no-collapsed", action="store_true")
+    ap.add_argument("--no-hi", action="store_true")
+    ap.add_argument("--only-hi", action="store_true",
+                    help="only the hydrodynamic-interaction line (Eqs. 1-3)")
     ap.add_argument("--only-collapsed", action="store_true",
                     help="only the collapsed-chain line (Sec. II model)")
     ap.add_argument("--only-adjoint", action="store_true",
@@ -353,6 +356,95 @@ def collapsed_line(sptr, n_chains=0, n_steps=3000, fp64_chains=64):
     return out
 
 
+def hi_flops_per_slot_step(n_beads):
+    """Floating-point operations of one hydrodynamic-interaction step of one
+    slot, counting an FMA as two: Cholesky of the 3N x 3N tensor (n^3/3), the
+    drift W F with the full symmetric tensor (2 n^2) and the noise L xi (n^2);
+    the tensor's assembly, forces and update are O(n^2) or less and not
+    counted."""
+    n = 3 * n_beads
+    return n ** 3 / 3.0 + 2.0 * n * n + n * n
+
+
+def hi_line(sptr, n_chains=0, n_steps=1500, fp64_chains=8, fp64_steps=100):
+    """The paper's full model with RPY hydrodynamic interaction: float32
+    throughput of one evolution window, the replica kernel against the float32
+    FMA peak, the FP64 path and the FP32 RSF error against it on a few chains,
+    and the CPU oracle on a bounded sample."""
+    import numpy as np
+    import torch
+    from paper_2206_05851_gb300 import bdra
+    from paper_2206_05851_gb300 import inputs as I
+
+    wl = I.collapsed_hi_128(**({"n_chains": n_chains} if n_chains else {}))
+    pos0 = I.initial_positions(wl)
+    S = wl.window_steps
+    stream = torch.cuda.current_stream()
+    out = {"workload": wl.name, "steps": n_steps, "window_steps": S, "dt": wl.dt}
+
+    def run(chains, p0, prec, steps, timed, window):
+        c = bdra.Context(chains, wl.dt, window, wl.seed, torch.from_numpy(p0).cuda(), precision=prec,
+                         max_windows=2 * steps // window + 2, thr_mask=0, bell_mask=0, stream=sptr)
+        c.step(min(window, 10))                          # warm-up
+        c.set_positions(torch.from_numpy(p0).cuda(), 0)
+        if timed:
+            bdra.bd_enable_timing(c.ptr, True)
+            bdra.bd_kernel_times(c.ptr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        times = bdra.bd_kernel_times(c.ptr) if timed else None
+        rsf = [c.replica_average(w) for w in range(steps // window)]
+        c.close()
+        return t, times, rsf
+
+    t, ((par_ms, rep_ms), (_, rep_n)), _ = run(wl.chains, pos0, bdra.BD_PREC_FP32, n_steps, True, S)
+    units = wl.bead_steps(n_steps)
+    out["value"] = units / t
+    out["unit"] = "bead-steps/s"
+    N = wl.chains[0].n_beads
+    slot_steps = sum(c.n_replicas for c in wl.chains) * n_steps
+    achieved = hi_flops_per_slot_step(N) * slot_steps / (rep_ms / 1e3) / 1e12
+    peak = 2.0 * SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    out["roofline"] = {"bound": "alu (float32 FMA)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": "hydrodynamic-interaction replica kernel (float32, one CTA per replica)",
+                       "avg_launch_ms": rep_ms / max(rep_n, 1), "launches": rep_n,
+                       "share_of_step": rep_ms / (t * 1e3), "flops_per_slot_step": hi_flops_per_slot_step(N),
+                       "peak_basis": f"{SMS} SMs x {LANES_PER_CLK_PER_SM} FMA/clk x 2 x {SM_MAX_MHZ:.0f} MHz "
+                                     "(derived, not measured)"}
+    out["parent_kernel_share"] = par_ms / (t * 1e3)
+    # FP64 and the FP32 force error on a few chains (a short window so that
+    # RSF samples exist)
+    sub = wl.chains[:fp64_chains]
+    psub = pos0[:sum(c.n_beads for c in sub)]
+    w_short = fp64_steps // 2
+    t64, _, r64 = run(sub, psub, bdra.BD_PREC_FP64, fp64_steps, False, w_short)
+    _, _, r32 = run(sub, psub, bdra.BD_PREC_FP32, fp64_steps, False, w_short)
+    out["fp64_plain"] = {"value": sum(c.n_replicas * c.n_beads for c in sub) * fp64_steps / t64,
+                         "unit": "bead-steps/s",
+                         "sample": f"first {len(sub)} chains, {fp64_steps} steps, window {w_short}",
+                         "rsf_max_rel_err_fp32_vs_fp64":
+                             float(max(np.abs(a - b).max() / np.abs(b).max() for a, b in zip(r32, r64)))}
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    sub = wl.chains[:cores]
+    psub = pos0[:sum(c.n_beads for c in sub)]
+    n_cpu = 200          # about 10 s of oracle work on 16 cores
+    tc = time.perf_counter()
+    O.run(sub, wl.dt, S, n_cpu, wl.seed, psub, thr_mask=0, bell_mask=0, n_threads=cores,
+          want_replicas=False, chain_ids=list(range(len(sub))))
+    tc = time.perf_counter() - tc
+    bs = sum(c.n_replicas * c.n_beads for c in sub) * n_cpu
+    out["cpu_baseline"] = {"value": bs / tc, "unit": "bead-steps/s", "cores": cores, "kind": "oracle",
+                           "sample": f"first {len(sub)} chains, {n_cpu} steps ({tc:.1f} s wall, FP64)"}
+    return out
+
+
 def adjoint_line(sptr, n_chains=0, n_steps=0):
     """Forward run plus reverse-mode adjoint of the differentiation workload
     (256 FENE chains, N=200, 32 replicas, 2e4 steps, parent checkpoints every
@@ -411,6 +503,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only_hi:
+        import torch
+        from paper_2206_05851_gb300 import bdra, build as B
+        if not B.up_to_date():
+            B.build()
+        bdra.load()
+        print(json.dumps({"hi": hi_line(torch.cuda.current_stream().cuda_stream, args.chains)}),
+              flush=True)
         return
     if args.only_collapsed:
         import torch
@@ -616,6 +717,8 @@ def main():
             out["conformation"] = conformation_line(wl, pos0, sptr)
         if not args.no_collapsed:
             out["collapsed"] = collapsed_line(sptr)
+        if not args.no_hi:
+            out["hi"] = hi_line(sptr)
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(wl, pos0)
     if rank == 0:

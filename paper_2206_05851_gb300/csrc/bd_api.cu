@@ -249,7 +249,7 @@ double default_variant_cost(int v)
 VariantChoice choose_variant(const bd_ctx* ctx, int N, int R, bool collapsed, bool hi)
 {
     const bd_config& cfg = ctx->cfg;
-    if (hi) return {kHIBase, 1, R, 0.0};      // one CTA per replica
+    if (hi) return {kHIBase + (N > kHISmallBeadsHost ? 1 : 0), 1, R, 0.0};   // one CTA per replica
     const int* vars = ctx->f64 ? kVariantsF64 : kVariantsF32;
     const int nv = ctx->f64 ? kNumVariantsF64 : kNumVariantsF32;
     VariantChoice best{0, 0, 0, 1e300};
@@ -418,7 +418,7 @@ bd_status plan(bd_ctx* ctx)
             begin += cnt;
         }
         if (hi) {
-            par.push_back({{kParentHIKey, 1}, c});
+            par.push_back({{kParentHIKey + (d.n_beads > kHISmallBeadsHost ? 1 : 0), 1}, c});
         } else {
             const int Lp = choose_parent_tile(d.n_beads);
             par.push_back({{Lp + (collapsed ? kParentLJKey : 0), (d.n_beads + Lp - 1) / Lp}, c});
@@ -478,9 +478,9 @@ bd_status plan(bd_ctx* ctx)
     ctx->par_classes.clear();
     for (size_t k = 0; k < par.size();) {
         const int key = par[k].first.first, G = par[k].first.second;
-        const bool hi = key == kParentHIKey;
+        const bool hi = key >= kParentHIKey;
         const int P = hi ? 1 : 32 / G;           // one CTA per parent with hydrodynamic interaction
-        const int L = hi ? 0 : key % kParentLJKey;
+        const int L = hi ? key - kParentHIKey : key % kParentLJKey;   // hi: 0 small, 1 large chains
         const bool lj = !hi && key >= kParentLJKey;
         if (ctx->par_classes.empty() || ctx->par_classes.back().L != L || ctx->par_classes.back().lj != lj ||
             ctx->par_classes.back().hi != hi)
@@ -574,7 +574,7 @@ cudaKernelNodeParams parent_node(const bd_ctx* ctx, size_t k, StepParams* pk, vo
     args[0] = pk;
     cudaKernelNodeParams kp = {};
     if (pc.hi)
-        kp.func = const_cast<void*>(ctx->f64 ? hi_parent_func_f64() : hi_parent_func_f32());
+        kp.func = const_cast<void*>(ctx->f64 ? hi_parent_func_f64(pc.L == 0) : hi_parent_func_f32(pc.L == 0));
     else
         kp.func = const_cast<void*>(ctx->f64 ? parent_func_f64(pc.L, pc.lj) : parent_func_f32(pc.L, pc.lj));
     kp.gridDim = dim3(pc.grid);
@@ -590,7 +590,8 @@ cudaKernelNodeParams replica_node(const bd_ctx* ctx, size_t k, StepParams* rk, v
     args[0] = rk;
     cudaKernelNodeParams kp = {};
     if (variant_hi(vc.variant))
-        kp.func = const_cast<void*>(ctx->f64 ? hi_replica_func_f64() : hi_replica_func_f32());
+        kp.func = const_cast<void*>(ctx->f64 ? hi_replica_func_f64(vc.variant == kHIBase)
+                                             : hi_replica_func_f32(vc.variant == kHIBase));
     else
         kp.func = const_cast<void*>(ctx->f64 ? persist_func_f64(vc.variant, ctx->conf)
                                              : persist_func_f32(vc.variant, ctx->conf));

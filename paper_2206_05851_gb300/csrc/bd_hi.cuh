@@ -34,13 +34,19 @@ constexpr int kHIThreads = 256;
 constexpr int kHIMaxBeads = 64;
 constexpr int kHINT = (3 * kHIMaxBeads + 3) / 4;                  // tile rows of the largest tensor
 constexpr int kHITiles = kHINT * (kHINT + 1) / 2;                 // its lower tiles
-constexpr int kHIMaxT = (kHITiles + kHIThreads - 1) / kHIThreads; // tiles per thread
+// Tiles per thread: kHIMaxT for chains of up to kHIMaxBeads beads, kHISmallT
+// (fewer registers, two CTAs per SM) for up to kHISmallBeads beads.
+constexpr int kHIMaxT = (kHITiles + kHIThreads - 1) / kHIThreads;
+constexpr int kHISmallBeads = 50;
+constexpr int kHISmallT = ((3 * kHISmallBeads + 3) / 4 * ((3 * kHISmallBeads + 3) / 4 + 1) / 2 +
+                           kHIThreads - 1) / kHIThreads;
 
 template <typename T> struct HIShared {
     alignas(16) T pos[4 * kHINT];      // bead positions [3N] (COM frame); padding 0
     alignas(16) T frc[4 * kHINT];      // bead forces [3N]; padding 0
     alignas(16) T xi[4 * kHINT];       // bead normals [3N]; padding 0
     alignas(16) T diag[16];            // factor of the current diagonal tile
+    alignas(16) T dinv[4];             // reciprocals of its diagonal
     alignas(16) T panel[kHINT][16];    // factor tiles of the current tile column, by tile row
     alignas(16) T part[kHITiles][8];   // per-tile partial products
     T com[3];
@@ -67,17 +73,17 @@ __device__ __forceinline__ void rpy_coef(T dx, T dy, T dz, T a, T& ci, T& cd)
 }
 
 // Per-thread state of the tensor tiles.
-template <typename T> struct HITiles {
-    T A[kHIMaxT][16];    // row-major 4 x 4
-    int I[kHIMaxT], J[kHIMaxT];   // -1: no tile
+template <typename T, int MAXT> struct HITiles {
+    T A[MAXT][16];       // row-major 4 x 4
+    int I[MAXT], J[MAXT];   // -1: no tile
 };
 
-template <typename T>
-__device__ __forceinline__ void hi_tiles_init(HITiles<T>& tl, int NT)
+template <typename T, int MAXT>
+__device__ __forceinline__ void hi_tiles_init(HITiles<T, MAXT>& tl, int NT)
 {
     const int total = NT * (NT + 1) / 2;
 #pragma unroll
-    for (int s = 0; s < kHIMaxT; ++s) {
+    for (int s = 0; s < MAXT; ++s) {
         const int t = threadIdx.x + s * kHIThreads;
         int I = -1, J = -1;
         if (t < total) {
@@ -119,11 +125,11 @@ __device__ __forceinline__ void hi_fill(T (&A)[16], const T (&ci)[2][2], const T
 
 // W's tiles from the positions (n = 3N rows; rows and columns >= n are the
 // identity's).
-template <typename T, bool FAST>
-__device__ __forceinline__ void hi_assemble(HITiles<T>& tl, const T* pos, int n, T a)
+template <typename T, bool FAST, int MAXT>
+__device__ __forceinline__ void hi_assemble(HITiles<T, MAXT>& tl, const T* pos, int n, T a)
 {
 #pragma unroll
-    for (int s = 0; s < kHIMaxT; ++s) {
+    for (int s = 0; s < MAXT; ++s) {
         if (tl.I[s] < 0) continue;
         const int r0 = 4 * tl.I[s], c0 = 4 * tl.J[s];
         const int br = r0 / 3, bc = c0 / 3;
@@ -156,18 +162,27 @@ __device__ __forceinline__ void hi_assemble(HITiles<T>& tl, const T* pos, int n,
     }
 }
 
-// Factor of a diagonal tile (lower part; the upper part is left as is).
-template <typename T>
-__device__ __forceinline__ void hi_chol4(T (&A)[16])
+// Factor of a diagonal tile (lower part; the upper part is left as is) and
+// the reciprocals of its diagonal. The fast float form takes both from one
+// approximate reciprocal square root.
+template <typename T, bool FAST>
+__device__ __forceinline__ void hi_chol4(T (&A)[16], T (&inv)[4])
 {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         T s = A[5 * j];
 #pragma unroll
         for (int k = 0; k < j; ++k) s = fma(-A[4 * j + k], A[4 * j + k], s);
-        const T l = sqrt(s);
+        T l, il;
+        if (FAST) {
+            il = Rsqrt<T, FAST>::rsqrt(s);
+            l = s * il;
+        } else {
+            l = sqrt(s);
+            il = T(1) / l;
+        }
         A[5 * j] = l;
-        const T il = T(1) / l;
+        inv[j] = il;
 #pragma unroll
         for (int i = j + 1; i < 4; ++i) {
             T v = A[4 * i + j];
@@ -178,63 +193,72 @@ __device__ __forceinline__ void hi_chol4(T (&A)[16])
     }
 }
 
-// X L^T = A for a tile below the diagonal tile L (lower).
+// X L^T = A for a tile below the diagonal tile L (lower; inv: 1 / its diagonal).
 template <typename T>
-__device__ __forceinline__ void hi_trsm4(T (&A)[16], const T* L)
+__device__ __forceinline__ void hi_trsm4(T (&A)[16], const T* L, const T* inv)
 {
-    T inv[4];
+    T Lr[16], iv[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) inv[c] = T(1) / L[5 * c];
+    for (int e = 0; e < 16; ++e) Lr[e] = L[e];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) iv[c] = inv[c];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             T v = A[4 * r + c];
 #pragma unroll
-            for (int k = 0; k < c; ++k) v = fma(-A[4 * r + k], L[4 * c + k], v);
-            A[4 * r + c] = v * inv[c];
+            for (int k = 0; k < c; ++k) v = fma(-A[4 * r + k], Lr[4 * c + k], v);
+            A[4 * r + c] = v * iv[c];
         }
 }
 
 // In-place lower Cholesky factor of the CTA's tiles (every thread calls it).
-template <typename T>
-__device__ __forceinline__ void hi_cholesky(HITiles<T>& tl, HIShared<T>& sm, int NT)
+template <typename T, bool FAST, int MAXT>
+__device__ __forceinline__ void hi_cholesky(HITiles<T, MAXT>& tl, HIShared<T>& sm, int NT)
 {
 #pragma unroll 1
     for (int K = 0; K < NT; ++K) {
 #pragma unroll
-        for (int s = 0; s < kHIMaxT; ++s)
+        for (int s = 0; s < MAXT; ++s)
             if (tl.I[s] == K && tl.J[s] == K) {
-                hi_chol4(tl.A[s]);
+                T inv[4];
+                hi_chol4<T, FAST>(tl.A[s], inv);
 #pragma unroll
                 for (int e = 0; e < 16; ++e) sm.diag[e] = tl.A[s][e];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) sm.dinv[e] = inv[e];
             }
         __syncthreads();
 #pragma unroll
-        for (int s = 0; s < kHIMaxT; ++s)
+        for (int s = 0; s < MAXT; ++s)
             if (tl.J[s] == K && tl.I[s] > K) {
-                hi_trsm4(tl.A[s], sm.diag);
+                hi_trsm4(tl.A[s], sm.diag, sm.dinv);
 #pragma unroll
                 for (int e = 0; e < 16; ++e) sm.panel[tl.I[s]][e] = tl.A[s][e];
             }
         __syncthreads();
 #pragma unroll
-        for (int s = 0; s < kHIMaxT; ++s)
+        for (int s = 0; s < MAXT; ++s)
             if (tl.J[s] > K) {
                 const T* Pi = sm.panel[tl.I[s]];
                 const T* Pj = sm.panel[tl.J[s]];
-                T li[16], lj[16];
+                T lj[16];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) { li[e] = Pi[e]; lj[e] = Pj[e]; }
+                for (int e = 0; e < 16; ++e) lj[e] = Pj[e];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i) {
+                    T li[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) li[k] = Pi[4 * i + k];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         T v = tl.A[s][4 * i + j];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) v = fma(-li[4 * i + k], lj[4 * j + k], v);
+                        for (int k = 0; k < 4; ++k) v = fma(-li[k], lj[4 * j + k], v);
                         tl.A[s][4 * i + j] = v;
                     }
+                }
             }
     }
 }
@@ -317,8 +341,8 @@ __device__ __forceinline__ void hi_store_bonds(const HIShared<T>& sm, T* bonds, 
 }
 
 // One step t -> t + 1 of the CTA's slot. Returns the thread's floor count.
-template <typename T, bool FAST>
-__device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T>& tl, const ChainDev& ch,
+template <typename T, bool FAST, int MAXT>
+__device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T, MAXT>& tl, const ChainDev& ch,
                                        const StepConst<T, FAST>& k, const StepParams& p, int N, int NT,
                                        uint32_t slot_key, uint32_t chain, uint32_t step, bool harmonic,
                                        bool lj)
@@ -333,11 +357,11 @@ __device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T>& tl, const Ch
         sm.xi[3 * tid + 1] = z1;
         sm.xi[3 * tid + 2] = z2;
     }
-    hi_assemble<T, FAST>(tl, sm.pos, n, (T)ch.hi_a);
+    hi_assemble<T, FAST, MAXT>(tl, sm.pos, n, (T)ch.hi_a);
     __syncthreads();
     // u = W F: per tile W_IJ F_J (rows I) and, below the diagonal, W_IJ^T F_I (rows J)
 #pragma unroll
-    for (int s = 0; s < kHIMaxT; ++s) {
+    for (int s = 0; s < MAXT; ++s) {
         if (tl.I[s] < 0) continue;
         const int I = tl.I[s], J = tl.J[s];
         T* out = sm.part[hi_tile(I, J)];
@@ -365,10 +389,10 @@ __device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T>& tl, const Ch
         for (int J = 0; J <= I; ++J) u += sm.part[hi_tile(I, J)][c];
         for (int I2 = I + 1; I2 < NT; ++I2) u += sm.part[hi_tile(I2, I)][4 + c];
     }
-    hi_cholesky<T>(tl, sm, NT);     // its first barrier also ends the reads of sm.part above
+    hi_cholesky<T, FAST, MAXT>(tl, sm, NT);     // its first barrier also ends the reads of sm.part above
     // w = L xi
 #pragma unroll
-    for (int s = 0; s < kHIMaxT; ++s) {
+    for (int s = 0; s < MAXT; ++s) {
         if (tl.I[s] < 0) continue;
         const int I = tl.I[s], J = tl.J[s];
         T* out = sm.part[hi_tile(I, J)];
@@ -419,8 +443,8 @@ __device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T>& tl, const Ch
 // Replicas: one CTA per work item (one replica), the items of this launch in
 // p.items. Spawn from the window-start snapshot, S steps, one force sample per
 // spring at the window end into the replica's partial row (its group).
-template <typename T, bool FAST>
-__global__ void __launch_bounds__(kHIThreads)
+template <typename T, bool FAST, int MAXT>
+__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && MAXT <= kHISmallT) ? 2 : 1)
 hi_replica_kernel(const StepParams p)
 {
     extern __shared__ __align__(16) unsigned char hi_smem_raw[];
@@ -439,7 +463,7 @@ hi_replica_kernel(const StepParams p)
         sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
     }
     __syncthreads();
-    HITiles<T> tl;
+    HITiles<T, MAXT> tl;
     hi_tiles_init(tl, NT);
     T* state = reinterpret_cast<T*>(p.state) + (ch.state_off + (int64_t)kglob * nb) * 3;
     const T* snap = reinterpret_cast<const T*>(p.snap);
@@ -451,8 +475,8 @@ hi_replica_kernel(const StepParams p)
 #pragma unroll 1
     for (int64_t t = p.t0; t < t_end; ++t) {
         if (s_in == 0) hi_load_bonds(sm, snap + ((w % p.win_ring) * p.M + ch.spr_off) * 3, N);
-        floored += hi_step<T, FAST>(sm, tl, ch, k, p, N, NT, key, (uint32_t)it.chain, (uint32_t)t,
-                                    harmonic, lj);
+        floored += hi_step<T, FAST, MAXT>(sm, tl, ch, k, p, N, NT, key, (uint32_t)it.chain, (uint32_t)t,
+                                          harmonic, lj);
         if (++s_in == p.S) {
             s_in = 0;
             const int i = threadIdx.x;
@@ -474,8 +498,8 @@ hi_replica_kernel(const StepParams p)
 // Parents: one CTA per chain (p.parent_warps[blockIdx.x].first indexes
 // p.parent_items). Window-start snapshots, then per step the update and the
 // instantaneous force of every spring: TSF sums and the ISF criteria.
-template <typename T, bool FAST>
-__global__ void __launch_bounds__(kHIThreads)
+template <typename T, bool FAST, int MAXT>
+__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && MAXT <= kHISmallT) ? 2 : 1)
 hi_parent_kernel(const StepParams p)
 {
     extern __shared__ __align__(16) unsigned char hi_smem_raw[];
@@ -492,7 +516,7 @@ hi_parent_kernel(const StepParams p)
         sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
     }
     __syncthreads();
-    HITiles<T> tl;
+    HITiles<T, MAXT> tl;
     hi_tiles_init(tl, NT);
     T* state = reinterpret_cast<T*>(p.state) + ch.state_off * 3;
     T* snap = reinterpret_cast<T*>(p.snap);
@@ -522,7 +546,7 @@ hi_parent_kernel(const StepParams p)
             // the parent's noise repeat the parent exactly
             hi_load_bonds(sm, row, N);
         }
-        floored += hi_step<T, FAST>(sm, tl, ch, k, p, N, NT, 0u, (uint32_t)c, (uint32_t)t, harmonic, lj);
+        floored += hi_step<T, FAST, MAXT>(sm, tl, ch, k, p, N, NT, 0u, (uint32_t)c, (uint32_t)t, harmonic, lj);
         if (mine) {
             const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
             const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];

@@ -26,9 +26,11 @@ static const int kNumVariantsF64 = 10;
 // Variant codes are below kVariantCodes (cost tables are indexed by code).
 // kHIBase (hydrodynamic interaction, one CTA per replica) is not a tile
 // variant: the planner gives it to every chain with an RPY radius.
-constexpr int kVariantCodes = kHIBase + 1;
+constexpr int kVariantCodes = kHIBase + 2;
 
-inline bool variant_hi(int v) { return v == kHIBase; }
+// kHIBase: chains of up to kHISmallBeadsHost beads (fewer tiles per thread,
+// two CTAs per SM); kHIBase + 1: up to kHIMaxBeadsHost.
+inline bool variant_hi(int v) { return v >= kHIBase; }
 inline bool variant_lj(int v) { return v >= kLJBase && v < kHIBase; }
 inline bool variant_paired(int v) { return v >= kPairBase && v < kLJBase; }
 inline int variant_tile(int v)
@@ -41,10 +43,11 @@ inline int variant_tile(int v)
 // one-time attribute set-up that allows it.
 constexpr int kHIThreadsHost = 256;
 constexpr int kHIMaxBeadsHost = 64;
-const void* hi_replica_func_f32();
-const void* hi_replica_func_f64();
-const void* hi_parent_func_f32();
-const void* hi_parent_func_f64();
+constexpr int kHISmallBeadsHost = 50;
+const void* hi_replica_func_f32(bool small);
+const void* hi_replica_func_f64(bool small);
+const void* hi_parent_func_f32(bool small);
+const void* hi_parent_func_f64(bool small);
 size_t hi_smem_f32();
 size_t hi_smem_f64();
 cudaError_t hi_prepare_f32();

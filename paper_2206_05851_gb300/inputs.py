@@ -282,6 +282,21 @@ def collapsed_1024(n_steps: int = 15_000, n_chains: int = 1024) -> Workload:
                     init_seed=6)
 
 
+def collapsed_hi_128(n_steps: int = 1_500, n_chains: int = 128) -> Workload:
+    """The paper's full model (Eqs. 1-3): 128 collapsed chains (N=50,
+    kappa=400, u=1) with RPY hydrodynamic interaction (bead radius a) in shear
+    at gamma-dot = 30 / tau, 50 replicas each, dt = 1e-5 tau, evolution time
+    S = 0.015 tau (1500 steps); force sampling only."""
+    chains = []
+    for _ in range(n_chains):
+        ch = collapsed_chain(50)
+        ch.hi_a = 1.0
+        chains.append(ch)
+    return Workload("collapsed_hi_128x_n50_r50_shear30", chains, dt=COLLAPSED_DT,
+                    window_steps=1500, n_steps=n_steps, seed=8, thr_mask=0, bell_mask=0,
+                    init_seed=8)
+
+
 def adjoint_256(n_steps: int = 20_000, n_chains: int = 256) -> Workload:
     """256 FENE chains, N=200, b=100, H=1, 32 replicas, uniaxial elongation
     Wi=5, dt=1e-3, window 100, Bell k0=1e-6 and dx F_max = 20 on the
