@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-hi", action="store_true")
     ap.add_argument("--only-hi", action="store_true",
                     help="only the hydrodynamic-interaction line (Eqs. 1-3)")
+    ap.add_argument("--hi-steps", type=int, default=1500,
+                    help="timed steps of the hydrodynamic-interaction line (one window: 1500)")
     ap.add_argument("--only-collapsed", action="store_true",
                     help="only the collapsed-chain line (Sec. II model)")
     ap.add_argument("--only-adjoint", action="store_true",
@@ -510,8 +512,8 @@ def main():
         if not B.up_to_date():
             B.build()
         bdra.load()
-        print(json.dumps({"hi": hi_line(torch.cuda.current_stream().cuda_stream, args.chains)}),
-              flush=True)
+        print(json.dumps({"hi": hi_line(torch.cuda.current_stream().cuda_stream, args.chains,
+                                         args.hi_steps)}), flush=True)
         return
     if args.only_collapsed:
         import torch

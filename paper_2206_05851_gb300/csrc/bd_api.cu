@@ -456,7 +456,7 @@ bd_status plan(bd_ctx* ctx)
             }
             vc.threads = kHIThreadsHost;
             vc.grid = vc.item_count;
-            vc.smem = ctx->f64 ? hi_smem_f64() : hi_smem_f32();
+            vc.smem = ctx->f64 ? hi_smem_f64(vc.variant == kHIBase) : hi_smem_f32(vc.variant == kHIBase);
             continue;
         }
         vc.smem = ctx->f64 ? persist_smem_f64(vc.variant) : persist_smem_f32(vc.variant);
@@ -486,7 +486,7 @@ bd_status plan(bd_ctx* ctx)
             ctx->par_classes.back().hi != hi)
             ctx->par_classes.push_back(ParClass{L, hi ? kHIThreadsHost : kParentThreads, 0,
                                                 (int)ctx->h_parent_warps.size(), 0, lj, hi,
-                                                hi ? (ctx->f64 ? hi_smem_f64() : hi_smem_f32()) : 0});
+                                                hi ? (ctx->f64 ? hi_smem_f64(L == 0) : hi_smem_f32(L == 0)) : 0});
         size_t e = k;
         while (e < par.size() && par[e].first == par[k].first) ++e;
         for (size_t j = k; j < e; j += P) {

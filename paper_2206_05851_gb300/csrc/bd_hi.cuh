@@ -15,8 +15,11 @@
 // tensor is held as 4 x 4 tiles of its lower triangle in the registers of
 // the CTA's threads (tile t of the row-major lower order belongs to thread
 // t mod kHIThreads). Per step:
-//   - bead forces (springs, Lennard-Jones) and bead normals, one thread per bead;
-//   - the tensor's tiles, each by its owner, from the positions;
+//   - bead forces (springs; Lennard-Jones split over four threads a bead) and
+//     bead normals;
+//   - the tensor, one 3 x 3 bead block per thread at a time, into a
+//     shared-memory copy of the lower tiles, from which each thread loads its
+//     own tiles;
 //   - the mobility-weighted force u = W F from per-tile partial products,
 //     summed in a fixed order (no atomics: the results do not depend on timing);
 //   - right-looking blocked Cholesky over tile columns K: the owner of (K, K)
@@ -32,27 +35,46 @@ namespace bdra {
 
 constexpr int kHIThreads = 256;
 constexpr int kHIMaxBeads = 64;
-constexpr int kHINT = (3 * kHIMaxBeads + 3) / 4;                  // tile rows of the largest tensor
-constexpr int kHITiles = kHINT * (kHINT + 1) / 2;                 // its lower tiles
-// Tiles per thread: kHIMaxT for chains of up to kHIMaxBeads beads, kHISmallT
-// (fewer registers, two CTAs per SM) for up to kHISmallBeads beads.
-constexpr int kHIMaxT = (kHITiles + kHIThreads - 1) / kHIThreads;
 constexpr int kHISmallBeads = 50;
-constexpr int kHISmallT = ((3 * kHISmallBeads + 3) / 4 * ((3 * kHISmallBeads + 3) / 4 + 1) / 2 +
-                           kHIThreads - 1) / kHIThreads;
+// Tile rows of the largest tensor of each kernel: chains of up to
+// kHISmallBeads beads (three tiles per thread, two CTAs per SM) and of up to
+// kHIMaxBeads (five tiles per thread).
+constexpr int kHINTSmall = (3 * kHISmallBeads + 3) / 4;
+constexpr int kHINTMax = (3 * kHIMaxBeads + 3) / 4;
 
-template <typename T> struct HIShared {
-    alignas(16) T pos[4 * kHINT];      // bead positions [3N] (COM frame); padding 0
-    alignas(16) T frc[4 * kHINT];      // bead forces [3N]; padding 0
-    alignas(16) T xi[4 * kHINT];       // bead normals [3N]; padding 0
+template <int NTM> struct HIDims {
+    static constexpr int tiles = NTM * (NTM + 1) / 2;                       // lower tiles
+    static constexpr int maxt = (tiles + kHIThreads - 1) / kHIThreads;      // tiles per thread
+};
+
+template <typename T, int NTM> struct HIShared {
+    static constexpr int kTiles = HIDims<NTM>::tiles;
+    static constexpr int kPanel = 20;  // panel row stride: 16-byte rows, conflict-free vector loads
+    alignas(16) T pos[4 * NTM];        // bead positions [3N] (COM frame); padding 0
+    alignas(16) T frc[4 * NTM];        // bead forces [3N]; padding 0
+    alignas(16) T xi[4 * NTM];         // bead normals [3N]; padding 0
     alignas(16) T diag[16];            // factor of the current diagonal tile
     alignas(16) T dinv[4];             // reciprocals of its diagonal
-    alignas(16) T panel[kHINT][16];    // factor tiles of the current tile column, by tile row
-    alignas(16) T part[kHITiles][8];   // per-tile partial products
+    alignas(16) T panel[NTM][kPanel];  // factor tiles of the current tile column, by tile row
+    // W's lower tiles (entry e of tile t at tiles[e][t]) until the threads
+    // have loaded theirs, then the per-tile partial products (part[c][t])
+    union {
+        T tiles[16][kTiles];
+        T part[8][kTiles];
+    } alignas(16) st;
     T com[3];
 };
 
 __device__ __forceinline__ int hi_tile(int I, int J) { return I * (I + 1) / 2 + J; }
+
+// Row-major lower-triangle index t = I (I + 1) / 2 + J back to (I, J).
+__device__ __forceinline__ void hi_untri(int t, int& I, int& J)
+{
+    I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (I * (I + 1) / 2 > t) --I;
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    J = t - I * (I + 1) / 2;
+}
 
 // The RPY block of two different beads as c_i I + c_d d d^T.
 template <typename T, bool FAST>
@@ -72,6 +94,35 @@ __device__ __forceinline__ void rpy_coef(T dx, T dy, T dz, T a, T& ci, T& cd)
     }
 }
 
+// 16 values from / to 16-byte aligned shared memory.
+__device__ __forceinline__ void hi_ld16(const float* src, float (&d)[16])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 v = reinterpret_cast<const float4*>(src)[q];
+        d[4 * q] = v.x; d[4 * q + 1] = v.y; d[4 * q + 2] = v.z; d[4 * q + 3] = v.w;
+    }
+}
+__device__ __forceinline__ void hi_ld16(const double* src, double (&d)[16])
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const double2 v = reinterpret_cast<const double2*>(src)[q];
+        d[2 * q] = v.x; d[2 * q + 1] = v.y;
+    }
+}
+__device__ __forceinline__ void hi_st16(float* dst, const float (&d)[16])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4*>(dst)[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+}
+__device__ __forceinline__ void hi_st16(double* dst, const double (&d)[16])
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(d[2 * q], d[2 * q + 1]);
+}
+
 // Per-thread state of the tensor tiles.
 template <typename T, int MAXT> struct HITiles {
     T A[MAXT][16];       // row-major 4 x 4
@@ -86,78 +137,64 @@ __device__ __forceinline__ void hi_tiles_init(HITiles<T, MAXT>& tl, int NT)
     for (int s = 0; s < MAXT; ++s) {
         const int t = threadIdx.x + s * kHIThreads;
         int I = -1, J = -1;
-        if (t < total) {
-            I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-            while (I * (I + 1) / 2 > t) --I;
-            while ((I + 1) * (I + 2) / 2 <= t) ++I;
-            J = t - I * (I + 1) / 2;
-        }
+        if (t < total) hi_untri(t, I, J);
         tl.I[s] = I;
         tl.J[s] = J;
     }
 }
 
-// Entries of one tile of W from the RPY coefficients of the (at most) 2 x 2
-// bead pairs it covers. The row of entry i is 3 br + PR + i (PR = r0 mod 3,
-// the tile's first row r0 = 4I), so its bead offset u and component x are
-// compile-time constants here, as are those of the columns (PC).
-template <typename T, int PR, int PC>
-__device__ __forceinline__ void hi_fill(T (&A)[16], const T (&ci)[2][2], const T (&cd)[2][2],
-                                        const T (&d)[2][2][3], int r0, int c0, int br, int bc, int n)
+// W's lower tiles into sm.st.tiles from the positions: bead pairs bi >= bj,
+// spread over the threads; a 3 x 3 block per pair (Eq. 2 on the diagonal,
+// Eq. 3 off it). Entries above the diagonal inside a diagonal tile are
+// written too (W is symmetric); rows and columns >= 3N are not written.
+template <typename T, bool FAST, int NTM>
+__device__ __forceinline__ void hi_assemble(HIShared<T, NTM>& sm, int N, T a)
 {
+    const int pairs = N * (N + 1) / 2;
+#pragma unroll 1
+    for (int k = threadIdx.x; k < pairs; k += kHIThreads) {
+        int bi, bj;
+        hi_untri(k, bi, bj);
+        T ci = T(1), cd = T(0), d[3] = {T(0), T(0), T(0)};
+        if (bi != bj) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int x = (PR + i) % 3, u = (PR + i) / 3;
-            const int y = (PC + j) % 3, v = (PC + j) / 3;
-            const int p = r0 + i, q = c0 + j;
-            T w;
-            if (p >= n || q >= n) w = p == q ? T(1) : T(0);          // padding: identity
-            else if (br + u == bc + v) w = x == y ? T(1) : T(0);      // Eq. 2
-            else {
-                w = cd[u][v] * d[u][v][x] * d[u][v][y];
-                if (x == y) w += ci[u][v];
-            }
-            A[4 * i + j] = w;
+            for (int c = 0; c < 3; ++c) d[c] = sm.pos[3 * bj + c] - sm.pos[3 * bi + c];
+            rpy_coef<T, FAST>(d[0], d[1], d[2], a, ci, cd);
         }
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+            for (int y = 0; y < 3; ++y) {
+                const int p = 3 * bi + x, q = 3 * bj + y;
+                if (p < q) continue;                    // diagonal block: lower part (mirrored below)
+                T w = cd * d[x] * d[y];
+                if (x == y) w += ci;
+                const int I = p >> 2, J = q >> 2, t = hi_tile(I, J);
+                sm.st.tiles[4 * (p & 3) + (q & 3)][t] = w;
+                if (I == J && p != q) sm.st.tiles[4 * (q & 3) + (p & 3)][t] = w;
+            }
+    }
 }
 
-// W's tiles from the positions (n = 3N rows; rows and columns >= n are the
-// identity's).
-template <typename T, bool FAST, int MAXT>
-__device__ __forceinline__ void hi_assemble(HITiles<T, MAXT>& tl, const T* pos, int n, T a)
+// The thread's tiles from sm.st.tiles; rows and columns >= n (the last tile
+// row only) are the identity's.
+template <typename T, int NTM, int MAXT>
+__device__ __forceinline__ void hi_load_tiles(HITiles<T, MAXT>& tl, const HIShared<T, NTM>& sm, int n)
 {
 #pragma unroll
     for (int s = 0; s < MAXT; ++s) {
         if (tl.I[s] < 0) continue;
-        const int r0 = 4 * tl.I[s], c0 = 4 * tl.J[s];
-        const int br = r0 / 3, bc = c0 / 3;
-        T ci[2][2], cd[2][2], d[2][2][3];
+        const int I = tl.I[s], J = tl.J[s], t = hi_tile(I, J);
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int e = 0; e < 16; ++e) tl.A[s][e] = sm.st.tiles[e][t];
+        if (4 * I + 3 >= n) {
 #pragma unroll
-            for (int v = 0; v < 2; ++v) {
-                const int bi = br + u, bj = bc + v;
-                d[u][v][0] = d[u][v][1] = d[u][v][2] = T(0);
-                ci[u][v] = cd[u][v] = T(0);
-                if (3 * bi < n && 3 * bj < n && bi != bj) {
-                    d[u][v][0] = pos[3 * bj] - pos[3 * bi];
-                    d[u][v][1] = pos[3 * bj + 1] - pos[3 * bi + 1];
-                    d[u][v][2] = pos[3 * bj + 2] - pos[3 * bi + 2];
-                    rpy_coef<T, FAST>(d[u][v][0], d[u][v][1], d[u][v][2], a, ci[u][v], cd[u][v]);
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int p = 4 * I + i, q = 4 * J + j;
+                    if (p >= n || q >= n) tl.A[s][4 * i + j] = p == q ? T(1) : T(0);
                 }
-            }
-        switch (3 * (r0 - 3 * br) + (c0 - 3 * bc)) {
-        case 0: hi_fill<T, 0, 0>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
-        case 1: hi_fill<T, 0, 1>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
-        case 2: hi_fill<T, 0, 2>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
-        case 3: hi_fill<T, 1, 0>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
-        case 4: hi_fill<T, 1, 1>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
-        case 5: hi_fill<T, 1, 2>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
-        case 6: hi_fill<T, 2, 0>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
-        case 7: hi_fill<T, 2, 1>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
-        default: hi_fill<T, 2, 2>(tl.A[s], ci, cd, d, r0, c0, br, bc, n); break;
         }
     }
 }
@@ -198,8 +235,7 @@ template <typename T>
 __device__ __forceinline__ void hi_trsm4(T (&A)[16], const T* L, const T* inv)
 {
     T Lr[16], iv[4];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) Lr[e] = L[e];
+    hi_ld16(L, Lr);
 #pragma unroll
     for (int c = 0; c < 4; ++c) iv[c] = inv[c];
 #pragma unroll
@@ -214,8 +250,8 @@ __device__ __forceinline__ void hi_trsm4(T (&A)[16], const T* L, const T* inv)
 }
 
 // In-place lower Cholesky factor of the CTA's tiles (every thread calls it).
-template <typename T, bool FAST, int MAXT>
-__device__ __forceinline__ void hi_cholesky(HITiles<T, MAXT>& tl, HIShared<T>& sm, int NT)
+template <typename T, bool FAST, int NTM, int MAXT>
+__device__ __forceinline__ void hi_cholesky(HITiles<T, MAXT>& tl, HIShared<T, NTM>& sm, int NT)
 {
 #pragma unroll 1
     for (int K = 0; K < NT; ++K) {
@@ -224,8 +260,7 @@ __device__ __forceinline__ void hi_cholesky(HITiles<T, MAXT>& tl, HIShared<T>& s
             if (tl.I[s] == K && tl.J[s] == K) {
                 T inv[4];
                 hi_chol4<T, FAST>(tl.A[s], inv);
-#pragma unroll
-                for (int e = 0; e < 16; ++e) sm.diag[e] = tl.A[s][e];
+                hi_st16(sm.diag, tl.A[s]);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) sm.dinv[e] = inv[e];
             }
@@ -234,77 +269,81 @@ __device__ __forceinline__ void hi_cholesky(HITiles<T, MAXT>& tl, HIShared<T>& s
         for (int s = 0; s < MAXT; ++s)
             if (tl.J[s] == K && tl.I[s] > K) {
                 hi_trsm4(tl.A[s], sm.diag, sm.dinv);
-#pragma unroll
-                for (int e = 0; e < 16; ++e) sm.panel[tl.I[s]][e] = tl.A[s][e];
+                hi_st16(sm.panel[tl.I[s]], tl.A[s]);
             }
         __syncthreads();
 #pragma unroll
         for (int s = 0; s < MAXT; ++s)
             if (tl.J[s] > K) {
-                const T* Pi = sm.panel[tl.I[s]];
-                const T* Pj = sm.panel[tl.J[s]];
-                T lj[16];
+                T li[16], lj[16];
+                hi_ld16(sm.panel[tl.I[s]], li);
+                hi_ld16(sm.panel[tl.J[s]], lj);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) lj[e] = Pj[e];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    T li[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) li[k] = Pi[4 * i + k];
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         T v = tl.A[s][4 * i + j];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) v = fma(-li[k], lj[4 * j + k], v);
+                        for (int k = 0; k < 4; ++k) v = fma(-li[4 * i + k], lj[4 * j + k], v);
                         tl.A[s][4 * i + j] = v;
                     }
-                }
             }
     }
 }
 
-// Bead forces into sm.frc (springs and pair forces), one thread per bead;
-// returns the FENE floor count of the thread's spring.
-template <typename T, bool FAST>
-__device__ __forceinline__ int hi_forces(HIShared<T>& sm, int N, const StepConst<T, FAST>& k,
+// Bead forces into sm.frc (springs and pair forces): four consecutive
+// threads a bead (N <= kHIThreads / 4), the pair sum split over them by
+// partner index mod 4 and combined by shuffles in a fixed order. Returns the
+// FENE floor count of the thread's spring (the bead's first thread).
+template <typename T, bool FAST, int NTM>
+__device__ __forceinline__ int hi_forces(HIShared<T, NTM>& sm, int N, const StepConst<T, FAST>& k,
                                          const ChainDev& ch, bool harmonic, bool lj)
 {
-    const int b = threadIdx.x;
+    const int b = threadIdx.x >> 2, q = threadIdx.x & 3;
     int floored = 0;
+    T f[3] = {T(0), T(0), T(0)};
     if (b < N) {
-        T f[3] = {T(0), T(0), T(0)};
-        const T r0 = (T)ch.r0;
-        // springs b (to bead b+1) and b-1 (from bead b-1)
+        if (q == 0) {
+            const T r0 = (T)ch.r0;
+            // springs b (to bead b+1) and b-1 (from bead b-1)
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const int i = b - side;               // spring index
-            if (i < 0 || i + 1 >= N) continue;
-            const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
-            const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];
-            const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
-            T c;
-            if (harmonic) {
-                c = harmonic_coef<T, FAST>(qx, qy, qz, k.H, r0);
-            } else {
-                int fl = 0;
-                c = spring_coef<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin, fl);
-                if (side == 0) floored += fl;
+            for (int side = 0; side < 2; ++side) {
+                const int i = b - side;               // spring index
+                if (i < 0 || i + 1 >= N) continue;
+                const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
+                const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];
+                const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
+                T c;
+                if (harmonic) {
+                    c = harmonic_coef<T, FAST>(qx, qy, qz, k.H, r0);
+                } else {
+                    int fl = 0;
+                    c = spring_coef<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin, fl);
+                    if (side == 0) floored += fl;
+                }
+                const T sg = side == 0 ? T(1) : T(-1);
+                f[0] = fma(sg * c, qx, f[0]); f[1] = fma(sg * c, qy, f[1]); f[2] = fma(sg * c, qz, f[2]);
             }
-            const T sg = side == 0 ? T(1) : T(-1);
-            f[0] = fma(sg * c, qx, f[0]); f[1] = fma(sg * c, qy, f[1]); f[2] = fma(sg * c, qz, f[2]);
         }
         if (lj) {
             LJConst<T> kl;
             kl.load(ch);
             const T x0 = sm.pos[3 * b], y0 = sm.pos[3 * b + 1], z0 = sm.pos[3 * b + 2];
 #pragma unroll 1
-            for (int j = 0; j < N; ++j) {
+            for (int j = q; j < N; j += 4) {
                 if (j == b || j == b - 1 || j == b + 1) continue;
                 const T dx = sm.pos[3 * j] - x0, dy = sm.pos[3 * j + 1] - y0, dz = sm.pos[3 * j + 2] - z0;
                 const T c = lj_coef<T, FAST>(dx, dy, dz, kl);
                 f[0] = fma(c, dx, f[0]); f[1] = fma(c, dy, f[1]); f[2] = fma(c, dz, f[2]);
             }
         }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        f[c] += __shfl_xor_sync(0xffffffffu, f[c], 1);
+        f[c] += __shfl_xor_sync(0xffffffffu, f[c], 2);
+    }
+    if (b < N && q == 0) {
         sm.frc[3 * b] = f[0];
         sm.frc[3 * b + 1] = f[1];
         sm.frc[3 * b + 2] = f[2];
@@ -313,8 +352,8 @@ __device__ __forceinline__ int hi_forces(HIShared<T>& sm, int N, const StepConst
 }
 
 // Positions from bonds [nb][3] (bead 0 at the origin), then the COM shift.
-template <typename T>
-__device__ __forceinline__ void hi_load_bonds(HIShared<T>& sm, const T* bonds, int N)
+template <typename T, int NTM>
+__device__ __forceinline__ void hi_load_bonds(HIShared<T, NTM>& sm, const T* bonds, int N)
 {
     __syncthreads();     // every thread is done reading the old positions
     if (threadIdx.x < 3) {
@@ -334,22 +373,22 @@ __device__ __forceinline__ void hi_load_bonds(HIShared<T>& sm, const T* bonds, i
     __syncthreads();
 }
 
-template <typename T>
-__device__ __forceinline__ void hi_store_bonds(const HIShared<T>& sm, T* bonds, int N)
+template <typename T, int NTM>
+__device__ __forceinline__ void hi_store_bonds(const HIShared<T, NTM>& sm, T* bonds, int N)
 {
     for (int e = threadIdx.x; e < 3 * (N - 1); e += blockDim.x) bonds[e] = sm.pos[e + 3] - sm.pos[e];
 }
 
 // One step t -> t + 1 of the CTA's slot. Returns the thread's floor count.
-template <typename T, bool FAST, int MAXT>
-__device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T, MAXT>& tl, const ChainDev& ch,
+template <typename T, bool FAST, int NTM, int MAXT>
+__device__ __forceinline__ int hi_step(HIShared<T, NTM>& sm, HITiles<T, MAXT>& tl, const ChainDev& ch,
                                        const StepConst<T, FAST>& k, const StepParams& p, int N, int NT,
                                        uint32_t slot_key, uint32_t chain, uint32_t step, bool harmonic,
                                        bool lj)
 {
     const int n = 3 * N;
     const int tid = threadIdx.x;
-    const int floored = hi_forces<T, FAST>(sm, N, k, ch, harmonic, lj);
+    const int floored = hi_forces<T, FAST, NTM>(sm, N, k, ch, harmonic, lj);
     if (tid < N) {
         T z0, z1, z2;
         bead_noise<T, FAST>((uint32_t)tid, slot_key, step, chain, p, z0, z1, z2);
@@ -357,20 +396,21 @@ __device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T, MAXT>& tl, co
         sm.xi[3 * tid + 1] = z1;
         sm.xi[3 * tid + 2] = z2;
     }
-    hi_assemble<T, FAST, MAXT>(tl, sm.pos, n, (T)ch.hi_a);
+    hi_assemble<T, FAST, NTM>(sm, N, (T)ch.hi_a);
     __syncthreads();
+    hi_load_tiles<T, NTM, MAXT>(tl, sm, n);
+    __syncthreads();                   // the partial products below overwrite the tile copy
     // u = W F: per tile W_IJ F_J (rows I) and, below the diagonal, W_IJ^T F_I (rows J)
 #pragma unroll
     for (int s = 0; s < MAXT; ++s) {
         if (tl.I[s] < 0) continue;
-        const int I = tl.I[s], J = tl.J[s];
-        T* out = sm.part[hi_tile(I, J)];
+        const int I = tl.I[s], J = tl.J[s], t = hi_tile(I, J);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             T v = T(0);
 #pragma unroll
             for (int j = 0; j < 4; ++j) v = fma(tl.A[s][4 * i + j], sm.frc[4 * J + j], v);
-            out[i] = v;
+            sm.st.part[i][t] = v;
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -379,30 +419,29 @@ __device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T, MAXT>& tl, co
 #pragma unroll
                 for (int i = 0; i < 4; ++i) v = fma(tl.A[s][4 * i + j], sm.frc[4 * I + i], v);
             }
-            out[4 + j] = v;
+            sm.st.part[4 + j][t] = v;
         }
     }
     __syncthreads();
     T u = T(0);
     if (tid < n) {
         const int I = tid >> 2, c = tid & 3;
-        for (int J = 0; J <= I; ++J) u += sm.part[hi_tile(I, J)][c];
-        for (int I2 = I + 1; I2 < NT; ++I2) u += sm.part[hi_tile(I2, I)][4 + c];
+        for (int J = 0; J <= I; ++J) u += sm.st.part[c][hi_tile(I, J)];
+        for (int I2 = I + 1; I2 < NT; ++I2) u += sm.st.part[4 + c][hi_tile(I2, I)];
     }
-    hi_cholesky<T, FAST, MAXT>(tl, sm, NT);     // its first barrier also ends the reads of sm.part above
+    hi_cholesky<T, FAST, NTM, MAXT>(tl, sm, NT);   // its first barrier also ends the reads of sm.st above
     // w = L xi
 #pragma unroll
     for (int s = 0; s < MAXT; ++s) {
         if (tl.I[s] < 0) continue;
-        const int I = tl.I[s], J = tl.J[s];
-        T* out = sm.part[hi_tile(I, J)];
+        const int I = tl.I[s], J = tl.J[s], t = hi_tile(I, J);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             T v = T(0);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (J < I || j <= i) v = fma(tl.A[s][4 * i + j], sm.xi[4 * J + j], v);
-            out[i] = v;
+            sm.st.part[i][t] = v;
         }
     }
     __syncthreads();
@@ -410,7 +449,7 @@ __device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T, MAXT>& tl, co
     if (tid < n) {
         const int I = tid >> 2, c = tid & 3;
         T w = T(0);
-        for (int J = 0; J <= I; ++J) w += sm.part[hi_tile(I, J)][c];
+        for (int J = 0; J <= I; ++J) w += sm.st.part[c][hi_tile(I, J)];
         const int x = tid % 3, b3 = tid - x;
         const T r = sm.pos[tid];
         // kappa . r dt: xx, yy, zz and xz (shear) only
@@ -443,12 +482,13 @@ __device__ __forceinline__ int hi_step(HIShared<T>& sm, HITiles<T, MAXT>& tl, co
 // Replicas: one CTA per work item (one replica), the items of this launch in
 // p.items. Spawn from the window-start snapshot, S steps, one force sample per
 // spring at the window end into the replica's partial row (its group).
-template <typename T, bool FAST, int MAXT>
-__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && MAXT <= kHISmallT) ? 2 : 1)
+template <typename T, bool FAST, int NTM>
+__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 2 : 1)
 hi_replica_kernel(const StepParams p)
 {
+    constexpr int MAXT = HIDims<NTM>::maxt;
     extern __shared__ __align__(16) unsigned char hi_smem_raw[];
-    HIShared<T>& sm = *reinterpret_cast<HIShared<T>*>(hi_smem_raw);
+    HIShared<T, NTM>& sm = *reinterpret_cast<HIShared<T, NTM>*>(hi_smem_raw);
     if ((int)blockIdx.x >= p.n_items) return;
     const ItemDev it = p.items[blockIdx.x];
     const ChainDev ch = p.chains[it.chain];
@@ -459,7 +499,7 @@ hi_replica_kernel(const StepParams p)
     const uint32_t key = (p.flags & BD_FLAG_IDENTICAL_NOISE) ? 0u : (uint32_t)kglob;
     StepConst<T, FAST> k;
     k.load(ch, p);
-    for (int e = threadIdx.x; e < 4 * kHINT; e += blockDim.x) {
+    for (int e = threadIdx.x; e < 4 * NTM; e += blockDim.x) {
         sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
     }
     __syncthreads();
@@ -475,7 +515,7 @@ hi_replica_kernel(const StepParams p)
 #pragma unroll 1
     for (int64_t t = p.t0; t < t_end; ++t) {
         if (s_in == 0) hi_load_bonds(sm, snap + ((w % p.win_ring) * p.M + ch.spr_off) * 3, N);
-        floored += hi_step<T, FAST, MAXT>(sm, tl, ch, k, p, N, NT, key, (uint32_t)it.chain, (uint32_t)t,
+        floored += hi_step<T, FAST, NTM, MAXT>(sm, tl, ch, k, p, N, NT, key, (uint32_t)it.chain, (uint32_t)t,
                                           harmonic, lj);
         if (++s_in == p.S) {
             s_in = 0;
@@ -498,12 +538,13 @@ hi_replica_kernel(const StepParams p)
 // Parents: one CTA per chain (p.parent_warps[blockIdx.x].first indexes
 // p.parent_items). Window-start snapshots, then per step the update and the
 // instantaneous force of every spring: TSF sums and the ISF criteria.
-template <typename T, bool FAST, int MAXT>
-__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && MAXT <= kHISmallT) ? 2 : 1)
+template <typename T, bool FAST, int NTM>
+__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 2 : 1)
 hi_parent_kernel(const StepParams p)
 {
+    constexpr int MAXT = HIDims<NTM>::maxt;
     extern __shared__ __align__(16) unsigned char hi_smem_raw[];
-    HIShared<T>& sm = *reinterpret_cast<HIShared<T>*>(hi_smem_raw);
+    HIShared<T, NTM>& sm = *reinterpret_cast<HIShared<T, NTM>*>(hi_smem_raw);
     if ((int)blockIdx.x >= p.n_parent_warps) return;
     const int c = p.parent_items[p.parent_warps[blockIdx.x].first];
     const ChainDev ch = p.chains[c];
@@ -512,7 +553,7 @@ hi_parent_kernel(const StepParams p)
     const bool lj = ch.lj_u > 0.0;
     StepConst<T, FAST> k;
     k.load(ch, p);
-    for (int e = threadIdx.x; e < 4 * kHINT; e += blockDim.x) {
+    for (int e = threadIdx.x; e < 4 * NTM; e += blockDim.x) {
         sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
     }
     __syncthreads();
@@ -546,7 +587,7 @@ hi_parent_kernel(const StepParams p)
             // the parent's noise repeat the parent exactly
             hi_load_bonds(sm, row, N);
         }
-        floored += hi_step<T, FAST, MAXT>(sm, tl, ch, k, p, N, NT, 0u, (uint32_t)c, (uint32_t)t, harmonic, lj);
+        floored += hi_step<T, FAST, NTM, MAXT>(sm, tl, ch, k, p, N, NT, 0u, (uint32_t)c, (uint32_t)t, harmonic, lj);
         if (mine) {
             const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
             const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];

@@ -11,20 +11,23 @@ static_assert(kHIThreads == kHIThreadsHost && kHIMaxBeads == kHIMaxBeadsHost &&
 
 const void* hi_replica_func_f32(bool small)
 {
-    return small ? (const void*)hi_replica_kernel<float, true, kHISmallT>
-                 : (const void*)hi_replica_kernel<float, true, kHIMaxT>;
+    return small ? (const void*)hi_replica_kernel<float, true, kHINTSmall>
+                 : (const void*)hi_replica_kernel<float, true, kHINTMax>;
 }
 const void* hi_parent_func_f32(bool small)
 {
-    return small ? (const void*)hi_parent_kernel<float, true, kHISmallT>
-                 : (const void*)hi_parent_kernel<float, true, kHIMaxT>;
+    return small ? (const void*)hi_parent_kernel<float, true, kHINTSmall>
+                 : (const void*)hi_parent_kernel<float, true, kHINTMax>;
 }
-size_t hi_smem_f32() { return sizeof(HIShared<float>); }
+size_t hi_smem_f32(bool small)
+{
+    return small ? sizeof(HIShared<float, kHINTSmall>) : sizeof(HIShared<float, kHINTMax>);
+}
 
 cudaError_t hi_prepare_f32()
 {
-    const int smem = (int)sizeof(HIShared<float>);
     for (int small = 0; small < 2; ++small) {
+        const int smem = (int)hi_smem_f32(small);
         cudaError_t e = cudaFuncSetAttribute(hi_replica_func_f32(small), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(hi_parent_func_f32(small), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

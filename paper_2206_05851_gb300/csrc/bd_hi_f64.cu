@@ -11,20 +11,23 @@ static_assert(kHIThreads == kHIThreadsHost && kHIMaxBeads == kHIMaxBeadsHost &&
 
 const void* hi_replica_func_f64(bool small)
 {
-    return small ? (const void*)hi_replica_kernel<double, false, kHISmallT>
-                 : (const void*)hi_replica_kernel<double, false, kHIMaxT>;
+    return small ? (const void*)hi_replica_kernel<double, false, kHINTSmall>
+                 : (const void*)hi_replica_kernel<double, false, kHINTMax>;
 }
 const void* hi_parent_func_f64(bool small)
 {
-    return small ? (const void*)hi_parent_kernel<double, false, kHISmallT>
-                 : (const void*)hi_parent_kernel<double, false, kHIMaxT>;
+    return small ? (const void*)hi_parent_kernel<double, false, kHINTSmall>
+                 : (const void*)hi_parent_kernel<double, false, kHINTMax>;
 }
-size_t hi_smem_f64() { return sizeof(HIShared<double>); }
+size_t hi_smem_f64(bool small)
+{
+    return small ? sizeof(HIShared<double, kHINTSmall>) : sizeof(HIShared<double, kHINTMax>);
+}
 
 cudaError_t hi_prepare_f64()
 {
-    const int smem = (int)sizeof(HIShared<double>);
     for (int small = 0; small < 2; ++small) {
+        const int smem = (int)hi_smem_f64(small);
         cudaError_t e = cudaFuncSetAttribute(hi_replica_func_f64(small), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(hi_parent_func_f64(small), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -48,8 +48,8 @@ const void* hi_replica_func_f32(bool small);
 const void* hi_replica_func_f64(bool small);
 const void* hi_parent_func_f32(bool small);
 const void* hi_parent_func_f64(bool small);
-size_t hi_smem_f32();
-size_t hi_smem_f64();
+size_t hi_smem_f32(bool small);
+size_t hi_smem_f64(bool small);
 cudaError_t hi_prepare_f32();
 cudaError_t hi_prepare_f64();
 
