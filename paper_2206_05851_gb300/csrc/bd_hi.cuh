@@ -13,8 +13,8 @@
 // One CTA integrates one slot (parent or replica) of a chain of N <= 64
 // beads, its positions (centre-of-mass frame) in shared memory. The 3N x 3N
 // tensor is held as 4 x 4 tiles of its lower triangle in the registers of
-// the CTA's threads (tile t of the row-major lower order belongs to thread
-// t mod kHIThreads). Per step:
+// the CTA's threads (tile t of the column-major lower order belongs to
+// thread t mod kHIThreads). Per step:
 //   - bead forces (springs; Lennard-Jones split over four threads a bead) and
 //     bead normals;
 //   - the tensor, one 3 x 3 bead block per thread at a time, into a
@@ -22,9 +22,10 @@
 //     own tiles;
 //   - the mobility-weighted force u = W F from per-tile partial products,
 //     summed in a fixed order (no atomics: the results do not depend on timing);
-//   - right-looking blocked Cholesky over tile columns K: the owner of (K, K)
-//     factors it, the owners of (I, K) solve against it, and every owner of a
-//     tile (I, J), K < J <= I, subtracts L_IK L_JK^T - two barriers a column;
+//   - right-looking blocked Cholesky over tile columns K: the owners of
+//     (I, K) solve against the factored (K, K), every owner of a tile (I, J),
+//     K < J <= I, subtracts L_IK L_JK^T, and the owner of (K+1, K+1)
+//     factors it as soon as its own update is done - two barriers a column;
 //   - the correlated noise L xi from per-tile partials, the update and the
 //     centre-of-mass shift.
 #pragma once
@@ -65,7 +66,18 @@ template <typename T, int NTM> struct HIShared {
     T com[3];
 };
 
-__device__ __forceinline__ int hi_tile(int I, int J) { return I * (I + 1) / 2 + J; }
+// Tiles of the lower triangle (I >= J) in column-major order over NT tile
+// rows: column J starts at J NT - J (J - 1) / 2. The tiles still to be
+// updated at column step K (J > K) are then a suffix of the order, so they
+// sit on consecutive threads and finished warps drop out whole.
+__device__ __forceinline__ int hi_tile(int I, int J, int NT) { return J * NT - J * (J - 1) / 2 + (I - J); }
+
+__device__ __forceinline__ void hi_uncol(int t, int NT, int& I, int& J)
+{
+    J = 0;
+    while (J + 1 < NT && (J + 1) * NT - (J + 1) * J / 2 <= t) ++J;
+    I = J + (t - (J * NT - J * (J - 1) / 2));
+}
 
 // Row-major lower-triangle index t = I (I + 1) / 2 + J back to (I, J).
 __device__ __forceinline__ void hi_untri(int t, int& I, int& J)
@@ -137,7 +149,7 @@ __device__ __forceinline__ void hi_tiles_init(HITiles<T, MAXT>& tl, int NT)
     for (int s = 0; s < MAXT; ++s) {
         const int t = threadIdx.x + s * kHIThreads;
         int I = -1, J = -1;
-        if (t < total) hi_untri(t, I, J);
+        if (t < total) hi_uncol(t, NT, I, J);
         tl.I[s] = I;
         tl.J[s] = J;
     }
@@ -151,6 +163,7 @@ template <typename T, bool FAST, int NTM>
 __device__ __forceinline__ void hi_assemble(HIShared<T, NTM>& sm, int N, T a)
 {
     const int pairs = N * (N + 1) / 2;
+    const int NT = (3 * N + 3) / 4;
 #pragma unroll 1
     for (int k = threadIdx.x; k < pairs; k += kHIThreads) {
         int bi, bj;
@@ -169,7 +182,7 @@ __device__ __forceinline__ void hi_assemble(HIShared<T, NTM>& sm, int N, T a)
                 if (p < q) continue;                    // diagonal block: lower part (mirrored below)
                 T w = cd * d[x] * d[y];
                 if (x == y) w += ci;
-                const int I = p >> 2, J = q >> 2, t = hi_tile(I, J);
+                const int I = p >> 2, J = q >> 2, t = hi_tile(I, J, NT);
                 sm.st.tiles[4 * (p & 3) + (q & 3)][t] = w;
                 if (I == J && p != q) sm.st.tiles[4 * (q & 3) + (p & 3)][t] = w;
             }
@@ -184,7 +197,7 @@ __device__ __forceinline__ void hi_load_tiles(HITiles<T, MAXT>& tl, const HIShar
 #pragma unroll
     for (int s = 0; s < MAXT; ++s) {
         if (tl.I[s] < 0) continue;
-        const int I = tl.I[s], J = tl.J[s], t = hi_tile(I, J);
+        const int I = tl.I[s], J = tl.J[s], t = hi_tile(I, J, (n + 3) >> 2);
 #pragma unroll
         for (int e = 0; e < 16; ++e) tl.A[s][e] = sm.st.tiles[e][t];
         if (4 * I + 3 >= n) {
@@ -250,21 +263,26 @@ __device__ __forceinline__ void hi_trsm4(T (&A)[16], const T* L, const T* inv)
 }
 
 // In-place lower Cholesky factor of the CTA's tiles (every thread calls it).
+// Column step K: the owners of (I, K), I > K, solve against the factored
+// diagonal tile; barrier; every owner of a tile (I, J), K < J <= I,
+// subtracts L_IK L_JK^T, and the owner of (K+1, K+1), right after its own
+// update, factors that tile for the next step (the column-major order makes
+// it the thread's first active tile); barrier.
 template <typename T, bool FAST, int NTM, int MAXT>
 __device__ __forceinline__ void hi_cholesky(HITiles<T, MAXT>& tl, HIShared<T, NTM>& sm, int NT)
 {
+#pragma unroll
+    for (int s = 0; s < MAXT; ++s)
+        if (tl.I[s] == 0 && tl.J[s] == 0) {
+            T inv[4];
+            hi_chol4<T, FAST>(tl.A[s], inv);
+            hi_st16(sm.diag, tl.A[s]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sm.dinv[e] = inv[e];
+        }
+    __syncthreads();
 #pragma unroll 1
     for (int K = 0; K < NT; ++K) {
-#pragma unroll
-        for (int s = 0; s < MAXT; ++s)
-            if (tl.I[s] == K && tl.J[s] == K) {
-                T inv[4];
-                hi_chol4<T, FAST>(tl.A[s], inv);
-                hi_st16(sm.diag, tl.A[s]);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) sm.dinv[e] = inv[e];
-            }
-        __syncthreads();
 #pragma unroll
         for (int s = 0; s < MAXT; ++s)
             if (tl.J[s] == K && tl.I[s] > K) {
@@ -287,7 +305,15 @@ __device__ __forceinline__ void hi_cholesky(HITiles<T, MAXT>& tl, HIShared<T, NT
                         for (int k = 0; k < 4; ++k) v = fma(-li[4 * i + k], lj[4 * j + k], v);
                         tl.A[s][4 * i + j] = v;
                     }
+                if (tl.I[s] == K + 1 && tl.J[s] == K + 1) {
+                    T inv[4];
+                    hi_chol4<T, FAST>(tl.A[s], inv);
+                    hi_st16(sm.diag, tl.A[s]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) sm.dinv[e] = inv[e];
+                }
             }
+        __syncthreads();
     }
 }
 
@@ -404,7 +430,7 @@ __device__ __forceinline__ int hi_step(HIShared<T, NTM>& sm, HITiles<T, MAXT>& t
 #pragma unroll
     for (int s = 0; s < MAXT; ++s) {
         if (tl.I[s] < 0) continue;
-        const int I = tl.I[s], J = tl.J[s], t = hi_tile(I, J);
+        const int I = tl.I[s], J = tl.J[s], t = hi_tile(I, J, NT);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             T v = T(0);
@@ -426,15 +452,15 @@ __device__ __forceinline__ int hi_step(HIShared<T, NTM>& sm, HITiles<T, MAXT>& t
     T u = T(0);
     if (tid < n) {
         const int I = tid >> 2, c = tid & 3;
-        for (int J = 0; J <= I; ++J) u += sm.st.part[c][hi_tile(I, J)];
-        for (int I2 = I + 1; I2 < NT; ++I2) u += sm.st.part[4 + c][hi_tile(I2, I)];
+        for (int J = 0; J <= I; ++J) u += sm.st.part[c][hi_tile(I, J, NT)];
+        for (int I2 = I + 1; I2 < NT; ++I2) u += sm.st.part[4 + c][hi_tile(I2, I, NT)];
     }
     hi_cholesky<T, FAST, NTM, MAXT>(tl, sm, NT);   // its first barrier also ends the reads of sm.st above
     // w = L xi
 #pragma unroll
     for (int s = 0; s < MAXT; ++s) {
         if (tl.I[s] < 0) continue;
-        const int I = tl.I[s], J = tl.J[s], t = hi_tile(I, J);
+        const int I = tl.I[s], J = tl.J[s], t = hi_tile(I, J, NT);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             T v = T(0);
@@ -449,7 +475,7 @@ __device__ __forceinline__ int hi_step(HIShared<T, NTM>& sm, HITiles<T, MAXT>& t
     if (tid < n) {
         const int I = tid >> 2, c = tid & 3;
         T w = T(0);
-        for (int J = 0; J <= I; ++J) w += sm.st.part[c][hi_tile(I, J)];
+        for (int J = 0; J <= I; ++J) w += sm.st.part[c][hi_tile(I, J, NT)];
         const int x = tid % 3, b3 = tid - x;
         const T r = sm.pos[tid];
         // kappa . r dt: xx, yy, zz and xz (shear) only
