@@ -254,12 +254,12 @@ def bell_16384(n_steps: int = 250_000, n_chains: int = 16384) -> Workload:
 
 
 # The collapsed-chain model of Sec. II in these units: length a (bead radius),
-# energy kT, and time 4 tau (tau the single-bead diffusion time, so that the
-# bead diffusivity is 1/4 as in Eq. 1 above): a paper time step of 1e-5 tau is
-# 4e-5 here, its shear rate 30 / tau is 7.5, its evolution time S = 0.015 tau
-# is 1500 steps.
+# energy kT, and a time unit of tau / 4 (tau the single-bead diffusion time,
+# so that the bead diffusivity is 1/4 as in Eq. 1 above): a time of x tau is
+# 4x here, so the paper's time step of 1e-5 tau is 4e-5, its shear rate
+# 30 / tau is 7.5, and its evolution time S = 0.015 tau is 1500 steps.
 COLLAPSED_DT = 4e-5
-COLLAPSED_TAU = 4.0
+COLLAPSED_TAU = 4.0      # tau in these time units
 
 
 def collapsed_chain(n_replicas: int, rate: float = 7.5, n_beads: int = 50) -> Chain:

@@ -1,7 +1,8 @@
 """GPU parity for the paper's collapsed-chain model (Sec. II): harmonic springs
 with rest length 2a and Lennard-Jones cohesion between non-adjacent beads, in
 the paper's units mapped to the Hookean ones of the library (length a,
-energy kT, bead diffusivity 1/4: t = 4 tau, shear rate gamma-dot / 4).
+energy kT, bead diffusivity 1/4, so that tau is 4 time units and a shear rate
+gamma-dot / tau is gamma-dot / 4).
 
 - Same seeded inputs and Philox draws as the FP64 oracle: parent and replica
   positions, RSF and TSF profiles within 1e-10 (FP64) / 1e-4 (FP32) relative;
