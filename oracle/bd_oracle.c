@@ -139,6 +139,46 @@ int ora_spring_force(int spring, double H, double b, double r0, double s_min, co
     return floored;
 }
 
+/* The coarse-grained vWF chain (supplementary material, Table S1): a monomer
+ * is two beads joined by an A2 domain, a FENE spring in parallel with a
+ * stiffer harmonic spring; monomers are joined by disulfide bonds, stiff
+ * harmonic springs. Spring i joins beads i and i+1, so even springs are A2
+ * domains and odd springs disulfide bonds. With x = |Q| - r0 the extension
+ * beyond the rest length:
+ *   A2:        f = f_B x + f_A x / (1 - x^2 / x_max^2)   (the sum of the two
+ *              springs' forces, the force on the domain),
+ *   disulfide: f = H x,
+ * both along Q and signed as Eq. 4; the FENE denominator is floored at s_min
+ * like the FENE law above. */
+int ora_chain_spring_force(const ora_chain* ch, int i, double s_min, const double Q[3], double F[3],
+                           double* tension)
+{
+    if (ch->spring != ORA_SPRING_VWF)
+        return ora_spring_force(ch->spring, ch->H, ch->b, ch->r0, s_min, Q, F, tension);
+    const double q = sqrt(Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2]);
+    const double x = q - ch->r0;
+    double f;
+    int floored = 0;
+    if (i % 2 == 0) {
+        double s = 1.0 - x * x / (ch->vwf_xmax * ch->vwf_xmax);
+        if (s < s_min) { s = s_min; floored = 1; }
+        f = ch->vwf_fb * x + ch->vwf_fa * x / s;
+    } else {
+        f = ch->H * x;
+    }
+    const double coef = q > 0.0 ? f / q : 0.0;
+    F[0] = coef * Q[0];
+    F[1] = coef * Q[1];
+    F[2] = coef * Q[2];
+    if (tension) *tension = f;
+    return floored;
+}
+
+int ora_spring_reacts(const ora_chain* ch, int i)
+{
+    return ch->spring != ORA_SPRING_VWF || i % 2 == 0;
+}
+
 /* Sec. II: U_LJ = u sum_{ij} [(2a/r_ij)^12 - 2 (2a/r_ij)^6] over non-adjacent
  * beads; the force on bead i from bead j is -dU/dr_i = (dU/dr) r_ij / r with
  * r_ij = r_j - r_i and dU/dr = (12 u / r) [(s/r)^6 - (s/r)^12]. */
@@ -262,7 +302,7 @@ int64_t ora_em_step(const ora_chain* ch, double dt, double s_min, double* r, con
         double Q[3] = { r[3 * (i + 1) + 0] - r[3 * i + 0],
                         r[3 * (i + 1) + 1] - r[3 * i + 1],
                         r[3 * (i + 1) + 2] - r[3 * i + 2] };
-        floored += ora_spring_force(ch->spring, ch->H, ch->b, ch->r0, s_min, Q, &F[3 * i], NULL);
+        floored += ora_chain_spring_force(ch, i, s_min, Q, &F[3 * i], NULL);
     }
     double* Flj = (double*)calloc(3 * (size_t)N, sizeof(double));
     ora_lj_forces(ch, r, Flj);
@@ -322,7 +362,7 @@ void ora_tensions(const ora_chain* ch, double s_min, const double* r, double* f)
                         r[3 * (i + 1) + 1] - r[3 * i + 1],
                         r[3 * (i + 1) + 2] - r[3 * i + 2] };
         double F[3];
-        ora_spring_force(ch->spring, ch->H, ch->b, ch->r0, s_min, Q, F, &f[i]);
+        ora_chain_spring_force(ch, i, s_min, Q, F, &f[i]);
     }
 }
 
@@ -467,7 +507,8 @@ int ora_rsf_tangent(const ora_problem* p, int64_t n_steps, double* pos, double* 
     const int S = p->window_steps;
     if (C <= 0 || S <= 0 || n_steps < 0) return 1;
     for (int c = 0; c < C; ++c)      /* tangents of the Hooke and FENE laws only */
-        if (p->chains[c].spring == ORA_SPRING_HARMONIC || p->chains[c].lj_u > 0.0 ||
+        if (p->chains[c].spring == ORA_SPRING_HARMONIC || p->chains[c].spring == ORA_SPRING_VWF ||
+            p->chains[c].lj_u > 0.0 ||
             p->chains[c].hi_a > 0.0) return 1;
     int64_t* bead_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
     int64_t* spr_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C + 1));
@@ -710,11 +751,12 @@ static int run_impl(const ora_problem* p, int64_t n_steps, double* pos, double* 
                 for (int i = 0; i + 1 < N; ++i) {
                     tsum[i] += f[i];
                     const int64_t m = so + i;
-                    ora_criteria_update(ORA_ISF, (p->thr_mask >> ORA_ISF) & 1,
-                                        (p->bell_mask >> ORA_ISF) & 1, ch, f[i], p->dt,
-                                        t + s + 1, E[ORA_ISF * N + i],
-                                        &lam[ORA_ISF * M + m], &first_thr[ORA_ISF * M + m],
-                                        &first_bell[ORA_ISF * M + m]);
+                    if (ora_spring_reacts(ch, i))
+                        ora_criteria_update(ORA_ISF, (p->thr_mask >> ORA_ISF) & 1,
+                                            (p->bell_mask >> ORA_ISF) & 1, ch, f[i], p->dt,
+                                            t + s + 1, E[ORA_ISF * N + i],
+                                            &lam[ORA_ISF * M + m], &first_thr[ORA_ISF * M + m],
+                                            &first_bell[ORA_ISF * M + m]);
                 }
             }
 
@@ -726,6 +768,7 @@ static int run_impl(const ora_problem* p, int64_t n_steps, double* pos, double* 
                     const double ft = tsum[i] / S;
                     if (rsf) rsf[w * M + m] = fr;
                     if (tsf) tsf[w * M + m] = ft;
+                    if (!ora_spring_reacts(ch, i)) continue;
                     ora_criteria_update(ORA_TSF, (p->thr_mask >> ORA_TSF) & 1,
                                         (p->bell_mask >> ORA_TSF) & 1, ch, ft, dT, t + S,
                                         E[ORA_TSF * N + i],

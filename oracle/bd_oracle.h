@@ -19,7 +19,7 @@
 extern "C" {
 #endif
 
-enum { ORA_SPRING_HOOKE = 0, ORA_SPRING_FENE = 1, ORA_SPRING_HARMONIC = 2 };
+enum { ORA_SPRING_HOOKE = 0, ORA_SPRING_FENE = 1, ORA_SPRING_HARMONIC = 2, ORA_SPRING_VWF = 3 };
 enum { ORA_FLOW_NONE = 0, ORA_FLOW_SHEAR = 1, ORA_FLOW_UNIAXIAL = 2, ORA_FLOW_PLANAR = 3 };
 enum { ORA_ISF = 0, ORA_TSF = 1, ORA_RSF = 2 };          /* criterion index q */
 enum { ORA_STREAM_BD = 0, ORA_STREAM_EXP1 = 1 };         /* Philox stream ids */
@@ -33,6 +33,8 @@ typedef struct {
                               non-adjacent beads (lj_u = 0: none) */
     double hi_a;           /* bead radius a of the RPY hydrodynamic interaction
                               (Eqs. 2-3); 0: free draining */
+    double vwf_fa, vwf_fb, vwf_xmax;  /* ORA_SPRING_VWF A2 domains: FENE and harmonic
+                              spring constants, FENE maximum extension beyond r0 */
 } ora_chain;
 
 typedef struct {
@@ -65,6 +67,14 @@ int ora_spring_force(int spring, double H, double b, double r0, double s_min, co
 /* Lennard-Jones forces between non-adjacent beads (|i - j| >= 2) of a
  * conformation r [N][3], added to F [N][3]: U = u sum [(s/r)^12 - 2 (s/r)^6]. */
 void ora_lj_forces(const ora_chain* ch, const double* r, double* F);
+/* Force and signed tension of spring i of a chain under its law (for
+ * ORA_SPRING_VWF the law depends on the spring: even springs are A2 domains,
+ * odd springs disulfide bonds); returns 1 when a FENE floor applied. */
+int ora_chain_spring_force(const ora_chain* ch, int i, double s_min, const double Q[3], double F[3],
+                           double* tension);
+/* 1 if spring i takes part in the threshold and Bell criteria (every spring,
+ * except the disulfide bonds of ORA_SPRING_VWF chains). */
+int ora_spring_reacts(const ora_chain* ch, int i);
 /* Eqs. 2-3: the RPY diffusion tensor block D_ij / D_0 (D_0 = kT/(6 pi eta a),
  * the single-bead diffusivity) for the separation d = r_j - r_i of two
  * different beads, row-major 3x3. */

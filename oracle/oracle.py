@@ -41,7 +41,8 @@ class _Chain(ctypes.Structure):
                 ("H", ctypes.c_double), ("b", ctypes.c_double), ("rate", ctypes.c_double),
                 ("f_c", ctypes.c_double), ("k0", ctypes.c_double), ("dx", ctypes.c_double),
                 ("r0", ctypes.c_double), ("lj_u", ctypes.c_double), ("lj_sigma", ctypes.c_double),
-                ("hi_a", ctypes.c_double)]
+                ("hi_a", ctypes.c_double), ("vwf_fa", ctypes.c_double), ("vwf_fb", ctypes.c_double),
+                ("vwf_xmax", ctypes.c_double)]
 
 
 class _Problem(ctypes.Structure):
@@ -94,6 +95,8 @@ def lib():
         _lib.ora_rpy_matrix.argtypes = [ctypes.c_int, ctypes.c_double, f64p, f64p]
         _lib.ora_cholesky.argtypes = [ctypes.c_int, f64p, f64p]
         _lib.ora_cholesky.restype = ctypes.c_int
+        _lib.ora_chain_spring_force.argtypes = [P(_Chain), ctypes.c_int, ctypes.c_double, f64p, f64p, f64p]
+        _lib.ora_chain_spring_force.restype = ctypes.c_int
     return _lib
 
 
@@ -105,7 +108,9 @@ def _chain_struct(ch) -> _Chain:
     return _Chain(int(ch.n_beads), int(ch.n_replicas), int(ch.spring), int(ch.flow),
                   float(ch.H), float(ch.b), float(ch.rate), float(ch.f_c), float(ch.k0),
                   float(ch.dx), float(getattr(ch, "r0", 0.0)), float(getattr(ch, "lj_u", 0.0)),
-                  float(getattr(ch, "lj_sigma", 0.0)), float(getattr(ch, "hi_a", 0.0)))
+                  float(getattr(ch, "lj_sigma", 0.0)), float(getattr(ch, "hi_a", 0.0)),
+                  float(getattr(ch, "vwf_fa", 0.0)), float(getattr(ch, "vwf_fb", 0.0)),
+                  float(getattr(ch, "vwf_xmax", 0.0)))
 
 
 # ---------------------------------------------------------------------------
@@ -162,6 +167,17 @@ def spring_force(spring: int, H: float, b: float, Q, s_min: float = S_MIN_DEFAUL
     t = np.zeros(1)
     fl = lib().ora_spring_force(spring, H, b, r0, s_min, _p(q, ctypes.c_double),
                                 _p(F, ctypes.c_double), _p(t, ctypes.c_double))
+    return F, float(t[0]), int(fl)
+
+
+def chain_spring_force(chain, i: int, Q, s_min: float = S_MIN_DEFAULT):
+    """(force [3], signed tension, floored) of spring i of `chain` under its law."""
+    q = np.ascontiguousarray(Q, dtype=np.float64)
+    F = np.zeros(3)
+    t = np.zeros(1)
+    cs = _chain_struct(chain)
+    fl = lib().ora_chain_spring_force(ctypes.byref(cs), int(i), s_min, _p(q, ctypes.c_double),
+                                      _p(F, ctypes.c_double), _p(t, ctypes.c_double))
     return F, float(t[0]), int(fl)
 
 

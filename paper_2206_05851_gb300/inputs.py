@@ -27,6 +27,7 @@ import numpy as np
 SPRING_HOOKE = 0
 SPRING_FENE = 1
 SPRING_HARMONIC = 2     # harmonic with a rest length r0 (the paper's collapsed-chain springs)
+SPRING_VWF = 3          # vWF: A2 domains (FENE || harmonic) alternating with disulfide bonds
 
 FLOW_NONE = 0
 FLOW_SHEAR = 1
@@ -57,6 +58,9 @@ class Chain:
     lj_u: float = 0.0      # Lennard-Jones depth between non-adjacent beads (0: none)
     lj_sigma: float = 0.0  # Lennard-Jones zero-force (minimum) distance
     hi_a: float = 0.0      # bead radius of the RPY hydrodynamic interaction (0: free draining)
+    vwf_fa: float = 0.0    # SPRING_VWF A2 domain: FENE spring constant
+    vwf_fb: float = 0.0    # SPRING_VWF A2 domain: harmonic spring constant
+    vwf_xmax: float = 0.0  # SPRING_VWF A2 domain: FENE maximum extension beyond r0
 
 
 @dataclasses.dataclass
@@ -166,7 +170,7 @@ def initial_globule(rng: np.random.Generator, chain: Chain, tries: int = 48) -> 
 def initial_coil(rng: np.random.Generator, chain: Chain) -> np.ndarray:
     """Equilibrium random-walk conformation [N][3], centre of mass at 0
     (for harmonic chains, the compact walk of initial_globule)."""
-    if chain.spring == SPRING_HARMONIC:
+    if chain.spring in (SPRING_HARMONIC, SPRING_VWF):
         return initial_globule(rng, chain)
     q = sample_connectors(rng, chain.n_beads - 1, chain.spring, chain.H, chain.b)
     r = np.zeros((chain.n_beads, 3))
@@ -295,6 +299,52 @@ def collapsed_hi_128(n_steps: int = 1_500, n_chains: int = 128) -> Workload:
     return Workload("collapsed_hi_128x_n50_r50_shear30", chains, dt=COLLAPSED_DT,
                     window_steps=1500, n_steps=n_steps, seed=8, thr_mask=0, bell_mask=0,
                     init_seed=8)
+
+
+# The coarse-grained vWF chain of the supplementary material (Table S1), in the
+# units above (length a = 15 nm, energy kT, time tau / 4): a monomer is two
+# beads joined by an A2 domain (a FENE spring in parallel with a harmonic
+# spring), monomers are joined by disulfide bonds (harmonic springs), and
+# non-adjacent beads attract with the Lennard-Jones energy epsilon = 1 kT.
+VWF_A_NM = 15.0                 # bead radius a
+VWF_KT_PN_NM = 4.143            # kT at 300 K (= the Lennard-Jones epsilon of Table S1)
+VWF_ETA = 0.001                 # viscosity, pN us / nm^2
+VWF_TAU_S = 6.0 * math.pi * VWF_ETA * VWF_A_NM ** 3 / VWF_KT_PN_NM * 1e-6   # 6 pi eta a^3 / kT
+VWF_TIME_UNIT_S = VWF_TAU_S / COLLAPSED_TAU
+VWF_FORCE_UNIT_PN = VWF_KT_PN_NM / VWF_A_NM          # kT / a
+VWF_SPRING_UNIT = VWF_KT_PN_NM / VWF_A_NM ** 2       # kT / a^2 in pN / nm
+VWF_K0_PER_S = 7e-4             # zero-force A2 unfolding rate
+VWF_FU_PN = 1.1                 # force scale of the unfolding rate k0 exp(f / f_u)
+
+
+def vwf_chain(n_replicas: int, n_beads: int = 50, hi: bool = True) -> Chain:
+    """The vWF chain (Table S1): 25 monomers, 50 beads; disulfide bonds 7.5
+    pN/nm, A2 domains 0.116 pN/nm (FENE, maximum extension 51.46 nm beyond the
+    rest length 2a) in parallel with 5 pN/nm (harmonic); Lennard-Jones u = 1 kT
+    at 2a; Bell unfolding of the A2 domains, k = k0 exp(f / f_u); no flow; RPY
+    hydrodynamic interaction (bead radius a) unless hi is False."""
+    return Chain(n_beads=n_beads, n_replicas=n_replicas, spring=SPRING_VWF, flow=FLOW_NONE,
+                 H=7.5 / VWF_SPRING_UNIT, r0=2.0, lj_u=1.0, lj_sigma=2.0,
+                 vwf_fa=0.116 / VWF_SPRING_UNIT, vwf_fb=5.0 / VWF_SPRING_UNIT,
+                 vwf_xmax=51.46 / VWF_A_NM, k0=VWF_K0_PER_S * VWF_TIME_UNIT_S,
+                 dx=VWF_FORCE_UNIT_PN / VWF_FU_PN, hi_a=1.0 if hi else 0.0)
+
+
+def vwf_mftu_seconds(hazard_rate: float) -> float:
+    """Mean first time to unfold any A2 domain (Table 1's MFTU) for a chain
+    whose A2 domains unfold at the summed rate `hazard_rate` (per time unit):
+    1 / rate, in seconds."""
+    return VWF_TIME_UNIT_S / hazard_rate
+
+
+def vwf_64(n_steps: int = 1_500, n_chains: int = 64, n_replicas: int = 40,
+           window_steps: int = 1_500) -> Workload:
+    """64 vWF chains at rest (Table 1's set-up): 50 beads, N_R = 40,
+    dt = 1e-5 tau, evolution time S = 0.015 tau (1500 steps), Bell unfolding
+    on ISF, TSF and RSF."""
+    chains = [vwf_chain(n_replicas) for _ in range(n_chains)]
+    return Workload("vwf_64x_n50_r40_rest", chains, dt=COLLAPSED_DT, window_steps=window_steps,
+                    n_steps=n_steps, seed=10, thr_mask=0, bell_mask=CRIT_ALL, init_seed=10)
 
 
 def adjoint_256(n_steps: int = 20_000, n_chains: int = 256) -> Workload:
