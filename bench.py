@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-conformation", action="store_true")
     ap.add_argument("--no-collapsed", action="store_true")
     ap.add_argument("--no-hi", action="store_true")
+    ap.add_argument("--no-vwf", action="store_true")
+    ap.add_argument("--only-vwf", action="store_true",
+                    help="only the vWF line (Table 1 set-up)")
     ap.add_argument("--only-hi", action="store_true",
                     help="only the hydrodynamic-interaction line (Eqs. 1-3)")
     ap.add_argument("--hi-steps", type=int, default=1500,
@@ -447,6 +450,54 @@ def hi_line(sptr, n_chains=0, n_steps=1500, fp64_chains=8, fp64_steps=100):
     return out
 
 
+def vwf_line(sptr, n_chains=0, windows=4):
+    """The coarse-grained vWF chain at rest with hydrodynamic interaction
+    (Table 1's set-up: 50 beads, N_R = 40, S = 0.015 tau): float32 throughput,
+    and the mean first time to unfold any A2 domain (MFTU) that the ISF, TSF
+    and RSF hazards of the run predict, 1 / (summed A2 unfolding rate per
+    chain), in seconds; with the run's mean A2 force."""
+    import numpy as np
+    import torch
+    from paper_2206_05851_gb300 import bdra
+    from paper_2206_05851_gb300 import inputs as I
+
+    wl = I.vwf_64(**({"n_chains": n_chains} if n_chains else {}))
+    pos0 = I.initial_positions(wl)
+    S = wl.window_steps
+    n = windows * S
+    stream = torch.cuda.current_stream()
+    c = bdra.Context(wl.chains, wl.dt, S, wl.seed, torch.from_numpy(pos0).cuda(),
+                     precision=bdra.BD_PREC_FP32, max_windows=windows + 2, thr_mask=0,
+                     bell_mask=I.CRIT_ALL, stream=sptr)
+    c.step(10)                                           # warm-up
+    c.set_positions(torch.from_numpy(pos0).cuda(), 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    c.step(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    haz, _, _ = c.kinetics()
+    rsf = np.array([c.replica_average(w) for w in range(windows)])
+    tsf = np.array([c.time_average(w) for w in range(windows)])
+    c.close()
+    offs = I.spring_offsets(wl.chains)
+    a2 = np.concatenate([np.arange(offs[k], offs[k + 1], 2) for k in range(len(wl.chains))])
+    T = n * wl.dt
+    C = len(wl.chains)
+    mftu = {crit: I.vwf_mftu_seconds(haz[q, a2].sum() / (C * T))
+            for q, crit in enumerate(("ISF", "TSF", "RSF"))}
+    return {"workload": wl.name, "steps": n, "windows": windows, "window_steps": S,
+            "value": wl.bead_steps(n) / t, "unit": "bead-steps/s",
+            "precision": "FP32 integrate, FP64 reduce and hazards",
+            "mftu_s": mftu,
+            "mean_a2_force_pN": {"RSF": float(rsf[:, a2].mean() * I.VWF_FORCE_UNIT_PN),
+                                 "TSF": float(tsf[:, a2].mean() * I.VWF_FORCE_UNIT_PN)},
+            "paper_table1_context_s": {"ISF": 1.82e-5, "TSF S=0.015": 0.42, "RSF N_R=40 S=0.015": 13.22},
+            "start": "compact globules (not equilibrated), run of windows x S from step 0"}
+
+
 def adjoint_line(sptr, n_chains=0, n_steps=0):
     """Forward run plus reverse-mode adjoint of the differentiation workload
     (256 FENE chains, N=200, 32 replicas, 2e4 steps, parent checkpoints every
@@ -505,6 +556,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only_vwf:
+        import torch
+        from paper_2206_05851_gb300 import bdra, build as B
+        if not B.up_to_date():
+            B.build()
+        bdra.load()
+        print(json.dumps({"vwf": vwf_line(torch.cuda.current_stream().cuda_stream, args.chains)}),
+              flush=True)
         return
     if args.only_hi:
         import torch
@@ -721,6 +781,8 @@ def main():
             out["collapsed"] = collapsed_line(sptr)
         if not args.no_hi:
             out["hi"] = hi_line(sptr)
+        if not args.no_vwf:
+            out["vwf"] = vwf_line(sptr)
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(wl, pos0)
     if rank == 0:

@@ -64,7 +64,16 @@ typedef enum {
  * cohesion (lj_u > 0); the sampled spring force is the signed H (|Q| - r0)
  * of Eq. 4. Chains of this law run one replica per lane with the pair forces
  * of all their beads, and have no adjoint. */
-enum { BD_SPRING_HOOKE = 0, BD_SPRING_FENE = 1, BD_SPRING_HARMONIC = 2 };
+/* BD_SPRING_VWF: the coarse-grained vWF chain of the supplementary material
+ * (Table S1). Spring i joins beads i and i+1; even springs are A2 domains, a
+ * FENE spring in parallel with a harmonic spring, with the signed force
+ * vwf_fb x + vwf_fa x / (1 - x^2 / vwf_xmax^2) along the bond (x = |Q| - r0;
+ * the denominator floored at s_min and counted as an overextension); odd
+ * springs are disulfide bonds, H x. Only the A2 domains take part in the
+ * threshold and Bell criteria (their unfolding); the disulfide bonds never
+ * have events and their hazard stays 0. Runs on the collapsed-chain (and,
+ * with hi_a > 0, hydrodynamic-interaction) kernels; no adjoint. */
+enum { BD_SPRING_HOOKE = 0, BD_SPRING_FENE = 1, BD_SPRING_HARMONIC = 2, BD_SPRING_VWF = 3 };
 enum { BD_FLOW_NONE = 0, BD_FLOW_SHEAR = 1, BD_FLOW_UNIAXIAL = 2, BD_FLOW_PLANAR = 3 };
 /* BD_PREC_FP64: every step in float64. BD_PREC_FP32: Eq. 1 integrated in
  * float32; the cross-replica force reduction and the Bell hazard
@@ -90,10 +99,10 @@ typedef struct {
     double f_c;          /* threshold-rupture force (kT / l_H) */
     double k0;           /* Bell zero-force rate */
     double dx;           /* Bell distance to the transition state (l_H) */
-    double r0;           /* BD_SPRING_HARMONIC rest length (>= 0); unused otherwise */
+    double r0;           /* BD_SPRING_HARMONIC / BD_SPRING_VWF rest length (>= 0); unused otherwise */
     double lj_u;         /* Lennard-Jones depth between non-adjacent beads, U = lj_u
                             [(s/r)^12 - 2 (s/r)^6] (Sec. II); 0 = none; needs
-                            BD_SPRING_HARMONIC */
+                            BD_SPRING_HARMONIC or BD_SPRING_VWF */
     double lj_sigma;     /* its minimum distance s (> 0 when lj_u > 0) */
     double hi_a;         /* bead radius a of the Rotne-Prager-Yamakawa hydrodynamic
                             interaction (Eqs. 1-3), in the chain's length unit;
@@ -102,6 +111,9 @@ typedef struct {
                             BD_FLAG_CONFORMATION; every step of every slot
                             factors the 3N x 3N diffusion tensor (Cholesky) for
                             the correlated noise */
+    double vwf_fa;       /* BD_SPRING_VWF: FENE spring constant of the A2 domains (>= 0) */
+    double vwf_fb;       /* BD_SPRING_VWF: harmonic spring constant of the A2 domains (>= 0) */
+    double vwf_xmax;     /* BD_SPRING_VWF: FENE maximum extension beyond r0 (> 0) */
 } bd_chain_desc;
 
 typedef struct {

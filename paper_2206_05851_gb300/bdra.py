@@ -40,7 +40,8 @@ class bd_chain_desc(ctypes.Structure):
                 ("H", ctypes.c_double), ("b", ctypes.c_double), ("rate", ctypes.c_double),
                 ("f_c", ctypes.c_double), ("k0", ctypes.c_double), ("dx", ctypes.c_double),
                 ("r0", ctypes.c_double), ("lj_u", ctypes.c_double), ("lj_sigma", ctypes.c_double),
-                ("hi_a", ctypes.c_double)]
+                ("hi_a", ctypes.c_double), ("vwf_fa", ctypes.c_double), ("vwf_fb", ctypes.c_double),
+                ("vwf_xmax", ctypes.c_double)]
 
 
 class bd_config(ctypes.Structure):
@@ -162,7 +163,9 @@ def make_config(chains: Sequence, dt: float, window_steps: int, seed: int, preci
         bd_chain_desc(int(c.n_beads), int(c.n_replicas), int(c.spring), int(c.flow),
                       float(c.H), float(c.b), float(c.rate), float(c.f_c), float(c.k0),
                       float(c.dx), float(getattr(c, "r0", 0.0)), float(getattr(c, "lj_u", 0.0)),
-                      float(getattr(c, "lj_sigma", 0.0)), float(getattr(c, "hi_a", 0.0)))
+                      float(getattr(c, "lj_sigma", 0.0)), float(getattr(c, "hi_a", 0.0)),
+                      float(getattr(c, "vwf_fa", 0.0)), float(getattr(c, "vwf_fb", 0.0)),
+                      float(getattr(c, "vwf_xmax", 0.0)))
               for c in chains])
     cfg = bd_config(len(chains), int(window_steps), arr, float(dt), int(seed), int(precision),
                     int(flags), int(thr_mask), int(bell_mask), int(max_windows), float(s_min),

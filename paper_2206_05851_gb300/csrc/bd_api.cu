@@ -324,15 +324,20 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
             return fail(ctx, BD_E_INVALID, "chain %d: n_beads %d outside [2, 512]", c, d.n_beads);
         if (d.n_replicas < 1 || d.n_replicas > 4096)
             return fail(ctx, BD_E_INVALID, "chain %d: n_replicas %d outside [1, 4096]", c, d.n_replicas);
-        if (d.spring != BD_SPRING_HOOKE && d.spring != BD_SPRING_FENE && d.spring != BD_SPRING_HARMONIC)
+        const bool rest_law = d.spring == BD_SPRING_HARMONIC || d.spring == BD_SPRING_VWF;
+        if (d.spring != BD_SPRING_HOOKE && d.spring != BD_SPRING_FENE && !rest_law)
             return fail(ctx, BD_E_INVALID, "chain %d: unknown spring law %d", c, d.spring);
-        if (d.spring == BD_SPRING_HARMONIC && (!(d.r0 >= 0) || !std::isfinite(d.r0)))
+        if (rest_law && (!(d.r0 >= 0) || !std::isfinite(d.r0)))
             return fail(ctx, BD_E_INVALID, "chain %d: harmonic rest length must be >= 0", c);
         if (!(d.lj_u >= 0) || !std::isfinite(d.lj_u))
             return fail(ctx, BD_E_INVALID, "chain %d: lj_u must be >= 0", c);
-        if (d.lj_u > 0 && (d.spring != BD_SPRING_HARMONIC || !(d.lj_sigma > 0) || !std::isfinite(d.lj_sigma)))
+        if (d.spring == BD_SPRING_VWF &&
+            (!(d.vwf_fa >= 0) || !(d.vwf_fb >= 0) || !(d.vwf_xmax > 0) || !std::isfinite(d.vwf_fa) ||
+             !std::isfinite(d.vwf_fb) || !std::isfinite(d.vwf_xmax)))
+            return fail(ctx, BD_E_INVALID, "chain %d: vWF needs vwf_fa, vwf_fb >= 0 and vwf_xmax > 0", c);
+        if (d.lj_u > 0 && (!rest_law || !(d.lj_sigma > 0) || !std::isfinite(d.lj_sigma)))
             return fail(ctx, BD_E_INVALID, "chain %d: Lennard-Jones needs the harmonic law and lj_sigma > 0", c);
-        if (d.spring == BD_SPRING_HARMONIC && cfg->checkpoint_steps > 0)
+        if (rest_law && cfg->checkpoint_steps > 0)
             return fail(ctx, BD_E_INVALID, "chain %d: the adjoint supports Hooke and FENE chains only", c);
         if (!(d.hi_a >= 0) || !std::isfinite(d.hi_a))
             return fail(ctx, BD_E_INVALID, "chain %d: hi_a must be >= 0", c);
@@ -354,7 +359,8 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
     }
     if (cfg->lanes_hint) {
         for (int c = 0; c < cfg->n_chains; ++c)
-            if (cfg->chains[c].spring != BD_SPRING_HARMONIC && !(cfg->chains[c].hi_a > 0) &&
+            if (cfg->chains[c].spring != BD_SPRING_HARMONIC && cfg->chains[c].spring != BD_SPRING_VWF &&
+                !(cfg->chains[c].hi_a > 0) &&
                 (cfg->chains[c].n_beads + cfg->lanes_hint - 1) / cfg->lanes_hint > 32)
                 return fail(ctx, BD_E_INVALID, "lanes_hint %d too small for chain %d (N=%d)",
                             cfg->lanes_hint, c, cfg->chains[c].n_beads);
@@ -374,7 +380,7 @@ bd_status plan(bd_ctx* ctx)
     for (int c = 0; c < C; ++c) {
         const bd_chain_desc& d = ctx->chains[c];
         ChainDev& h = ctx->h_chains[c];
-        const bool collapsed = d.spring == BD_SPRING_HARMONIC;
+        const bool collapsed = d.spring == BD_SPRING_HARMONIC || d.spring == BD_SPRING_VWF;
         const bool hi = d.hi_a > 0;
         const VariantChoice vc = choose_variant(ctx, d.n_beads, d.n_replicas, collapsed, hi);
         if (!vc.variant)
@@ -395,6 +401,9 @@ bd_status plan(bd_ctx* ctx)
         }
         h.f_c = d.f_c; h.k0 = d.k0; h.dx = d.dx;
         h.r0 = collapsed ? d.r0 : 0.0;
+        h.vwf_fa = d.spring == BD_SPRING_VWF ? d.vwf_fa : 0.0;
+        h.vwf_fb = d.spring == BD_SPRING_VWF ? d.vwf_fb : 0.0;
+        h.vwf_ix2 = d.spring == BD_SPRING_VWF ? 1.0 / (d.vwf_xmax * d.vwf_xmax) : 0.0;
         h.lj_u = d.lj_u;
         h.lj_s2 = d.lj_sigma * d.lj_sigma;
         // float32 step constants, rounded as (float)(double expression);
@@ -819,7 +828,8 @@ bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost
         for (int c = 0; c < ctx->cfg.n_chains; ++c) {
             const int N = ctx->chains[c].n_beads, R = ctx->chains[c].n_replicas;
             const int G = (N + L - 1) / L;
-            if (G > 32 || variant_lj(v) != (ctx->chains[c].spring == BD_SPRING_HARMONIC) ||
+            const bool rest_law = ctx->chains[c].spring == BD_SPRING_HARMONIC || ctx->chains[c].spring == BD_SPRING_VWF;
+            if (G > 32 || variant_lj(v) != rest_law ||
                 ctx->chains[c].hi_a > 0) continue;
             const int per_warp = (variant_paired(v) ? 2 : 1) * (32 / G);
             const int groups = (R + per_warp - 1) / per_warp;

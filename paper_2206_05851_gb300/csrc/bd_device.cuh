@@ -31,6 +31,7 @@ struct ChainDev {
     double f_c, k0, dx;  // threshold force; Bell rate k0 exp(f dx)
     double r0, lj_u, lj_s2;  // harmonic rest length; Lennard-Jones depth and min distance^2
     double hi_a;         // RPY bead radius (hydrodynamic interaction); 0: free draining
+    double vwf_fa, vwf_fb, vwf_ix2;  // vWF A2 domains: FENE and harmonic constants, 1 / x_max^2
     // float32 step constants, rounded once on the host from the values
     // above (so the kernels never rebuild them from doubles): H, H/b, D dt,
     // sqrt(2 D dt) times the fast normals' sign, kappa_xx dt, kappa_yy dt,

@@ -340,8 +340,12 @@ __device__ __forceinline__ int hi_forces(HIShared<T, NTM>& sm, int N, const Step
                 const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];
                 const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
                 T c;
-                if (harmonic) {
-                    c = harmonic_coef<T, FAST>(qx, qy, qz, k.H, r0);
+                if (harmonic) {          // the laws with a rest length (harmonic, vWF)
+                    LJConst<T> kl;
+                    kl.load(ch);
+                    int fl = 0;
+                    c = rest_law_coef<T, FAST>(qx, qy, qz, (i & 1) == 0, k.H, kl, k.smin, fl);
+                    if (side == 0) floored += fl;
                 } else {
                     int fl = 0;
                     c = spring_coef<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin, fl);
@@ -519,7 +523,9 @@ hi_replica_kernel(const StepParams p)
     const ItemDev it = p.items[blockIdx.x];
     const ChainDev ch = p.chains[it.chain];
     const int N = ch.N, nb = N - 1, NT = (3 * N + 3) / 4;
-    const bool harmonic = ch.spring == BD_SPRING_HARMONIC;
+    const bool harmonic = ch.spring == BD_SPRING_HARMONIC || ch.spring == BD_SPRING_VWF;
+    LJConst<T> kl;
+    kl.load(ch);
     const bool lj = ch.lj_u > 0.0;
     const int kglob = it.rep_begin + 1;
     const uint32_t key = (p.flags & BD_FLAG_IDENTICAL_NOISE) ? 0u : (uint32_t)kglob;
@@ -550,7 +556,7 @@ hi_replica_kernel(const StepParams p)
                 const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
                 const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];
                 const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
-                const T f = harmonic ? harmonic_tension<T>(qx, qy, qz, k.H, (T)ch.r0)
+                const T f = harmonic ? rest_law_tension<T, FAST>(qx, qy, qz, (i & 1) == 0, k.H, kl, k.smin)
                                      : spring_tension<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin);
                 p.part_hist[(w % p.win_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb + i] = (double)f;
             }
@@ -575,7 +581,9 @@ hi_parent_kernel(const StepParams p)
     const int c = p.parent_items[p.parent_warps[blockIdx.x].first];
     const ChainDev ch = p.chains[c];
     const int N = ch.N, nb = N - 1, NT = (3 * N + 3) / 4;
-    const bool harmonic = ch.spring == BD_SPRING_HARMONIC;
+    const bool harmonic = ch.spring == BD_SPRING_HARMONIC || ch.spring == BD_SPRING_VWF;
+    LJConst<T> kl;
+    kl.load(ch);
     const bool lj = ch.lj_u > 0.0;
     StepConst<T, FAST> k;
     k.load(ch, p);
@@ -598,8 +606,9 @@ hi_parent_kernel(const StepParams p)
     const double k0dt = ch.k0 * p.dt, dxs = ch.dx;
     T tsf = mine ? (T)p.tsf_acc[m] : T(0);
     double haz = 0.0, rem = mine ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0;
-    bool thr_done = !mine || p.first_thr[CRIT_Q_ISF * M + m] >= 0;
-    bool bell_done = !mine || p.first_bell[CRIT_Q_ISF * M + m] >= 0;
+    const bool quiet = ch.spring == BD_SPRING_VWF && (i & 1);   // disulfide bonds do not unfold
+    bool thr_done = !mine || quiet || p.first_thr[CRIT_Q_ISF * M + m] >= 0;
+    bool bell_done = !mine || quiet || p.first_bell[CRIT_Q_ISF * M + m] >= 0;
     int floored = 0;
     int s_in = (int)(p.t0 % p.S);
     int64_t w = p.t0 / p.S;
@@ -618,14 +627,14 @@ hi_parent_kernel(const StepParams p)
             const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
             const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];
             const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
-            const T f = harmonic ? harmonic_tension<T>(qx, qy, qz, k.H, (T)ch.r0)
+            const T f = harmonic ? rest_law_tension<T, FAST>(qx, qy, qz, (i & 1) == 0, k.H, kl, k.smin)
                                  : spring_tension<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin);
             tsf += f;
             if (isf_thr && !thr_done && f >= fc) {
                 thr_done = true;
                 p.first_thr[CRIT_Q_ISF * M + m] = t + 1;
             }
-            if (isf_bell) {
+            if (isf_bell && !quiet) {
                 haz = fma(k0dt, exp(dxs * (double)f), haz);
                 if (!bell_done && haz >= rem) {
                     bell_done = true;

@@ -46,15 +46,54 @@ __device__ __forceinline__ T harmonic_tension(T qx, T qy, T qz, T H, T r0)
     return H * (sqrt(bond_q2(qx, qy, qz)) - r0);
 }
 
-// Per-chain constants of the pair forces, in the integration precision.
+// Per-chain constants of the pair forces and of the spring law with a rest
+// length, in the integration precision.
 template <typename T> struct LJConst {
     T r0, u12, s2;      // rest length; 12 u; s^2
+    T fa, fb, ix2;      // vWF A2 domains: FENE and harmonic constants, 1 / x_max^2
     int N;
+    bool vwf;           // BD_SPRING_VWF: even springs A2 domains, odd springs disulfide bonds
     __device__ __forceinline__ void load(const ChainDev& ch)
     {
         r0 = (T)ch.r0; u12 = (T)(12.0 * ch.lj_u); s2 = (T)ch.lj_s2; N = ch.N;
+        vwf = ch.spring == BD_SPRING_VWF;
+        fa = (T)ch.vwf_fa; fb = (T)ch.vwf_fb; ix2 = (T)ch.vwf_ix2;
     }
 };
+
+// The signed force along the bond of spring i (Eq. 4) for the laws with a
+// rest length: harmonic H x, x = |Q| - r0; for the vWF chain (supplementary
+// material, Table S1) even springs are A2 domains, f_B x + f_A x / s with
+// s = 1 - x^2 / x_max^2 floored at smin (counted in floored), odd springs
+// disulfide bonds H x.
+template <typename T, bool FAST>
+__device__ __forceinline__ T rest_law_force(T q, bool a2, T H, const LJConst<T>& kl, T smin, int& floored)
+{
+    const T x = q - kl.r0;
+    if (!kl.vwf || !a2) return H * x;
+    const T s = fma(-x * x, kl.ix2, T(1));
+    floored += s < smin;
+    return fma(kl.fb, x, Div<T, FAST>::div(kl.fa * x, fmax(s, smin)));
+}
+
+// The same as a coefficient c of F = c Q (zero for a bond of zero length).
+template <typename T, bool FAST>
+__device__ __forceinline__ T rest_law_coef(T qx, T qy, T qz, bool a2, T H, const LJConst<T>& kl, T smin,
+                                           int& floored)
+{
+    if (!kl.vwf) return harmonic_coef<T, FAST>(qx, qy, qz, H, kl.r0);
+    const T q2 = bond_q2(qx, qy, qz);
+    if (!(q2 > T(0))) return T(0);
+    const T iq = Rsqrt<T, FAST>::rsqrt(q2);
+    return rest_law_force<T, FAST>(q2 * iq, a2, H, kl, smin, floored) * iq;
+}
+
+template <typename T, bool FAST>
+__device__ __forceinline__ T rest_law_tension(T qx, T qy, T qz, bool a2, T H, const LJConst<T>& kl, T smin)
+{
+    int dummy = 0;
+    return rest_law_force<T, FAST>(sqrt(bond_q2(qx, qy, qz)), a2, H, kl, smin, dummy);
+}
 
 // Inclusive prefix sum over the lanes of a slot (seg: the lane's position in
 // its slot; lanes outside slots pass seg 0 and get junk they never use).
@@ -100,17 +139,20 @@ __device__ __forceinline__ T lj_coef(T dx, T dy, T dz, const LJConst<T>& kl)
 // only the first half of the ring takes. Beads of different lanes are
 // adjacent only across the boundary to the next lane (d = 1, no wrap).
 template <typename T, int L, bool FAST, bool TAB>
-__device__ __forceinline__ void step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L], const LaneCtx& lc,
-                                              const StepConst<T, FAST>& k, const LJConst<T>& kl,
-                                              bool in_slot, int seg, int G, int slot_base,
-                                              uint32_t step, const StepParams& p, const uint4* ptab)
+__device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L], const LaneCtx& lc,
+                                             const StepConst<T, FAST>& k, const LJConst<T>& kl,
+                                             bool in_slot, int seg, int G, int slot_base,
+                                             uint32_t step, const StepParams& p, const uint4* ptab)
 {
     const int lane = threadIdx.x & 31;
-    // spring forces of the lane's bonds
+    int floored = 0;
+    // spring forces of the lane's bonds (bond b joins beads b and b+1)
     T fx[L], fy[L], fz[L];
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-        const T c = harmonic_coef<T, FAST>(qx[j], qy[j], qz[j], k.H, kl.r0);
+        int fl = 0;
+        const T c = rest_law_coef<T, FAST>(qx[j], qy[j], qz[j], ((lc.bead0 + j) & 1) == 0, k.H, kl, k.smin, fl);
+        if (j < lc.nv) floored += fl;
         fx[j] = c * qx[j]; fy[j] = c * qy[j]; fz[j] = c * qz[j];
     }
     // bead positions (common offset dropped): exclusive prefix over the slot
@@ -215,6 +257,7 @@ __device__ __forceinline__ void step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L]
         fmx = fx[j]; fmy = fy[j]; fmz = fz[j];
         xcx = xnx; xcy = xny; xcz = xnz;
     }
+    return floored;
 }
 
 }  // namespace bdra

@@ -146,6 +146,7 @@ __global__ void window_criteria_kernel(const ChainDev* chains, const int32_t* sp
     if (m >= M) return;
     const ChainDev ch = chains[spring_chain[m]];
     const int64_t i = m - ch.spr_off;
+    if (ch.spring == BD_SPRING_VWF && (i & 1)) return;   // disulfide bonds do not unfold
     const double dT = (double)S * dt;
     for (int q = CRIT_Q_TSF; q <= CRIT_Q_RSF; ++q) {
         const bool thr = (thr_mask >> q) & 1, bell = (bell_mask >> q) & 1;

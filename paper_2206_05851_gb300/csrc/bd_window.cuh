@@ -129,7 +129,7 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
         if (s_in == 0)   // spawn: copy the halted parent (Sec. II)
             load_bonds<T, L>(qx, qy, qz, snap + ((int64_t)(w % p.win_ring) * p.M + ch.spr_off) * 3, lc);
         if constexpr (LJ)
-            step_bonds_lj<T, L, FAST, TAB>(qx, qy, qz, lc, k, kl, sw < P, sw < P ? lane - sw * G : 0, G,
+            floored += step_bonds_lj<T, L, FAST, TAB>(qx, qy, qz, lc, k, kl, sw < P, sw < P ? lane - sw * G : 0, G,
                                            sw < P ? sw * G : lane, (uint32_t)t, p, ptab);
         else
             floored += step_bonds<T, L, FAST, TAB>(qx, qy, qz, lc, k, (uint32_t)t, p, ptab);
@@ -142,7 +142,7 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
                     const int i = lc.bead0 + j;
                     if (i < nb)
                         wsm[sw * nb + i] =
-                            LJ ? harmonic_tension<T>(qx[j], qy[j], qz[j], k.H, kl.r0)
+                            LJ ? rest_law_tension<T, FAST>(qx[j], qy[j], qz[j], (i & 1) == 0, k.H, kl, k.smin)
                                : spring_tension<T, FAST>(qx[j], qy[j], qz[j], k.H, k.Hinvb, k.smin);
                 }
             }
@@ -215,7 +215,8 @@ parent_kernel(const StepParams p)
     // accumulated in float64 whatever the integration precision
     T tsf[L];
     double haz[L], rem[L];
-    uint32_t thr_done = 0, bell_done = 0;
+    // quiet: springs outside the criteria (the disulfide bonds of a vWF chain)
+    uint32_t thr_done = 0, bell_done = 0, quiet = 0;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
         const int i = lc.bead0 + j;
@@ -224,9 +225,12 @@ parent_kernel(const StepParams p)
         tsf[j] = v ? (T)p.tsf_acc[m] : T(0);
         haz[j] = 0.0;
         rem[j] = v ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0;
+        if (ch.spring == BD_SPRING_VWF && (i & 1)) quiet |= 1u << j;
         if (!v || p.first_thr[CRIT_Q_ISF * M + m] >= 0) thr_done |= 1u << j;
         if (!v || p.first_bell[CRIT_Q_ISF * M + m] >= 0) bell_done |= 1u << j;
     }
+    thr_done |= quiet;
+    bell_done |= quiet;
 
     int floored = 0;
     int s_in = (int)(p.t0 % p.S);
@@ -237,7 +241,7 @@ parent_kernel(const StepParams p)
         if (s_in == 0)   // the conformation the replicas of window w start from
             store_bonds<T, L>(qx, qy, qz, snap + ((w % p.win_ring) * M + ch.spr_off) * 3, lc);
         if constexpr (LJ)
-            step_bonds_lj<T, L, FAST, true>(qx, qy, qz, lc, k, kl, sw < P, sw < P ? lane - sw * G : 0, G,
+            floored += step_bonds_lj<T, L, FAST, true>(qx, qy, qz, lc, k, kl, sw < P, sw < P ? lane - sw * G : 0, G,
                                             sw < P ? sw * G : lane, (uint32_t)t, p, my_tab);
         else
             floored += step_bonds<T, L, FAST, true>(qx, qy, qz, lc, k, (uint32_t)t, p, my_tab);
@@ -246,14 +250,14 @@ parent_kernel(const StepParams p)
             for (int j = 0; j < L; ++j) {
                 const int i = lc.bead0 + j;
                 if (i < nb) {
-                    const T f = LJ ? harmonic_tension<T>(qx[j], qy[j], qz[j], k.H, kl.r0)
+                    const T f = LJ ? rest_law_tension<T, FAST>(qx[j], qy[j], qz[j], (i & 1) == 0, k.H, kl, k.smin)
                                    : spring_tension<T, FAST>(qx[j], qy[j], qz[j], k.H, k.Hinvb, k.smin);
                     tsf[j] += f;
                     if (isf_thr && !(thr_done & (1u << j)) && f >= fc) {
                         thr_done |= 1u << j;
                         p.first_thr[CRIT_Q_ISF * M + ch.spr_off + i] = t + 1;
                     }
-                    if (isf_bell) {
+                    if (isf_bell && !(quiet & (1u << j))) {
                         haz[j] = fma(k0dt, exp(dxs * (double)f), haz[j]);
                         if (!(bell_done & (1u << j)) && haz[j] >= rem[j]) {
                             bell_done |= 1u << j;
