@@ -439,7 +439,7 @@ def hi_line(sptr, n_chains=0, n_steps=1500, fp64_chains=8, fp64_steps=100):
     cores = os.cpu_count() or 1
     sub = wl.chains[:cores]
     psub = pos0[:sum(c.n_beads for c in sub)]
-    n_cpu = 200          # about 10 s of oracle work on 16 cores
+    n_cpu = 600          # about 10 s of oracle work on 16 cores
     tc = time.perf_counter()
     O.run(sub, wl.dt, S, n_cpu, wl.seed, psub, thr_mask=0, bell_mask=0, n_threads=cores,
           want_replicas=False, chain_ids=list(range(len(sub))))
@@ -784,7 +784,7 @@ def main():
         if not args.no_vwf:
             out["vwf"] = vwf_line(sptr)
         if not args.no_cpu:
-            out["cpu_baseline"] = cpu_baseline(wl, pos0)
+            out["cpu_baseline"] = cpu_baseline(wl, pos0, n_steps=20_000)   # about 10 s on 16 cores
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
