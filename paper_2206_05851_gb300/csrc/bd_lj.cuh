@@ -126,6 +126,83 @@ __device__ __forceinline__ T lj_coef(T dx, T dy, T dz, const LJConst<T>& kl)
     return fma(-x6, x6, x6) * (kl.u12 * ir2);
 }
 
+// The ring part of the pair forces (d = 1 .. G/2, as in step_bonds_lj) with
+// the float32 arithmetic of two of the lane's beads at a time in packed
+// two-wide instructions (FFMA2 / FMUL2): the lane's beads 2jp and 2jp+1
+// against one partner bead; an odd last bead goes alone. Each half rounds
+// as the scalar form; only the order of the partner reaction's sum differs.
+template <int L>
+__device__ __forceinline__ void lj_ring_pairs_packed(const float (&px)[L], const float (&py)[L], const float (&pz)[L],
+                                                     float (&gx)[L], float (&gy)[L], float (&gz)[L],
+                                                     const LJConst<float>& kl, bool in_slot, int seg, int G,
+                                                     int slot_base)
+{
+    constexpr int LP = L / 2;
+    const int lane = threadIdx.x & 31;
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 s2v = make_float2(kl.s2, kl.s2), u12v = make_float2(kl.u12, kl.u12);
+    float2 gx2[LP], gy2[LP], gz2[LP];
+#pragma unroll
+    for (int jp = 0; jp < LP; ++jp) gx2[jp] = gy2[jp] = gz2[jp] = make_float2(0.0f, 0.0f);
+    const int half = G >> 1;
+#pragma unroll 1
+    for (int d = 1; d <= half; ++d) {
+        int pf = seg + d;
+        if (pf >= G) pf -= G;
+        int pb = seg - d;
+        if (pb < 0) pb += G;
+        const int srcf = in_slot ? slot_base + pf : lane;    // < 32: slots fit the warp
+        const int srcb = in_slot ? slot_base + pb : lane;
+        const bool skip = 2 * d == G && seg >= half;
+        const bool bonded = d == 1 && seg + 1 < G;          // my last bead - its first bead
+#pragma unroll
+        for (int kk = 0; kk < L; ++kk) {
+            float bx = __shfl_sync(0xffffffffu, px[kk], srcf);
+            const float by = __shfl_sync(0xffffffffu, py[kk], srcf);
+            const float bz = __shfl_sync(0xffffffffu, pz[kk], srcf);
+            if (skip) bx = -lj_far<float>() * 1000.0f;
+            const float2 Bx = make_float2(bx, bx), By = make_float2(by, by), Bz = make_float2(bz, bz);
+            float2 hx2 = make_float2(0.0f, 0.0f), hy2 = hx2, hz2 = hx2;
+#pragma unroll
+            for (int jp = 0; jp < LP; ++jp) {
+                const float2 dx = __ffma2_rn(make_float2(px[2 * jp], px[2 * jp + 1]), m1, Bx);
+                const float2 dy = __ffma2_rn(make_float2(py[2 * jp], py[2 * jp + 1]), m1, By);
+                const float2 dz = __ffma2_rn(make_float2(pz[2 * jp], pz[2 * jp + 1]), m1, Bz);
+                const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                const float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+                const float2 x2 = __fmul2_rn(s2v, ir2);
+                const float2 x6 = __fmul2_rn(__fmul2_rn(x2, x2), x2);
+                float2 c = __fmul2_rn(__ffma2_rn(make_float2(-x6.x, -x6.y), x6, x6), __fmul2_rn(u12v, ir2));
+                if (kk == 0 && 2 * jp + 1 == L - 1 && bonded) c.y = 0.0f;
+                gx2[jp] = __ffma2_rn(c, dx, gx2[jp]);
+                gy2[jp] = __ffma2_rn(c, dy, gy2[jp]);
+                gz2[jp] = __ffma2_rn(c, dz, gz2[jp]);
+                hx2 = __ffma2_rn(c, dx, hx2);
+                hy2 = __ffma2_rn(c, dy, hy2);
+                hz2 = __ffma2_rn(c, dz, hz2);
+            }
+            float hx = hx2.x + hx2.y, hy = hy2.x + hy2.y, hz = hz2.x + hz2.y;
+            if constexpr (L & 1) {
+                const float dx = bx - px[L - 1], dy = by - py[L - 1], dz = bz - pz[L - 1];
+                float c = lj_coef<float, true>(dx, dy, dz, kl);
+                if (kk == 0 && bonded) c = 0.0f;
+                gx[L - 1] = fmaf(c, dx, gx[L - 1]); gy[L - 1] = fmaf(c, dy, gy[L - 1]); gz[L - 1] = fmaf(c, dz, gz[L - 1]);
+                hx = fmaf(c, dx, hx); hy = fmaf(c, dy, hy); hz = fmaf(c, dz, hz);
+            }
+            // the reaction on bead kk of this lane, from the lane d places back
+            gx[kk] -= __shfl_sync(0xffffffffu, hx, srcb);
+            gy[kk] -= __shfl_sync(0xffffffffu, hy, srcb);
+            gz[kk] -= __shfl_sync(0xffffffffu, hz, srcb);
+        }
+    }
+#pragma unroll
+    for (int jp = 0; jp < LP; ++jp) {
+        gx[2 * jp] += gx2[jp].x; gx[2 * jp + 1] += gx2[jp].y;
+        gy[2 * jp] += gy2[jp].x; gy[2 * jp + 1] += gy2[jp].y;
+        gz[2 * jp] += gz2[jp].x; gz[2 * jp + 1] += gz2[jp].y;
+    }
+}
+
 // One Eq. 1 step of the lane's L bonds of a collapsed chain. in_slot: the
 // lane belongs to a slot, slot_base its first lane, seg its position in it, G
 // the lanes per slot. Every lane of the warp calls it.
@@ -186,6 +263,9 @@ __device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L],
         }
     // pairs with the lanes d places round the ring
     const int half = G >> 1;
+    if constexpr (sizeof(T) == 4 && FAST && L >= 2) {
+        lj_ring_pairs_packed<L>(px, py, pz, gx, gy, gz, kl, in_slot, seg, G, slot_base);
+    } else {
 #pragma unroll 1
     for (int d = 1; d <= half; ++d) {
         int pf = seg + d;
@@ -216,6 +296,7 @@ __device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L],
             gy[kk] -= __shfl_sync(0xffffffffu, hy, srcb);
             gz[kk] -= __shfl_sync(0xffffffffu, hz, srcb);
         }
+    }
     }
     // halo: spring force of the previous lane's last bond and the next lane's
     // first bond; the next lane's first-bead pair force and noise

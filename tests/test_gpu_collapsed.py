@@ -163,3 +163,34 @@ def test_collapsed_conformation_diagnostics(oracle_run, prec):
     want = O.conformation(chains, DT, S, sum(STEPS), 7, pos0)
     for got, w in zip(g["conf"], want):
         assert np.abs(got - w).max() <= TOL[prec] * np.abs(w).max()
+
+
+def test_full_size_workloads_on_sampled_chains():
+    # the bench's launch configurations (1024 collapsed chains; 128 with
+    # hydrodynamic interaction; 64 vWF chains), float32, 300 steps; sampled
+    # chains re-run alone by the oracle with their own chain ids in the noise
+    # counter
+    import torch
+    for wl, sample in ((I.collapsed_1024(n_steps=300), [0, 611, 1023]),
+                       (I.collapsed_hi_128(n_steps=300), [5, 127]),
+                       (I.vwf_64(n_steps=300), [0, 63])):
+        S = 100
+        pos0 = I.initial_positions(wl)
+        ctx = bdra.Context(wl.chains, wl.dt, S, wl.seed, pos0, precision=bdra.BD_PREC_FP32,
+                           max_windows=4, thr_mask=wl.thr_mask, bell_mask=wl.bell_mask,
+                           stream=torch.cuda.current_stream().cuda_stream)
+        ctx.step(300)
+        pos = ctx.positions(False)
+        rsf = np.array([ctx.replica_average(w) for w in range(3)])
+        ctx.close()
+        boff = I.bead_offsets(wl.chains)
+        soff = I.spring_offsets(wl.chains)
+        sub = [wl.chains[c] for c in sample]
+        sub_pos = np.concatenate([pos0[boff[c]:boff[c + 1]] for c in sample])
+        r = O.run(sub, wl.dt, S, 300, wl.seed, sub_pos, thr_mask=wl.thr_mask, bell_mask=wl.bell_mask,
+                  n_threads=8, chain_ids=sample)
+        got = np.concatenate([pos[boff[c]:boff[c + 1]] for c in sample])
+        nb = [c.n_beads for c in sub]
+        assert _rel(got, O.com_frame(r["pos"], nb), nb) <= 1e-4, wl.name
+        rs = np.concatenate([rsf[:, soff[c]:soff[c + 1]] for c in sample], axis=1)
+        assert np.abs(rs - r["rsf"]).max() / np.abs(r["rsf"]).max() <= 1e-4, wl.name
