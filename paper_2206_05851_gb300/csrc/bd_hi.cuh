@@ -38,7 +38,7 @@ constexpr int kHIThreads = 256;
 constexpr int kHIMaxBeads = 64;
 constexpr int kHISmallBeads = 50;
 // Tile rows of the largest tensor of each kernel: chains of up to
-// kHISmallBeads beads (three tiles per thread, two CTAs per SM) and of up to
+// kHISmallBeads beads (three tiles per thread, three CTAs per SM in float32) and of up to
 // kHIMaxBeads (five tiles per thread).
 constexpr int kHINTSmall = (3 * kHISmallBeads + 3) / 4;
 constexpr int kHINTMax = (3 * kHIMaxBeads + 3) / 4;
@@ -513,7 +513,7 @@ __device__ __forceinline__ int hi_step(HIShared<T, NTM>& sm, HITiles<T, MAXT>& t
 // p.items. Spawn from the window-start snapshot, S steps, one force sample per
 // spring at the window end into the replica's partial row (its group).
 template <typename T, bool FAST, int NTM>
-__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 2 : 1)
+__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 3 : 1)
 hi_replica_kernel(const StepParams p)
 {
     constexpr int MAXT = HIDims<NTM>::maxt;
@@ -571,7 +571,7 @@ hi_replica_kernel(const StepParams p)
 // p.parent_items). Window-start snapshots, then per step the update and the
 // instantaneous force of every spring: TSF sums and the ISF criteria.
 template <typename T, bool FAST, int NTM>
-__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 2 : 1)
+__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 3 : 1)
 hi_parent_kernel(const StepParams p)
 {
     constexpr int MAXT = HIDims<NTM>::maxt;

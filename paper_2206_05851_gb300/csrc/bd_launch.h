@@ -29,7 +29,7 @@ static const int kNumVariantsF64 = 10;
 constexpr int kVariantCodes = kHIBase + 2;
 
 // kHIBase: chains of up to kHISmallBeadsHost beads (fewer tiles per thread,
-// two CTAs per SM); kHIBase + 1: up to kHIMaxBeadsHost.
+// three CTAs per SM in float32); kHIBase + 1: up to kHIMaxBeadsHost.
 inline bool variant_hi(int v) { return v >= kHIBase; }
 inline bool variant_lj(int v) { return v >= kLJBase && v < kHIBase; }
 inline bool variant_paired(int v) { return v >= kPairBase && v < kLJBase; }
