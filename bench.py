@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-vwf", action="store_true")
     ap.add_argument("--only-vwf", action="store_true",
                     help="only the vWF line (Table 1 set-up)")
+    ap.add_argument("--only-rest", action="store_true",
+                    help="only the collapsed chain at rest (mean middle-spring force, RSF spread)")
     ap.add_argument("--only-hi", action="store_true",
                     help="only the hydrodynamic-interaction line (Eqs. 1-3)")
     ap.add_argument("--hi-steps", type=int, default=1500,
@@ -471,6 +473,8 @@ def vwf_line(sptr, n_chains=0, windows=4):
                      bell_mask=I.CRIT_ALL, stream=sptr)
     c.step(10)                                           # warm-up
     c.set_positions(torch.from_numpy(pos0).cuda(), 0)
+    bdra.bd_enable_timing(c.ptr, True)
+    bdra.bd_kernel_times(c.ptr)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -478,6 +482,7 @@ def vwf_line(sptr, n_chains=0, windows=4):
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
+    (par_ms, rep_ms), (_, rep_n) = bdra.bd_kernel_times(c.ptr)
     haz, _, _ = c.kinetics()
     rsf = np.array([c.replica_average(w) for w in range(windows)])
     tsf = np.array([c.time_average(w) for w in range(windows)])
@@ -488,14 +493,72 @@ def vwf_line(sptr, n_chains=0, windows=4):
     C = len(wl.chains)
     mftu = {crit: I.vwf_mftu_seconds(haz[q, a2].sum() / (C * T))
             for q, crit in enumerate(("ISF", "TSF", "RSF"))}
+    N = wl.chains[0].n_beads
+    slot_steps = sum(ch.n_replicas for ch in wl.chains) * n
+    achieved = hi_flops_per_slot_step(N) * slot_steps / (rep_ms / 1e3) / 1e12
+    peak = 2.0 * SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    sub = wl.chains[:cores]
+    psub = pos0[:sum(ch.n_beads for ch in sub)]
+    n_cpu = 300
+    tc = time.perf_counter()
+    O.run(sub, wl.dt, S, n_cpu, wl.seed, psub, thr_mask=0, bell_mask=I.CRIT_ALL, n_threads=cores,
+          want_replicas=False, chain_ids=list(range(len(sub))))
+    tc = time.perf_counter() - tc
+    bs = sum(ch.n_replicas * ch.n_beads for ch in sub) * n_cpu
     return {"workload": wl.name, "steps": n, "windows": windows, "window_steps": S,
             "value": wl.bead_steps(n) / t, "unit": "bead-steps/s",
+            "roofline": {"bound": "alu (float32 FMA)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "hydrodynamic-interaction replica kernel (float32)",
+                         "share_of_step": rep_ms / (t * 1e3), "launches": rep_n},
+            "parent_kernel_share": par_ms / (t * 1e3),
+            "cpu_baseline": {"value": bs / tc, "unit": "bead-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {len(sub)} chains, {n_cpu} steps ({tc:.1f} s wall, FP64)"},
             "precision": "FP32 integrate, FP64 reduce and hazards",
             "mftu_s": mftu,
             "mean_a2_force_pN": {"RSF": float(rsf[:, a2].mean() * I.VWF_FORCE_UNIT_PN),
                                  "TSF": float(tsf[:, a2].mean() * I.VWF_FORCE_UNIT_PN)},
             "paper_table1_context_s": {"ISF": 1.82e-5, "TSF S=0.015": 0.42, "RSF N_R=40 S=0.015": 13.22},
             "start": "compact globules (not equilibrated), run of windows x S from step 0"}
+
+
+def rest_line(sptr, n_chains=128, windows=6, skip=2):
+    """The paper's collapsed chain with hydrodynamic interaction at rest
+    (Fig. 1-2 set-up: N = 50, S = 0.02 tau = 2000 steps): the mean force of
+    the middle (25th) spring and the spread of its RSF for N_R = 10 and 50,
+    over chains and windows after the first `skip` windows (context for the
+    paper's 0.55 and 6.7 / 3.3; float32)."""
+    import numpy as np
+    import torch
+    from paper_2206_05851_gb300 import bdra
+    from paper_2206_05851_gb300 import inputs as I
+
+    S = 2000
+    out = {"chains": n_chains, "window_steps": S, "windows": windows, "skipped_windows": skip}
+    for R in (10, 50):
+        chains = []
+        for _ in range(n_chains):
+            ch = I.collapsed_chain(R, rate=0.0)
+            ch.hi_a = 1.0
+            chains.append(ch)
+        wl = I.custom(chains, I.COLLAPSED_DT, S, windows * S)
+        pos0 = I.initial_positions(wl, seed=12)
+        c = bdra.Context(chains, wl.dt, S, 12, torch.from_numpy(pos0).cuda(), precision=bdra.BD_PREC_FP32,
+                         max_windows=windows + 1, stream=sptr)
+        t0 = time.perf_counter()
+        c.step(windows * S)
+        rsf = np.array([c.replica_average(w) for w in range(windows)])
+        tsf = np.array([c.time_average(w) for w in range(windows)])
+        t = time.perf_counter() - t0
+        c.close()
+        mid = I.spring_offsets(chains)[:-1] + 24
+        r = rsf[skip:, mid]
+        out[f"N_R={R}"] = {"rsf_mean": float(r.mean()), "rsf_std": float(r.std()),
+                           "tsf_mean": float(tsf[skip:, mid].mean()), "seconds": t}
+    out["paper_context"] = {"mean_force_spring25": 0.55, "rsf_std_S0.02": {"N_R=10": 6.7, "N_R=50": 3.3}}
+    return out
 
 
 def adjoint_line(sptr, n_chains=0, n_steps=0):
@@ -556,6 +619,14 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only_rest:
+        import torch
+        from paper_2206_05851_gb300 import bdra, build as B
+        if not B.up_to_date():
+            B.build()
+        bdra.load()
+        print(json.dumps({"rest": rest_line(torch.cuda.current_stream().cuda_stream)}), flush=True)
         return
     if args.only_vwf:
         import torch
