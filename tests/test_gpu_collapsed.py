@@ -165,6 +165,23 @@ def test_collapsed_conformation_diagnostics(oracle_run, prec):
         assert np.abs(got - w).max() <= TOL[prec] * np.abs(w).max()
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_longest_collapsed_chain(prec):
+    # the maximum bead count (512: 16 springs per lane, 32 lanes per slot)
+    ch = [_collapsed(512, 3, I.FLOW_SHEAR, 7.5)]
+    pos0 = I.initial_positions(I.custom(ch, DT, 10, 30), seed=8)
+    r = O.run(ch, DT, 10, 30, 3, pos0, thr_mask=7, bell_mask=7, n_threads=4)
+    import torch
+    ctx = bdra.Context(ch, DT, 10, 3, pos0, precision=prec, max_windows=4, thr_mask=7, bell_mask=7,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    ctx.step(30)
+    pos = ctx.positions(False)
+    rsf = np.array([ctx.replica_average(w) for w in range(3)])
+    ctx.close()
+    assert _rel(pos, O.com_frame(r["pos"], [512]), [512]) <= TOL[prec]
+    assert np.abs(rsf - r["rsf"]).max() / np.abs(r["rsf"]).max() <= TOL[prec]
+
+
 def test_full_size_workloads_on_sampled_chains():
     # the bench's launch configurations (1024 collapsed chains; 128 with
     # hydrodynamic interaction; 64 vWF chains), float32, 300 steps; sampled

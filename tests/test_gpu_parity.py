@@ -304,9 +304,11 @@ def test_edge_cases(prec):
     compare_profiles(g, r, TOL[prec])
 
 
-def test_many_replica_groups():
-    # 1000 replicas of a short chain: several CTAs per chain, one parent copy
-    ch = [I.Chain(n_beads=24, n_replicas=1000, spring=I.SPRING_FENE, flow=I.FLOW_PLANAR,
+@pytest.mark.parametrize("R", [1000, 4096])
+def test_many_replica_groups(R):
+    # 1000 replicas and the maximum 4096 of a short chain: many work items per
+    # chain, one parent copy
+    ch = [I.Chain(n_beads=24, n_replicas=R, spring=I.SPRING_FENE, flow=I.FLOW_PLANAR,
                   b=50.0, rate=0.05)]
     pos0 = I.initial_positions(I.custom(ch, 1e-3, 10, 30), seed=4)
     for prec in PRECS:
