@@ -106,11 +106,10 @@ typedef struct {
     double lj_sigma;     /* its minimum distance s (> 0 when lj_u > 0) */
     double hi_a;         /* bead radius a of the Rotne-Prager-Yamakawa hydrodynamic
                             interaction (Eqs. 1-3), in the chain's length unit;
-                            0 = free draining. With hi_a > 0: n_beads <= 64, no
-                            adjoint (checkpoint_steps 0) and no
-                            BD_FLAG_CONFORMATION; every step of every slot
-                            factors the 3N x 3N diffusion tensor (Cholesky) for
-                            the correlated noise */
+                            0 = free draining. With hi_a > 0: n_beads <= 64 and
+                            no adjoint (checkpoint_steps 0); every step of every
+                            slot factors the 3N x 3N diffusion tensor (Cholesky)
+                            for the correlated noise */
     double vwf_fa;       /* BD_SPRING_VWF: FENE spring constant of the A2 domains (>= 0) */
     double vwf_fb;       /* BD_SPRING_VWF: harmonic spring constant of the A2 domains (>= 0) */
     double vwf_xmax;     /* BD_SPRING_VWF: FENE maximum extension beyond r0 (> 0) */

@@ -347,8 +347,6 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
                             c, kHIMaxBeadsHost);
             if (cfg->checkpoint_steps > 0)
                 return fail(ctx, BD_E_INVALID, "chain %d: no adjoint with hydrodynamic interaction", c);
-            if (cfg->flags & BD_FLAG_CONFORMATION)
-                return fail(ctx, BD_E_INVALID, "chain %d: no Eq. 5 diagnostics with hydrodynamic interaction", c);
         }
         if (d.flow < BD_FLOW_NONE || d.flow > BD_FLOW_PLANAR)
             return fail(ctx, BD_E_INVALID, "chain %d: unknown flow %d", c, d.flow);

@@ -509,6 +509,45 @@ __device__ __forceinline__ int hi_step(HIShared<T, NTM>& sm, HITiles<T, MAXT>& t
     return floored;
 }
 
+// Eq. 5 at a window end (BD_FLAG_CONFORMATION): the replica's COM-frame
+// positions against those of the halted parent it was formed from (the
+// window-start snapshot, rebuilt from its bonds in sm.frc, which the next
+// step overwrites anyway): per bead and component |dr|, their bead means
+// (D-bar of this replica) and, for the chain's first replica, R_GZ of the
+// parent. The per-bead values go to the replica's own partial row (its
+// group), which the window fold averages over the replicas.
+template <typename T, int NTM>
+__device__ __forceinline__ void hi_conformation(HIShared<T, NTM>& sm, const ItemDev& it, const ChainDev& ch,
+                                                const StepParams& p, int64_t w, int kglob)
+{
+    const int N = ch.N;
+    const T* pc = reinterpret_cast<const T*>(p.snap) + ((w % p.win_ring) * p.M + ch.spr_off) * 3;
+    if (threadIdx.x < 3) {
+        const int c = threadIdx.x;
+        T x = T(0), s = T(0);
+        sm.frc[c] = x;
+        for (int i = 0; i + 1 < N; ++i) {
+            x += pc[3 * i + c];
+            sm.frc[3 * (i + 1) + c] = x;
+            s += x;
+        }
+        const T cm = s / (T)N;
+        T dsum = T(0), z2 = T(0);
+        for (int b = 0; b < N; ++b) {
+            const T pp = sm.frc[3 * b + c] - cm;
+            sm.frc[3 * b + c] = pp;
+            dsum += fabs(sm.pos[3 * b + c] - pp);
+            z2 = fma(pp, pp, z2);
+        }
+        p.dbar[((int64_t)w * p.n_rep + ch.rep_off + kglob - 1) * 3 + c] = (double)dsum / N;
+        if (c == 2 && it.group == 0) p.rgz[(int64_t)w * p.n_chains + it.chain] = sqrt((double)z2 / N);
+    }
+    __syncthreads();
+    double* out = p.dbead_part + ((w % p.win_ring) * p.bpart_stride + ch.bpart_off + (int64_t)it.group * N) * 3;
+    for (int e = threadIdx.x; e < 3 * N; e += blockDim.x) out[e] = (double)fabs(sm.pos[e] - sm.frc[e]);
+    __syncthreads();
+}
+
 // Replicas: one CTA per work item (one replica), the items of this launch in
 // p.items. Spawn from the window-start snapshot, S steps, one force sample per
 // spring at the window end into the replica's partial row (its group).
@@ -560,6 +599,7 @@ hi_replica_kernel(const StepParams p)
                                      : spring_tension<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin);
                 p.part_hist[(w % p.win_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb + i] = (double)f;
             }
+            if (p.flags & BD_FLAG_CONFORMATION) hi_conformation(sm, it, ch, p, w, kglob);
             ++w;
         }
     }

@@ -150,3 +150,23 @@ def test_identical_noise_replicas_equal_parent(prec):
             np.testing.assert_array_equal(rep[o + k * ch.n_beads:o + (k + 1) * ch.n_beads], p)
         o += ch.n_replicas * ch.n_beads
         po += ch.n_beads
+
+
+@pytest.mark.parametrize("prec", [bdra.BD_PREC_FP64, bdra.BD_PREC_FP32])
+def test_conformation_diagnostics_with_hi(prec):
+    # Eq. 5 for the paper's set-up (collapsed chains with hydrodynamic
+    # interaction in shear): D-bar per replica, per-bead D over replicas, R_GZ
+    import torch
+    chains = [_collapsed(50, 4), _collapsed(12, 3, I.FLOW_NONE, 0.0), _collapsed(12, 2, hi=0.0)]
+    dt, S, n = 4e-5, 50, 150
+    pos0 = I.initial_positions(I.custom(chains, dt, S, n), seed=17)
+    ctx = bdra.Context(chains, dt, S, 9, pos0, precision=prec, max_windows=n // S,
+                       flags=bdra.BD_FLAG_CONFORMATION, stream=torch.cuda.current_stream().cuda_stream)
+    ctx.step(70)
+    ctx.step(80)
+    got = [ctx.conformation(w) for w in range(n // S)]
+    ctx.close()
+    want = O.conformation(chains, dt, S, n, 9, pos0)
+    for k in range(3):
+        g = np.array([x[k] for x in got])
+        assert np.abs(g - want[k]).max() <= TOL[prec] * np.abs(want[k]).max(), k
