@@ -557,7 +557,27 @@ def rest_line(sptr, n_chains=128, windows=6, skip=2):
         r = rsf[skip:, mid]
         out[f"N_R={R}"] = {"rsf_mean": float(r.mean()), "rsf_std": float(r.std()),
                            "tsf_mean": float(tsf[skip:, mid].mean()), "seconds": t}
-    out["paper_context"] = {"mean_force_spring25": 0.55, "rsf_std_S0.02": {"N_R=10": 6.7, "N_R=50": 3.3}}
+    # Fig. 6 set-up: shear at 30 / tau, N_R = 50, S = 0.015 tau; replica-vs-parent D-bar (Eq. 5)
+    chains = []
+    for _ in range(64):
+        ch = I.collapsed_chain(50)
+        ch.hi_a = 1.0
+        chains.append(ch)
+    S6, w6 = 1500, 3
+    wl = I.custom(chains, I.COLLAPSED_DT, S6, w6 * S6)
+    pos0 = I.initial_positions(wl, seed=13)
+    c = bdra.Context(chains, wl.dt, S6, 13, torch.from_numpy(pos0).cuda(), precision=bdra.BD_PREC_FP32,
+                     max_windows=w6, flags=bdra.BD_FLAG_CONFORMATION, stream=sptr)
+    c.step(w6 * S6)
+    conf = [c.conformation(w) for w in range(1, w6)]
+    c.close()
+    dbar = np.concatenate([x[0] for x in conf])          # [replicas x windows][3]
+    rgz = np.concatenate([x[2] for x in conf])
+    out["shear30_eq5"] = {"windows_used": w6 - 1, "dbar_max": dbar.max(axis=0).tolist(),
+                          "dbar_mean": dbar.mean(axis=0).tolist(), "rgz_mean": float(rgz.mean()),
+                          "rgz_max": float(rgz.max())}
+    out["paper_context"] = {"mean_force_spring25": 0.55, "rsf_std_S0.02": {"N_R=10": 6.7, "N_R=50": 3.3},
+                            "max_dbar_x_S0.015": 0.65}
     return out
 
 
