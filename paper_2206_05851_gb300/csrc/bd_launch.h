@@ -15,13 +15,14 @@ static const int kNumTiles = 6;
 // with 4 or 7 springs (larger pair tiles spill at 128 registers);
 // float64: one replica per lane with 2..16 springs; both precisions: the
 // collapsed-chain step (harmonic springs, Lennard-Jones pair forces) with 2,
-// 4, 7 or 16 springs per lane. (bd_variants.h lists the same.)
+// 4, 5, 7 or 16 springs per lane (5: the paper's 50-bead chain fills ten
+// lanes exactly). (bd_variants.h lists the same.)
 static const int kVariantsF32[] = {4, 7, 10, 13, 16, kPairBase + 4, kPairBase + 7,
-                                   kLJBase + 2, kLJBase + 4, kLJBase + 7, kLJBase + 16};
-static const int kNumVariantsF32 = 11;
+                                   kLJBase + 2, kLJBase + 4, kLJBase + 5, kLJBase + 7, kLJBase + 16};
+static const int kNumVariantsF32 = 12;
 static const int kVariantsF64[] = {2, 4, 7, 10, 13, 16,
-                                   kLJBase + 2, kLJBase + 4, kLJBase + 7, kLJBase + 16};
-static const int kNumVariantsF64 = 10;
+                                   kLJBase + 2, kLJBase + 4, kLJBase + 5, kLJBase + 7, kLJBase + 16};
+static const int kNumVariantsF64 = 11;
 
 // Variant codes are below kVariantCodes (cost tables are indexed by code).
 // kHIBase (hydrodynamic interaction, one CTA per replica) is not a tile

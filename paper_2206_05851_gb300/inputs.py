@@ -134,35 +134,52 @@ def sample_connectors(rng: np.random.Generator, n: int, spring: int,
 
 
 def initial_globule(rng: np.random.Generator, chain: Chain, tries: int = 48) -> np.ndarray:
-    """Compact conformation [N][3] of a harmonic chain, centre of mass at 0.
+    """Compact conformation [N][3] of a harmonic or vWF chain, centre of mass at 0.
 
     A walk with bonds of the rest length r0 (1 if r0 = 0): each new bead is
     the candidate, among `tries` random directions, nearest the beads placed
     so far (their centroid) that keeps at least 0.95 lj_sigma from every
-    earlier non-adjacent bead; if none does, the one farthest from them. With
-    lj_sigma = 0 the walk is freely jointed (first candidate taken). This
-    stands in for an equilibrated globule: the Lennard-Jones contacts start
-    near their minimum, none overlapping.
+    earlier non-adjacent bead. When no direction does (the walk has buried
+    its end), up to 16 more sets of directions are drawn; if still none, the
+    walk steps back four beads and regrows them taking the valid direction
+    farthest from the centroid. With lj_sigma = 0 the walk is freely jointed
+    (first candidate taken). This stands in for an equilibrated globule: the
+    Lennard-Jones contacts start near their minimum, none overlapping.
     """
     N = chain.n_beads
     r0 = chain.r0 if chain.r0 > 0 else 1.0
     dmin = 0.95 * chain.lj_sigma
     r = np.zeros((N, 3))
-    for i in range(1, N):
-        u = rng.normal(size=(tries, 3))
-        u /= np.linalg.norm(u, axis=1, keepdims=True)
-        cand = r[i - 1] + r0 * u
+    escape = 0          # beads still to grow away from the centroid
+    backtracks = 0
+    i = 1
+    while i < N:
         if dmin <= 0 or i < 2:
-            r[i] = cand[0]
+            u = rng.normal(size=3)
+            r[i] = r[i - 1] + r0 * u / np.linalg.norm(u)
+            i += 1
             continue
-        d = np.linalg.norm(cand[:, None, :] - r[None, :i - 1, :], axis=2).min(axis=1)
-        ok = d >= dmin
-        if ok.any():
-            cen = r[:i].mean(axis=0)
-            dist = np.linalg.norm(cand - cen, axis=1)
-            r[i] = cand[np.flatnonzero(ok)[np.argmin(dist[ok])]]
-        else:
-            r[i] = cand[np.argmax(d)]
+        chosen = None
+        for _ in range(17):
+            u = rng.normal(size=(tries, 3))
+            u /= np.linalg.norm(u, axis=1, keepdims=True)
+            cand = r[i - 1] + r0 * u
+            d = np.linalg.norm(cand[:, None, :] - r[None, :i - 1, :], axis=2).min(axis=1)
+            ok = np.flatnonzero(d >= dmin)
+            if ok.size:
+                dist = np.linalg.norm(cand[ok] - r[:i].mean(axis=0), axis=1)
+                chosen = cand[ok[np.argmax(dist) if escape else np.argmin(dist)]]
+                break
+        if chosen is None and backtracks < 1000:
+            backtracks += 1
+            i = max(2, i - 4)
+            escape = 4
+            continue
+        if chosen is None:                       # give up: the farthest candidate
+            chosen = cand[np.argmax(d)]
+        r[i] = chosen
+        escape = max(0, escape - 1)
+        i += 1
     r -= r.mean(axis=0)
     return r
 

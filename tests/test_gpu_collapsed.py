@@ -8,7 +8,7 @@ gamma-dot / tau is gamma-dot / 4).
   positions, RSF and TSF profiles within 1e-10 (FP64) / 1e-4 (FP32) relative;
   FP64 first-event steps (signed Eq. 4 force against the threshold, Bell
   hazards) equal.
-- Every collapsed-chain tile (2, 4, 7, 16 springs per lane), ragged slots,
+- Every collapsed-chain tile (2, 4, 5, 7, 16 springs per lane), ragged slots,
   the two-bead chain (no pair), a harmonic chain without cohesion, and a
   FENE chain in the same batch.
 - Identical noise: the replicas follow the parent (their positions come from
@@ -45,6 +45,7 @@ def _collapsed(N, R, flow=I.FLOW_NONE, rate=0.0, u=1.0):
 def _chains():
     return [_collapsed(50, 16, I.FLOW_SHEAR, 7.5),           # the paper's chain at gamma-dot 30
             _collapsed(12, 5),
+            _collapsed(48, 9, I.FLOW_PLANAR, 1.0),                # five springs per lane
             _collapsed(3, 3, I.FLOW_UNIAXIAL, 2.0),
             _collapsed(120, 6, I.FLOW_PLANAR, 1.0),
             _collapsed(300, 3, I.FLOW_SHEAR, 7.5),

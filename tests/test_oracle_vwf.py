@@ -89,7 +89,7 @@ def test_small_extension_stiffness_and_floor():
 
 def test_only_a2_domains_unfold():
     N = 9
-    chains = [_chain(N, R=4, k0=50.0, dx=0.2) for _ in range(3)]
+    chains = [_chain(N, R=4, k0=500.0, dx=0.2) for _ in range(3)]
     pos0 = I.initial_positions(I.custom(chains, 1e-4, 20, 400), seed=3)
     out = O.run(chains, 1e-4, 20, 400, seed=2, pos0=pos0, thr_mask=0, bell_mask=7, n_threads=4)
     fb = out["first_bell"].reshape(3, len(chains), N - 1)
