@@ -96,6 +96,27 @@ def test_bad_config_rejected_without_device(lib, kw):
     assert st == bdra.BD_E_INVALID and ptr is None
 
 
+COLLAPSED = I.Chain(n_beads=12, n_replicas=3, spring=I.SPRING_HARMONIC, H=400.0, r0=2.0, lj_u=1.0,
+                    lj_sigma=2.0)
+
+
+@pytest.mark.parametrize("chain,kw", [
+    (dict(r0=-1.0), {}), (dict(lj_sigma=0.0), {}), (dict(lj_u=-1.0), {}),
+    (dict(spring=I.SPRING_FENE, lj_u=1.0), {}),                  # pair forces need a rest-length law
+    (dict(hi_a=-0.5), {}), (dict(hi_a=1.0, n_beads=65), {}),     # RPY limits
+    (dict(hi_a=1.0), dict(checkpoint_steps=10)),                  # no adjoint with RPY
+    ({}, dict(checkpoint_steps=10)),                             # no adjoint for collapsed chains
+    (dict(spring=I.SPRING_VWF, vwf_fa=6.3, vwf_fb=271.5, vwf_xmax=0.0), {}),
+    (dict(spring=I.SPRING_VWF, vwf_fa=-1.0, vwf_fb=271.5, vwf_xmax=3.4), {}),
+    (dict(spring=I.SPRING_VWF, vwf_fa=6.3, vwf_fb=math.inf, vwf_xmax=3.4), {})])
+def test_bad_model_parameters_rejected_without_device(lib, chain, kw):
+    import dataclasses
+    ch = dataclasses.replace(COLLAPSED, **chain)
+    cfg, _keep = _cfg([ch], **kw)
+    st, ptr = _create(cfg, np.zeros((ch.n_beads, 3)))
+    assert st == bdra.BD_E_INVALID and ptr is None
+
+
 def test_null_arguments_rejected(lib):
     cfg, _keep = _cfg([GOOD])
     st, _ = _create(cfg, None)
