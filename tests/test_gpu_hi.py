@@ -170,3 +170,20 @@ def test_conformation_diagnostics_with_hi(prec):
     for k in range(3):
         g = np.array([x[k] for x in got])
         assert np.abs(g - want[k]).max() <= TOL[prec] * np.abs(want[k]).max(), k
+
+
+def test_windows_across_chunks():
+    # 75 windows of 2 steps: the step graph runs chunks of at most 64 windows,
+    # so window snapshots and partial rows cross a chunk boundary (ring rows)
+    chains = [_collapsed(12, 3), _collapsed(12, 2, hi=0.0),
+              I.Chain(n_beads=9, n_replicas=3, spring=I.SPRING_FENE, flow=I.FLOW_SHEAR, b=50.0, rate=1.0,
+                      hi_a=0.5)]
+    dt, S, steps = 4e-5, 2, [61, 89]
+    pos0 = I.initial_positions(I.custom(chains, dt, S, sum(steps)), seed=21)
+    g = _gpu(chains, dt, S, steps, pos0, bdra.BD_PREC_FP64, thr=0, bell=0)
+    r = O.run(chains, dt, S, sum(steps), 9, pos0, thr_mask=0, bell_mask=0, n_threads=4)
+    assert g["rsf"].shape[0] == 75
+    for key in ("rsf", "tsf"):
+        assert np.abs(g[key] - r[key]).max() <= 1e-10 * np.abs(r[key]).max(), key
+    nb = [c.n_beads for c in chains]
+    assert _rel(g["pos"], O.com_frame(r["pos"], nb), nb) <= 1e-10
