@@ -10,9 +10,14 @@
  * What it follows:
  *   - Eq. 1 (Sec. II): Euler-Maruyama update of every bead, taken literally in
  *     the laboratory frame, with the free-draining diffusion tensor of Eq. 2
- *     (D_ij = delta_ij kT/zeta I; no hydrodynamic interaction).
- *   - Eq. 4 (Sec. II): the instantaneous spring force (ISF) of a spring,
- *     here the magnitude of the spring-law force.
+ *     (D_ij = delta_ij kT/zeta I) or, for chains with a bead radius, the RPY
+ *     tensor of Eqs. 2-3 and noise from its lower Cholesky factor.
+ *   - Sec. II's collapsed chain: harmonic springs with a rest length and
+ *     Lennard-Jones cohesion between non-adjacent beads; the supplement's
+ *     coarse-grained vWF chain (A2 domains and disulfide bonds, Table S1).
+ *   - Eq. 4 (Sec. II): the instantaneous spring force (ISF) of a spring: the
+ *     magnitude of the FENE / Hooke force, the signed force along the bond
+ *     for the laws with a rest length.
  *   - Sec. II, "Computing ISF, TSF and RSF": TSF is the mean of per-step
  *     samples over the sampling time S; RSF halts the parent, forms N_R
  *     replicas of it, each with its own noise stream, evolves them for S,
