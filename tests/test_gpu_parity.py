@@ -397,6 +397,59 @@ def test_full_size_sampled_parity():
     assert np.abs(rs - r["rsf"]).max() / np.abs(r["rsf"]).max() <= 1e-4
 
 
+def _sampled(wl, g, pos0, sample, n, autotuned=False):
+    boff, soff = I.bead_offsets(wl.chains), I.spring_offsets(wl.chains)
+    sub = [wl.chains[c] for c in sample]
+    sub_pos = np.concatenate([pos0[boff[c]:boff[c + 1]] for c in sample])
+    r = ora_run(sub, wl.dt, wl.window_steps, n, wl.seed, sub_pos, thr=wl.thr_mask,
+                bell=wl.bell_mask, chain_ids=sample)
+    nb = [c.n_beads for c in sub]
+    got = np.concatenate([g["pos"][boff[c]:boff[c + 1]] for c in sample])
+    assert rel_err_chains(got, O.com_frame(r["pos"], nb), nb) <= 1e-4
+    cols = np.concatenate([np.arange(soff[c], soff[c + 1]) for c in sample])
+    for key in ("rsf", "tsf"):
+        assert np.abs(g[key][:, cols] - r[key]).max() / np.abs(r[key]).max() <= 1e-4, key
+    # Bell hazards in log space (R14), zero where the oracle's are zero
+    lam = g["haz"][:, cols]
+    pos = r["lam"] > 0
+    assert (np.abs(np.log(lam[pos]) - np.log(r["lam"][pos])) <= 1e-4 * np.abs(np.log(r["lam"][pos])) + 2e-3).all()
+    np.testing.assert_array_equal(lam[~pos], r["lam"][~pos])
+    return r
+
+
+def test_full_size_uneven_batch_sampled_parity():
+    # C3 launch configuration: 4096 chains of 20..500 beads and 8..128
+    # replicas, shear and elongation, one persistent launch per step variant,
+    # shapes picked by the autotuner; FP32, 200 steps; sampled chains of
+    # different shapes re-run alone by the oracle
+    wl = I.uneven_4096(n_steps=200)
+    pos0 = I.initial_positions(wl)
+    ctx = bdra.Context(wl.chains, wl.dt, wl.window_steps, wl.seed, pos0, precision=bdra.BD_PREC_FP32,
+                       max_windows=3, thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=_stream())
+    ctx.autotune(probe_steps=8)
+    ctx.step(200)
+    g = dict(pos=ctx.positions(False),
+             rsf=np.array([ctx.replica_average(w) for w in range(2)]),
+             tsf=np.array([ctx.time_average(w) for w in range(2)]))
+    g["haz"], _, _ = ctx.kinetics()
+    ctx.close()
+    sizes = [(c.n_beads, c.n_replicas) for c in wl.chains]
+    sample = [int(np.argmax([n for n, _ in sizes])), int(np.argmin([n for n, _ in sizes])),
+              int(np.argmax([r for _, r in sizes])), 1234, 4095]
+    _sampled(wl, g, pos0, sample, 200)
+
+
+def test_full_size_bell_workload_sampled_parity():
+    # C4 launch configuration: 16384 chains, N = 50, 32 replicas, start-up
+    # uniaxial Wi = 10, Bell and threshold criteria on ISF, TSF and RSF; FP32,
+    # 1000 steps; sampled chains against the oracle
+    wl = I.bell_16384(n_steps=1000)
+    pos0 = I.initial_positions(wl)
+    g = gpu_run(wl.chains, wl.dt, wl.window_steps, [1000], wl.seed, pos0, bdra.BD_PREC_FP32,
+                thr=wl.thr_mask, bell=wl.bell_mask, want_all=False)
+    _sampled(wl, g, pos0, [0, 8191, 16383], 1000)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_autotune_changes_shapes_not_results(prec):
     # the autotuner times every step variant and re-plans; results must not move
