@@ -44,10 +44,12 @@ METRIC = ("bead-steps/s (chains×replicas×beads×steps) FP32 batched vs FP64 pl
 ALGO_OPS_PER_BEAD_STEP = 67.5
 PHILOX_ROUNDS_PER_BEAD_STEP = 8
 # Minimal lane-instructions per non-adjacent Lennard-Jones pair of the
-# collapsed-chain model, the pair evaluated once: separation 3, r^2 3,
-# reciprocal 1, (s/r)^2 1, ^6 2, 12 u (x^6 - x^12) / r^2 3, force on both
-# beads 6.
-LJ_PAIR_OPS = 19
+# collapsed-chain model, the pair evaluated once, in units of the LJ length s
+# (x = s/r): separation 3, r^2 3, reciprocal 1, x^4, x^6, x^8 3, x^8 - x^14 1,
+# force on both beads 6; per bead, scaling its position to and its pair force
+# from those units, 6.
+LJ_PAIR_OPS = 17
+LJ_BEAD_OPS = 6
 SMS, LANES_PER_CLK_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -281,10 +283,11 @@ def conformation_line(wl, pos0, sptr, n_steps=2000):
 
 def lj_ops_per_bead_step(n_beads):
     """Minimal lane-instructions per bead-step of the collapsed-chain step: the
-    noise and bond update of the free-draining step (ALGO_OPS_PER_BEAD_STEP)
-    plus LJ_PAIR_OPS per non-adjacent pair, each pair counted once (Newton's
-    third law): (N-1)(N-2)/2 pairs per chain-step."""
-    return ALGO_OPS_PER_BEAD_STEP + LJ_PAIR_OPS * (n_beads - 1) * (n_beads - 2) / (2.0 * n_beads)
+    noise and bond update of the free-draining step (ALGO_OPS_PER_BEAD_STEP),
+    LJ_BEAD_OPS, and LJ_PAIR_OPS per non-adjacent pair, each pair counted once
+    (Newton's third law): (N-1)(N-2)/2 pairs per chain-step."""
+    return (ALGO_OPS_PER_BEAD_STEP + LJ_BEAD_OPS
+            + LJ_PAIR_OPS * (n_beads - 1) * (n_beads - 2) / (2.0 * n_beads))
 
 
 def collapsed_line(sptr, n_chains=0, n_steps=3000, fp64_chains=64):

@@ -50,12 +50,15 @@ __device__ __forceinline__ T harmonic_tension(T qx, T qy, T qz, T H, T r0)
 // length, in the integration precision.
 template <typename T> struct LJConst {
     T r0, u12, s2;      // rest length; 12 u; s^2
+    T isig, k12;        // 1 / s and 12 u / s (the pair forces in units of s)
     T fa, fb, ix2;      // vWF A2 domains: FENE and harmonic constants, 1 / x_max^2
     int N;
     bool vwf;           // BD_SPRING_VWF: even springs A2 domains, odd springs disulfide bonds
     __device__ __forceinline__ void load(const ChainDev& ch)
     {
         r0 = (T)ch.r0; u12 = (T)(12.0 * ch.lj_u); s2 = (T)ch.lj_s2; N = ch.N;
+        const double sig = ch.lj_s2 > 0.0 ? sqrt(ch.lj_s2) : 1.0;
+        isig = (T)(1.0 / sig); k12 = (T)(12.0 * ch.lj_u / sig);
         vwf = ch.spring == BD_SPRING_VWF;
         fa = (T)ch.vwf_fa; fb = (T)ch.vwf_fb; ix2 = (T)ch.vwf_ix2;
     }
@@ -126,6 +129,20 @@ __device__ __forceinline__ T lj_coef(T dx, T dy, T dz, const LJConst<T>& kl)
     return fma(-x6, x6, x6) * (kl.u12 * ir2);
 }
 
+// The same force for a separation d' = d / s in units of s: with x = 1/|d'|,
+// c' = x^8 - x^14 and the force on a is (12 u / s) c' d' (kl.k12, applied
+// once per bead after the pair sums). One multiply a pair fewer than the
+// unscaled form.
+template <typename T, bool FAST>
+__device__ __forceinline__ T lj_coef_scaled(T dx, T dy, T dz)
+{
+    const T ir2 = Rsqrt<T, FAST>::rcp(fma(dx, dx, fma(dy, dy, dz * dz)));
+    const T x4 = ir2 * ir2;
+    const T x6 = x4 * ir2;
+    const T x8 = x4 * x4;
+    return fma(-x8, x6, x8);
+}
+
 // The ring part of the pair forces (d = 1 .. G/2, as in step_bonds_lj) with
 // the float32 arithmetic of two of the lane's beads at a time in packed
 // two-wide instructions (FFMA2 / FMUL2): the lane's beads 2jp and 2jp+1
@@ -140,7 +157,7 @@ __device__ __forceinline__ void lj_ring_pairs_packed(const float (&px)[L], const
     constexpr int LP = L / 2;
     const int lane = threadIdx.x & 31;
     const float2 m1 = make_float2(-1.0f, -1.0f);
-    const float2 s2v = make_float2(kl.s2, kl.s2), u12v = make_float2(kl.u12, kl.u12);
+
     float2 gx2[LP], gy2[LP], gz2[LP];
 #pragma unroll
     for (int jp = 0; jp < LP; ++jp) gx2[jp] = gy2[jp] = gz2[jp] = make_float2(0.0f, 0.0f);
@@ -170,9 +187,10 @@ __device__ __forceinline__ void lj_ring_pairs_packed(const float (&px)[L], const
                 const float2 dz = __ffma2_rn(make_float2(pz[2 * jp], pz[2 * jp + 1]), m1, Bz);
                 const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
                 const float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
-                const float2 x2 = __fmul2_rn(s2v, ir2);
-                const float2 x6 = __fmul2_rn(__fmul2_rn(x2, x2), x2);
-                float2 c = __fmul2_rn(__ffma2_rn(make_float2(-x6.x, -x6.y), x6, x6), __fmul2_rn(u12v, ir2));
+                const float2 x4 = __fmul2_rn(ir2, ir2);
+                const float2 x6 = __fmul2_rn(x4, ir2);
+                const float2 x8 = __fmul2_rn(x4, x4);
+                float2 c = __ffma2_rn(make_float2(-x8.x, -x8.y), x6, x8);
                 if (kk == 0 && 2 * jp + 1 == L - 1 && bonded) c.y = 0.0f;
                 gx2[jp] = __ffma2_rn(c, dx, gx2[jp]);
                 gy2[jp] = __ffma2_rn(c, dy, gy2[jp]);
@@ -184,7 +202,7 @@ __device__ __forceinline__ void lj_ring_pairs_packed(const float (&px)[L], const
             float hx = hx2.x + hx2.y, hy = hy2.x + hy2.y, hz = hz2.x + hz2.y;
             if constexpr (L & 1) {
                 const float dx = bx - px[L - 1], dy = by - py[L - 1], dz = bz - pz[L - 1];
-                float c = lj_coef<float, true>(dx, dy, dz, kl);
+                float c = lj_coef_scaled<float, true>(dx, dy, dz);
                 if (kk == 0 && bonded) c = 0.0f;
                 gx[L - 1] = fmaf(c, dx, gx[L - 1]); gy[L - 1] = fmaf(c, dy, gy[L - 1]); gz[L - 1] = fmaf(c, dz, gz[L - 1]);
                 hx = fmaf(c, dx, hx); hy = fmaf(c, dy, hy); hz = fmaf(c, dz, hz);
@@ -242,9 +260,9 @@ __device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L],
 #pragma unroll
         for (int j = 0; j < L; ++j) {
             const bool real = lc.bead0 + j < kl.N;
-            px[j] = real ? x : lj_far<T>() * (T)(lc.bead0 + j + 1);
-            py[j] = real ? y : T(0);
-            pz[j] = real ? z : T(0);
+            px[j] = real ? x * kl.isig : lj_far<T>() * (T)(lc.bead0 + j + 1);   // in units of s
+            py[j] = real ? y * kl.isig : T(0);
+            pz[j] = real ? z * kl.isig : T(0);
             x += qx[j]; y += qy[j]; z += qz[j];
         }
     }
@@ -257,7 +275,7 @@ __device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L],
 #pragma unroll
         for (int kk = j + 2; kk < L; ++kk) {
             const T dx = px[kk] - px[j], dy = py[kk] - py[j], dz = pz[kk] - pz[j];
-            const T c = lj_coef<T, FAST>(dx, dy, dz, kl);
+            const T c = lj_coef_scaled<T, FAST>(dx, dy, dz);
             gx[j] = fma(c, dx, gx[j]); gy[j] = fma(c, dy, gy[j]); gz[j] = fma(c, dz, gz[j]);
             gx[kk] = fma(-c, dx, gx[kk]); gy[kk] = fma(-c, dy, gy[kk]); gz[kk] = fma(-c, dz, gz[kk]);
         }
@@ -286,7 +304,7 @@ __device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L],
 #pragma unroll
             for (int j = 0; j < L; ++j) {
                 const T dx = bx - px[j], dy = by - py[j], dz = bz - pz[j];
-                T c = lj_coef<T, FAST>(dx, dy, dz, kl);
+                T c = lj_coef_scaled<T, FAST>(dx, dy, dz);
                 if (kk == 0 && j == L - 1 && bonded) c = T(0);
                 gx[j] = fma(c, dx, gx[j]); gy[j] = fma(c, dy, gy[j]); gz[j] = fma(c, dz, gz[j]);
                 hx = fma(c, dx, hx); hy = fma(c, dy, hy); hz = fma(c, dz, hz);
@@ -298,6 +316,8 @@ __device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L],
         }
     }
     }
+#pragma unroll
+    for (int j = 0; j < L; ++j) { gx[j] *= kl.k12; gy[j] *= kl.k12; gz[j] *= kl.k12; }
     // halo: spring force of the previous lane's last bond and the next lane's
     // first bond; the next lane's first-bead pair force and noise
     T fmx = shfl(fx[L - 1], lc.src_prev), fmy = shfl(fy[L - 1], lc.src_prev), fmz = shfl(fz[L - 1], lc.src_prev);
