@@ -419,14 +419,15 @@ def hi_line(sptr, n_chains=0, n_steps=1500, fp64_chains=8, fp64_steps=100):
     N = wl.chains[0].n_beads
     slot_steps = sum(c.n_replicas for c in wl.chains) * n_steps
     achieved = hi_flops_per_slot_step(N) * slot_steps / (rep_ms / 1e3) / 1e12
-    peak = 2.0 * SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    derived = 2.0 * SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak = bdra.bd_probe_fp32_fma(sptr) / 1e12           # measured, outside the timed region
     out["roofline"] = {"bound": "alu (float32 FMA)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                        "frac": achieved / peak, "traffic": None,
                        "kernel": "hydrodynamic-interaction replica kernel (float32, one CTA per replica)",
                        "avg_launch_ms": rep_ms / max(rep_n, 1), "launches": rep_n,
                        "share_of_step": rep_ms / (t * 1e3), "flops_per_slot_step": hi_flops_per_slot_step(N),
-                       "peak_basis": f"{SMS} SMs x {LANES_PER_CLK_PER_SM} FMA/clk x 2 x {SM_MAX_MHZ:.0f} MHz "
-                                     "(derived, not measured)"}
+                       "peak_basis": "measured by bd_probe_fp32_fma on this GPU after the timed region",
+                       "peak_derived": derived, "frac_of_derived": achieved / derived}
     out["parent_kernel_share"] = par_ms / (t * 1e3)
     # FP64 and the FP32 force error on a few chains (a short window so that
     # RSF samples exist)
@@ -499,7 +500,7 @@ def vwf_line(sptr, n_chains=0, windows=4):
     N = wl.chains[0].n_beads
     slot_steps = sum(ch.n_replicas for ch in wl.chains) * n
     achieved = hi_flops_per_slot_step(N) * slot_steps / (rep_ms / 1e3) / 1e12
-    peak = 2.0 * SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak = bdra.bd_probe_fp32_fma(sptr) / 1e12           # measured, outside the timed region
     from oracle import oracle as O
     cores = os.cpu_count() or 1
     sub = wl.chains[:cores]
@@ -515,7 +516,8 @@ def vwf_line(sptr, n_chains=0, windows=4):
             "roofline": {"bound": "alu (float32 FMA)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "hydrodynamic-interaction replica kernel (float32)",
-                         "share_of_step": rep_ms / (t * 1e3), "launches": rep_n},
+                         "share_of_step": rep_ms / (t * 1e3), "launches": rep_n,
+                         "peak_basis": "measured by bd_probe_fp32_fma"},
             "parent_kernel_share": par_ms / (t * 1e3),
             "cpu_baseline": {"value": bs / tc, "unit": "bead-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"first {len(sub)} chains, {n_cpu} steps ({tc:.1f} s wall, FP64)"},

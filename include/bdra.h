@@ -317,6 +317,15 @@ bd_status bd_philox_normals(uint64_t seed, int64_t n, const uint32_t* ctr, int32
  * NULL pointer, BD_E_OOM / BD_E_CUDA on device failures. */
 bd_status bd_probe_philox_rounds(void* stream, double* rounds_per_s);
 
+/* Measured float32 FMA throughput of the current device (no counterpart in
+ * the paper: the denominator of the float32 roofline of the RPY Cholesky
+ * kernels): independent fused multiply-add chains at full occupancy, no
+ * memory traffic (about 5 ms). *flops_per_s (host) receives floating-point
+ * operations per second, an FMA counted as two. Runs on `stream`;
+ * synchronises. BD_E_INVALID for a NULL pointer, BD_E_OOM / BD_E_CUDA on
+ * device failures. */
+bd_status bd_probe_fp32_fma(void* stream, double* flops_per_s);
+
 /* Largest n_springs bd_compact_events_noalloc accepts (its fixed scratch
  * holds one count per 256 springs: 32 KiB of device memory). */
 #define BD_NOALLOC_MAX_SPRINGS (1 << 20)

@@ -104,6 +104,7 @@ def load() -> ctypes.CDLL:
         "bd_kernel_times": ([vp, P(ctypes.c_double), P(ctypes.c_int64)], st),
         "bd_adjoint": ([vp, vp, vp, vp], st),
         "bd_probe_philox_rounds": ([vp, P(ctypes.c_double)], st),
+        "bd_probe_fp32_fma": ([vp, P(ctypes.c_double)], st),
         "bd_philox_normals": ([ctypes.c_uint64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp], st),
         "bd_compact_events_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.c_int32, vp,
                                        ctypes.c_int64, vp, vp], st),
@@ -289,6 +290,13 @@ def bd_probe_philox_rounds(stream: Optional[int] = None) -> float:
     """Measured Philox4x32 rounds per second of the current device."""
     r = ctypes.c_double(0.0)
     _check(load().bd_probe_philox_rounds(stream, ctypes.byref(r)))
+    return r.value
+
+
+def bd_probe_fp32_fma(stream: Optional[int] = None) -> float:
+    """Measured float32 FMA throughput of the current device, FLOP/s."""
+    r = ctypes.c_double(0.0)
+    _check(load().bd_probe_fp32_fma(stream, ctypes.byref(r)))
     return r.value
 
 

@@ -35,10 +35,79 @@ philox_round_probe(uint32_t* sink, int iters, uint32_t k0, uint32_t k1)
     sink[g] = acc;
 }
 
+// Float32 fused multiply-adds: every thread runs kProbeChains independent
+// chains x = fma(x, b, c) with b just below 1 (values stay finite), so the
+// rate is the SM's float32 FMA throughput.
+__global__ void __launch_bounds__(kProbeThreads, 2)
+fma_probe(float* sink, int iters, float b, float c)
+{
+    float x[kProbeChains];
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) x[j] = (float)(g & 255u) + (float)j;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < kProbeChains; ++j) x[j] = __fmaf_rn(x[j], b, c);
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) acc += x[j];
+    sink[g] = acc;
+}
+
+// Times `launch(iters)` on `stream` after a warm-up launch (iters 256) and
+// returns its duration in ms (0 on failure).
+template <typename F>
+float probe_time(cudaStream_t st, F launch, int iters)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.0f;
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        launch(256);
+        cudaEventRecord(e0, st);
+        launch(iters);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess)
+            ms = 0.0f;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGetLastError();
+    return ms;
+}
+
 }  // namespace
 }  // namespace bdra
 
 using namespace bdra;
+
+extern "C" bd_status bd_probe_fp32_fma(void* stream, double* flops_per_s)
+{
+    if (!flops_per_s) return BD_E_INVALID;
+    *flops_per_s = 0.0;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return BD_E_CUDA;
+    }
+    const int blocks = 2 * sms, iters = 16384;
+    float* sink = nullptr;
+    if (cudaMalloc((void**)&sink, sizeof(float) * (size_t)blocks * kProbeThreads) != cudaSuccess) {
+        cudaGetLastError();
+        return BD_E_OOM;
+    }
+    const float ms = probe_time(st, [&](int n) {
+        fma_probe<<<blocks, kProbeThreads, 0, st>>>(sink, n, 0.99999994f, 1e-3f);
+    }, iters);
+    cudaFree(sink);
+    cudaGetLastError();
+    if (!(ms > 0.0f)) return BD_E_CUDA;
+    *flops_per_s = 2.0 * (double)blocks * kProbeThreads * iters * kProbeChains / (ms * 1e-3);
+    return BD_OK;
+}
 
 extern "C" bd_status bd_probe_philox_rounds(void* stream, double* rounds_per_s)
 {
