@@ -14,7 +14,11 @@ Workload shapes follow the configurations the replica-averaging method is
 benchmarked on: free-draining FENE chains under uniaxial / planar elongation
 and steady shear, tens of replicas per chain, re-spawned every window of
 100 steps (Sec. II of the paper describes the replica procedure; the FENE
-spring is named in its supplementary vWF model, Table S1).
+spring is named in its supplementary vWF model, Table S1). The paper's own
+model is here too, in units of the bead radius a (see COLLAPSED_DT): the
+collapsed chain (harmonic springs with rest length 2a, Lennard-Jones
+cohesion), with RPY hydrodynamic interaction, and the coarse-grained vWF
+chain of Table S1; its starting conformations are compact globules.
 """
 from __future__ import annotations
 
