@@ -187,3 +187,31 @@ def test_windows_across_chunks():
         assert np.abs(g[key] - r[key]).max() <= 1e-10 * np.abs(r[key]).max(), key
     nb = [c.n_beads for c in chains]
     assert _rel(g["pos"], O.com_frame(r["pos"], nb), nb) <= 1e-10
+
+
+@pytest.mark.slow
+def test_paper_rsf_spread_at_rest():
+    # The paper's collapsed chain with RPY at rest (Sec. III, Fig. 2 set-up,
+    # S = 0.02 tau): the spread of the middle (25th) spring's RSF over chains
+    # and windows is 6.7 for N_R = 10 and 3.3 for N_R = 50. The same set-up
+    # here (128 chains from the starting globules, windows 3-6) lands within
+    # 15% of both, and the spread falls as N_R^-1/2 between them.
+    import torch
+    S, windows, skip = 2000, 6, 2
+    spread = {}
+    for R in (10, 50):
+        chains = []
+        for _ in range(128):
+            ch = I.collapsed_chain(R, rate=0.0)
+            ch.hi_a = 1.0
+            chains.append(ch)
+        pos0 = I.initial_positions(I.custom(chains, I.COLLAPSED_DT, S, windows * S), seed=12)
+        ctx = bdra.Context(chains, I.COLLAPSED_DT, S, 12, pos0, precision=bdra.BD_PREC_FP32,
+                           max_windows=windows, stream=torch.cuda.current_stream().cuda_stream)
+        ctx.step(windows * S)
+        rsf = np.array([ctx.replica_average(w) for w in range(skip, windows)])
+        ctx.close()
+        mid = I.spring_offsets(chains)[:-1] + 24
+        spread[R] = rsf[:, mid].std()
+    assert abs(spread[10] / 6.7 - 1) < 0.15 and abs(spread[50] / 3.3 - 1) < 0.15, spread
+    assert abs(spread[10] / spread[50] / np.sqrt(5) - 1) < 0.15, spread
