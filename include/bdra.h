@@ -15,10 +15,17 @@
  * (Sec. I: a threshold rupture force; Sec. III: the Bell rate
  * k = k0 exp(f dx / kT) and the survival exp(-integral of k dt)).
  *
- * Model realised here: free-draining chains (Eq. 2 diagonal diffusion, no
- * hydrodynamic interaction), Hookean or FENE springs F = H Q / (1 - H Q^2/b),
+ * Model realised here: bead-spring chains with Hookean or FENE springs
+ * F = H Q / (1 - H Q^2/b), the paper's collapsed-chain springs (harmonic with
+ * a rest length) and Lennard-Jones cohesion (Sec. II), the coarse-grained vWF
+ * chain (supplementary Table S1); free draining (Eq. 2 diagonal diffusion) or
+ * with the Rotne-Prager-Yamakawa hydrodynamic interaction (Eqs. 1-3);
  * homogeneous shear (v = gdot z x_hat, Sec. II), uniaxial or planar
- * elongation. Units: length sqrt(kT/H0), time zeta/(4 H0), kT = 1.
+ * elongation. Units: kT = 1 and a single-bead diffusivity of 1/4 (the
+ * update of Eq. 1 is r += [kappa r + F/4] dt + sqrt(dt/2) xi for free
+ * draining); the length unit is the caller's: sqrt(kT/H0) for the FENE
+ * chains (time zeta/(4 H0)), the bead radius a for the paper's model (time
+ * tau/4, tau = 6 pi eta a^3 / kT).
  *
  * Conventions for every entry point:
  *   - All functions are extern "C", never throw, and return a bd_status.
