@@ -215,3 +215,46 @@ def test_paper_rsf_spread_at_rest():
         spread[R] = rsf[:, mid].std()
     assert abs(spread[10] / 6.7 - 1) < 0.15 and abs(spread[50] / 3.3 - 1) < 0.15, spread
     assert abs(spread[10] / spread[50] / np.sqrt(5) - 1) < 0.15, spread
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("hi", [0.0, 1.0])
+def test_float32_trimer_samples_the_stationary_density(hi):
+    # Long float32 runs of three collapsed beads at rest (kappa 50, u 2, rest
+    # and sigma 2), free draining and with RPY: bond length and bead angle
+    # against 3-D quadrature of exp(-U), as the oracle's pin, so that the
+    # fast float path (approximate reciprocals and square roots, float32
+    # Cholesky) is checked against the statics over 10^4 relaxation times of
+    # a bond, not only against the oracle over short runs.
+    import math
+    import torch
+    from scipy import integrate
+    kappa, u, R0, SIG = 50.0, 2.0, 2.0, 2.0
+
+    def weight(r1, r2, c):
+        r02 = math.sqrt(max(r1 * r1 + r2 * r2 - 2 * r1 * r2 * c, 1e-12))
+        x = SIG / r02
+        return r1 * r1 * r2 * r2 * math.exp(-0.5 * kappa * ((r1 - R0) ** 2 + (r2 - R0) ** 2)
+                                            - u * (x ** 12 - 2 * x ** 6))
+
+    lo, hi_ = R0 - 1.0, R0 + 1.0
+    opts = dict(epsabs=1e-13, epsrel=1e-8)
+    Z = integrate.tplquad(lambda c, r2, r1: weight(r1, r2, c), lo, hi_, lo, hi_, -1, 1, **opts)[0]
+    mc = integrate.tplquad(lambda c, r2, r1: c * weight(r1, r2, c), lo, hi_, lo, hi_, -1, 1, **opts)[0] / Z
+    mr = integrate.tplquad(lambda c, r2, r1: r1 * weight(r1, r2, c), lo, hi_, lo, hi_, -1, 1, **opts)[0] / Z
+    C, R, dt, steps = 512, 8, 2e-3, 40000
+    chains = [I.Chain(n_beads=3, n_replicas=R, spring=I.SPRING_HARMONIC, H=kappa, r0=R0, lj_u=u,
+                      lj_sigma=SIG, hi_a=hi) for _ in range(C)]
+    pos0 = np.zeros((3 * C, 3))
+    pos0[:, 2] = np.tile([0.0, 2.0, 4.0], C)
+    ctx = bdra.Context(chains, dt, steps, 33, pos0, precision=bdra.BD_PREC_FP32, max_windows=1,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    ctx.step(steps)
+    allpos = ctx.positions(True).reshape(C, R + 1, 3, 3)
+    ctx.close()
+    q1, q2 = allpos[:, :, 1] - allpos[:, :, 0], allpos[:, :, 2] - allpos[:, :, 1]
+    n1, n2 = np.linalg.norm(q1, axis=-1).ravel(), np.linalg.norm(q2, axis=-1).ravel()
+    cos_bead = (-(q1 * q2).sum(axis=-1)).ravel() / (n1 * n2)
+    for est, want in ((cos_bead, mc), (n1, mr)):
+        sd = est.std() / math.sqrt(est.size)
+        assert abs(est.mean() - want) < 5 * sd + 0.005 * abs(want), (est.mean(), want, sd)
