@@ -107,3 +107,47 @@ def test_vwf_chains_match_oracle(oracle_run, prec):
         pos = r["lam"] > 0
         assert (np.abs(np.log(haz[pos]) - np.log(r["lam"][pos])) <= 1e-4 * np.abs(np.log(r["lam"][pos])) + 2e-3).all()
         np.testing.assert_array_equal(haz[~pos], r["lam"][~pos])
+
+
+@pytest.mark.slow
+def test_float32_vwf_trimer_samples_the_stationary_density():
+    # one A2 domain (FENE in parallel with harmonic) and one disulfide bond,
+    # Lennard-Jones between the ends, at rest, float32 with RPY: both bond
+    # lengths and the bead angle against 3-D quadrature of exp(-U)
+    import math
+    import torch
+    from scipy import integrate
+    fa, fb, xmax, H, u, R0, SIG = 20.0, 30.0, 0.8, 50.0, 2.0, 2.0, 2.0
+
+    def weight(r1, r2, c):
+        x1, x2 = r1 - R0, r2 - R0
+        if abs(x1) >= xmax:
+            return 0.0
+        ua2 = 0.5 * fb * x1 * x1 - 0.5 * fa * xmax ** 2 * math.log(1 - (x1 / xmax) ** 2)
+        r02 = math.sqrt(max(r1 * r1 + r2 * r2 - 2 * r1 * r2 * c, 1e-12))
+        s = SIG / r02
+        return r1 * r1 * r2 * r2 * math.exp(-ua2 - 0.5 * H * x2 * x2 - u * (s ** 12 - 2 * s ** 6))
+
+    opts = dict(epsabs=1e-13, epsrel=1e-8)
+    lim = (R0 - xmax, R0 + xmax, R0 - 1.0, R0 + 1.0, -1, 1)
+    Z = integrate.tplquad(lambda c, r2, r1: weight(r1, r2, c), *lim, **opts)[0]
+    want = {k: integrate.tplquad(lambda c, r2, r1: f(r1, r2, c) * weight(r1, r2, c), *lim, **opts)[0] / Z
+            for k, f in (("cos", lambda r1, r2, c: c), ("r1", lambda r1, r2, c: r1),
+                         ("r2", lambda r1, r2, c: r2))}
+    C, R, dt, steps = 512, 8, 2e-3, 40000
+    chains = [I.Chain(n_beads=3, n_replicas=R, spring=I.SPRING_VWF, H=H, r0=R0, lj_u=u, lj_sigma=SIG,
+                      vwf_fa=fa, vwf_fb=fb, vwf_xmax=xmax, hi_a=1.0) for _ in range(C)]
+    pos0 = np.zeros((3 * C, 3))
+    pos0[:, 2] = np.tile([0.0, 2.0, 4.0], C)
+    ctx = bdra.Context(chains, dt, steps, 35, pos0, precision=bdra.BD_PREC_FP32, max_windows=1,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    ctx.step(steps)
+    allpos = ctx.positions(True).reshape(C, R + 1, 3, 3)
+    assert ctx.info().overextensions == 0
+    ctx.close()
+    q1, q2 = allpos[:, :, 1] - allpos[:, :, 0], allpos[:, :, 2] - allpos[:, :, 1]
+    n1, n2 = np.linalg.norm(q1, axis=-1).ravel(), np.linalg.norm(q2, axis=-1).ravel()
+    cos_bead = (-(q1 * q2).sum(axis=-1)).ravel() / (n1 * n2)
+    for est, key in ((cos_bead, "cos"), (n1, "r1"), (n2, "r2")):
+        sd = est.std() / math.sqrt(est.size)
+        assert abs(est.mean() - want[key]) < 5 * sd + 0.003 * abs(want[key]), (key, est.mean(), want[key], sd)
