@@ -873,6 +873,13 @@ def main():
             out["adjoint"] = adjoint_line(sptr, args.adjoint_chains, args.adjoint_steps)
         if not args.no_conformation:
             out["conformation"] = conformation_line(wl, pos0, sptr)
+        # measured per-unit ceilings of this GPU (context for every fraction above)
+        out["measured_unit_peaks"] = {
+            "philox_rounds_per_s": philox_peak,
+            "fp32_fma_flops": bdra.bd_probe_fp32_fma(sptr),
+            "fp64_fma_flops": bdra.bd_probe_fp64_fma(sptr),
+            "mufu_rsqrt_per_s": bdra.bd_probe_mufu(sptr),
+            "basis": "independent chains at full occupancy, no memory traffic (bd_probe_*)"}
         if not args.no_collapsed:
             out["collapsed"] = collapsed_line(sptr)
         if not args.no_hi:

@@ -333,6 +333,12 @@ bd_status bd_probe_philox_rounds(void* stream, double* rounds_per_s);
  * device failures. */
 bd_status bd_probe_fp32_fma(void* stream, double* flops_per_s);
 
+/* The same for float64 FMA (the FP64 path's unit; FLOP/s, an FMA counted as
+ * two) and for the special-function unit (approximate reciprocal square
+ * roots per second). Same conventions. */
+bd_status bd_probe_fp64_fma(void* stream, double* flops_per_s);
+bd_status bd_probe_mufu(void* stream, double* ops_per_s);
+
 /* Largest n_springs bd_compact_events_noalloc accepts (its fixed scratch
  * holds one count per 256 springs: 32 KiB of device memory). */
 #define BD_NOALLOC_MAX_SPRINGS (1 << 20)

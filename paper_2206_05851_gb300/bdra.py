@@ -105,6 +105,8 @@ def load() -> ctypes.CDLL:
         "bd_adjoint": ([vp, vp, vp, vp], st),
         "bd_probe_philox_rounds": ([vp, P(ctypes.c_double)], st),
         "bd_probe_fp32_fma": ([vp, P(ctypes.c_double)], st),
+        "bd_probe_fp64_fma": ([vp, P(ctypes.c_double)], st),
+        "bd_probe_mufu": ([vp, P(ctypes.c_double)], st),
         "bd_philox_normals": ([ctypes.c_uint64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp], st),
         "bd_compact_events_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.c_int32, vp,
                                        ctypes.c_int64, vp, vp], st),
@@ -297,6 +299,20 @@ def bd_probe_fp32_fma(stream: Optional[int] = None) -> float:
     """Measured float32 FMA throughput of the current device, FLOP/s."""
     r = ctypes.c_double(0.0)
     _check(load().bd_probe_fp32_fma(stream, ctypes.byref(r)))
+    return r.value
+
+
+def bd_probe_fp64_fma(stream: Optional[int] = None) -> float:
+    """Measured float64 FMA throughput of the current device, FLOP/s."""
+    r = ctypes.c_double(0.0)
+    _check(load().bd_probe_fp64_fma(stream, ctypes.byref(r)))
+    return r.value
+
+
+def bd_probe_mufu(stream: Optional[int] = None) -> float:
+    """Measured special-function (approximate rsqrt) throughput, ops/s."""
+    r = ctypes.c_double(0.0)
+    _check(load().bd_probe_mufu(stream, ctypes.byref(r)))
     return r.value
 
 

@@ -55,6 +55,47 @@ fma_probe(float* sink, int iters, float b, float c)
     sink[g] = acc;
 }
 
+// Float64 fused multiply-adds, the same way (the FP64 path's unit).
+__global__ void __launch_bounds__(kProbeThreads, 2)
+dfma_probe(double* sink, int iters, double b, double c)
+{
+    double x[kProbeChains];
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) x[j] = (double)(g & 255u) + (double)j;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < kProbeChains; ++j) x[j] = __fma_rn(x[j], b, c);
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) acc += x[j];
+    sink[g] = acc;
+}
+
+// Special-function unit: independent chains of approximate reciprocal square
+// roots (one MUFU operation each), x = rsqrt(x) + c stays in [1, 2).
+__global__ void __launch_bounds__(kProbeThreads, 2)
+mufu_probe(float* sink, int iters, float c)
+{
+    float x[kProbeChains];
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) x[j] = 1.0f + (float)((g + j) & 7u) * 0.125f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < kProbeChains; ++j) {
+            float r;
+            asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[j]));
+            x[j] = r + c;
+        }
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) acc += x[j];
+    sink[g] = acc;
+}
+
 // Times `launch(iters)` on `stream` after a warm-up launch (iters 256) and
 // returns its duration in ms (0 on failure).
 template <typename F>
@@ -81,6 +122,66 @@ float probe_time(cudaStream_t st, F launch, int iters)
 }  // namespace bdra
 
 using namespace bdra;
+
+namespace {
+// Device SM count (0 on failure).
+int probe_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms;
+}
+}  // namespace
+
+extern "C" bd_status bd_probe_fp64_fma(void* stream, double* flops_per_s)
+{
+    if (!flops_per_s) return BD_E_INVALID;
+    *flops_per_s = 0.0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int sms = probe_sms();
+    if (!sms) return BD_E_CUDA;
+    const int blocks = 2 * sms, iters = 1024;
+    double* sink = nullptr;
+    if (cudaMalloc((void**)&sink, sizeof(double) * (size_t)blocks * kProbeThreads) != cudaSuccess) {
+        cudaGetLastError();
+        return BD_E_OOM;
+    }
+    const float ms = probe_time(st, [&](int n) {
+        dfma_probe<<<blocks, kProbeThreads, 0, st>>>(sink, n, 0.9999999999999999, 1e-3);
+    }, iters);
+    cudaFree(sink);
+    cudaGetLastError();
+    if (!(ms > 0.0f)) return BD_E_CUDA;
+    *flops_per_s = 2.0 * (double)blocks * kProbeThreads * iters * kProbeChains / (ms * 1e-3);
+    return BD_OK;
+}
+
+extern "C" bd_status bd_probe_mufu(void* stream, double* ops_per_s)
+{
+    if (!ops_per_s) return BD_E_INVALID;
+    *ops_per_s = 0.0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int sms = probe_sms();
+    if (!sms) return BD_E_CUDA;
+    const int blocks = 2 * sms, iters = 4096;
+    float* sink = nullptr;
+    if (cudaMalloc((void**)&sink, sizeof(float) * (size_t)blocks * kProbeThreads) != cudaSuccess) {
+        cudaGetLastError();
+        return BD_E_OOM;
+    }
+    const float ms = probe_time(st, [&](int n) {
+        mufu_probe<<<blocks, kProbeThreads, 0, st>>>(sink, n, 0.75f);
+    }, iters);
+    cudaFree(sink);
+    cudaGetLastError();
+    if (!(ms > 0.0f)) return BD_E_CUDA;
+    *ops_per_s = (double)blocks * kProbeThreads * iters * kProbeChains / (ms * 1e-3);
+    return BD_OK;
+}
 
 extern "C" bd_status bd_probe_fp32_fma(void* stream, double* flops_per_s)
 {

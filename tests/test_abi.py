@@ -129,6 +129,8 @@ def test_null_arguments_rejected(lib):
 def test_probe_rejects_null_output(lib):
     assert lib.bd_probe_philox_rounds(None, None) == bdra.BD_E_INVALID
     assert lib.bd_probe_fp32_fma(None, None) == bdra.BD_E_INVALID
+    assert lib.bd_probe_fp64_fma(None, None) == bdra.BD_E_INVALID
+    assert lib.bd_probe_mufu(None, None) == bdra.BD_E_INVALID
 
 
 def test_binding_fails_loudly_when_library_missing(monkeypatch, tmp_path):
