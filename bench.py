@@ -562,6 +562,26 @@ def rest_line(sptr, n_chains=128, windows=6, skip=2):
         r = rsf[skip:, mid]
         out[f"N_R={R}"] = {"rsf_mean": float(r.mean()), "rsf_std": float(r.std()),
                            "tsf_mean": float(tsf[skip:, mid].mean()), "seconds": t}
+    # Fig. 2: the TSF of the same spring needs a longer sampling time for the
+    # same spread (the paper: S = 0.07 tau for N_R = 10, 0.36 tau for N_R = 50)
+    tsf_spread = {}
+    for s_tau in (0.02, 0.07, 0.36):
+        St = int(round(s_tau * 1e5))                     # steps of 1e-5 tau
+        chains = []
+        for _ in range(n_chains):
+            ch = I.collapsed_chain(1, rate=0.0)
+            ch.hi_a = 1.0
+            chains.append(ch)
+        nw = 3
+        pos0 = I.initial_positions(I.custom(chains, I.COLLAPSED_DT, St, nw * St), seed=12)
+        c = bdra.Context(chains, I.COLLAPSED_DT, St, 12, torch.from_numpy(pos0).cuda(),
+                         precision=bdra.BD_PREC_FP32, max_windows=nw, stream=sptr)
+        c.step(nw * St)
+        tsf = np.array([c.time_average(w) for w in range(1, nw)])
+        c.close()
+        mid = I.spring_offsets(chains)[:-1] + 24
+        tsf_spread[f"S={s_tau}"] = float(tsf[:, mid].std())
+    out["tsf_spread_vs_S"] = tsf_spread
     # Fig. 6 set-up: shear at 30 / tau, N_R = 50, S = 0.015 tau; replica-vs-parent D-bar (Eq. 5)
     chains = []
     for _ in range(64):
@@ -582,6 +602,7 @@ def rest_line(sptr, n_chains=128, windows=6, skip=2):
                           "dbar_mean": dbar.mean(axis=0).tolist(), "rgz_mean": float(rgz.mean()),
                           "rgz_max": float(rgz.max())}
     out["paper_context"] = {"mean_force_spring25": 0.55, "rsf_std_S0.02": {"N_R=10": 6.7, "N_R=50": 3.3},
+                            "tsf_S_matching_rsf": {"N_R=10": 0.07, "N_R=50": 0.36},
                             "max_dbar_x_S0.015": 0.65}
     return out
 
