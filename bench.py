@@ -542,7 +542,7 @@ def rest_line(sptr, n_chains=128, windows=6, skip=2):
 
     S = 2000
     out = {"chains": n_chains, "window_steps": S, "windows": windows, "skipped_windows": skip}
-    for R in (10, 50):
+    for R in (10, 20, 40, 50):
         chains = []
         for _ in range(n_chains):
             ch = I.collapsed_chain(R, rate=0.0)
@@ -601,7 +601,10 @@ def rest_line(sptr, n_chains=128, windows=6, skip=2):
     out["shear30_eq5"] = {"windows_used": w6 - 1, "dbar_max": dbar.max(axis=0).tolist(),
                           "dbar_mean": dbar.mean(axis=0).tolist(), "rgz_mean": float(rgz.mean()),
                           "rgz_max": float(rgz.max())}
+    out["rsf_spread_reduction"] = {"N_R 10->20": out["N_R=20"]["rsf_std"] / out["N_R=10"]["rsf_std"] - 1,
+                                   "N_R 20->40": out["N_R=40"]["rsf_std"] / out["N_R=20"]["rsf_std"] - 1}
     out["paper_context"] = {"mean_force_spring25": 0.55, "rsf_std_S0.02": {"N_R=10": 6.7, "N_R=50": 3.3},
+                            "rsf_spread_reduction": {"N_R 10->20": -0.27, "N_R 20->40": -0.24},
                             "tsf_S_matching_rsf": {"N_R=10": 0.07, "N_R=50": 0.36},
                             "max_dbar_x_S0.015": 0.65}
     return out
