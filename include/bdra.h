@@ -257,9 +257,10 @@ bd_status bd_autotune(bd_ctx* ctx, int32_t probe_steps, int32_t force);
  * per lane, 200 for the collapsed-chain step; 300 for hydrodynamic
  * interaction, one CTA per replica) and groups[c] (work items) per chain,
  * host arrays of n_chains; cost_ns (host, may be NULL) receives the
- * per-warp-step cost of each compiled tile variant, 12 values in the order
- * float32 {4, 7, 10, 13, 16, 104, 107, 202, 204, 205, 207, 216} or 11 values
- * in the order float64 {2, 4, 7, 10, 13, 16, 202, 204, 205, 207, 216}. Any pointer
+ * per-warp-step cost of each compiled tile variant, 22 values in the order
+ * float32 {4, 7, 10, 13, 16, 104, 107, 202, 204, 205, 207, 216, 5, 6, 8, 9,
+ * 11, 12, 14, 15, 105, 106} or 11 values in the order float64 {2, 4, 7, 10,
+ * 13, 16, 202, 204, 205, 207, 216}. Any pointer
  * may be NULL. */
 bd_status bd_get_plan(bd_ctx* ctx, int32_t* variant, int32_t* groups, double* cost_ns);
 

@@ -257,7 +257,8 @@ def bd_get_plan(ctx: int, n_chains: int, precision: int = BD_PREC_FP32):
     v = np.zeros(n_chains, dtype=np.int32)
     g = np.zeros(n_chains, dtype=np.int32)
     names = ([2, 4, 7, 10, 13, 16, 202, 204, 205, 207, 216] if precision == BD_PREC_FP64
-             else [4, 7, 10, 13, 16, 104, 107, 202, 204, 205, 207, 216])
+             else [4, 7, 10, 13, 16, 104, 107, 202, 204, 205, 207, 216,
+                   5, 6, 8, 9, 11, 12, 14, 15, 105, 106])
     c = np.zeros(len(names))
     _check(load().bd_get_plan(ctx, v.ctypes.data, g.ctypes.data, c.ctypes.data), ctx)
     return v, g, dict(zip(names, c.tolist()))

@@ -23,6 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path
 UNITS = [("bd_window_f32.cu", ["-fmad=false"]), ("bd_window_f64.cu", ["-fmad=false"]),
          ("bd_window_f32c.cu", ["-fmad=false"]), ("bd_window_f64c.cu", ["-fmad=false"]),
          ("bd_hi_f32.cu", ["-fmad=false"]), ("bd_hi_f64.cu", ["-fmad=false"]),
+         ("bd_window_f32b.cu", ["-fmad=false"]),
          ("bd_adjoint_f32.cu", ["-fmad=false"]), ("bd_adjoint_f64.cu", ["-fmad=false"]),
          ("bd_support.cu", []), ("bd_api.cu", []), ("bd_noalloc.cu", []), ("bd_probe.cu", [])]
 

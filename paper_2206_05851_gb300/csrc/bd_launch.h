@@ -12,14 +12,15 @@ static const int kNumTiles = 6;
 
 // Replica step variants compiled into the persistent kernel (ItemDev::variant):
 // float32: one replica per lane with 4..16 springs, two replicas per lane
-// with 4 or 7 springs (larger pair tiles spill at 128 registers);
+// with 4..7 springs (larger pair tiles spill at 128 registers);
 // float64: one replica per lane with 2..16 springs; both precisions: the
 // collapsed-chain step (harmonic springs, Lennard-Jones pair forces) with 2,
 // 4, 5, 7 or 16 springs per lane (5: the paper's 50-bead chain fills ten
 // lanes exactly). (bd_variants.h lists the same.)
 static const int kVariantsF32[] = {4, 7, 10, 13, 16, kPairBase + 4, kPairBase + 7,
-                                   kLJBase + 2, kLJBase + 4, kLJBase + 5, kLJBase + 7, kLJBase + 16};
-static const int kNumVariantsF32 = 12;
+                                   kLJBase + 2, kLJBase + 4, kLJBase + 5, kLJBase + 7, kLJBase + 16,
+                                   5, 6, 8, 9, 11, 12, 14, 15, kPairBase + 5, kPairBase + 6};
+static const int kNumVariantsF32 = 22;
 static const int kVariantsF64[] = {2, 4, 7, 10, 13, 16,
                                    kLJBase + 2, kLJBase + 4, kLJBase + 5, kLJBase + 7, kLJBase + 16};
 static const int kNumVariantsF64 = 11;
@@ -60,6 +61,7 @@ const void* parent_func_f64(int L, bool lj);
 const void* persist_plain_f32(int variant);     // without the Eq. 5 diagnostics
 const void* persist_plain_f64(int variant);
 const void* persist_conf_f32(int variant);      // with them (bd_window_f32c.cu)
+const void* persist_more_f32(int variant, bool conf);   // the in-between tiles (bd_window_f32b.cu)
 const void* persist_conf_f64(int variant);
 const void* persist_func_f32(int variant, bool conf);
 const void* persist_func_f64(int variant, bool conf);

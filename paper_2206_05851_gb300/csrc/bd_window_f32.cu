@@ -30,9 +30,9 @@ const void* persist_plain_f32(int v)
 {
     switch (v) {
 #define X(x) case x: return (const void*)replica_persist_kernel<float, true, x, false>;
-        BD_VARIANTS_F32(X)
+        BD_VARIANTS_F32_MAIN(X)
 #undef X
-    default: return nullptr;
+    default: return persist_more_f32(v, false);
     }
 }
 

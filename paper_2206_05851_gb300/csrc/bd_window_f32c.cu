@@ -12,9 +12,9 @@ const void* persist_conf_f32(int v)
 {
     switch (v) {
 #define X(x) case x: return (const void*)replica_persist_kernel<float, true, x, true>;
-        BD_VARIANTS_F32(X)
+        BD_VARIANTS_F32_MAIN(X)
 #undef X
-    default: return nullptr;
+    default: return persist_more_f32(v, true);
     }
 }
 

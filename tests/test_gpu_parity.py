@@ -268,7 +268,7 @@ def test_results_do_not_depend_on_tile(prec):
     S, dt = 10, 1e-3
     pos0 = I.initial_positions(I.custom(chains, dt, S, 60), seed=9)
     if prec == bdra.BD_PREC_FP32:      # one and two replicas per lane (packed float32)
-        shapes = [(1, L) for L in (4, 7, 10, 13, 16)] + [(2, L) for L in (4, 7)]
+        shapes = [(1, L) for L in range(4, 17)] + [(2, L) for L in range(4, 8)]
     else:
         shapes = [(1, L) for L in (2, 4, 7, 10, 13, 16)]
     runs = [gpu_run(chains, dt, S, [60], 7, pos0, prec, lanes=L, layout=lay) for lay, L in shapes]
