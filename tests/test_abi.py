@@ -37,6 +37,22 @@ def test_header_declares_the_method_calls():
         assert n in names
 
 
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header compiles as strict C99, without C++
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "t.c"
+    src.write_text('#include "bdra.h"\nint main(void) { bd_config c; bd_chain_desc d; '
+                   '(void)c; (void)d; return 0; }\n')
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc,
+                        "-fsyntax-only", str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_every_declared_symbol_is_exported(lib):
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
