@@ -276,3 +276,25 @@ def test_float32_trimer_samples_the_stationary_density(hi):
     for est, want in ((cos_bead, mc), (n1, mr)):
         sd = est.std() / math.sqrt(est.size)
         assert abs(est.mean() - want) < 5 * sd + 0.005 * abs(want), (est.mean(), want, sd)
+
+
+def test_fene_floor_with_hi_matches_oracle_exactly():
+    # FENE chains with RPY driven onto the FENE floor (strong uniaxial flow):
+    # FP64 positions, floor counts and first events equal the oracle's
+    chains = [I.Chain(n_beads=10, n_replicas=3, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL, b=20.0,
+                      rate=4.0, f_c=3.0, k0=1e-3, dx=0.5, hi_a=0.5),
+              I.Chain(n_beads=6, n_replicas=2, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL, b=20.0,
+                      rate=8.0, f_c=3.0, k0=1e-3, dx=0.5, hi_a=0.5)]
+    # 300 steps: long enough for the floor, short enough that the oracle's
+    # laboratory-frame centre of mass (which grows as exp(rate t)) stays
+    # small next to the chain, so its rounding stays below the tolerance
+    dt, S, steps = 2e-3, 20, [130, 170]
+    pos0 = I.initial_positions(I.custom(chains, dt, S, sum(steps)), seed=3)
+    g = _gpu(chains, dt, S, steps, pos0, bdra.BD_PREC_FP64, seed=5)
+    r = O.run(chains, dt, S, sum(steps), 5, pos0, thr_mask=7, bell_mask=7, n_threads=2)
+    assert r["overext"].sum() > 10
+    assert g["info"].overextensions == int(r["overext"].sum())
+    nb = [c.n_beads for c in chains]
+    assert _rel(g["pos"], O.com_frame(r["pos"], nb), nb) <= 1e-10
+    np.testing.assert_array_equal(g["first_thr"], r["first_thr"])
+    np.testing.assert_array_equal(g["first_bell"], r["first_bell"])
