@@ -4,8 +4,18 @@ normals and the Exp(1) thresholds of the first-passage test.
 The random displacement R_i of Eq. 1 (Sec. II) has zero mean and covariance
 2 D dt; each replica gets a unique random-number seed (Sec. II, RSF). Both are
 realised with a counter-based Philox stream; these tests tie the oracle's
-stream to the published generator and to the normal / exponential laws.
+stream to an independent implementation of the published generator and to
+the normal / exponential laws.
+
+The independent implementation is the CUDA toolkit's host-side cuRAND
+Philox4x32-10 generator (called through its C API, on the CPU). Its output
+layout was established by comparison: the 64-bit seed is the key (low word
+first), and output block b (four words) is the generator evaluated at the
+counter (r, j, 0) with r, j = divmod(b, 65536), r a 64-bit pair of counter
+words 0-1 and j counter word 2; the generator offset counts words.
 """
+import ctypes
+import ctypes.util
 import os
 
 import numpy as np
@@ -14,25 +24,64 @@ from scipy import stats
 
 from oracle import oracle as O
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+CURAND_LANES = 65536     # counter word 2 of consecutive output blocks
 
 
-def _kat_rows():
-    rows = []
-    with open(GOLDEN) as fh:
-        for line in fh:
-            line = line.strip()
-            if not line or line.startswith("#"):
-                continue
-            w = [int(x, 16) for x in line.split()]
-            rows.append((w[0:4], w[4:6], w[6:10]))
-    return rows
+def _curand():
+    names = [os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64", "libcurand.so"),
+             ctypes.util.find_library("curand")]
+    for n in names:
+        if n:
+            try:
+                return ctypes.CDLL(n)
+            except OSError:
+                pass
+    pytest.skip("cuRAND host library not found")
 
 
-@pytest.mark.parametrize("ctr,key,expect", _kat_rows())
-def test_philox_known_answers(ctr, key, expect):
-    out = O.philox(ctr, key)
-    assert [int(x) for x in out] == expect
+def _curand_blocks(seed, first_block, n_blocks):
+    lib = _curand()
+    g = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(g), CURAND_RNG_PSEUDO_PHILOX4_32_10) == 0
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(g, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(g, ctypes.c_ulonglong(4 * first_block)) == 0
+        out = np.zeros(4 * n_blocks, dtype=np.uint32)
+        assert lib.curandGenerate(g, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                  ctypes.c_size_t(out.size)) == 0
+    finally:
+        lib.curandDestroyGenerator(g)
+    return out.reshape(n_blocks, 4)
+
+
+def _counters_of(first_block, n_blocks):
+    b = first_block + np.arange(n_blocks, dtype=np.uint64)
+    r, j = b // CURAND_LANES, b % CURAND_LANES
+    ctr = np.zeros((n_blocks, 4), dtype=np.uint32)
+    ctr[:, 0] = (r & 0xFFFFFFFF).astype(np.uint32)
+    ctr[:, 1] = (r >> np.uint64(32)).astype(np.uint32)
+    ctr[:, 2] = j.astype(np.uint32)
+    return ctr
+
+
+@pytest.mark.parametrize("seed", [0, 0x0123456789ABCDEF, 0xFFFFFFFFFFFFFFFF, 42])
+def test_philox_matches_curand_over_two_counter_rounds(seed):
+    # 2 x 65536 consecutive blocks: counter word 2 over its range, word 0 = 0, 1
+    n = 2 * CURAND_LANES
+    want = _curand_blocks(seed, 0, n)
+    got = O.philox_many(_counters_of(0, n), [seed & 0xFFFFFFFF, seed >> 32])
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("first_block", [CURAND_LANES * (1 << 32) + 5,             # counter word 1 = 1
+                                         CURAND_LANES * 0x3F_FFFF_FFFF + 65500,    # words 0-1 and 2 near full
+                                         123_456_789_012])
+def test_philox_matches_curand_at_large_counters(first_block):
+    seed = 0x9E3779B97F4A7C15
+    want = _curand_blocks(seed, first_block, 64)
+    got = O.philox_many(_counters_of(first_block, 64), [seed & 0xFFFFFFFF, seed >> 32])
+    assert np.array_equal(got, want)
 
 
 def test_philox_batch_matches_single():

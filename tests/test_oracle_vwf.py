@@ -12,11 +12,13 @@ the even springs, disulfide bonds (harmonic) on the odd springs, rest length
   bond does, under all three criteria.
 - Statics: three beads (one A2 domain, one disulfide bond) at rest sample
   exp(-U): bond lengths and bead angle against 3-D quadrature.
-- Units: the library's conversion of Table S1 reproduces the supplement's
-  mean-force unfolding time 1 / (25 k0 exp(f / f_u)) computed in seconds
-  from the printed SI values.
+- Units: every library-unit constant of the chain follows from Table S1's
+  printed SI values (`tests/golden/vwf_table_s1.txt`), and the conversion
+  reproduces the supplement's mean-force unfolding time 1 / (25 k0 exp(f /
+  f_u)) computed in seconds from those values.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -26,6 +28,7 @@ from oracle import oracle as O
 from paper_2206_05851_gb300 import inputs as I
 
 R0, SIG = 2.0, 2.0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "vwf_table_s1.txt")
 
 
 def _chain(N, R=1, fa=20.0, fb=30.0, xmax=0.8, H=50.0, u=2.0, **kw):
@@ -133,14 +136,41 @@ def test_three_beads_at_rest_match_the_stationary_density():
     assert out["overext"].sum() == 0
 
 
-def test_unit_conversion_reproduces_the_mean_force_unfolding_time():
-    # Supplementary material: MFTU = 1 / [25 k0 exp(<f>/f_u)] at <f> = 0.28 pN,
-    # k0 = 7e-4 / s, f_u = 1.1 pN (seconds, straight from the printed values)
-    want = 1.0 / (25 * 7e-4 * math.exp(0.28 / 1.1))
+def _table_s1():
+    vals = {}
+    with open(GOLDEN) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                name, value, _unit = line.split()
+                vals[name] = float(value)
+    return vals
+
+
+def test_library_units_follow_table_s1():
+    # lengths in a, energies in kT = epsilon, time unit tau / 4 with
+    # tau = 6 pi eta a^3 / kT (the collapsed chain's units)
+    t = _table_s1()
+    a, kT = t["a"], t["epsilon"]
+    assert 1.380649e-2 * t["T"] == pytest.approx(kT, rel=1e-3)      # k_B T at 300 K in pN nm
+    tau_s = 6 * math.pi * t["eta"] * a ** 3 / kT * 1e-6               # us -> s
+    assert I.VWF_TAU_S == pytest.approx(tau_s, rel=1e-12)
     ch = I.vwf_chain(1)
-    f = 0.28 / I.VWF_FORCE_UNIT_PN                   # the same force in kT / a
+    assert ch.H == pytest.approx(t["f_harm"] * a * a / kT, rel=1e-12)
+    assert ch.vwf_fa == pytest.approx(t["f_A"] * a * a / kT, rel=1e-12)
+    assert ch.vwf_fb == pytest.approx(t["f_B"] * a * a / kT, rel=1e-12)
+    assert ch.vwf_xmax == pytest.approx(t["r_max"] / a, rel=1e-12)
+    assert ch.k0 == pytest.approx(t["k0"] * tau_s / 4, rel=1e-12)
+    assert ch.dx == pytest.approx((kT / a) / t["f_u"], rel=1e-12)
+    assert ch.spring == I.SPRING_VWF and ch.lj_u == 1.0 and ch.r0 == 2.0 and ch.lj_sigma == 2.0
+
+
+def test_unit_conversion_reproduces_the_mean_force_unfolding_time():
+    # Supplementary material: MFTU = 1 / [25 k0 exp(<f>/f_u)] in seconds,
+    # straight from the printed SI values
+    t = _table_s1()
+    want = 1.0 / (25 * t["k0"] * math.exp(t["mean_a2_force"] / t["f_u"]))
+    ch = I.vwf_chain(1)
+    f = t["mean_a2_force"] / I.VWF_FORCE_UNIT_PN                     # the same force in kT / a
     got = I.vwf_mftu_seconds(25 * ch.k0 * math.exp(ch.dx * f))
     assert got == pytest.approx(want, rel=1e-12)
-    # Table S1 in these units: the disulfide bond is the collapsed chain's kappa ~ 400 kT/a^2
-    assert ch.H == pytest.approx(7.5 * 15 ** 2 / 4.143, rel=1e-12)
-    assert I.VWF_TAU_S == pytest.approx(6 * math.pi * 0.001 * 15 ** 3 / 4.143 * 1e-6, rel=1e-12)
