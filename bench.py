@@ -43,6 +43,16 @@ METRIC = ("bead-steps/s (chains×replicas×beads×steps) FP32 batched vs FP64 pl
 # bit/compare ops (angle bits 2, floor clamp and count 2).
 ALGO_OPS_PER_BEAD_STEP = 67.5
 PHILOX_ROUNDS_PER_BEAD_STEP = 8
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum), each
+# from one single-pass ncu capture of the current kernels, reported only at the
+# workloads captured: the replica kernel at the default workload and chunk (the
+# mean of one bench step's two launches, 64 and 36 windows: mostly the per-group
+# FP64 sample rows of the fixed-order reduction, 13 MB a window) and the HI
+# replica kernel over one 1500-step window of its default workload.
+REPLICA_TRAFFIC_BYTES = (178_089_472 + 855_967_232 + 134_258_688 + 488_113_408) / 2
+REPLICA_TRAFFIC_AT = ("fene_1024x_n100_r64_planar_wi5", 10_000)
+HI_TRAFFIC_BYTES = 4_716_544 + 858_368
+HI_TRAFFIC_AT = ("collapsed_hi_128x_n50_r50_shear30", 1500)
 # Minimal lane-instructions per non-adjacent Lennard-Jones pair of the
 # collapsed-chain model, the pair evaluated once, in units of the LJ length s
 # (x = s/r): separation 3, r^2 3, reciprocal 1, x^4, x^6, x^8 3, x^8 - x^14 1,
@@ -422,7 +432,9 @@ def hi_line(sptr, n_chains=0, n_steps=1500, fp64_chains=8, fp64_steps=100):
     derived = 2.0 * SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     peak = bdra.bd_probe_fp32_fma(sptr) / 1e12           # measured, outside the timed region
     out["roofline"] = {"bound": "alu (float32 FMA)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": None,
+                       "frac": achieved / peak,
+                       "traffic": HI_TRAFFIC_BYTES if (wl.name, n_steps) == HI_TRAFFIC_AT else None,
+                       "traffic_unit": "bytes per launch (ncu capture)",
                        "kernel": "hydrodynamic-interaction replica kernel (float32, one CTA per replica)",
                        "avg_launch_ms": rep_ms / max(rep_n, 1), "launches": rep_n,
                        "share_of_step": rep_ms / (t * 1e3), "flops_per_slot_step": hi_flops_per_slot_step(N),
@@ -794,7 +806,9 @@ def main():
     achieved = ALGO_OPS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3) / 1e12
     peak = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak,
+            "traffic": REPLICA_TRAFFIC_BYTES if (wl.name, chunk) == REPLICA_TRAFFIC_AT else None,
+            "traffic_unit": "bytes per launch (ncu capture)",
             "kernel": "replica kernel (planner's float32 tile)", "avg_launch_ms": rep_ms / max(rep_n, 1),
             "launches": rep_n, "share_of_step": rep_ms / t_ms,
             "peak_basis": f"issue rate {SMS} SMs x {LANES_PER_CLK_PER_SM} lane-instr/clk x "
