@@ -47,12 +47,16 @@ PHILOX_ROUNDS_PER_BEAD_STEP = 8
 # from one single-pass ncu capture of the current kernels, reported only at the
 # workloads captured: the replica kernel at the default workload and chunk (the
 # mean of one bench step's two launches, 64 and 36 windows: mostly the per-group
-# FP64 sample rows of the fixed-order reduction, 13 MB a window) and the HI
-# replica kernel over one 1500-step window of its default workload.
+# FP64 sample rows of the fixed-order reduction, 13 MB a window), the HI replica
+# kernel over one 1500-step window of its default workload, and the
+# collapsed-chain kernel over its timed 3000 steps (its sample rows still sit in
+# L2 when it ends, so they are not in its count).
 REPLICA_TRAFFIC_BYTES = (178_089_472 + 855_967_232 + 134_258_688 + 488_113_408) / 2
 REPLICA_TRAFFIC_AT = ("fene_1024x_n100_r64_planar_wi5", 10_000)
 HI_TRAFFIC_BYTES = 4_716_544 + 858_368
 HI_TRAFFIC_AT = ("collapsed_hi_128x_n50_r50_shear30", 1500)
+COLLAPSED_TRAFFIC_BYTES = 32_545_280 + 958_208
+COLLAPSED_TRAFFIC_AT = ("collapsed_1024x_n50_r50_shear30", 3000)
 # Minimal lane-instructions per non-adjacent Lennard-Jones pair of the
 # collapsed-chain model, the pair evaluated once, in units of the LJ length s
 # (x = s/r): separation 3, r^2 3, reciprocal 1, x^4, x^6, x^8 3, x^8 - x^14 1,
@@ -345,7 +349,9 @@ def collapsed_line(sptr, n_chains=0, n_steps=3000, fp64_chains=64):
     achieved = ops * units / (rep_ms / 1e3) / 1e12
     peak = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                       "frac": achieved / peak, "traffic": None,
+                       "frac": achieved / peak,
+                       "traffic": COLLAPSED_TRAFFIC_BYTES if (wl.name, n_steps) == COLLAPSED_TRAFFIC_AT else None,
+                       "traffic_unit": "bytes per launch (ncu capture)",
                        "kernel": "collapsed-chain replica kernel (float32)",
                        "avg_launch_ms": rep_ms / max(rep_n, 1), "launches": rep_n,
                        "share_of_step": rep_ms / (t * 1e3), "ops_per_bead_step": ops,
