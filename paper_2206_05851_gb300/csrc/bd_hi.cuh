@@ -57,6 +57,9 @@ template <typename T, int NTM> struct HIShared {
     alignas(16) T diag[16];            // factor of the current diagonal tile
     alignas(16) T dinv[4];             // reciprocals of its diagonal
     alignas(16) T panel[NTM][kPanel];  // factor tiles of the current tile column, by tile row
+    // bead pairs bi >= bj in row-major order as (bi << 8) | bj, for the chains of this kernel
+    static constexpr int kBeads = NTM <= kHINTSmall ? kHISmallBeads : kHIMaxBeads;
+    uint16_t pair[kBeads * (kBeads + 1) / 2];
     // W's lower tiles (entry e of tile t at tiles[e][t]) until the threads
     // have loaded theirs, then the per-tile partial products (part[c][t])
     union {
@@ -155,36 +158,65 @@ __device__ __forceinline__ void hi_tiles_init(HITiles<T, MAXT>& tl, int NT)
     }
 }
 
+// The bead pairs of a chain of N beads into sm.pair (once per kernel).
+template <typename T, int NTM>
+__device__ __forceinline__ void hi_pairs_init(HIShared<T, NTM>& sm, int N)
+{
+    for (int k = threadIdx.x; k < N * (N + 1) / 2; k += blockDim.x) {
+        int bi, bj;
+        hi_untri(k, bi, bj);
+        sm.pair[k] = (uint16_t)((bi << 8) | bj);
+    }
+}
+
 // W's lower tiles into sm.st.tiles from the positions: bead pairs bi >= bj,
 // spread over the threads; a 3 x 3 block per pair (Eq. 2 on the diagonal,
 // Eq. 3 off it). Entries above the diagonal inside a diagonal tile are
 // written too (W is symmetric); rows and columns >= 3N are not written.
+// Entry (p, q) of tile (I, J) = (p >> 2, q >> 2) is element
+// (4 (p & 3) + (q & 3)) kTiles + J NT - J (J + 1) / 2 + I of the tile copy:
+// a part of the row p plus a part of the column q.
 template <typename T, bool FAST, int NTM>
 __device__ __forceinline__ void hi_assemble(HIShared<T, NTM>& sm, int N, T a)
 {
+    constexpr int kT = HIShared<T, NTM>::kTiles;
     const int pairs = N * (N + 1) / 2;
     const int NT = (3 * N + 3) / 4;
+    T* tiles = &sm.st.tiles[0][0];
 #pragma unroll 1
     for (int k = threadIdx.x; k < pairs; k += kHIThreads) {
-        int bi, bj;
-        hi_untri(k, bi, bj);
+        const int bi = sm.pair[k] >> 8, bj = sm.pair[k] & 0xFF;
         T ci = T(1), cd = T(0), d[3] = {T(0), T(0), T(0)};
         if (bi != bj) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) d[c] = sm.pos[3 * bj + c] - sm.pos[3 * bi + c];
             rpy_coef<T, FAST>(d[0], d[1], d[2], a, ci, cd);
         }
+        int row[3], rowm[3], I[3], col[3], colm[3], J[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            const int p = 3 * bi + x;
+            I[x] = p >> 2;
+            row[x] = 4 * (p & 3) * kT + I[x];    // p as the entry's row
+            rowm[x] = (p & 3) * kT + I[x];       // p as the mirrored entry's column
+        }
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+            const int q = 3 * bj + y;
+            J[y] = q >> 2;
+            const int cs = J[y] * NT - J[y] * (J[y] + 1) / 2;
+            col[y] = (q & 3) * kT + cs;
+            colm[y] = 4 * (q & 3) * kT + cs;
+        }
 #pragma unroll
         for (int x = 0; x < 3; ++x)
 #pragma unroll
             for (int y = 0; y < 3; ++y) {
-                const int p = 3 * bi + x, q = 3 * bj + y;
-                if (p < q) continue;                    // diagonal block: lower part (mirrored below)
+                if (bi == bj && x < y) continue;        // diagonal block: lower part (mirrored below)
                 T w = cd * d[x] * d[y];
                 if (x == y) w += ci;
-                const int I = p >> 2, J = q >> 2, t = hi_tile(I, J, NT);
-                sm.st.tiles[4 * (p & 3) + (q & 3)][t] = w;
-                if (I == J && p != q) sm.st.tiles[4 * (q & 3) + (p & 3)][t] = w;
+                tiles[row[x] + col[y]] = w;
+                if (I[x] == J[y] && (bi != bj || x != y)) tiles[rowm[x] + colm[y]] = w;
             }
     }
 }
@@ -573,6 +605,7 @@ hi_replica_kernel(const StepParams p)
     for (int e = threadIdx.x; e < 4 * NTM; e += blockDim.x) {
         sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
     }
+    hi_pairs_init(sm, N);
     __syncthreads();
     HITiles<T, MAXT> tl;
     hi_tiles_init(tl, NT);
@@ -630,6 +663,7 @@ hi_parent_kernel(const StepParams p)
     for (int e = threadIdx.x; e < 4 * NTM; e += blockDim.x) {
         sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
     }
+    hi_pairs_init(sm, N);
     __syncthreads();
     HITiles<T, MAXT> tl;
     hi_tiles_init(tl, NT);
