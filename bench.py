@@ -53,7 +53,7 @@ PHILOX_ROUNDS_PER_BEAD_STEP = 8
 # L2 when it ends, so they are not in its count).
 REPLICA_TRAFFIC_BYTES = (178_089_472 + 855_967_232 + 134_258_688 + 488_113_408) / 2
 REPLICA_TRAFFIC_AT = ("fene_1024x_n100_r64_planar_wi5", 10_000)
-HI_TRAFFIC_BYTES = 4_716_544 + 858_368
+HI_TRAFFIC_BYTES = 4_601_344 + 793_600
 HI_TRAFFIC_AT = ("collapsed_hi_128x_n50_r50_shear30", 1500)
 COLLAPSED_TRAFFIC_BYTES = 32_545_280 + 958_208
 COLLAPSED_TRAFFIC_AT = ("collapsed_1024x_n50_r50_shear30", 3000)
