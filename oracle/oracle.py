@@ -21,6 +21,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bd_oracle.c")
 _LIB = os.path.join(_HERE, "libbdoracle.so")
+# A prebuilt oracle library to load instead (the planted-mistake tests point
+# this at copies of the oracle with one mistake compiled in).
+_LIB_OVERRIDE = os.environ.get("BD_ORACLE_LIB")
 
 ISF, TSF, RSF = 0, 1, 2
 S_MIN_DEFAULT = 1e-3
@@ -28,6 +31,8 @@ S_MIN_DEFAULT = 1e-3
 
 def build(force: bool = False) -> str:
     """Compile bd_oracle.c with gcc (OpenMP over chains) into libbdoracle.so."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "bd_oracle.h"))):
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]

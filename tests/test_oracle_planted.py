@@ -1,0 +1,121 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (a dropped
+term, a wrong sign, index or operand, a transposed tensor), compiles the copy,
+and runs, against it, the pin that should catch it (one test of
+``tests/test_oracle_*.py``, in a subprocess that loads the copy through
+``BD_ORACLE_LIB``). The case passes when that pin fails. The committed oracle
+is untouched: the mistakes exist only in temporary copies.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+
+# (name, original source text, planted text, pin that must fail)
+PLANTED = [
+    # Philox4x32-10 (Salmon et al., SC'11, Sec. 4)
+    ("philox_wrong_word", "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi1 ^ c3 ^ k0;",
+     "test_oracle_noise.py::test_philox_matches_curand_over_two_counter_rounds[0]"),
+    ("philox_key_bump", "k1 += W1;", "k1 += W0;",
+     "test_oracle_noise.py::test_philox_matches_curand_over_two_counter_rounds[0]"),
+    ("uniform_not_open", "return ((double)x + 0.5) * (1.0 / 4294967296.0);",
+     "return ((double)x + 1.0) * (1.0 / 4294967296.0);",
+     "test_oracle_noise.py::test_uniform_open_interval_endpoints"),
+    # Box-Muller normals for the random displacement of Eq. 1
+    ("box_muller_radius", "double rho0 = sqrt(-2.0 * log(u0));", "double rho0 = sqrt(-log(u0));",
+     "test_oracle_noise.py::test_normals_are_standard_normal"),
+    ("box_muller_reused_angle", "xi[2] = rho1 * cos(2.0 * ORA_PI * u3);", "xi[2] = rho1 * cos(2.0 * ORA_PI * u1);",
+     "test_oracle_noise.py::test_normals_are_standard_normal"),
+    ("exp1_sign", "return -log(ora_uniform(x[0]));", "return log(ora_uniform(x[0]));",
+     "test_oracle_noise.py::test_exp1_thresholds_are_unit_exponential"),
+    # spring laws
+    ("fene_dropped_H", "double s = 1.0 - H * q2 / b;", "double s = 1.0 - q2 / b;",
+     "test_oracle_model.py::test_fene_force_is_gradient_of_potential"),
+    ("harmonic_not_unit_vector", "coef = q > 0.0 ? H * (q - r0) / q : 0.0;", "coef = q > 0.0 ? H * (q - r0) : 0.0;",
+     "test_oracle_collapsed.py::test_zero_noise_step_moves_beads_down_the_potential_gradient"),
+    ("vwf_constants_swapped", "f = ch->vwf_fb * x + ch->vwf_fa * x / s;", "f = ch->vwf_fa * x + ch->vwf_fb * x / s;",
+     "test_oracle_vwf.py::test_zero_noise_step_is_minus_grad_u"),
+    ("vwf_disulfide_reacts", "return ch->spring != ORA_SPRING_VWF || i % 2 == 0;", "return 1;",
+     "test_oracle_vwf.py::test_only_a2_domains_unfold"),
+    # Lennard-Jones cohesion (Sec. II)
+    ("lj_factor", "const double dUdr_over_r = 12.0 * ch->lj_u * (x6 - x6 * x6) / rr;",
+     "const double dUdr_over_r = 6.0 * ch->lj_u * (x6 - x6 * x6) / rr;",
+     "test_oracle_collapsed.py::test_zero_noise_step_moves_beads_down_the_potential_gradient"),
+    # Eq. 1 (free draining) and the flows
+    ("diffusivity", "const double D = 0.25, kT = 1.0;\n    const int N = ch->n_beads;\n    double kappa[9];\n    ora_flow_gradient",
+     "const double D = 0.5, kT = 1.0;\n    const int N = ch->n_beads;\n    double kappa[9];\n    ora_flow_gradient",
+     "test_oracle_model.py::test_free_bead_noise_amplitude"),
+    ("spring_reaction_sign", "if (i > 0)     fb -= F[3 * (i - 1) + d];", "if (i > 0)     fb += F[3 * (i - 1) + d];",
+     "test_oracle_model.py::test_zero_noise_rouse_modes_decay_exactly"),
+    ("shear_transposed", "case ORA_FLOW_SHEAR:    kappa[0 * 3 + 2] = rate; break;",
+     "case ORA_FLOW_SHEAR:    kappa[2 * 3 + 0] = rate; break;",
+     "test_oracle_model.py::test_shear_advection_direction"),
+    # RPY tensor (Eqs. 2-3), its factor and the HI step
+    ("rpy_far_coefficient", "cd = pre * (1.0 - 2.0 * a * a / rr);", "cd = pre * (1.0 - 2.0 * a * a / (3.0 * rr));",
+     "test_oracle_hi.py::test_contact_mobilities"),
+    ("rpy_overlap_coefficient", "ci = pre * (r / (2.0 * a)) * (8.0 / 3.0 - 3.0 * r / (4.0 * a));",
+     "ci = pre * (r / (2.0 * a)) * (8.0 / 3.0 - 3.0 * r / (8.0 * a));",
+     "test_oracle_hi.py::test_divergence_free"),
+    ("noise_transposed_factor",
+     "for (int q = 0; q <= p; ++q) noise[p] += Lc[p * n + q] * xi[q];",
+     "for (int q = p; q < n; ++q) noise[p] += Lc[q * n + p] * xi[q];",
+     "test_oracle_hi.py::test_noise_covariance_is_2_D_dt"),
+    ("hi_drift_without_mobility", "for (int q = 0; q < n; ++q) drift[p] += W[p * n + q] * Fb[q];",
+     "for (int q = 0; q < n; ++q) drift[p] += (p == q ? 1.0 : 0.0) * Fb[q];",
+     "test_oracle_hi.py::test_zero_noise_drift_is_mobility_times_force"),
+    # the estimator and the kinetics
+    ("rsf_counts_the_parent", "const double fr = rsum[i] / R;", "const double fr = rsum[i] / (R + 1);",
+     "test_oracle_method.py::test_identical_noise_replicas_reproduce_parent"),
+    ("bell_sign", "*lam += ch->k0 * exp(f * ch->dx) * dT;", "*lam += ch->k0 * exp(-f * ch->dx) * dT;",
+     "test_oracle_method.py::test_bell_constant_force_survival_closed_form"),
+    # the pathwise tangent
+    ("tangent_db_sign", "*dc_db = -ch->H * ch->H * q2 / (ch->b * ch->b * s * s);",
+     "*dc_db = ch->H * ch->H * q2 / (ch->b * ch->b * s * s);",
+     "test_oracle_tangent.py::test_tangent_matches_common_random_number_finite_differences[1]"),
+    ("force_tangent_dropped_factor",
+     "const double dc = dcq * 2.0 * qdq + dcH * dH + dcb * db;\n    for (int d = 0; d < 3; ++d) dF[d]",
+     "const double dc = dcq * qdq + dcH * dH + dcb * db;\n    for (int d = 0; d < 3; ++d) dF[d]",
+     "test_oracle_tangent.py::test_tangent_matches_common_random_number_finite_differences[0]"),
+    ("tension_tangent_dropped_division", "return dc * q + c * qdq / q;", "return dc * q + c * qdq;",
+     "test_oracle_tangent.py::test_tangent_matches_common_random_number_finite_differences[0]"),
+]
+
+
+@pytest.mark.parametrize("name,orig,planted,pin", PLANTED, ids=[p[0] for p in PLANTED])
+def test_planted_mistake_fails_its_pin(tmp_path, name, orig, planted, pin):
+    src = open(os.path.join(ORACLE, "bd_oracle.c")).read()
+    assert src.count(orig) == 1, f"{name}: the original text must occur once"
+    shutil.copy(os.path.join(ORACLE, "bd_oracle.h"), tmp_path / "bd_oracle.h")
+    (tmp_path / "bd_oracle.c").write_text(src.replace(orig, planted))
+    lib = str(tmp_path / "libbdoracle_planted.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", lib,
+                    str(tmp_path / "bd_oracle.c"), "-lm"], check=True)
+    env = dict(os.environ, BD_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", pin)], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    tail = (r.stdout + r.stderr)[-2000:]
+    # exit code 1: the pin ran and failed (not a collection or usage error)
+    assert r.returncode == 1 and " failed" in r.stdout, f"{name}: {pin} did not catch it\n{tail}"
+
+
+def test_unplanted_copy_passes_the_pins(tmp_path):
+    # the control: a copy built and loaded the same way, without a mistake, passes
+    shutil.copy(os.path.join(ORACLE, "bd_oracle.h"), tmp_path / "bd_oracle.h")
+    shutil.copy(os.path.join(ORACLE, "bd_oracle.c"), tmp_path / "bd_oracle.c")
+    lib = str(tmp_path / "libbdoracle_copy.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", lib,
+                    str(tmp_path / "bd_oracle.c"), "-lm"], check=True)
+    pins = sorted({p[3] for p in PLANTED})
+    env = dict(os.environ, BD_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                        *[os.path.join(ROOT, "tests", p) for p in pins]], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, (r.stdout + r.stderr)[-2000:]
+    assert " passed" in r.stdout and " failed" not in r.stdout
