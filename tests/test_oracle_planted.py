@@ -74,6 +74,31 @@ PLANTED = [
      "test_oracle_method.py::test_identical_noise_replicas_reproduce_parent"),
     ("bell_sign", "*lam += ch->k0 * exp(f * ch->dx) * dT;", "*lam += ch->k0 * exp(-f * ch->dx) * dT;",
      "test_oracle_method.py::test_bell_constant_force_survival_closed_form"),
+    ("threshold_last_not_first", "if (thr_on && *first_thr < 0 && f >= ch->f_c) *first_thr = step;",
+     "if (thr_on && f >= ch->f_c) *first_thr = step;",
+     "test_oracle_method.py::test_threshold_events_recount_from_window_profiles"),
+    ("tsf_normalisation", "const double ft = tsum[i] / S;", "const double ft = tsum[i] / (S + 1);",
+     "test_oracle_method.py::test_run_matches_procedure_written_out"),
+    ("isf_interval", "(p->bell_mask >> ORA_ISF) & 1, ch, f[i], p->dt,",
+     "(p->bell_mask >> ORA_ISF) & 1, ch, f[i], S * p->dt,",
+     "test_oracle_method.py::test_bell_isf_hazard_at_equilibrium_matches_quadrature"),
+    ("replica_noise_step_offset",
+     "(uint32_t)(t + s), cid, &xi[3 * i]);\n                    nover += ora_em_step(ch, p->dt, p->s_min, rk, xi);",
+     "(uint32_t)(t + s + 1), cid, &xi[3 * i]);\n                    nover += ora_em_step(ch, p->dt, p->s_min, rk, xi);",
+     "test_oracle_method.py::test_identical_noise_replicas_reproduce_parent"),
+    ("replicas_not_respawned",
+     "double* rk = rep + 3 * (size_t)N * (k - 1);\n                memcpy(rk, parent, sizeof(double) * 3 * (size_t)N);",
+     "double* rk = rep + 3 * (size_t)N * (k - 1);",
+     "test_oracle_method.py::test_run_matches_procedure_written_out"),
+    # Eq. 5 and R_GZ (Sec. III)
+    ("eq5_laboratory_frame", "const double d = fabs((rk[3 * i + j] - ck[j]) - (parent[3 * i + j] - cp[j]));",
+     "const double d = fabs(rk[3 * i + j] - parent[3 * i + j]);",
+     "test_oracle_conformation.py::test_hookean_per_bead_difference_matches_exact_gaussian_expectation"),
+    ("eq5_mean_over_springs", "dbar[(w * NR + repc_off[c] + k - 1) * 3 + j] = dsum[j] / N;",
+     "dbar[(w * NR + repc_off[c] + k - 1) * 3 + j] = dsum[j] / (N - 1);",
+     "test_oracle_conformation.py::test_two_beads_reduce_to_half_the_bond_change"),
+    ("rgz_sample_variance", "return sqrt(s2 / N);", "return sqrt(s2 / (N - 1));",
+     "test_oracle_conformation.py::test_rgz_of_a_straight_chain_along_z"),
     # the pathwise tangent
     ("tangent_db_sign", "*dc_db = -ch->H * ch->H * q2 / (ch->b * ch->b * s * s);",
      "*dc_db = ch->H * ch->H * q2 / (ch->b * ch->b * s * s);",
