@@ -7,6 +7,7 @@ and runs, against it, the pin that should catch it (one test of
 ``BD_ORACLE_LIB``). The case passes when that pin fails. The committed oracle
 is untouched: the mistakes exist only in temporary copies.
 """
+import concurrent.futures as cf
 import os
 import shutil
 import subprocess
@@ -112,35 +113,54 @@ PLANTED = [
 ]
 
 
-@pytest.mark.parametrize("name,orig,planted,pin", PLANTED, ids=[p[0] for p in PLANTED])
-def test_planted_mistake_fails_its_pin(tmp_path, name, orig, planted, pin):
-    src = open(os.path.join(ORACLE, "bd_oracle.c")).read()
-    assert src.count(orig) == 1, f"{name}: the original text must occur once"
-    shutil.copy(os.path.join(ORACLE, "bd_oracle.h"), tmp_path / "bd_oracle.h")
-    (tmp_path / "bd_oracle.c").write_text(src.replace(orig, planted))
-    lib = str(tmp_path / "libbdoracle_planted.so")
+def _build(tmp, name, source):
+    d = os.path.join(tmp, name)
+    os.makedirs(d)
+    shutil.copy(os.path.join(ORACLE, "bd_oracle.h"), os.path.join(d, "bd_oracle.h"))
+    with open(os.path.join(d, "bd_oracle.c"), "w") as fh:
+        fh.write(source)
+    lib = os.path.join(d, "libbdoracle_planted.so")
     subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", lib,
-                    str(tmp_path / "bd_oracle.c"), "-lm"], check=True)
-    env = dict(os.environ, BD_ORACLE_LIB=lib)
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", pin)], cwd=ROOT, env=env,
-                       capture_output=True, text=True, timeout=600)
-    tail = (r.stdout + r.stderr)[-2000:]
+                    os.path.join(d, "bd_oracle.c"), "-lm"], check=True)
+    return lib
+
+
+def _run_pins(lib, pins, extra=()):
+    # one thread per pin process: the cases run side by side
+    env = dict(os.environ, BD_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", *extra,
+                           *[os.path.join(ROOT, "tests", p) for p in pins]], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=900)
+
+
+@pytest.fixture(scope="module")
+def planted_results(tmp_path_factory):
+    """Every planted case compiled and its pin run, in parallel: name -> (returncode, output)."""
+    src = open(os.path.join(ORACLE, "bd_oracle.c")).read()
+    tmp = str(tmp_path_factory.mktemp("planted"))
+
+    def one(case):
+        name, orig, planted, pin = case
+        if src.count(orig) != 1:
+            return name, (None, f"the original text occurs {src.count(orig)} times")
+        r = _run_pins(_build(tmp, name, src.replace(orig, planted)), [pin], extra=("-x",))
+        return name, (r.returncode, (r.stdout + r.stderr)[-2000:])
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return dict(ex.map(one, PLANTED))
+
+
+@pytest.mark.parametrize("name,pin", [(p[0], p[3]) for p in PLANTED], ids=[p[0] for p in PLANTED])
+def test_planted_mistake_fails_its_pin(planted_results, name, pin):
+    rc, out = planted_results[name]
+    assert rc is not None, f"{name}: {out}"
     # exit code 1: the pin ran and failed (not a collection or usage error)
-    assert r.returncode == 1 and " failed" in r.stdout, f"{name}: {pin} did not catch it\n{tail}"
+    assert rc == 1 and " failed" in out, f"{name}: {pin} did not catch it\n{out}"
 
 
 def test_unplanted_copy_passes_the_pins(tmp_path):
     # the control: a copy built and loaded the same way, without a mistake, passes
-    shutil.copy(os.path.join(ORACLE, "bd_oracle.h"), tmp_path / "bd_oracle.h")
-    shutil.copy(os.path.join(ORACLE, "bd_oracle.c"), tmp_path / "bd_oracle.c")
-    lib = str(tmp_path / "libbdoracle_copy.so")
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", lib,
-                    str(tmp_path / "bd_oracle.c"), "-lm"], check=True)
-    pins = sorted({p[3] for p in PLANTED})
-    env = dict(os.environ, BD_ORACLE_LIB=lib)
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
-                        *[os.path.join(ROOT, "tests", p) for p in pins]], cwd=ROOT, env=env,
-                       capture_output=True, text=True, timeout=900)
+    lib = _build(str(tmp_path), "control", open(os.path.join(ORACLE, "bd_oracle.c")).read())
+    r = _run_pins(lib, sorted({p[3] for p in PLANTED}))
     assert r.returncode == 0, (r.stdout + r.stderr)[-2000:]
     assert " passed" in r.stdout and " failed" not in r.stdout
