@@ -169,7 +169,9 @@ typedef struct {
  * launch shapes, allocates the device state and sets every parent to
  * init_pos (float64 [sum N][3], host or device; any frame) at step 0 with its
  * replicas spawned from it. Cites Sec. II (problem set-up). *out receives the
- * context, or NULL on failure. */
+ * context, or NULL on failure. Positions are not checked for finiteness: a
+ * NaN or infinite coordinate propagates into that chain's results (other
+ * chains are unaffected) and never faults. */
 bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out);
 
 /* Replica spawn (Sec. II): replicas 1..N_R of every chain <- parent. Also
