@@ -34,8 +34,12 @@
  *   updates of a window; hazard of a window force held constant over the
  *   window; first passage when the integrated hazard reaches an Exp(1) draw.
  *
- * Every function here is pinned by physics or by published values in the
- * CPU part of the test-suite.
+ * Every function here is pinned in the CPU part of the test-suite: by the
+ * physics (closed forms, exact Euler laws, stationary densities), by values
+ * the paper prints, and Philox by an independent implementation of its
+ * definition (the CUDA toolkit's host-side generator). Planted-mistake tests
+ * compile copies of this file with one plausible error each and check that
+ * its pin fails.
  */
 #include "bd_oracle.h"
 

@@ -7,7 +7,9 @@ library never imports it, and the two share no code. Inputs come from
 method's arithmetic); everything the oracle computes is its own.
 
 Every oracle function is pinned in ``tests/test_oracle_*.py`` against values
-the physics or the published Philox definition fix.
+the physics and the paper fix, and Philox against an independent
+implementation (the CUDA toolkit's host-side generator);
+``tests/test_oracle_planted.py`` checks that the pins catch planted mistakes.
 """
 from __future__ import annotations
 
