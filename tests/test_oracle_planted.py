@@ -48,6 +48,11 @@ PLANTED = [
     ("lj_factor", "const double dUdr_over_r = 12.0 * ch->lj_u * (x6 - x6 * x6) / rr;",
      "const double dUdr_over_r = 6.0 * ch->lj_u * (x6 - x6 * x6) / rr;",
      "test_oracle_collapsed.py::test_zero_noise_step_moves_beads_down_the_potential_gradient"),
+    ("lj_includes_bonded_neighbours", "for (int j = i + 2; j < N; ++j) {", "for (int j = i + 1; j < N; ++j) {",
+     "test_oracle_collapsed.py::test_zero_noise_step_moves_beads_down_the_potential_gradient"),
+    ("vwf_odd_springs_are_a2", "if (i % 2 == 0) {\n        double s = 1.0 - x * x / (ch->vwf_xmax * ch->vwf_xmax);",
+     "if (i % 2 == 1) {\n        double s = 1.0 - x * x / (ch->vwf_xmax * ch->vwf_xmax);",
+     "test_oracle_vwf.py::test_zero_noise_step_is_minus_grad_u"),
     # Eq. 1 (free draining) and the flows
     ("diffusivity", "const double D = 0.25, kT = 1.0;\n    const int N = ch->n_beads;\n    double kappa[9];\n    ora_flow_gradient",
      "const double D = 0.5, kT = 1.0;\n    const int N = ch->n_beads;\n    double kappa[9];\n    ora_flow_gradient",
@@ -67,6 +72,12 @@ PLANTED = [
      "for (int q = 0; q <= p; ++q) noise[p] += Lc[p * n + q] * xi[q];",
      "for (int q = p; q < n; ++q) noise[p] += Lc[q * n + p] * xi[q];",
      "test_oracle_hi.py::test_noise_covariance_is_2_D_dt"),
+    ("cholesky_wrong_row", "for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];",
+     "for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[i * n + k];",
+     "test_oracle_hi.py::test_tensor_positive_definite_and_factor"),
+    ("rpy_diagonal_block", "for (int k = 0; k < 9; ++k) blk[k] = (k % 4 == 0) ? 1.0 : 0.0;",
+     "for (int k = 0; k < 9; ++k) blk[k] = (k % 4 == 0) ? 0.75 : 0.0;",
+     "test_oracle_hi.py::test_vanishing_radius_is_free_draining"),
     ("hi_drift_without_mobility", "for (int q = 0; q < n; ++q) drift[p] += W[p * n + q] * Fb[q];",
      "for (int q = 0; q < n; ++q) drift[p] += (p == q ? 1.0 : 0.0) * Fb[q];",
      "test_oracle_hi.py::test_zero_noise_drift_is_mobility_times_force"),
