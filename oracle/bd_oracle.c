@@ -27,7 +27,7 @@
  *     either a threshold rupture force or the Bell rate k = k0 exp(f dx / kT)
  *     with the survival integral exp(-int k dt).
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent (the same readings hold on the GPU side):
  *   FENE law F = H Q / (1 - H Q^2 / b); noise from Philox4x32-10 keyed by
  *   (bead, slot | stream << 24, step, chain) with key = seed; Box-Muller;
  *   FENE floor s_min on 1 - H Q^2 / b; TSF samples taken after each of the S

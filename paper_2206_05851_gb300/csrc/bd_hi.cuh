@@ -678,7 +678,7 @@ hi_parent_kernel(const StepParams p)
     const bool isf_bell = (p.bell_mask & BD_CRIT_ISF) != 0;
     const T fc = (T)ch.f_c;
     const double k0dt = ch.k0 * p.dt, dxs = ch.dx;
-    T tsf = mine ? (T)p.tsf_acc[m] : T(0);
+    double tsf = mine ? p.tsf_acc[m] : 0.0;     // the time-average sum in float64
     double haz = 0.0, rem = mine ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0;
     const bool quiet = ch.spring == BD_SPRING_VWF && (i & 1);   // disulfide bonds do not unfold
     bool thr_done = !mine || quiet || p.first_thr[CRIT_Q_ISF * M + m] >= 0;
@@ -703,7 +703,7 @@ hi_parent_kernel(const StepParams p)
             const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
             const T f = harmonic ? rest_law_tension<T, FAST>(qx, qy, qz, (i & 1) == 0, k.H, kl, k.smin)
                                  : spring_tension<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin);
-            tsf += f;
+            tsf += (double)f;
             if (isf_thr && !thr_done && f >= fc) {
                 thr_done = true;
                 p.first_thr[CRIT_Q_ISF * M + m] = t + 1;
@@ -719,8 +719,8 @@ hi_parent_kernel(const StepParams p)
         if (++s_in == p.S) {
             s_in = 0;
             if (mine) {
-                p.tsf_hist[w * M + m] = (double)tsf / (double)p.S;
-                tsf = T(0);
+                p.tsf_hist[w * M + m] = tsf / (double)p.S;
+                tsf = 0.0;
                 if (isf_bell) {
                     const double lam = p.lam[CRIT_Q_ISF * M + m] + haz;
                     p.lam[CRIT_Q_ISF * M + m] = lam;
@@ -734,7 +734,7 @@ hi_parent_kernel(const StepParams p)
     __syncthreads();
     hi_store_bonds(sm, state, N);
     if (mine) {
-        p.tsf_acc[m] = (double)tsf;
+        p.tsf_acc[m] = tsf;
         if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += haz;
     }
     if (floored) atomicAdd(p.overext + c, (unsigned long long)floored);

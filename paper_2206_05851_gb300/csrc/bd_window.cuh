@@ -211,9 +211,11 @@ parent_kernel(const StepParams p)
     T qx[L], qy[L], qz[L];
     load_bonds<T, L>(qx, qy, qz, state, lc);
 
-    // per-spring sampling state of this lane's springs; the Bell hazard is
-    // accumulated in float64 whatever the integration precision
-    T tsf[L];
+    // per-spring sampling state of this lane's springs; the time-average sum
+    // and the Bell hazard are accumulated in float64 whatever the integration
+    // precision (a float32 sum over a 1500-step window would lose about three
+    // digits of the TSF before the division)
+    double tsf[L];
     double haz[L], rem[L];
     // quiet: springs outside the criteria (the disulfide bonds of a vWF chain)
     uint32_t thr_done = 0, bell_done = 0, quiet = 0;
@@ -222,7 +224,7 @@ parent_kernel(const StepParams p)
         const int i = lc.bead0 + j;
         const int64_t m = ch.spr_off + i;
         const bool v = active && i < nb;
-        tsf[j] = v ? (T)p.tsf_acc[m] : T(0);
+        tsf[j] = v ? p.tsf_acc[m] : 0.0;
         haz[j] = 0.0;
         rem[j] = v ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0;
         if (ch.spring == BD_SPRING_VWF && (i & 1)) quiet |= 1u << j;
@@ -252,7 +254,7 @@ parent_kernel(const StepParams p)
                 if (i < nb) {
                     const T f = LJ ? rest_law_tension<T, FAST>(qx[j], qy[j], qz[j], (i & 1) == 0, k.H, kl, k.smin)
                                    : spring_tension<T, FAST>(qx[j], qy[j], qz[j], k.H, k.Hinvb, k.smin);
-                    tsf[j] += f;
+                    tsf[j] += (double)f;
                     if (isf_thr && !(thr_done & (1u << j)) && f >= fc) {
                         thr_done |= 1u << j;
                         p.first_thr[CRIT_Q_ISF * M + ch.spr_off + i] = t + 1;
@@ -275,8 +277,8 @@ parent_kernel(const StepParams p)
                     const int i = lc.bead0 + j;
                     if (i < nb) {
                         const int64_t m = ch.spr_off + i;
-                        p.tsf_hist[w * M + m] = (double)tsf[j] / (double)p.S;
-                        tsf[j] = T(0);
+                        p.tsf_hist[w * M + m] = tsf[j] / (double)p.S;
+                        tsf[j] = 0.0;
                         if (isf_bell) {
                             const double lam = p.lam[CRIT_Q_ISF * M + m] + haz[j];
                             p.lam[CRIT_Q_ISF * M + m] = lam;
@@ -296,7 +298,7 @@ parent_kernel(const StepParams p)
             const int i = lc.bead0 + j;
             if (i < nb) {
                 const int64_t m = ch.spr_off + i;
-                p.tsf_acc[m] = (double)tsf[j];
+                p.tsf_acc[m] = tsf[j];
                 if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += haz[j];
             }
         }

@@ -1,15 +1,19 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
 the same seeded inputs and the same Philox draws.
 
-Tolerances (relative, per chain, centre-of-mass frame): 1e-10 in FP64 mode,
-1e-4 in FP32 mode; event steps equal in FP64 mode; FP32 event steps equal
-except at near-ties of the force with the threshold (|f - f_c| < 1e-3 f_c).
+Tolerances (relative, per chain, centre-of-mass frame; force profiles per
+chain and window): 1e-10 in FP64 mode, 1e-4 in FP32 mode; event steps equal
+in FP64 mode; FP32 event steps equal except at near-ties, checked one by one
+against the oracle's own force or hazard at the earlier of the two steps
+(parity_events.py: |f - f_c| < 1e-4 f_c; the Bell hazard within the float32
+log-hazard tolerance of its Exp(1) level).
 """
 import math
 
 import numpy as np
 import pytest
 
+import parity_events as PE
 from oracle import oracle as O
 from paper_2206_05851_gb300 import bdra
 from paper_2206_05851_gb300 import inputs as I
@@ -88,13 +92,8 @@ def compare_states(g, r, chains, tol):
         assert rel_err_chains(rep, O.com_frame(r["rep"], sizes), sizes) <= tol
 
 
-def compare_profiles(g, r, tol):
-    for key in ("rsf", "tsf"):
-        a, b = g[key], r[key]
-        assert a.shape == b.shape
-        if a.size:
-            err = np.abs(a - b).max() / np.abs(b).max()
-            assert err <= tol, f"{key} rel err {err:.3e}"
+def compare_profiles(g, r, chains, tol):
+    PE.check_profiles(g, r, chains, tol)
 
 
 def compare_events_exact(g, r):
@@ -103,27 +102,13 @@ def compare_events_exact(g, r):
     np.testing.assert_allclose(g["haz"], r["lam"], rtol=1e-9, atol=1e-300)
 
 
-def compare_events_fp32(g, r, chains, S):
-    """Window criteria: equal except at near-ties; ISF: nearly all equal."""
-    fc = np.concatenate([[c.f_c] * (c.n_beads - 1) for c in chains])
-    for q, key in ((O.TSF, "tsf"), (O.RSF, "rsf")):
-        prof = r[key]
-        for m in np.nonzero(g["first_thr"][q] != r["first_thr"][q])[0]:
-            last = max(g["first_thr"][q][m], r["first_thr"][q][m])
-            upto = prof.shape[0] if last < 0 else last // S
-            near = np.abs(prof[:upto, m] - fc[m]) < 1e-3 * fc[m]
-            assert near.any(), f"criterion {q} spring {m}: threshold event differs, no near-tie"
-    n_isf = max(1, int((r["first_thr"][O.ISF] >= 0).sum()))
-    diff = int((g["first_thr"][O.ISF] != r["first_thr"][O.ISF]).sum())
-    assert diff <= max(1, n_isf // 20)
-    # Bell hazards: k0 exp(dx f) turns a relative force error e into a hazard
-    # error of about dx f e, so compare the log-hazard (the log-survival
-    # exponent) to 1e-4 of its size, plus an absolute floor.
-    pos = r["lam"] > 0
-    lg, lr = np.log(g["haz"][pos]), np.log(r["lam"][pos])
-    bad = np.abs(lg - lr) > 1e-4 * np.abs(lr) + 2e-3
-    assert not bad.any(), (np.nonzero(pos)[0][bad][:5], lg[bad][:5], lr[bad][:5])
-    np.testing.assert_array_equal(g["haz"][~pos], r["lam"][~pos])
+def compare_events_fp32(g, r, chains, dt, S, seed, pos0, thr=7, bell=7, chain_ids=None, cols=None):
+    """Event steps equal the oracle's except at near-ties (each checked at its
+    step against the oracle's own force or hazard); hazards in log space."""
+    replay = PE.OracleReplay(chains, dt, S, seed, pos0, thr, bell, chain_ids)
+    counts = PE.compare_events_fp32(g, r, chains, S, replay, cols=cols)
+    PE.compare_hazards_fp32(g["haz"] if cols is None else g["haz"][:, cols], r["lam"])
+    return counts
 
 
 def c1_like(rate_wi=2.0, n=20, R=16, b=50.0):
@@ -159,7 +144,7 @@ def test_single_chain_1000_steps(prec):
     g = gpu_run(wl.chains, wl.dt, wl.window_steps, [1000], wl.seed, pos0, prec)
     r = ora_run(wl.chains, wl.dt, wl.window_steps, 1000, wl.seed, pos0)
     compare_states(g, r, wl.chains, TOL[prec])
-    compare_profiles(g, r, TOL[prec])
+    compare_profiles(g, r, wl.chains, TOL[prec])
     assert g["info"].overextensions == int(r["overext"].sum()) == 0
 
 
@@ -186,11 +171,11 @@ def test_ragged_batch_split_calls(prec):
     g = gpu_run(chains, dt, S, steps, seed, pos0, prec)
     r = ora_run(chains, dt, S, 140, seed, pos0)
     compare_states(g, r, chains, TOL[prec])
-    compare_profiles(g, r, TOL[prec])
+    compare_profiles(g, r, chains, TOL[prec])
     if prec == bdra.BD_PREC_FP64:
         compare_events_exact(g, r)
     else:
-        compare_events_fp32(g, r, chains, S)
+        compare_events_fp32(g, r, chains, dt, S, seed, pos0)
 
 
 def _event_chains(extreme: bool):
@@ -223,7 +208,8 @@ def test_events_and_kinetics(prec):
         compare_events_exact(g, r)
     else:
         assert r["overext"].sum() == 0
-        compare_events_fp32(g, r, chains, S)
+        counts = compare_events_fp32(g, r, chains, dt, S, seed, pos0)
+        assert counts["thr_equal"] > 20 and counts["bell_equal"] > 10, counts
     # the event list is the kinetic state, in (chain, spring, criterion, kind) order
     ev = g["events"]
     so = I.spring_offsets(chains)
@@ -293,7 +279,7 @@ def test_edge_cases(prec):
     g = gpu_run(ch, 1e-3, 1, [5, 0, 7], 1, pos0, prec)
     r = ora_run(ch, 1e-3, 1, 12, 1, pos0)
     compare_states(g, r, ch, TOL[prec])
-    compare_profiles(g, r, TOL[prec])
+    compare_profiles(g, r, ch, TOL[prec])
     # maximum chain length (512 beads, 16 springs per lane, 32 lanes per slot)
     ch = [I.Chain(n_beads=512, n_replicas=3, spring=I.SPRING_FENE, flow=I.FLOW_SHEAR, b=100.0,
                   rate=0.01)]
@@ -301,7 +287,7 @@ def test_edge_cases(prec):
     g = gpu_run(ch, 1e-3, 4, [12], 2, pos0, prec, thr=0, bell=0)
     r = ora_run(ch, 1e-3, 4, 12, 2, pos0, thr=0, bell=0)
     compare_states(g, r, ch, TOL[prec])
-    compare_profiles(g, r, TOL[prec])
+    compare_profiles(g, r, ch, TOL[prec])
 
 
 @pytest.mark.parametrize("R", [1000, 4096])
@@ -315,7 +301,7 @@ def test_many_replica_groups(R):
         g = gpu_run(ch, 1e-3, 10, [30], 6, pos0, prec, thr=0, bell=0)
         r = ora_run(ch, 1e-3, 10, 30, 6, pos0, thr=0, bell=0)
         compare_states(g, r, ch, TOL[prec])
-        compare_profiles(g, r, TOL[prec])
+        compare_profiles(g, r, ch, TOL[prec])
 
 
 def test_capacity_and_state_errors():
@@ -378,26 +364,12 @@ def test_device_and_host_buffers_agree():
     ctx.close()
 
 
-def test_full_size_sampled_parity():
-    # The benchmark's launch configuration: 1024 chains, N = 100, 64 replicas,
-    # planar elongation Wi = 5, FP32 integration. Sampled chains are re-run
-    # on their own by the oracle (same chain ids in the noise counter).
-    wl = I.planar_1024(n_steps=200)
-    pos0 = I.initial_positions(wl)
-    g = gpu_run(wl.chains, wl.dt, wl.window_steps, [200], wl.seed, pos0, bdra.BD_PREC_FP32,
-                thr=wl.thr_mask, bell=wl.bell_mask, want_all=False)
-    sample = [0, 517, 1023]
-    sub = [wl.chains[c] for c in sample]
-    sub_pos = np.concatenate([pos0[100 * c:100 * (c + 1)] for c in sample])
-    r = ora_run(sub, wl.dt, wl.window_steps, 200, wl.seed, sub_pos, thr=wl.thr_mask,
-                bell=wl.bell_mask, chain_ids=sample)
-    got = np.concatenate([g["pos"][100 * c:100 * (c + 1)] for c in sample])
-    assert rel_err_chains(got, O.com_frame(r["pos"], [100] * 3), [100] * 3) <= 1e-4
-    rs = np.concatenate([g["rsf"][:, 99 * c:99 * (c + 1)] for c in sample], axis=1)
-    assert np.abs(rs - r["rsf"]).max() / np.abs(r["rsf"]).max() <= 1e-4
-
-
-def _sampled(wl, g, pos0, sample, n, autotuned=False):
+def _sampled(wl, g, pos0, sample, n):
+    """Sampled chains of a full-size float32 run against the oracle, which
+    re-runs them alone with their global chain ids in the noise counter:
+    positions per chain, RSF / TSF per (chain, window), Bell hazards in log
+    space, and every event step equal up to the near-ties the oracle's own
+    forces and hazards show."""
     boff, soff = I.bead_offsets(wl.chains), I.spring_offsets(wl.chains)
     sub = [wl.chains[c] for c in sample]
     sub_pos = np.concatenate([pos0[boff[c]:boff[c + 1]] for c in sample])
@@ -407,36 +379,49 @@ def _sampled(wl, g, pos0, sample, n, autotuned=False):
     got = np.concatenate([g["pos"][boff[c]:boff[c + 1]] for c in sample])
     assert rel_err_chains(got, O.com_frame(r["pos"], nb), nb) <= 1e-4
     cols = np.concatenate([np.arange(soff[c], soff[c + 1]) for c in sample])
-    for key in ("rsf", "tsf"):
-        assert np.abs(g[key][:, cols] - r[key]).max() / np.abs(r[key]).max() <= 1e-4, key
-    # Bell hazards in log space (R14), zero where the oracle's are zero
-    lam = g["haz"][:, cols]
-    pos = r["lam"] > 0
-    assert (np.abs(np.log(lam[pos]) - np.log(r["lam"][pos])) <= 1e-4 * np.abs(np.log(r["lam"][pos])) + 2e-3).all()
-    np.testing.assert_array_equal(lam[~pos], r["lam"][~pos])
-    return r
+    PE.check_profiles({k: g[k][:, cols] for k in ("rsf", "tsf")}, r, sub, 1e-4)
+    counts = compare_events_fp32(g, r, sub, wl.dt, wl.window_steps, wl.seed, sub_pos,
+                                 wl.thr_mask, wl.bell_mask, chain_ids=sample, cols=cols)
+    return r, counts
+
+
+def _full_size(wl, n, autotune=False):
+    ctx = bdra.Context(wl.chains, wl.dt, wl.window_steps, wl.seed, I.initial_positions(wl),
+                       precision=bdra.BD_PREC_FP32, max_windows=n // wl.window_steps + 1,
+                       thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=_stream())
+    if autotune:
+        ctx.autotune(probe_steps=8)
+    ctx.step(n)
+    nw = n // wl.window_steps
+    g = dict(pos=ctx.positions(False),
+             rsf=np.array([ctx.replica_average(w) for w in range(nw)]).reshape(nw, ctx.M),
+             tsf=np.array([ctx.time_average(w) for w in range(nw)]).reshape(nw, ctx.M))
+    g["haz"], g["first_thr"], g["first_bell"] = ctx.kinetics()
+    ctx.close()
+    return g
+
+
+def test_full_size_sampled_parity():
+    # The benchmark's launch configuration: 1024 chains, N = 100, 64 replicas,
+    # planar elongation Wi = 5, FP32 integration, 1000 steps. Sampled chains
+    # are re-run on their own by the oracle (same chain ids in the noise
+    # counter).
+    wl = I.planar_1024(n_steps=1000)
+    g = _full_size(wl, 1000)
+    _sampled(wl, g, I.initial_positions(wl), [0, 517, 1023], 1000)
 
 
 def test_full_size_uneven_batch_sampled_parity():
     # C3 launch configuration: 4096 chains of 20..500 beads and 8..128
     # replicas, shear and elongation, one persistent launch per step variant,
-    # shapes picked by the autotuner; FP32, 200 steps; sampled chains of
+    # shapes picked by the autotuner; FP32, 1000 steps; sampled chains of
     # different shapes re-run alone by the oracle
-    wl = I.uneven_4096(n_steps=200)
-    pos0 = I.initial_positions(wl)
-    ctx = bdra.Context(wl.chains, wl.dt, wl.window_steps, wl.seed, pos0, precision=bdra.BD_PREC_FP32,
-                       max_windows=3, thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=_stream())
-    ctx.autotune(probe_steps=8)
-    ctx.step(200)
-    g = dict(pos=ctx.positions(False),
-             rsf=np.array([ctx.replica_average(w) for w in range(2)]),
-             tsf=np.array([ctx.time_average(w) for w in range(2)]))
-    g["haz"], _, _ = ctx.kinetics()
-    ctx.close()
+    wl = I.uneven_4096(n_steps=1000)
+    g = _full_size(wl, 1000, autotune=True)
     sizes = [(c.n_beads, c.n_replicas) for c in wl.chains]
     sample = [int(np.argmax([n for n, _ in sizes])), int(np.argmin([n for n, _ in sizes])),
               int(np.argmax([r for _, r in sizes])), 1234, 4095]
-    _sampled(wl, g, pos0, sample, 200)
+    _sampled(wl, g, I.initial_positions(wl), sample, 1000)
 
 
 def test_full_size_bell_workload_sampled_parity():
@@ -444,10 +429,8 @@ def test_full_size_bell_workload_sampled_parity():
     # uniaxial Wi = 10, Bell and threshold criteria on ISF, TSF and RSF; FP32,
     # 1000 steps; sampled chains against the oracle
     wl = I.bell_16384(n_steps=1000)
-    pos0 = I.initial_positions(wl)
-    g = gpu_run(wl.chains, wl.dt, wl.window_steps, [1000], wl.seed, pos0, bdra.BD_PREC_FP32,
-                thr=wl.thr_mask, bell=wl.bell_mask, want_all=False)
-    _sampled(wl, g, pos0, [0, 8191, 16383], 1000)
+    g = _full_size(wl, 1000)
+    _sampled(wl, g, I.initial_positions(wl), [0, 8191, 16383], 1000)
 
 
 @pytest.mark.parametrize("prec", PRECS)
