@@ -8,6 +8,14 @@ spring constant H). Its backward pass is ``bd_adjoint``: pathwise derivatives
 with the noise held fixed, parent checkpoints every K steps. Everything here
 is argument marshalling; the forward and backward work runs in the library's
 kernels, on torch's current CUDA stream.
+
+Device memory. The run's context (state, histories, parent checkpoints and,
+after the first backward, the adjoint's replay buffers: about 24 GB for 256
+chains of 200 beads) is held by the autograd graph only until its backward
+pass, which releases it, the way autograd frees saved tensors. A second
+backward through the same graph then raises; set ``RunSpec.retain_run`` to
+keep the context for repeated backward passes (it is then released with the
+graph). ``release_run(output)`` frees it early without a backward pass.
 """
 from __future__ import annotations
 
@@ -37,6 +45,7 @@ class RunSpec:
     precision: int = bdra.BD_PREC_FP32
     s_min: float = 1e-3
     flags: int = 0
+    retain_run: bool = False    # keep the device context after backward (repeated backward passes)
 
 
 class _ReplicaAveragedRun(torch.autograd.Function):
@@ -60,6 +69,7 @@ class _ReplicaAveragedRun(torch.autograd.Function):
         ls = torch.empty((len(chains), 3), dtype=torch.float64, device=dev)
         bdra.bd_detect_events(run.ptr, ev, 6 * run.M, ls)
         ctx.run = run
+        ctx.retain_run = spec.retain_run
         ctx.n_windows = W
         ctx.param_device, ctx.param_dtype = params.device, params.dtype
         return rsf, ls[:, 2].contiguous()
@@ -67,13 +77,21 @@ class _ReplicaAveragedRun(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g_rsf: Optional[torch.Tensor], g_ls: Optional[torch.Tensor]):
         run = ctx.run
+        if run is None or not run.ptr:
+            raise RuntimeError("the run's device context was released after its first backward pass "
+                               "(or by release_run); set RunSpec.retain_run for repeated backward passes")
         dev = torch.device("cuda", torch.cuda.current_device())
         C = len(run.chains)
         gr = None if g_rsf is None else g_rsf.to(dev, torch.float64).contiguous()
         gl = None if g_ls is None else g_ls.to(dev, torch.float64).contiguous()
         out = torch.empty((C, 3), dtype=torch.float64, device=dev)
         bdra.bd_adjoint(run.ptr, C, run.M, ctx.n_windows, gr, gl, out)
-        return out.to(ctx.param_device, ctx.param_dtype), None
+        grad = out.to(ctx.param_device, ctx.param_dtype)
+        if not ctx.retain_run:
+            # bd_destroy synchronises the context's stream before it frees
+            run.close()
+            ctx.run = None
+        return grad, None
 
 
 def replica_averaged_run(params: torch.Tensor, spec: RunSpec):
@@ -85,6 +103,16 @@ def replica_averaged_run(params: torch.Tensor, spec: RunSpec):
     if spec.checkpoint_steps <= 0:
         raise ValueError("checkpoint_steps must be > 0 for the backward pass")
     return _ReplicaAveragedRun.apply(params, spec)
+
+
+def release_run(output: torch.Tensor) -> None:
+    """Free the device context behind an output of replica_averaged_run now
+    (for outputs that will not be differentiated)."""
+    node = output.grad_fn
+    run = getattr(node, "run", None) if node is not None else None
+    if run is not None:
+        run.close()
+        node.run = None
 
 
 def chain_params(chains: Sequence) -> torch.Tensor:

@@ -250,6 +250,55 @@ def test_autograd_function_backward_is_the_adjoint():
     assert_close(params.grad.numpy(), oracle_grad(chains, r, dr, G1, None, DT, S), 1e-10, "rsf only")
 
 
+def test_autograd_releases_device_memory():
+    """Forward and backward through the autograd function twice, on chains
+    shaped like the 256-chain adjoint workload (N = 200, 32 replicas,
+    checkpoints every 1000 steps) but fewer: the device memory of the run's
+    context (state, histories, checkpoints, the adjoint's replay buffers) is
+    returned after each backward pass, and a second backward through a
+    released graph raises instead of touching freed memory."""
+    import gc
+    import torch
+    from paper_2206_05851_gb300.autograd import RunSpec, chain_params, release_run, replica_averaged_run
+    wl = I.adjoint_256(n_steps=2000, n_chains=16)
+    pos0 = I.initial_positions(wl)
+    spec = RunSpec(wl.chains, wl.dt, wl.window_steps, wl.n_steps, wl.seed, pos0,
+                   I.ADJOINT_CHECKPOINT_STEPS, precision=F32)
+
+    def free_bytes():
+        gc.collect()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        return torch.cuda.mem_get_info()[0]
+
+    base = free_bytes()
+    grads = []
+    for _ in range(2):
+        params = chain_params(wl.chains).requires_grad_(True)
+        rsf, ls = replica_averaged_run(params, spec)
+        assert free_bytes() < base              # the context holds its buffers until backward
+        loss = rsf[:, 99].sum() + ls.sum()
+        loss.backward(retain_graph=True)
+        grads.append(params.grad.clone())
+        assert free_bytes() >= base - (16 << 20), "context not released by backward"
+        with pytest.raises(RuntimeError, match="released"):
+            loss.backward()
+        del rsf, ls, loss
+    np.testing.assert_array_equal(grads[0].numpy(), grads[1].numpy())
+    assert free_bytes() >= base - (16 << 20)
+    # kept for a second backward on request; released early on request
+    params = chain_params(wl.chains).requires_grad_(True)
+    rsf, ls = replica_averaged_run(params, dataclasses.replace(spec, retain_run=True))
+    rsf.sum().backward(retain_graph=True)
+    g1 = params.grad.clone()
+    params.grad = None
+    rsf.sum().backward()
+    np.testing.assert_array_equal(params.grad.numpy(), g1.numpy())
+    release_run(rsf)
+    assert free_bytes() >= base - (16 << 20)
+    del rsf, ls
+
+
 def test_adjoint_workload_full_size_sampled_chains():
     """256 FENE chains, N=200, 32 replicas, Wi=5, 2e4 steps, checkpoints every 1000
     steps, float32: the mid-chain RSF averaged over the windows plus the
