@@ -12,11 +12,18 @@ Philox4x32-10 generator (called through its C API, on the CPU). Its output
 layout was established by comparison: the 64-bit seed is the key (low word
 first), and output block b (four words) is the generator evaluated at the
 counter (r, j, 0) with r, j = divmod(b, 65536), r a 64-bit pair of counter
-words 0-1 and j counter word 2; the generator offset counts words.
+words 0-1 and j counter word 2; the generator offset counts words. That
+layout never reaches counter word 3, the chain id of the method's counter;
+a second independent implementation, Triton's Philox4x32 (its own source,
+run by its interpreter on the CPU, ``philox_triton_ref.py``), takes all four
+words and pins the oracle there.
 """
 import ctypes
 import ctypes.util
+import io
 import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -82,6 +89,36 @@ def test_philox_matches_curand_at_large_counters(first_block):
     want = _curand_blocks(seed, first_block, 64)
     got = O.philox_many(_counters_of(first_block, 64), [seed & 0xFFFFFFFF, seed >> 32])
     assert np.array_equal(got, want)
+
+
+def _triton_blocks(ctr, seed):
+    pytest.importorskip("triton")
+    buf = io.BytesIO()
+    np.save(buf, np.ascontiguousarray(ctr, dtype=np.uint32))
+    script = os.path.join(os.path.dirname(os.path.abspath(__file__)), "philox_triton_ref.py")
+    r = subprocess.run([sys.executable, script], input=buf.getvalue() + int(seed).to_bytes(8, "little"),
+                       capture_output=True, timeout=600)
+    assert r.returncode == 0, r.stderr.decode()[-2000:]
+    return np.load(io.BytesIO(r.stdout))
+
+
+def test_philox_matches_triton_on_all_four_counter_words():
+    # random counters (every word, word 3 included) and the method's own
+    # counters: (bead, slot | stream << 24, step, chain) with chain ids up to
+    # 16383 in word 3, for two keys
+    rng = np.random.default_rng(17)
+    rand = rng.integers(0, 2**32, size=(1024, 4), dtype=np.uint64).astype(np.uint32)
+    meth = np.zeros((1024, 4), dtype=np.uint32)
+    meth[:, 0] = rng.integers(0, 512, size=1024)
+    meth[:, 1] = rng.integers(0, 4097, size=1024) | (rng.integers(0, 2, size=1024) << 24)
+    meth[:, 2] = rng.integers(0, 250_000, size=1024)
+    meth[:, 3] = rng.integers(1, 16384, size=1024)
+    ctr = np.concatenate([rand, meth])
+    assert (ctr[:, 3] != 0).mean() > 0.99
+    for seed in (0x0123456789ABCDEF, 5):
+        want = _triton_blocks(ctr, seed)
+        got = O.philox_many(ctr, [seed & 0xFFFFFFFF, seed >> 32])
+        assert np.array_equal(got, want)
 
 
 def test_philox_batch_matches_single():

@@ -25,6 +25,14 @@ PLANTED = [
      "test_oracle_noise.py::test_philox_matches_curand_over_two_counter_rounds[0]"),
     ("philox_key_bump", "k1 += W1;", "k1 += W0;",
      "test_oracle_noise.py::test_philox_matches_curand_over_two_counter_rounds[0]"),
+    # counter word 3 (the chain id) entering the rounds wrongly: invisible to
+    # the cuRAND layout, whose word 3 is always 0
+    ("philox_word3_into_word1", "uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];",
+     "uint32_t c0 = ctr[0], c1 = ctr[1] ^ ctr[3], c2 = ctr[2], c3 = 0;",
+     "test_oracle_noise.py::test_philox_matches_triton_on_all_four_counter_words"),
+    ("philox_word3_scaled", "uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];",
+     "uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3] * 3u;",
+     "test_oracle_noise.py::test_philox_matches_triton_on_all_four_counter_words"),
     ("uniform_not_open", "return ((double)x + 0.5) * (1.0 / 4294967296.0);",
      "return ((double)x + 1.0) * (1.0 / 4294967296.0);",
      "test_oracle_noise.py::test_uniform_open_interval_endpoints"),
