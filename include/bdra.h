@@ -40,7 +40,8 @@
  *     order, x y z). Spring profiles are float64 [M] with
  *     M = sum_c (N_c - 1), chain c's springs starting at sum_{c'<c} (N_c' - 1).
  *   - Noise: Philox4x32-10 (Salmon et al., SC'11) with key = (seed low word,
- *     seed high word) and counter (bead, slot | stream << 24, step, chain);
+ *     seed high word) and counter (bead, slot | stream << 24, step, chain),
+ *     chain = bd_config.chain_id_base + the chain's index in the context;
  *     slot 0 is the parent, slots 1..R the replicas; stream 0 drives Eq. 1,
  *     stream 1 the Exp(1) thresholds of the Bell first-passage test. Results
  *     therefore do not depend on the launch shape.
@@ -143,6 +144,14 @@ typedef struct {
     int32_t checkpoint_steps;     /* 0: no adjoint; else K, a multiple of window_steps:
                                      bd_step keeps the parent conformation every K
                                      steps so that bd_adjoint can recompute the run */
+    int32_t chain_id_base;        /* noise-counter chain word of chain 0 (>= 0): chain c
+                                     draws with chain id chain_id_base + c. A workload
+                                     split into contiguous chain ranges over several
+                                     contexts (one per GPU, Sec. II: the replica sets
+                                     are independent simulations) draws, with each
+                                     range's first global index here, exactly the noise
+                                     of the whole workload in one context. 0 for a
+                                     context that holds the whole workload */
 } bd_config;
 
 /* A first event of one spring under one criterion. */
@@ -341,6 +350,16 @@ bd_status bd_probe_fp32_fma(void* stream, double* flops_per_s);
  * roots per second). Same conventions. */
 bd_status bd_probe_fp64_fma(void* stream, double* flops_per_s);
 bd_status bd_probe_mufu(void* stream, double* ops_per_s);
+
+/* Measured instruction-issue rate of the current device (no counterpart in
+ * the paper: the denominator of the issue roofline of the free-draining and
+ * collapsed-chain replica kernels, whose work is a mix of integer and
+ * float32 instructions): independent chains of two float32 FMAs and one
+ * three-input logic operation, full occupancy, no memory traffic (about
+ * 5 ms), so that no single pipe but issue binds. *lane_instr_per_s (host)
+ * receives thread-instructions per second for the whole device (loop control
+ * not counted: low by at most 3%). Same conventions as the probes above. */
+bd_status bd_probe_issue(void* stream, double* lane_instr_per_s);
 
 /* Largest n_springs bd_compact_events_noalloc accepts (its fixed scratch
  * holds one count per 256 springs: 32 KiB of device memory). */

@@ -52,7 +52,7 @@ class bd_config(ctypes.Structure):
                 ("bell_mask", ctypes.c_int32), ("max_windows", ctypes.c_int64),
                 ("s_min", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("lanes_hint", ctypes.c_int32), ("layout_hint", ctypes.c_int32),
-                ("checkpoint_steps", ctypes.c_int32)]
+                ("checkpoint_steps", ctypes.c_int32), ("chain_id_base", ctypes.c_int32)]
 
 
 class bd_event(ctypes.Structure):
@@ -107,6 +107,7 @@ def load() -> ctypes.CDLL:
         "bd_probe_fp32_fma": ([vp, P(ctypes.c_double)], st),
         "bd_probe_fp64_fma": ([vp, P(ctypes.c_double)], st),
         "bd_probe_mufu": ([vp, P(ctypes.c_double)], st),
+        "bd_probe_issue": ([vp, P(ctypes.c_double)], st),
         "bd_philox_normals": ([ctypes.c_uint64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp], st),
         "bd_compact_events_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.c_int32, vp,
                                        ctypes.c_int64, vp, vp], st),
@@ -159,7 +160,7 @@ def make_config(chains: Sequence, dt: float, window_steps: int, seed: int, preci
                 max_windows: int, thr_mask: int = 0, bell_mask: int = 0, flags: int = 0,
                 s_min: float = 1e-3, stream: Optional[int] = None,
                 lanes_hint: int = 0, layout_hint: int = 0,
-                checkpoint_steps: int = 0) -> Tuple[bd_config, ctypes.Array]:
+                checkpoint_steps: int = 0, chain_id_base: int = 0) -> Tuple[bd_config, ctypes.Array]:
     """Build a bd_config (and the chain array it points to) from chain records
     with the fields of bd_chain_desc."""
     arr = (bd_chain_desc * len(chains))(*[
@@ -172,7 +173,8 @@ def make_config(chains: Sequence, dt: float, window_steps: int, seed: int, preci
               for c in chains])
     cfg = bd_config(len(chains), int(window_steps), arr, float(dt), int(seed), int(precision),
                     int(flags), int(thr_mask), int(bell_mask), int(max_windows), float(s_min),
-                    stream, int(lanes_hint), int(layout_hint), int(checkpoint_steps))
+                    stream, int(lanes_hint), int(layout_hint), int(checkpoint_steps),
+                    int(chain_id_base))
     return cfg, arr
 
 
@@ -317,6 +319,14 @@ def bd_probe_mufu(stream: Optional[int] = None) -> float:
     return r.value
 
 
+def bd_probe_issue(stream: Optional[int] = None) -> float:
+    """Measured instruction-issue rate (mixed float32 / integer stream) of the
+    current device, thread-instructions per second."""
+    r = ctypes.c_double(0.0)
+    _check(load().bd_probe_issue(stream, ctypes.byref(r)))
+    return r.value
+
+
 NOALLOC_MAX_SPRINGS = 1 << 20
 
 
@@ -348,11 +358,12 @@ class Context:
                  init_pos, precision: int = BD_PREC_FP32, max_windows: int = 1024,
                  thr_mask: int = 0, bell_mask: int = 0, flags: int = 0,
                  s_min: float = 1e-3, stream: Optional[int] = None, lanes_hint: int = 0,
-                 layout_hint: int = 0, checkpoint_steps: int = 0):
+                 layout_hint: int = 0, checkpoint_steps: int = 0, chain_id_base: int = 0):
         self.chains = list(chains)
         self.cfg, self._arr = make_config(self.chains, dt, window_steps, seed, precision,
                                           max_windows, thr_mask, bell_mask, flags, s_min,
-                                          stream, lanes_hint, layout_hint, checkpoint_steps)
+                                          stream, lanes_hint, layout_hint, checkpoint_steps,
+                                          chain_id_base)
         self.ptr = bd_create(self.cfg, init_pos)
         self.M = sum(c.n_beads - 1 for c in self.chains)
         self.n_beads = sum(c.n_beads for c in self.chains)

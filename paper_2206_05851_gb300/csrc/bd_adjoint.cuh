@@ -176,7 +176,8 @@ __device__ __forceinline__ bool parent_lane(const StepParams& p, ParentLane& out
     const bool active = (sw < P) && (sw < pw.count);
     out.chain = p.parent_items[pw.first + (active ? sw : 0)];
     const int nb = p.chains[out.chain].N - 1;
-    out.lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, active, 0u, (uint32_t)out.chain);
+    out.lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, active, 0u,
+                       (uint32_t)out.chain + p.chain_base);
     return true;
 }
 
@@ -192,7 +193,7 @@ __device__ __forceinline__ const uint4* parent_table(const StepParams& p, uint4*
     for (int e = lane; e < P * G * L; e += 32) {
         const int s2 = e / (G * L);
         const int c2 = p.parent_items[pw.first + min(s2, pw.count - 1)];
-        tab[e] = PhiloxSplit::bead_part((uint32_t)(e - s2 * G * L), (uint32_t)c2, p.rk0, p.rk1);
+        tab[e] = PhiloxSplit::bead_part((uint32_t)(e - s2 * G * L), (uint32_t)c2 + p.chain_base, p.rk0, p.rk1);
     }
     __syncwarp();
     return tab + (sw < P ? sw : 0) * G * L;
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_replica_window_kernel(const A
     const int seg = sw < P ? lane - sw * G : 0;
     const int kglob = it.rep_begin + sw + 1;
     const uint32_t key = (p.flags & BD_FLAG_IDENTICAL_NOISE) ? 0u : (uint32_t)kglob;
-    const LaneCtx lc = make_lane(seg, G, L, lane, nb, active, key, (uint32_t)it.chain);
+    const LaneCtx lc = make_lane(seg, G, L, lane, nb, active, key, (uint32_t)it.chain + p.chain_base);
     const int64_t w = a.w_batch0 + blockIdx.y;
     const int64_t tw = w * p.S;
     const int64_t row = a.state_bonds * 3;                  // one step of repbuf
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_replica_window_kernel(const A
     {
         uint4* tab = tab_all[threadIdx.x >> 5];
         for (int b = lane; b < G * L; b += 32)
-            tab[b] = PhiloxSplit::bead_part((uint32_t)b, (uint32_t)it.chain, p.rk0, p.rk1);
+            tab[b] = PhiloxSplit::bead_part((uint32_t)b, (uint32_t)it.chain + p.chain_base, p.rk0, p.rk1);
         __syncwarp();
         StepConst<T, FAST> k;
         k.load(ch, p);

@@ -299,6 +299,8 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
         return fail(ctx, BD_E_INVALID, "unknown flags");
     if (cfg->checkpoint_steps < 0 || (cfg->checkpoint_steps > 0 && cfg->checkpoint_steps % cfg->window_steps))
         return fail(ctx, BD_E_INVALID, "checkpoint_steps must be 0 or a positive multiple of window_steps");
+    if (cfg->chain_id_base < 0 || (int64_t)cfg->chain_id_base + cfg->n_chains - 1 > INT32_MAX)
+        return fail(ctx, BD_E_INVALID, "chain_id_base must be >= 0 with chain_id_base + n_chains - 1 <= 2^31 - 1");
     if (cfg->layout_hint < 0 || cfg->layout_hint > 2)
         return fail(ctx, BD_E_INVALID, "layout_hint must be 0, 1 or 2");
     if (cfg->layout_hint == 2 && cfg->precision != BD_PREC_FP32)
@@ -531,6 +533,7 @@ StepParams base_params(const bd_ctx* ctx)
     p.n_rep = ctx->n_rep;
     p.bpart_stride = ctx->bpart_stride;
     p.n_chains = ctx->cfg.n_chains;
+    p.chain_base = (uint32_t)ctx->cfg.chain_id_base;
     p.tsf_hist = ctx->d_tsf;
     p.tsf_acc = ctx->d_tsf_acc;
     p.lam = ctx->d_lam;
@@ -1153,7 +1156,7 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
         if (cfg->checkpoint_steps > 0) BD_TRY(adj_plan(ctx));
         {
             cudaError_t e = run_exp1(ctx->d_chains, ctx->d_spring_chain, M, ctx->rk0[0], ctx->rk1[0],
-                                     ctx->d_exp1, ctx->stream);
+                                     (uint32_t)cfg->chain_id_base, ctx->d_exp1, ctx->stream);
             if (e != cudaSuccess) { cudaGetLastError(); s = fail(ctx, BD_E_CUDA, "exp1: %s", cudaGetErrorString(e)); goto failed; }
         }
         BD_TRY(reset_kinetics(ctx));

@@ -92,7 +92,8 @@ struct StepParams {
     double* dbead_part;         // [win_ring][bpart_stride][3] per-group per-bead sums
     double* rgz;                // [max_windows][n_chains] parent's z radius of gyration
     int64_t n_rep, bpart_stride;
-    int32_t n_chains, pad_conf;
+    int32_t n_chains;
+    uint32_t chain_base;        // noise-counter chain word of chain 0 (chain c: chain_base + c)
     int64_t part_stride, M;
     int32_t win_ring, pad_ring;  // windows one chunk touches (started or ended) + 1
     int64_t t0, n_steps;

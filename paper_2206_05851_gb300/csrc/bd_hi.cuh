@@ -619,7 +619,7 @@ hi_replica_kernel(const StepParams p)
 #pragma unroll 1
     for (int64_t t = p.t0; t < t_end; ++t) {
         if (s_in == 0) hi_load_bonds(sm, snap + ((w % p.win_ring) * p.M + ch.spr_off) * 3, N);
-        floored += hi_step<T, FAST, NTM, MAXT>(sm, tl, ch, k, p, N, NT, key, (uint32_t)it.chain, (uint32_t)t,
+        floored += hi_step<T, FAST, NTM, MAXT>(sm, tl, ch, k, p, N, NT, key, (uint32_t)it.chain + p.chain_base, (uint32_t)t,
                                           harmonic, lj);
         if (++s_in == p.S) {
             s_in = 0;
@@ -696,7 +696,7 @@ hi_parent_kernel(const StepParams p)
             // the parent's noise repeat the parent exactly
             hi_load_bonds(sm, row, N);
         }
-        floored += hi_step<T, FAST, NTM, MAXT>(sm, tl, ch, k, p, N, NT, 0u, (uint32_t)c, (uint32_t)t, harmonic, lj);
+        floored += hi_step<T, FAST, NTM, MAXT>(sm, tl, ch, k, p, N, NT, 0u, (uint32_t)c + p.chain_base, (uint32_t)t, harmonic, lj);
         if (mine) {
             const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
             const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];

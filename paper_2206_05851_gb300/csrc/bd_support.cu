@@ -15,9 +15,9 @@ constexpr int kThreads = 256;
 inline int blocks_for(int64_t n) { return (int)((n + kThreads - 1) / kThreads); }
 
 // Exp(1) threshold of spring i, criterion q, chain c: -ln u, u from the
-// Philox stream 1 counter (i, 1 << 24, q, c).
+// Philox stream 1 counter (i, 1 << 24, q, chain_base + c).
 __global__ void exp1_kernel(const ChainDev* chains, const int32_t* spring_chain, int64_t M,
-                            uint32_t k0, uint32_t k1, double* exp1)
+                            uint32_t k0, uint32_t k1, uint32_t chain_base, double* exp1)
 {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
@@ -25,7 +25,7 @@ __global__ void exp1_kernel(const ChainDev* chains, const int32_t* spring_chain,
     const uint32_t i = (uint32_t)(m - chains[c].spr_off);
     for (int q = 0; q < 3; ++q) {
         const uint4 x = philox4x32_10(make_uint4(i, (uint32_t)STREAM_EXP1 << 24, (uint32_t)q,
-                                                 (uint32_t)c), k0, k1);
+                                                 (uint32_t)c + chain_base), k0, k1);
         const double u = ((double)x.x + 0.5) * 2.3283064365386963e-10;
         exp1[q * M + m] = -log(u);
     }
@@ -313,10 +313,10 @@ __global__ void normals_kernel(int64_t n, const uint32_t* ctr, StepParams p, dou
 }  // namespace
 
 cudaError_t run_exp1(const ChainDev* chains, const int32_t* spring_chain, int64_t M, uint32_t k0,
-                     uint32_t k1, double* exp1, cudaStream_t st)
+                     uint32_t k1, uint32_t chain_base, double* exp1, cudaStream_t st)
 {
     if (M == 0) return cudaSuccess;
-    exp1_kernel<<<blocks_for(M), kThreads, 0, st>>>(chains, spring_chain, M, k0, k1, exp1);
+    exp1_kernel<<<blocks_for(M), kThreads, 0, st>>>(chains, spring_chain, M, k0, k1, chain_base, exp1);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,7 @@
 namespace bdra {
 
 cudaError_t run_exp1(const ChainDev* chains, const int32_t* spring_chain, int64_t M, uint32_t k0,
-                     uint32_t k1, double* exp1, cudaStream_t st);
+                     uint32_t k1, uint32_t chain_base, double* exp1, cudaStream_t st);
 cudaError_t run_set_bonds(bool f64, const ChainDev* chains, const int32_t* spring_chain, int64_t M,
                           const double* pos, void* state, cudaStream_t st);
 cudaError_t run_spawn(bool f64, const ChainDev* chains, const int32_t* spring_chain, int64_t M,

@@ -104,14 +104,14 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
     const int kglob = it.rep_begin + sw + 1;
     const uint32_t key = (p.flags & BD_FLAG_IDENTICAL_NOISE) ? 0u : (uint32_t)kglob;
     const LaneCtx lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, active, key,
-                                 (uint32_t)it.chain);
+                                 (uint32_t)it.chain + p.chain_base);
     StepConst<T, FAST> k;
     k.load(ch, p);
     LJConst<T> kl;
     if (LJ) kl.load(ch);
     if (TAB) {
         for (int b = lane; b < G * L; b += 32)
-            ptab[b] = PhiloxSplit::bead_part((uint32_t)b, (uint32_t)it.chain, p.rk0, p.rk1);
+            ptab[b] = PhiloxSplit::bead_part((uint32_t)b, (uint32_t)it.chain + p.chain_base, p.rk0, p.rk1);
         __syncwarp();
     }
 
@@ -187,7 +187,7 @@ parent_kernel(const StepParams p)
     const ChainDev ch = p.chains[c];
     const int nb = ch.N - 1;
     const LaneCtx lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, active, 0u,
-                                 (uint32_t)c);
+                                 (uint32_t)c + p.chain_base);
     StepConst<T, FAST> k;
     k.load(ch, p);
     LJConst<T> kl;
@@ -196,7 +196,7 @@ parent_kernel(const StepParams p)
     for (int e = lane; e < P * G * L; e += 32) {
         const int s2 = e / (G * L);
         const int c2 = p.parent_items[pw.first + min(s2, pw.count - 1)];
-        ptab[e] = PhiloxSplit::bead_part((uint32_t)(e - s2 * G * L), (uint32_t)c2, p.rk0, p.rk1);
+        ptab[e] = PhiloxSplit::bead_part((uint32_t)(e - s2 * G * L), (uint32_t)c2 + p.chain_base, p.rk0, p.rk1);
     }
     __syncwarp();
     const uint4* my_tab = ptab + (sw < P ? sw : 0) * G * L;

@@ -241,13 +241,13 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
     const int ka = it.rep_begin + ra + 1, kb = it.rep_begin + rb + 1;
     const bool same = (p.flags & BD_FLAG_IDENTICAL_NOISE) != 0;
     const LaneCtx lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, act_a,
-                                 same ? 0u : (uint32_t)ka, (uint32_t)it.chain);
+                                 same ? 0u : (uint32_t)ka, (uint32_t)it.chain + p.chain_base);
     const uint32_t keyb = same ? 0u : (uint32_t)kb;
     StepConst2 k;
     k.load(ch, p);
     if (TAB) {       // bead parts of the noise counter for every bead a lane of this chain draws
         for (int b = lane; b < G * L; b += 32)
-            ptab[b] = PhiloxSplit::bead_part((uint32_t)b, (uint32_t)it.chain, p.rk0, p.rk1);
+            ptab[b] = PhiloxSplit::bead_part((uint32_t)b, (uint32_t)it.chain + p.chain_base, p.rk0, p.rk1);
         __syncwarp();
     }
 

@@ -53,6 +53,35 @@ def test_header_is_plain_c(tmp_path):
     assert r.returncode == 0, r.stderr
 
 
+def test_binding_structs_match_the_header(tmp_path):
+    # the ctypes mirrors of bd_chain_desc, bd_config, bd_event and bd_info
+    # have the C structs' sizes and field offsets
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = [bdra.bd_chain_desc, bdra.bd_config, bdra.bd_event, bdra.bd_info]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "bdra.h"', 'int main(void) {']
+    for st in structs:
+        lines.append(f'printf("%zu\\n", sizeof({st.__name__}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({st.__name__}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([gcc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = []
+    for st in structs:
+        want.append(ctypes.sizeof(st))
+        want += [getattr(st, f).offset for f, _ in st._fields_]
+    assert got == want
+
+
 def test_every_declared_symbol_is_exported(lib):
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
@@ -104,11 +133,12 @@ def test_bad_chain_rejected_without_device(lib, field, value):
                                 dict(layout_hint=3),
                                 dict(layout_hint=2, precision=bdra.BD_PREC_FP64),
                                 dict(layout_hint=2, lanes_hint=13),
-                                dict(checkpoint_steps=15), dict(checkpoint_steps=-10)])
+                                dict(checkpoint_steps=15), dict(checkpoint_steps=-10),
+                                dict(chain_id_base=-1), dict(chain_id_base=2**31 - 1)])
 def test_bad_config_rejected_without_device(lib, kw):
     ch = I.Chain(n_beads=100, n_replicas=4, spring=I.SPRING_FENE, b=50.0)
-    cfg, _keep = _cfg([ch], **kw)
-    st, ptr = _create(cfg, np.zeros((100, 3)))
+    cfg, _keep = _cfg([ch, ch], **kw)          # two chains: ids base, base + 1
+    st, ptr = _create(cfg, np.zeros((200, 3)))
     assert st == bdra.BD_E_INVALID and ptr is None
 
 
@@ -147,6 +177,7 @@ def test_probe_rejects_null_output(lib):
     assert lib.bd_probe_fp32_fma(None, None) == bdra.BD_E_INVALID
     assert lib.bd_probe_fp64_fma(None, None) == bdra.BD_E_INVALID
     assert lib.bd_probe_mufu(None, None) == bdra.BD_E_INVALID
+    assert lib.bd_probe_issue(None, None) == bdra.BD_E_INVALID
 
 
 def test_binding_fails_loudly_when_library_missing(monkeypatch, tmp_path):
