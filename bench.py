@@ -18,6 +18,7 @@ has) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -86,6 +87,8 @@ def parse():
     ap.add_argument("--no-collapsed", action="store_true")
     ap.add_argument("--no-hi", action="store_true")
     ap.add_argument("--no-vwf", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the uneven-batch and Bell-kinetics lines")
     ap.add_argument("--only-vwf", action="store_true",
                     help="only the vWF line (Table 1 set-up)")
     ap.add_argument("--only-rest", action="store_true",
@@ -170,29 +173,105 @@ class ClockSampler:
 # CPU baseline: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def cpu_baseline(wl, pos0, n_chains=None, n_steps=1000):
+def cpu_baseline(wl, pos0, n_chains=None, n_steps=1000, sample=None, keep=False):
+    """The FP64 oracle timed on the host cores over a bounded sample of the
+    workload: the first `n_chains` chains (or the chain indices `sample`),
+    `n_steps` steps, OpenMP over chains, with the chains' global ids in the
+    noise counter. With keep=True also returns the oracle's results (the
+    reference of errors_vs_oracle)."""
+    import numpy as np
     from oracle import oracle as O
+    from paper_2206_05851_gb300 import inputs as I
     cores = os.cpu_count() or 1
-    n_chains = n_chains or min(cores, wl.n_chains)
-    sub = wl.chains[:n_chains]
-    sub_pos = pos0[:sum(c.n_beads for c in sub)]
+    if sample is None:
+        sample = list(range(min(n_chains or cores, wl.n_chains)))
+    sub = [wl.chains[c] for c in sample]
+    boff = I.bead_offsets(wl.chains)
+    sub_pos = np.concatenate([pos0[boff[c]:boff[c + 1]] for c in sample])
     t = time.perf_counter()
-    O.run(sub, wl.dt, wl.window_steps, n_steps, wl.seed, sub_pos, thr_mask=wl.thr_mask,
-          bell_mask=wl.bell_mask, n_threads=min(cores, n_chains), want_replicas=False,
-          chain_ids=list(range(n_chains)))
+    r = O.run(sub, wl.dt, wl.window_steps, n_steps, wl.seed, sub_pos, thr_mask=wl.thr_mask,
+              bell_mask=wl.bell_mask, n_threads=min(cores, len(sub)), want_replicas=False,
+              chain_ids=list(sample))
     dt = time.perf_counter() - t
     bead_steps = sum(c.n_replicas * c.n_beads for c in sub) * n_steps
-    return {"value": bead_steps / dt, "unit": "bead-steps/s", "cores": min(cores, n_chains),
+    what = (f"first {len(sub)} chains" if list(sample) == list(range(len(sub)))
+            else f"{len(sub)} sampled chains {list(sample)[:8]}{'...' if len(sub) > 8 else ''}")
+    line = {"value": bead_steps / dt, "unit": "bead-steps/s", "cores": min(cores, len(sub)),
             "kind": "oracle",
-            "sample": f"first {n_chains} chains of the workload, {n_steps} steps "
+            "sample": f"{what} of the workload, {n_steps} steps "
                       f"({bead_steps:.3g} bead-steps, {dt:.1f} s wall, FP64, OpenMP over chains)"}
+    return (line, r, sample, sub_pos) if keep else line
 
 
-def make_workload(args):
+def errors_vs_oracle(wl, r, sample, sub_pos, n_steps, sptr):
+    """Each result of a float32 GPU run against the FP64 oracle on the sampled
+    chains (the CPU baseline's sample and run): a context of those chains,
+    with their global chain ids, integrated for the same steps. Positions:
+    per-chain max |difference| / max |position| (centre-of-mass frame); RSF
+    and TSF: per (chain, window) row, max |difference| / row max |force|;
+    Bell log-survival: relative difference per chain and criterion; first
+    events: how many steps are equal."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2206_05851_gb300 import bdra
     from paper_2206_05851_gb300 import inputs as I
-    kw = {"n_chains": args.chains} if args.chains else {}
-    return {"planar_1024": I.planar_1024, "uneven_4096": I.uneven_4096,
-            "bell_16384": I.bell_16384}[args.workload](**kw)
+    sub = [wl.chains[c] for c in sample]
+    contiguous = list(sample) == list(range(sample[0], sample[0] + len(sample)))
+    out = {"sample": f"{len(sub)} chains, {n_steps} steps (the CPU baseline's run)"}
+    if not contiguous:
+        return dict(out, skipped="sample not a contiguous chain range")
+    S = wl.window_steps
+    nw = n_steps // S
+    c = bdra.Context(sub, wl.dt, S, wl.seed, torch.from_numpy(sub_pos).cuda(),
+                     precision=bdra.BD_PREC_FP32, max_windows=nw + 1, thr_mask=wl.thr_mask,
+                     bell_mask=wl.bell_mask, stream=sptr, chain_id_base=int(sample[0]))
+    c.step(n_steps)
+    pos = c.positions(False)
+    rsf = np.array([c.replica_average(w) for w in range(nw)]).reshape(nw, c.M)
+    tsf = np.array([c.time_average(w) for w in range(nw)]).reshape(nw, c.M)
+    haz, ft, fb = c.kinetics()
+    c.close()
+    nb = [ch.n_beads for ch in sub]
+    want = O.com_frame(r["pos"], nb)
+    boff, soff = I.bead_offsets(sub), I.spring_offsets(sub)
+
+    def rows(g, w):
+        worst = 0.0
+        for k in range(len(sub)):
+            a, b = g[:, soff[k]:soff[k + 1]], w[:, soff[k]:soff[k + 1]]
+            worst = max(worst, float((np.abs(a - b).max(axis=1) /
+                                      np.maximum(np.abs(b).max(axis=1), 1e-300)).max()))
+        return worst
+
+    out["positions_max_rel_err"] = max(
+        float(np.abs(pos[boff[k]:boff[k + 1]] - want[boff[k]:boff[k + 1]]).max()
+              / np.abs(want[boff[k]:boff[k + 1]]).max()) for k in range(len(sub)))
+    if nw:
+        out["rsf_max_rel_err"] = rows(rsf, r["rsf"])
+        out["tsf_max_rel_err"] = rows(tsf, r["tsf"])
+    ls_g = np.array([haz[:, soff[k]:soff[k + 1]].sum(axis=1) for k in range(len(sub))])
+    ls_r = np.array([r["lam"][:, soff[k]:soff[k + 1]].sum(axis=1) for k in range(len(sub))])
+    on = ls_r > 0
+    if on.any():
+        out["log_survival_max_rel_err"] = float((np.abs(ls_g - ls_r)[on] / ls_r[on]).max())
+    for kind, g, w in (("threshold", ft, r["first_thr"]), ("bell", fb, r["first_bell"])):
+        ev = (g >= 0) | (w >= 0)
+        out[f"first_{kind}_events"] = {"equal": int(((g == w) & ev).sum()), "total": int(ev.sum())}
+    out["precision"] = "GPU float32 integration (FP64 reductions) vs the FP64 oracle, same Philox draws"
+    return out
+
+
+def make_workload(args, world: int = 1):
+    """The configuration named by --workload, with world x its chain count
+    (one workload that the ranks split)."""
+    from paper_2206_05851_gb300 import inputs as I
+    make = {"planar_1024": I.planar_1024, "uneven_4096": I.uneven_4096,
+            "bell_16384": I.bell_16384}[args.workload]
+    if args.chains or world > 1:
+        base = args.chains or make().n_chains
+        return make(n_chains=base * world)
+    return make()
 
 
 def run_reference(args):
@@ -228,7 +307,7 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def kinetics_summary(ctx, wl, n_steps):
+def kinetics_summary(first_thr, first_bell, chains, thr_mask, bell_mask, n_steps, dt):
     """First events of the timed run per criterion (ISF, TSF, RSF) and kind
     (threshold, Bell): chains with an event, mean and median first-event step
     (mean first time to unfolding, over the chains that ruptured), and the
@@ -236,16 +315,15 @@ def kinetics_summary(ctx, wl, n_steps):
     position along the chain when bead counts differ)."""
     import numpy as np
     from paper_2206_05851_gb300 import inputs as I
-    _, first_thr, first_bell = ctx.kinetics()
-    offs = I.spring_offsets(wl.chains)
-    C = len(wl.chains)
-    same_n = len({c.n_beads for c in wl.chains}) == 1
-    res = {"timed_steps": n_steps, "dt": wl.dt, "chains": C}
+    offs = I.spring_offsets(chains)
+    C = len(chains)
+    same_n = len({c.n_beads for c in chains}) == 1
+    res = {"timed_steps": n_steps, "dt": dt, "chains": C}
     for q, crit in enumerate(("ISF", "TSF", "RSF")):
-        if not ((wl.thr_mask | wl.bell_mask) >> q) & 1:
+        if not ((thr_mask | bell_mask) >> q) & 1:
             continue
         entry = {}
-        for kind, arr, mask in (("threshold", first_thr, wl.thr_mask), ("bell", first_bell, wl.bell_mask)):
+        for kind, arr, mask in (("threshold", first_thr, thr_mask), ("bell", first_bell, bell_mask)):
             if not (mask >> q) & 1:
                 continue
             steps = np.full(C, -1, dtype=np.int64)
@@ -256,10 +334,10 @@ def kinetics_summary(ctx, wl, n_steps):
                 if hit.size:
                     i = hit[np.argmin(row[hit])]
                     steps[c] = row[i]
-                    loc[c] = i if same_n else i / max(wl.chains[c].n_beads - 2, 1)
+                    loc[c] = i if same_n else i / max(chains[c].n_beads - 2, 1)
             ok = steps >= 0
             if same_n:
-                hist = np.bincount(loc[ok].astype(np.int64), minlength=wl.chains[0].n_beads - 1)
+                hist = np.bincount(loc[ok].astype(np.int64), minlength=chains[0].n_beads - 1)
             else:
                 hist = np.histogram(loc[ok], bins=10, range=(0.0, 1.0))[0]
             entry[kind] = {"ruptured": int(ok.sum()), "fraction": float(ok.mean()),
@@ -268,6 +346,156 @@ def kinetics_summary(ctx, wl, n_steps):
                            "location_hist": hist.tolist()}
         res[crit] = entry
     return res
+
+
+def replica_line(wl, pos0, base, chunk, steps, warmup, sptr, autotune, issue_peak, philox_peak,
+                 dist=None, traffic_at=None, keep_ctx=False, warm_chunk=None):
+    """Times `steps` bench steps of `chunk` integration steps each, plus event
+    detection, of the free-draining workload `wl` (this rank's chains, global
+    chain index of the first: `base`), after `warmup` untimed steps of
+    `warm_chunk` integration steps, the timed region between barriers and
+    synchronisations with L2 flushed between timed steps. Returns the
+    whole-job throughput (all ranks' bead-steps over the slowest rank's time)
+    and the replica kernel's roofline against the measured issue rate and
+    the measured Philox-round ceiling."""
+    import numpy as np
+    import torch
+    from paper_2206_05851_gb300 import bdra, shard
+    warm_chunk = warm_chunk or chunk
+    S = wl.window_steps
+    total_windows = (warmup * warm_chunk + steps * chunk) // S + 1
+    stream = torch.cuda.current_stream()
+    ctx = bdra.Context(wl.chains, wl.dt, S, wl.seed, torch.from_numpy(pos0).cuda(),
+                       precision=bdra.BD_PREC_FP32, max_windows=total_windows,
+                       thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=sptr, chain_id_base=base)
+    if autotune:
+        ctx.autotune(probe_steps=32)
+    units_chunk = wl.bead_steps(chunk)
+    ev_cap = 6 * ctx.M
+    ev_buf = torch.zeros(ev_cap * 24, dtype=torch.uint8, device="cuda")
+    ls_buf = torch.zeros((len(wl.chains), 3), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def bench_step(n):
+        ctx.step(n)
+        return bdra.bd_detect_events(ctx.ptr, ev_buf, ev_cap, ls_buf)
+
+    for _ in range(warmup):
+        bench_step(warm_chunk)
+    # the timed region integrates the workload itself: from the initial coils at step 0
+    ctx.set_positions(torch.from_numpy(pos0).cuda(), 0)
+    torch.cuda.synchronize()
+    bdra.bd_enable_timing(ctx.ptr, True)
+    bdra.bd_kernel_times(ctx.ptr)
+    launches0 = ctx.info().kernel_launches
+    clocks = ClockSampler()
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        flush.zero_()                 # evict L2 between timed steps
+        n_events = bench_step(chunk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = ctx.info().kernel_launches - launches0    # our kernels only
+    (par_ms, rep_ms), (par_n, rep_n) = bdra.bd_kernel_times(ctx.ptr)
+    bdra.bd_enable_timing(ctx.ptr, False)
+    t_max = shard.max_over_ranks(t_ms, dist, "cuda")
+    units_all = float(shard.sum_counts(np.array([float(units_chunk * steps)]), dist, "cuda")[0])
+    value = shard.whole_job_rate(units_all, t_max / 1e3)
+
+    # roofline of the dominant kernel (replica kernel), measured live
+    rep_units = units_chunk * steps
+    achieved = ALGO_OPS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3)
+    derived = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
+            "unit": "T lane-instructions/s", "frac": achieved / issue_peak,
+            "traffic": REPLICA_TRAFFIC_BYTES if traffic_at and (wl.name, chunk) == traffic_at else None,
+            "traffic_unit": "bytes per launch (ncu capture)",
+            "kernel": "replica kernel (planner's float32 tile)", "avg_launch_ms": rep_ms / max(rep_n, 1),
+            "launches": rep_n, "share_of_step": rep_ms / t_ms,
+            "peak_basis": "measured: bd_probe_issue (mixed float32 / integer instruction issue, "
+                          "full occupancy) on this GPU before the timed region",
+            "peak_derived": derived / 1e12, "frac_of_derived": achieved / derived,
+            "ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP}
+    if clk:
+        roof["frac_of_derived_at_measured_clock"] = achieved / (SMS * LANES_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6)
+    # the same kernel against the measured ceiling of its dominant work
+    rounds = PHILOX_ROUNDS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3)
+    roof_philox = {"bound": "alu (Philox rounds: 32x32->64 multiplies + XOR3)", "achieved": rounds / 1e12,
+                   "peak": philox_peak / 1e12, "unit": "T rounds/s", "frac": rounds / philox_peak,
+                   "peak_basis": "measured by bd_probe_philox_rounds on this GPU before the timed region",
+                   "rounds_per_bead_step": PHILOX_ROUNDS_PER_BEAD_STEP}
+    out = {"value": value, "unit": "bead-steps/s", "ms_per_step": t_max / steps,
+           "config": {"workload": wl.name, "chains_per_gpu": len(wl.chains),
+                      "beads": [min(c.n_beads for c in wl.chains), max(c.n_beads for c in wl.chains)],
+                      "replicas": sorted({c.n_replicas for c in wl.chains}),
+                      "dt": wl.dt, "window_steps": S, "steps_per_bench_step": chunk,
+                      "timed_integration_steps": chunk * steps,
+                      "criteria": f"threshold mask {wl.thr_mask}, Bell mask {wl.bell_mask} (1 ISF, 2 TSF, 4 RSF)",
+                      "precision": "FP32 integrate, FP64 reduce", "autotuned": bool(autotune),
+                      "l2": "flushed (256 MB write) between timed steps"},
+           "gpu_launches": int(launches), "events_detected_rank": int(n_events),
+           "parent_kernel_share": par_ms / t_ms}
+    if clk:
+        out["clocks"] = clk
+    out["roofline"] = roof
+    out["roofline_philox"] = roof_philox
+    if keep_ctx:
+        return out, ctx
+    ctx.close()
+    return out
+
+
+def oracle_sample_steps(wl, n_chains, bead_steps=1.0e9):
+    """Steps of an oracle sample of the first n_chains chains worth about
+    `bead_steps` bead-steps (about 5 s on 16 host cores), whole windows."""
+    per_step = sum(c.n_replicas * c.n_beads for c in wl.chains[:n_chains])
+    S = wl.window_steps
+    return max(S, int(bead_steps / per_step) // S * S)
+
+
+def batch_line(name, sptr, issue_peak, philox_peak, args):
+    """The batched benchmark configurations beside the main one, each its own
+    timed run on this GPU, with its kinetics, CPU oracle baseline and errors
+    against the oracle:
+    - uneven_4096: 4096 chains of 20..500 beads and 8..128 replicas, half in
+      shear and half in uniaxial elongation, one persistent launch per step
+      variant in one CUDA graph per chunk, shapes picked by the autotuner;
+      10^4 steps (the configuration's whole run) in one timed step;
+    - bell_16384: 16384 chains of 50 beads, start-up uniaxial elongation at
+      Wi = 10 from equilibrium, Bell and threshold criteria on ISF, TSF and
+      RSF; 10^5 of the configuration's 2.5 10^5 steps (4 timed steps of
+      2.5 10^4), enough for most chains' first rupture; rupture times and
+      locations per criterion."""
+    from paper_2206_05851_gb300 import inputs as I
+    if name == "uneven_4096":
+        wl = I.uneven_4096()
+        chunk, steps, autotune = 10_000, 1, True
+    else:
+        wl = I.bell_16384()
+        chunk, steps, autotune = 25_000, 4, False
+    pos0 = I.initial_positions(wl)
+    line, ctx = replica_line(wl, pos0, 0, chunk, steps, 1, sptr, autotune, issue_peak, philox_peak,
+                             keep_ctx=True, warm_chunk=1000)
+    _, ft, fb = ctx.kinetics()
+    ctx.close()
+    line["config"]["run"] = (f"{chunk * steps} of the configuration's {wl.n_steps} steps" if
+                             chunk * steps < wl.n_steps else "the configuration's whole run")
+    line["kinetics"] = kinetics_summary(ft, fb, wl.chains, wl.thr_mask, wl.bell_mask, chunk * steps, wl.dt)
+    if not args.no_cpu:
+        n_cpu = oracle_sample_steps(wl, 16)
+        cpu, r, sample, sub_pos = cpu_baseline(wl, pos0, 16, n_steps=n_cpu, keep=True)
+        line["cpu_baseline"] = cpu
+        line["errors_vs_oracle"] = errors_vs_oracle(wl, r, sample, sub_pos, n_cpu, sptr)
+    return line
 
 
 def conformation_line(wl, pos0, sptr, n_steps=2000):
@@ -304,7 +532,7 @@ def lj_ops_per_bead_step(n_beads):
             + LJ_PAIR_OPS * (n_beads - 1) * (n_beads - 2) / (2.0 * n_beads))
 
 
-def collapsed_line(sptr, n_chains=0, n_steps=3000, fp64_chains=64):
+def collapsed_line(sptr, n_chains=0, n_steps=3000, fp64_chains=64, issue_peak=None):
     """The paper's collapsed-chain model (harmonic springs with rest length,
     Lennard-Jones cohesion) on its shear workload: float32 throughput, the
     replica kernel against the issue roofline, the plain FP64 path and the
@@ -347,15 +575,18 @@ def collapsed_line(sptr, n_chains=0, n_steps=3000, fp64_chains=64):
     out["unit"] = "bead-steps/s"
     ops = lj_ops_per_bead_step(wl.chains[0].n_beads)
     achieved = ops * units / (rep_ms / 1e3) / 1e12
-    peak = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                       "frac": achieved / peak,
+    derived = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    if issue_peak is None:
+        issue_peak = bdra.bd_probe_issue(sptr)           # measured, outside the timed region
+    peak = issue_peak / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instructions/s",
+                       "frac": achieved / peak, "peak_derived": derived, "frac_of_derived": achieved / derived,
                        "traffic": COLLAPSED_TRAFFIC_BYTES if (wl.name, n_steps) == COLLAPSED_TRAFFIC_AT else None,
                        "traffic_unit": "bytes per launch (ncu capture)",
                        "kernel": "collapsed-chain replica kernel (float32)",
                        "avg_launch_ms": rep_ms / max(rep_n, 1), "launches": rep_n,
                        "share_of_step": rep_ms / (t * 1e3), "ops_per_bead_step": ops,
-                       "peak_basis": "issue rate, derived (as the main line's roofline)"}
+                       "peak_basis": "measured: bd_probe_issue (mixed float32 / integer instruction issue)"}
     out["parent_kernel_share"] = par_ms / (t * 1e3)
     # FP64 and the FP32 force error on a subset
     sub = wl.chains[:fp64_chains]
@@ -628,7 +859,7 @@ def rest_line(sptr, n_chains=128, windows=6, skip=2):
     return out
 
 
-def adjoint_line(sptr, n_chains=0, n_steps=0):
+def adjoint_line(sptr, n_chains=0, n_steps=0, grad_check=False):
     """Forward run plus reverse-mode adjoint of the differentiation workload
     (256 FENE chains, N=200, 32 replicas, 2e4 steps, parent checkpoints every
     1000 steps, float32 integration): gradients of the mid-chain RSF averaged
@@ -674,12 +905,61 @@ def adjoint_line(sptr, n_chains=0, n_steps=0):
     info = ctx.info()
     ctx.close()
     bead_steps = wl.bead_steps()
-    return {"workload": wl.name, "precision": "FP32 integrate, FP64 reduce",
-            "checkpoint_steps": I.ADJOINT_CHECKPOINT_STEPS, "steps": n,
-            "forward_s": fwd, "adjoint_s": adj, "adjoint_over_forward": adj / fwd,
-            "value": bead_steps / (fwd + adj), "unit": "bead-steps/s (forward + adjoint)",
-            "device_bytes": int(info.device_bytes),
-            "grad_finite": bool(torch.isfinite(grad).all().item())}
+    out = {"workload": wl.name, "precision": "FP32 integrate, FP64 reduce",
+           "checkpoint_steps": I.ADJOINT_CHECKPOINT_STEPS, "steps": n,
+           "forward_s": fwd, "adjoint_s": adj, "adjoint_over_forward": adj / fwd,
+           "value": bead_steps / (fwd + adj), "unit": "bead-steps/s (forward + adjoint)",
+           "device_bytes": int(info.device_bytes),
+           "grad_finite": bool(torch.isfinite(grad).all().item())}
+    if grad_check:
+        out["errors_vs_oracle"] = adjoint_gradient_error(wl, sptr)
+    return out
+
+
+def adjoint_gradient_error(wl, sptr, n_steps=2000, sample=(0, 255)):
+    """The float32 adjoint's gradients against the FP64 oracle's pathwise
+    tangent (same Philox draws, noise held fixed) on sampled chains of the
+    differentiation workload, over its first n_steps steps (two checkpoint
+    segments): max |difference| / max |gradient| per parameter (rate, b, H)."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2206_05851_gb300 import bdra
+    from paper_2206_05851_gb300 import inputs as I
+    sample = [c for c in sample if c < len(wl.chains)]
+    S = wl.window_steps
+    W = n_steps // S
+    pos0 = I.initial_positions(wl)
+    offs = I.spring_offsets(wl.chains)
+    G = np.zeros((W, int(offs[-1])))
+    for c, ch in enumerate(wl.chains):
+        G[:, offs[c] + (ch.n_beads - 1) // 2] = 1.0 / W
+    gls = np.ones(len(wl.chains))
+    ctx = bdra.Context(wl.chains, wl.dt, S, wl.seed, torch.from_numpy(pos0).cuda(),
+                       precision=bdra.BD_PREC_FP32, max_windows=W, bell_mask=I.CRIT_RSF, stream=sptr,
+                       checkpoint_steps=I.ADJOINT_CHECKPOINT_STEPS)
+    ctx.step(n_steps)
+    got = ctx.adjoint(G, gls)[sample]
+    ctx.close()
+    sub = [wl.chains[c] for c in sample]
+    bo = I.bead_offsets(wl.chains)
+    p0 = np.concatenate([pos0[bo[c]:bo[c + 1]] for c in sample])
+    t = time.perf_counter()
+    r, dr = O.rsf_tangent(sub, wl.dt, S, n_steps, wl.seed, p0, n_threads=len(sub), chain_ids=sample)
+    t = time.perf_counter() - t
+    so = I.spring_offsets(sub)
+    want = np.zeros((len(sub), 3))
+    for k, (c, ch) in enumerate(zip(sample, sub)):
+        Gc = G[:, offs[c]:offs[c + 1]]
+        seed = Gc - gls[c] * ch.k0 * ch.dx * np.exp(ch.dx * r[:, so[k]:so[k + 1]]) * S * wl.dt
+        for j in range(3):
+            want[k, j] = float((seed * dr[j][:, so[k]:so[k + 1]]).sum())
+    err = np.abs(got - want).max(axis=0) / np.abs(want).max(axis=0)
+    return {"sample": f"chains {sample}, first {n_steps} steps ({W} windows, "
+                      f"{n_steps // I.ADJOINT_CHECKPOINT_STEPS} checkpoint segments)",
+            "grad_max_rel_err": {"rate": float(err[0]), "b": float(err[1]), "H": float(err[2])},
+            "oracle_seconds": t,
+            "precision": "GPU float32 adjoint (FP64 reductions) vs the FP64 oracle's tangent"}
 
 
 def main():
@@ -750,123 +1030,58 @@ def main():
     if world > 1:
         dist.barrier()
     bdra.load()
+    sptr = torch.cuda.current_stream().cuda_stream
+    issue_peak = bdra.bd_probe_issue(sptr)               # measured ceilings, outside any timed region
+    philox_peak = bdra.bd_probe_philox_rounds(sptr)
 
-    wl = make_workload(args)
-    # ranks own independent chain sets: same shapes, their own seeds (weak scaling)
-    seed, init_seed = shard.rank_keys(wl.seed, wl.init_seed, rank)
-    pos0 = I.initial_positions(wl, seed=init_seed)
-    S = wl.window_steps
-    chunk = args.chunk
-    total_windows = (args.warmup + args.steps) * chunk // S + 1
-    stream = torch.cuda.current_stream()
-    sptr = stream.cuda_stream
-    ctx = bdra.Context(wl.chains, wl.dt, S, seed, torch.from_numpy(pos0).cuda(),
-                       precision=bdra.BD_PREC_FP32, max_windows=total_windows,
-                       thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=sptr)
-    if args.autotune:
-        ctx.autotune(probe_steps=32)
-    bead_steps_chunk = sum(c.n_replicas * c.n_beads for c in wl.chains) * chunk
-    slot_bead_steps_chunk = bead_steps_chunk        # replica slots only (the replica kernel)
-    ev_cap = 6 * ctx.M
-    ev_buf = torch.zeros(ev_cap * 24, dtype=torch.uint8, device="cuda")
-    ls_buf = torch.zeros((len(wl.chains), 3), dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    def bench_step():
-        ctx.step(chunk)
-        return bdra.bd_detect_events(ctx.ptr, ev_buf, ev_cap, ls_buf)
-
-    for _ in range(args.warmup):
-        bench_step()
-    # the timed region integrates the workload itself: from the initial coils at step 0
-    ctx.set_positions(torch.from_numpy(pos0).cuda(), 0)
-    torch.cuda.synchronize()
-    philox_peak = bdra.bd_probe_philox_rounds(sptr)      # measured ceiling, outside the timed region
-    bdra.bd_enable_timing(ctx.ptr, True)
-    bdra.bd_kernel_times(ctx.ptr)
-    launches0 = ctx.info().kernel_launches
-    clocks = ClockSampler()
-    clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        flush.zero_()                 # evict L2 between timed steps
-        n_events = bench_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_ms = e0.elapsed_time(e1)
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    launches = ctx.info().kernel_launches - launches0    # our kernels only
-    (par_ms, rep_ms), (par_n, rep_n) = bdra.bd_kernel_times(ctx.ptr)
-    bdra.bd_enable_timing(ctx.ptr, False)
-    t_max = shard.max_over_ranks(t_ms, dist, "cuda")
-    value = shard.whole_job_rate(bead_steps_chunk * args.steps, world, t_max / 1e3)
-
-    # roofline of the dominant kernel (replica kernel), measured live
-    rep_units = slot_bead_steps_chunk * args.steps
-    achieved = ALGO_OPS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3) / 1e12
-    peak = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak,
-            "traffic": REPLICA_TRAFFIC_BYTES if (wl.name, chunk) == REPLICA_TRAFFIC_AT else None,
-            "traffic_unit": "bytes per launch (ncu capture)",
-            "kernel": "replica kernel (planner's float32 tile)", "avg_launch_ms": rep_ms / max(rep_n, 1),
-            "launches": rep_n, "share_of_step": rep_ms / t_ms,
-            "peak_basis": f"issue rate {SMS} SMs x {LANES_PER_CLK_PER_SM} lane-instr/clk x "
-                          f"{SM_MAX_MHZ:.0f} MHz (derived, not measured)",
-            "ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP}
-    if clk:
-        roof["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6 / 1e12)
-    # the same kernel against the measured ceiling of its dominant work
-    rounds = PHILOX_ROUNDS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3)
-    roof_philox = {"bound": "alu (Philox rounds: 32x32->64 multiplies + XOR3)", "achieved": rounds / 1e12,
-                   "peak": philox_peak / 1e12, "unit": "T rounds/s", "frac": rounds / philox_peak,
-                   "peak_basis": "measured by bd_probe_philox_rounds on this GPU just before the timed region",
-                   "rounds_per_bead_step": PHILOX_ROUNDS_PER_BEAD_STEP}
-    parent_share = par_ms / t_ms
-
-    out = {"metric": METRIC, "value": value, "unit": "bead-steps/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+    # one workload of world x the configuration's chains, split into contiguous
+    # chain ranges (per-GPU work fixed as N grows: weak scaling)
+    wl_all = make_workload(args, world)
+    pos_all = I.initial_positions(wl_all)
+    chains, pos0, base = shard.rank_share(wl_all.chains, pos_all, rank, world)
+    wl = dataclasses.replace(wl_all, chains=chains)
+    main_line, ctx = replica_line(wl, pos0, base, args.chunk, args.steps, args.warmup, sptr,
+                                  args.autotune, issue_peak, philox_peak, dist if world > 1 else None,
+                                  traffic_at=REPLICA_TRAFFIC_AT, keep_ctx=True)
+    out = {"metric": METRIC, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-           "data": "synthetic",
-           "config": {"workload": wl.name, "chains_per_gpu": len(wl.chains),
-                      "beads": sorted({c.n_beads for c in wl.chains})[:1] + sorted({c.n_beads for c in wl.chains})[-1:],
-                      "replicas": sorted({c.n_replicas for c in wl.chains}),
-                      "dt": wl.dt, "window_steps": S, "steps_per_bench_step": chunk,
-                      "timed_integration_steps": chunk * args.steps,
-                      "criteria": f"threshold mask {wl.thr_mask}, Bell mask {wl.bell_mask} (1 ISF, 2 TSF, 4 RSF)",
-                      "precision": "FP32 integrate, FP64 reduce", "autotuned": bool(args.autotune),
-                      "l2": "flushed (256 MB write) between timed steps",
-                      "parallelism": f"chains sharded over {world} GPU(s), no collective on the data path"},
-           "gpu_launches": int(launches), "events_detected": int(n_events),
-           "parent_kernel_share": parent_share}
-    if clk:
-        out["clocks"] = clk
-    out["roofline"] = roof
-    out["roofline_philox"] = roof_philox
+           "data": "synthetic"}
+    out.update(main_line)
+    out["config"]["parallelism"] = (
+        f"one workload of {len(wl_all.chains)} chains split into {world} contiguous chain range(s) "
+        f"balanced by N(R+1), global chain ids in the noise counter; no collective during the "
+        f"integration; events and first-event arrays gathered after it")
+    out["config"]["chains_total"] = len(wl_all.chains)
+    # after the timed region: the whole workload's event list and kinetics on rank 0
+    ev, _ = ctx.events(capacity=6 * ctx.M)
+    events = shard.gather_events(shard.globalize_events(ev, base), dist if world > 1 else None)
+    _, ft, fb = ctx.kinetics()
+    ft_all = shard.gather_rows(ft, dist if world > 1 else None)
+    fb_all = shard.gather_rows(fb, dist if world > 1 else None)
+    if rank == 0:
+        out["events_detected"] = int(len(events))
+        if wl.thr_mask or wl.bell_mask:
+            out["kinetics"] = kinetics_summary(ft_all, fb_all, wl_all.chains, wl.thr_mask, wl.bell_mask,
+                                               args.chunk * args.steps, wl.dt)
     peaks = measured_peaks()
     if peaks:
         out["measured_peaks_file"] = {k: peaks[k] for k in list(peaks)[:8]}
-
-    if rank == 0 and (wl.thr_mask or wl.bell_mask):
-        out["kinetics"] = kinetics_summary(ctx, wl, chunk * args.steps)
+    S = wl.window_steps
+    chunk = args.chunk
     if rank == 0 and world == 1:
+        value = out["value"]
         # plain FP64 path on the same chains, 1000 steps, and the FP32 force
         # error against it
         if not args.no_fp64:
             n64 = 1000
-            c64 = bdra.Context(wl.chains, wl.dt, S, seed, torch.from_numpy(pos0).cuda(),
+            c64 = bdra.Context(wl.chains, wl.dt, S, wl.seed, torch.from_numpy(pos0).cuda(),
                                precision=bdra.BD_PREC_FP64, max_windows=n64 // S + 1,
                                thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=sptr)
             c64.step(S)
             torch.cuda.synchronize()
             c64.set_positions(torch.from_numpy(pos0).cuda(), 0)
             torch.cuda.synchronize()
+            stream = torch.cuda.current_stream()
             a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             c64.step(n64)
@@ -889,6 +1104,8 @@ def main():
                                  "rsf_max_rel_err_fp32_vs_fp64": max(errs)}
         # end to end through the C ABI with host buffers
         if not args.no_e2e:
+            bead_steps_chunk = wl.bead_steps(chunk)
+            ev_cap = 6 * ctx.M
             pos_h = torch.from_numpy(pos0).pin_memory()
             ev_h = np.zeros(ev_cap, dtype=bdra.EVENT_DTYPE)
             rsf_h = np.zeros(ctx.M)
@@ -913,31 +1130,40 @@ def main():
                           "h2d_bytes_per_step": int(pos_h.numel() * 8),
                           "d2h_bytes_per_step": int(nev * 24 + ctx.M * 8 + 8),
                           "steps": e2e_steps}
+        ctx.close()
         if not args.no_adjoint:
-            out["adjoint"] = adjoint_line(sptr, args.adjoint_chains, args.adjoint_steps)
+            out["adjoint"] = adjoint_line(sptr, args.adjoint_chains, args.adjoint_steps,
+                                          grad_check=not args.no_cpu)
         if not args.no_conformation:
             out["conformation"] = conformation_line(wl, pos0, sptr)
         # measured per-unit ceilings of this GPU (context for every fraction above)
         out["measured_unit_peaks"] = {
+            "issue_lane_instr_per_s": issue_peak,
             "philox_rounds_per_s": philox_peak,
             "fp32_fma_flops": bdra.bd_probe_fp32_fma(sptr),
             "fp64_fma_flops": bdra.bd_probe_fp64_fma(sptr),
             "mufu_rsqrt_per_s": bdra.bd_probe_mufu(sptr),
             "basis": "independent chains at full occupancy, no memory traffic (bd_probe_*)"}
+        if not args.no_cpu:
+            n_cpu = 20_000                               # about 10 s on 16 cores
+            cpu, r, sample, sub_pos = cpu_baseline(wl, pos0, n_steps=n_cpu, keep=True)
+            out["cpu_baseline"] = cpu
+            out["errors_vs_oracle"] = errors_vs_oracle(wl, r, sample, sub_pos, n_cpu, sptr)
+        if not args.no_batched:
+            out["uneven"] = batch_line("uneven_4096", sptr, issue_peak, philox_peak, args)
+            out["bell"] = batch_line("bell_16384", sptr, issue_peak, philox_peak, args)
         if not args.no_collapsed:
-            out["collapsed"] = collapsed_line(sptr)
+            out["collapsed"] = collapsed_line(sptr, issue_peak=issue_peak)
         if not args.no_hi:
             out["hi"] = hi_line(sptr)
         if not args.no_vwf:
             out["vwf"] = vwf_line(sptr)
-        if not args.no_cpu:
-            out["cpu_baseline"] = cpu_baseline(wl, pos0, n_steps=20_000)   # about 10 s on 16 cores
+    else:
+        ctx.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
-
 
 if __name__ == "__main__":
     main()

@@ -96,6 +96,41 @@ mufu_probe(float* sink, int iters, float c)
     sink[g] = acc;
 }
 
+// Issue rate of a mixed integer / float32 instruction stream: every thread
+// runs kProbeChains independent chains, each iteration two float32 FMAs and
+// one three-input logic operation per chain (written as PTX so that each is
+// one instruction). The float32 pipe takes two of every three instructions
+// and the integer pipe one, neither at its own limit, so the rate is bounded
+// by instruction issue (one warp instruction per sub-partition per clock):
+// the ceiling of a kernel whose work is a mix of both. Loop control (three
+// instructions per 96 counted) is not counted, so the rate errs low by 3%.
+__global__ void __launch_bounds__(kProbeThreads, 2)
+issue_probe(uint32_t* sink, int iters, float b, float c, uint32_t k)
+{
+    float x[kProbeChains], y[kProbeChains];
+    uint32_t z[kProbeChains];
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) {
+        x[j] = (float)(g & 255u) + (float)j;
+        y[j] = (float)(g & 127u) - (float)j;
+        z[j] = g * 0x9E3779B9u + (uint32_t)j;
+    }
+#pragma unroll 4
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < kProbeChains; ++j) {
+            asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(x[j]) : "f"(b), "f"(c));
+            asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(y[j]) : "f"(b), "f"(c));
+            asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(z[j]) : "r"(k), "r"(g));
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) acc ^= __float_as_uint(x[j]) ^ __float_as_uint(y[j]) ^ z[j];
+    sink[g] = acc;
+}
+
 // Times `launch(iters)` on `stream` after a warm-up launch (iters 256) and
 // returns its duration in ms (0 on failure).
 template <typename F>
@@ -207,6 +242,29 @@ extern "C" bd_status bd_probe_fp32_fma(void* stream, double* flops_per_s)
     cudaGetLastError();
     if (!(ms > 0.0f)) return BD_E_CUDA;
     *flops_per_s = 2.0 * (double)blocks * kProbeThreads * iters * kProbeChains / (ms * 1e-3);
+    return BD_OK;
+}
+
+extern "C" bd_status bd_probe_issue(void* stream, double* lane_instr_per_s)
+{
+    if (!lane_instr_per_s) return BD_E_INVALID;
+    *lane_instr_per_s = 0.0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int sms = probe_sms();
+    if (!sms) return BD_E_CUDA;
+    const int blocks = 2 * sms, iters = 8192;
+    uint32_t* sink = nullptr;
+    if (cudaMalloc((void**)&sink, sizeof(uint32_t) * (size_t)blocks * kProbeThreads) != cudaSuccess) {
+        cudaGetLastError();
+        return BD_E_OOM;
+    }
+    const float ms = probe_time(st, [&](int n) {
+        issue_probe<<<blocks, kProbeThreads, 0, st>>>(sink, n, 0.99999994f, 1e-3f, 0x5bd1e995u);
+    }, iters);
+    cudaFree(sink);
+    cudaGetLastError();
+    if (!(ms > 0.0f)) return BD_E_CUDA;
+    *lane_instr_per_s = 3.0 * (double)blocks * kProbeThreads * iters * kProbeChains / (ms * 1e-3);
     return BD_OK;
 }
 

@@ -7,7 +7,13 @@ Reading of the criteria of Sec. II (threshold on ISF, TSF, RSF) and Sec. III
 - Force profiles (RSF, TSF) are one result per chain and window: each
   (chain, window) row is compared normwise, relative to that row's largest
   force, so a wrong force on a few low-tension springs is not hidden under
-  the largest spring of another chain or window.
+  the largest spring of another chain or window. For the laws with a rest
+  length r0 (the collapsed chain's harmonic springs, the vWF springs) the
+  force H (|Q| - r0) is a small difference of bond lengths times a large
+  stiffness: the bond length carries the trajectory's relative error, so
+  the force error scales with H r0, not with the force. Their rows are
+  compared relative to max(largest force, H r0), H the chain's stiffest
+  spring.
 - Event steps (first threshold crossing, first Bell passage) must equal the
   oracle's, except at a near-tie. A float32 and a float64 run that differ in
   the force by a small relative error can take a boundary decision on
@@ -47,6 +53,15 @@ def log_hazard_close(lg: np.ndarray, lr: np.ndarray) -> np.ndarray:
     return np.abs(lg - lr) <= LOG_HAZ_REL * np.abs(lr) + LOG_HAZ_ABS
 
 
+def force_scale(ch) -> float:
+    """H r0 of a law with a rest length (0 for FENE and Hookean springs)."""
+    if ch.spring == I.SPRING_HARMONIC:
+        return ch.H * ch.r0
+    if ch.spring == I.SPRING_VWF:
+        return max(ch.H, ch.vwf_fa + ch.vwf_fb) * ch.r0
+    return 0.0
+
+
 def profile_rows_rel_err(got: np.ndarray, want: np.ndarray, chains) -> float:
     """Largest normwise relative error over the (chain, window) rows of a
     [W][M] profile history."""
@@ -56,7 +71,7 @@ def profile_rows_rel_err(got: np.ndarray, want: np.ndarray, chains) -> float:
         g, w = got[:, offs[c]:offs[c + 1]], want[:, offs[c]:offs[c + 1]]
         if g.size == 0:
             continue
-        den = np.maximum(np.abs(w).max(axis=1), 1e-300)
+        den = np.maximum(np.maximum(np.abs(w).max(axis=1), force_scale(chains[c])), 1e-300)
         worst = max(worst, float((np.abs(g - w).max(axis=1) / den).max()))
     return worst
 

@@ -284,7 +284,8 @@ def test_autograd_releases_device_memory():
         with pytest.raises(RuntimeError, match="released"):
             loss.backward()
         del rsf, ls, loss
-    np.testing.assert_array_equal(grads[0].numpy(), grads[1].numpy())
+    # the float64 gradient partials meet in atomics: equal up to their order
+    np.testing.assert_allclose(grads[0].numpy(), grads[1].numpy(), rtol=1e-12, atol=0)
     assert free_bytes() >= base - (16 << 20)
     # kept for a second backward on request; released early on request
     params = chain_params(wl.chains).requires_grad_(True)
@@ -293,7 +294,7 @@ def test_autograd_releases_device_memory():
     g1 = params.grad.clone()
     params.grad = None
     rsf.sum().backward()
-    np.testing.assert_array_equal(params.grad.numpy(), g1.numpy())
+    np.testing.assert_allclose(params.grad.numpy(), g1.numpy(), rtol=1e-12, atol=0)
     release_run(rsf)
     assert free_bytes() >= base - (16 << 20)
     del rsf, ls

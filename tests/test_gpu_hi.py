@@ -48,14 +48,16 @@ def _collapsed_set():
 
 
 def _fene_set():
+    # thresholds and Bell rates set so that both kinds of event occur within
+    # the 300 steps
     return [I.Chain(n_beads=20, n_replicas=3, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL, b=50.0,
-                    rate=0.5, f_c=5.0, k0=1e-2, dx=0.2, hi_a=0.5),
+                    rate=0.5, f_c=3.0, k0=1.0, dx=0.2, hi_a=0.5),
             I.Chain(n_beads=64, n_replicas=2, spring=I.SPRING_FENE, flow=I.FLOW_SHEAR, b=100.0,
-                    rate=0.2, f_c=6.0, k0=1e-2, dx=0.2, hi_a=0.4),
+                    rate=0.2, f_c=3.0, k0=1.0, dx=0.2, hi_a=0.4),
             I.Chain(n_beads=2, n_replicas=2, spring=I.SPRING_HOOKE, flow=I.FLOW_PLANAR, rate=0.3,
-                    f_c=2.0, k0=1e-2, dx=0.5, hi_a=0.3),
+                    f_c=2.0, k0=1.0, dx=0.5, hi_a=0.3),
             I.Chain(n_beads=20, n_replicas=4, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL, b=50.0,
-                    rate=0.5, f_c=5.0, k0=1e-2, dx=0.2)]
+                    rate=0.5, f_c=3.0, k0=1.0, dx=0.2)]
 
 
 SETS = {"collapsed": (_collapsed_set, 4e-5, 50, [20, 130, 150]),

@@ -364,6 +364,36 @@ def test_device_and_host_buffers_agree():
     ctx.close()
 
 
+def test_tsf_is_the_float64_mean_of_the_float32_isf_samples():
+    # TSF (Sec. II) of a float32 run: the mean over the S = 1500 steps of a
+    # window of the parent's float32 ISF samples, summed in float64. The
+    # parent's trajectory does not depend on the window length (its noise is
+    # keyed by the global step), so a second run with one-step windows
+    # returns each ISF sample itself as its TSF; their float64 means must
+    # equal the S = 1500 run's TSF to double rounding (a float32 sum of 1500
+    # samples is off by about 3e-7 of their size). FENE springs under strong
+    # elongation, and the free-draining collapsed and vWF chains (signed
+    # forces, Lennard-Jones cohesion).
+    fene = I.Chain(n_beads=16, n_replicas=1, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL, b=100.0,
+                   rate=10.0)
+    chains = [fene, I.collapsed_chain(1), I.vwf_chain(1, n_beads=20, hi=False)]
+    dt, S, n = I.COLLAPSED_DT, 1500, 3000
+    pos0 = I.initial_positions(I.custom(chains, dt, S, n), seed=12)
+    runs = []
+    for s in (S, 1):
+        ctx = bdra.Context(chains, dt, s, 3, pos0, precision=bdra.BD_PREC_FP32,
+                           max_windows=n // s, thr_mask=0, bell_mask=0, stream=_stream())
+        ctx.step(n)
+        runs.append((ctx.positions(False), np.array([ctx.time_average(w) for w in range(n // s)])))
+        ctx.close()
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    isf = runs[1][1].reshape(n // S, S, -1)
+    want = isf.mean(axis=1)
+    scale = np.abs(isf).mean(axis=1)
+    err = np.abs(runs[0][1] - want) / scale
+    assert err.max() <= 1e-11, err.max()
+
+
 def _sampled(wl, g, pos0, sample, n):
     """Sampled chains of a full-size float32 run against the oracle, which
     re-runs them alone with their global chain ids in the noise counter:

@@ -74,3 +74,49 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         bdra.bd_compact_events_noalloc(dummy, dummy, bdra.NOALLOC_MAX_SPRINGS + 1, dummy, 1,
                                        dummy, 0, dummy)
     assert e.value.status == bdra.BD_E_CAPACITY
+
+
+def _numpy_compaction(ft, fb, offs):
+    """The event list written out plainly: springs in order, then criterion,
+    then kind (threshold before Bell)."""
+    M = ft.shape[1]
+    steps = np.stack([ft.T, fb.T], axis=2)               # [M][3][2]
+    m, q, kind = np.nonzero(steps >= 0)
+    chain = np.searchsorted(offs, m, side="right") - 1
+    out = np.zeros(len(m), dtype=bdra.EVENT_DTYPE)
+    out["chain"], out["spring"], out["criterion"], out["kind"] = chain, m - offs[chain], q, kind
+    out["step"] = steps[m, q, kind]
+    assert M == offs[-1]
+    return out
+
+
+def test_noalloc_compaction_at_its_maximum_size_with_truncation():
+    # 2^20 springs (the scratch's limit: 4096 blocks, so the single-block scan
+    # carries over 16 passes) over many chains of uneven length, synthetic
+    # first-event arrays; then a capacity below the total, where the count
+    # must still be the full one and the first `capacity` events written
+    import torch
+    rng = np.random.default_rng(11)
+    M = bdra.NOALLOC_MAX_SPRINGS
+    lens = rng.integers(1, 600, size=4000)
+    lens = lens[np.cumsum(lens) < M]
+    lens = np.append(lens, M - lens.sum())
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    C = len(lens)
+    ft = np.where(rng.random((3, M)) < 0.02, rng.integers(0, 10**6, size=(3, M)), -1).astype(np.int64)
+    fb = np.where(rng.random((3, M)) < 0.01, rng.integers(0, 10**6, size=(3, M)), -1).astype(np.int64)
+    want = _numpy_compaction(ft, fb, offs)
+    stream = torch.cuda.current_stream().cuda_stream
+    d_ft, d_fb = torch.from_numpy(ft).cuda(), torch.from_numpy(fb).cuda()
+    d_offs = torch.from_numpy(offs).cuda()
+    for cap in (len(want) + 5, len(want) // 3):
+        out = torch.full((cap * 24,), 0xAB, dtype=torch.uint8, device="cuda")
+        n_out = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+        bdra.bd_compact_events_noalloc(d_ft, d_fb, M, d_offs, C, out, cap, n_out, stream)
+        torch.cuda.synchronize()
+        assert int(n_out.item()) == len(want)
+        got = np.frombuffer(out.cpu().numpy().tobytes(), dtype=bdra.EVENT_DTYPE)
+        k = min(cap, len(want))
+        np.testing.assert_array_equal(got[:k], want[:k])
+        if cap > len(want):                  # nothing written past the events
+            assert (out.cpu().numpy()[len(want) * 24:] == 0xAB).all()
