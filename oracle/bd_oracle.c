@@ -29,7 +29,8 @@
  *
  * Readings where the paper is silent (the same readings hold on the GPU side):
  *   FENE law F = H Q / (1 - H Q^2 / b); noise from Philox4x32-10 keyed by
- *   (bead, slot | stream << 24, step, chain) with key = seed; Box-Muller;
+ *   (bead, replica pair | stream << 24, step, chain) with key = seed, six
+ *   21-bit uniforms per output and Box-Muller, three normals per slot;
  *   FENE floor s_min on 1 - H Q^2 / b; TSF samples taken after each of the S
  *   updates of a window; hazard of a window force held constant over the
  *   window; first passage when the integrated hazard reaches an Exp(1) draw.
@@ -85,23 +86,41 @@ double ora_uniform(uint32_t x)
     return ((double)x + 0.5) * (1.0 / 4294967296.0);
 }
 
-/* Box-Muller (1958): two uniforms -> two independent standard normals. The
- * random displacement R_i of Eq. 1 needs three per bead: the first pair and
- * the cosine branch of the second pair. */
+/* The random displacement R_i of Eq. 1 needs three standard normals per bead
+ * and slot. Replicas 2j-1 and 2j (j >= 1) share one Philox output per (bead,
+ * step), counter (bead, j | stream << 24, step, chain); the parent (slot 0)
+ * has counter word j = 0. The output's 128 bits give six 21-bit uniforms
+ * u = (m + 1/2) 2^-21: m0..m3 the top 21 bits of words 0..3, m4 the low 11
+ * bits of word 0 above the low 10 bits of word 1, m5 the same of words 2
+ * and 3. Box-Muller (1958) turns the pairs (u0, u1), (u2, u3), (u4, u5) into
+ * six independent normals z_k = r (cos, sin)(2 pi u_angle),
+ * r = sqrt(-2 ln u_radius); the odd slot (and the parent) takes z0, z1, z2,
+ * the even replica slot z3, z4, z5. */
+double ora_uniform21(uint32_t m)
+{
+    return ((double)m + 0.5) * (1.0 / 2097152.0);
+}
+
 void ora_normals3(uint64_t seed, uint32_t bead, uint32_t slot, uint32_t stream,
                   uint32_t step, uint32_t chain, double xi[3])
 {
-    uint32_t ctr[4] = { bead, slot | (stream << 24), step, chain };
+    const uint32_t pair = (slot + 1u) / 2u;
+    const int second = slot != 0u && slot % 2u == 0u;
+    uint32_t ctr[4] = { bead, pair | (stream << 24), step, chain };
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
     uint32_t x[4];
     ora_philox4x32_10(ctr, key, x);
-    double u0 = ora_uniform(x[0]), u1 = ora_uniform(x[1]);
-    double u2 = ora_uniform(x[2]), u3 = ora_uniform(x[3]);
-    double rho0 = sqrt(-2.0 * log(u0));
-    double rho1 = sqrt(-2.0 * log(u2));
-    xi[0] = rho0 * cos(2.0 * ORA_PI * u1);
-    xi[1] = rho0 * sin(2.0 * ORA_PI * u1);
-    xi[2] = rho1 * cos(2.0 * ORA_PI * u3);
+    const uint32_t m[6] = { x[0] >> 11, x[1] >> 11, x[2] >> 11, x[3] >> 11,
+                            ((x[0] & 0x7FFu) << 10) | (x[1] & 0x3FFu),
+                            ((x[2] & 0x7FFu) << 10) | (x[3] & 0x3FFu) };
+    double z[6];
+    for (int k = 0; k < 3; ++k) {
+        const double rho = sqrt(-2.0 * log(ora_uniform21(m[2 * k])));
+        const double theta = 2.0 * ORA_PI * ora_uniform21(m[2 * k + 1]);
+        z[2 * k] = rho * cos(theta);
+        z[2 * k + 1] = rho * sin(theta);
+    }
+    for (int d = 0; d < 3; ++d) xi[d] = z[3 * second + d];
 }
 
 /* Exp(1) threshold of the first-passage test: E = -ln u, one uniform from the

@@ -54,7 +54,11 @@ typedef struct {
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* u = (x + 1/2) 2^-32 in (0, 1). */
 double ora_uniform(uint32_t x);
-/* Three standard normals for (bead, slot, stream, step, chain). */
+/* u = (m + 1/2) 2^-21 in (0, 1) for a 21-bit field m. */
+double ora_uniform21(uint32_t m);
+/* Three standard normals for (bead, slot, stream, step, chain): replicas
+ * 2j-1 and 2j share the Philox output of counter word 1 = j | stream << 24
+ * (the parent: j = 0) and take its two halves. */
 void ora_normals3(uint64_t seed, uint32_t bead, uint32_t slot, uint32_t stream,
                   uint32_t step, uint32_t chain, double xi[3]);
 /* Unit-mean exponential threshold for a (spring, criterion, chain). */

@@ -72,6 +72,8 @@ def lib():
         _lib.ora_philox4x32_10.argtypes = [u32p, u32p, u32p]
         _lib.ora_uniform.argtypes = [ctypes.c_uint32]
         _lib.ora_uniform.restype = ctypes.c_double
+        _lib.ora_uniform21.argtypes = [ctypes.c_uint32]
+        _lib.ora_uniform21.restype = ctypes.c_double
         _lib.ora_normals3.argtypes = [ctypes.c_uint64] + [ctypes.c_uint32] * 5 + [f64p]
         _lib.ora_exp1.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                   ctypes.c_uint32]
@@ -144,6 +146,10 @@ def philox_many(ctr: np.ndarray, key: Sequence[int]) -> np.ndarray:
 
 def uniform(x: int) -> float:
     return lib().ora_uniform(int(x))
+
+
+def uniform21(m: int) -> float:
+    return lib().ora_uniform21(int(m))
 
 
 def normals3(seed: int, bead: int, slot: int, stream: int, step: int, chain: int) -> np.ndarray:

@@ -134,6 +134,10 @@ def test_uniform_open_interval_endpoints():
     assert O.uniform(0) == 2.0**-33
     assert O.uniform(0xFFFFFFFF) == 1.0 - 2.0**-33
     assert O.uniform(0x80000000) == 0.5 + 2.0**-33
+    # the 21-bit uniforms of the Box-Muller normals
+    assert O.uniform21(0) == 2.0**-22
+    assert O.uniform21(2**21 - 1) == 1.0 - 2.0**-22
+    assert O.uniform21(2**20) == 0.5 + 2.0**-22
 
 
 def _counters(n, slot=3, stream=0, step=11, chain=5):
@@ -166,13 +170,33 @@ def test_normals_depend_on_every_counter_word():
     assert np.array_equal(O.normals3(7, 1, 2, 0, 3, 4), base)
 
 
-def test_normals3_uses_the_philox_words_of_its_counter():
-    # The stream is a function of the Philox output alone: two counters that
-    # share the output words would share normals. Check that the slot and the
-    # stream id occupy disjoint bit fields of counter word 1.
-    a = O.normals3(9, 0, 5, 1, 0, 0)
-    b = O.normals3(9, 0, 5 | (1 << 24), 0, 0, 0)
-    assert np.array_equal(a, b)
+def test_replica_pairs_share_one_philox_output_as_three_box_muller_pairs():
+    # Replicas 2j-1 and 2j draw the six normals of one Philox output (each
+    # replica's own stream in law): their normals are the three Box-Muller
+    # pairs (z0, z1), (z2, z3), (z4, z5) of slots (2j-1: z0 z1 z2, 2j: z3 z4
+    # z5). A Box-Muller pair's squared radius is exponential with mean 2,
+    # and all six are uncorrelated standard normals; a wrong half, a reused
+    # angle or radius, or two replicas drawing the same half breaks one.
+    n = 40_000
+    for j in (1, 7):
+        a = O.normals3_many(5, _counters(n, slot=2 * j - 1))
+        b = O.normals3_many(5, _counters(n, slot=2 * j))
+        z = np.concatenate([a, b], axis=1)                   # z0 .. z5
+        r2 = np.array([z[:, 2 * k] ** 2 + z[:, 2 * k + 1] ** 2 for k in range(3)])
+        for k in range(3):
+            assert stats.kstest(r2[k], "expon", args=(0, 2.0)).pvalue > 1e-4, (j, k)
+        cr = np.corrcoef(r2)                                 # independent radii
+        assert np.all(np.abs(cr[np.triu_indices(3, 1)]) < 5.0 / np.sqrt(n))
+        c = np.corrcoef(z.T)
+        assert np.all(np.abs(c[np.triu_indices(6, 1)]) < 5.0 / np.sqrt(n))
+        for d in range(6):
+            assert stats.kstest(z[:, d], "norm").pvalue > 1e-4
+        # 21-bit radial uniforms bound every normal by sqrt(-2 ln 2^-22)
+        assert np.abs(z).max() <= np.sqrt(44.0 * np.log(2.0))
+    # the parent (slot 0) has its own counter word (0), not a replica's
+    p0 = O.normals3_many(5, _counters(1000, slot=0))
+    p1 = O.normals3_many(5, _counters(1000, slot=1))
+    assert not np.allclose(p0, p1)
 
 
 def test_exp1_thresholds_are_unit_exponential():

@@ -37,10 +37,17 @@ PLANTED = [
      "return ((double)x + 1.0) * (1.0 / 4294967296.0);",
      "test_oracle_noise.py::test_uniform_open_interval_endpoints"),
     # Box-Muller normals for the random displacement of Eq. 1
-    ("box_muller_radius", "double rho0 = sqrt(-2.0 * log(u0));", "double rho0 = sqrt(-log(u0));",
+    ("box_muller_radius", "const double rho = sqrt(-2.0 * log(ora_uniform21(m[2 * k])));",
+     "const double rho = sqrt(-log(ora_uniform21(m[2 * k])));",
      "test_oracle_noise.py::test_normals_are_standard_normal"),
-    ("box_muller_reused_angle", "xi[2] = rho1 * cos(2.0 * ORA_PI * u3);", "xi[2] = rho1 * cos(2.0 * ORA_PI * u1);",
-     "test_oracle_noise.py::test_normals_are_standard_normal"),
+    ("box_muller_reused_angle", "z[2 * k + 1] = rho * sin(theta);", "z[2 * k + 1] = rho * cos(theta);",
+     "test_oracle_noise.py::test_replica_pairs_share_one_philox_output_as_three_box_muller_pairs"),
+    ("replica_pair_same_half", "for (int d = 0; d < 3; ++d) xi[d] = z[3 * second + d];",
+     "for (int d = 0; d < 3; ++d) xi[d] = z[d];",
+     "test_oracle_noise.py::test_replica_pairs_share_one_philox_output_as_three_box_muller_pairs"),
+    ("uniform21_radius_field_reused", "((x[0] & 0x7FFu) << 10) | (x[1] & 0x3FFu),",
+     "x[0] >> 11,",
+     "test_oracle_noise.py::test_replica_pairs_share_one_philox_output_as_three_box_muller_pairs"),
     ("exp1_sign", "return -log(ora_uniform(x[0]));", "return log(ora_uniform(x[0]));",
      "test_oracle_noise.py::test_exp1_thresholds_are_unit_exponential"),
     # spring laws
