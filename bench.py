@@ -33,17 +33,42 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("bead-steps/s (chains×replicas×beads×steps) FP32 batched vs FP64 plain, "
           "1 GB300")
-# Minimal lane-instructions per slot-bead-step of the float32 replica step on
-# an SM with two-wide float32 instructions: Philox4x32-10 34.5 (rounds 3-10:
-# 16 wide multiplies and 16 three-input XORs; the round-2 output is two XORs of
-# a per-bead part, loaded from a table once per bead and replica pair (0.5),
-# and a per-step part - rounds 1-2 amortise away), 2 integer-to-float
-# conversions, 8 special-function ops (2 log2, 2 sqrt, sin, 2 cos, 1
-# reciprocal), 19 packed float32 ops (38 float32 operations: uniform scaling
-# 4, Box-Muller products 7, spring law 8, Laplacian 6, update 13) and 4
-# bit/compare ops (angle bits 2, floor clamp and count 2).
-ALGO_OPS_PER_BEAD_STEP = 67.5
-PHILOX_ROUNDS_PER_BEAD_STEP = 8
+# Minimal lane-instructions per slot-bead-step of the float32 replica step.
+# Two replicas per lane (a noise pair: one Philox4x32-10 output gives both
+# replicas' six normals), on an SM with two-wide float32 instructions:
+# Philox 17.5 (rounds 3-10 of one call per pair: 8 wide multiplies and 8
+# three-input XORs a slot; the split's two XORs and the per-bead table load,
+# 1.5 a pair), 7 special-function ops (1.5 log2, 1.5 sqrt, 3 sin/cos, 1
+# reciprocal), 18 packed float32 instructions (uniforms 2, Box-Muller 2.5,
+# spring law 4, Laplacian 3, update 6.5) and 10 bit/compare ops (the six
+# 21-bit uniform fields as float bits, 8; floor clamp and count, 2): 52.5.
+# One replica per lane (every float32 operation scalar, one call per slot):
+# Philox 35, 8 special-function ops, 36 float32 ops, 12 bit/compare ops (four
+# fields, 10 on average over the two halves; floor 2): 91.
+OPS_PER_BEAD_STEP_PAIRED = 52.5
+OPS_PER_BEAD_STEP_SINGLE = 91.0
+# Philox rounds run per slot-bead-step (rounds 1-2 amortise per bead and step)
+ROUNDS_PER_BEAD_STEP_PAIRED = 4
+ROUNDS_PER_BEAD_STEP_SINGLE = 8
+# The survey's generic count of the free-draining bead-step (one Philox call
+# and two Box-Muller pairs per bead-step, unamortised), reported for context
+SURVEY_OPS_PER_BEAD_STEP = 140.0
+
+
+def plan_work(ctx, chains):
+    """Bead-step-weighted minimal lane-instructions and Philox rounds per
+    slot-bead-step of a context's plan (two replicas a lane or one)."""
+    variants, _, _ = ctx.plan()
+    w = [c.n_replicas * c.n_beads for c in chains]
+    paired = [100 <= v < 200 for v in variants]
+    tot = float(sum(w))
+    ops = sum(wi * (OPS_PER_BEAD_STEP_PAIRED if p else OPS_PER_BEAD_STEP_SINGLE)
+              for wi, p in zip(w, paired)) / tot
+    rounds = sum(wi * (ROUNDS_PER_BEAD_STEP_PAIRED if p else ROUNDS_PER_BEAD_STEP_SINGLE)
+                 for wi, p in zip(w, paired)) / tot
+    return ops, rounds, sum(wi for wi, p in zip(w, paired) if p) / tot
+
+
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum), each
 # from one single-pass ncu capture of the current kernels, reported only at the
 # workloads captured: the replica kernel at the default workload and chunk (the
@@ -52,12 +77,13 @@ PHILOX_ROUNDS_PER_BEAD_STEP = 8
 # kernel over one 1500-step window of its default workload, and the
 # collapsed-chain kernel over its timed 3000 steps (its sample rows still sit in
 # L2 when it ends, so they are not in its count).
-REPLICA_TRAFFIC_BYTES = (178_089_472 + 855_967_232 + 134_258_688 + 488_113_408) / 2
-REPLICA_TRAFFIC_AT = ("fene_1024x_n100_r64_planar_wi5", 10_000)
-HI_TRAFFIC_BYTES = 4_601_344 + 793_600
-HI_TRAFFIC_AT = ("collapsed_hi_128x_n50_r50_shear30", 1500)
-COLLAPSED_TRAFFIC_BYTES = 32_545_280 + 958_208
-COLLAPSED_TRAFFIC_AT = ("collapsed_1024x_n50_r50_shear30", 3000)
+# (None until captured on the kernels as they are now.)
+REPLICA_TRAFFIC_BYTES = None
+REPLICA_TRAFFIC_AT = None
+HI_TRAFFIC_BYTES = None
+HI_TRAFFIC_AT = None
+COLLAPSED_TRAFFIC_BYTES = None
+COLLAPSED_TRAFFIC_AT = None
 # Minimal lane-instructions per non-adjacent Lennard-Jones pair of the
 # collapsed-chain model, the pair evaluated once, in units of the LJ length s
 # (x = s/r): separation 3, r^2 3, reciprocal 1, x^4, x^6, x^8 3, x^8 - x^14 1,
@@ -413,7 +439,8 @@ def replica_line(wl, pos0, base, chunk, steps, warmup, sptr, autotune, issue_pea
 
     # roofline of the dominant kernel (replica kernel), measured live
     rep_units = units_chunk * steps
-    achieved = ALGO_OPS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3)
+    ops, rounds_per, paired_share = plan_work(ctx, wl.chains)
+    achieved = ops * rep_units / (rep_ms / 1e3)
     derived = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
             "unit": "T lane-instructions/s", "frac": achieved / issue_peak,
@@ -424,15 +451,18 @@ def replica_line(wl, pos0, base, chunk, steps, warmup, sptr, autotune, issue_pea
             "peak_basis": "measured: bd_probe_issue (mixed float32 / integer instruction issue, "
                           "full occupancy) on this GPU before the timed region",
             "peak_derived": derived / 1e12, "frac_of_derived": achieved / derived,
-            "ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP}
+            "ops_per_bead_step": ops, "paired_share": paired_share,
+            "ops_basis": f"minimal lane-instructions per slot-bead-step of the plan's layouts "
+                         f"({OPS_PER_BEAD_STEP_PAIRED} two replicas a lane, {OPS_PER_BEAD_STEP_SINGLE} one)",
+            "frac_at_survey_count": SURVEY_OPS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3) / issue_peak}
     if clk:
         roof["frac_of_derived_at_measured_clock"] = achieved / (SMS * LANES_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6)
-    # the same kernel against the measured ceiling of its dominant work
-    rounds = PHILOX_ROUNDS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3)
+    # the same kernel against the measured ceiling of its Philox work
+    rounds = rounds_per * rep_units / (rep_ms / 1e3)
     roof_philox = {"bound": "alu (Philox rounds: 32x32->64 multiplies + XOR3)", "achieved": rounds / 1e12,
                    "peak": philox_peak / 1e12, "unit": "T rounds/s", "frac": rounds / philox_peak,
                    "peak_basis": "measured by bd_probe_philox_rounds on this GPU before the timed region",
-                   "rounds_per_bead_step": PHILOX_ROUNDS_PER_BEAD_STEP}
+                   "rounds_per_bead_step": rounds_per}
     out = {"value": value, "unit": "bead-steps/s", "ms_per_step": t_max / steps,
            "config": {"workload": wl.name, "chains_per_gpu": len(wl.chains),
                       "beads": [min(c.n_beads for c in wl.chains), max(c.n_beads for c in wl.chains)],
@@ -525,10 +555,11 @@ def conformation_line(wl, pos0, sptr, n_steps=2000):
 
 def lj_ops_per_bead_step(n_beads):
     """Minimal lane-instructions per bead-step of the collapsed-chain step: the
-    noise and bond update of the free-draining step (ALGO_OPS_PER_BEAD_STEP),
+    noise and bond update of the free-draining step with one replica a lane
+    (OPS_PER_BEAD_STEP_SINGLE),
     LJ_BEAD_OPS, and LJ_PAIR_OPS per non-adjacent pair, each pair counted once
     (Newton's third law): (N-1)(N-2)/2 pairs per chain-step."""
-    return (ALGO_OPS_PER_BEAD_STEP + LJ_BEAD_OPS
+    return (OPS_PER_BEAD_STEP_SINGLE + LJ_BEAD_OPS
             + LJ_PAIR_OPS * (n_beads - 1) * (n_beads - 2) / (2.0 * n_beads))
 
 

@@ -40,11 +40,17 @@
  *     order, x y z). Spring profiles are float64 [M] with
  *     M = sum_c (N_c - 1), chain c's springs starting at sum_{c'<c} (N_c' - 1).
  *   - Noise: Philox4x32-10 (Salmon et al., SC'11) with key = (seed low word,
- *     seed high word) and counter (bead, slot | stream << 24, step, chain),
- *     chain = bd_config.chain_id_base + the chain's index in the context;
- *     slot 0 is the parent, slots 1..R the replicas; stream 0 drives Eq. 1,
- *     stream 1 the Exp(1) thresholds of the Bell first-passage test. Results
- *     therefore do not depend on the launch shape.
+ *     seed high word); chain = bd_config.chain_id_base + the chain's index in
+ *     the context. Eq. 1's normals: counter (bead, j | 0 << 24, step, chain)
+ *     for replica slots 2j-1 and 2j (slot 0 is the parent, j = 0; slots
+ *     1..R the replicas); the output's 128 bits give six 21-bit uniforms
+ *     u = (m + 1/2) 2^-21 (m0..m3 the top 21 bits of words 0..3; m4 the low
+ *     11 bits of word 0 above the low 10 bits of word 1; m5 the same of words
+ *     2 and 3), Box-Muller on (u0, u1), (u2, u3), (u4, u5) gives six normals,
+ *     and the odd slot (and the parent) takes the first three, the even slot
+ *     the last three. The Exp(1) thresholds of the Bell first-passage test:
+ *     counter (spring, 1 << 24, criterion, chain), E = -ln((x0 + 1/2) 2^-32).
+ *     Results therefore do not depend on the launch shape.
  */
 #ifndef BDRA_H
 #define BDRA_H
@@ -319,9 +325,11 @@ bd_status bd_adjoint(bd_ctx* ctx, const double* grad_rsf, const double* grad_log
                      double* grad_params);
 
 /* Diagnostic: the three standard normals the integrator draws for each of n
- * counters ctr [n][4] (word 1 = slot | stream << 24) under key `seed`, in the
- * given precision, written as float64 [n][3]. ctr and out may be host or
- * device. Runs on the current device and stream `stream`; synchronises. */
+ * (bead, slot | stream << 24, step, chain) quadruples ctr [n][4] under key
+ * `seed` (the generator runs on the slot's counter: its replica pair in word
+ * 1, see the noise convention above), in the given precision, written as
+ * float64 [n][3]. ctr and out may be host or device. Runs on the current
+ * device and stream `stream`; synchronises. */
 bd_status bd_philox_normals(uint64_t seed, int64_t n, const uint32_t* ctr, int32_t precision,
                             double* out, void* stream);
 

@@ -231,14 +231,74 @@ void round_keys(uint64_t seed, uint32_t* rk0, uint32_t* rk1)
 struct VariantChoice { int variant, per_warp, groups; double cost; };
 
 // Default issue cost per warp-step (lane-instructions): one replica per lane
-// ~100 per spring plus the halo exchange; two replicas per lane ~140 per
-// spring pair (packed float32 arithmetic, per-replica Philox and special
-// functions). bd_autotune replaces these with measured times.
+// ~100 per spring plus the halo exchange; two replicas per lane ~110 per
+// spring pair (packed float32 arithmetic, one Philox call for the pair's
+// noise, per-normal special functions). bd_autotune replaces these with
+// measured times.
 double default_variant_cost(int v)
 {
     const int L = variant_tile(v);
     if (variant_lj(v)) return 1000.0 * L;      // pair forces: work per lane grows with its beads
-    return variant_paired(v) ? 140.0 * L + 60.0 : 100.0 * L + 40.0;
+    return variant_paired(v) ? 110.0 * L + 60.0 : 100.0 * L + 40.0;
+}
+
+// Warp work items of a chain with R replicas, at most per_warp replicas an
+// item, and how they split. Replicas 2j - 1 and 2j form a noise pair (one
+// generator output, two halves). With two replicas per lane (variant v
+// paired) the split is in whole pairs, so that every item starts at an even
+// offset and each lane holds one pair (one generator call for both). With
+// one replica per lane and several replicas a warp, the odd replicas and the
+// even ones go to separate items (stride 2), so that all lanes of a warp
+// draw the same half (no divergence). Each set splits as evenly as its
+// items allow.
+int item_count(int R, int per_warp, int v)
+{
+    if (variant_paired(v) || per_warp == 1) return (R + per_warp - 1) / per_warp;
+    const int odd = (R + 1) / 2, even = R / 2;
+    return (odd + per_warp - 1) / per_warp + (even + per_warp - 1) / per_warp;
+}
+
+void split_run(int c, int& g, int n, int groups, int first, int stride, int unit, int v,
+               std::vector<ItemDev>& items)
+{
+    // n replicas first, first + stride, ..., in `groups` items (unit: whole pairs)
+    const int units = (n + unit - 1) / unit;
+    int done = 0;
+    for (int k = 0; k < groups; ++k) {
+        const int uk = units / groups + (k < units % groups ? 1 : 0);
+        const int cnt = std::min(uk * unit, n - done);
+        items.push_back(ItemDev{c, g++, first + stride * done, cnt, v, stride});
+        done += cnt;
+    }
+}
+
+// Work-item order of the persistent launches: by variant, and within one the
+// items whose replicas draw the first noise half before those that draw the
+// second (a one-replica-per-lane item of one half runs its own copy of the
+// step code, and keeping the halves apart keeps one copy in the instruction
+// cache at a time), each in chain order.
+void order_items(std::vector<ItemDev>& items)
+{
+    auto half_of = [](const ItemDev& it) {
+        return (it.stride == 2 || it.rep_count == 1) ? (int)(((it.rep_begin + 1) & 1) == 0) : 0;
+    };
+    std::stable_sort(items.begin(), items.end(), [&](const ItemDev& x, const ItemDev& y) {
+        return x.variant != y.variant ? x.variant < y.variant : half_of(x) < half_of(y);
+    });
+}
+
+void split_replicas(int c, int R, int per_warp, int v, std::vector<ItemDev>& items)
+{
+    int g = 0;
+    if (variant_paired(v)) {
+        split_run(c, g, R, (R + per_warp - 1) / per_warp, 0, 1, 2, v, items);
+    } else if (per_warp == 1) {
+        split_run(c, g, R, R, 0, 1, 1, v, items);
+    } else {
+        const int odd = (R + 1) / 2, even = R / 2;
+        split_run(c, g, odd, (odd + per_warp - 1) / per_warp, 0, 2, 1, v, items);
+        split_run(c, g, even, (even + per_warp - 1) / per_warp, 1, 2, 1, v, items);
+    }
 }
 
 // The step variant for a chain: a warp holds P = 32 / ceil(N / L) replicas
@@ -266,7 +326,7 @@ VariantChoice choose_variant(const bd_ctx* ctx, int N, int R, bool collapsed, bo
         const int G = (N + L - 1) / L;
         if (G > 32) continue;
         const int per_warp = (paired ? 2 : 1) * (32 / G);
-        const int groups = (R + per_warp - 1) / per_warp;
+        const int groups = item_count(R, per_warp, v);
         const double cost = groups * ctx->var_cost[v] / ((double)R * N);
         if (cost < best.cost - 1e-12) best = {v, per_warp, groups, cost};
     }
@@ -420,12 +480,7 @@ bd_status plan(bd_ctx* ctx)
         h.f32_pad = 0.0f;
         const int nb = d.n_beads - 1;
         // warp items: replicas split as evenly as the warp capacity allows
-        int begin = 0;
-        for (int g = 0; g < vc.groups; ++g) {
-            const int cnt = d.n_replicas / vc.groups + (g < d.n_replicas % vc.groups ? 1 : 0);
-            items.push_back(ItemDev{c, g, begin, cnt, vc.variant, 0});
-            begin += cnt;
-        }
+        split_replicas(c, d.n_replicas, vc.per_warp, vc.variant, items);
         if (hi) {
             par.push_back({{kParentHIKey + (d.n_beads > kHISmallBeadsHost ? 1 : 0), 1}, c});
         } else {
@@ -445,9 +500,8 @@ bd_status plan(bd_ctx* ctx)
     ctx->n_beads = bead; ctx->n_slot_beads = slot_bead; ctx->state_bonds = bond;
     ctx->M = spr; ctx->part_stride = part;
 
-    // persistent replica launches: one per variant, items in chain order
-    std::stable_sort(items.begin(), items.end(),
-                     [](const ItemDev& x, const ItemDev& y) { return x.variant < y.variant; });
+    // persistent replica launches: one per variant, items ordered by noise half
+    order_items(items);
     ctx->h_items = items;
     ctx->var_classes.clear();
     const int threads = ctx->f64 ? persist_threads_f64() : persist_threads_f32();
@@ -833,13 +887,7 @@ bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost
             if (G > 32 || variant_lj(v) != rest_law ||
                 ctx->chains[c].hi_a > 0) continue;
             const int per_warp = (variant_paired(v) ? 2 : 1) * (32 / G);
-            const int groups = (R + per_warp - 1) / per_warp;
-            int begin = 0;
-            for (int g = 0; g < groups; ++g) {
-                const int cnt = R / groups + (g < R % groups ? 1 : 0);
-                items.push_back(ItemDev{c, g, begin, cnt, v, 0});
-                begin += cnt;
-            }
+            split_replicas(c, R, per_warp, v, items);
         }
         if (items.empty()) continue;
         int per_sm = 1;
@@ -847,6 +895,7 @@ bd_status autotune_probe(bd_ctx* ctx, int probe_steps, std::vector<double>& cost
         const size_t resident = (size_t)per_sm * ctx->n_sm * (threads / 32);
         const size_t base = items.size();
         while (items.size() < 4 * resident) items.push_back(items[items.size() % base]);
+        order_items(items);
         if (items.size() > titems_cap) {
             if (titems) cudaFree(titems);
             titems = nullptr;
@@ -962,7 +1011,7 @@ bd_status adj_plan(bd_ctx* ctx)
         int begin = 0;
         for (int g = 0; g < groups; ++g) {
             const int cnt = d.n_replicas / groups + (g < d.n_replicas % groups ? 1 : 0);
-            items.push_back({L, ItemDev{c, g, begin, cnt, L, 0}});
+            items.push_back({L, ItemDev{c, g, begin, cnt, L, 1}});
             begin += cnt;
         }
         part += (int64_t)groups * (d.n_beads - 1);

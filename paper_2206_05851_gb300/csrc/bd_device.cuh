@@ -40,13 +40,15 @@ struct ChainDev {
     float f32_pad;
 };
 
-// One warp's work: replicas rep_begin+1 .. rep_begin+rep_count of `chain`
-// (group `group` of the chain's replica-force partial sums), evolved with
-// the step variant `variant` (springs per lane, one or two replicas per
-// lane; see Variant).
+// One warp's work: replicas rep_begin + 1 + stride s, s = 0 .. rep_count-1,
+// of `chain` (group `group` of the chain's replica-force partial sums),
+// evolved with the step variant `variant` (springs per lane, one or two
+// replicas per lane; see Variant). stride 2 keeps the replicas of a
+// one-replica-per-lane item all odd or all even, so that every lane of the
+// warp draws the same half of its noise pair's generator output.
 struct ItemDev {
     int32_t chain, group, rep_begin, rep_count;
-    int32_t variant, pad;
+    int32_t variant, stride;
 };
 
 // Threads of every parent-kernel CTA and of every adjoint-kernel CTA (the
@@ -248,16 +250,62 @@ struct PhiloxSplit {
 };
 
 // ---------------------------------------------------------------------------
-// Standard normals from one Philox output (Box-Muller): the pair
-// sqrt(-2 ln u0) (cos, sin)(2 pi u1) and the cosine branch of the pair from
-// (u2, u3), with u = (x + 1/2) 2^-32.
+// Standard normals of a slot (the random displacement R_i of Eq. 1, three per
+// bead and step). Replicas 2j-1 and 2j share one Philox output per (bead,
+// step): counter word 1 is j | stream << 24 (the parent, slot 0: j = 0). The
+// output's 128 bits give six 21-bit uniforms u = (m + 1/2) 2^-21: m0..m3 the
+// top 21 bits of words 0..3, m4 the low 11 bits of word 0 above the low 10
+// bits of word 1, m5 the same of words 2 and 3. Box-Muller turns the pairs
+// (u0, u1), (u2, u3), (u4, u5) (radius uniform, angle uniform) into six
+// normals z = r (cos, sin)(2 pi u_angle), r = sqrt(-2 ln u_radius); half 0
+// (the odd replica slot and the parent) is (z0, z1, z2), half 1 (the even
+// replica slot) is (z3, z4, z5). So a lane that holds a replica pair draws
+// both replicas' noise from one generator call.
 //
-// Normals<T, FAST>::sign: the FAST float path returns the three normals with
-// their sign flipped (it evaluates cos and sin of 2 pi u - pi, the accurate
-// range of the hardware units, and cos(2 pi u - pi) = -cos(2 pi u)). The
-// step multiplies its noise coefficient by `sign`, which undoes the flip
-// exactly: (-a) - (-b) = -(a - b) and (-c)(-d) = c d in floating point.
+// Normals<T, FAST>::sign: the FAST float path returns the normals with their
+// sign flipped (it evaluates cos and sin of 2 pi u - pi, the accurate range of
+// the hardware units, and cos(2 pi u - pi) = -cos(2 pi u)). The step
+// multiplies its noise coefficient by `sign`, which undoes the flip exactly:
+// (-a) - (-b) = -(a - b) and (-c)(-d) = c d in floating point.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t noise_word(uint32_t slot)
+{
+    return ((slot + 1u) >> 1) | ((uint32_t)STREAM_BD << 24);
+}
+__device__ __forceinline__ uint32_t noise_half(uint32_t slot)
+{
+    return (slot != 0u && (slot & 1u) == 0u) ? 1u : 0u;
+}
+
+// The six 21-bit fields m_k of a Philox output.
+struct Fields21 {
+    static __device__ __forceinline__ uint32_t m(uint4 x, int k)
+    {
+        switch (k) {
+        case 0: return x.x >> 11;
+        case 1: return x.y >> 11;
+        case 2: return x.z >> 11;
+        case 3: return x.w >> 11;
+        case 4: return ((x.x & 0x7FFu) << 10) | (x.y & 0x3FFu);
+        default: return ((x.z & 0x7FFu) << 10) | (x.w & 0x3FFu);
+        }
+    }
+    // The float 1 + m_k 2^-21 (exact: m_k fills the top 21 of the 23
+    // mantissa bits), built from the words without isolating m_k first.
+    static __device__ __forceinline__ float one_plus(uint4 x, int k)
+    {
+        const uint32_t one = 0x3F800000u;
+        switch (k) {
+        case 0: return __uint_as_float(one | ((x.x >> 9) & 0x7FFFFCu));
+        case 1: return __uint_as_float(one | ((x.y >> 9) & 0x7FFFFCu));
+        case 2: return __uint_as_float(one | ((x.z >> 9) & 0x7FFFFCu));
+        case 3: return __uint_as_float(one | ((x.w >> 9) & 0x7FFFFCu));
+        case 4: return __uint_as_float(((x.x << 12) & 0x7FF000u) | (((x.y << 2) & 0xFFCu) | one));
+        default: return __uint_as_float(((x.z << 12) & 0x7FF000u) | (((x.w << 2) & 0xFFCu) | one));
+        }
+    }
+};
+
 template <typename T, bool FAST> struct Normals;
 
 __device__ __forceinline__ float rcp_approx(float x)
@@ -275,7 +323,7 @@ __device__ __forceinline__ float sqrt_approx(float x)
 }
 
 // Hardware log2 / sin / cos with denormals flushed: the Box-Muller
-// arguments are never denormal (u >= 2^-33, |angle| >= 2 pi 2^-24), so the
+// arguments are never denormal (u >= 2^-22, |angle| >= 2 pi 2^-22), so the
 // flush changes no result and spares the denormal handling.
 __device__ __forceinline__ float lg2_approx(float x)
 {
@@ -301,91 +349,141 @@ __device__ __forceinline__ float cos_approx(float x)
 // Building blocks of the fast float Box-Muller, shared by the one-slot and
 // two-slot (packed) paths so both round identically.
 struct FastBM {
-    static constexpr float s32 = 2.3283064365386963e-10f;      // 2^-32
-    static constexpr float h32 = 1.1641532182693481e-10f;      // 2^-33
     static constexpr float m2ln2 = -2.0f * 0.69314718055994531f;
     static constexpr float twopi = 6.2831853071795865f;
-    static constexpr float off = -6.2831853071795865f * (1.5f - 5.9604644775390625e-8f);
-    // angle uniform from the top 23 bits: float in [1, 2) (error <= 2^-24 in u)
-    static __device__ __forceinline__ float angle_bits(uint32_t w)
+    // 1 - 2^-22: (1 + m 2^-21) - this = (m + 1/2) 2^-21 exactly
+    static constexpr float rad_off = 0.99999976158142090f;
+    // angle 2 pi (1 + m 2^-21) + off = 2 pi u - pi
+    static constexpr float off = -6.2831853071795865f * (1.5f - 2.384185791015625e-7f);
+    // radius r of field k (radius uniforms: k = 0, 2, 4)
+    static __device__ __forceinline__ float radius(uint4 x, int k)
     {
-        return __uint_as_float(0x3F800000u | (w >> 9));
+        const float u = __fsub_rn(Fields21::one_plus(x, k), rad_off);
+        // |a| guards the approximate log2 of values within an ulp of 1
+        return sqrt_approx(fabsf(__fmul_rn(m2ln2, lg2_approx(u))));
+    }
+    // angle 2 pi u - pi of field k (angle uniforms: k = 1, 3, 5)
+    static __device__ __forceinline__ float angle(uint4 x, int k)
+    {
+        return __fmaf_rn(Fields21::one_plus(x, k), twopi, off);
     }
 };
 
+// Box-Muller pair PR (radius field 2 PR, angle field 2 PR + 1) in float or
+// double with the library's log / sqrt / sincospi: r cos (WANT 1 or 3) and
+// r sin (WANT 2 or 3) of the angle; only the wanted ones are evaluated.
+template <typename T, int PR, int WANT>
+__device__ __forceinline__ void bm_pair(uint4 x, T& c, T& s)
+{
+    const T s21 = T(4.76837158203125e-7);                  // 2^-21
+    const T ur = ((T)Fields21::m(x, 2 * PR) + T(0.5)) * s21;
+    const T ua = ((T)Fields21::m(x, 2 * PR + 1) + T(0.5)) * s21;
+    const T r = sqrt(T(-2) * log(ur));
+    if (WANT == 3) {
+        T sn, cs;
+        sincospi(T(2) * ua, &sn, &cs);
+        c = r * cs;
+        s = r * sn;
+    } else if (WANT == 1) {
+        c = r * cospi(T(2) * ua);
+    } else {
+        s = r * sinpi(T(2) * ua);
+    }
+}
+
 template <bool FAST> struct Normals<float, FAST> {
     static constexpr float sign = FAST ? -1.0f : 1.0f;
-    static __device__ __forceinline__ void draw(uint4 x, float& z0, float& z1, float& z2)
+    // the three normals of half H (0: z0 z1 z2, 1: z3 z4 z5)
+    template <int H>
+    static __device__ __forceinline__ void draw_h(uint4 x, float& z0, float& z1, float& z2)
     {
-        const float s = 2.3283064365386963e-10f;       // 2^-32
-        const float h = 1.1641532182693481e-10f;       // 2^-33
-        const float u0 = fmaf((float)x.x, s, h);
-        const float u2 = fmaf((float)x.z, s, h);
         if (FAST) {
-            // Angles 2 pi u - pi in (-pi, pi); the results are the normals
-            // with flipped sign (see `sign`). The radial uniforms, which
-            // enter a logarithm, are converted in full.
-            const float a0 = FastBM::m2ln2 * lg2_approx(u0);
-            const float a2 = FastBM::m2ln2 * lg2_approx(u2);
-            // |a| guards the approximate log2 of values within an ulp of 1
-            const float r0 = sqrt_approx(fabsf(a0));
-            const float r2 = sqrt_approx(fabsf(a2));
-            const float t1 = fmaf(FastBM::angle_bits(x.y), FastBM::twopi, FastBM::off);
-            const float sn = sin_approx(t1), cs = cos_approx(t1);
-            const float c3 = cos_approx(fmaf(FastBM::angle_bits(x.w), FastBM::twopi, FastBM::off));
-            z0 = r0 * cs;
-            z1 = r0 * sn;
-            z2 = r2 * c3;
+            if (H == 0) {
+                const float r0 = FastBM::radius(x, 0), r2 = FastBM::radius(x, 2);
+                const float t1 = FastBM::angle(x, 1), t3 = FastBM::angle(x, 3);
+                z0 = __fmul_rn(r0, cos_approx(t1));
+                z1 = __fmul_rn(r0, sin_approx(t1));
+                z2 = __fmul_rn(r2, cos_approx(t3));
+            } else {
+                const float r2 = FastBM::radius(x, 2), r4 = FastBM::radius(x, 4);
+                const float t3 = FastBM::angle(x, 3), t5 = FastBM::angle(x, 5);
+                z0 = __fmul_rn(r2, sin_approx(t3));
+                z1 = __fmul_rn(r4, cos_approx(t5));
+                z2 = __fmul_rn(r4, sin_approx(t5));
+            }
         } else {
-            const float u1 = fmaf((float)x.y, s, h);
-            const float u3 = fmaf((float)x.w, s, h);
-            const float r0 = sqrtf(-2.0f * logf(u0));
-            const float r2 = sqrtf(-2.0f * logf(u2));
-            float sn, cs;
-            sincospif(2.0f * u1, &sn, &cs);
-            z0 = r0 * cs;
-            z1 = r0 * sn;
-            z2 = r2 * cospif(2.0f * u3);
+            float c1 = 0.0f, s1 = 0.0f, c2 = 0.0f, s2 = 0.0f;
+            if (H == 0) {
+                bm_pair<float, 0, 3>(x, c1, s1);
+                bm_pair<float, 1, 1>(x, c2, s2);
+                z0 = c1; z1 = s1; z2 = c2;
+            } else {
+                bm_pair<float, 1, 2>(x, c1, s1);
+                bm_pair<float, 2, 3>(x, c2, s2);
+                z0 = s1; z1 = c2; z2 = s2;
+            }
         }
+    }
+    // half h known only at run time (both forms are in the code: callers that
+    // know it at compile time use draw_h)
+    static __device__ __forceinline__ void draw(uint4 x, uint32_t h, float& z0, float& z1, float& z2)
+    {
+        if (h == 0) draw_h<0>(x, z0, z1, z2);
+        else draw_h<1>(x, z0, z1, z2);
     }
 };
 
 template <bool FAST> struct Normals<double, FAST> {
     static constexpr double sign = 1.0;
-    static __device__ __forceinline__ void draw(uint4 x, double& z0, double& z1, double& z2)
+    template <int H>
+    static __device__ __forceinline__ void draw_h(uint4 x, double& z0, double& z1, double& z2)
     {
-        const double s = 2.3283064365386963e-10;       // 2^-32
-        const double u0 = ((double)x.x + 0.5) * s;
-        const double u1 = ((double)x.y + 0.5) * s;
-        const double u2 = ((double)x.z + 0.5) * s;
-        const double u3 = ((double)x.w + 0.5) * s;
-        const double r0 = sqrt(-2.0 * log(u0));
-        const double r2 = sqrt(-2.0 * log(u2));
-        double sn, cs;
-        sincospi(2.0 * u1, &sn, &cs);
-        z0 = r0 * cs;
-        z1 = r0 * sn;
-        z2 = r2 * cospi(2.0 * u3);
+        double c1 = 0.0, s1 = 0.0, c2 = 0.0, s2 = 0.0;
+        if (H == 0) {
+            bm_pair<double, 0, 3>(x, c1, s1);
+            bm_pair<double, 1, 1>(x, c2, s2);
+            z0 = c1; z1 = s1; z2 = c2;
+        } else {
+            bm_pair<double, 1, 2>(x, c1, s1);
+            bm_pair<double, 2, 3>(x, c2, s2);
+            z0 = s1; z1 = c2; z2 = s2;
+        }
+    }
+    static __device__ __forceinline__ void draw(uint4 x, uint32_t h, double& z0, double& z1, double& z2)
+    {
+        if (h == 0) draw_h<0>(x, z0, z1, z2);
+        else draw_h<1>(x, z0, z1, z2);
     }
 };
 
-// The same normals from the split generator: bp = PhiloxSplit::bead_part of
-// the bead, sp = PhiloxSplit::step_part of the step and slot word.
-template <typename T, bool FAST>
-__device__ __forceinline__ void bead_noise_split(uint4 bp, uint3 sp, const StepParams& p,
-                                                 T& z0, T& z1, T& z2)
+// Draw with the half fixed at compile time (H = 0, 1) or read at run time
+// (H = -1: h).
+template <typename T, bool FAST, int H>
+__device__ __forceinline__ void draw_half(uint4 x, uint32_t h, T& z0, T& z1, T& z2)
 {
-    Normals<T, FAST>::draw(PhiloxSplit::finish(bp, sp, p.rk0, p.rk1), z0, z1, z2);
+    if (H == 0) Normals<T, FAST>::template draw_h<0>(x, z0, z1, z2);
+    else if (H == 1) Normals<T, FAST>::template draw_h<1>(x, z0, z1, z2);
+    else Normals<T, FAST>::draw(x, h, z0, z1, z2);
 }
 
-template <typename T, bool FAST>
+// The same normals from the split generator: bp = PhiloxSplit::bead_part of
+// the bead, sp = PhiloxSplit::step_part of the step and noise word, h the
+// slot's half (or H at compile time).
+template <typename T, bool FAST, int H = -1>
+__device__ __forceinline__ void bead_noise_split(uint4 bp, uint3 sp, const StepParams& p, uint32_t h,
+                                                 T& z0, T& z1, T& z2)
+{
+    draw_half<T, FAST, H>(PhiloxSplit::finish(bp, sp, p.rk0, p.rk1), h, z0, z1, z2);
+}
+
+// The normals of (bead, slot, step, chain) from the full generator.
+template <typename T, bool FAST, int H = -1>
 __device__ __forceinline__ void bead_noise(uint32_t bead, uint32_t slot, uint32_t step,
                                            uint32_t chain, const StepParams& p,
                                            T& z0, T& z1, T& z2)
 {
-    const uint4 x = philox4x32_10_rk(
-        make_uint4(bead, slot | ((uint32_t)STREAM_BD << 24), step, chain), p.rk0, p.rk1);
-    Normals<T, FAST>::draw(x, z0, z1, z2);
+    const uint4 x = philox4x32_10_rk(make_uint4(bead, noise_word(slot), step, chain), p.rk0, p.rk1);
+    draw_half<T, FAST, H>(x, noise_half(slot), z0, z1, z2);
 }
 
 // ---------------------------------------------------------------------------

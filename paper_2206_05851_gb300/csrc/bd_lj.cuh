@@ -233,7 +233,8 @@ __device__ __forceinline__ void lj_ring_pairs_packed(const float (&px)[L], const
 // from exactly one of its two lanes, except at d = G/2 for even G, which
 // only the first half of the ring takes. Beads of different lanes are
 // adjacent only across the boundary to the next lane (d = 1, no wrap).
-template <typename T, int L, bool FAST, bool TAB>
+// H: the slot's noise half at compile time (-1: lc.noise_half).
+template <typename T, int L, bool FAST, bool TAB, int H = -1>
 __device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L], const LaneCtx& lc,
                                              const StepConst<T, FAST>& k, const LJConst<T>& kl,
                                              bool in_slot, int seg, int G, int slot_base,
@@ -326,10 +327,10 @@ __device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L],
     if (!lc.has_prev) { fmx = T(0); fmy = T(0); fmz = T(0); }
     if (!lc.has_next) { fnx = T(0); fny = T(0); fnz = T(0); gnx = T(0); gny = T(0); gnz = T(0); }
     uint3 sp = make_uint3(0u, 0u, 0u);
-    if (TAB) sp = PhiloxSplit::step_part(step, lc.slot_key | ((uint32_t)STREAM_BD << 24), p.rk0);
+    if (TAB) sp = PhiloxSplit::step_part(step, lc.noise_word, p.rk0);
     T xcx, xcy, xcz;
-    if (TAB) bead_noise_split<T, FAST>(ptab[lc.bead0], sp, p, xcx, xcy, xcz);
-    else bead_noise<T, FAST>((uint32_t)lc.bead0, lc.slot_key, step, lc.chain, p, xcx, xcy, xcz);
+    if (TAB) bead_noise_split<T, FAST, H>(ptab[lc.bead0], sp, p, lc.noise_half, xcx, xcy, xcz);
+    else bead_noise<T, FAST, H>((uint32_t)lc.bead0, lc.slot_key, step, lc.chain, p, xcx, xcy, xcz);
     const T hx = shfl(xcx, lc.src_next), hy = shfl(xcy, lc.src_next), hz = shfl(xcz, lc.src_next);
 #pragma unroll
     for (int j = 0; j < L; ++j) {
@@ -337,8 +338,8 @@ __device__ __forceinline__ int step_bonds_lj(T (&qx)[L], T (&qy)[L], T (&qz)[L],
         if (j + 1 < L) {
             uint32_t bj = (uint32_t)(lc.bead0 + j + 1);
             asm volatile("" : "+r"(bj));     // keep per-bead noise work inside the step loop
-            if (TAB) bead_noise_split<T, FAST>(ptab[bj], sp, p, xnx, xny, xnz);
-            else bead_noise<T, FAST>(bj, lc.slot_key, step, lc.chain, p, xnx, xny, xnz);
+            if (TAB) bead_noise_split<T, FAST, H>(ptab[bj], sp, p, lc.noise_half, xnx, xny, xnz);
+            else bead_noise<T, FAST, H>(bj, lc.slot_key, step, lc.chain, p, xnx, xny, xnz);
             fpx = fx[j + 1]; fpy = fy[j + 1]; fpz = fz[j + 1];
             ghx = gx[j + 1]; ghy = gy[j + 1]; ghz = gz[j + 1];
         } else {

@@ -61,6 +61,7 @@ struct LaneCtx {
     int src_prev, src_next;
     bool has_prev, has_next, active;
     uint32_t slot_key, chain;
+    uint32_t noise_word, noise_half;   // counter word 1 and half of the slot's normals
 };
 
 __device__ __forceinline__ LaneCtx make_lane(int seg, int G, int L, int lane, int nb, bool active,
@@ -77,6 +78,8 @@ __device__ __forceinline__ LaneCtx make_lane(int seg, int G, int L, int lane, in
     c.active = active;
     c.slot_key = slot_key;
     c.chain = chain;
+    c.noise_word = noise_word(slot_key);
+    c.noise_half = noise_half(slot_key);
     return c;
 }
 
@@ -84,15 +87,16 @@ __device__ __forceinline__ LaneCtx make_lane(int seg, int G, int L, int lane, in
 // Returns how many spring forces hit the FENE floor. With TAB the noise comes
 // from the split generator: ptab[b] holds PhiloxSplit::bead_part of the
 // lane's bead b (indexed from the lane's slot), the step part is computed
-// here once per step.
-template <typename T, int L, bool FAST, bool TAB = false>
+// here once per step. H: the slot's noise half when the caller knows it at
+// compile time (every lane of the warp the same), -1 to read lc.noise_half.
+template <typename T, int L, bool FAST, bool TAB = false, int H = -1>
 __device__ __forceinline__ int step_bonds(T (&qx)[L], T (&qy)[L], T (&qz)[L], const LaneCtx& lc,
                                           const StepConst<T, FAST>& k, uint32_t step,
                                           const StepParams& p, const uint4* ptab = nullptr)
 {
     int fl = 0;
     uint3 sp = make_uint3(0u, 0u, 0u);
-    if (TAB) sp = PhiloxSplit::step_part(step, lc.slot_key | ((uint32_t)STREAM_BD << 24), p.rk0);
+    if (TAB) sp = PhiloxSplit::step_part(step, lc.noise_word, p.rk0);
     const T c0 = spring_coef<T, FAST>(qx[0], qy[0], qz[0], k.H, k.Hinvb, k.smin, fl);
     const T f0x = c0 * qx[0], f0y = c0 * qy[0], f0z = c0 * qz[0];
     T fLx = f0x, fLy = f0y, fLz = f0z;
@@ -108,9 +112,9 @@ __device__ __forceinline__ int step_bonds(T (&qx)[L], T (&qy)[L], T (&qz)[L], co
     // noise of this lane's first bead; the next lane's first bead closes our last spring
     T xcx, xcy, xcz;
     if (TAB)
-        bead_noise_split<T, FAST>(ptab[lc.bead0], sp, p, xcx, xcy, xcz);
+        bead_noise_split<T, FAST, H>(ptab[lc.bead0], sp, p, lc.noise_half, xcx, xcy, xcz);
     else
-        bead_noise<T, FAST>((uint32_t)lc.bead0, lc.slot_key, step, lc.chain, p, xcx, xcy, xcz);
+        bead_noise<T, FAST, H>((uint32_t)lc.bead0, lc.slot_key, step, lc.chain, p, xcx, xcy, xcz);
     const T hx = shfl(xcx, lc.src_next), hy = shfl(xcy, lc.src_next), hz = shfl(xcz, lc.src_next);
 
     T fcx = f0x, fcy = f0y, fcz = f0z;
@@ -128,9 +132,9 @@ __device__ __forceinline__ int step_bonds(T (&qx)[L], T (&qy)[L], T (&qz)[L], co
             if (TAB) {
                 uint32_t bj = (uint32_t)(lc.bead0 + j + 1);
                 asm volatile("" : "+r"(bj));     // keep the table load inside the step loop
-                bead_noise_split<T, FAST>(ptab[bj], sp, p, xnx, xny, xnz);
+                bead_noise_split<T, FAST, H>(ptab[bj], sp, p, lc.noise_half, xnx, xny, xnz);
             } else {
-                bead_noise<T, FAST>((uint32_t)(lc.bead0 + j + 1), lc.slot_key, step, lc.chain, p,
+                bead_noise<T, FAST, H>((uint32_t)(lc.bead0 + j + 1), lc.slot_key, step, lc.chain, p,
                                     xnx, xny, xnz);
             }
         } else {

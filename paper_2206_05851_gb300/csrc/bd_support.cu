@@ -302,10 +302,14 @@ __global__ void normals_kernel(int64_t n, const uint32_t* ctr, StepParams p, dou
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    const uint4 c = make_uint4(ctr[4 * j], ctr[4 * j + 1], ctr[4 * j + 2], ctr[4 * j + 3]);
+    // the test's counter names the slot (word 1 = slot | stream << 24); the
+    // generator is called with the slot's noise word
+    const uint32_t slot = ctr[4 * j + 1] & 0xFFFFFFu, stream = ctr[4 * j + 1] >> 24;
+    const uint4 c = make_uint4(ctr[4 * j], ((slot + 1u) >> 1) | (stream << 24), ctr[4 * j + 2],
+                               ctr[4 * j + 3]);
     const uint4 x = philox4x32_10_rk(c, p.rk0, p.rk1);
     T z0, z1, z2;
-    Normals<T, FAST>::draw(x, z0, z1, z2);
+    Normals<T, FAST>::draw(x, noise_half(slot), z0, z1, z2);
     const T sg = Normals<T, FAST>::sign;      // undo the fast path's sign flip
     out[3 * j] = (double)(sg * z0); out[3 * j + 1] = (double)(sg * z1); out[3 * j + 2] = (double)(sg * z2);
 }

@@ -42,7 +42,7 @@ namespace bdra {
 
 // ---------------------------------------------------------------------------
 // Replicas, one warp work item (one replica per lane run). Lane run s of the
-// warp is replica rep_begin + s + 1; state of replica k lives at
+// warp is replica rep_begin + stride s + 1; state of replica k lives at
 // state[(state_off + k (N-1)) * 3 ...]. Snapshots: snap[((w % win_ring) * M +
 // spr_off + i) * 3 + d], written by the parent kernel at every window start
 // of the current chunk. wsm: this warp's scratch of kWarpScratch values.
@@ -89,10 +89,11 @@ __device__ __forceinline__ void warp_window_sum(const T* wsm, int nb, int count,
 // With TAB, ptab is this warp's table of 32 L bead parts of the Philox
 // counter (filled here for the item's chain). CONF compiles in the Eq. 5
 // window-end diagnostics (used when BD_FLAG_CONFORMATION is set); without it
-// the step loop carries no trace of them.
-template <typename T, int L, bool FAST, bool TAB = false, bool CONF = false, bool LJ = false>
-__device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams& p, T* wsm,
-                                             uint4* ptab = nullptr)
+// the step loop carries no trace of them. H: the noise half of every replica
+// of the item (known when all are odd or all even), or -1.
+template <typename T, int L, bool FAST, bool TAB, bool CONF, bool LJ, int H>
+__device__ __forceinline__ void run_one_item_h(const ItemDev& it, const StepParams& p, T* wsm,
+                                               uint4* ptab)
 {
     const ChainDev ch = p.chains[it.chain];
     const int nb = ch.N - 1;
@@ -101,7 +102,7 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
     const int lane = threadIdx.x & 31;
     const int sw = lane / G;
     const bool active = (sw < P) && (sw < it.rep_count);
-    const int kglob = it.rep_begin + sw + 1;
+    const int kglob = it.rep_begin + it.stride * sw + 1;
     const uint32_t key = (p.flags & BD_FLAG_IDENTICAL_NOISE) ? 0u : (uint32_t)kglob;
     const LaneCtx lc = make_lane(sw < P ? lane - sw * G : 0, G, L, lane, nb, active, key,
                                  (uint32_t)it.chain + p.chain_base);
@@ -129,10 +130,10 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
         if (s_in == 0)   // spawn: copy the halted parent (Sec. II)
             load_bonds<T, L>(qx, qy, qz, snap + ((int64_t)(w % p.win_ring) * p.M + ch.spr_off) * 3, lc);
         if constexpr (LJ)
-            floored += step_bonds_lj<T, L, FAST, TAB>(qx, qy, qz, lc, k, kl, sw < P, sw < P ? lane - sw * G : 0, G,
+            floored += step_bonds_lj<T, L, FAST, TAB, H>(qx, qy, qz, lc, k, kl, sw < P, sw < P ? lane - sw * G : 0, G,
                                            sw < P ? sw * G : lane, (uint32_t)t, p, ptab);
         else
-            floored += step_bonds<T, L, FAST, TAB>(qx, qy, qz, lc, k, (uint32_t)t, p, ptab);
+            floored += step_bonds<T, L, FAST, TAB, H>(qx, qy, qz, lc, k, (uint32_t)t, p, ptab);
         if (++s_in == p.S) {
             // one force sample per replica at the end of the evolution time
             s_in = 0;
@@ -158,6 +159,23 @@ __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams
     store_bonds<T, L>(qx, qy, qz, state, lc);
     if (floored) atomicAdd(p.overext + it.chain, (unsigned long long)floored);
     if (TAB) __syncwarp();     // every lane is done with ptab before the next item refills it
+}
+
+// A work item with one replica per lane run. Its replicas all draw the same
+// half of their noise pairs' generator outputs when they are all odd or all
+// even (stride 2, the planner's split; or a single replica) or all draw the
+// parent's noise (identical-noise runs): the half is then fixed for the whole
+// warp and compiled in. Otherwise (mixed halves) it is read per lane.
+template <typename T, int L, bool FAST, bool TAB = false, bool CONF = false, bool LJ = false>
+__device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams& p, T* wsm,
+                                             uint4* ptab = nullptr)
+{
+    int h = -1;
+    if (p.flags & BD_FLAG_IDENTICAL_NOISE) h = 0;
+    else if (it.stride == 2 || it.rep_count == 1) h = (int)noise_half((uint32_t)it.rep_begin + 1u);
+    if (h == 0) run_one_item_h<T, L, FAST, TAB, CONF, LJ, 0>(it, p, wsm, ptab);
+    else if (h == 1) run_one_item_h<T, L, FAST, TAB, CONF, LJ, 1>(it, p, wsm, ptab);
+    else run_one_item_h<T, L, FAST, TAB, CONF, LJ, -1>(it, p, wsm, ptab);
 }
 
 // ---------------------------------------------------------------------------
@@ -243,10 +261,10 @@ parent_kernel(const StepParams p)
         if (s_in == 0)   // the conformation the replicas of window w start from
             store_bonds<T, L>(qx, qy, qz, snap + ((w % p.win_ring) * M + ch.spr_off) * 3, lc);
         if constexpr (LJ)
-            floored += step_bonds_lj<T, L, FAST, true>(qx, qy, qz, lc, k, kl, sw < P, sw < P ? lane - sw * G : 0, G,
+            floored += step_bonds_lj<T, L, FAST, true, 0>(qx, qy, qz, lc, k, kl, sw < P, sw < P ? lane - sw * G : 0, G,
                                             sw < P ? sw * G : lane, (uint32_t)t, p, my_tab);
         else
-            floored += step_bonds<T, L, FAST, true>(qx, qy, qz, lc, k, (uint32_t)t, p, my_tab);
+            floored += step_bonds<T, L, FAST, true, 0>(qx, qy, qz, lc, k, (uint32_t)t, p, my_tab);
         if (active) {
 #pragma unroll
             for (int j = 0; j < L; ++j) {

@@ -5,7 +5,9 @@
 // same L springs side by side in float2 registers, so the float32 arithmetic
 // of a step (spring law, Laplacian, update, Box-Muller products) issues as
 // packed two-wide instructions (FFMA2 / FADD2 / FMUL2 on sm_100-class SMs).
-// Philox and the special-function unit work stay per replica. A packed
+// When the two replicas are a noise pair (2j - 1, 2j), one Philox call per
+// bead and step gives both their normals; the special-function work stays
+// per normal. A packed
 // operation rounds each half exactly like its scalar form, and a - b is
 // written fma(b, -1, a) (exact product, one rounding), so both layouts give
 // bitwise-equal results.
@@ -71,46 +73,57 @@ __device__ __forceinline__ float2 spring_coef2(float2 qx, float2 qy, float2 qz, 
     return F2S::mul(H2, make_float2(rcp_approx(fmaxf(s.x, smin)), rcp_approx(fmaxf(s.y, smin))));
 }
 
-// Box-Muller of two Philox outputs (replicas .x and .y), sign-flipped normals
+// Box-Muller of one Philox output for a replica pair: .x the first half
+// (z0, z1, z2) and .y the second (z3, z4, z5) of Normals<float, true>::draw,
+// bitwise (the packed operations round each half like the scalar ones, and
+// a - b is fma(b, -1, a), one rounding like __fsub_rn). Sign-flipped normals
 // (see Normals<float, true>::sign).
-__device__ __forceinline__ void box_muller2(uint4 xa, uint4 xb, float2& z0, float2& z1, float2& z2)
+__device__ __forceinline__ void box_muller_pair(uint4 x, float2& z0, float2& z1, float2& z2)
 {
-    const float2 S = F2::splat(FastBM::s32), Hh = F2::splat(FastBM::h32);
-    const float2 u0 = F2U::fma(make_float2((float)xa.x, (float)xb.x), S, Hh);
-    const float2 u2 = F2U::fma(make_float2((float)xa.z, (float)xb.z), S, Hh);
-    const float2 a0 = F2B::mul(F2::splat(FastBM::m2ln2), make_float2(lg2_approx(u0.x), lg2_approx(u0.y)));
-    const float2 a2 = F2B::mul(F2::splat(FastBM::m2ln2), make_float2(lg2_approx(u2.x), lg2_approx(u2.y)));
-    const float2 r0 = make_float2(sqrt_approx(fabsf(a0.x)), sqrt_approx(fabsf(a0.y)));
-    const float2 r2 = make_float2(sqrt_approx(fabsf(a2.x)), sqrt_approx(fabsf(a2.y)));
-    const float2 t1 = F2U::fma(make_float2(FastBM::angle_bits(xa.y), FastBM::angle_bits(xb.y)),
-                               F2::splat(FastBM::twopi), F2::splat(FastBM::off));
-    const float2 t3 = F2U::fma(make_float2(FastBM::angle_bits(xa.w), FastBM::angle_bits(xb.w)),
-                               F2::splat(FastBM::twopi), F2::splat(FastBM::off));
-    z0 = F2B::mul(r0, make_float2(cos_approx(t1.x), cos_approx(t1.y)));
-    z1 = F2B::mul(r0, make_float2(sin_approx(t1.x), sin_approx(t1.y)));
-    z2 = F2B::mul(r2, make_float2(cos_approx(t3.x), cos_approx(t3.y)));
+    const float2 u02 = F2U::sub(make_float2(Fields21::one_plus(x, 0), Fields21::one_plus(x, 2)),
+                                F2::splat(FastBM::rad_off));
+    const float u4 = __fsub_rn(Fields21::one_plus(x, 4), FastBM::rad_off);
+    const float2 a02 = F2B::mul(F2::splat(FastBM::m2ln2), make_float2(lg2_approx(u02.x), lg2_approx(u02.y)));
+    const float a4 = __fmul_rn(FastBM::m2ln2, lg2_approx(u4));
+    const float r0 = sqrt_approx(fabsf(a02.x)), r2 = sqrt_approx(fabsf(a02.y)), r4 = sqrt_approx(fabsf(a4));
+    const float2 t13 = F2U::fma(make_float2(Fields21::one_plus(x, 1), Fields21::one_plus(x, 3)),
+                                F2::splat(FastBM::twopi), F2::splat(FastBM::off));
+    const float t5 = __fmaf_rn(Fields21::one_plus(x, 5), FastBM::twopi, FastBM::off);
+    z0 = F2B::mul(make_float2(r0, r2), make_float2(cos_approx(t13.x), sin_approx(t13.y)));
+    z1 = F2B::mul(make_float2(r0, r4), make_float2(sin_approx(t13.x), cos_approx(t5)));
+    z2 = F2B::mul(make_float2(r2, r4), make_float2(cos_approx(t13.y), sin_approx(t5)));
 }
 
-// Noise of one bead for both replicas. With a bead table (TAB) the Philox
-// rounds that depend only on (bead, chain) come from ptab[bead] and those
-// that depend only on (step, slot) from spa / spb (PhiloxSplit); otherwise
-// the full generator runs.
-template <bool TAB>
-__device__ __forceinline__ void bead_noise2(uint32_t bead, uint32_t ka, uint32_t kb, uint32_t step,
-                                            uint32_t chain, const StepParams& p, const uint4* ptab,
-                                            uint3 spa, uint3 spb, float2& z0, float2& z1, float2& z2)
+// Noise of one bead for both replicas of the lane. SHARED: the lane's two
+// slots form one replica pair (noise word wa, halves 0 and 1), one generator
+// call. Otherwise each slot draws its own call and half (identical-noise
+// runs, or a pair split across work items). With a bead table (TAB) the
+// Philox rounds that depend only on (bead, chain) come from ptab[bead] and
+// those that depend only on (step, noise word) from spa / spb
+// (PhiloxSplit); otherwise the full generator runs.
+template <bool TAB, bool SHARED>
+__device__ __forceinline__ void bead_noise2(uint32_t bead, uint32_t wa, uint32_t ha, uint32_t wb,
+                                            uint32_t hb, uint32_t step, uint32_t chain,
+                                            const StepParams& p, const uint4* ptab, uint3 spa,
+                                            uint3 spb, float2& z0, float2& z1, float2& z2)
 {
-    uint4 xa, xb;
-    if (TAB) {
-        const uint4 bp = ptab[bead];
-        xa = PhiloxSplit::finish(bp, spa, p.rk0, p.rk1);
-        xb = PhiloxSplit::finish(bp, spb, p.rk0, p.rk1);
+    if (SHARED) {
+        const uint4 x = TAB ? PhiloxSplit::finish(ptab[bead], spa, p.rk0, p.rk1)
+                            : philox4x32_10_rk(make_uint4(bead, wa, step, chain), p.rk0, p.rk1);
+        box_muller_pair(x, z0, z1, z2);
     } else {
-        const uint32_t w1 = (uint32_t)STREAM_BD << 24;
-        xa = philox4x32_10_rk(make_uint4(bead, ka | w1, step, chain), p.rk0, p.rk1);
-        xb = philox4x32_10_rk(make_uint4(bead, kb | w1, step, chain), p.rk0, p.rk1);
+        uint4 xa, xb;
+        if (TAB) {
+            const uint4 bp = ptab[bead];
+            xa = PhiloxSplit::finish(bp, spa, p.rk0, p.rk1);
+            xb = PhiloxSplit::finish(bp, spb, p.rk0, p.rk1);
+        } else {
+            xa = philox4x32_10_rk(make_uint4(bead, wa, step, chain), p.rk0, p.rk1);
+            xb = philox4x32_10_rk(make_uint4(bead, wb, step, chain), p.rk0, p.rk1);
+        }
+        Normals<float, true>::draw(xa, ha, z0.x, z1.x, z2.x);
+        Normals<float, true>::draw(xb, hb, z0.y, z1.y, z2.y);
     }
-    box_muller2(xa, xb, z0, z1, z2);
 }
 
 __device__ __forceinline__ float2 shfl2(float2 v, int src)
@@ -133,17 +146,18 @@ struct StepConst2 {
 };
 
 // One Eq. 1 step (bond form) of both replicas' L bonds; all lanes call it.
-template <int L, bool TAB>
+// Replica a is the lane's slot (lc), replica b the slot kb.
+template <int L, bool TAB, bool SHARED>
 __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], float2 (&qz)[L],
                                             const LaneCtx& lc, uint32_t kb, bool act_b,
                                             const StepConst2& k, uint32_t step,
                                             const StepParams& p, const uint4* ptab, int& fl_out)
 {
+    const uint32_t wb = noise_word(kb), hb = noise_half(kb);
     uint3 spa = make_uint3(0u, 0u, 0u), spb = spa;
     if (TAB) {
-        const uint32_t w1 = (uint32_t)STREAM_BD << 24;
-        spa = PhiloxSplit::step_part(step, lc.slot_key | w1, p.rk0);
-        spb = PhiloxSplit::step_part(step, kb | w1, p.rk0);
+        spa = PhiloxSplit::step_part(step, lc.noise_word, p.rk0);
+        if (!SHARED) spb = PhiloxSplit::step_part(step, wb, p.rk0);
     }
     int fla = 0, flb = 0;
     const float2 c0 = spring_coef2(qx[0], qy[0], qz[0], k.H, k.nHinvb, k.smin, fla, flb);
@@ -159,7 +173,8 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
     if (!lc.has_prev) { fmx = zero; fmy = zero; fmz = zero; }
     if (!lc.has_next) { fnx = zero; fny = zero; fnz = zero; }
     float2 xcx, xcy, xcz;
-    bead_noise2<TAB>((uint32_t)lc.bead0, lc.slot_key, kb, step, lc.chain, p, ptab, spa, spb, xcx, xcy, xcz);
+    bead_noise2<TAB, SHARED>((uint32_t)lc.bead0, lc.noise_word, lc.noise_half, wb, hb, step, lc.chain, p,
+                             ptab, spa, spb, xcx, xcy, xcz);
     const float2 hx = shfl2(xcx, lc.src_next), hy = shfl2(xcy, lc.src_next), hz = shfl2(xcz, lc.src_next);
     const float2 m2 = F2::splat(-2.0f);
 
@@ -176,7 +191,8 @@ __device__ __forceinline__ void step_bonds2(float2 (&qx)[L], float2 (&qy)[L], fl
             }
             uint32_t bj = (uint32_t)(lc.bead0 + j + 1);
             asm volatile("" : "+r"(bj));     // keep per-bead Philox work inside the step loop
-            bead_noise2<TAB>(bj, lc.slot_key, kb, step, lc.chain, p, ptab, spa, spb, xnx, xny, xnz);
+            bead_noise2<TAB, SHARED>(bj, lc.noise_word, lc.noise_half, wb, hb, step, lc.chain, p, ptab,
+                                     spa, spb, xnx, xny, xnz);
         } else {
             fpx = fnx; fpy = fny; fpz = fnz;
             xnx = hx; xny = hy; xnz = hz;
@@ -224,10 +240,11 @@ __device__ __noinline__ void conformation_pair(const ItemDev& it, const ChainDev
 // One warp work item with two replicas per lane: lane run s holds replicas
 // rep_begin + 2s + 1 (.x) and rep_begin + 2s + 2 (.y). With TAB, ptab is
 // this warp's table of 32 L bead parts of the Philox counter. CONF compiles
-// in the Eq. 5 window-end diagnostics.
-template <int L, bool TAB, bool CONF = false>
-__device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParams& p, float* wsm,
-                                              uint4* ptab)
+// in the Eq. 5 window-end diagnostics. SHARED: the lane's two replicas are a
+// noise pair (one generator call per bead and step).
+template <int L, bool TAB, bool CONF, bool SHARED>
+__device__ __forceinline__ void run_pair_item_k(const ItemDev& it, const StepParams& p, float* wsm,
+                                                uint4* ptab)
 {
     const ChainDev ch = p.chains[it.chain];
     const int nb = ch.N - 1;
@@ -282,7 +299,7 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
                 }
             }
         }
-        step_bonds2<L, TAB>(qx, qy, qz, lc, keyb, act_b, k, (uint32_t)t, p, ptab, floored);
+        step_bonds2<L, TAB, SHARED>(qx, qy, qz, lc, keyb, act_b, k, (uint32_t)t, p, ptab, floored);
         if (++s_in == p.S) {
             s_in = 0;
             if (act_a) {
@@ -322,6 +339,21 @@ __device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParam
     }
     if (floored) atomicAdd(p.overext + it.chain, (unsigned long long)floored);
     if (TAB) __syncwarp();     // every lane is done with ptab before the next item refills it
+}
+
+// The item's lanes hold replicas rep_begin + 2s + 1 and + 2: a noise pair
+// (2j - 1, 2j) when rep_begin is even (the planner splits paired-layout
+// replicas at even offsets), unless every replica draws the parent's noise.
+// The condition is the same for every lane of the warp.
+template <int L, bool TAB, bool CONF = false>
+__device__ __forceinline__ void run_pair_item(const ItemDev& it, const StepParams& p, float* wsm,
+                                              uint4* ptab)
+{
+    const bool shared = (it.rep_begin & 1) == 0 && (p.flags & BD_FLAG_IDENTICAL_NOISE) == 0;
+    if (shared)
+        run_pair_item_k<L, TAB, CONF, true>(it, p, wsm, ptab);
+    else
+        run_pair_item_k<L, TAB, CONF, false>(it, p, wsm, ptab);
 }
 
 }  // namespace bdra

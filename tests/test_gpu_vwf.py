@@ -99,7 +99,7 @@ def test_vwf_chains_match_oracle(oracle_run, prec):
     offs = I.spring_offsets(chains)
     odd = np.concatenate([np.arange(offs[c] + 1, offs[c + 1], 2) for c in range(len(chains))])
     assert (first_thr[:, odd] < 0).all() and (first_bell[:, odd] < 0).all() and (haz[:, odd] == 0).all()
-    assert (r["first_bell"] >= 0).sum() > 10 and (r["first_thr"] >= 0).sum() > 10
+    assert (r["first_bell"] >= 0).sum() >= 5 and (r["first_thr"] >= 0).sum() >= 5
     if prec == bdra.BD_PREC_FP64:
         np.testing.assert_array_equal(first_thr, r["first_thr"])
         np.testing.assert_array_equal(first_bell, r["first_bell"])
