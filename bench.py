@@ -12,6 +12,14 @@ FENE coils from a seeded generator) and resident in HBM.
 
 Metric: bead-steps/s = chains x replicas x beads x steps / time.
 
+Beside the main line the default run reports the FP64 path on the same
+chains, an end-to-end run through the C ABI with host buffers, the batched
+uneven (4096 chains) and Bell-kinetics (16384 chains) configurations, the
+differentiation workload, the paper's model lines (collapsed chains, RPY,
+vWF), each with its roofline, CPU oracle baseline and errors against the
+oracle. Under torchrun each rank integrates its contiguous range of one
+workload of N x the configuration's chains (weak scaling).
+
 --impl reference times the CPU FP64 oracle (the only reference this method
 has) on a bounded sample of the same workload.
 """
