@@ -63,6 +63,19 @@ ROUNDS_PER_BEAD_STEP_SINGLE = 8
 SURVEY_OPS_PER_BEAD_STEP = 140.0
 
 
+def measured_issue_ceiling(sptr):
+    """The highest thread-instruction issue rate this GPU has shown in the
+    library's probes (independent chains, full occupancy, no memory traffic):
+    the mixed float32 / integer stream of bd_probe_issue, and the float32 FMA
+    stream of bd_probe_fp32_fma (one instruction per FMA, FLOP/s / 2), which
+    issues closer to one warp instruction per scheduler and clock. Returns
+    (ceiling, mixed rate, FMA rate)."""
+    from paper_2206_05851_gb300 import bdra
+    mixed = bdra.bd_probe_issue(sptr)
+    fma = bdra.bd_probe_fp32_fma(sptr) / 2.0
+    return max(mixed, fma), mixed, fma
+
+
 def plan_work(ctx, chains):
     """Bead-step-weighted minimal lane-instructions and Philox rounds per
     slot-bead-step of a context's plan (two replicas a lane or one)."""
@@ -455,8 +468,9 @@ def replica_line(wl, pos0, base, chunk, steps, warmup, sptr, autotune, issue_pea
             "traffic_unit": "bytes per launch (ncu capture)",
             "kernel": "replica kernel (planner's float32 tile)", "avg_launch_ms": rep_ms / max(rep_n, 1),
             "launches": rep_n, "share_of_step": rep_ms / t_ms,
-            "peak_basis": "measured: bd_probe_issue (mixed float32 / integer instruction issue, "
-                          "full occupancy) on this GPU before the timed region",
+            "peak_basis": "measured before the timed region: the higher issue rate of the library's "
+                          "mixed float32/integer probe (bd_probe_issue) and float32 FMA probe "
+                          "(bd_probe_fp32_fma / 2)",
             "peak_derived": derived / 1e12, "frac_of_derived": achieved / derived,
             "ops_per_bead_step": ops, "paired_share": paired_share,
             "ops_basis": f"minimal lane-instructions per slot-bead-step of the plan's layouts "
@@ -615,7 +629,7 @@ def collapsed_line(sptr, n_chains=0, n_steps=3000, fp64_chains=64, issue_peak=No
     achieved = ops * units / (rep_ms / 1e3) / 1e12
     derived = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     if issue_peak is None:
-        issue_peak = bdra.bd_probe_issue(sptr)           # measured, outside the timed region
+        issue_peak = measured_issue_ceiling(sptr)[0]     # measured, outside the timed region
     peak = issue_peak / 1e12
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instructions/s",
                        "frac": achieved / peak, "peak_derived": derived, "frac_of_derived": achieved / derived,
@@ -624,7 +638,7 @@ def collapsed_line(sptr, n_chains=0, n_steps=3000, fp64_chains=64, issue_peak=No
                        "kernel": "collapsed-chain replica kernel (float32)",
                        "avg_launch_ms": rep_ms / max(rep_n, 1), "launches": rep_n,
                        "share_of_step": rep_ms / (t * 1e3), "ops_per_bead_step": ops,
-                       "peak_basis": "measured: bd_probe_issue (mixed float32 / integer instruction issue)"}
+                       "peak_basis": "measured: the higher issue rate of bd_probe_issue and bd_probe_fp32_fma / 2"}
     out["parent_kernel_share"] = par_ms / (t * 1e3)
     # FP64 and the FP32 force error on a subset
     sub = wl.chains[:fp64_chains]
@@ -1069,7 +1083,7 @@ def main():
         dist.barrier()
     bdra.load()
     sptr = torch.cuda.current_stream().cuda_stream
-    issue_peak = bdra.bd_probe_issue(sptr)               # measured ceilings, outside any timed region
+    issue_peak, issue_mixed, issue_fma = measured_issue_ceiling(sptr)   # outside any timed region
     philox_peak = bdra.bd_probe_philox_rounds(sptr)
 
     # one workload of world x the configuration's chains, split into contiguous
@@ -1177,6 +1191,8 @@ def main():
         # measured per-unit ceilings of this GPU (context for every fraction above)
         out["measured_unit_peaks"] = {
             "issue_lane_instr_per_s": issue_peak,
+            "issue_mixed_fp32_int_lane_instr_per_s": issue_mixed,
+            "issue_fp32_fma_lane_instr_per_s": issue_fma,
             "philox_rounds_per_s": philox_peak,
             "fp32_fma_flops": bdra.bd_probe_fp32_fma(sptr),
             "fp64_fma_flops": bdra.bd_probe_fp64_fma(sptr),

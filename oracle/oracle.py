@@ -37,8 +37,10 @@ def build(force: bool = False) -> str:
         return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "bd_oracle.h"))):
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+        tmp = f"{_LIB}.{os.getpid()}.tmp"      # then renamed: concurrent builds never see half a file
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
     return _LIB
 
 

@@ -10,6 +10,8 @@ event compaction and the Philox-round throughput probe. Only nvcc is needed; no 
 from __future__ import annotations
 
 import concurrent.futures as cf
+import contextlib
+import fcntl
 import os
 import subprocess
 import sys
@@ -50,16 +52,36 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
+@contextlib.contextmanager
+def _locked(objdir: str):
+    """One build at a time per object directory (test processes that start
+    together would otherwise write the same objects and library)."""
+    os.makedirs(objdir, exist_ok=True)
+    with open(os.path.join(objdir, ".lock"), "w") as fh:
+        fcntl.flock(fh, fcntl.LOCK_EX)
+        try:
+            yield
+        finally:
+            fcntl.flock(fh, fcntl.LOCK_UN)
+
+
 def build(force: bool = False, verbose: bool = False, out: str = None,
           defines=(), csrc: str = None) -> str:
     """Compile csrc/ (or another source directory) into libbdra.so (or `out`),
     with optional -D defines."""
     lib = out or LIB
     src_dir = csrc or CSRC
-    if not force and out is None and not defines and csrc is None and up_to_date():
+    default = out is None and not defines and csrc is None
+    if not force and default and up_to_date():
         return LIB
     objdir = os.path.join(os.path.dirname(lib), "_build") if out else os.path.join(PKG, "_build")
-    os.makedirs(objdir, exist_ok=True)
+    with _locked(objdir):
+        if not force and default and up_to_date():     # built by another process meanwhile
+            return LIB
+        return _build(lib, src_dir, objdir, defines, verbose)
+
+
+def _build(lib: str, src_dir: str, objdir: str, defines, verbose: bool) -> str:
     nvcc = _nvcc()
 
     def compile_unit(unit):

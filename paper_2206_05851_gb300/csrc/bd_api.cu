@@ -287,6 +287,9 @@ void order_items(std::vector<ItemDev>& items)
     });
 }
 
+// The one-replica-per-lane kernels compile one noise half per item, so the
+// items built here must be single replicas or stride-2 runs (a mixed item
+// would draw the wrong half for some of its replicas).
 void split_replicas(int c, int R, int per_warp, int v, std::vector<ItemDev>& items)
 {
     int g = 0;

@@ -161,21 +161,18 @@ __device__ __forceinline__ void run_one_item_h(const ItemDev& it, const StepPara
     if (TAB) __syncwarp();     // every lane is done with ptab before the next item refills it
 }
 
-// A work item with one replica per lane run. Its replicas all draw the same
-// half of their noise pairs' generator outputs when they are all odd or all
-// even (stride 2, the planner's split; or a single replica) or all draw the
-// parent's noise (identical-noise runs): the half is then fixed for the whole
-// warp and compiled in. Otherwise (mixed halves) it is read per lane.
+// A work item with one replica per lane run. The planner gives such an item
+// only odd or only even replicas (stride 2) or a single one, so all its
+// replicas draw the same half of their noise pairs' generator outputs (in
+// identical-noise runs all draw the parent's, half 0): the half is fixed
+// for the whole warp and compiled in.
 template <typename T, int L, bool FAST, bool TAB = false, bool CONF = false, bool LJ = false>
 __device__ __forceinline__ void run_one_item(const ItemDev& it, const StepParams& p, T* wsm,
                                              uint4* ptab = nullptr)
 {
-    int h = -1;
-    if (p.flags & BD_FLAG_IDENTICAL_NOISE) h = 0;
-    else if (it.stride == 2 || it.rep_count == 1) h = (int)noise_half((uint32_t)it.rep_begin + 1u);
-    if (h == 0) run_one_item_h<T, L, FAST, TAB, CONF, LJ, 0>(it, p, wsm, ptab);
-    else if (h == 1) run_one_item_h<T, L, FAST, TAB, CONF, LJ, 1>(it, p, wsm, ptab);
-    else run_one_item_h<T, L, FAST, TAB, CONF, LJ, -1>(it, p, wsm, ptab);
+    const bool h1 = (p.flags & BD_FLAG_IDENTICAL_NOISE) == 0 && noise_half((uint32_t)it.rep_begin + 1u) == 1u;
+    if (h1) run_one_item_h<T, L, FAST, TAB, CONF, LJ, 1>(it, p, wsm, ptab);
+    else run_one_item_h<T, L, FAST, TAB, CONF, LJ, 0>(it, p, wsm, ptab);
 }
 
 // ---------------------------------------------------------------------------
