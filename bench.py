@@ -125,6 +125,10 @@ def parse():
     ap.add_argument("--workload", default="planar_1024",
                     choices=["planar_1024", "uneven_4096", "bell_16384"])
     ap.add_argument("--autotune", action="store_true", help="measure step variants first")
+    ap.add_argument("--lanes-hint", type=int, default=0,
+                    help="force the springs-per-lane tile of the main line (profiling)")
+    ap.add_argument("--layout-hint", type=int, default=0,
+                    help="force one (1) or two (2) replicas per lane on the main line (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -395,7 +399,8 @@ def kinetics_summary(first_thr, first_bell, chains, thr_mask, bell_mask, n_steps
 
 
 def replica_line(wl, pos0, base, chunk, steps, warmup, sptr, autotune, issue_peak, philox_peak,
-                 dist=None, traffic_at=None, keep_ctx=False, warm_chunk=None):
+                 dist=None, traffic_at=None, keep_ctx=False, warm_chunk=None, lanes_hint=0,
+                 layout_hint=0):
     """Times `steps` bench steps of `chunk` integration steps each, plus event
     detection, of the free-draining workload `wl` (this rank's chains, global
     chain index of the first: `base`), after `warmup` untimed steps of
@@ -413,7 +418,8 @@ def replica_line(wl, pos0, base, chunk, steps, warmup, sptr, autotune, issue_pea
     stream = torch.cuda.current_stream()
     ctx = bdra.Context(wl.chains, wl.dt, S, wl.seed, torch.from_numpy(pos0).cuda(),
                        precision=bdra.BD_PREC_FP32, max_windows=total_windows,
-                       thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=sptr, chain_id_base=base)
+                       thr_mask=wl.thr_mask, bell_mask=wl.bell_mask, stream=sptr, chain_id_base=base,
+                       lanes_hint=lanes_hint, layout_hint=layout_hint)
     if autotune:
         ctx.autotune(probe_steps=32)
     units_chunk = wl.bead_steps(chunk)
@@ -1094,7 +1100,8 @@ def main():
     wl = dataclasses.replace(wl_all, chains=chains)
     main_line, ctx = replica_line(wl, pos0, base, args.chunk, args.steps, args.warmup, sptr,
                                   args.autotune, issue_peak, philox_peak, dist if world > 1 else None,
-                                  traffic_at=REPLICA_TRAFFIC_AT, keep_ctx=True)
+                                  traffic_at=REPLICA_TRAFFIC_AT, keep_ctx=True,
+                                  lanes_hint=args.lanes_hint, layout_hint=args.layout_hint)
     out = {"metric": METRIC, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic"}
@@ -1193,6 +1200,7 @@ def main():
             "issue_lane_instr_per_s": issue_peak,
             "issue_mixed_fp32_int_lane_instr_per_s": issue_mixed,
             "issue_fp32_fma_lane_instr_per_s": issue_fma,
+            "int_alu_lop3_per_s": bdra.bd_probe_int_alu(sptr),
             "philox_rounds_per_s": philox_peak,
             "fp32_fma_flops": bdra.bd_probe_fp32_fma(sptr),
             "fp64_fma_flops": bdra.bd_probe_fp64_fma(sptr),

@@ -369,6 +369,13 @@ bd_status bd_probe_mufu(void* stream, double* ops_per_s);
  * not counted: low by at most 3%). Same conventions as the probes above. */
 bd_status bd_probe_issue(void* stream, double* lane_instr_per_s);
 
+/* Measured integer-ALU throughput (no counterpart in the paper: the unit of
+ * the noise fields' bit operations and Philox's XORs): independent chains of
+ * three-input logic operations (LOP3), full occupancy, no memory traffic.
+ * *ops_per_s (host) receives operations per second for the whole device.
+ * Same conventions as the probes above. */
+bd_status bd_probe_int_alu(void* stream, double* ops_per_s);
+
 /* Largest n_springs bd_compact_events_noalloc accepts (its fixed scratch
  * holds one count per 256 springs: 32 KiB of device memory). */
 #define BD_NOALLOC_MAX_SPRINGS (1 << 20)

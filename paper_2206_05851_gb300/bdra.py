@@ -108,6 +108,7 @@ def load() -> ctypes.CDLL:
         "bd_probe_fp64_fma": ([vp, P(ctypes.c_double)], st),
         "bd_probe_mufu": ([vp, P(ctypes.c_double)], st),
         "bd_probe_issue": ([vp, P(ctypes.c_double)], st),
+        "bd_probe_int_alu": ([vp, P(ctypes.c_double)], st),
         "bd_philox_normals": ([ctypes.c_uint64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp], st),
         "bd_compact_events_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.c_int32, vp,
                                        ctypes.c_int64, vp, vp], st),
@@ -324,6 +325,13 @@ def bd_probe_issue(stream: Optional[int] = None) -> float:
     current device, thread-instructions per second."""
     r = ctypes.c_double(0.0)
     _check(load().bd_probe_issue(stream, ctypes.byref(r)))
+    return r.value
+
+
+def bd_probe_int_alu(stream: Optional[int] = None) -> float:
+    """Measured integer-ALU (three-input logic) throughput, ops/s."""
+    r = ctypes.c_double(0.0)
+    _check(load().bd_probe_int_alu(stream, ctypes.byref(r)))
     return r.value
 
 

@@ -131,6 +131,27 @@ issue_probe(uint32_t* sink, int iters, float b, float c, uint32_t k)
     sink[g] = acc;
 }
 
+// Integer ALU pipe: independent chains of three-input logic operations
+// (LOP3, one instruction each, written as PTX), full occupancy.
+__global__ void __launch_bounds__(kProbeThreads, 2)
+lop3_probe(uint32_t* sink, int iters, uint32_t k)
+{
+    uint32_t z[kProbeChains];
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) z[j] = g * 0x9E3779B9u + (uint32_t)j;
+#pragma unroll 4
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < kProbeChains; ++j)
+            asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(z[j]) : "r"(k), "r"(g));
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) acc ^= z[j];
+    sink[g] = acc;
+}
+
 // Times `launch(iters)` on `stream` after a warm-up launch (iters 256) and
 // returns its duration in ms (0 on failure).
 template <typename F>
@@ -265,6 +286,29 @@ extern "C" bd_status bd_probe_issue(void* stream, double* lane_instr_per_s)
     cudaGetLastError();
     if (!(ms > 0.0f)) return BD_E_CUDA;
     *lane_instr_per_s = 3.0 * (double)blocks * kProbeThreads * iters * kProbeChains / (ms * 1e-3);
+    return BD_OK;
+}
+
+extern "C" bd_status bd_probe_int_alu(void* stream, double* ops_per_s)
+{
+    if (!ops_per_s) return BD_E_INVALID;
+    *ops_per_s = 0.0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int sms = probe_sms();
+    if (!sms) return BD_E_CUDA;
+    const int blocks = 2 * sms, iters = 8192;
+    uint32_t* sink = nullptr;
+    if (cudaMalloc((void**)&sink, sizeof(uint32_t) * (size_t)blocks * kProbeThreads) != cudaSuccess) {
+        cudaGetLastError();
+        return BD_E_OOM;
+    }
+    const float ms = probe_time(st, [&](int n) {
+        lop3_probe<<<blocks, kProbeThreads, 0, st>>>(sink, n, 0x5bd1e995u);
+    }, iters);
+    cudaFree(sink);
+    cudaGetLastError();
+    if (!(ms > 0.0f)) return BD_E_CUDA;
+    *ops_per_s = (double)blocks * kProbeThreads * iters * kProbeChains / (ms * 1e-3);
     return BD_OK;
 }
 

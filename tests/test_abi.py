@@ -178,6 +178,7 @@ def test_probe_rejects_null_output(lib):
     assert lib.bd_probe_fp64_fma(None, None) == bdra.BD_E_INVALID
     assert lib.bd_probe_mufu(None, None) == bdra.BD_E_INVALID
     assert lib.bd_probe_issue(None, None) == bdra.BD_E_INVALID
+    assert lib.bd_probe_int_alu(None, None) == bdra.BD_E_INVALID
 
 
 def test_binding_fails_loudly_when_library_missing(monkeypatch, tmp_path):
