@@ -58,9 +58,10 @@ OPS_PER_BEAD_STEP_SINGLE = 91.0
 # Philox rounds run per slot-bead-step (rounds 1-2 amortise per bead and step)
 ROUNDS_PER_BEAD_STEP_PAIRED = 4
 ROUNDS_PER_BEAD_STEP_SINGLE = 8
-# The survey's generic count of the free-draining bead-step (one Philox call
-# and two Box-Muller pairs per bead-step, unamortised), reported for context
-SURVEY_OPS_PER_BEAD_STEP = 140.0
+# A generic count of the free-draining bead-step (one unamortised Philox call
+# and two Box-Muller pairs per bead-step, about 140 lane-instructions),
+# reported for context
+GENERIC_OPS_PER_BEAD_STEP = 140.0
 
 
 def measured_issue_ceiling(sptr):
@@ -481,7 +482,7 @@ def replica_line(wl, pos0, base, chunk, steps, warmup, sptr, autotune, issue_pea
             "ops_per_bead_step": ops, "paired_share": paired_share,
             "ops_basis": f"minimal lane-instructions per slot-bead-step of the plan's layouts "
                          f"({OPS_PER_BEAD_STEP_PAIRED} two replicas a lane, {OPS_PER_BEAD_STEP_SINGLE} one)",
-            "frac_at_survey_count": SURVEY_OPS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3) / issue_peak}
+            "frac_at_generic_count": GENERIC_OPS_PER_BEAD_STEP * rep_units / (rep_ms / 1e3) / issue_peak}
     if clk:
         roof["frac_of_derived_at_measured_clock"] = achieved / (SMS * LANES_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6)
     # the same kernel against the measured ceiling of its Philox work
