@@ -99,11 +99,11 @@ def plan_work(ctx, chains):
 # kernel over one 1500-step window of its default workload, and the
 # collapsed-chain kernel over its timed 3000 steps (its sample rows still sit in
 # L2 when it ends, so they are not in its count).
-REPLICA_TRAFFIC_BYTES = (177_558_528 + 854_656_512 + 132_652_800 + 487_505_664) / 2
+REPLICA_TRAFFIC_BYTES = (172_927_744 + 853_351_168 + 129_504_768 + 486_531_584) / 2
 REPLICA_TRAFFIC_AT = ("fene_1024x_n100_r64_planar_wi5", 10_000)
 HI_TRAFFIC_BYTES = 4_345_600 + 760_832
 HI_TRAFFIC_AT = ("collapsed_hi_128x_n50_r50_shear30", 1500)
-COLLAPSED_TRAFFIC_BYTES = 32_902_400 + 449_280
+COLLAPSED_TRAFFIC_BYTES = 33_043_456 + 667_904
 COLLAPSED_TRAFFIC_AT = ("collapsed_1024x_n50_r50_shear30", 3000)
 # Minimal lane-instructions per non-adjacent Lennard-Jones pair of the
 # collapsed-chain model, the pair evaluated once, in units of the LJ length s
