@@ -62,10 +62,10 @@ template <typename T, int NTM> struct HIShared {
     uint16_t pair[kBeads * (kBeads + 1) / 2];
     // W's lower tiles (entry e of tile t at tiles[e][t]) until the threads
     // have loaded theirs, then the per-tile partial products (part[c][t])
-    union {
+    union alignas(16) {
         T tiles[16][kTiles];
         T part[8][kTiles];
-    } alignas(16) st;
+    } st;
     T com[3];
 };
 
