@@ -306,6 +306,111 @@ struct Fields21 {
     }
 };
 
+// Per-spring window sums of a parent: the running sum of its ISF samples
+// for the TSF (Sec. II) and the ISF Bell hazard of the current window with
+// the Exp(1) budget left at its start, rem = E - Lambda (Sec. III; a first
+// passage when the window's hazard reaches rem). Lambda itself lives in
+// float64 memory and is advanced at every window end and launch end.
+struct BellConst {
+    double k0dt, dx;     // k0 dt and dx of the chain's Bell law
+    float k0dtf, dxf;    // the same rounded to float32
+    __device__ void load(double k0, double dt, double dx_)
+    {
+        k0dt = k0 * dt;
+        dx = dx_;
+        k0dtf = (float)k0dt;
+        dxf = (float)dx_;
+    }
+};
+
+template <typename T> struct ParentSums;
+
+// Float64 integration: float64 sums.
+template <> struct ParentSums<double> {
+    double tsf, haz, rem;
+    __device__ __forceinline__ void start(double tsf0, double rem0)
+    {
+        tsf = tsf0;
+        haz = 0.0;
+        rem = rem0;
+    }
+    __device__ __forceinline__ void add_isf(double f) { tsf += f; }
+    // one step's hazard k0 dt e^(dx f); true once the window's hazard reaches rem
+    __device__ __forceinline__ bool add_hazard(double f, const BellConst& b, double*)
+    {
+        haz = fma(b.k0dt, exp(b.dx * f), haz);
+        return haz >= rem;
+    }
+    __device__ __forceinline__ double tsf_sum() const { return tsf; }
+    __device__ __forceinline__ double hazard() const { return haz; }
+    __device__ __forceinline__ void next_window(double rem0)
+    {
+        tsf = 0.0;
+        haz = 0.0;
+        rem = rem0;
+    }
+};
+
+// Float32 integration. Summing the float32 samples in float64 took two or
+// three float64 instructions per spring and step (widening, add, compare),
+// and float64 runs at 1/64 of the float32 rate on this GPU: the parent
+// kernels were float64-pipe bound. The sums are float-float pairs instead,
+// value hi + lo: each addition is the error-free TwoSum followed by a
+// renormalisation, so |lo| <= ulp(hi) / 2 and a sum of n terms is within
+// n 2^-47 max|partial sum| of the exact one (n 2^-53 for a float64 sum):
+// 1.1e-11 of the mean sample for a 1500-step window. The hazard increment
+// k0 dt e^(dx f) is taken in float32 (expf, within 2 ulp, and two product
+// roundings): about 1e-7 relative, two orders below the error of the float32
+// tension itself. An increment with dx f >= 80 (e^80 = 5.5e34, far past any
+// budget) takes the float64 exponential and goes straight into Lambda in
+// memory, the budget lowered by the same amount, so the pairs overflow only
+// where the float64 sums would.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x)
+{
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    const float l = __fadd_rn(lo, e);
+    hi = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+__device__ __forceinline__ void ff_from(double d, float& hi, float& lo)
+{
+    hi = __double2float_rn(d);
+    lo = isinf(hi) ? 0.0f : __double2float_rn(d - (double)hi);
+}
+__device__ __forceinline__ double ff_to(float hi, float lo) { return (double)hi + (double)lo; }
+
+template <> struct ParentSums<float> {
+    float t_hi, t_lo, h_hi, h_lo, r_hi, r_lo;
+    __device__ __forceinline__ void start(double tsf0, double rem0)
+    {
+        ff_from(tsf0, t_hi, t_lo);
+        h_hi = h_lo = 0.0f;
+        ff_from(rem0, r_hi, r_lo);
+    }
+    __device__ __forceinline__ void add_isf(float f) { ff_add(t_hi, t_lo, f); }
+    __device__ __forceinline__ bool add_hazard(float f, const BellConst& b, double* lam)
+    {
+        const float x = __fmul_rn(b.dxf, f);
+        if (x < 80.0f) {
+            ff_add(h_hi, h_lo, __fmul_rn(b.k0dtf, expf(x)));
+        } else {
+            const double inc = b.k0dt * exp(b.dx * (double)f);
+            *lam += inc;
+            ff_from(ff_to(r_hi, r_lo) - inc, r_hi, r_lo);
+        }
+        return __fadd_rn(__fsub_rn(h_hi, r_hi), __fsub_rn(h_lo, r_lo)) >= 0.0f;
+    }
+    __device__ __forceinline__ double tsf_sum() const { return ff_to(t_hi, t_lo); }
+    __device__ __forceinline__ double hazard() const { return ff_to(h_hi, h_lo); }
+    __device__ __forceinline__ void next_window(double rem0)
+    {
+        t_hi = t_lo = h_hi = h_lo = 0.0f;
+        ff_from(rem0, r_hi, r_lo);
+    }
+};
+
 template <typename T, bool FAST> struct Normals;
 
 __device__ __forceinline__ float rcp_approx(float x)

@@ -677,9 +677,10 @@ hi_parent_kernel(const StepParams p)
     const bool isf_thr = (p.thr_mask & BD_CRIT_ISF) != 0;
     const bool isf_bell = (p.bell_mask & BD_CRIT_ISF) != 0;
     const T fc = (T)ch.f_c;
-    const double k0dt = ch.k0 * p.dt, dxs = ch.dx;
-    double tsf = mine ? p.tsf_acc[m] : 0.0;     // the time-average sum in float64
-    double haz = 0.0, rem = mine ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0;
+    BellConst bk;
+    bk.load(ch.k0, p.dt, ch.dx);
+    ParentSums<T> sums;     // time-average sum and window hazard: float64, or float-float pairs
+    sums.start(mine ? p.tsf_acc[m] : 0.0, mine ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0);
     const bool quiet = ch.spring == BD_SPRING_VWF && (i & 1);   // disulfide bonds do not unfold
     bool thr_done = !mine || quiet || p.first_thr[CRIT_Q_ISF * M + m] >= 0;
     bool bell_done = !mine || quiet || p.first_bell[CRIT_Q_ISF * M + m] >= 0;
@@ -703,14 +704,14 @@ hi_parent_kernel(const StepParams p)
             const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
             const T f = harmonic ? rest_law_tension<T, FAST>(qx, qy, qz, (i & 1) == 0, k.H, kl, k.smin)
                                  : spring_tension<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin);
-            tsf += (double)f;
+            sums.add_isf(f);
             if (isf_thr && !thr_done && f >= fc) {
                 thr_done = true;
                 p.first_thr[CRIT_Q_ISF * M + m] = t + 1;
             }
             if (isf_bell && !quiet) {
-                haz = fma(k0dt, exp(dxs * (double)f), haz);
-                if (!bell_done && haz >= rem) {
+                const bool reached = sums.add_hazard(f, bk, p.lam + CRIT_Q_ISF * M + m);
+                if (!bell_done && reached) {
                     bell_done = true;
                     p.first_bell[CRIT_Q_ISF * M + m] = t + 1;
                 }
@@ -719,14 +720,14 @@ hi_parent_kernel(const StepParams p)
         if (++s_in == p.S) {
             s_in = 0;
             if (mine) {
-                p.tsf_hist[w * M + m] = tsf / (double)p.S;
-                tsf = 0.0;
+                p.tsf_hist[w * M + m] = sums.tsf_sum() / (double)p.S;
+                double rem = 0.0;
                 if (isf_bell) {
-                    const double lam = p.lam[CRIT_Q_ISF * M + m] + haz;
+                    const double lam = p.lam[CRIT_Q_ISF * M + m] + sums.hazard();
                     p.lam[CRIT_Q_ISF * M + m] = lam;
-                    haz = 0.0;
                     rem = p.exp1[CRIT_Q_ISF * M + m] - lam;
                 }
+                sums.next_window(rem);
             }
             ++w;
         }
@@ -734,8 +735,8 @@ hi_parent_kernel(const StepParams p)
     __syncthreads();
     hi_store_bonds(sm, state, N);
     if (mine) {
-        p.tsf_acc[m] = tsf;
-        if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += haz;
+        p.tsf_acc[m] = sums.tsf_sum();
+        if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += sums.hazard();
     }
     if (floored) atomicAdd(p.overext + c, (unsigned long long)floored);
 }

@@ -219,19 +219,19 @@ parent_kernel(const StepParams p)
     const bool isf_thr = (p.thr_mask & BD_CRIT_ISF) != 0;
     const bool isf_bell = (p.bell_mask & BD_CRIT_ISF) != 0;
     const T fc = (T)ch.f_c;
-    const double k0dt = ch.k0 * p.dt, dxs = ch.dx;
+    BellConst bk;
+    bk.load(ch.k0, p.dt, ch.dx);
 
     T* state = reinterpret_cast<T*>(p.state) + ch.state_off * 3;
     T* snap = reinterpret_cast<T*>(p.snap);
     T qx[L], qy[L], qz[L];
     load_bonds<T, L>(qx, qy, qz, state, lc);
 
-    // per-spring sampling state of this lane's springs; the time-average sum
-    // and the Bell hazard are accumulated in float64 whatever the integration
-    // precision (a float32 sum over a 1500-step window would lose about three
-    // digits of the TSF before the division)
-    double tsf[L];
-    double haz[L], rem[L];
+    // per-spring sampling state of this lane's springs: the time-average sum
+    // and the Bell hazard in float64, or float-float pairs with float32
+    // integration (a plain float32 sum over a 1500-step window would lose
+    // about three digits of the TSF before the division)
+    ParentSums<T> sums[L];
     // quiet: springs outside the criteria (the disulfide bonds of a vWF chain)
     uint32_t thr_done = 0, bell_done = 0, quiet = 0;
 #pragma unroll
@@ -239,9 +239,7 @@ parent_kernel(const StepParams p)
         const int i = lc.bead0 + j;
         const int64_t m = ch.spr_off + i;
         const bool v = active && i < nb;
-        tsf[j] = v ? p.tsf_acc[m] : 0.0;
-        haz[j] = 0.0;
-        rem[j] = v ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0;
+        sums[j].start(v ? p.tsf_acc[m] : 0.0, v ? p.exp1[CRIT_Q_ISF * M + m] - p.lam[CRIT_Q_ISF * M + m] : 0.0);
         if (ch.spring == BD_SPRING_VWF && (i & 1)) quiet |= 1u << j;
         if (!v || p.first_thr[CRIT_Q_ISF * M + m] >= 0) thr_done |= 1u << j;
         if (!v || p.first_bell[CRIT_Q_ISF * M + m] >= 0) bell_done |= 1u << j;
@@ -269,14 +267,14 @@ parent_kernel(const StepParams p)
                 if (i < nb) {
                     const T f = LJ ? rest_law_tension<T, FAST>(qx[j], qy[j], qz[j], (i & 1) == 0, k.H, kl, k.smin)
                                    : spring_tension<T, FAST>(qx[j], qy[j], qz[j], k.H, k.Hinvb, k.smin);
-                    tsf[j] += (double)f;
+                    sums[j].add_isf(f);
                     if (isf_thr && !(thr_done & (1u << j)) && f >= fc) {
                         thr_done |= 1u << j;
                         p.first_thr[CRIT_Q_ISF * M + ch.spr_off + i] = t + 1;
                     }
                     if (isf_bell && !(quiet & (1u << j))) {
-                        haz[j] = fma(k0dt, exp(dxs * (double)f), haz[j]);
-                        if (!(bell_done & (1u << j)) && haz[j] >= rem[j]) {
+                        const bool reached = sums[j].add_hazard(f, bk, p.lam + CRIT_Q_ISF * M + ch.spr_off + i);
+                        if (!(bell_done & (1u << j)) && reached) {
                             bell_done |= 1u << j;
                             p.first_bell[CRIT_Q_ISF * M + ch.spr_off + i] = t + 1;
                         }
@@ -292,14 +290,14 @@ parent_kernel(const StepParams p)
                     const int i = lc.bead0 + j;
                     if (i < nb) {
                         const int64_t m = ch.spr_off + i;
-                        p.tsf_hist[w * M + m] = tsf[j] / (double)p.S;
-                        tsf[j] = 0.0;
+                        p.tsf_hist[w * M + m] = sums[j].tsf_sum() / (double)p.S;
+                        double rem = 0.0;
                         if (isf_bell) {
-                            const double lam = p.lam[CRIT_Q_ISF * M + m] + haz[j];
+                            const double lam = p.lam[CRIT_Q_ISF * M + m] + sums[j].hazard();
                             p.lam[CRIT_Q_ISF * M + m] = lam;
-                            haz[j] = 0.0;
-                            rem[j] = p.exp1[CRIT_Q_ISF * M + m] - lam;
+                            rem = p.exp1[CRIT_Q_ISF * M + m] - lam;
                         }
+                        sums[j].next_window(rem);
                     }
                 }
             }
@@ -313,8 +311,8 @@ parent_kernel(const StepParams p)
             const int i = lc.bead0 + j;
             if (i < nb) {
                 const int64_t m = ch.spr_off + i;
-                p.tsf_acc[m] = tsf[j];
-                if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += haz[j];
+                p.tsf_acc[m] = sums[j].tsf_sum();
+                if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += sums[j].hazard();
             }
         }
     }
