@@ -313,13 +313,13 @@ struct Fields21 {
 // float64 memory and is advanced at every window end and launch end.
 struct BellConst {
     double k0dt, dx;     // k0 dt and dx of the chain's Bell law
-    float k0dtf, dxf;    // the same rounded to float32
+    float dxf, lnk;      // dx and ln(k0 dt) (-inf for k0 dt <= 0) in float32
     __device__ void load(double k0, double dt, double dx_)
     {
         k0dt = k0 * dt;
         dx = dx_;
-        k0dtf = (float)k0dt;
         dxf = (float)dx_;
+        lnk = k0dt > 0.0 ? (float)log(k0dt) : -INFINITY;
     }
 };
 
@@ -359,12 +359,14 @@ template <> struct ParentSums<double> {
 // renormalisation, so |lo| <= ulp(hi) / 2 and a sum of n terms is within
 // n 2^-47 max|partial sum| of the exact one (n 2^-53 for a float64 sum):
 // 1.1e-11 of the mean sample for a 1500-step window. The hazard increment
-// k0 dt e^(dx f) is taken in float32 (expf, within 2 ulp, and two product
-// roundings): about 1e-7 relative, two orders below the error of the float32
-// tension itself. An increment with dx f >= 80 (e^80 = 5.5e34, far past any
-// budget) takes the float64 exponential and goes straight into Lambda in
-// memory, the budget lowered by the same amount, so the pairs overflow only
-// where the float64 sums would.
+// k0 dt e^(dx f) = e^y, y = dx f + ln(k0 dt), is taken in float32 (three
+// roundings in y, about 1e-6 absolute for |y| up to 20, and expf within 2
+// ulp): about 1e-6 relative, an order below the error the float32 tension
+// itself brings. An increment outside e^(+-64) (e^64 = 6e27, far past any
+// budget; e^-64 = 2e-28, below float32's reach in a sum) takes the float64
+// exponential and goes straight into Lambda in memory, the budget lowered by
+// the same amount, so the pairs neither overflow nor flush tiny hazards to
+// zero where the float64 sums would not.
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float x)
 {
     const float s = __fadd_rn(hi, x);
@@ -392,9 +394,9 @@ template <> struct ParentSums<float> {
     __device__ __forceinline__ void add_isf(float f) { ff_add(t_hi, t_lo, f); }
     __device__ __forceinline__ bool add_hazard(float f, const BellConst& b, double* lam)
     {
-        const float x = __fmul_rn(b.dxf, f);
-        if (x < 80.0f) {
-            ff_add(h_hi, h_lo, __fmul_rn(b.k0dtf, expf(x)));
+        const float y = __fadd_rn(__fmul_rn(b.dxf, f), b.lnk);
+        if (fabsf(y) < 64.0f) {
+            ff_add(h_hi, h_lo, expf(y));
         } else {
             const double inc = b.k0dt * exp(b.dx * (double)f);
             *lam += inc;

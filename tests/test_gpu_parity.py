@@ -226,6 +226,31 @@ def test_events_and_kinetics(prec):
                                    rtol=1e-12)
 
 
+def test_fp32_isf_hazard_beyond_the_float32_range():
+    # A float32 run sums each step's ISF Bell increment k0 dt e^(dx f) in a
+    # float-float pair only while it lies within e^(+-64); larger ones (past
+    # float32 range once summed) and smaller ones (lost in a float32 sum) go
+    # to the float64 hazard directly. With k0 dt = 2e-40 and dx = 25 a
+    # tension below 1.08 gives the small ones, above 6.2 the large ones (and
+    # the events); hazards in log space and first passages as the oracle's,
+    # off the FENE floor.
+    b = 30.0
+    chains = [I.Chain(n_beads=8, n_replicas=2, spring=I.SPRING_FENE, flow=I.FLOW_UNIAXIAL, b=b,
+                      rate=0.3, f_c=1e9, k0=1e-37, dx=25.0),
+              I.Chain(n_beads=12, n_replicas=3, spring=I.SPRING_FENE, flow=I.FLOW_SHEAR, b=b,
+                      rate=1.0, f_c=1e9, k0=1e-37, dx=25.0)]
+    S, dt, n, seed = 10, 2e-3, 1000, 5
+    pos0 = I.initial_positions(I.custom(chains, dt, S, n), seed=3)
+    g = gpu_run(chains, dt, S, [n], seed, pos0, bdra.BD_PREC_FP32, thr=0, bell=1, want_all=False)
+    r = ora_run(chains, dt, S, n, seed, pos0, thr=0, bell=1)
+    assert r["overext"].sum() == 0
+    lam = r["lam"][0]
+    big = math.exp(64.0)
+    assert (lam > big).any() and (lam < big).any(), (lam.min(), lam.max())
+    counts = compare_events_fp32(g, r, chains, dt, S, seed, pos0, thr=0, bell=1)
+    assert counts["bell_equal"] >= 3, counts
+
+
 @pytest.mark.parametrize("prec,layout", [(bdra.BD_PREC_FP64, 0), (bdra.BD_PREC_FP32, 1),
                                          (bdra.BD_PREC_FP32, 2)])
 def test_identical_noise_replicas_reproduce_parent(prec, layout):
