@@ -181,17 +181,18 @@ def test_longest_collapsed_chain(prec):
                        stream=torch.cuda.current_stream().cuda_stream)
     ctx.step(30)
     pos = ctx.positions(False)
-    rsf = np.array([ctx.replica_average(w) for w in range(3)])
+    g = {"rsf": np.array([ctx.replica_average(w) for w in range(3)]),
+         "tsf": np.array([ctx.time_average(w) for w in range(3)])}
     ctx.close()
     assert _rel(pos, O.com_frame(r["pos"], [512]), [512]) <= TOL[prec]
-    assert np.abs(rsf - r["rsf"]).max() / np.abs(r["rsf"]).max() <= TOL[prec]
+    PE.check_profiles(g, r, ch, TOL[prec])
 
 
 def test_full_size_workloads_on_sampled_chains():
     # the bench's launch configurations (1024 collapsed chains; 128 with
     # hydrodynamic interaction; 64 vWF chains), float32, 300 steps; sampled
     # chains re-run alone by the oracle with their own chain ids in the noise
-    # counter
+    # counter: positions per chain, RSF and TSF per (chain, window) row
     import torch
     for wl, sample in ((I.collapsed_1024(n_steps=300), [0, 611, 1023]),
                        (I.collapsed_hi_128(n_steps=300), [5, 127]),
@@ -204,6 +205,7 @@ def test_full_size_workloads_on_sampled_chains():
         ctx.step(300)
         pos = ctx.positions(False)
         rsf = np.array([ctx.replica_average(w) for w in range(3)])
+        tsf = np.array([ctx.time_average(w) for w in range(3)])
         ctx.close()
         boff = I.bead_offsets(wl.chains)
         soff = I.spring_offsets(wl.chains)
@@ -214,5 +216,6 @@ def test_full_size_workloads_on_sampled_chains():
         got = np.concatenate([pos[boff[c]:boff[c + 1]] for c in sample])
         nb = [c.n_beads for c in sub]
         assert _rel(got, O.com_frame(r["pos"], nb), nb) <= 1e-4, wl.name
-        rs = np.concatenate([rsf[:, soff[c]:soff[c + 1]] for c in sample], axis=1)
-        assert np.abs(rs - r["rsf"]).max() / np.abs(r["rsf"]).max() <= 1e-4, wl.name
+        g = {k: np.concatenate([v[:, soff[c]:soff[c + 1]] for c in sample], axis=1)
+             for k, v in (("rsf", rsf), ("tsf", tsf))}
+        PE.check_profiles(g, r, sub, 1e-4)

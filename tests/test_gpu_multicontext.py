@@ -12,6 +12,7 @@ range with its global chain ids."""
 import numpy as np
 import pytest
 
+import parity_events as PE
 from oracle import oracle as O
 from paper_2206_05851_gb300 import bdra, shard
 from paper_2206_05851_gb300 import inputs as I
@@ -126,7 +127,7 @@ def test_range_matches_the_oracle_with_global_chain_ids():
     nb = [c.n_beads for c in sub]
     want = O.com_frame(r["pos"], nb)
     assert np.abs(g["pos"] - want).max() / np.abs(want).max() <= 1e-10
-    assert np.abs(g["rsf"] - r["rsf"]).max() / np.abs(r["rsf"]).max() <= 1e-10
+    PE.check_profiles(g, r, sub, 1e-10)
     np.testing.assert_array_equal(g["first_thr"], r["first_thr"])
     np.testing.assert_array_equal(g["first_bell"], r["first_bell"])
     # and the same range without the base draws other noise
