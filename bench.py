@@ -100,7 +100,12 @@ def plan_work(ctx, chains):
 # collapsed-chain kernel over its timed 3000 steps (its sample rows still sit in
 # L2 when it ends, so they are not in its count).
 REPLICA_TRAFFIC_BYTES = (172_927_744 + 853_351_168 + 129_504_768 + 486_531_584) / 2
-REPLICA_TRAFFIC_AT = ("fene_1024x_n100_r64_planar_wi5", 10_000)
+REPLICA_TRAFFIC_AT = ("fene_1024x_n100_r64_planar_wi5", 10_000, REPLICA_TRAFFIC_BYTES)
+# the Bell workload's replica kernel: the mean of one 25 000-step bench step's
+# five launches (53, 53, 53, 53 and 38 windows)
+BELL_TRAFFIC_BYTES = (894_479_104 + 1_680_933_632 + 889_691_648 + 1_676_391_168 + 885_231_616 +
+                      1_674_400_000 + 883_840_000 + 1_673_981_440 + 627_121_920 + 1_027_543_296) / 5
+BELL_TRAFFIC_AT = ("fene_16384x_n50_r32_uniaxial_wi10_bell", 25_000, BELL_TRAFFIC_BYTES)
 HI_TRAFFIC_BYTES = 4_345_600 + 760_832
 HI_TRAFFIC_AT = ("collapsed_hi_128x_n50_r50_shear30", 1500)
 COLLAPSED_TRAFFIC_BYTES = 33_043_456 + 667_904
@@ -471,7 +476,7 @@ def replica_line(wl, pos0, base, chunk, steps, warmup, sptr, autotune, issue_pea
     derived = SMS * LANES_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
             "unit": "T lane-instructions/s", "frac": achieved / issue_peak,
-            "traffic": REPLICA_TRAFFIC_BYTES if traffic_at and (wl.name, chunk) == traffic_at else None,
+            "traffic": traffic_at[2] if traffic_at and (wl.name, chunk) == traffic_at[:2] else None,
             "traffic_unit": "bytes per launch (ncu capture)",
             "kernel": "replica kernel (planner's float32 tile)", "avg_launch_ms": rep_ms / max(rep_n, 1),
             "launches": rep_n, "share_of_step": rep_ms / t_ms,
@@ -542,7 +547,7 @@ def batch_line(name, sptr, issue_peak, philox_peak, args):
         chunk, steps, autotune = 25_000, 4, False
     pos0 = I.initial_positions(wl)
     line, ctx = replica_line(wl, pos0, 0, chunk, steps, 1, sptr, autotune, issue_peak, philox_peak,
-                             keep_ctx=True, warm_chunk=1000)
+                             keep_ctx=True, warm_chunk=1000, traffic_at=BELL_TRAFFIC_AT)
     _, ft, fb = ctx.kinetics()
     ctx.close()
     line["config"]["run"] = (f"{chunk * steps} of the configuration's {wl.n_steps} steps" if
@@ -1101,7 +1106,8 @@ def main():
     wl = dataclasses.replace(wl_all, chains=chains)
     main_line, ctx = replica_line(wl, pos0, base, args.chunk, args.steps, args.warmup, sptr,
                                   args.autotune, issue_peak, philox_peak, dist if world > 1 else None,
-                                  traffic_at=REPLICA_TRAFFIC_AT, keep_ctx=True,
+                                  traffic_at=BELL_TRAFFIC_AT if args.workload == "bell_16384" else REPLICA_TRAFFIC_AT,
+                                  keep_ctx=True,
                                   lanes_hint=args.lanes_hint, layout_hint=args.layout_hint)
     out = {"metric": METRIC, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
