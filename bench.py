@@ -1106,7 +1106,8 @@ def main():
     wl = dataclasses.replace(wl_all, chains=chains)
     main_line, ctx = replica_line(wl, pos0, base, args.chunk, args.steps, args.warmup, sptr,
                                   args.autotune, issue_peak, philox_peak, dist if world > 1 else None,
-                                  traffic_at=BELL_TRAFFIC_AT if args.workload == "bell_16384" else REPLICA_TRAFFIC_AT,
+                                  traffic_at=None if world > 1 else (BELL_TRAFFIC_AT if args.workload == "bell_16384"
+                                                                     else REPLICA_TRAFFIC_AT),
                                   keep_ctx=True,
                                   lanes_hint=args.lanes_hint, layout_hint=args.layout_hint)
     out = {"metric": METRIC, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
