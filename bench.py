@@ -106,7 +106,7 @@ REPLICA_TRAFFIC_AT = ("fene_1024x_n100_r64_planar_wi5", 10_000, REPLICA_TRAFFIC_
 BELL_TRAFFIC_BYTES = (894_479_104 + 1_680_933_632 + 889_691_648 + 1_676_391_168 + 885_231_616 +
                       1_674_400_000 + 883_840_000 + 1_673_981_440 + 627_121_920 + 1_027_543_296) / 5
 BELL_TRAFFIC_AT = ("fene_16384x_n50_r32_uniaxial_wi10_bell", 25_000, BELL_TRAFFIC_BYTES)
-HI_TRAFFIC_BYTES = 4_345_600 + 760_832
+HI_TRAFFIC_BYTES = 5_221_632 + 256
 HI_TRAFFIC_AT = ("collapsed_hi_128x_n50_r50_shear30", 1500)
 COLLAPSED_TRAFFIC_BYTES = 33_043_456 + 667_904
 COLLAPSED_TRAFFIC_AT = ("collapsed_1024x_n50_r50_shear30", 3000)
@@ -687,6 +687,49 @@ def hi_flops_per_slot_step(n_beads):
     return n ** 3 / 3.0 + 2.0 * n * n + n * n
 
 
+def hi_tc_flops_per_slot_step(n_beads):
+    """Floating-point operations the tensor cores execute per slot-step in the
+    float32 factorisation of chains of up to 50 beads (an FMA as two): the
+    trailing block T (the last 3N - t0 <= 126 rows, t0 = 3 max(0, N - 42)) is
+    updated as M = 128 rows x N columns x K MMAs, three tf32 products per
+    float32 product; after the head (K = t0 rounded up to 8) and after every
+    32-column panel but the last (K = 32), over the next panel's 32 columns
+    and the rest of the 16-column-padded width."""
+    hb = max(0, n_beads - 42)
+    t0 = 3 * hb
+    m = 3 * n_beads - t0
+    width = (m + 15) // 16 * 16
+    panels = (m + 31) // 32
+    flops = 0.0
+    if t0 > 0:
+        flops += 3 * 2 * 128 * max(width, 32) * (8 * ((t0 + 7) // 8))
+    for pn in range(panels - 1):
+        c1 = 32 * (pn + 1)
+        flops += 3 * 2 * 128 * (32 + max(0, width - c1 - 32)) * 32
+    return flops
+
+
+def tf32_peak_tflops():
+    """Dense tf32 tensor peak: the measured bf16 GEMM rate (MEASURED_PEAKS.json,
+    burst) times the nominal tf32 / bf16 ratio 1.1 / 2.25."""
+    mp = measured_peaks()
+    return (mp.get("bf16_tflops") or 1900.0) * (1.1 / 2.25)
+
+
+def hi_tensor_roofline(n_beads, slot_steps, rep_ms):
+    """The tensor-core part of the float32 factorisation: the tf32 flops the
+    MMAs execute (hi_tc_flops_per_slot_step, six to seven times the useful
+    trailing-update flops: three products, the full square, padding) per second
+    of the replica kernel against the dense tf32 peak."""
+    if n_beads > 50:
+        return None
+    ach = hi_tc_flops_per_slot_step(n_beads) * slot_steps / (rep_ms / 1e3) / 1e12
+    peak = tf32_peak_tflops()
+    return {"achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "flops_per_slot_step": hi_tc_flops_per_slot_step(n_beads),
+            "peak_basis": "measured bf16 GEMM (MEASURED_PEAKS.json) x nominal tf32/bf16 1.1/2.25"}
+
+
 def hi_line(sptr, n_chains=0, n_steps=1500, fp64_chains=8, fp64_steps=100):
     """The paper's full model with RPY hydrodynamic interaction: float32
     throughput of one evolution window, the replica kernel against the float32
@@ -740,7 +783,8 @@ def hi_line(sptr, n_chains=0, n_steps=1500, fp64_chains=8, fp64_steps=100):
                        "avg_launch_ms": rep_ms / max(rep_n, 1), "launches": rep_n,
                        "share_of_step": rep_ms / (t * 1e3), "flops_per_slot_step": hi_flops_per_slot_step(N),
                        "peak_basis": "measured by bd_probe_fp32_fma on this GPU after the timed region",
-                       "peak_derived": derived, "frac_of_derived": achieved / derived}
+                       "peak_derived": derived, "frac_of_derived": achieved / derived,
+                       "tensor": hi_tensor_roofline(N, slot_steps, rep_ms)}
     out["parent_kernel_share"] = par_ms / (t * 1e3)
     # FP64 and the FP32 force error on a few chains (a short window so that
     # RSF samples exist)
@@ -830,7 +874,8 @@ def vwf_line(sptr, n_chains=0, windows=4):
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "hydrodynamic-interaction replica kernel (float32)",
                          "share_of_step": rep_ms / (t * 1e3), "launches": rep_n,
-                         "peak_basis": "measured by bd_probe_fp32_fma"},
+                         "peak_basis": "measured by bd_probe_fp32_fma",
+                         "tensor": hi_tensor_roofline(N, slot_steps, rep_ms)},
             "parent_kernel_share": par_ms / (t * 1e3),
             "cpu_baseline": {"value": bs / tc, "unit": "bead-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"first {len(sub)} chains, {n_cpu} steps ({tc:.1f} s wall, FP64)"},

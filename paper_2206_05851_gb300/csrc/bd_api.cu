@@ -87,6 +87,7 @@ struct bd_ctx {
     int64_t* d_first_bell = nullptr;
     double* d_exp1 = nullptr;
     unsigned long long* d_overext = nullptr;
+    int32_t* d_dev_err = nullptr;       // error bits set by kernels whose bounded waits gave up
     int64_t* d_evt_scratch = nullptr;
     int32_t* d_queue = nullptr;         // one work-item counter per variant launch
     // the step chunk as a CUDA graph: queue reset, parent kernels, one
@@ -520,7 +521,7 @@ bd_status plan(bd_ctx* ctx)
                 cudaGetLastError();
                 return fail(ctx, BD_E_CUDA, "hydrodynamic-interaction kernels: %s", cudaGetErrorString(e));
             }
-            vc.threads = kHIThreadsHost;
+            vc.threads = ctx->f64 ? hi_threads_f64(vc.variant == kHIBase) : hi_threads_f32(vc.variant == kHIBase);
             vc.grid = vc.item_count;
             vc.smem = ctx->f64 ? hi_smem_f64(vc.variant == kHIBase) : hi_smem_f32(vc.variant == kHIBase);
             continue;
@@ -550,7 +551,8 @@ bd_status plan(bd_ctx* ctx)
         const bool lj = !hi && key >= kParentLJKey;
         if (ctx->par_classes.empty() || ctx->par_classes.back().L != L || ctx->par_classes.back().lj != lj ||
             ctx->par_classes.back().hi != hi)
-            ctx->par_classes.push_back(ParClass{L, hi ? kHIThreadsHost : kParentThreads, 0,
+            ctx->par_classes.push_back(ParClass{L, hi ? (ctx->f64 ? hi_threads_f64(L == 0) : hi_threads_f32(L == 0))
+                                                      : kParentThreads, 0,
                                                 (int)ctx->h_parent_warps.size(), 0, lj, hi,
                                                 hi ? (ctx->f64 ? hi_smem_f64(L == 0) : hi_smem_f32(L == 0)) : 0});
         size_t e = k;
@@ -598,6 +600,7 @@ StepParams base_params(const bd_ctx* ctx)
     p.first_bell = ctx->d_first_bell;
     p.exp1 = ctx->d_exp1;
     p.overext = ctx->d_overext;
+    p.dev_err = ctx->d_dev_err;
     p.part_stride = ctx->part_stride;
     p.M = ctx->M;
     p.dt = ctx->cfg.dt;
@@ -1110,6 +1113,20 @@ bd_status adj_parents(bd_ctx* ctx, int kind, AdjParams a, cudaStream_t st)
     }
     return BD_OK;
 }
+// Kernels whose bounded waits gave up leave bits in the context's device
+// error word (StepParams::dev_err); the calls below that synchronise the
+// stream report them as BD_E_TIMEOUT.
+bd_status check_device_error(bd_ctx* ctx)
+{
+    int32_t e = 0;
+    BD_CUDA(ctx, cudaMemcpyAsync(&e, ctx->d_dev_err, sizeof(e), cudaMemcpyDeviceToHost, ctx->stream));
+    BD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (e)
+        return fail(ctx, BD_E_TIMEOUT, "a tensor-core completion wait gave up (device error bits 0x%x); "
+                    "the steps run since are not valid", (unsigned)e);
+    return BD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1202,6 +1219,12 @@ bd_status bd_create(const bd_config* cfg, const double* init_pos, bd_ctx** out)
         BD_TRY(dalloc(ctx, (void**)&ctx->d_first_bell, sizeof(int64_t) * 3 * (size_t)M));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_exp1, sizeof(double) * 3 * (size_t)M));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_overext, sizeof(unsigned long long) * (size_t)C));
+        BD_TRY(dalloc(ctx, (void**)&ctx->d_dev_err, sizeof(int32_t)));
+        if (cudaMemsetAsync(ctx->d_dev_err, 0, sizeof(int32_t), ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            s = fail(ctx, BD_E_CUDA, "device error word");
+            goto failed;
+        }
         BD_TRY(dalloc(ctx, (void**)&ctx->d_evt_scratch, sizeof(int64_t) * (size_t)(event_blocks(M) + 1)));
         BD_TRY(dalloc(ctx, (void**)&ctx->d_queue, sizeof(int32_t) * ctx->var_classes.size()));
         BD_TRY(build_graph(ctx));
@@ -1379,6 +1402,8 @@ bd_status bd_detect_events(bd_ctx* ctx, bd_event* out, int64_t capacity, int64_t
         if (s != BD_OK) return s;
     }
     *n_out = total;
+    s = check_device_error(ctx);
+    if (s != BD_OK) return s;
     if (total > capacity)
         return fail(ctx, BD_E_CAPACITY, "%lld events, capacity %lld", (long long)total,
                     (long long)capacity);
@@ -1451,6 +1476,8 @@ bd_status bd_get_info(bd_ctx* ctx, bd_info* out)
     BD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     int64_t tot = 0;
     for (unsigned long long v : ov) tot += (int64_t)v;
+    const bd_status se = check_device_error(ctx);
+    if (se != BD_OK) return se;
     out->n_springs = ctx->M;
     out->step = ctx->step;
     out->windows_done = ctx->step / ctx->cfg.window_steps;

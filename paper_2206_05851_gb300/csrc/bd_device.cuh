@@ -71,6 +71,9 @@ constexpr int32_t kLJBase = 200;
 // Chains with hydrodynamic interaction (Eqs. 1-3): one CTA per replica.
 constexpr int32_t kHIBase = 300;
 
+// Bits of StepParams::dev_err.
+enum { BD_DEV_ERR_TC_WAIT = 1 };   // a tensor-core completion wait gave up
+
 struct StepParams {
     const ChainDev* chains;
     const ItemDev* items;       // replica kernel: warp work items, longest first
@@ -89,6 +92,7 @@ struct StepParams {
     int64_t* first_bell;        // [3][M]
     const double* exp1;         // [3][M] Exp(1) thresholds
     unsigned long long* overext;  // [n_chains]
+    int32_t* dev_err;           // error bits of kernels whose bounded waits gave up (BD_DEV_ERR_*)
     // conformation diagnostics of Eq. 5 (with BD_FLAG_CONFORMATION)
     double* dbar;               // [max_windows][sum R][3] replica vs halted parent, bead mean
     double* dbead_part;         // [win_ring][bpart_stride][3] per-group per-bead sums

@@ -350,19 +350,22 @@ __device__ __forceinline__ void hi_cholesky(HITiles<T, MAXT>& tl, HIShared<T, NT
 }
 
 // Bead forces into sm.frc (springs and pair forces): four consecutive
-// threads a bead (N <= kHIThreads / 4), the pair sum split over them by
-// partner index mod 4 and combined by shuffles in a fixed order. Returns the
-// FENE floor count of the thread's spring (the bead's first thread).
-template <typename T, bool FAST, int NTM>
-__device__ __forceinline__ int hi_forces(HIShared<T, NTM>& sm, int N, const StepConst<T, FAST>& k,
-                                         const ChainDev& ch, bool harmonic, bool lj)
+// threads a bead (blockDim.x / 4 beads at a time), the pair sum split over
+// them by partner index mod 4 and combined by shuffles in a fixed order.
+// Returns the FENE floor count of the thread's springs (the bead's first
+// thread).
+template <typename T, bool FAST, typename SM>
+__device__ __forceinline__ int hi_forces(SM& sm, int N, const StepConst<T, FAST>& k,
+                                         const LJConst<T>& kl, bool harmonic, bool lj)
 {
-    const int b = threadIdx.x >> 2, q = threadIdx.x & 3;
     int floored = 0;
+    const int q = threadIdx.x & 3;
+#pragma unroll 1
+    for (int base = 0; base < N; base += (int)(blockDim.x >> 2)) {
+    const int b = base + (int)(threadIdx.x >> 2);
     T f[3] = {T(0), T(0), T(0)};
     if (b < N) {
         if (q == 0) {
-            const T r0 = (T)ch.r0;
             // springs b (to bead b+1) and b-1 (from bead b-1)
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
@@ -373,8 +376,6 @@ __device__ __forceinline__ int hi_forces(HIShared<T, NTM>& sm, int N, const Step
                 const T qz = sm.pos[3 * i + 5] - sm.pos[3 * i + 2];
                 T c;
                 if (harmonic) {          // the laws with a rest length (harmonic, vWF)
-                    LJConst<T> kl;
-                    kl.load(ch);
                     int fl = 0;
                     c = rest_law_coef<T, FAST>(qx, qy, qz, (i & 1) == 0, k.H, kl, k.smin, fl);
                     if (side == 0) floored += fl;
@@ -388,8 +389,6 @@ __device__ __forceinline__ int hi_forces(HIShared<T, NTM>& sm, int N, const Step
             }
         }
         if (lj) {
-            LJConst<T> kl;
-            kl.load(ch);
             const T x0 = sm.pos[3 * b], y0 = sm.pos[3 * b + 1], z0 = sm.pos[3 * b + 2];
 #pragma unroll 1
             for (int j = q; j < N; j += 4) {
@@ -410,12 +409,13 @@ __device__ __forceinline__ int hi_forces(HIShared<T, NTM>& sm, int N, const Step
         sm.frc[3 * b + 1] = f[1];
         sm.frc[3 * b + 2] = f[2];
     }
+    }
     return floored;
 }
 
 // Positions from bonds [nb][3] (bead 0 at the origin), then the COM shift.
-template <typename T, int NTM>
-__device__ __forceinline__ void hi_load_bonds(HIShared<T, NTM>& sm, const T* bonds, int N)
+template <typename T, typename SM>
+__device__ __forceinline__ void hi_load_bonds(SM& sm, const T* bonds, int N)
 {
     __syncthreads();     // every thread is done reading the old positions
     if (threadIdx.x < 3) {
@@ -435,8 +435,8 @@ __device__ __forceinline__ void hi_load_bonds(HIShared<T, NTM>& sm, const T* bon
     __syncthreads();
 }
 
-template <typename T, int NTM>
-__device__ __forceinline__ void hi_store_bonds(const HIShared<T, NTM>& sm, T* bonds, int N)
+template <typename T, typename SM>
+__device__ __forceinline__ void hi_store_bonds(const SM& sm, T* bonds, int N)
 {
     for (int e = threadIdx.x; e < 3 * (N - 1); e += blockDim.x) bonds[e] = sm.pos[e + 3] - sm.pos[e];
 }
@@ -444,13 +444,14 @@ __device__ __forceinline__ void hi_store_bonds(const HIShared<T, NTM>& sm, T* bo
 // One step t -> t + 1 of the CTA's slot. Returns the thread's floor count.
 template <typename T, bool FAST, int NTM, int MAXT>
 __device__ __forceinline__ int hi_step(HIShared<T, NTM>& sm, HITiles<T, MAXT>& tl, const ChainDev& ch,
-                                       const StepConst<T, FAST>& k, const StepParams& p, int N, int NT,
+                                       const StepConst<T, FAST>& k, const LJConst<T>& kl,
+                                       const StepParams& p, int N, int NT,
                                        uint32_t slot_key, uint32_t chain, uint32_t step, bool harmonic,
                                        bool lj)
 {
     const int n = 3 * N;
     const int tid = threadIdx.x;
-    const int floored = hi_forces<T, FAST, NTM>(sm, N, k, ch, harmonic, lj);
+    const int floored = hi_forces<T, FAST>(sm, N, k, kl, harmonic, lj);
     if (tid < N) {
         T z0, z1, z2;
         bead_noise<T, FAST>((uint32_t)tid, slot_key, step, chain, p, z0, z1, z2);
@@ -548,8 +549,8 @@ __device__ __forceinline__ int hi_step(HIShared<T, NTM>& sm, HITiles<T, MAXT>& t
 // (D-bar of this replica) and, for the chain's first replica, R_GZ of the
 // parent. The per-bead values go to the replica's own partial row (its
 // group), which the window fold averages over the replicas.
-template <typename T, int NTM>
-__device__ __forceinline__ void hi_conformation(HIShared<T, NTM>& sm, const ItemDev& it, const ChainDev& ch,
+template <typename T, typename SM>
+__device__ __forceinline__ void hi_conformation(SM& sm, const ItemDev& it, const ChainDev& ch,
                                                 const StepParams& p, int64_t w, int kglob)
 {
     const int N = ch.N;
@@ -580,20 +581,44 @@ __device__ __forceinline__ void hi_conformation(HIShared<T, NTM>& sm, const Item
     __syncthreads();
 }
 
+// The CUDA-core engine of a slot: W's lower 4 x 4 tiles in the registers
+// of the CTA's threads (hi_step). Engines give the kernel bodies below their
+// shared memory, their per-thread state and their step.
+template <typename T, bool FAST, int NTM> struct HITileEngine {
+    using Shared = HIShared<T, NTM>;
+    static constexpr int kMaxT = HIDims<NTM>::maxt;
+    HITiles<T, kMaxT> tl;
+    int NT;
+    __device__ __forceinline__ void begin(Shared& sm, int N)
+    {
+        NT = (3 * N + 3) / 4;
+        for (int e = threadIdx.x; e < 4 * NTM; e += blockDim.x) {
+            sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
+        }
+        hi_pairs_init(sm, N);
+        __syncthreads();
+        hi_tiles_init(tl, NT);
+    }
+    __device__ __forceinline__ int step(Shared& sm, const ChainDev& ch, const StepConst<T, FAST>& k,
+                                        const LJConst<T>& kl, const StepParams& p, int N, uint32_t key,
+                                        uint32_t chain, uint32_t t, bool harmonic, bool lj)
+    {
+        return hi_step<T, FAST, NTM, kMaxT>(sm, tl, ch, k, kl, p, N, NT, key, chain, t, harmonic, lj);
+    }
+    __device__ __forceinline__ bool failed() const { return false; }
+    __device__ __forceinline__ void end(Shared&, int32_t*) {}
+};
+
 // Replicas: one CTA per work item (one replica), the items of this launch in
 // p.items. Spawn from the window-start snapshot, S steps, one force sample per
 // spring at the window end into the replica's partial row (its group).
-template <typename T, bool FAST, int NTM>
-__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 3 : 1)
-hi_replica_kernel(const StepParams p)
+template <typename T, bool FAST, typename E>
+__device__ __forceinline__ void hi_replica_body(const StepParams& p, typename E::Shared& sm)
 {
-    constexpr int MAXT = HIDims<NTM>::maxt;
-    extern __shared__ __align__(16) unsigned char hi_smem_raw[];
-    HIShared<T, NTM>& sm = *reinterpret_cast<HIShared<T, NTM>*>(hi_smem_raw);
     if ((int)blockIdx.x >= p.n_items) return;
     const ItemDev it = p.items[blockIdx.x];
     const ChainDev ch = p.chains[it.chain];
-    const int N = ch.N, nb = N - 1, NT = (3 * N + 3) / 4;
+    const int N = ch.N, nb = N - 1;
     const bool harmonic = ch.spring == BD_SPRING_HARMONIC || ch.spring == BD_SPRING_VWF;
     LJConst<T> kl;
     kl.load(ch);
@@ -602,13 +627,8 @@ hi_replica_kernel(const StepParams p)
     const uint32_t key = (p.flags & BD_FLAG_IDENTICAL_NOISE) ? 0u : (uint32_t)kglob;
     StepConst<T, FAST> k;
     k.load(ch, p);
-    for (int e = threadIdx.x; e < 4 * NTM; e += blockDim.x) {
-        sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
-    }
-    hi_pairs_init(sm, N);
-    __syncthreads();
-    HITiles<T, MAXT> tl;
-    hi_tiles_init(tl, NT);
+    E eng;
+    eng.begin(sm, N);
     T* state = reinterpret_cast<T*>(p.state) + (ch.state_off + (int64_t)kglob * nb) * 3;
     const T* snap = reinterpret_cast<const T*>(p.snap);
     hi_load_bonds(sm, state, N);
@@ -619,8 +639,8 @@ hi_replica_kernel(const StepParams p)
 #pragma unroll 1
     for (int64_t t = p.t0; t < t_end; ++t) {
         if (s_in == 0) hi_load_bonds(sm, snap + ((w % p.win_ring) * p.M + ch.spr_off) * 3, N);
-        floored += hi_step<T, FAST, NTM, MAXT>(sm, tl, ch, k, p, N, NT, key, (uint32_t)it.chain + p.chain_base, (uint32_t)t,
-                                          harmonic, lj);
+        floored += eng.step(sm, ch, k, kl, p, N, key, (uint32_t)it.chain + p.chain_base, (uint32_t)t, harmonic, lj);
+        if (eng.failed()) break;
         if (++s_in == p.S) {
             s_in = 0;
             const int i = threadIdx.x;
@@ -632,10 +652,11 @@ hi_replica_kernel(const StepParams p)
                                      : spring_tension<T, FAST>(qx, qy, qz, k.H, k.Hinvb, k.smin);
                 p.part_hist[(w % p.win_ring) * p.part_stride + ch.part_off + (int64_t)it.group * nb + i] = (double)f;
             }
-            if (p.flags & BD_FLAG_CONFORMATION) hi_conformation(sm, it, ch, p, w, kglob);
+            if (p.flags & BD_FLAG_CONFORMATION) hi_conformation<T>(sm, it, ch, p, w, kglob);
             ++w;
         }
     }
+    eng.end(sm, p.dev_err);
     hi_store_bonds(sm, state, N);
     if (floored) atomicAdd(p.overext + it.chain, (unsigned long long)floored);
 }
@@ -643,30 +664,21 @@ hi_replica_kernel(const StepParams p)
 // Parents: one CTA per chain (p.parent_warps[blockIdx.x].first indexes
 // p.parent_items). Window-start snapshots, then per step the update and the
 // instantaneous force of every spring: TSF sums and the ISF criteria.
-template <typename T, bool FAST, int NTM>
-__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 3 : 1)
-hi_parent_kernel(const StepParams p)
+template <typename T, bool FAST, typename E>
+__device__ __forceinline__ void hi_parent_body(const StepParams& p, typename E::Shared& sm)
 {
-    constexpr int MAXT = HIDims<NTM>::maxt;
-    extern __shared__ __align__(16) unsigned char hi_smem_raw[];
-    HIShared<T, NTM>& sm = *reinterpret_cast<HIShared<T, NTM>*>(hi_smem_raw);
     if ((int)blockIdx.x >= p.n_parent_warps) return;
     const int c = p.parent_items[p.parent_warps[blockIdx.x].first];
     const ChainDev ch = p.chains[c];
-    const int N = ch.N, nb = N - 1, NT = (3 * N + 3) / 4;
+    const int N = ch.N, nb = N - 1;
     const bool harmonic = ch.spring == BD_SPRING_HARMONIC || ch.spring == BD_SPRING_VWF;
     LJConst<T> kl;
     kl.load(ch);
     const bool lj = ch.lj_u > 0.0;
     StepConst<T, FAST> k;
     k.load(ch, p);
-    for (int e = threadIdx.x; e < 4 * NTM; e += blockDim.x) {
-        sm.pos[e] = T(0); sm.frc[e] = T(0); sm.xi[e] = T(0);
-    }
-    hi_pairs_init(sm, N);
-    __syncthreads();
-    HITiles<T, MAXT> tl;
-    hi_tiles_init(tl, NT);
+    E eng;
+    eng.begin(sm, N);
     T* state = reinterpret_cast<T*>(p.state) + ch.state_off * 3;
     T* snap = reinterpret_cast<T*>(p.snap);
     hi_load_bonds(sm, state, N);
@@ -697,7 +709,8 @@ hi_parent_kernel(const StepParams p)
             // the parent's noise repeat the parent exactly
             hi_load_bonds(sm, row, N);
         }
-        floored += hi_step<T, FAST, NTM, MAXT>(sm, tl, ch, k, p, N, NT, 0u, (uint32_t)c + p.chain_base, (uint32_t)t, harmonic, lj);
+        floored += eng.step(sm, ch, k, kl, p, N, 0u, (uint32_t)c + p.chain_base, (uint32_t)t, harmonic, lj);
+        if (eng.failed()) break;
         if (mine) {
             const T qx = sm.pos[3 * i + 3] - sm.pos[3 * i];
             const T qy = sm.pos[3 * i + 4] - sm.pos[3 * i + 1];
@@ -732,6 +745,7 @@ hi_parent_kernel(const StepParams p)
             ++w;
         }
     }
+    eng.end(sm, p.dev_err);
     __syncthreads();
     hi_store_bonds(sm, state, N);
     if (mine) {
@@ -739,6 +753,22 @@ hi_parent_kernel(const StepParams p)
         if (isf_bell) p.lam[CRIT_Q_ISF * M + m] += sums.hazard();
     }
     if (floored) atomicAdd(p.overext + c, (unsigned long long)floored);
+}
+
+template <typename T, bool FAST, int NTM>
+__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 3 : 1)
+hi_replica_kernel(const StepParams p)
+{
+    extern __shared__ __align__(16) unsigned char hi_smem_raw[];
+    hi_replica_body<T, FAST, HITileEngine<T, FAST, NTM>>(p, *reinterpret_cast<HIShared<T, NTM>*>(hi_smem_raw));
+}
+
+template <typename T, bool FAST, int NTM>
+__global__ void __launch_bounds__(kHIThreads, (sizeof(T) == 4 && NTM <= kHINTSmall) ? 3 : 1)
+hi_parent_kernel(const StepParams p)
+{
+    extern __shared__ __align__(16) unsigned char hi_smem_raw[];
+    hi_parent_body<T, FAST, HITileEngine<T, FAST, NTM>>(p, *reinterpret_cast<HIShared<T, NTM>*>(hi_smem_raw));
 }
 
 }  // namespace bdra

@@ -24,6 +24,11 @@ size_t hi_smem_f64(bool small)
     return small ? sizeof(HIShared<double, kHINTSmall>) : sizeof(HIShared<double, kHINTMax>);
 }
 
+int hi_threads_f64(bool)
+{
+    return kHIThreads;
+}
+
 cudaError_t hi_prepare_f64()
 {
     for (int small = 0; small < 2; ++small) {

@@ -52,6 +52,8 @@ const void* hi_parent_func_f32(bool small);
 const void* hi_parent_func_f64(bool small);
 size_t hi_smem_f32(bool small);
 size_t hi_smem_f64(bool small);
+int hi_threads_f32(bool small);        // threads of a CTA of these kernels
+int hi_threads_f64(bool small);
 cudaError_t hi_prepare_f32();
 cudaError_t hi_prepare_f64();
 
