@@ -60,8 +60,18 @@ def _fene_set():
                     rate=0.5, f_c=3.0, k0=1.0, dx=0.2)]
 
 
+def _tc_shapes_set():
+    # the float32 tensor-core kernel's shapes besides 50 beads: the smallest
+    # head (43 beads: 3 head rows, one 8-deep head update), no head with a
+    # full 126-row trailing block (42), a partial last panel (33 beads: 99
+    # rows) and a 15-row head (47)
+    return [_collapsed(43, 2), _collapsed(42, 2, I.FLOW_NONE, 0.0), _collapsed(33, 2),
+            _collapsed(47, 2, I.FLOW_UNIAXIAL, 2.0)]
+
+
 SETS = {"collapsed": (_collapsed_set, 4e-5, 50, [20, 130, 150]),
-        "fene": (_fene_set, 1e-3, 50, [20, 130, 150])}
+        "fene": (_fene_set, 1e-3, 50, [20, 130, 150]),
+        "tc_shapes": (_tc_shapes_set, 4e-5, 50, [20, 130, 150])}
 
 
 def _gpu(chains, dt, S, steps, pos0, prec, seed=9, flags=0, thr=7, bell=7):
