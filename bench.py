@@ -1020,8 +1020,32 @@ def adjoint_line(sptr, n_chains=0, n_steps=0, grad_check=False):
            "value": bead_steps / (fwd + adj), "unit": "bead-steps/s (forward + adjoint)",
            "device_bytes": int(info.device_bytes),
            "grad_finite": bool(torch.isfinite(grad).all().item())}
+    # HBM roofline of the adjoint's stored replica states: every window's S + 1
+    # states of every slot's bonds (float32 x 3) written once by the
+    # replica-window kernel's forward sweep and read back once by its backward
+    # sweep; over the whole adjoint call (the replica-window kernel is about 84%
+    # of the adjoint's launch time in profiles/adjoint_fene256_n200_r32.md, so
+    # the kernel's own rate is higher)
+    slot_bonds = sum((ch.n_replicas + 1) * (ch.n_beads - 1) for ch in wl.chains)
+    stream_bytes = 2.0 * W * (S + 1) * slot_bonds * 3 * 4
+    mp = measured_peaks() or {}
+    hbm = mp.get("hbm_gbs") or 6800.0
+    out["roofline"] = {"bound": "hbm", "achieved": stream_bytes / adj / 1e9, "peak": hbm, "unit": "GB/s",
+                       "frac": stream_bytes / adj / 1e9 / hbm, "traffic": None,
+                       "bytes_per_adjoint": stream_bytes,
+                       "kernel": "adjoint call (replica-window kernel: forward recompute storing the states, "
+                                 "backward sweep over them)",
+                       "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)" if mp.get("hbm_gbs")
+                                     else "fallback 6.8 TB/s"}
     if grad_check:
-        out["errors_vs_oracle"] = adjoint_gradient_error(wl, sptr)
+        ev = adjoint_gradient_error(wl, sptr)
+        out["errors_vs_oracle"] = ev
+        out["cpu_baseline"] = {"value": ev["oracle_bead_steps"] / ev["oracle_seconds"],
+                               "unit": "bead-steps/s (forward + gradient)", "cores": ev["oracle_threads"],
+                               "kind": "oracle",
+                               "sample": f"{ev['sample']}: the FP64 oracle's forward run with its pathwise "
+                                         f"tangent in (rate, b, H), one thread a chain "
+                                         f"({ev['oracle_seconds']:.1f} s wall)"}
     return out
 
 
@@ -1067,7 +1091,8 @@ def adjoint_gradient_error(wl, sptr, n_steps=2000, sample=(0, 255)):
     return {"sample": f"chains {sample}, first {n_steps} steps ({W} windows, "
                       f"{n_steps // I.ADJOINT_CHECKPOINT_STEPS} checkpoint segments)",
             "grad_max_rel_err": {"rate": float(err[0]), "b": float(err[1]), "H": float(err[2])},
-            "oracle_seconds": t,
+            "oracle_seconds": t, "oracle_threads": len(sub),
+            "oracle_bead_steps": sum(ch.n_replicas * ch.n_beads for ch in sub) * n_steps,
             "precision": "GPU float32 adjoint (FP64 reductions) vs the FP64 oracle's tangent"}
 
 

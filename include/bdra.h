@@ -99,8 +99,13 @@ enum { BD_CRIT_ISF = 1, BD_CRIT_TSF = 2, BD_CRIT_RSF = 4 };
 /* BD_FLAG_IDENTICAL_NOISE: every replica draws the parent's noise (slot 0),
  * so replicas reproduce the parent exactly - a consistency check.
  * BD_FLAG_CONFORMATION: at every window end also compute the conformation
- * diagnostics of Eq. 5 (bd_conformation). */
-enum { BD_FLAG_IDENTICAL_NOISE = 1, BD_FLAG_CONFORMATION = 2 };
+ * diagnostics of Eq. 5 (bd_conformation).
+ * BD_FLAG_TEST_TC_STALL: failure test of the tensor-core kernels (float32
+ * chains with hydrodynamic interaction of up to 50 beads): they issue no MMA
+ * and no completion, so their bounded waits give up (about a second each);
+ * the results of such a run are invalid and bd_detect_events / bd_get_info
+ * return BD_E_TIMEOUT. No device fault or hang is involved. */
+enum { BD_FLAG_IDENTICAL_NOISE = 1, BD_FLAG_CONFORMATION = 2, BD_FLAG_TEST_TC_STALL = 4 };
 
 /* One parent chain with its replica set. */
 typedef struct {

@@ -26,6 +26,7 @@ BD_PREC_FP64, BD_PREC_FP32 = 0, 1
 BD_CRIT_ISF, BD_CRIT_TSF, BD_CRIT_RSF = 1, 2, 4
 BD_FLAG_IDENTICAL_NOISE = 1
 BD_FLAG_CONFORMATION = 2
+BD_FLAG_TEST_TC_STALL = 4
 
 
 class BdError(RuntimeError):

@@ -359,7 +359,7 @@ bd_status validate(bd_ctx* ctx, const bd_config* cfg)
     if (!(cfg->s_min > 0 && cfg->s_min < 1)) return fail(ctx, BD_E_INVALID, "s_min must be in (0, 1)");
     if ((cfg->thr_mask & ~7) || (cfg->bell_mask & ~7))
         return fail(ctx, BD_E_INVALID, "criterion masks use bits 0..2 only");
-    if (cfg->flags & ~(BD_FLAG_IDENTICAL_NOISE | BD_FLAG_CONFORMATION))
+    if (cfg->flags & ~(BD_FLAG_IDENTICAL_NOISE | BD_FLAG_CONFORMATION | BD_FLAG_TEST_TC_STALL))
         return fail(ctx, BD_E_INVALID, "unknown flags");
     if (cfg->checkpoint_steps < 0 || (cfg->checkpoint_steps > 0 && cfg->checkpoint_steps % cfg->window_steps))
         return fail(ctx, BD_E_INVALID, "checkpoint_steps must be 0 or a positive multiple of window_steps");

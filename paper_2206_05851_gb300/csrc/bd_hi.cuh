@@ -589,7 +589,7 @@ template <typename T, bool FAST, int NTM> struct HITileEngine {
     static constexpr int kMaxT = HIDims<NTM>::maxt;
     HITiles<T, kMaxT> tl;
     int NT;
-    __device__ __forceinline__ void begin(Shared& sm, int N)
+    __device__ __forceinline__ void begin(Shared& sm, int N, int32_t)
     {
         NT = (3 * N + 3) / 4;
         for (int e = threadIdx.x; e < 4 * NTM; e += blockDim.x) {
@@ -628,7 +628,7 @@ __device__ __forceinline__ void hi_replica_body(const StepParams& p, typename E:
     StepConst<T, FAST> k;
     k.load(ch, p);
     E eng;
-    eng.begin(sm, N);
+    eng.begin(sm, N, p.flags);
     T* state = reinterpret_cast<T*>(p.state) + (ch.state_off + (int64_t)kglob * nb) * 3;
     const T* snap = reinterpret_cast<const T*>(p.snap);
     hi_load_bonds(sm, state, N);
@@ -678,7 +678,7 @@ __device__ __forceinline__ void hi_parent_body(const StepParams& p, typename E::
     StepConst<T, FAST> k;
     k.load(ch, p);
     E eng;
-    eng.begin(sm, N);
+    eng.begin(sm, N, p.flags);
     T* state = reinterpret_cast<T*>(p.state) + ch.state_off * 3;
     T* snap = reinterpret_cast<T*>(p.snap);
     hi_load_bonds(sm, state, N);

@@ -71,6 +71,7 @@ struct TCState {
     uint32_t ph_next, ph_rest;
     bool pend_next, pend_rest;
     bool bad;            // a wait gave up
+    bool stall;          // BD_FLAG_TEST_TC_STALL: no MMA and no completion is issued
     int t0, m, hb, P;    // head rows, T rows, head beads, panels
 
     __device__ __forceinline__ void setup(int N)
@@ -247,8 +248,10 @@ __device__ __forceinline__ void tc_issue_update(HITCShared& sm, uint32_t tbase, 
 
 // The two-part update after a panel (or the head): next panel's columns
 // [c1, c1 + 32), then the rest up to the padded width of T. Thread 0 only.
-__device__ __forceinline__ void tc_issue_two(HITCShared& sm, uint32_t tbase, int c1, int m, int ks)
+// With `stall` (a failure test) nothing is issued, so the waits give up.
+__device__ __forceinline__ void tc_issue_two(HITCShared& sm, uint32_t tbase, int c1, int m, int ks, bool stall)
 {
+    if (stall) return;
     tc::fence_after_sync();
     tc_issue_update(sm, tbase, c1, 32, ks);
     tc::mma_commit(&sm.bar_next);
@@ -366,7 +369,7 @@ __device__ __forceinline__ int hi_tc_step(HITCShared& sm, TCState& ts, const Cha
         }
         tc::fence_async_smem();
         __syncthreads();
-        if (tid == 0) tc_issue_two(sm, ts.taddr, 0, m, (t0 + 7) >> 3);
+        if (tid == 0) tc_issue_two(sm, ts.taddr, 0, m, (t0 + 7) >> 3, ts.stall);
         ts.pend_next = ts.pend_rest = true;
     }
 
@@ -407,7 +410,7 @@ __device__ __forceinline__ int hi_tc_step(HITCShared& sm, TCState& ts, const Cha
             if (!head && warp > pn) tc_put_operand<8>(sm, tid, A, !valid);
             tc::fence_async_smem();
             __syncthreads();
-            if (tid == 0) tc_issue_two(sm, ts.taddr, c0 + 32, m, 4);
+            if (tid == 0) tc_issue_two(sm, ts.taddr, c0 + 32, m, 4, ts.stall);
             ts.pend_next = ts.pend_rest = true;
         } else {
             __syncthreads();       // every read of sm.lt done before the next step writes it
@@ -486,12 +489,13 @@ __device__ __forceinline__ void hi_tc_end(HITCShared& sm, TCState& ts, int32_t* 
 struct HITCEngine {
     using Shared = HITCShared;
     TCState ts;
-    __device__ __forceinline__ void begin(Shared& sm, int N)
+    __device__ __forceinline__ void begin(Shared& sm, int N, int32_t flags)
     {
         for (int e = threadIdx.x; e < 4 * kHINTSmall; e += blockDim.x) {
             sm.pos[e] = 0.0f; sm.frc[e] = 0.0f; sm.xi[e] = 0.0f;
         }
         hi_tc_begin(sm, ts, N);
+        ts.stall = (flags & BD_FLAG_TEST_TC_STALL) != 0;
     }
     __device__ __forceinline__ int step(Shared& sm, const ChainDev& ch, const StepConst<float, true>& k,
                                         const LJConst<float>& kl, const StepParams& p, int N, uint32_t key,

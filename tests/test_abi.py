@@ -129,7 +129,7 @@ def test_bad_chain_rejected_without_device(lib, field, value):
 
 @pytest.mark.parametrize("kw", [dict(dt=0.0), dict(window_steps=0), dict(precision=5),
                                 dict(max_windows=-1), dict(s_min=0.0), dict(thr_mask=8),
-                                dict(flags=4), dict(lanes_hint=3), dict(lanes_hint=2),
+                                dict(flags=8), dict(lanes_hint=3), dict(lanes_hint=2),
                                 dict(layout_hint=3),
                                 dict(layout_hint=2, precision=bdra.BD_PREC_FP64),
                                 dict(layout_hint=2, lanes_hint=13),
