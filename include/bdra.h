@@ -70,7 +70,8 @@ typedef enum {
     BD_E_OOM = 3,       /* device allocation failed */
     BD_E_STATE = 4,     /* call not valid in the context's current state */
     BD_E_TIMEOUT = 5,   /* a kernel's bounded wait on the tensor cores gave up (reported by
-                           bd_detect_events and bd_get_info; the steps run since are invalid) */
+                           bd_detect_events and bd_get_info, and again by every later call of
+                           theirs on the context: the steps run since are invalid) */
     BD_E_CAPACITY = 6   /* output or history capacity exceeded */
 } bd_status;
 
