@@ -131,21 +131,22 @@ __device__ __forceinline__ void tc_pairs_init(HITCShared& sm, int N)
     }
 }
 
-// Row r = 3 bi + x of W at the three columns of bead bj: W[r][3 bj + y].
-__device__ __forceinline__ void tc_w3(const HITCShared& sm, int bi, int x, int bj, float& w0, float& w1, float& w2)
+// Row r = 3 bi + x of W at the three columns of bead bj: W[r][3 bj + y],
+// zero unless `on`. Branch-free: the diagonal block reads any pair (the
+// first; N >= 2) and takes the identity by selects, and bj past the chain
+// is clamped for the read.
+__device__ __forceinline__ void tc_w3(const HITCShared& sm, int bi, int x, int bj, int N, bool on, float& w0,
+                                      float& w1, float& w2)
 {
-    if (bi == bj) {
-        w0 = x == 0 ? 1.0f : 0.0f;
-        w1 = x == 1 ? 1.0f : 0.0f;
-        w2 = x == 2 ? 1.0f : 0.0f;
-        return;
-    }
-    const int hi = bi > bj ? bi : bj, lo = bi > bj ? bj : bi;
-    const float4 e = sm.pe[hi * (hi - 1) / 2 + lo];
-    const float ex = x == 0 ? e.x : (x == 1 ? e.y : e.z);
-    w0 = __fmaf_rn(ex, e.x, x == 0 ? e.w : 0.0f);
-    w1 = __fmaf_rn(ex, e.y, x == 1 ? e.w : 0.0f);
-    w2 = __fmaf_rn(ex, e.z, x == 2 ? e.w : 0.0f);
+    const int bc = bj < N ? bj : N - 1;
+    const int hi = bi > bc ? bi : bc, lo = bi > bc ? bc : bi;
+    const bool same = hi == lo;
+    const float4 e = sm.pe[same ? 0 : hi * (hi - 1) / 2 + lo];
+    const float ex = same ? 0.0f : (x == 0 ? e.x : (x == 1 ? e.y : e.z));
+    const float ci = same ? 1.0f : e.w;
+    w0 = on ? __fmaf_rn(ex, e.x, x == 0 ? ci : 0.0f) : 0.0f;
+    w1 = on ? __fmaf_rn(ex, e.y, x == 1 ? ci : 0.0f) : 0.0f;
+    w2 = on ? __fmaf_rn(ex, e.z, x == 2 ? ci : 0.0f) : 0.0f;
 }
 
 // Lower Cholesky factor of a K x K block held one row a lane (A[j], j < K;
@@ -295,7 +296,8 @@ __device__ __forceinline__ int hi_tc_step(HITCShared& sm, TCState& ts, const Cha
     const bool valid = head ? lane < t0 : tid < m;
     const int bi = valid ? row / 3 : 0, x = valid ? row - 3 * (row / 3) : 0;
     float A[32];
-    float u = 0.0f, w = 0.0f;
+    float w = 0.0f;
+    float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;     // (W F)_row over the columns of each component
     if (!head) {
 #pragma unroll 1
         for (int q = 0; q < 6; ++q) {         // TMEM columns [24 q, 24 q + 24): beads hb + 8 q ..
@@ -303,13 +305,12 @@ __device__ __forceinline__ int hi_tc_step(HITCShared& sm, TCState& ts, const Cha
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
                 const int bj = hb + 8 * q + b;
-                float w0 = 0.0f, w1 = 0.0f, w2 = 0.0f;
-                if (valid && bj < N) {
-                    tc_w3(sm, bi, x, bj, w0, w1, w2);
-                    u = __fmaf_rn(w0, sm.frc[3 * bj], u);
-                    u = __fmaf_rn(w1, sm.frc[3 * bj + 1], u);
-                    u = __fmaf_rn(w2, sm.frc[3 * bj + 2], u);
-                }
+                float w0, w1, w2;
+                tc_w3(sm, bi, x, bj, N, valid && bj < N, w0, w1, w2);
+                const int fb = 3 * (bj < N ? bj : N - 1);
+                u0 = __fmaf_rn(w0, sm.frc[fb], u0);
+                u1 = __fmaf_rn(w1, sm.frc[fb + 1], u1);
+                u2 = __fmaf_rn(w2, sm.frc[fb + 2], u2);
                 V[3 * b] = w0; V[3 * b + 1] = w1; V[3 * b + 2] = w2;
             }
             tc::tmem_st8(ts.taddr + 24 * q, V);
@@ -319,26 +320,26 @@ __device__ __forceinline__ int hi_tc_step(HITCShared& sm, TCState& ts, const Cha
             }
         }
     } else if (valid) {
-#pragma unroll 1
+#pragma unroll 4
         for (int bj = hb; bj < N; ++bj) {
             float w0, w1, w2;
-            tc_w3(sm, bi, x, bj, w0, w1, w2);
-            u = __fmaf_rn(w0, sm.frc[3 * bj], u);
-            u = __fmaf_rn(w1, sm.frc[3 * bj + 1], u);
-            u = __fmaf_rn(w2, sm.frc[3 * bj + 2], u);
+            tc_w3(sm, bi, x, bj, N, true, w0, w1, w2);
+            u0 = __fmaf_rn(w0, sm.frc[3 * bj], u0);
+            u1 = __fmaf_rn(w1, sm.frc[3 * bj + 1], u1);
+            u2 = __fmaf_rn(w2, sm.frc[3 * bj + 2], u2);
         }
     }
 #pragma unroll
     for (int b = 0; b < kTCHeadBeads; ++b) {
-        float w0 = 0.0f, w1 = 0.0f, w2 = 0.0f;
-        if (valid && b < hb) {
-            tc_w3(sm, bi, x, b, w0, w1, w2);
-            u = __fmaf_rn(w0, sm.frc[3 * b], u);
-            u = __fmaf_rn(w1, sm.frc[3 * b + 1], u);
-            u = __fmaf_rn(w2, sm.frc[3 * b + 2], u);
-        }
+        float w0, w1, w2;
+        tc_w3(sm, bi, x, b, N, valid && b < hb, w0, w1, w2);
+        const int fb = 3 * (b < N ? b : N - 1);
+        u0 = __fmaf_rn(w0, sm.frc[fb], u0);
+        u1 = __fmaf_rn(w1, sm.frc[fb + 1], u1);
+        u2 = __fmaf_rn(w2, sm.frc[fb + 2], u2);
         A[3 * b] = w0; A[3 * b + 1] = w1; A[3 * b + 2] = w2;
     }
+    const float u = __fadd_rn(__fadd_rn(u0, u1), u2);
 #pragma unroll
     for (int j = 3 * kTCHeadBeads; j < 32; ++j) A[j] = 0.0f;
     if (head && !valid) {        // identity rows below the head block
