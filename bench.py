@@ -803,13 +803,19 @@ def hi_line(sptr, n_chains=0, n_steps=1500, fp64_chains=8, fp64_steps=100):
     sub = wl.chains[:cores]
     psub = pos0[:sum(c.n_beads for c in sub)]
     n_cpu = 600          # about 10 s of oracle work on 16 cores
+    s_cmp = 100          # windows of the comparison run (RSF rows to compare)
     tc = time.perf_counter()
-    O.run(sub, wl.dt, S, n_cpu, wl.seed, psub, thr_mask=0, bell_mask=0, n_threads=cores,
-          want_replicas=False, chain_ids=list(range(len(sub))))
+    r = O.run(sub, wl.dt, s_cmp, n_cpu, wl.seed, psub, thr_mask=0, bell_mask=0, n_threads=cores,
+              want_replicas=False, chain_ids=list(range(len(sub))))
     tc = time.perf_counter() - tc
     bs = sum(c.n_replicas * c.n_beads for c in sub) * n_cpu
     out["cpu_baseline"] = {"value": bs / tc, "unit": "bead-steps/s", "cores": cores, "kind": "oracle",
-                           "sample": f"first {len(sub)} chains, {n_cpu} steps ({tc:.1f} s wall, FP64)"}
+                           "sample": f"first {len(sub)} chains, {n_cpu} steps in windows of {s_cmp} "
+                                     f"({tc:.1f} s wall, FP64)"}
+    # the float32 tensor-core path on the same chains, windows and steps
+    import dataclasses
+    cmp_wl = dataclasses.replace(wl, chains=list(sub), window_steps=s_cmp, thr_mask=0, bell_mask=0)
+    out["errors_vs_oracle"] = errors_vs_oracle(cmp_wl, r, list(range(len(sub))), psub, n_cpu, sptr)
     return out
 
 
