@@ -9,7 +9,8 @@ runs the kernel's schedule in numpy - the head columns (t0 = 3 max(0, N - 42)
 rows) factored and solved in float32, the trailing block updated with their
 outer product, then 32-column panels of the trailing block, each diagonal
 block factored and the rows below solved in float32 and the rest of the
-block updated - on the oracle's tensor of collapsed-chain conformations, and
+block updated - on the oracle's tensor of collapsed-chain and vWF-chain
+conformations, and
 compares the factor with the float64 Cholesky factor of the same tensor:
 
 - with three tf32 products the factor has float32-class accuracy (about
@@ -95,14 +96,15 @@ def _tc_schedule(W, N, split):
     return L
 
 
-def _conformation(N, seed):
-    ch = I.collapsed_chain(2, n_beads=N)
+def _conformation(N, seed, vwf=False):
+    ch = I.vwf_chain(2, n_beads=N) if vwf else I.collapsed_chain(2, n_beads=N)
     return I.initial_positions(I.custom([ch], 1e-5, 10, 10), seed=seed)
 
 
-@pytest.mark.parametrize("N,seed", [(12, 1), (20, 8), (33, 2), (42, 7), (43, 3), (50, 4), (50, 5)])
-def test_three_tf32_products_keep_float32_accuracy(N, seed):
-    W = O.rpy_matrix(1.0, _conformation(N, seed))
+@pytest.mark.parametrize("N,seed,vwf", [(12, 1, False), (20, 8, False), (33, 2, False), (42, 7, False),
+                                        (43, 3, False), (50, 4, False), (50, 5, False), (50, 6, True)])
+def test_three_tf32_products_keep_float32_accuracy(N, seed, vwf):
+    W = O.rpy_matrix(1.0, _conformation(N, seed, vwf))
     L64 = np.linalg.cholesky(W)
     scale = np.abs(L64).max()
     e32 = np.abs(_chol32(W).astype(np.float64) - L64).max() / scale
