@@ -869,11 +869,16 @@ def vwf_line(sptr, n_chains=0, windows=4):
     sub = wl.chains[:cores]
     psub = pos0[:sum(ch.n_beads for ch in sub)]
     n_cpu = 300
+    s_cmp = 100          # windows of the comparison run (RSF rows to compare)
     tc = time.perf_counter()
-    O.run(sub, wl.dt, S, n_cpu, wl.seed, psub, thr_mask=0, bell_mask=I.CRIT_ALL, n_threads=cores,
-          want_replicas=False, chain_ids=list(range(len(sub))))
+    r = O.run(sub, wl.dt, s_cmp, n_cpu, wl.seed, psub, thr_mask=0, bell_mask=I.CRIT_ALL, n_threads=cores,
+              want_replicas=False, chain_ids=list(range(len(sub))))
     tc = time.perf_counter() - tc
     bs = sum(ch.n_replicas * ch.n_beads for ch in sub) * n_cpu
+    # the float32 tensor-core path on the same chains, windows and steps
+    import dataclasses
+    cmp_wl = dataclasses.replace(wl, chains=list(sub), window_steps=s_cmp, thr_mask=0, bell_mask=I.CRIT_ALL)
+    ev = errors_vs_oracle(cmp_wl, r, list(range(len(sub))), psub, n_cpu, sptr)
     return {"workload": wl.name, "steps": n, "windows": windows, "window_steps": S,
             "value": wl.bead_steps(n) / t, "unit": "bead-steps/s",
             "roofline": {"bound": "alu (float32 FMA)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -884,7 +889,9 @@ def vwf_line(sptr, n_chains=0, windows=4):
                          "tensor": hi_tensor_roofline(N, slot_steps, rep_ms)},
             "parent_kernel_share": par_ms / (t * 1e3),
             "cpu_baseline": {"value": bs / tc, "unit": "bead-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {len(sub)} chains, {n_cpu} steps ({tc:.1f} s wall, FP64)"},
+                             "sample": f"first {len(sub)} chains, {n_cpu} steps in windows of {s_cmp} "
+                                       f"({tc:.1f} s wall, FP64)"},
+            "errors_vs_oracle": ev,
             "precision": "FP32 integrate, FP64 reduce and hazards",
             "mftu_s": mftu,
             "mean_a2_force_pN": {"RSF": float(rsf[:, a2].mean() * I.VWF_FORCE_UNIT_PN),
